@@ -1,0 +1,292 @@
+"""FP64 CPU oracle for the MAC and nodal projections (plain C, loaded with ctypes).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference legs may import this package.  The CUDA
+library never calls it and shares no code, header or table with it.
+
+Arrays are float64 numpy arrays in x-fastest order (numpy shape (nz, ny, nx));
+MAC face arrays carry n_d + 1 entries along their own direction, nodal arrays
+have n nodes on a periodic axis and n + 1 on a wall axis.
+
+Functions without a pin in the CPU tests: none.  Readings of the paper are
+listed in the C sources' headers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["oracle.c", "oracle_nodal.c"]
+
+PERIODIC, NEUMANN, DIRICHLET = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/liboracle.so (portable C, -O2)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Geom(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double), ("lo", C.c_int * 3), ("hi", C.c_int * 3)]
+
+
+_lib = None
+_P = C.POINTER(C.c_double)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        G = C.POINTER(_Geom)
+        sig = {
+            "or_fill_planar": (C.c_int, [G, _P, C.c_int, _P]),
+            "or_fill_spherical": (C.c_int, [G, _P, C.c_int, C.c_double, _P, _P]),
+            "or_mac_coeffs": (None, [G, _P, _P, _P, _P, _P]),
+            "or_mac_apply": (None, [G, _P, _P, _P, _P, _P]),
+            "or_mac_divergence": (None, [G, _P, _P, _P, _P, _P]),
+            "or_mac_rhs": (None, [G, _P, _P, _P, _P, _P, C.c_int, _P, _P]),
+            "or_mac_correct": (None, [G, _P, _P, _P, _P, _P]),
+            "or_mac_solve": (C.c_int, [G, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P]),
+            "or_mac_dense_solve": (C.c_int, [G, _P, _P, _P, _P, _P]),
+            "or_mac_project": (C.c_int, [G, _P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int, _P]),
+            "or_nd_nnode": (C.c_long, [G]),
+            "or_nd_weights": (None, [G, _P]),
+            "or_nd_apply": (None, [G, _P, _P, _P]),
+            "or_nd_divergence": (None, [G, _P, _P, _P, _P]),
+            "or_nd_gradient": (None, [G, _P, _P, _P, _P]),
+            "or_nd_rhs": (None, [G, _P, _P, _P, _P, _P, C.c_int, _P, _P]),
+            "or_nd_correct": (None, [G, _P, _P, _P, _P, _P]),
+            "or_nd_solve": (C.c_int, [G, _P, _P, _P, C.c_double, C.c_int, _P]),
+            "or_nd_dense_solve": (C.c_int, [G, _P, _P, _P]),
+            "or_nd_project": (C.c_int, [G, _P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _g(geom):
+    g = _Geom()
+    for d in range(3):
+        g.n[d] = int(geom.n[d])
+        g.lo[d] = int(geom.lo[d])
+        g.hi[d] = int(geom.hi[d])
+    g.h = float(geom.dx)
+    return C.byref(g)
+
+
+def _arr(a):
+    """float64, C-contiguous numpy copy/view of a numpy array or CPU torch tensor."""
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(_P)
+
+
+def face_shape(geom, d):
+    nx, ny, nz = geom.n
+    return [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][d]
+
+
+def cell_shape(geom):
+    return (geom.n[2], geom.n[1], geom.n[0])
+
+
+def node_shape(geom):
+    m = [geom.n[d] + (0 if geom.lo[d] == PERIODIC else 1) for d in range(3)]
+    return (m[2], m[1], m[0])
+
+
+def singular(geom):
+    return all(geom.lo[d] != DIRICHLET and geom.hi[d] != DIRICHLET for d in range(3))
+
+
+# --- Fill -------------------------------------------------------------------------
+
+def fill(geom, prof, spherical=False, dr=None, center=(0.5, 0.5, 0.5)):
+    lib = _load()
+    prof = _arr(prof)
+    out = np.empty(cell_shape(geom))
+    if spherical:
+        c = np.ascontiguousarray(center, dtype=np.float64)
+        rc = lib.or_fill_spherical(_g(geom), _p(prof), prof.size, float(dr), _p(c), _p(out))
+    else:
+        rc = lib.or_fill_planar(_g(geom), _p(prof), prof.size, _p(out))
+    if rc:
+        raise ValueError("oracle fill: profile too short")
+    return out
+
+
+# --- MAC ----------------------------------------------------------------------------
+
+def mac_coeffs(geom, rho, beta0):
+    lib = _load()
+    b = [np.empty(face_shape(geom, d)) for d in range(3)]
+    lib.or_mac_coeffs(_g(geom), _p(_arr(rho)), _p(_arr(beta0)), _p(b[0]), _p(b[1]), _p(b[2]))
+    return b
+
+
+def mac_apply(geom, b, phi):
+    lib = _load()
+    b = [_arr(x) for x in b]
+    out = np.empty(cell_shape(geom))
+    lib.or_mac_apply(_g(geom), _p(b[0]), _p(b[1]), _p(b[2]), _p(_arr(phi)), _p(out))
+    return out
+
+
+def mac_divergence(geom, u, beta0):
+    lib = _load()
+    u = [_arr(x) for x in u]
+    out = np.empty(cell_shape(geom))
+    lib.or_mac_divergence(_g(geom), _p(u[0]), _p(u[1]), _p(u[2]), _p(_arr(beta0)), _p(out))
+    return out
+
+
+def mac_rhs(geom, u, beta0, sbar, remove_mean=True):
+    lib = _load()
+    u = [_arr(x) for x in u]
+    f = np.empty(cell_shape(geom))
+    m = C.c_double(0.0)
+    lib.or_mac_rhs(_g(geom), _p(u[0]), _p(u[1]), _p(u[2]), _p(_arr(beta0)), _p(_arr(sbar)),
+                   int(bool(remove_mean)), _p(f), C.byref(m))
+    return f, m.value
+
+
+def mac_correct(geom, rho, phi, u):
+    lib = _load()
+    u = [_arr(x).copy() for x in u]
+    lib.or_mac_correct(_g(geom), _p(_arr(rho)), _p(_arr(phi)), _p(u[0]), _p(u[1]), _p(u[2]))
+    return u
+
+
+def mac_solve(geom, b, f, phi0=None, tol=1e-13, maxit=200):
+    """MG-preconditioned CG; returns (phi, iterations, relative residual)."""
+    lib = _load()
+    b = [_arr(x) for x in b]
+    phi = np.zeros(cell_shape(geom)) if phi0 is None else _arr(phi0).copy()
+    rr = C.c_double(0.0)
+    it = lib.or_mac_solve(_g(geom), _p(b[0]), _p(b[1]), _p(b[2]), _p(_arr(f)), _p(phi),
+                          float(tol), int(maxit), C.byref(rr))
+    if it == -2:
+        raise RuntimeError("oracle mac_solve: coarse factorisation failed")
+    return phi, it, rr.value
+
+
+def mac_dense_solve(geom, b, f):
+    lib = _load()
+    b = [_arr(x) for x in b]
+    phi = np.zeros(cell_shape(geom))
+    rc = lib.or_mac_dense_solve(_g(geom), _p(b[0]), _p(b[1]), _p(b[2]), _p(_arr(f)), _p(phi))
+    if rc:
+        raise RuntimeError(f"oracle dense solve failed ({rc})")
+    return phi
+
+
+def mac_project(geom, u, rho, beta0, sbar, tol=1e-13, maxit=200, remove_mean=True, phi0=None):
+    """Full MAC projection.  Returns (u_new, phi, info dict)."""
+    lib = _load()
+    u = [_arr(x).copy() for x in u]
+    phi = np.zeros(cell_shape(geom)) if phi0 is None else _arr(phi0).copy()
+    out = np.zeros(4)
+    rc = lib.or_mac_project(_g(geom), _p(u[0]), _p(u[1]), _p(u[2]), _p(_arr(rho)), _p(_arr(beta0)),
+                            _p(_arr(sbar)), _p(phi), float(tol), int(maxit), int(bool(remove_mean)), _p(out))
+    info = dict(mean=out[0], rel_resid=out[1], div_err=out[2], iters=int(out[3]), ok=(rc == 0))
+    return u, phi, info
+
+
+# --- nodal -------------------------------------------------------------------------
+
+def nd_weights(geom):
+    lib = _load()
+    w = np.empty(node_shape(geom))
+    lib.or_nd_weights(_g(geom), _p(w))
+    return w
+
+
+def nd_apply(geom, sigma, phi):
+    lib = _load()
+    out = np.empty(node_shape(geom))
+    lib.or_nd_apply(_g(geom), _p(_arr(sigma)), _p(_arr(phi)), _p(out))
+    return out
+
+
+def nd_divergence(geom, v):
+    lib = _load()
+    v = [_arr(x) for x in v]
+    out = np.empty(node_shape(geom))
+    lib.or_nd_divergence(_g(geom), _p(v[0]), _p(v[1]), _p(v[2]), _p(out))
+    return out
+
+
+def nd_gradient(geom, phi):
+    lib = _load()
+    G = [np.empty(cell_shape(geom)) for _ in range(3)]
+    lib.or_nd_gradient(_g(geom), _p(_arr(phi)), _p(G[0]), _p(G[1]), _p(G[2]))
+    return G
+
+
+def nd_rhs(geom, u, beta0, sbar, remove_mean=True):
+    lib = _load()
+    u = [_arr(x) for x in u]
+    f = np.empty(node_shape(geom))
+    m = C.c_double(0.0)
+    lib.or_nd_rhs(_g(geom), _p(u[0]), _p(u[1]), _p(u[2]), _p(_arr(beta0)), _p(_arr(sbar)),
+                  int(bool(remove_mean)), _p(f), C.byref(m))
+    return f, m.value
+
+
+def nd_correct(geom, rho, phi, u):
+    lib = _load()
+    u = [_arr(x).copy() for x in u]
+    lib.or_nd_correct(_g(geom), _p(_arr(rho)), _p(_arr(phi)), _p(u[0]), _p(u[1]), _p(u[2]))
+    return u
+
+
+def nd_solve(geom, sigma, f, phi0=None, tol=1e-13, maxit=300):
+    lib = _load()
+    phi = np.zeros(node_shape(geom)) if phi0 is None else _arr(phi0).copy()
+    rr = C.c_double(0.0)
+    it = lib.or_nd_solve(_g(geom), _p(_arr(sigma)), _p(_arr(f)), _p(phi), float(tol), int(maxit), C.byref(rr))
+    if it == -2:
+        raise RuntimeError("oracle nd_solve: coarse factorisation failed")
+    return phi, it, rr.value
+
+
+def nd_dense_solve(geom, sigma, f):
+    lib = _load()
+    phi = np.zeros(node_shape(geom))
+    rc = lib.or_nd_dense_solve(_g(geom), _p(_arr(sigma)), _p(_arr(f)), _p(phi))
+    if rc:
+        raise RuntimeError(f"oracle nodal dense solve failed ({rc})")
+    return phi
+
+
+def nd_project(geom, u, rho, beta0, sbar, tol=1e-13, maxit=300, phi0=None):
+    lib = _load()
+    u = [_arr(x).copy() for x in u]
+    phi = np.zeros(node_shape(geom)) if phi0 is None else _arr(phi0).copy()
+    out = np.zeros(4)
+    rc = lib.or_nd_project(_g(geom), _p(u[0]), _p(u[1]), _p(u[2]), _p(_arr(rho)), _p(_arr(beta0)),
+                           _p(_arr(sbar)), _p(phi), float(tol), int(maxit), _p(out))
+    info = dict(mean=out[0], rel_resid=out[1], div_err=out[2], iters=int(out[3]), ok=(rc == 0))
+    return u, phi, info
