@@ -1,0 +1,371 @@
+"""Benchmark: MAC projection solves/s to 1e-10 relative residual on the planar
+256^3 workload (periodic x,y, walls in z, density contrast 1e5,
+beta0 = rho0^(3/5), 16 Fourier modes, 3 hotspots; seeded synthetic inputs),
+FP32 V-cycles inside FP64 iterative refinement, with the plain FP64 solve
+beside it.
+
+One step = one pass of the whole hot path: base-state Fill of beta0, face
+coefficients and the multigrid hierarchy, right-hand side with mean removal,
+the refinement loop (FP64 residual, FP32 V-cycle, FP64 update) to 1e-10, mean
+normalisation, the velocity correction and the divergence check.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MAC projection solves/s to 1e-10 rel residual (planar 256^3, mixed FP32/FP64)"
+UNIT = "solves/s"
+WORKLOAD = "planar256"
+N = 256
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mx", choices=["mx", "reference"])
+    p.add_argument("--n", type=int, default=N, help="cube edge of the planar workload")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+
+def algorithmic_bytes_per_cell():
+    """Compulsory DRAM bytes per finest-level cell of each traced phase
+    (FP32 V-cycle arrays w = 4 B, FP64 arrays 8 B).
+      smooth_fine   (one colour pass of red-black Gauss-Seidel, half a sweep):
+                    a full sweep reads e, f, bx, by, bz and writes e = 6 x 4 B,
+                    so one colour pass = 12 B/cell
+      resid64       read phi, f, bx, by, bz (8 B each), write rhat (4 B) = 44 B
+    """
+    return {"smooth_fine": 12.0, "resid64": 44.0}
+
+
+def setup_inputs(mx, W, dev, n, copies):
+    import torch
+    w = W.planar256(device=dev, n=n)
+    g = w.geom
+    us = [[t.clone() for t in w.u] for _ in range(copies)]
+    return w, g, us
+
+
+def run_mx(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    from paper_1908_03634_gb300 import build as B
+    B.build()
+    import paper_1908_03634_gb300 as mx
+    from paper_1908_03634_gb300 import workloads as W
+
+    K, Wm = args.steps, args.warmup
+    n = args.n
+    copies = K + Wm
+    w, g, us = setup_inputs(mx, W, dev, n, copies)
+    rho, sbar, prof = w.rho.contiguous(), w.sbar.contiguous(), w.prof_beta0.contiguous()
+    beta0 = torch.empty_like(rho)
+    phi = torch.zeros_like(rho)
+    stream = torch.cuda.current_stream()
+    ctx = mx.mx_create(local, stream)
+    opts = mx.default_opts(prec=mx.MX_PREC_MIXED)
+
+    def step(u, o=opts):
+        mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
+        return mx.mx_mac_project(ctx, g, u[0], u[1], u[2], rho, beta0, sbar, phi, o)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    infos = []
+    for s in range(Wm):
+        infos.append(step(us[s])[1])
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(K):
+        infos.append(step(us[Wm + s])[1])
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    last = infos[-1]
+    assert all(i["status"] == 0 for i in infos), infos[-1]
+    value = world * K / (ms_total / 1e3)
+    vcycles = statistics.mean(i["vcycles"] for i in infos[Wm:])
+    # launches per step: fill 1 + setup (coeffs, round 6, coarsen L-1, rhs 4) + loop + finish
+    nlev = 0
+    m = n
+    while m % 2 == 0 and m >= 4:
+        m //= 2
+        nlev += 1
+    nlev += 1
+    per_vcycle = 1 + (nlev - 1) * (4 * 2 + 1) + 1 + (nlev - 1) * (1 + 4 * 2) + 1 + 2 + 1   # memset, sweeps, restrict, bottom, prolong, update, resid+finalize, cond
+    per_setup = 1 + 1 + 6 + (nlev - 1) + 4 + 2 + 1
+    launches = int(round(K * (per_setup + vcycles * per_vcycle + 8)))
+
+    # ---- plain FP64 solve (the comparison) ----
+    fp64 = None
+    if not args.no_fp64:
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        u64 = [t.clone() for t in w.u]
+        step(u64, o64)  # warm-up (plan, graph)
+        kk = max(2, min(5, K // 4))
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        i64 = []
+        f0.record(stream)
+        for s in range(kk):
+            for d in range(3):
+                u64[d].copy_(w.u[d])
+            i64.append(step(u64, o64)[1])
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / kk
+        fp64 = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "vcycles": i64[-1]["vcycles"],
+                "rel_resid": i64[-1]["rel_resid"], "note": "includes a 3-array restore of U per solve"}
+
+    # ---- traced pass: per-phase device time with CUDA events on the launching stream ----
+    mx.mx_profile_enable(ctx, True)
+    ut = [t.clone() for t in w.u]
+    nt = 2
+    for s in range(nt):
+        for d in range(3):
+            ut[d].copy_(w.u[d])
+        step(ut)
+    prof = mx.mx_profile_read(ctx)
+    mx.mx_profile_enable(ctx, False)
+    bpc = algorithmic_bytes_per_cell()
+    ncell = g.ncell
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    phases = {}
+    for name, (pms, pn) in prof.items():
+        phases[name] = {"ms_per_step": pms / nt, "launches_per_step": pn / nt}
+    sm_ms, sm_n = prof["smooth_fine"]
+    per_launch_ms = sm_ms / max(sm_n, 1)
+    achieved = bpc["smooth_fine"] * ncell / (per_launch_ms * 1e-3) / 1e9
+    r_ms, r_n = prof["resid64"]
+    resid_per_launch = r_ms / max(r_n / 2, 1)   # resid64 phase = residual + its 1-block finalize
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get("rbgs_fp32_per_launch_bytes_256")
+    except (OSError, ValueError):
+        pass
+    roofline = {"kernel": "rbgs_kernel<float> (finest level, one colour)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "peak_source": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": bpc["smooth_fine"] * ncell,
+                "ms_per_launch": per_launch_ms,
+                "resid64": {"ms_per_launch": resid_per_launch,
+                            "achieved_GBs": round(bpc["resid64"] * ncell / (resid_per_launch * 1e-3) / 1e9, 1)}}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: t.cpu().pin_memory()
+        h_rho, h_sbar, h_prof = pin(rho), pin(sbar), pin(prof)
+        h_u = [pin(t) for t in w.u]
+        h_out_u = [torch.empty_like(t).pin_memory() for t in h_u]
+        h_phi = torch.empty_like(h_rho).pin_memory()
+        d_u = [torch.empty_like(t) for t in w.u]
+        d_rho, d_sbar, d_prof = torch.empty_like(rho), torch.empty_like(sbar), torch.empty_like(prof)
+        h2d = sum(t.numel() * 8 for t in [h_rho, h_sbar, h_prof] + h_u)
+        d2h = sum(t.numel() * 8 for t in h_out_u + [h_phi])
+        ke = max(3, min(10, K))
+
+        def e2e_step():
+            for src, dst in zip([h_rho, h_sbar, h_prof] + h_u, [d_rho, d_sbar, d_prof] + d_u):
+                dst.copy_(src, non_blocking=True)
+            mx.mx_fill_base_state(ctx, g, 0, d_prof, g.dx, (0.5, 0.5, 0.5), beta0)
+            mx.mx_mac_project(ctx, g, d_u[0], d_u[1], d_u[2], d_rho, beta0, d_sbar, phi, opts)
+            for src, dst in zip(d_u + [phi], h_out_u + [h_phi]):
+                dst.copy_(src, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        q1.record(stream)
+        barrier()
+        ems = q0.elapsed_time(q1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * ke / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(n_sample=128, n_full=n)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"planar{n}", "cells": g.ncell, "bc": "periodic x,y / wall z",
+                   "density_contrast": 1e5, "beta0": "rho0^(3/5)", "rel_tol": 1e-10,
+                   "precision": "FP32 V-cycles in FP64 iterative refinement", "nu1": 2, "nu2": 2,
+                   "l2_policy": "inputs larger than L2 (fresh U copy per step, ~1.5 GB working set)",
+                   "parallelism": f"replicas x{world}"},
+        "vcycles_per_solve": vcycles, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
+        "fp64": fp64, "phases": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    mx.mx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_sample(n_sample, n_full, reps=1):
+    """The FP64 oracle (single-threaded C) solving the same recipe at n_sample^3;
+    its solves/s is scaled by (n_sample/n_full)^3 to the full workload (its cost
+    per solve grows linearly with the cell count at a fixed iteration count)."""
+    import oracle as O
+    from paper_1908_03634_gb300 import workloads as W
+    O.build()
+    w = W.planar256(device="cpu", n=n_sample)
+    b0 = O.fill(w.geom, w.prof_beta0)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, _, info = O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-10)
+    dt = (time.perf_counter() - t0) / reps
+    scale = (n_sample / n_full) ** 3
+    return {"value": round(scale / dt, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle solve of the planar{n_full} recipe at {n_sample}^3 "
+                      f"({dt:.2f} s, {info['iters']} MG-PCG iterations), scaled by ({n_sample}/{n_full})^3"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step solves the planar recipe at
+    64^3 (bounded sample), reported in solves/s of the full workload."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle as O
+    from paper_1908_03634_gb300 import workloads as W
+    O.build()
+    ns = 64
+    w = W.planar256(device="cpu", n=ns)
+    b0 = O.fill(w.geom, w.prof_beta0)
+    for _ in range(args.warmup):
+        O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-10)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, info = O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-10)
+    dt = (time.perf_counter() - t0) / args.steps
+    scale = (ns / args.n) ** 3
+    v = scale / dt
+    sample = (f"oracle solve of the planar{args.n} recipe at {ns}^3 per step ({dt:.3f} s, "
+              f"{info['iters']} MG-PCG iterations), scaled by ({ns}/{args.n})^3")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"planar{args.n}", "rel_tol": 1e-10},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_mx(a)

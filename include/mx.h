@@ -1,0 +1,187 @@
+/*
+ * mx.h -- C ABI of the GB300 (sm_103a) projection solver for the MAESTROeX low
+ * Mach number time step (Fan et al. 2019, "MAESTROeX: A Massively Parallel Low
+ * Mach Number Astrophysical Solver").
+ *
+ * The library enforces the velocity divergence constraint
+ *     div(beta0 U) = beta0 Sbar                                  (Eq. div1/div2/div3)
+ * by a projection (Appendix A): it solves the variable-coefficient elliptic
+ * equation div((beta0/rho) grad phi) = div(beta0 U) - beta0 Sbar with geometric
+ * multigrid and subtracts (1/rho) grad phi from U.  Two discretisations:
+ *   MAC   (Steps 3 and 7): U on cell faces, phi at cell centres, 7-point operator;
+ *   nodal (Step 11):       U at cell centres, phi on nodes, 27-point trilinear
+ *                          finite-element operator (an approximate projection).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Domain: n[0] x n[1] x n[2] cubic cells of width dx.  Arrays are contiguous,
+ * x fastest: cell (i,j,k) is element i + n0*(j + n1*k).
+ * MAC face arrays hold n_d + 1 faces along their own direction d: the x-face
+ * array is (n0+1) x n1 x n2, face i sitting at x = i*dx.  On a periodic axis
+ * face n_d is the image of face 0; callers pass equal values and the library
+ * writes equal values.
+ * Nodal arrays hold n_d nodes on a periodic axis and n_d + 1 on a wall axis.
+ *
+ * Boundaries (per face of the box, lo/hi per axis): periodic (both sides of an
+ * axis must then be periodic), Neumann wall (no flux; the normal velocity on the
+ * wall is taken as 0 and the projected velocity is 0 there), homogeneous
+ * Dirichlet phi = 0 (MAC only).  Periodic axes need an even cell count.
+ *
+ * Pointers: every array argument is a DEVICE pointer (cudaMalloc / torch CUDA
+ * memory) on the context's device, owned by the caller; the library neither
+ * frees nor keeps them past the call.  Scalars and structs are host memory.
+ * Work is enqueued on the context's stream; calls that report norms return
+ * after that stream has synchronised.
+ *
+ * Errors: every function returns an mx_status; mx_last_error() gives a one-line
+ * description of the last failure on that context.  On MX_ERR_NOCONV the best
+ * phi and the corrected U are still written and info reports the residual.
+ * MX_ERR_CUDA leaves the outputs unspecified.
+ */
+#ifndef MX_H
+#define MX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mx_ctx mx_ctx;
+
+typedef enum {
+    MX_OK = 0,
+    MX_ERR_ARG = 1,       /* invalid argument: sizes, boundaries, null pointers */
+    MX_ERR_CUDA = 2,      /* a CUDA call failed */
+    MX_ERR_OOM = 3,       /* device workspace allocation failed */
+    MX_ERR_NOCONV = 4,    /* tolerance not reached within the iteration caps, or divergence */
+    MX_ERR_INCOMPAT = 5,  /* singular problem with a right-hand side of non-zero mean */
+    MX_ERR_TIMEOUT = 6    /* a device-side loop hit its hard iteration cap */
+} mx_status;
+
+typedef enum { MX_BC_PERIODIC = 0, MX_BC_NEUMANN = 1, MX_BC_DIRICHLET = 2 } mx_bc;
+typedef enum { MX_PREC_FP64 = 0, MX_PREC_MIXED = 1 } mx_prec;
+typedef enum { MX_OP_MAC = 0, MX_OP_NODAL = 1 } mx_op;
+
+/* n = cell counts, dx = cell width, lo/hi = mx_bc per axis */
+typedef struct {
+    int n[3];
+    double dx;
+    int lo[3];
+    int hi[3];
+} mx_geom;
+
+/* Solver options.  mx_default_opts() fills: rel_tol 1e-10, max_outer 100,
+ * max_vcycles 100, prec MX_PREC_MIXED, remove_mean 1, use_initial_guess 0,
+ * use_graph 1, nu1 = nu2 = 2 (0 = autotuned), bottom_iters 200. */
+typedef struct {
+    double rel_tol;        /* stop when ||f - L phi||_inf <= rel_tol ||f||_inf */
+    int max_outer;         /* iterative-refinement iterations (one V-cycle each) */
+    int max_vcycles;       /* total V-cycle cap */
+    int prec;              /* mx_prec: FP32 V-cycles in FP64 refinement, or all FP64 */
+    int remove_mean;       /* singular problems: subtract the RHS mean first */
+    int use_initial_guess; /* 1: phi holds the initial guess on entry; 0: start from 0 */
+    int use_graph;         /* 1: run the refinement loop as one CUDA graph */
+    int nu1, nu2;          /* pre/post smoothing sweeps (red+black each) */
+    int bottom_iters;      /* BiCGStab iteration cap on the coarsest grid */
+} mx_opts;
+
+typedef struct {
+    int outer_iters;          /* refinement iterations performed */
+    int vcycles;              /* V-cycles performed */
+    double rel_resid;         /* final ||f - L phi||_inf / ||f||_inf (FP64) */
+    double rel_resid_l2;      /* final ||f - L phi||_2 / ||f||_2 */
+    double div_err_linf;      /* MAC: max |D(beta0 U) - beta0 Sbar - c|; nodal: same at nodes */
+    double rhs_mean_removed;  /* c, the mean subtracted from the RHS */
+    double rhs_linf;          /* ||f||_inf after mean removal */
+    double ms;                /* wall time of the call on the stream (CUDA events) */
+    int status;               /* mx_status of the solve */
+} mx_info;
+
+/* Create a context on CUDA device `device`, enqueuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns its
+ * device workspace (multigrid hierarchy, reduction scratch, graphs). */
+mx_status mx_create(mx_ctx **ctx, int device, void *cuda_stream);
+mx_status mx_destroy(mx_ctx *ctx);
+mx_status mx_set_stream(mx_ctx *ctx, void *cuda_stream);
+const char *mx_last_error(const mx_ctx *ctx);
+void mx_default_opts(mx_opts *opts);
+/* 1 if the library was built for this device (sm_103), else 0 */
+int mx_device_supported(int device);
+
+/* Fill (Sec. 3.1): map a 1D base-state profile onto the Cartesian cells.
+ * planar (spherical = 0): direct injection, cell (i,j,k) takes prof[k];
+ *   requires nr >= n[2].
+ * spherical (spherical = 1): prof[m] is the value at radius (m + 1/2) dr from
+ *   center (host array of 3 coordinates); each cell centre takes the linear
+ *   interpolation in r between the two bracketing radial cell centres (the
+ *   first/last interval is extended linearly); requires nr >= 2.
+ * prof: device, nr doubles; out_cells: device, n0 n1 n2 doubles. */
+mx_status mx_fill_base_state(mx_ctx *ctx, const mx_geom *geom, int spherical, const double *prof,
+                             int nr, double dr, const double center[3], double *out_cells);
+
+/* MAC projection (Steps 3 and 7; Eq. div1, div2; Appendix A).
+ * ux, uy, uz: face velocities U^ADV,dagger (in) -> projected U^ADV (out).
+ * rho, beta0, sbar: cell fields; sbar is the whole bracket of the constraint's
+ *   right-hand side (S - dp0/dt / (Gamma1 p0)), multiplied by beta0 inside.
+ * phi: cell field (out; in as initial guess if opts->use_initial_guess).
+ * Face coefficient b = beta0_f / rho_f with arithmetic face averages (the
+ * interior cell on a Dirichlet face).  On singular problems (no Dirichlet face)
+ * the RHS mean c is removed (remove_mean = 1) and phi has zero mean; with
+ * remove_mean = 0 a RHS of mean above 1e-12 ||f||_inf returns MX_ERR_INCOMPAT.
+ * opts may be NULL (defaults); info may be NULL. */
+mx_status mx_mac_project(mx_ctx *ctx, const mx_geom *geom, double *ux, double *uy, double *uz,
+                         const double *rho, const double *beta0, const double *sbar, double *phi,
+                         const mx_opts *opts, mx_info *info);
+
+/* Nodal projection (Step 11; Eq. div3; Appendix A).  ux, uy, uz: cell-centred
+ * velocity (in/out); phi_nodes: nodal field (out).  Only periodic and Neumann
+ * boundaries.  sigma = beta0/rho per cell; the weighted RHS mean is removed. */
+mx_status mx_nodal_project(mx_ctx *ctx, const mx_geom *geom, double *ux, double *uy, double *uz,
+                           const double *rho, const double *beta0, const double *sbar,
+                           double *phi_nodes, const mx_opts *opts, mx_info *info);
+
+/* Apply the operator L = div((beta0/rho) grad .) to phi (MAC: cells -> cells;
+ * nodal: nodes -> nodes).  prec = MX_PREC_FP64 computes in FP64;
+ * MX_PREC_MIXED rounds the coefficients and phi to FP32 and computes in FP32
+ * (the arithmetic of the V-cycle), still writing doubles. */
+mx_status mx_apply_op(mx_ctx *ctx, const mx_geom *geom, int op, int prec, const double *rho,
+                      const double *beta0, const double *phi, double *Lphi);
+
+/* r = f - L phi (device, same layout as phi) and, if rnorm_linf is not NULL,
+ * its max norm to the host. */
+mx_status mx_residual(mx_ctx *ctx, const mx_geom *geom, int op, int prec, const double *rho,
+                      const double *beta0, const double *phi, const double *f, double *r,
+                      double *rnorm_linf);
+
+/* Batched MAC projections of nbox independent boxes (AMR-style patches, the
+ * analogue of the paper's 64^3 grids per MPI task, Sec. 4.1).  Each box has its
+ * own geometry and arrays (host arrays of device pointers, length nbox); every
+ * smoothing / restriction / prolongation phase runs as one launch over a work
+ * list of tiles of all boxes.  infos: host array of nbox (may be NULL). */
+mx_status mx_mac_project_batched(mx_ctx *ctx, int nbox, const mx_geom *geoms, double *const *ux,
+                                 double *const *uy, double *const *uz, const double *const *rho,
+                                 const double *const *beta0, const double *const *sbar,
+                                 double *const *phi, const mx_opts *opts, mx_info *infos);
+
+/* Tracing: per-phase device time of mx_mac_project.  While enabled, the
+ * refinement loop runs from the host (no graph) and every phase is bracketed by
+ * CUDA events on the context's stream.  mx_profile_read copies, per phase, the
+ * accumulated milliseconds and kernel launches since the last read (host arrays
+ * of MX_PH_COUNT entries) and resets the counters. */
+enum {
+    MX_PH_SETUP = 0,          /* coefficients, hierarchy, right-hand side */
+    MX_PH_RESID64 = 1,        /* FP64 residual + norms of the refinement loop */
+    MX_PH_SMOOTH_FINE = 2,    /* red-black sweeps on the finest level */
+    MX_PH_RESTRICT_FINE = 3,  /* residual + restriction from the finest level */
+    MX_PH_PROLONG_FINE = 4,   /* prolongation onto the finest level */
+    MX_PH_COARSE = 5,         /* all coarser levels and the bottom solve */
+    MX_PH_UPDATE = 6,         /* zeroing of the correction and phi += scale e */
+    MX_PH_FINISH = 7,         /* mean normalisation, velocity correction, divergence check */
+    MX_PH_COUNT = 8
+};
+mx_status mx_profile_enable(mx_ctx *ctx, int enable);
+mx_status mx_profile_read(mx_ctx *ctx, double *ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MX_H */

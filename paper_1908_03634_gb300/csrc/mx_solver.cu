@@ -1,0 +1,492 @@
+// MAC projection driver: workspace plans, the V-cycle, the FP64
+// iterative-refinement loop (FP32 V-cycles for the correction, FP64 residual
+// and accumulation), optional CUDA-graph execution of that loop, and the
+// mx_mac_project / mx_apply_op / mx_residual entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "mx_solver.cuh"
+#include "mx_stencil.cuh"
+
+// implemented with the nodal kernels
+mx_status nodal_apply(mx_ctx *c, const mx_geom *geom, int prec, const double *rho, const double *beta0,
+                      const double *phi, const double *f, double *out, double *rnorm);
+void destroy_nodal_plans(mx_ctx *c);
+void destroy_batch_plan(mx_ctx *c);
+
+// ------------------------------------------------------------------------------
+// plans
+
+template <typename T>
+static void carve_level(Bump &b, Level<T> &L, const DGeom &g, bool coefs, bool fe) {
+    L.g = g;
+    if (coefs) {
+        L.bx = b.take<T>(g.N);
+        L.by = b.take<T>(g.N);
+        L.bz = b.take<T>(g.N);
+        L.hx = gper(g, 0) ? nullptr : b.take<T>((size_t)g.n[1] * g.n[2]);
+        L.hy = gper(g, 1) ? nullptr : b.take<T>((size_t)g.n[0] * g.n[2]);
+        L.hz = gper(g, 2) ? nullptr : b.take<T>((size_t)g.n[0] * g.n[1]);
+    } else {
+        L.bx = L.by = L.bz = L.hx = L.hy = L.hz = nullptr;
+    }
+    if (fe) {
+        L.f = b.take<T>(g.N);
+        L.e = b.take<T>(g.N);
+    } else {
+        L.f = L.e = nullptr;
+    }
+}
+
+template <typename T>
+static void carve_hier(Bump &b, Hier<T> &H, const DGeom *gs, int nl, bool level0_coefs) {
+    H.nlev = nl;
+    for (int l = 0; l < nl; l++) carve_level(b, H.lev[l], gs[l], l > 0 || level0_coefs, true);
+    H.bot_scratch = b.take<T>(7 * (size_t)gs[nl - 1].N);
+}
+
+static void carve_plan(Bump &b, MacPlan &P) {
+    DGeom gs[MX_MAXLEV];
+    const int nl = mac_levels(P.g, gs);
+    carve_level(b, P.L64, P.g, true, true);
+    if (P.prec == MX_PREC_MIXED) {
+        carve_hier(b, P.H32, gs, nl, true);
+        P.tmp32 = b.take<float>(P.g.N);
+        P.H64.nlev = 0;
+    } else {
+        carve_hier(b, P.H64, gs, nl, false);
+        Level<double> &l0 = P.H64.lev[0];
+        l0.bx = P.L64.bx; l0.by = P.L64.by; l0.bz = P.L64.bz;
+        l0.hx = P.L64.hx; l0.hy = P.L64.hy; l0.hz = P.L64.hz;
+        P.H32.nlev = 0;
+    }
+    P.tmp64 = b.take<double>(P.g.N);
+}
+
+static bool same_geom(const DGeom &a, const DGeom &b) {
+    for (int d = 0; d < 3; d++)
+        if (a.n[d] != b.n[d] || a.lo[d] != b.lo[d] || a.hi[d] != b.hi[d]) return false;
+    return a.h == b.h;
+}
+
+static void free_plan(MacPlan *p) {
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->mem) cudaFree(p->mem);
+    delete p;
+}
+
+mx_status ensure_partials(mx_ctx *c, long long nblocks) {
+    if (nblocks <= c->max_partials) return MX_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->partials);
+    c->partials = nullptr;
+    if (cudaMalloc(&c->partials, sizeof(double) * 3 * nblocks) != cudaSuccess) {
+        cudaGetLastError();
+        c->max_partials = 0;
+        return set_err(c, MX_ERR_OOM, "reduction scratch cudaMalloc failed");
+    }
+    c->max_partials = int(nblocks);
+    for (MacPlan *p : c->plans)  // graphs captured the old scratch pointer
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+    return MX_OK;
+}
+
+MacPlan *get_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st) {
+    *st = ensure_partials(c, std::max<long long>(stencil_blocks(g), red_blocks(g.N)));
+    if (*st) return nullptr;
+    for (MacPlan *p : c->plans)
+        if (p->prec == prec && same_geom(p->g, g)) {
+            p->last_use = ++c->use_counter;
+            return p;
+        }
+    // keep at most 4 plans: evict the least recently used
+    if (c->plans.size() >= 4) {
+        auto it = std::min_element(c->plans.begin(), c->plans.end(),
+                                   [](MacPlan *a, MacPlan *b) { return a->last_use < b->last_use; });
+        cudaStreamSynchronize(c->stream);
+        free_plan(*it);
+        c->plans.erase(it);
+    }
+    MacPlan *P = new MacPlan();
+    P->g = g;
+    P->prec = prec;
+    Bump dry{nullptr, 0};
+    carve_plan(dry, *P);
+    P->bytes = dry.off + 256;
+    if (cudaMalloc(&P->mem, P->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        *st = set_err(c, MX_ERR_OOM, "plan workspace cudaMalloc failed");
+        return nullptr;
+    }
+    Bump real{(char *)P->mem, 0};
+    carve_plan(real, *P);
+    P->last_use = ++c->use_counter;
+    c->plans.push_back(P);
+    return P;
+}
+
+void destroy_plans(mx_ctx *c) {
+    for (MacPlan *p : c->plans) free_plan(p);
+    c->plans.clear();
+    destroy_nodal_plans(c);
+    destroy_batch_plan(c);
+}
+
+// ------------------------------------------------------------------------------
+// V-cycle on the correction equation L e = r (level-0 f holds r, e is zeroed here)
+
+template <typename T>
+void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc) {
+    prof_begin(pc, s, MX_PH_UPDATE);
+    cudaMemsetAsync(H.lev[0].e, 0, sizeof(T) * H.lev[0].g.N, s);
+    prof_end(pc, s, MX_PH_UPDATE, 1);
+    int ncoarse = 0;
+    for (int l = 0; l < H.nlev - 1; l++) {
+        if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
+        for (int q = 0; q < nu1; q++) {
+            k_rbgs(s, H.lev[l], 0);
+            k_rbgs(s, H.lev[l], 1);
+        }
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_SMOOTH_FINE, 2 * nu1);
+            prof_begin(pc, s, MX_PH_RESTRICT_FINE);
+        }
+        k_resid_restrict(s, H.lev[l], H.lev[l + 1]);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_RESTRICT_FINE, 1);
+            prof_begin(pc, s, MX_PH_COARSE);
+        } else {
+            ncoarse += 2 * nu1 + 1;
+        }
+    }
+    if (H.nlev == 1) prof_begin(pc, s, MX_PH_COARSE);
+    k_bottom(s, H.lev[H.nlev - 1], H.bot_scratch, bot_iters, singular);
+    ncoarse += 1;
+    for (int l = H.nlev - 2; l >= 0; l--) {
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_COARSE, ncoarse);
+            prof_begin(pc, s, MX_PH_PROLONG_FINE);
+        }
+        k_prolong(s, H.lev[l + 1], H.lev[l]);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_PROLONG_FINE, 1);
+            prof_begin(pc, s, MX_PH_SMOOTH_FINE);
+        } else {
+            ncoarse += 1 + 2 * nu2;
+        }
+        for (int q = 0; q < nu2; q++) {
+            k_rbgs(s, H.lev[l], 0);
+            k_rbgs(s, H.lev[l], 1);
+        }
+        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, 2 * nu2);
+    }
+    if (H.nlev == 1) prof_end(pc, s, MX_PH_COARSE, ncoarse);
+}
+template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *);
+template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *);
+
+template <typename T>
+static void build_hierarchy(cudaStream_t s, Hier<T> &H) {
+    for (int l = 0; l + 1 < H.nlev; l++) k_coarsen_coeffs(s, H.lev[l], H.lev[l + 1]);
+}
+
+// One refinement iteration after the residual: V-cycle, update, next residual.
+template <typename T>
+static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular,
+                    int nb, mx_ctx *pc) {
+    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc);
+    prof_begin(pc, s, MX_PH_UPDATE);
+    k_update<T>(s, P.g, phi, H.lev[0].e, c->state);
+    prof_end(pc, s, MX_PH_UPDATE, 1);
+    prof_begin(pc, s, MX_PH_RESID64);
+    k_residual64<T>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
+    k_finalize_residual(s, c->partials, nb, c->state);
+    prof_end(pc, s, MX_PH_RESID64, 2);
+}
+
+// Conditional-while graph of the refinement loop: the finalize kernel of each
+// iteration sets the loop condition from the FP64 residual.
+__global__ void set_cond_kernel(cudaGraphConditionalHandle h, const SolveState *st) {
+    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+template <typename T>
+static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular, int nb) {
+    cudaStream_t s = c->stream;
+    if (!P.graph || P.graph_phi != phi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 || P.graph_bot != o.bottom_iters) {
+        if (P.graph) {
+            cudaGraphExecDestroy(P.graph);
+            P.graph = nullptr;
+        }
+        cudaGraph_t graph;
+        MX_CUDA(c, cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle handle;
+        MX_CUDA(c, cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        MX_CUDA(c, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t cs;
+        MX_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            ir_body<T>(cs, c, P, H, phi, o, singular, nb, nullptr);
+            set_cond_kernel<<<1, 1, 0, cs>>>(handle, c->state);
+            cudaGraph_t captured;
+            e = cudaStreamEndCapture(cs, &captured);
+        }
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return set_err(c, MX_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&P.graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            P.graph = nullptr;
+            return set_err(c, MX_ERR_CUDA, std::string("graph instantiate failed: ") + cudaGetErrorString(e));
+        }
+        P.graph_phi = phi;
+        P.graph_nu1 = o.nu1;
+        P.graph_nu2 = o.nu2;
+        P.graph_bot = o.bottom_iters;
+    }
+    // the while node runs its body while the condition is 1; enter only if the
+    // first residual asked for a V-cycle
+    MX_CUDA(c, cudaGraphLaunch(P.graph, s));
+    return MX_OK;
+}
+
+template <typename T>
+static mx_status run_ir(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular) {
+    cudaStream_t s = c->stream;
+    const int nb = stencil_blocks(P.g);
+    prof_begin(c, s, MX_PH_RESID64);
+    k_residual64<T>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
+    k_finalize_residual(s, c->partials, nb, c->state);
+    prof_end(c, s, MX_PH_RESID64, 2);
+    if (o.use_graph && !c->prof) {
+        // the loop is entered unconditionally by the while node; a first
+        // residual that already meets the tolerance is handled on the host
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (c->hstate->done) return MX_OK;
+        return run_loop_graph<T>(c, P, H, phi, o, singular, nb);
+    }
+    for (;;) {
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (c->hstate->done) break;
+        ir_body<T>(s, c, P, H, phi, o, singular, nb, c);
+        prof_flush(c);
+    }
+    return MX_OK;
+}
+
+// ------------------------------------------------------------------------------
+
+static mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
+    if (in) o = *in;
+    else mx_default_opts(&o);
+    if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.max_vcycles < 0 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
+        o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.bottom_iters < 1 || o.bottom_iters > 100000)
+        return set_err(c, MX_ERR_ARG, "invalid options");
+    if (o.nu1 == 0 && o.nu2 == 0) {
+        o.nu1 = 2;
+        o.nu2 = 2;
+    }
+    return MX_OK;
+}
+
+static void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0) {
+    cudaStream_t s = c->stream;
+    k_mac_coeffs64(s, P.L64, rho, beta0);
+    if (P.prec == MX_PREC_MIXED) {
+        k_round_coeffs(s, P.L64, P.H32.lev[0]);
+        build_hierarchy(s, P.H32);
+    } else {
+        build_hierarchy(s, P.H64);
+    }
+}
+
+extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, double *uy, double *uz,
+                                    const double *rho, const double *beta0, const double *sbar, double *phi,
+                                    const mx_opts *opts, mx_info *info) {
+    if (!c) return MX_ERR_ARG;
+    mx_status st = check_geom(c, geom, false);
+    if (st) return st;
+    if (!ux || !uy || !uz || !rho || !beta0 || !sbar || !phi) return set_err(c, MX_ERR_ARG, "mac_project: null array");
+    mx_opts o;
+    if ((st = check_opts(c, opts, o))) return st;
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
+    const DGeom g = make_dgeom(geom);
+    const int singular = geom_singular(g);
+    MacPlan *P = get_mac_plan(c, g, o.prec, &st);
+    if (!P) return st;
+    cudaStream_t s = c->stream;
+    const int nb = stencil_blocks(g);
+    const int nbr = red_blocks(g.N);
+    MX_CUDA(c, cudaEventRecord(c->ev0, s));
+
+    // device state: tolerance and caps
+    SolveState init = {};
+    init.tol = o.rel_tol;
+    init.maxit = std::min(o.max_outer, o.max_vcycles);
+    *c->hstate = init;
+    MX_CUDA(c, cudaMemcpyAsync(c->state, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+
+    prof_begin(c, s, MX_PH_SETUP);
+    setup_coefficients(c, *P, rho, beta0);
+    // right-hand side f = D(beta0 U) - beta0 Sbar, mean removal, norms
+    k_mac_rhs(s, g, ux, uy, uz, beta0, sbar, P->L64.f, c->partials, nb);
+    k_finalize_rhs(s, c->partials, nb, c->state, g.N, singular && o.remove_mean, 0);
+    if (singular && !o.remove_mean) {
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (std::fabs(c->hstate->aux) > 1e-12 * c->hstate->fnorm) {
+            if (info) {
+                std::memset(info, 0, sizeof(*info));
+                info->status = MX_ERR_INCOMPAT;
+            }
+            return set_err(c, MX_ERR_INCOMPAT, "singular problem: right-hand side has non-zero mean and remove_mean = 0");
+        }
+    }
+    k_sub_mean_norm(s, g, P->L64.f, c->state, c->partials, nbr);
+    k_finalize_rhs(s, c->partials, nbr, c->state, g.N, 0, 1);
+    if (!o.use_initial_guess) MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.N, s));
+    prof_end(c, s, MX_PH_SETUP, 0);
+
+    if (o.prec == MX_PREC_MIXED) st = run_ir<float>(c, *P, P->H32, phi, o, singular);
+    else st = run_ir<double>(c, *P, P->H64, phi, o, singular);
+    if (st) return st;
+
+    prof_begin(c, s, MX_PH_FINISH);
+    if (singular) {  // normalise mean(phi) = 0
+        k_sum_partials(s, g, phi, c->partials, nbr);
+        k_finalize_sum(s, c->partials, nbr, &c->state->aux, 1.0 / double(g.N));
+        k_sub_scalar(s, g.N, phi, &c->state->aux);
+    }
+    k_mac_correct(s, g, rho, phi, ux, uy, uz);
+    k_mac_divcheck(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials, nb);
+    k_finalize_max(s, c->partials, nb, &c->state->div_err);
+    prof_end(c, s, MX_PH_FINISH, singular ? 8 : 5);
+    MX_CUDA(c, cudaEventRecord(c->ev1, s));
+    MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MX_CUDA(c, cudaStreamSynchronize(s));
+    MX_CUDA(c, cudaGetLastError());
+    const SolveState &hs = *c->hstate;
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        info->outer_iters = hs.iter;
+        info->vcycles = hs.iter;
+        info->rel_resid = hs.fnorm > 0 ? hs.rnorm / hs.fnorm : hs.rnorm;
+        info->rel_resid_l2 = hs.fnorm2 > 0 ? hs.rnorm2 / hs.fnorm2 : hs.rnorm2;
+        info->div_err_linf = hs.div_err;
+        info->rhs_mean_removed = hs.mean;
+        info->rhs_linf = hs.fnorm;
+        info->ms = ms;
+        info->status = hs.status;
+    }
+    if (hs.status != MX_OK) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "no convergence: relative residual %.3e after %d V-cycles", hs.rnorm / (hs.fnorm > 0 ? hs.fnorm : 1.0), hs.iter);
+        return set_err(c, (mx_status)hs.status, buf);
+    }
+    return MX_OK;
+}
+
+// ------------------------------------------------------------------------------
+// operator and residual entry points
+
+__global__ void resid_combine_kernel(const double *f, const float *lphi, double *r, long long n, double *part) {
+    double mx = 0.0, s2 = 0.0, s1 = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const float v = float(f[q]) - lphi[q];
+        r[q] = double(v);
+        mx = fmax(mx, fabs(double(v)));
+        s2 += double(v) * double(v);
+        s1 += double(v);
+    }
+    block_red3(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = mx;
+        part[3 * blockIdx.x + 1] = s2;
+        part[3 * blockIdx.x + 2] = s1;
+    }
+}
+
+static mx_status mac_apply_or_residual(mx_ctx *c, const mx_geom *geom, int prec, const double *rho, const double *beta0,
+                                       const double *phi, const double *f, double *out, double *rnorm) {
+    const DGeom g = make_dgeom(geom);
+    mx_status st;
+    MacPlan *P = get_mac_plan(c, g, prec, &st);
+    if (!P) return st;
+    cudaStream_t s = c->stream;
+    k_mac_coeffs64(s, P->L64, rho, beta0);
+    if (prec == MX_PREC_FP64) {
+        if (f) {
+            const int nb = stencil_blocks(g);
+            k_residual_plain(s, P->L64, phi, f, out, c->partials, nb);
+            if (rnorm) k_finalize_max(s, c->partials, nb, &c->state->rnorm);
+        } else {
+            k_apply<double>(s, P->L64, phi, out);
+        }
+    } else {
+        Level<float> &l0 = P->H32.lev[0];
+        k_round_coeffs(s, P->L64, l0);
+        k_cast<float>(s, g.N, phi, l0.e);
+        k_apply<float>(s, l0, l0.e, P->tmp32);
+        if (f) {
+            const int nbr = red_blocks(g.N);
+            resid_combine_kernel<<<nbr, 256, 0, s>>>(f, P->tmp32, out, g.N, c->partials);
+            if (rnorm) k_finalize_max(s, c->partials, nbr, &c->state->rnorm);
+        } else {
+            k_uncast<float>(s, g.N, P->tmp32, out);
+        }
+    }
+    if (rnorm) {
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        *rnorm = c->hstate->rnorm;
+    }
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+extern "C" mx_status mx_apply_op(mx_ctx *c, const mx_geom *geom, int op, int prec, const double *rho,
+                                 const double *beta0, const double *phi, double *Lphi) {
+    if (!c) return MX_ERR_ARG;
+    const bool nodal = op == MX_OP_NODAL;
+    if (op != MX_OP_MAC && !nodal) return set_err(c, MX_ERR_ARG, "unknown operator");
+    if (prec != MX_PREC_FP64 && prec != MX_PREC_MIXED) return set_err(c, MX_ERR_ARG, "unknown precision");
+    mx_status st = check_geom(c, geom, nodal);
+    if (st) return st;
+    if (!rho || !beta0 || !phi || !Lphi) return set_err(c, MX_ERR_ARG, "apply_op: null array");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
+    if (nodal) return nodal_apply(c, geom, prec, rho, beta0, phi, nullptr, Lphi, nullptr);
+    return mac_apply_or_residual(c, geom, prec, rho, beta0, phi, nullptr, Lphi, nullptr);
+}
+
+extern "C" mx_status mx_residual(mx_ctx *c, const mx_geom *geom, int op, int prec, const double *rho,
+                                 const double *beta0, const double *phi, const double *f, double *r, double *rnorm_linf) {
+    if (!c) return MX_ERR_ARG;
+    const bool nodal = op == MX_OP_NODAL;
+    if (op != MX_OP_MAC && !nodal) return set_err(c, MX_ERR_ARG, "unknown operator");
+    if (prec != MX_PREC_FP64 && prec != MX_PREC_MIXED) return set_err(c, MX_ERR_ARG, "unknown precision");
+    mx_status st = check_geom(c, geom, nodal);
+    if (st) return st;
+    if (!rho || !beta0 || !phi || !f || !r) return set_err(c, MX_ERR_ARG, "residual: null array");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
+    if (nodal) return nodal_apply(c, geom, prec, rho, beta0, phi, f, r, rnorm_linf);
+    return mac_apply_or_residual(c, geom, prec, rho, beta0, phi, f, r, rnorm_linf);
+}

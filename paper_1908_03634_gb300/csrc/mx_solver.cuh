@@ -1,0 +1,36 @@
+// Solver plans: device workspace for one geometry and precision, holding the
+// FP64 finest-level operator and the multigrid hierarchy of the correction solve.
+#pragma once
+
+#include "mx_internal.cuh"
+
+template <typename T>
+struct Hier {
+    int nlev = 0;
+    Level<T> lev[MX_MAXLEV];
+    T *bot_scratch = nullptr;  // 7 vectors of the coarsest level (BiCGStab)
+};
+
+struct MacPlan {
+    DGeom g;
+    int prec = MX_PREC_MIXED;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    Level<double> L64;  // FP64 finest-level coefficients; L64.f = FP64 right-hand side
+    Hier<float> H32;    // mixed: the FP32 correction hierarchy
+    Hier<double> H64;   // FP64: the FP64 correction hierarchy (level 0 shares L64's coefficients)
+    float *tmp32 = nullptr;
+    double *tmp64 = nullptr;
+    // CUDA graph of the refinement loop, keyed by the pointers it was captured with
+    cudaGraphExec_t graph = nullptr;
+    const void *graph_phi = nullptr;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1;
+    long long last_use = 0;
+};
+
+MacPlan *get_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st);
+void destroy_plans(mx_ctx *c);
+mx_status ensure_partials(mx_ctx *c, long long nblocks);
+
+template <typename T>
+void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *prof = nullptr);

@@ -1,0 +1,105 @@
+// Device helpers shared by the cell-centred kernels: neighbour access with the
+// boundary closures, the 7-point face-flux operator and block reductions.
+#pragma once
+
+#include "mx_internal.cuh"
+
+// Coefficients of the 6 faces of cell (i,j,k): w, e, s, n, b, t (x-, x+, y-, y+, z-, z+).
+template <typename T>
+__device__ __forceinline__ void face_coefs(const Level<T> &L, int i, int j, int k, long long c, T b[6]) {
+    const DGeom &g = L.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    b[0] = L.bx[c];
+    b[1] = (i + 1 < nx) ? L.bx[c + 1] : (gper(g, 0) ? L.bx[c - (nx - 1)] : L.hx[j + (long long)ny * k]);
+    b[2] = L.by[c];
+    b[3] = (j + 1 < ny) ? L.by[c + nx] : (gper(g, 1) ? L.by[c - (long long)(ny - 1) * nx] : L.hy[i + (long long)nx * k]);
+    b[4] = L.bz[c];
+    b[5] = (k + 1 < nz) ? L.bz[c + g.nxy] : (gper(g, 2) ? L.bz[c - (long long)(nz - 1) * g.nxy] : L.hz[i + (long long)nx * j]);
+}
+
+// The 6 neighbour values of cell (i,j,k); 0 beyond a non-periodic face.
+template <typename T>
+__device__ __forceinline__ void nb_vals(const DGeom &g, const T *p, int i, int j, int k, long long c, T v[6]) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    v[0] = i > 0 ? p[c - 1] : (gper(g, 0) ? p[c + nx - 1] : T(0));
+    v[1] = i + 1 < nx ? p[c + 1] : (gper(g, 0) ? p[c - (nx - 1)] : T(0));
+    v[2] = j > 0 ? p[c - nx] : (gper(g, 1) ? p[c + (long long)(ny - 1) * nx] : T(0));
+    v[3] = j + 1 < ny ? p[c + nx] : (gper(g, 1) ? p[c - (long long)(ny - 1) * nx] : T(0));
+    v[4] = k > 0 ? p[c - g.nxy] : (gper(g, 2) ? p[c + (long long)(nz - 1) * g.nxy] : T(0));
+    v[5] = k + 1 < nz ? p[c + g.nxy] : (gper(g, 2) ? p[c - (long long)(nz - 1) * g.nxy] : T(0));
+}
+
+// h^2 (L p)_c = sum_faces b_f (p_nb - p_c)
+template <typename T>
+__device__ __forceinline__ T flux_sum(const T b[6], const T v[6], T pc) {
+    T s = b[0] * (v[0] - pc);
+    s += b[1] * (v[1] - pc);
+    s += b[2] * (v[2] - pc);
+    s += b[3] * (v[3] - pc);
+    s += b[4] * (v[4] - pc);
+    s += b[5] * (v[5] - pc);
+    return s;
+}
+
+__device__ __forceinline__ int flat_tid() {
+    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+__device__ __forceinline__ int flat_bid() {
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+// Block-wide (max, sum, sum) of three doubles; result valid in thread 0.
+// Fixed shuffle order: deterministic.
+__device__ __forceinline__ void block_red3(double &a, double &b, double &c) {
+    __shared__ double sh[96];
+    const int t = flat_tid();
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int lane = t & 31, wid = t >> 5;
+    if (lane == 0) {
+        sh[wid] = a;
+        sh[32 + wid] = b;
+        sh[64 + wid] = c;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (nthr + 31) >> 5;
+        a = lane < nw ? sh[lane] : 0.0;
+        b = lane < nw ? sh[32 + lane] : 0.0;
+        c = lane < nw ? sh[64 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+    }
+    __syncthreads();
+}
+
+// Reduce nb partial triples (max, sum, sum) with one block; results in thread 0.
+__device__ __forceinline__ void reduce_partials3(const double *p, int nb, double &a, double &b, double &c) {
+    a = 0.0;
+    b = 0.0;
+    c = 0.0;
+    for (int q = flat_tid(); q < nb; q += blockDim.x * blockDim.y * blockDim.z) {
+        a = fmax(a, p[3 * q]);
+        b += p[3 * q + 1];
+        c += p[3 * q + 2];
+    }
+    block_red3(a, b, c);
+}
+
+// Launch shape of the cell-centred stencil kernels: (32 x 8) threads per block,
+// each thread walking ZC cells in z.
+constexpr int SX = 32, SY = 8, ZC = 8;
+inline dim3 stencil_grid(const DGeom &g) {
+    return dim3((g.n[0] + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + ZC - 1) / ZC);
+}
+inline int stencil_blocks(const DGeom &g) {
+    dim3 d = stencil_grid(g);
+    return int(d.x * d.y * d.z);
+}
