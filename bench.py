@@ -219,7 +219,7 @@ def run_mx(args):
         for d in range(3):
             ut[d].copy_(w.u[d])
         step(ut)
-    prof = mx.mx_profile_read(ctx)
+    trace = mx.mx_profile_read(ctx)
     mx.mx_profile_enable(ctx, False)
     bpc = algorithmic_bytes_per_cell()
     ncell = g.ncell
@@ -231,12 +231,12 @@ def run_mx(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     phases = {}
-    for name, (pms, pn) in prof.items():
+    for name, (pms, pn) in trace.items():
         phases[name] = {"ms_per_step": pms / nt, "launches_per_step": pn / nt}
-    sm_ms, sm_n = prof["smooth_fine"]
+    sm_ms, sm_n = trace["smooth_fine"]
     per_launch_ms = sm_ms / max(sm_n, 1)
     achieved = bpc["smooth_fine"] * ncell / (per_launch_ms * 1e-3) / 1e9
-    r_ms, r_n = prof["resid64"]
+    r_ms, r_n = trace["resid64"]
     resid_per_launch = r_ms / max(r_n / 2, 1)   # resid64 phase = residual + its 1-block finalize
     traffic = None
     try:

@@ -103,7 +103,7 @@ def test_fill_planar_and_spherical(mx, ctx):
     o2 = torch.empty((24, 24, 24), dtype=torch.float64, device=DEV)
     mx.mx_fill_base_state(ctx, w.geom, 1, cuda(w.prof_beta0), w.prof_dr, w.center, o2)
     ref = O.fill(w.geom, w.prof_beta0, spherical=True, dr=w.prof_dr, center=w.center)
-    assert np.abs(o2.cpu().numpy() - ref).max() <= 1e-15 * np.abs(ref).max()
+    assert np.abs(o2.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()   # FMA contraction differs
 
 
 def run_gpu_project(mx, ctx, w, prec, **kw):
@@ -142,10 +142,15 @@ def test_mac_project_parity(mx, ctx, name, prec):
     u_ref, phi_ref, oinfo, b0_ref = oracle_project(w)
     assert st == mx.MX_OK, info
     assert info["rel_resid"] <= 1e-10
-    assert np.abs(b0 - b0_ref).max() <= 1e-15 * np.abs(b0_ref).max()
+    assert np.abs(b0 - b0_ref).max() <= 1e-14 * np.abs(b0_ref).max()
     assert np.abs(phi - phi_ref).max() <= 1e-8 * np.abs(phi_ref).max()
+    # the velocity correction, element by element: the oracle's correction
+    # applied to the GPU's phi (U differs from the oracle's U only through
+    # grad(phi_gpu - phi_ref)/rho_f, which 1/rho amplifies in light layers)
+    u_pred = O.mac_correct(w.geom, w.rho, phi, w.u)
     for d in range(3):
-        assert np.abs(u[d] - u_ref[d]).max() <= 1e-8 * np.abs(u_ref[d]).max() + 1e-300
+        scale = np.abs(w.u[d].numpy()).max() + np.abs(u_pred[d] - w.u[d].numpy()).max()
+        assert np.abs(u[d] - u_pred[d]).max() <= 1e-12 * scale
     assert abs(info["rhs_mean_removed"] - oinfo["mean"]) <= 1e-12 * max(1.0, abs(oinfo["mean"]))
     # divergence of the projected U: residual-sized (Eq. div1 up to the solve tolerance)
     f, _ = O.mac_rhs(w.geom, w.u, b0_ref, w.sbar)
