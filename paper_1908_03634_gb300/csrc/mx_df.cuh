@@ -1,0 +1,21 @@
+// Double-float (hi + lo float pairs) storage of the refinement loop's
+// high-precision quantities; the hi parts of the coefficients are the FP32
+// finest-level coefficients of the V-cycle.
+#pragma once
+
+#include "mx_internal.cuh"
+
+struct DFArrays {
+    float *bxl, *byl, *bzl;  // lo parts of the lo-face coefficients
+    float *hxl, *hyl, *hzl;  // lo parts of the high-boundary planes
+    float *fh, *fl;          // h^2 f
+    float *ph, *pl;          // phi
+};
+
+void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho, const double *beta0);
+void k_sub_mean_split(cudaStream_t s, const DGeom &g, const double *f, const SolveState *st, const DFArrays &D,
+                      double *partials, int nb);
+void k_df_from_double(cudaStream_t s, long long n, const double *x, const DFArrays &D);
+void k_df_to_double(cudaStream_t s, long long n, const DFArrays &D, double *x);
+void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float *e, const SolveState *st);
+void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials);

@@ -37,6 +37,7 @@ struct Level {
     T *bx, *by, *bz;  // lo-face coefficients, one per cell
     T *hx, *hy, *hz;  // high-boundary face coefficients (non-periodic axes)
     T *f, *e;         // right-hand side and correction
+    T *e2;            // second correction buffer (single-pass sweeps write e2 <-> e)
 };
 
 // Device-resident state of one solve (norms, control flags).

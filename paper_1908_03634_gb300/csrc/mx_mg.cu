@@ -4,6 +4,7 @@
 // BiCGStab bottom solve, and the FP64 residual / update of the refinement loop.
 // Templated on the V-cycle precision T (float for the mixed-precision path,
 // double for the plain FP64 path).
+#include "mx_rbgs.cuh"
 #include "mx_stencil.cuh"
 
 // ------------------------------------------------------------------------------
@@ -166,15 +167,7 @@ __global__ void rbgs_kernel(Level<T> L, int colour, T h2) {
         T b[6], v[6];
         face_coefs(L, i, j, k, c, b);
         nb_vals(g, L.e, i, j, k, c, v);
-        T num = b[0] * v[0];
-        num += b[1] * v[1];
-        num += b[2] * v[2];
-        num += b[3] * v[3];
-        num += b[4] * v[4];
-        num += b[5] * v[5];
-        num -= h2 * L.f[c];
-        const T den = ((b[0] + b[1]) + (b[2] + b[3])) + (b[4] + b[5]);
-        L.e[c] = num / den;
+        L.e[c] = gs_update(b, v, L.f[c], h2);
     }
 }
 

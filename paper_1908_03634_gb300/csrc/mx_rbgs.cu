@@ -1,0 +1,132 @@
+// One full red-black Gauss-Seidel sweep (red cells, then black cells) of the
+// FP32 correction equation L e = f in a single pass over memory.
+//
+// A block owns a TX x TY column tile and marches up a z-chunk.  The old e
+// plane t+1 is staged in shared memory with a 2-cell halo (5-plane ring);
+// red cells of plane t are updated on the tile plus a 1-cell halo (the halo is
+// recomputed redundantly, so no block reads another block's output), then black
+// cells of plane t-1 are updated on the tile from the new red values of planes
+// t-2, t-1, t.  In z the pipeline lags by one plane: red(t) only reads black
+// values that black(t-1) has not yet replaced.  The result goes to a second
+// buffer (e_out), so overlapping halos never race.  Per cell the arithmetic is
+// exactly that of the two-pass colour kernels (gs_update), so both produce
+// bit-identical sweeps.
+//
+// Variants: ZERO = the input correction is identically 0 (first sweep of a
+// V-cycle level: no read of e); PROLONG = the input is e + P e_coarse
+// (piecewise-constant prolongation applied on load, the first sweep after the
+// coarse-grid correction).
+#include "mx_rbgs.cuh"
+#include "mx_stencil.cuh"
+
+constexpr int TX = 32, TY = 8;
+constexpr int R1X = TX + 2, R1Y = TY + 2;  // tile + 1 halo: red updates
+constexpr int R2X = TX + 4, R2Y = TY + 4;  // tile + 2 halo: staged old e
+constexpr int NSLOT = 5;
+constexpr int RB_THREADS = ((R1X * R1Y + 31) / 32) * 32;  // 352
+constexpr int ZCH = 32;                                    // z-chunk per block
+
+__device__ __forceinline__ int wrap_or_neg(int x, int n, bool per) {
+    if (x >= 0 && x < n) return x;
+    if (!per) return -1;
+    return x < 0 ? x + n : x - n;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(RB_THREADS, 4)
+    rbgs_fused_kernel(Level<float> L, const float *__restrict__ ein, float *__restrict__ eout,
+                      const float *__restrict__ ecoarse, int ncx, int ncy, float h2) {
+    __shared__ float slot[NSLOT][R2Y][R2X];
+    const DGeom &g = L.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const bool px_ = gper(g, 0), py_ = gper(g, 1), pz_ = gper(g, 2);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * ZCH, z1 = min(z0 + ZCH, nz);
+    const int tid = threadIdx.x;
+
+    // this thread's R1 position
+    const bool active = tid < R1X * R1Y;
+    const int rx = active ? tid % R1X : 0, ry = active ? tid / R1X : 0;
+    const int gxu = x0 - 1 + rx, gyu = y0 - 1 + ry;  // unwrapped (colour parity)
+    const int gx = wrap_or_neg(gxu, nx, px_), gy = wrap_or_neg(gyu, ny, py_);
+    const bool inplane = active && gx >= 0 && gy >= 0;
+    const bool interior = inplane && rx >= 1 && rx <= TX && ry >= 1 && ry <= TY;
+    const int qx = rx + 1, qy = ry + 1;  // position in the R2 slot
+
+    auto load_plane = [&](int t) {
+        const int sl = ((t % NSLOT) + NSLOT) % NSLOT;
+        const int gz = wrap_or_neg(t, nz, pz_);
+        for (int q = tid; q < R2X * R2Y; q += RB_THREADS) {
+            const int ax = q % R2X, ay = q / R2X;
+            float v = 0.f;
+            if (MODE != RB_ZERO && gz >= 0) {
+                const int lx = wrap_or_neg(x0 - 2 + ax, nx, px_), ly = wrap_or_neg(y0 - 2 + ay, ny, py_);
+                if (lx >= 0 && ly >= 0) {
+                    const long long c = lx + (long long)nx * (ly + (long long)ny * gz);
+                    v = ein[c];
+                    if (MODE == RB_PROLONG)
+                        v += ecoarse[(lx >> 1) + (long long)ncx * ((ly >> 1) + (long long)ncy * (gz >> 1))];
+                }
+            }
+            slot[sl][ay][ax] = v;
+        }
+    };
+
+    load_plane(z0 - 2);
+    load_plane(z0 - 1);
+    for (int t = z0 - 1; t <= z1; t++) {
+        load_plane(t + 1);
+        __syncthreads();
+        const int st = ((t % NSLOT) + NSLOT) % NSLOT;
+        const int sm = ((t - 1) % NSLOT + NSLOT) % NSLOT;
+        const int sp = ((t + 1) % NSLOT + NSLOT) % NSLOT;
+        const int gz = wrap_or_neg(t, nz, pz_);
+        // red cells of plane t on the tile + 1 halo
+        if (inplane && gz >= 0 && ((gxu + gyu + t) & 1) == 0) {
+            const long long c = gx + (long long)nx * (gy + (long long)ny * gz);
+            float b[6], v[6];
+            face_coefs(L, gx, gy, gz, c, b);
+            v[0] = slot[st][qy][qx - 1];
+            v[1] = slot[st][qy][qx + 1];
+            v[2] = slot[st][qy - 1][qx];
+            v[3] = slot[st][qy + 1][qx];
+            v[4] = slot[sm][qy][qx];
+            v[5] = slot[sp][qy][qx];
+            slot[st][qy][qx] = gs_update(b, v, L.f[c], h2);
+        }
+        // plane t-1 of the tile is final after its black cells
+        const int tb = t - 1;
+        if (interior && tb >= z0 && tb < z1) {
+            const long long c = gx + (long long)nx * (gy + (long long)ny * tb);
+            if (((gxu + gyu + tb) & 1) == 1) {
+                const int s2 = ((tb - 1) % NSLOT + NSLOT) % NSLOT;
+                float b[6], v[6];
+                face_coefs(L, gx, gy, tb, c, b);
+                v[0] = slot[sm][qy][qx - 1];
+                v[1] = slot[sm][qy][qx + 1];
+                v[2] = slot[sm][qy - 1][qx];
+                v[3] = slot[sm][qy + 1][qx];
+                v[4] = slot[s2][qy][qx];
+                v[5] = slot[st][qy][qx];
+                eout[c] = gs_update(b, v, L.f[c], h2);
+            } else {
+                eout[c] = slot[sm][qy][qx];
+            }
+        }
+    }
+}
+
+void k_rbgs_fused(cudaStream_t s, const Level<float> &L, const float *ein, float *eout, int mode,
+                  const Level<float> *coarse) {
+    const DGeom &g = L.g;
+    dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + ZCH - 1) / ZCH);
+    const float h2 = float(g.h * g.h);
+    const float *ec = coarse ? coarse->e : nullptr;
+    const int ncx = coarse ? coarse->g.n[0] : 0, ncy = coarse ? coarse->g.n[1] : 0;
+    if (mode == RB_ZERO)
+        rbgs_fused_kernel<RB_ZERO><<<grid, RB_THREADS, 0, s>>>(L, ein, eout, ec, ncx, ncy, h2);
+    else if (mode == RB_PROLONG)
+        rbgs_fused_kernel<RB_PROLONG><<<grid, RB_THREADS, 0, s>>>(L, ein, eout, ec, ncx, ncy, h2);
+    else
+        rbgs_fused_kernel<RB_PLAIN><<<grid, RB_THREADS, 0, s>>>(L, ein, eout, ec, ncx, ncy, h2);
+}

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mx_rbgs.cuh"
 #include "mx_solver.cuh"
 #include "mx_stencil.cuh"
 
@@ -31,11 +32,13 @@ static void carve_level(Bump &b, Level<T> &L, const DGeom &g, bool coefs, bool f
     } else {
         L.bx = L.by = L.bz = L.hx = L.hy = L.hz = nullptr;
     }
+    L.e2 = nullptr;
     if (fe) {
         L.f = b.take<T>(g.N);
         L.e = b.take<T>(g.N);
+        L.e2 = b.take<T>(g.N);
     } else {
-        L.f = L.e = nullptr;
+        L.f = L.e = L.e2 = nullptr;
     }
 }
 
@@ -49,19 +52,33 @@ static void carve_hier(Bump &b, Hier<T> &H, const DGeom *gs, int nl, bool level0
 static void carve_plan(Bump &b, MacPlan &P) {
     DGeom gs[MX_MAXLEV];
     const int nl = mac_levels(P.g, gs);
-    carve_level(b, P.L64, P.g, true, true);
+    const DGeom &g = P.g;
     if (P.prec == MX_PREC_MIXED) {
         carve_hier(b, P.H32, gs, nl, true);
-        P.tmp32 = b.take<float>(P.g.N);
+        DFArrays &D = P.D;
+        D.bxl = b.take<float>(g.N);
+        D.byl = b.take<float>(g.N);
+        D.bzl = b.take<float>(g.N);
+        D.hxl = gper(g, 0) ? nullptr : b.take<float>((size_t)g.n[1] * g.n[2]);
+        D.hyl = gper(g, 1) ? nullptr : b.take<float>((size_t)g.n[0] * g.n[2]);
+        D.hzl = gper(g, 2) ? nullptr : b.take<float>((size_t)g.n[0] * g.n[1]);
+        D.fh = b.take<float>(g.N);
+        D.fl = b.take<float>(g.N);
+        D.ph = b.take<float>(g.N);
+        D.pl = b.take<float>(g.N);
+        P.tmp32 = b.take<float>(g.N);
         P.H64.nlev = 0;
+        P.L64 = Level<double>{};
+        P.L64.g = g;
     } else {
+        carve_level(b, P.L64, g, true, true);
         carve_hier(b, P.H64, gs, nl, false);
         Level<double> &l0 = P.H64.lev[0];
         l0.bx = P.L64.bx; l0.by = P.L64.by; l0.bz = P.L64.bz;
         l0.hx = P.L64.hx; l0.hy = P.L64.hy; l0.hz = P.L64.hz;
         P.H32.nlev = 0;
     }
-    P.tmp64 = b.take<double>(P.g.N);
+    P.tmp64 = b.take<double>(g.N);
 }
 
 static bool same_geom(const DGeom &a, const DGeom &b) {
@@ -140,8 +157,66 @@ void destroy_plans(mx_ctx *c) {
 // ------------------------------------------------------------------------------
 // V-cycle on the correction equation L e = r (level-0 f holds r, e is zeroed here)
 
+// Single-pass sweeps: each level ping-pongs between e and e2; the first pre-
+// sweep starts from e = 0 without reading it, and the first post-sweep applies
+// the prolongation on load.  The number of sweeps fixes which buffer holds the
+// final correction; the first output buffer is chosen so that it ends in e.
+static void vcycle_fused(cudaStream_t s, Hier<float> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc) {
+    const int nl = H.nlev;
+    float *cur[MX_MAXLEV];
+    for (int l = 0; l < nl - 1; l++) {
+        Level<float> &L = H.lev[l];
+        float *bufs[2] = {L.e, L.e2};
+        int w = ((nu1 + nu2) % 2 == 1) ? 0 : 1;
+        const float *in = nullptr;
+        if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
+        for (int q = 0; q < nu1; q++) {
+            k_rbgs_fused(s, L, in, bufs[w], q == 0 ? RB_ZERO : RB_PLAIN, nullptr);
+            in = bufs[w];
+            w ^= 1;
+        }
+        cur[l] = const_cast<float *>(in);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_SMOOTH_FINE, nu1);
+            prof_begin(pc, s, MX_PH_RESTRICT_FINE);
+        }
+        Level<float> Lc = L;
+        Lc.e = cur[l];
+        k_resid_restrict(s, Lc, H.lev[l + 1]);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_RESTRICT_FINE, 1);
+            prof_begin(pc, s, MX_PH_COARSE);
+        }
+    }
+    if (nl == 1) prof_begin(pc, s, MX_PH_COARSE);
+    k_bottom(s, H.lev[nl - 1], H.bot_scratch, bot_iters, singular);
+    for (int l = nl - 2; l >= 0; l--) {
+        Level<float> &L = H.lev[l];
+        float *other = cur[l] == L.e ? L.e2 : L.e;
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_COARSE, 0);
+            prof_begin(pc, s, MX_PH_SMOOTH_FINE);
+        }
+        const float *in = cur[l];
+        float *out = other;
+        for (int q = 0; q < nu2; q++) {
+            k_rbgs_fused(s, L, in, out, q == 0 ? RB_PROLONG : RB_PLAIN, q == 0 ? &H.lev[l + 1] : nullptr);
+            in = out;
+            out = (out == L.e) ? L.e2 : L.e;
+        }
+        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, nu2);
+    }
+    if (nl == 1) prof_end(pc, s, MX_PH_COARSE, 0);
+}
+
 template <typename T>
-void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc) {
+void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc, int fused) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (fused && nu1 >= 1 && nu2 >= 1) {
+            vcycle_fused(s, H, nu1, nu2, bot_iters, singular, pc);
+            return;
+        }
+    }
     prof_begin(pc, s, MX_PH_UPDATE);
     cudaMemsetAsync(H.lev[0].e, 0, sizeof(T) * H.lev[0].g.N, s);
     prof_end(pc, s, MX_PH_UPDATE, 1);
@@ -187,8 +262,8 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
     }
     if (H.nlev == 1) prof_end(pc, s, MX_PH_COARSE, ncoarse);
 }
-template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *);
-template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *);
+template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *, int);
+template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *, int);
 
 template <typename T>
 static void build_hierarchy(cudaStream_t s, Hier<T> &H) {
@@ -196,17 +271,51 @@ static void build_hierarchy(cudaStream_t s, Hier<T> &H) {
 }
 
 // One refinement iteration after the residual: V-cycle, update, next residual.
-template <typename T>
-static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular,
-                    int nb, mx_ctx *pc) {
-    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc);
+// Mixed precision: FP32 V-cycle, double-float update and residual.
+static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const mx_opts &o, int singular, int nb,
+                    mx_ctx *pc) {
+    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused);
     prof_begin(pc, s, MX_PH_UPDATE);
-    k_update<T>(s, P.g, phi, H.lev[0].e, c->state);
+    k_df_update(s, P.g, P.D, H.lev[0].e, c->state);
     prof_end(pc, s, MX_PH_UPDATE, 1);
     prof_begin(pc, s, MX_PH_RESID64);
-    k_residual64<T>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
+    k_df_resid(s, H.lev[0], P.D, c->state, c->partials);
     k_finalize_residual(s, c->partials, nb, c->state);
     prof_end(pc, s, MX_PH_RESID64, 2);
+}
+// Plain FP64: FP64 V-cycle, FP64 update and residual.
+static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, const mx_opts &o, int singular, int nb,
+                    mx_ctx *pc, double *phi) {
+    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc);
+    prof_begin(pc, s, MX_PH_UPDATE);
+    k_update<double>(s, P.g, phi, H.lev[0].e, c->state);
+    prof_end(pc, s, MX_PH_UPDATE, 1);
+    prof_begin(pc, s, MX_PH_RESID64);
+    k_residual64<double>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
+    k_finalize_residual(s, c->partials, nb, c->state);
+    prof_end(pc, s, MX_PH_RESID64, 2);
+}
+
+template <typename T>
+static void ir_first_residual(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, int nb);
+template <>
+void ir_first_residual<float>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, int nb) {
+    k_df_resid(s, H.lev[0], P.D, c->state, c->partials);
+    k_finalize_residual(s, c->partials, nb, c->state);
+}
+template <>
+void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, int nb) {
+    k_residual64<double>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
+    k_finalize_residual(s, c->partials, nb, c->state);
+}
+
+static void ir_step(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, const mx_opts &o, int singular,
+                    int nb, mx_ctx *pc) {
+    ir_body(s, c, P, H, o, singular, nb, pc);
+}
+static void ir_step(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, const mx_opts &o,
+                    int singular, int nb, mx_ctx *pc) {
+    ir_body(s, c, P, H, o, singular, nb, pc, phi);
 }
 
 // Conditional-while graph of the refinement loop: the finalize kernel of each
@@ -218,7 +327,8 @@ __global__ void set_cond_kernel(cudaGraphConditionalHandle h, const SolveState *
 template <typename T>
 static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular, int nb) {
     cudaStream_t s = c->stream;
-    if (!P.graph || P.graph_phi != phi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 || P.graph_bot != o.bottom_iters) {
+    if (!P.graph || P.graph_phi != phi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 || P.graph_bot != o.bottom_iters ||
+        P.graph_fused != o.fused) {
         if (P.graph) {
             cudaGraphExecDestroy(P.graph);
             P.graph = nullptr;
@@ -239,7 +349,7 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
         MX_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            ir_body<T>(cs, c, P, H, phi, o, singular, nb, nullptr);
+            ir_step(cs, c, P, H, phi, o, singular, nb, nullptr);
             set_cond_kernel<<<1, 1, 0, cs>>>(handle, c->state);
             cudaGraph_t captured;
             e = cudaStreamEndCapture(cs, &captured);
@@ -259,6 +369,7 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
         P.graph_nu1 = o.nu1;
         P.graph_nu2 = o.nu2;
         P.graph_bot = o.bottom_iters;
+        P.graph_fused = o.fused;
     }
     // the while node runs its body while the condition is 1; enter only if the
     // first residual asked for a V-cycle
@@ -271,8 +382,7 @@ static mx_status run_ir(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx
     cudaStream_t s = c->stream;
     const int nb = stencil_blocks(P.g);
     prof_begin(c, s, MX_PH_RESID64);
-    k_residual64<T>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
-    k_finalize_residual(s, c->partials, nb, c->state);
+    ir_first_residual<T>(s, c, P, H, phi, nb);
     prof_end(c, s, MX_PH_RESID64, 2);
     if (o.use_graph && !c->prof) {
         // the loop is entered unconditionally by the while node; a first
@@ -286,7 +396,7 @@ static mx_status run_ir(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         MX_CUDA(c, cudaStreamSynchronize(s));
         if (c->hstate->done) break;
-        ir_body<T>(s, c, P, H, phi, o, singular, nb, c);
+        ir_step(s, c, P, H, phi, o, singular, nb, c);
         prof_flush(c);
     }
     return MX_OK;
@@ -309,11 +419,11 @@ static mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
 
 static void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0) {
     cudaStream_t s = c->stream;
-    k_mac_coeffs64(s, P.L64, rho, beta0);
     if (P.prec == MX_PREC_MIXED) {
-        k_round_coeffs(s, P.L64, P.H32.lev[0]);
+        k_mac_coeffs_df(s, P.H32.lev[0], P.D, rho, beta0);
         build_hierarchy(s, P.H32);
     } else {
+        k_mac_coeffs64(s, P.L64, rho, beta0);
         build_hierarchy(s, P.H64);
     }
 }
@@ -347,7 +457,8 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     prof_begin(c, s, MX_PH_SETUP);
     setup_coefficients(c, *P, rho, beta0);
     // right-hand side f = D(beta0 U) - beta0 Sbar, mean removal, norms
-    k_mac_rhs(s, g, ux, uy, uz, beta0, sbar, P->L64.f, c->partials, nb);
+    double *f64 = o.prec == MX_PREC_MIXED ? P->tmp64 : P->L64.f;
+    k_mac_rhs(s, g, ux, uy, uz, beta0, sbar, f64, c->partials, nb);
     k_finalize_rhs(s, c->partials, nb, c->state, g.N, singular && o.remove_mean, 0);
     if (singular && !o.remove_mean) {
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -360,14 +471,25 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
             return set_err(c, MX_ERR_INCOMPAT, "singular problem: right-hand side has non-zero mean and remove_mean = 0");
         }
     }
-    k_sub_mean_norm(s, g, P->L64.f, c->state, c->partials, nbr);
+    if (o.prec == MX_PREC_MIXED) {
+        k_sub_mean_split(s, g, f64, c->state, P->D, c->partials, nbr);
+        if (o.use_initial_guess) {
+            k_df_from_double(s, g.N, phi, P->D);
+        } else {
+            MX_CUDA(c, cudaMemsetAsync(P->D.ph, 0, sizeof(float) * g.N, s));
+            MX_CUDA(c, cudaMemsetAsync(P->D.pl, 0, sizeof(float) * g.N, s));
+        }
+    } else {
+        k_sub_mean_norm(s, g, f64, c->state, c->partials, nbr);
+        if (!o.use_initial_guess) MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.N, s));
+    }
     k_finalize_rhs(s, c->partials, nbr, c->state, g.N, 0, 1);
-    if (!o.use_initial_guess) MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.N, s));
     prof_end(c, s, MX_PH_SETUP, 0);
 
     if (o.prec == MX_PREC_MIXED) st = run_ir<float>(c, *P, P->H32, phi, o, singular);
     else st = run_ir<double>(c, *P, P->H64, phi, o, singular);
     if (st) return st;
+    if (o.prec == MX_PREC_MIXED) k_df_to_double(s, g.N, P->D, phi);
 
     prof_begin(c, s, MX_PH_FINISH);
     if (singular) {  // normalise mean(phi) = 0
@@ -432,7 +554,8 @@ static mx_status mac_apply_or_residual(mx_ctx *c, const mx_geom *geom, int prec,
     MacPlan *P = get_mac_plan(c, g, prec, &st);
     if (!P) return st;
     cudaStream_t s = c->stream;
-    k_mac_coeffs64(s, P->L64, rho, beta0);
+    if (prec == MX_PREC_FP64) k_mac_coeffs64(s, P->L64, rho, beta0);
+    else k_mac_coeffs_df(s, P->H32.lev[0], P->D, rho, beta0);
     if (prec == MX_PREC_FP64) {
         if (f) {
             const int nb = stencil_blocks(g);
@@ -443,7 +566,6 @@ static mx_status mac_apply_or_residual(mx_ctx *c, const mx_geom *geom, int prec,
         }
     } else {
         Level<float> &l0 = P->H32.lev[0];
-        k_round_coeffs(s, P->L64, l0);
         k_cast<float>(s, g.N, phi, l0.e);
         k_apply<float>(s, l0, l0.e, P->tmp32);
         if (f) {

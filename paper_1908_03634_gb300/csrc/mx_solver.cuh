@@ -2,6 +2,7 @@
 // FP64 finest-level operator and the multigrid hierarchy of the correction solve.
 #pragma once
 
+#include "mx_df.cuh"
 #include "mx_internal.cuh"
 
 template <typename T>
@@ -16,15 +17,16 @@ struct MacPlan {
     int prec = MX_PREC_MIXED;
     void *mem = nullptr;
     size_t bytes = 0;
-    Level<double> L64;  // FP64 finest-level coefficients; L64.f = FP64 right-hand side
+    Level<double> L64;  // FP64 path: finest-level coefficients; L64.f = FP64 right-hand side
     Hier<float> H32;    // mixed: the FP32 correction hierarchy
+    DFArrays D;         // mixed: double-float phi, h^2 f and coefficient lo parts
     Hier<double> H64;   // FP64: the FP64 correction hierarchy (level 0 shares L64's coefficients)
     float *tmp32 = nullptr;
     double *tmp64 = nullptr;
     // CUDA graph of the refinement loop, keyed by the pointers it was captured with
     cudaGraphExec_t graph = nullptr;
     const void *graph_phi = nullptr;
-    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_fused = -1;
     long long last_use = 0;
 };
 
@@ -33,4 +35,5 @@ void destroy_plans(mx_ctx *c);
 mx_status ensure_partials(mx_ctx *c, long long nblocks);
 
 template <typename T>
-void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *prof = nullptr);
+void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *prof = nullptr,
+            int fused = 0);

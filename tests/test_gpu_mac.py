@@ -219,3 +219,16 @@ def test_argument_errors(mx, ctx):
     with pytest.raises(mx.MXError) as e:
         mx.mx_mac_project(ctx, g2, *u2, one2, one2, one2, one2.clone(), mx.default_opts())
     assert e.value.status == mx.MX_ERR_ARG
+
+
+@pytest.mark.parametrize("nu", [(2, 2), (1, 1), (3, 2), (1, 2)])
+@pytest.mark.parametrize("name", ["planar32", "star512_at_40", "ragged_neumann"])
+def test_single_pass_sweeps_bit_identical_to_two_pass(mx, ctx, name, nu):
+    """The fused red+black sweep (with the prolongation applied on load) does
+    per cell exactly the arithmetic of the two colour kernels."""
+    w = WORKLOADS[name]()
+    a = run_gpu_project(mx, ctx, w, 1, fused=1, nu1=nu[0], nu2=nu[1])
+    b = run_gpu_project(mx, ctx, w, 1, fused=0, nu1=nu[0], nu2=nu[1])
+    assert a[1]["vcycles"] == b[1]["vcycles"]
+    assert np.array_equal(a[2], b[2])
+    assert a[1]["status"] == 0
