@@ -26,10 +26,14 @@ constexpr int NSLOT = 5;
 constexpr int RB_THREADS = ((R1X * R1Y + 31) / 32) * 32;  // 352
 constexpr int ZCH = 32;                                    // z-chunk per block
 
-__device__ __forceinline__ int wrap_or_neg(int x, int n, bool per) {
-    if (x >= 0 && x < n) return x;
-    if (!per) return -1;
-    return x < 0 ? x + n : x - n;
+// Map an unwrapped coordinate u of a tile position to a cell index, or -1 when
+// the position holds no cell: beyond a non-periodic wall, or farther than
+// `reach` cells past the end of the box (tiles wider than a small coarse level
+// must not wrap more than once).
+__device__ __forceinline__ int map_coord(int u, int n, bool per, int reach) {
+    if (u >= 0 && u < n) return u;
+    if (!per || u < -reach || u >= n + reach) return -1;
+    return u < 0 ? u + n : u - n;
 }
 
 template <int MODE>
@@ -48,19 +52,20 @@ __global__ void __launch_bounds__(RB_THREADS, 4)
     const bool active = tid < R1X * R1Y;
     const int rx = active ? tid % R1X : 0, ry = active ? tid / R1X : 0;
     const int gxu = x0 - 1 + rx, gyu = y0 - 1 + ry;  // unwrapped (colour parity)
-    const int gx = wrap_or_neg(gxu, nx, px_), gy = wrap_or_neg(gyu, ny, py_);
+    const int gx = map_coord(gxu, nx, px_, 1), gy = map_coord(gyu, ny, py_, 1);
     const bool inplane = active && gx >= 0 && gy >= 0;
-    const bool interior = inplane && rx >= 1 && rx <= TX && ry >= 1 && ry <= TY;
+    // owned cells: inside the tile and inside the box (unwrapped)
+    const bool interior = inplane && rx >= 1 && rx <= TX && ry >= 1 && ry <= TY && gxu < nx && gyu < ny;
     const int qx = rx + 1, qy = ry + 1;  // position in the R2 slot
 
     auto load_plane = [&](int t) {
         const int sl = ((t % NSLOT) + NSLOT) % NSLOT;
-        const int gz = wrap_or_neg(t, nz, pz_);
+        const int gz = map_coord(t, nz, pz_, 2);
         for (int q = tid; q < R2X * R2Y; q += RB_THREADS) {
             const int ax = q % R2X, ay = q / R2X;
             float v = 0.f;
             if (MODE != RB_ZERO && gz >= 0) {
-                const int lx = wrap_or_neg(x0 - 2 + ax, nx, px_), ly = wrap_or_neg(y0 - 2 + ay, ny, py_);
+                const int lx = map_coord(x0 - 2 + ax, nx, px_, 2), ly = map_coord(y0 - 2 + ay, ny, py_, 2);
                 if (lx >= 0 && ly >= 0) {
                     const long long c = lx + (long long)nx * (ly + (long long)ny * gz);
                     v = ein[c];
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(RB_THREADS, 4)
         const int st = ((t % NSLOT) + NSLOT) % NSLOT;
         const int sm = ((t - 1) % NSLOT + NSLOT) % NSLOT;
         const int sp = ((t + 1) % NSLOT + NSLOT) % NSLOT;
-        const int gz = wrap_or_neg(t, nz, pz_);
+        const int gz = map_coord(t, nz, pz_, 1);
         // red cells of plane t on the tile + 1 halo
         if (inplane && gz >= 0 && ((gxu + gyu + t) & 1) == 0) {
             const long long c = gx + (long long)nx * (gy + (long long)ny * gz);
