@@ -6,6 +6,7 @@
 #include <map>
 #include <memory>
 
+#include "mx_coarse.cuh"
 #include "mx_stencil.cuh"
 #include "mx_solver.cuh"
 
@@ -139,7 +140,8 @@ mx_status mx_create(mx_ctx **out, int device, void *stream) {
     if (cudaMalloc(&c->state, sizeof(SolveState) * 4) != cudaSuccess ||
         cudaMallocHost(&c->hstate, sizeof(SolveState) * 4) != cudaSuccess ||
         cudaMalloc(&c->partials, sizeof(double) * 3 * c->max_partials) != cudaSuccess ||
-        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        coarse_init() != cudaSuccess) {
         cudaGetLastError();
         mx_destroy(c);
         return MX_ERR_CUDA;

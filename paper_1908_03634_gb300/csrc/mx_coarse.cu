@@ -1,0 +1,264 @@
+// The coarse end of the V-cycle in one CTA: every level of at most
+// COARSE_MAX_CELLS cells, from the first such level down to the bottom solve and
+// back up, with the corrections and right-hand sides held in shared memory.
+// On these levels a grid-wide launch does a few microseconds of work, so one
+// launch replaces the dozens of per-level launches (smoothing, restriction,
+// BiCGStab bottom solve, prolongation) that would otherwise dominate.
+#include "mx_coarse.cuh"
+#include "mx_rbgs.cuh"
+#include "mx_stencil.cuh"
+
+constexpr int CT = 1024;  // threads of the coarse CTA
+
+template <typename T>
+struct CoarseArgs {
+    int nl;                        // number of levels handled (the last is the bottom)
+    Level<T> lev[COARSE_MAX_LEVELS];
+    int nu1, nu2, bot_iters, singular;
+};
+
+__device__ __forceinline__ void cell_ijk(const DGeom &g, int c, int &i, int &j, int &k) {
+    i = c % g.n[0];
+    const int r = c / g.n[0];
+    j = r % g.n[1];
+    k = r / g.n[1];
+}
+
+template <typename T>
+__device__ void cta_colour(const Level<T> &L, T *e, const T *f, int colour, T h2) {
+    const DGeom &g = L.g;
+    for (int c = threadIdx.x; c < g.N; c += CT) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        if (((i + j + k) & 1) != colour) continue;
+        T b[6], v[6];
+        face_coefs(L, i, j, k, c, b);
+        nb_vals(g, e, i, j, k, c, v);
+        e[c] = gs_update(b, v, f[c], h2);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void cta_resid_restrict(const Level<T> &F, const T *ef, const T *ff, const DGeom &gc, T *fc, T *ec, T ih2) {
+    const DGeom &g = F.g;
+    for (int C = threadIdx.x; C < gc.N; C += CT) {
+        int I, J, K;
+        cell_ijk(gc, C, I, J, K);
+        T s = T(0);
+        for (int dk = 0; dk < 2; dk++)
+            for (int dj = 0; dj < 2; dj++)
+                for (int di = 0; di < 2; di++) {
+                    const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                    const int c = i + g.n[0] * (j + g.n[1] * k);
+                    T b[6], v[6];
+                    face_coefs(F, i, j, k, c, b);
+                    nb_vals(g, ef, i, j, k, c, v);
+                    s += ff[c] - flux_sum(b, v, ef[c]) * ih2;
+                }
+        fc[C] = s * T(0.125);
+        ec[C] = T(0);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void cta_prolong(const DGeom &gc, const T *ec, const DGeom &g, T *ef) {
+    for (int c = threadIdx.x; c < g.N; c += CT) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        ef[c] += ec[(i >> 1) + gc.n[0] * ((j >> 1) + gc.n[1] * (k >> 1))];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ T cta_dot(const T *a, const T *b, int n) {
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n; q += CT) s += double(a[q]) * double(b[q]);
+    double m = 0.0, z = 0.0;
+    block_red3(m, s, z);
+    __shared__ double res;
+    if (threadIdx.x == 0) res = s;
+    __syncthreads();
+    const T out = T(res);
+    __syncthreads();
+    return out;
+}
+
+template <typename T>
+__device__ void cta_apply(const Level<T> &L, const T *x, T *y, T ih2) {
+    const DGeom &g = L.g;
+    for (int c = threadIdx.x; c < g.N; c += CT) {
+        int i, j, k;
+        cell_ijk(g, c, i, j, k);
+        T b[6], v[6];
+        face_coefs(L, i, j, k, c, b);
+        nb_vals(g, x, i, j, k, c, v);
+        y[c] = flux_sum(b, v, x[c]) * ih2;
+    }
+    __syncthreads();
+}
+
+// BiCGStab on L x = f (x starts at 0), projected onto mean-free vectors when
+// the problem is singular; stops at relative residual 1e-6 or `iters`.
+template <typename T>
+__device__ void cta_bicgstab(const Level<T> &L, T *x, const T *f, T *scr, int iters, int singular, T ih2) {
+    const int n = int(L.g.N);
+    T *r = scr, *r0 = scr + n, *p = scr + 2 * n, *v = scr + 3 * n, *sv = scr + 4 * n, *tv = scr + 5 * n;
+    T mean = T(0);
+    if (singular) {
+        double s = 0.0;
+        for (int q = threadIdx.x; q < n; q += CT) s += double(f[q]);
+        double m = 0.0, z = 0.0;
+        block_red3(m, s, z);
+        __shared__ double sm;
+        if (threadIdx.x == 0) sm = s / n;
+        __syncthreads();
+        mean = T(sm);
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < n; q += CT) {
+        const T b = f[q] - mean;
+        x[q] = T(0);
+        r[q] = b;
+        r0[q] = b;
+        p[q] = T(0);
+        v[q] = T(0);
+    }
+    __syncthreads();
+    const T bnorm2 = cta_dot(r, r, n);
+    if (!(bnorm2 > T(0))) return;
+    const T tol2 = bnorm2 * T(1e-12);
+    T rho = T(1), alpha = T(1), omega = T(1);
+    for (int it = 0; it < iters; it++) {
+        const T rho1 = cta_dot(r0, r, n);
+        if (rho1 == T(0) || omega == T(0)) break;
+        const T beta = (rho1 / rho) * (alpha / omega);
+        for (int q = threadIdx.x; q < n; q += CT) p[q] = r[q] + beta * (p[q] - omega * v[q]);
+        __syncthreads();
+        cta_apply(L, p, v, ih2);
+        const T r0v = cta_dot(r0, v, n);
+        if (r0v == T(0)) break;
+        alpha = rho1 / r0v;
+        for (int q = threadIdx.x; q < n; q += CT) sv[q] = r[q] - alpha * v[q];
+        __syncthreads();
+        const T ss = cta_dot(sv, sv, n);
+        if (ss <= tol2) {
+            for (int q = threadIdx.x; q < n; q += CT) x[q] += alpha * p[q];
+            __syncthreads();
+            break;
+        }
+        cta_apply(L, sv, tv, ih2);
+        const T tt = cta_dot(tv, tv, n);
+        const T ts = cta_dot(tv, sv, n);
+        omega = tt > T(0) ? ts / tt : T(0);
+        for (int q = threadIdx.x; q < n; q += CT) {
+            x[q] += alpha * p[q] + omega * sv[q];
+            r[q] = sv[q] - omega * tv[q];
+        }
+        __syncthreads();
+        rho = rho1;
+        const T rr = cta_dot(r, r, n);
+        if (rr <= tol2) break;
+    }
+    if (singular) {
+        double s = 0.0;
+        for (int q = threadIdx.x; q < n; q += CT) s += double(x[q]);
+        double m = 0.0, z = 0.0;
+        block_red3(m, s, z);
+        __shared__ double sm2;
+        if (threadIdx.x == 0) sm2 = s / n;
+        __syncthreads();
+        const T mx = T(sm2);
+        for (int q = threadIdx.x; q < n; q += CT) x[q] -= mx;
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT) coarse_vcycle_kernel(CoarseArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *e[COARSE_MAX_LEVELS], *f[COARSE_MAX_LEVELS];
+    size_t off = 0;
+    for (int l = 0; l < A.nl; l++) {
+        e[l] = sm + off;
+        off += A.lev[l].g.N;
+        f[l] = sm + off;
+        off += A.lev[l].g.N;
+    }
+    T *scr = sm + off;  // 6 bottom vectors
+    // right-hand side of the first level from global memory
+    for (int c = threadIdx.x; c < A.lev[0].g.N; c += CT) {
+        f[0][c] = A.lev[0].f[c];
+        e[0][c] = T(0);
+    }
+    __syncthreads();
+    const int nb = A.nl - 1;
+    for (int l = 0; l < nb; l++) {
+        const Level<T> &L = A.lev[l];
+        const T h2 = T(L.g.h * L.g.h);
+        for (int q = 0; q < A.nu1; q++) {
+            cta_colour(L, e[l], f[l], 0, h2);
+            cta_colour(L, e[l], f[l], 1, h2);
+        }
+        cta_resid_restrict(L, e[l], f[l], A.lev[l + 1].g, f[l + 1], e[l + 1], T(1.0 / (L.g.h * L.g.h)));
+    }
+    {
+        const Level<T> &L = A.lev[nb];
+        cta_bicgstab(L, e[nb], f[nb], scr, A.bot_iters, A.singular, T(1.0 / (L.g.h * L.g.h)));
+    }
+    for (int l = nb - 1; l >= 0; l--) {
+        const Level<T> &L = A.lev[l];
+        const T h2 = T(L.g.h * L.g.h);
+        cta_prolong(A.lev[l + 1].g, e[l + 1], L.g, e[l]);
+        for (int q = 0; q < A.nu2; q++) {
+            cta_colour(L, e[l], f[l], 0, h2);
+            cta_colour(L, e[l], f[l], 1, h2);
+        }
+    }
+    for (int c = threadIdx.x; c < A.lev[0].g.N; c += CT) A.lev[0].e[c] = e[0][c];
+}
+
+template <typename T>
+size_t coarse_smem_bytes(const Level<T> *levs, int nl) {
+    size_t n = 0;
+    for (int l = 0; l < nl; l++) n += 2 * (size_t)levs[l].g.N;
+    n += 6 * (size_t)levs[nl - 1].g.N;
+    return n * sizeof(T);
+}
+
+template <typename T>
+bool coarse_fits(const Level<T> *levs, int nl) {
+    return nl >= 1 && nl <= COARSE_MAX_LEVELS && levs[0].g.N <= COARSE_MAX_CELLS &&
+           coarse_smem_bytes(levs, nl) <= COARSE_MAX_SMEM;
+}
+
+template <typename T>
+void k_coarse_vcycle(cudaStream_t s, const Level<T> *levs, int nl, int nu1, int nu2, int bot_iters, int singular) {
+    CoarseArgs<T> A;
+    A.nl = nl;
+    for (int l = 0; l < nl; l++) A.lev[l] = levs[l];
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.bot_iters = bot_iters;
+    A.singular = singular;
+    const size_t smem = coarse_smem_bytes(levs, nl);
+    coarse_vcycle_kernel<T><<<1, CT, smem, s>>>(A);
+}
+
+// Allow the coarse kernels more than the default 48 KB of dynamic shared
+// memory (called once per device, outside any stream capture).
+cudaError_t coarse_init() {
+    cudaError_t e = cudaFuncSetAttribute(coarse_vcycle_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         COARSE_MAX_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(coarse_vcycle_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                COARSE_MAX_SMEM);
+}
+
+template bool coarse_fits<float>(const Level<float> *, int);
+template bool coarse_fits<double>(const Level<double> *, int);
+template void k_coarse_vcycle<float>(cudaStream_t, const Level<float> *, int, int, int, int, int);
+template void k_coarse_vcycle<double>(cudaStream_t, const Level<double> *, int, int, int, int, int);

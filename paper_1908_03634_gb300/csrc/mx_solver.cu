@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mx_coarse.cuh"
 #include "mx_rbgs.cuh"
 #include "mx_solver.cuh"
 #include "mx_stencil.cuh"
@@ -157,110 +158,96 @@ void destroy_plans(mx_ctx *c) {
 // ------------------------------------------------------------------------------
 // V-cycle on the correction equation L e = r (level-0 f holds r, e is zeroed here)
 
-// Single-pass sweeps: each level ping-pongs between e and e2; the first pre-
-// sweep starts from e = 0 without reading it, and the first post-sweep applies
-// the prolongation on load.  The number of sweeps fixes which buffer holds the
-// final correction; the first output buffer is chosen so that it ends in e.
-static void vcycle_fused(cudaStream_t s, Hier<float> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc) {
-    const int nl = H.nlev;
-    float *cur[MX_MAXLEV];
-    for (int l = 0; l < nl - 1; l++) {
-        Level<float> &L = H.lev[l];
-        float *bufs[2] = {L.e, L.e2};
-        int w = ((nu1 + nu2) % 2 == 1) ? 0 : 1;
-        const float *in = nullptr;
-        if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
-        for (int q = 0; q < nu1; q++) {
-            k_rbgs_fused(s, L, in, bufs[w], q == 0 ? RB_ZERO : RB_PLAIN, nullptr);
-            in = bufs[w];
-            w ^= 1;
-        }
-        cur[l] = const_cast<float *>(in);
-        if (l == 0) {
-            prof_end(pc, s, MX_PH_SMOOTH_FINE, nu1);
-            prof_begin(pc, s, MX_PH_RESTRICT_FINE);
-        }
-        Level<float> Lc = L;
-        Lc.e = cur[l];
-        k_resid_restrict(s, Lc, H.lev[l + 1]);
-        if (l == 0) {
-            prof_end(pc, s, MX_PH_RESTRICT_FINE, 1);
-            prof_begin(pc, s, MX_PH_COARSE);
-        }
-    }
-    if (nl == 1) prof_begin(pc, s, MX_PH_COARSE);
-    k_bottom(s, H.lev[nl - 1], H.bot_scratch, bot_iters, singular);
-    for (int l = nl - 2; l >= 0; l--) {
-        Level<float> &L = H.lev[l];
-        float *other = cur[l] == L.e ? L.e2 : L.e;
-        if (l == 0) {
-            prof_end(pc, s, MX_PH_COARSE, 0);
-            prof_begin(pc, s, MX_PH_SMOOTH_FINE);
-        }
-        const float *in = cur[l];
-        float *out = other;
-        for (int q = 0; q < nu2; q++) {
-            k_rbgs_fused(s, L, in, out, q == 0 ? RB_PROLONG : RB_PLAIN, q == 0 ? &H.lev[l + 1] : nullptr);
-            in = out;
-            out = (out == L.e) ? L.e2 : L.e;
-        }
-        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, nu2);
-    }
-    if (nl == 1) prof_end(pc, s, MX_PH_COARSE, 0);
+// V-cycle on the correction equation L e = r (level-0 f holds r).
+//  * levels of >= FUSED_MIN_CELLS cells (FP32, fused = 1): single-pass sweeps
+//    ping-ponging between e and e2; the first pre-sweep starts from e = 0
+//    without reading it and the first post-sweep applies the prolongation on
+//    load; the first output buffer is chosen so that the result ends in e;
+//  * other levels above the coarse end: two-pass colour kernels in place;
+//  * the coarse end (levels of <= COARSE_MAX_CELLS cells, down to the bottom):
+//    one single-CTA kernel; without such a level, a BiCGStab bottom kernel.
+constexpr long long FUSED_MIN_CELLS = 1LL << 20;
+
+template <typename T>
+static int coarse_start(const Hier<T> &H) {
+    for (int l = 0; l < H.nlev; l++)
+        if (H.lev[l].g.N <= COARSE_MAX_CELLS && coarse_fits(&H.lev[l], H.nlev - l)) return l;
+    return H.nlev;
 }
 
 template <typename T>
 void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc, int fused) {
-    if constexpr (sizeof(T) == sizeof(float)) {
-        if (fused && nu1 >= 1 && nu2 >= 1) {
-            vcycle_fused(s, H, nu1, nu2, bot_iters, singular, pc);
-            return;
-        }
+    const int nl = H.nlev;
+    const int lc = coarse_start(H);
+    const int ldown = lc < nl ? lc : nl - 1;  // levels with their own kernels
+    const bool can_fuse = sizeof(T) == sizeof(float) && fused && nu1 >= 1 && nu2 >= 1;
+    auto is_fused = [&](int l) { return can_fuse && H.lev[l].g.N >= FUSED_MIN_CELLS; };
+    T *cur[MX_MAXLEV];
+    if (ldown > 0 && !is_fused(0)) {
+        prof_begin(pc, s, MX_PH_UPDATE);
+        cudaMemsetAsync(H.lev[0].e, 0, sizeof(T) * H.lev[0].g.N, s);
+        prof_end(pc, s, MX_PH_UPDATE, 1);
     }
-    prof_begin(pc, s, MX_PH_UPDATE);
-    cudaMemsetAsync(H.lev[0].e, 0, sizeof(T) * H.lev[0].g.N, s);
-    prof_end(pc, s, MX_PH_UPDATE, 1);
-    int ncoarse = 0;
-    for (int l = 0; l < H.nlev - 1; l++) {
+    for (int l = 0; l < ldown; l++) {
+        Level<T> &L = H.lev[l];
         if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
-        for (int q = 0; q < nu1; q++) {
-            k_rbgs(s, H.lev[l], 0);
-            k_rbgs(s, H.lev[l], 1);
+        if (is_fused(l)) {
+            float *bufs[2] = {(float *)L.e, (float *)L.e2};
+            int w = ((nu1 + nu2) % 2 == 1) ? 0 : 1;
+            const float *in = nullptr;
+            for (int q = 0; q < nu1; q++) {
+                k_rbgs_fused(s, *(Level<float> *)&L, in, bufs[w], q == 0 ? RB_ZERO : RB_PLAIN, nullptr);
+                in = bufs[w];
+                w ^= 1;
+            }
+            cur[l] = (T *)in;
+        } else {
+            for (int q = 0; q < nu1; q++) {
+                k_rbgs(s, L, 0);
+                k_rbgs(s, L, 1);
+            }
+            cur[l] = L.e;
         }
         if (l == 0) {
-            prof_end(pc, s, MX_PH_SMOOTH_FINE, 2 * nu1);
+            prof_end(pc, s, MX_PH_SMOOTH_FINE, is_fused(0) ? nu1 : 2 * nu1);
             prof_begin(pc, s, MX_PH_RESTRICT_FINE);
         }
-        k_resid_restrict(s, H.lev[l], H.lev[l + 1]);
+        Level<T> Lc = L;
+        Lc.e = cur[l];
+        k_resid_restrict(s, Lc, H.lev[l + 1]);
         if (l == 0) {
             prof_end(pc, s, MX_PH_RESTRICT_FINE, 1);
-            prof_begin(pc, s, MX_PH_COARSE);
-        } else {
-            ncoarse += 2 * nu1 + 1;
+            prof_begin(pc, s, MX_PH_COARSE);  // everything below the finest level
         }
     }
-    if (H.nlev == 1) prof_begin(pc, s, MX_PH_COARSE);
-    k_bottom(s, H.lev[H.nlev - 1], H.bot_scratch, bot_iters, singular);
-    ncoarse += 1;
-    for (int l = H.nlev - 2; l >= 0; l--) {
+    if (ldown == 0) prof_begin(pc, s, MX_PH_COARSE);
+    if (lc < nl) k_coarse_vcycle(s, &H.lev[lc], nl - lc, nu1, nu2, bot_iters, singular);
+    else k_bottom(s, H.lev[nl - 1], H.bot_scratch, bot_iters, singular);
+    if (ldown == 0) prof_end(pc, s, MX_PH_COARSE, 1);
+    for (int l = ldown - 1; l >= 0; l--) {
+        Level<T> &L = H.lev[l];
         if (l == 0) {
-            prof_end(pc, s, MX_PH_COARSE, ncoarse);
-            prof_begin(pc, s, MX_PH_PROLONG_FINE);
-        }
-        k_prolong(s, H.lev[l + 1], H.lev[l]);
-        if (l == 0) {
-            prof_end(pc, s, MX_PH_PROLONG_FINE, 1);
+            prof_end(pc, s, MX_PH_COARSE, 0);
             prof_begin(pc, s, MX_PH_SMOOTH_FINE);
+        }
+        if (is_fused(l)) {
+            const float *in = (const float *)cur[l];
+            float *out = (float *)(cur[l] == L.e ? L.e2 : L.e);
+            for (int q = 0; q < nu2; q++) {
+                k_rbgs_fused(s, *(Level<float> *)&L, in, out, q == 0 ? RB_PROLONG : RB_PLAIN,
+                             q == 0 ? (const Level<float> *)&H.lev[l + 1] : nullptr);
+                in = out;
+                out = (out == (float *)L.e) ? (float *)L.e2 : (float *)L.e;
+            }
         } else {
-            ncoarse += 1 + 2 * nu2;
+            k_prolong(s, H.lev[l + 1], L);
+            for (int q = 0; q < nu2; q++) {
+                k_rbgs(s, L, 0);
+                k_rbgs(s, L, 1);
+            }
         }
-        for (int q = 0; q < nu2; q++) {
-            k_rbgs(s, H.lev[l], 0);
-            k_rbgs(s, H.lev[l], 1);
-        }
-        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, 2 * nu2);
+        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, is_fused(0) ? nu2 : 1 + 2 * nu2);
     }
-    if (H.nlev == 1) prof_end(pc, s, MX_PH_COARSE, ncoarse);
 }
 template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *, int);
 template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *, int);
