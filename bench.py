@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-graph", action="store_true",
+                   help="run the refinement loop from the host (same kernels; for profilers that "
+                        "cannot see inside conditional CUDA graphs)")
     return p.parse_args()
 
 
@@ -146,7 +149,7 @@ def run_mx(args):
     phi = torch.zeros_like(rho)
     stream = torch.cuda.current_stream()
     ctx = mx.mx_create(local, stream)
-    opts = mx.default_opts(prec=mx.MX_PREC_MIXED)
+    opts = mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=0 if args.no_graph else 1)
 
     def step(u, o=opts):
         mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
@@ -193,7 +196,7 @@ def run_mx(args):
     # ---- plain FP64 solve (the comparison) ----
     fp64 = None
     if not args.no_fp64:
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=0 if args.no_graph else 1)
         u64 = [t.clone() for t in w.u]
         step(u64, o64)  # warm-up (plan, graph)
         kk = max(2, min(5, K // 4))

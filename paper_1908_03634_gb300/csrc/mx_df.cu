@@ -161,57 +161,111 @@ __device__ __forceinline__ void df_term(float bh, float bl, float qh, float ql, 
     Se += e1 + te;
 }
 
-__global__ void df_resid_kernel(Level<float> L, DFArrays D, const SolveState *st, float ih2, double *part) {
+// phi += sc * e in double-float (sc = (sh, sl))
+__device__ __forceinline__ void df_axpy(float &ph, float &pl, float sh, float sl, float ev) {
+    const float t = sh * ev;
+    const float te = fmaf(sh, ev, -t) + sl * ev;
+    float h, e1;
+    two_sum(ph, t, h, e1);
+    const float l = pl + (te + e1);
+    two_sum(h, l, ph, pl);
+}
+
+// Tile of the residual kernel: owned cells plus a 1-cell halo of phi in shared memory.
+constexpr int DX = 32, DY = 8, DZ = 8;
+constexpr int DHX = DX + 2, DHY = DY + 2, DHZ = DZ + 2;
+constexpr int DF_THREADS = 256;
+
+__device__ __forceinline__ int df_map(int u, int n, bool per) {
+    if (u >= 0 && u < n) return u;
+    if (!per || u < -1 || u > n) return -1;
+    return u < 0 ? u + n : u - n;
+}
+
+// UPDATE: phi_new = phi_old + scale * e is formed while staging (for the halo
+// too, from the same inputs, so neighbouring tiles agree bit for bit), written
+// to the other phi buffer, and the residual is taken of phi_new.  The two phi
+// buffers alternate with the V-cycle count held on the device.
+template <bool UPDATE>
+__global__ void __launch_bounds__(DF_THREADS)
+    df_resid_tile_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const SolveState *st, float ih2,
+                         double *part) {
+    __shared__ float sh_[DHZ][DHY][DHX], sl_[DHZ][DHY][DHX];
     const DGeom &g = L.g;
-    const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
-    const int k0 = blockIdx.z * ZC;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
+    const int x0 = blockIdx.x * DX, y0 = blockIdx.y * DY, z0 = blockIdx.z * DZ;
+    const int tid = threadIdx.x;
+    const int it = st->iter;
+    const int src = UPDATE ? ((it - 1) & 1) : (it & 1), dst = it & 1;
+    const float *__restrict__ sph = src ? D.ph2 : D.ph;
+    const float *__restrict__ spl = src ? D.pl2 : D.pl;
+    float *__restrict__ dph = dst ? D.ph2 : D.ph;
+    float *__restrict__ dpl = dst ? D.pl2 : D.pl;
+    float sch = 0.f, scl = 0.f;
+    if (UPDATE) {
+        sch = __double2float_rn(st->scale);
+        scl = __double2float_rn(st->scale - double(sch));
+    }
+    for (int q = tid; q < DHX * DHY * DHZ; q += DF_THREADS) {
+        const int ax = q % DHX, ay = (q / DHX) % DHY, az = q / (DHX * DHY);
+        const int lx = df_map(x0 - 1 + ax, nx, px), ly = df_map(y0 - 1 + ay, ny, py), lz = df_map(z0 - 1 + az, nz, pz);
+        float h = 0.f, l = 0.f;
+        if (lx >= 0 && ly >= 0 && lz >= 0) {
+            const long long c = lx + (long long)nx * (ly + (long long)ny * lz);
+            h = sph[c];
+            l = spl[c];
+            if (UPDATE) df_axpy(h, l, sch, scl, e[c]);
+        }
+        sh_[az][ay][ax] = h;
+        sl_[az][ay][ax] = l;
+    }
+    __syncthreads();
     const float c_hat = float(double(ih2) * st->inv_scale);
     float mx = 0.f, s2f = 0.f, s1f = 0.f;
-    if (i < g.n[0] && j < g.n[1]) {
-        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-        const int k1 = min(k0 + ZC, nz);
-        for (int k = k0; k < k1; k++) {
-            const long long c = i + (long long)nx * (j + (long long)ny * k);
-            // neighbour indices (valid array positions; out-of-box neighbours read as 0)
-            const bool hw = i > 0 || gper(g, 0), he = i + 1 < nx || gper(g, 0);
-            const bool hs = j > 0 || gper(g, 1), hn = j + 1 < ny || gper(g, 1);
-            const bool hb = k > 0 || gper(g, 2), ht = k + 1 < nz || gper(g, 2);
-            const long long cw = i > 0 ? c - 1 : c + nx - 1, ce = i + 1 < nx ? c + 1 : c - (nx - 1);
-            const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
-            const long long cn = j + 1 < ny ? c + nx : c - (long long)(ny - 1) * nx;
-            const long long cb = k > 0 ? c - g.nxy : c + (long long)(nz - 1) * g.nxy;
-            const long long ct = k + 1 < nz ? c + g.nxy : c - (long long)(nz - 1) * g.nxy;
-            // high-side face coefficients: the neighbour's low face, or the boundary plane
-            float beh, bel, bnh, bnl, bth, btl;
-            if (i + 1 < nx || gper(g, 0)) { beh = L.bx[ce]; bel = D.bxl[ce]; }
-            else { const long long q = j + (long long)ny * k; beh = L.hx[q]; bel = D.hxl[q]; }
-            if (j + 1 < ny || gper(g, 1)) { bnh = L.by[cn]; bnl = D.byl[cn]; }
-            else { const long long q = i + (long long)nx * k; bnh = L.hy[q]; bnl = D.hyl[q]; }
-            if (k + 1 < nz || gper(g, 2)) { bth = L.bz[ct]; btl = D.bzl[ct]; }
-            else { const long long q = i + (long long)nx * j; bth = L.hz[q]; btl = D.hzl[q]; }
-            const float ch = D.ph[c], cl = D.pl[c];
-            float Sh = 0.f, Se = 0.f;
-            df_term(L.bx[c], D.bxl[c], hw ? D.ph[cw] : 0.f, hw ? D.pl[cw] : 0.f, ch, cl, Sh, Se);
-            df_term(beh, bel, he ? D.ph[ce] : 0.f, he ? D.pl[ce] : 0.f, ch, cl, Sh, Se);
-            df_term(L.by[c], D.byl[c], hs ? D.ph[cs] : 0.f, hs ? D.pl[cs] : 0.f, ch, cl, Sh, Se);
-            df_term(bnh, bnl, hn ? D.ph[cn] : 0.f, hn ? D.pl[cn] : 0.f, ch, cl, Sh, Se);
-            df_term(L.bz[c], D.bzl[c], hb ? D.ph[cb] : 0.f, hb ? D.pl[cb] : 0.f, ch, cl, Sh, Se);
-            df_term(bth, btl, ht ? D.ph[ct] : 0.f, ht ? D.pl[ct] : 0.f, ch, cl, Sh, Se);
-            // R = h^2 f - S
-            float Rh, Re;
-            two_sum(D.fh[c], -Sh, Rh, Re);
-            Re += D.fl[c] - Se;
-            const float R = Rh + Re;
-            L.f[c] = R * c_hat;
-            const float r = R * ih2;
-            mx = fmaxf(mx, fabsf(r));
-            s2f = fmaf(r, r, s2f);
-            s1f += r;
+    for (int q = tid; q < DX * DY * DZ; q += DF_THREADS) {
+        const int ix = q % DX, iy = (q / DX) % DY, iz = q / (DX * DY);
+        const int i = x0 + ix, j = y0 + iy, k = z0 + iz;
+        if (i >= nx || j >= ny || k >= nz) continue;
+        const long long c = i + (long long)nx * (j + (long long)ny * k);
+        const int ax = ix + 1, ay = iy + 1, az = iz + 1;
+        const float ch = sh_[az][ay][ax], cl = sl_[az][ay][ax];
+        if (UPDATE) {
+            dph[c] = ch;
+            dpl[c] = cl;
         }
+        // high-side face coefficients: the neighbour's low face, or the boundary plane
+        float beh, bel, bnh, bnl, bth, btl;
+        if (i + 1 < nx) { beh = L.bx[c + 1]; bel = D.bxl[c + 1]; }
+        else if (px) { beh = L.bx[c - (nx - 1)]; bel = D.bxl[c - (nx - 1)]; }
+        else { const long long q2 = j + (long long)ny * k; beh = L.hx[q2]; bel = D.hxl[q2]; }
+        if (j + 1 < ny) { bnh = L.by[c + nx]; bnl = D.byl[c + nx]; }
+        else if (py) { const long long o = c - (long long)(ny - 1) * nx; bnh = L.by[o]; bnl = D.byl[o]; }
+        else { const long long q2 = i + (long long)nx * k; bnh = L.hy[q2]; bnl = D.hyl[q2]; }
+        if (k + 1 < nz) { bth = L.bz[c + g.nxy]; btl = D.bzl[c + g.nxy]; }
+        else if (pz) { const long long o = c - (long long)(nz - 1) * g.nxy; bth = L.bz[o]; btl = D.bzl[o]; }
+        else { const long long q2 = i + (long long)nx * j; bth = L.hz[q2]; btl = D.hzl[q2]; }
+        float Sh = 0.f, Se = 0.f;
+        df_term(L.bx[c], D.bxl[c], sh_[az][ay][ax - 1], sl_[az][ay][ax - 1], ch, cl, Sh, Se);
+        df_term(beh, bel, sh_[az][ay][ax + 1], sl_[az][ay][ax + 1], ch, cl, Sh, Se);
+        df_term(L.by[c], D.byl[c], sh_[az][ay - 1][ax], sl_[az][ay - 1][ax], ch, cl, Sh, Se);
+        df_term(bnh, bnl, sh_[az][ay + 1][ax], sl_[az][ay + 1][ax], ch, cl, Sh, Se);
+        df_term(L.bz[c], D.bzl[c], sh_[az - 1][ay][ax], sl_[az - 1][ay][ax], ch, cl, Sh, Se);
+        df_term(bth, btl, sh_[az + 1][ay][ax], sl_[az + 1][ay][ax], ch, cl, Sh, Se);
+        // R = h^2 f - S
+        float Rh, Re;
+        two_sum(D.fh[c], -Sh, Rh, Re);
+        Re += D.fl[c] - Se;
+        const float R = Rh + Re;
+        L.f[c] = R * c_hat;
+        const float r = R * ih2;
+        mx = fmaxf(mx, fabsf(r));
+        s2f = fmaf(r, r, s2f);
+        s1f += r;
     }
     double dm = double(mx), s2 = double(s2f), s1 = double(s1f);
     block_red3(dm, s2, s1);
-    if (flat_tid() == 0) {
+    if (tid == 0) {
         double *p = part + 3 * flat_bid();
         p[0] = dm;
         p[1] = s2;
@@ -219,7 +273,28 @@ __global__ void df_resid_kernel(Level<float> L, DFArrays D, const SolveState *st
     }
 }
 
-void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials) {
-    const float ih2 = float(1.0 / (L0.g.h * L0.g.h));
-    df_resid_kernel<<<stencil_grid(L0.g), dim3(SX, SY), 0, s>>>(L0, D, st, ih2, partials);
+int df_resid_blocks(const DGeom &g) {
+    return ((g.n[0] + DX - 1) / DX) * ((g.n[1] + DY - 1) / DY) * ((g.n[2] + DZ - 1) / DZ);
+}
+
+void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
+                double *partials) {
+    const DGeom &g = L0.g;
+    const float ih2 = float(1.0 / (g.h * g.h));
+    dim3 grid((g.n[0] + DX - 1) / DX, (g.n[1] + DY - 1) / DY, (g.n[2] + DZ - 1) / DZ);
+    if (e) df_resid_tile_kernel<true><<<grid, DF_THREADS, 0, s>>>(L0, D, e, st, ih2, partials);
+    else df_resid_tile_kernel<false><<<grid, DF_THREADS, 0, s>>>(L0, D, nullptr, st, ih2, partials);
+}
+
+// final phi (double) from the current double-float buffer (selected by the V-cycle count)
+__global__ void df_final_kernel(DFArrays D, const SolveState *st, double *__restrict__ x, long long n) {
+    const int b = st->iter & 1;
+    const float *__restrict__ hi = b ? D.ph2 : D.ph;
+    const float *__restrict__ lo = b ? D.pl2 : D.pl;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        x[q] = double(hi[q]) + double(lo[q]);
+}
+
+void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x) {
+    df_final_kernel<<<red_blocks(n), 256, 0, s>>>(D, st, x, n);
 }

@@ -9,7 +9,8 @@ struct DFArrays {
     float *bxl, *byl, *bzl;  // lo parts of the lo-face coefficients
     float *hxl, *hyl, *hzl;  // lo parts of the high-boundary planes
     float *fh, *fl;          // h^2 f
-    float *ph, *pl;          // phi
+    float *ph, *pl;          // phi, buffer 0
+    float *ph2, *pl2;        // phi, buffer 1 (the buffers alternate with the V-cycle count)
 };
 
 void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho, const double *beta0);
@@ -18,4 +19,9 @@ void k_sub_mean_split(cudaStream_t s, const DGeom &g, const double *f, const Sol
 void k_df_from_double(cudaStream_t s, long long n, const double *x, const DFArrays &D);
 void k_df_to_double(cudaStream_t s, long long n, const DFArrays &D, double *x);
 void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float *e, const SolveState *st);
-void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials);
+// r = f - L phi (e == nullptr: phi in buffer iter&1) or, with e, phi_new = phi +
+// scale e (read from buffer (iter-1)&1, written to buffer iter&1) and its residual.
+void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
+                double *partials);
+int df_resid_blocks(const DGeom &g);
+void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x);

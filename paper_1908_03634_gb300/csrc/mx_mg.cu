@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(BOT_THREADS) bottom_kernel(Level<T> L, T *scr,
     __syncthreads();
     const T bnorm2 = bot_dot(bvec, bvec, n);
     if (!(bnorm2 > T(0))) return;
-    const T tol2 = bnorm2 * T(1e-12);
+    const T tol2 = bnorm2 * T(1e-8);  // 1e-4 relative: ample for a multigrid bottom solve
     T rho = T(1), alpha = T(1), omega = T(1);
     for (int it = 0; it < iters; it++) {
         const T rho1 = bot_dot(r0, r, n);

@@ -67,6 +67,8 @@ static void carve_plan(Bump &b, MacPlan &P) {
         D.fl = b.take<float>(g.N);
         D.ph = b.take<float>(g.N);
         D.pl = b.take<float>(g.N);
+        D.ph2 = b.take<float>(g.N);
+        D.pl2 = b.take<float>(g.N);
         P.tmp32 = b.take<float>(g.N);
         P.H64.nlev = 0;
         P.L64 = Level<double>{};
@@ -262,12 +264,9 @@ static void build_hierarchy(cudaStream_t s, Hier<T> &H) {
 static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const mx_opts &o, int singular, int nb,
                     mx_ctx *pc) {
     vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused);
-    prof_begin(pc, s, MX_PH_UPDATE);
-    k_df_update(s, P.g, P.D, H.lev[0].e, c->state);
-    prof_end(pc, s, MX_PH_UPDATE, 1);
-    prof_begin(pc, s, MX_PH_RESID64);
-    k_df_resid(s, H.lev[0], P.D, c->state, c->partials);
-    k_finalize_residual(s, c->partials, nb, c->state);
+    prof_begin(pc, s, MX_PH_RESID64);  // update phi += scale e fused with the next residual
+    k_df_resid(s, H.lev[0], P.D, H.lev[0].e, c->state, c->partials);
+    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state);
     prof_end(pc, s, MX_PH_RESID64, 2);
 }
 // Plain FP64: FP64 V-cycle, FP64 update and residual.
@@ -287,8 +286,9 @@ template <typename T>
 static void ir_first_residual(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, int nb);
 template <>
 void ir_first_residual<float>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, int nb) {
-    k_df_resid(s, H.lev[0], P.D, c->state, c->partials);
-    k_finalize_residual(s, c->partials, nb, c->state);
+    (void)nb;
+    k_df_resid(s, H.lev[0], P.D, nullptr, c->state, c->partials);
+    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state);
 }
 template <>
 void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, int nb) {
@@ -476,7 +476,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     if (o.prec == MX_PREC_MIXED) st = run_ir<float>(c, *P, P->H32, phi, o, singular);
     else st = run_ir<double>(c, *P, P->H64, phi, o, singular);
     if (st) return st;
-    if (o.prec == MX_PREC_MIXED) k_df_to_double(s, g.N, P->D, phi);
+    if (o.prec == MX_PREC_MIXED) k_df_final(s, g.N, P->D, c->state, phi);
 
     prof_begin(c, s, MX_PH_FINISH);
     if (singular) {  // normalise mean(phi) = 0
