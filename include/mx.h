@@ -71,7 +71,7 @@ typedef struct {
 
 /* Solver options.  mx_default_opts() fills: rel_tol 1e-10, max_outer 100,
  * max_vcycles 100, prec MX_PREC_MIXED, remove_mean 1, use_initial_guess 0,
- * use_graph 1, nu1 = nu2 = 2 (0 = autotuned), bottom_iters 200, fused 1. */
+ * use_graph 1, nu1 = nu2 = 2 (0 = autotuned), bottom_iters 200, fused 0. */
 typedef struct {
     double rel_tol;        /* stop when ||f - L phi||_inf <= rel_tol ||f||_inf */
     int max_outer;         /* iterative-refinement iterations (one V-cycle each) */
@@ -82,8 +82,8 @@ typedef struct {
     int use_graph;         /* 1: run the refinement loop as one CUDA graph */
     int nu1, nu2;          /* pre/post smoothing sweeps (red+black each) */
     int bottom_iters;      /* BiCGStab iteration cap on the coarsest grid */
-    int fused;             /* 1: single-pass sweeps with fused prolongation (default);
-                              0: two-pass colour kernels (bit-identical results) */
+    int fused;             /* 1: single-pass tile sweeps with the prolongation fused on load;
+                              0: two-pass colour kernels (default; bit-identical results) */
 } mx_opts;
 
 typedef struct {

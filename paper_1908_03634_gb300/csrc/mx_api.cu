@@ -206,7 +206,7 @@ void mx_default_opts(mx_opts *o) {
     o->nu1 = 2;
     o->nu2 = 2;
     o->bottom_iters = 200;
-    o->fused = 1;
+    o->fused = 0;
 }
 
 int mx_device_supported(int device) {

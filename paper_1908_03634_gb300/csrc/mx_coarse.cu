@@ -72,16 +72,42 @@ __device__ void cta_prolong(const DGeom &gc, const T *ec, const DGeom &g, T *ef)
     __syncthreads();
 }
 
+// dot product accumulated in T (FP32 on the mixed path: the bottom solve only
+// needs a 1e-4 reduction, and FP64 is slow on this part)
 template <typename T>
 __device__ T cta_dot(const T *a, const T *b, int n) {
-    double s = 0.0;
-    for (int q = threadIdx.x; q < n; q += CT) s += double(a[q]) * double(b[q]);
-    double m = 0.0, z = 0.0;
-    block_red3(m, s, z);
-    __shared__ double res;
+    T s = T(0);
+    for (int q = threadIdx.x; q < n; q += CT) s += a[q] * b[q];
+    __shared__ T res;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        float m = 0.f, z = 0.f;
+        block_red3f(m, s, z);
+    } else {
+        double m = 0.0, z = 0.0;
+        block_red3(m, s, z);
+    }
     if (threadIdx.x == 0) res = s;
     __syncthreads();
-    const T out = T(res);
+    const T out = res;
+    __syncthreads();
+    return out;
+}
+
+template <typename T>
+__device__ T cta_sum(const T *a, int n) {
+    T s = T(0);
+    for (int q = threadIdx.x; q < n; q += CT) s += a[q];
+    __shared__ T res;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        float m = 0.f, z = 0.f;
+        block_red3f(m, s, z);
+    } else {
+        double m = 0.0, z = 0.0;
+        block_red3(m, s, z);
+    }
+    if (threadIdx.x == 0) res = s;
+    __syncthreads();
+    const T out = res;
     __syncthreads();
     return out;
 }
@@ -106,18 +132,7 @@ template <typename T>
 __device__ void cta_bicgstab(const Level<T> &L, T *x, const T *f, T *scr, int iters, int singular, T ih2) {
     const int n = int(L.g.N);
     T *r = scr, *r0 = scr + n, *p = scr + 2 * n, *v = scr + 3 * n, *sv = scr + 4 * n, *tv = scr + 5 * n;
-    T mean = T(0);
-    if (singular) {
-        double s = 0.0;
-        for (int q = threadIdx.x; q < n; q += CT) s += double(f[q]);
-        double m = 0.0, z = 0.0;
-        block_red3(m, s, z);
-        __shared__ double sm;
-        if (threadIdx.x == 0) sm = s / n;
-        __syncthreads();
-        mean = T(sm);
-        __syncthreads();
-    }
+    const T mean = singular ? cta_sum(f, n) / T(n) : T(0);
     for (int q = threadIdx.x; q < n; q += CT) {
         const T b = f[q] - mean;
         x[q] = T(0);
@@ -163,14 +178,7 @@ __device__ void cta_bicgstab(const Level<T> &L, T *x, const T *f, T *scr, int it
         if (rr <= tol2) break;
     }
     if (singular) {
-        double s = 0.0;
-        for (int q = threadIdx.x; q < n; q += CT) s += double(x[q]);
-        double m = 0.0, z = 0.0;
-        block_red3(m, s, z);
-        __shared__ double sm2;
-        if (threadIdx.x == 0) sm2 = s / n;
-        __syncthreads();
-        const T mx = T(sm2);
+        const T mx = cta_sum(x, n) / T(n);
         for (int q = threadIdx.x; q < n; q += CT) x[q] -= mx;
         __syncthreads();
     }
@@ -203,11 +211,11 @@ __global__ void __launch_bounds__(CT) coarse_vcycle_kernel(CoarseArgs<T> A) {
             cta_colour(L, e[l], f[l], 0, h2);
             cta_colour(L, e[l], f[l], 1, h2);
         }
-        cta_resid_restrict(L, e[l], f[l], A.lev[l + 1].g, f[l + 1], e[l + 1], T(1.0 / (L.g.h * L.g.h)));
+        cta_resid_restrict(L, e[l], f[l], A.lev[l + 1].g, f[l + 1], e[l + 1], T(1) / T(L.g.h * L.g.h));
     }
     {
         const Level<T> &L = A.lev[nb];
-        cta_bicgstab(L, e[nb], f[nb], scr, A.bot_iters, A.singular, T(1.0 / (L.g.h * L.g.h)));
+        cta_bicgstab(L, e[nb], f[nb], scr, A.bot_iters, A.singular, T(1) / T(L.g.h * L.g.h));
     }
     for (int l = nb - 1; l >= 0; l--) {
         const Level<T> &L = A.lev[l];

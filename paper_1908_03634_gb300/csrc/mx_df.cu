@@ -257,19 +257,18 @@ __global__ void __launch_bounds__(DF_THREADS)
         two_sum(D.fh[c], -Sh, Rh, Re);
         Re += D.fl[c] - Se;
         const float R = Rh + Re;
-        L.f[c] = R * c_hat;
-        const float r = R * ih2;
-        mx = fmaxf(mx, fabsf(r));
-        s2f = fmaf(r, r, s2f);
-        s1f += r;
+        const float rh = R * c_hat;  // r / scale: O(1), so its FP32 norms neither over- nor underflow
+        L.f[c] = rh;
+        mx = fmaxf(mx, fabsf(rh));
+        s2f = fmaf(rh, rh, s2f);
+        s1f += rh;
     }
-    double dm = double(mx), s2 = double(s2f), s1 = double(s1f);
-    block_red3(dm, s2, s1);
+    block_red3f(mx, s2f, s1f);
     if (tid == 0) {
         double *p = part + 3 * flat_bid();
-        p[0] = dm;
-        p[1] = s2;
-        p[2] = s1;
+        p[0] = double(mx);
+        p[1] = double(s2f);
+        p[2] = double(s1f);
     }
 }
 

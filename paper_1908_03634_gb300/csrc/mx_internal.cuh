@@ -143,7 +143,7 @@ void k_round_coeffs(cudaStream_t s, const Level<double> &src, const Level<float>
 template <typename T>
 void k_residual64(cudaStream_t s, const Level<double> &L64, const double *phi, const double *f, T *rhat,
                   const SolveState *st, double *partials, int nb);
-void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveState *st);
+void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveState *st, int scaled = 0);
 template <typename T>
 void k_update(cudaStream_t s, const DGeom &g, double *phi, const T *e, const SolveState *st);
 template <typename T>

@@ -103,10 +103,16 @@ void k_residual64(cudaStream_t s, const Level<double> &L64, const double *phi, c
 }
 
 // Convergence control of the refinement loop (single block).
-__global__ void finalize_residual_kernel(const double *part, int nb, SolveState *st) {
+__global__ void finalize_residual_kernel(const double *part, int nb, SolveState *st, int scaled) {
     double a, b, c;
     reduce_partials3(part, nb, a, b, c);
     if (flat_tid() == 0) {
+        if (scaled) {  // partials of r / scale
+            const double sc = st->scale;
+            a *= sc;
+            b *= sc * sc;
+            c *= sc;
+        }
         st->rnorm = a;
         st->rnorm2 = sqrt(b);
         st->rsum = c;
@@ -132,8 +138,8 @@ __global__ void finalize_residual_kernel(const double *part, int nb, SolveState 
     }
 }
 
-void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveState *st) {
-    finalize_residual_kernel<<<1, 1024, 0, s>>>(partials, nb, st);
+void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveState *st, int scaled) {
+    finalize_residual_kernel<<<1, 1024, 0, s>>>(partials, nb, st, scaled);
 }
 
 template <typename T>

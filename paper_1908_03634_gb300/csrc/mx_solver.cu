@@ -266,7 +266,7 @@ static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const
     vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused);
     prof_begin(pc, s, MX_PH_RESID64);  // update phi += scale e fused with the next residual
     k_df_resid(s, H.lev[0], P.D, H.lev[0].e, c->state, c->partials);
-    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state);
+    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
     prof_end(pc, s, MX_PH_RESID64, 2);
 }
 // Plain FP64: FP64 V-cycle, FP64 update and residual.
@@ -288,7 +288,7 @@ template <>
 void ir_first_residual<float>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, int nb) {
     (void)nb;
     k_df_resid(s, H.lev[0], P.D, nullptr, c->state, c->partials);
-    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state);
+    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
 }
 template <>
 void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, int nb) {

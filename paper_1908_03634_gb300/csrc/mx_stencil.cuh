@@ -80,6 +80,39 @@ __device__ __forceinline__ void block_red3(double &a, double &b, double &c) {
     __syncthreads();
 }
 
+// Block-wide (max, sum, sum) of three floats (FP32 shuffles; GB300 runs FP64
+// at 1/64 of the FP32 rate, so hot kernels keep their partials in FP32 and only
+// the one-block finalize kernels accumulate in FP64).  Result in thread 0.
+__device__ __forceinline__ void block_red3f(float &a, float &b, float &c) {
+    __shared__ float shf[96];
+    const int t = flat_tid();
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int lane = t & 31, wid = t >> 5;
+    if (lane == 0) {
+        shf[wid] = a;
+        shf[32 + wid] = b;
+        shf[64 + wid] = c;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (nthr + 31) >> 5;
+        a = lane < nw ? shf[lane] : 0.f;
+        b = lane < nw ? shf[32 + lane] : 0.f;
+        c = lane < nw ? shf[64 + lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+    }
+    __syncthreads();
+}
+
 // Reduce nb partial triples (max, sum, sum) with one block; results in thread 0.
 __device__ __forceinline__ void reduce_partials3(const double *p, int nb, double &a, double &b, double &c) {
     a = 0.0;
