@@ -1,18 +1,967 @@
-// Nodal projection (Step 11; Eq. div3; Appendix A) -- placeholder until the
-// nodal kernels land.
-#include "mx_solver.cuh"
+// Nodal projection (Step 11; Eq. div3; Appendix A) on the GPU.
+//
+// phi lives on nodes; a periodic axis of n cells has n nodes, a wall axis n+1.
+// The operator is the trilinear finite-element discretisation of
+// div(sigma grad phi) with cell-centred sigma = beta0/rho and lumped node
+// weights w (1 inside, 1/2 on a wall, ...).  On cubic cells the element
+// stiffness couples a node only to the corners that differ from it in two or
+// three indices (edge neighbours have coefficient 0), so
+//     12 w h^2 (L phi)_n = sum_m c_m (phi_m - phi_n),
+// over the 12 face-diagonal neighbours m (c_m = sum of sigma over the two cells
+// holding both nodes) and the 8 body-diagonal ones (c_m = sigma of the one
+// cell).  Gauss-Seidel with the four colours (i mod 2, j mod 2) updates nodes
+// that are never coupled to each other.  Coarse levels: sigma averaged over 8
+// cells, full-weighting restriction scaled by the node weights, trilinear
+// prolongation.  The refinement loop runs in double-float as for the MAC solve.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 
-mx_status nodal_apply(mx_ctx *c, const mx_geom *, int, const double *, const double *, const double *, const double *,
-                      double *, double *) {
-    return set_err(c, MX_ERR_ARG, "nodal operator not built yet");
+#include "mx_solver.cuh"
+#include "mx_stencil.cuh"
+
+struct NGeom {
+    int n[3];   // cells
+    int m[3];   // nodes
+    int per[3];
+    long long N, M;  // cells, nodes
+    double h;
+};
+
+template <typename T>
+struct NLevel {
+    NGeom g;
+    T *sigma;  // cells
+    T *f, *e;  // nodes
+};
+
+struct NDF {             // double-float arrays of the finest level
+    float *sh, *sl;      // sigma
+    float *fh, *fl;      // 12 h^2 w f  (the scaled nodal RHS)
+    float *ph, *pl;      // phi
+};
+
+struct NodalPlan {
+    NGeom g;
+    int prec;
+    void *mem = nullptr;
+    int nlev = 0;
+    NLevel<float> L32[MX_MAXLEV];
+    NLevel<double> L64[MX_MAXLEV];
+    NDF D;
+    double *sigma64 = nullptr, *f64 = nullptr;
+    float *bot32 = nullptr;
+    double *bot64 = nullptr;
+    long long last_use = 0;
+};
+
+static NGeom make_ngeom(const DGeom &d) {
+    NGeom g;
+    for (int a = 0; a < 3; a++) {
+        g.n[a] = d.n[a];
+        g.per[a] = d.lo[a] == MX_BC_PERIODIC;
+        g.m[a] = d.n[a] + (g.per[a] ? 0 : 1);
+    }
+    g.N = (long long)g.n[0] * g.n[1] * g.n[2];
+    g.M = (long long)g.m[0] * g.m[1] * g.m[2];
+    g.h = d.h;
+    return g;
 }
-void destroy_nodal_plans(mx_ctx *) {}
+
+static int nodal_levels(const NGeom &g0, NGeom *out) {
+    int nl = 0;
+    out[nl++] = g0;
+    for (;;) {
+        const NGeom &g = out[nl - 1];
+        bool ok = nl < MX_MAXLEV;
+        for (int a = 0; a < 3; a++) ok = ok && g.n[a] % 2 == 0 && g.n[a] >= 4;
+        if (!ok) break;
+        NGeom c = g;
+        for (int a = 0; a < 3; a++) {
+            c.n[a] = g.n[a] / 2;
+            c.m[a] = c.n[a] + (c.per[a] ? 0 : 1);
+        }
+        c.N = (long long)c.n[0] * c.n[1] * c.n[2];
+        c.M = (long long)c.m[0] * c.m[1] * c.m[2];
+        c.h = 2.0 * g.h;
+        out[nl++] = c;
+    }
+    return nl;
+}
+
+// ---- device helpers ------------------------------------------------------------------
+
+__device__ __forceinline__ int cell_wrap(const NGeom &g, int d, int i) {  // -1: outside a wall
+    if (i >= 0 && i < g.n[d]) return i;
+    if (!g.per[d]) return -1;
+    return i < 0 ? i + g.n[d] : i - g.n[d];
+}
+__device__ __forceinline__ int node_wrap(const NGeom &g, int d, int a) {
+    if (a >= 0 && a < g.m[d]) return a;
+    if (!g.per[d]) return -1;
+    return a < 0 ? a + g.m[d] : a - g.m[d];
+}
+__device__ __forceinline__ long long nidx(const NGeom &g, int a, int b, int c) {
+    return a + (long long)g.m[0] * (b + (long long)g.m[1] * c);
+}
+__device__ __forceinline__ long long cidx(const NGeom &g, int i, int j, int k) {
+    return i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
+}
+// node weight: (number of cells touching the node)/8
+__device__ __forceinline__ float node_w(const NGeom &g, int a, int b, int c) {
+    float w = 1.f;
+    if (!g.per[0] && (a == 0 || a == g.m[0] - 1)) w *= 0.5f;
+    if (!g.per[1] && (b == 0 || b == g.m[1] - 1)) w *= 0.5f;
+    if (!g.per[2] && (c == 0 || c == g.m[2] - 1)) w *= 0.5f;
+    return w;
+}
+__device__ __forceinline__ void node_of(const NGeom &g, long long q, int &a, int &b, int &c) {
+    a = int(q % g.m[0]);
+    const long long r = q / g.m[0];
+    b = int(r % g.m[1]);
+    c = int(r / g.m[1]);
+}
+
+// sigma of the 8 cells around node (a,b,c): s[iz][iy][ix], index 0 = cell a-1, 1 = cell a
+template <typename T>
+__device__ __forceinline__ void cell_ring(const NGeom &g, const T *sig, int a, int b, int c, T s[2][2][2]) {
+    for (int dz = 0; dz < 2; dz++) {
+        const int k = cell_wrap(g, 2, c - 1 + dz);
+        for (int dy = 0; dy < 2; dy++) {
+            const int j = cell_wrap(g, 1, b - 1 + dy);
+            for (int dx = 0; dx < 2; dx++) {
+                const int i = cell_wrap(g, 0, a - 1 + dx);
+                s[dz][dy][dx] = (i >= 0 && j >= 0 && k >= 0) ? sig[cidx(g, i, j, k)] : T(0);
+            }
+        }
+    }
+}
+
+// Visit the 20 coupled neighbours of node (a,b,c): fn(coef, node index or -1)
+template <typename T, typename F>
+__device__ __forceinline__ void for_couplings(const NGeom &g, int a, int b, int c, const T s[2][2][2], F fn) {
+    for (int oz = -1; oz <= 1; oz++)
+        for (int oy = -1; oy <= 1; oy++)
+            for (int ox = -1; ox <= 1; ox++) {
+                const int nz_ = (ox != 0) + (oy != 0) + (oz != 0);
+                if (nz_ < 2) continue;
+                // cells holding both nodes: along an axis with offset o != 0 the one
+                // cell on that side, along an axis with o == 0 both cells
+                T coef = T(0);
+                for (int dz = 0; dz < 2; dz++) {
+                    if (oz != 0 && dz != (oz > 0)) continue;
+                    for (int dy = 0; dy < 2; dy++) {
+                        if (oy != 0 && dy != (oy > 0)) continue;
+                        for (int dx = 0; dx < 2; dx++) {
+                            if (ox != 0 && dx != (ox > 0)) continue;
+                            coef += s[dz][dy][dx];
+                        }
+                    }
+                }
+                const int na = node_wrap(g, 0, a + ox), nb = node_wrap(g, 1, b + oy), nc = node_wrap(g, 2, c + oz);
+                fn(coef, (na >= 0 && nb >= 0 && nc >= 0) ? nidx(g, na, nb, nc) : -1LL);
+            }
+}
+
+// ---- setup: sigma = beta0/rho (FP64, then FP32 copy and double-float split) -----------
+
+__global__ void nd_sigma_kernel(long long N, const double *__restrict__ rho, const double *__restrict__ beta0,
+                                double *__restrict__ s64, float *__restrict__ s32, float *__restrict__ sl) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const double v = beta0[q] / rho[q];
+        if (s64) s64[q] = v;
+        if (s32) {
+            const float hi = __double2float_rn(v);
+            s32[q] = hi;
+            if (sl) sl[q] = __double2float_rn(v - double(hi));
+        }
+    }
+}
+
+template <typename T>
+__global__ void nd_coarsen_sigma_kernel(NLevel<T> F, NLevel<T> C) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.g.N; q += (long long)gridDim.x * blockDim.x) {
+        const int I = int(q % C.g.n[0]), J = int((q / C.g.n[0]) % C.g.n[1]), K = int(q / ((long long)C.g.n[0] * C.g.n[1]));
+        T s = T(0);
+        for (int e = 0; e < 8; e++) s += F.sigma[cidx(F.g, 2 * I + (e & 1), 2 * J + ((e >> 1) & 1), 2 * K + ((e >> 2) & 1))];
+        C.sigma[q] = s * T(0.125);
+    }
+}
+
+// ---- RHS f = D(beta0 U) - Sbar_n, with weighted sums for the mean -----------------------
+
+__global__ void nd_rhs_kernel(NGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                              const double *__restrict__ uz, const double *__restrict__ beta0,
+                              const double *__restrict__ sbar, double *__restrict__ f, double *part, int sub_mean,
+                              const SolveState *st) {
+    double mx = 0.0, s1 = 0.0, s0 = 0.0;  // max|f|, sum w f, sum w
+    const double cm = sub_mean ? st->mean : 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        double div = 0.0, sb = 0.0;
+        int cnt = 0;
+        for (int e = 0; e < 8; e++) {
+            const int dx = e & 1, dy = (e >> 1) & 1, dz = (e >> 2) & 1;  // 1: cell on the + side
+            const int i = cell_wrap(g, 0, a - 1 + dx), j = cell_wrap(g, 1, b - 1 + dy), k = cell_wrap(g, 2, c - 1 + dz);
+            if (i < 0 || j < 0 || k < 0) continue;
+            const long long cc = cidx(g, i, j, k);
+            const double bt = beta0[cc];
+            div += (dx ? 1.0 : -1.0) * bt * ux[cc] + (dy ? 1.0 : -1.0) * bt * uy[cc] + (dz ? 1.0 : -1.0) * bt * uz[cc];
+            sb += bt * sbar[cc];
+            cnt++;
+        }
+        const double w = cnt / 8.0;
+        const double v = div / (4.0 * g.h * w) - sb / cnt - cm;
+        if (f) f[q] = v;
+        mx = fmax(mx, fabs(v));
+        s1 += w * v;
+        s0 += w;
+    }
+    block_red3(mx, s1, s0);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = mx;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s0;
+    }
+}
+
+// stage 0: weighted mean; stage 1: norms of the final RHS + initial state
+__global__ void nd_finalize_rhs_kernel(const double *part, int nb, SolveState *st, int remove_mean, int stage) {
+    double a, b, c;
+    reduce_partials3(part, nb, a, b, c);
+    if (threadIdx.x == 0) {
+        if (stage == 0) {
+            st->mean = remove_mean ? b / c : 0.0;
+            st->aux = b / c;
+            st->fnorm = a;
+        } else {
+            st->fnorm = a;
+            st->fnorm2 = 0.0;
+            st->fsum = b;
+            st->scale = a > 0.0 ? a : 1.0;
+            st->inv_scale = 1.0 / st->scale;
+            st->best = INFINITY;
+            st->iter = 0;
+            st->done = 0;
+            st->status = MX_OK;
+        }
+    }
+}
+
+// subtract the weighted mean, norms, and store 12 h^2 w f as double-float (mixed) or f (FP64)
+__global__ void nd_rhs_final_kernel(NGeom g, double *__restrict__ f, const SolveState *st, float *__restrict__ fh,
+                                    float *__restrict__ fl, double *part) {
+    const double m = st->mean, h2 = g.h * g.h;
+    double mx = 0.0, s2 = 0.0, s1 = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        const double v = f[q] - m;
+        f[q] = v;
+        if (fh) {
+            const double sv = 12.0 * h2 * double(node_w(g, a, b, c)) * v;
+            const float hi = __double2float_rn(sv);
+            fh[q] = hi;
+            fl[q] = __double2float_rn(sv - double(hi));
+        }
+        mx = fmax(mx, fabs(v));
+        s2 += v * v;
+        s1 += v;
+    }
+    block_red3(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = mx;
+        part[3 * blockIdx.x + 1] = s2;
+        part[3 * blockIdx.x + 2] = s1;
+    }
+}
+
+// ---- multigrid kernels (T = float or double) -----------------------------------------
+
+// Gauss-Seidel on the nodes of one colour (a mod 2, b mod 2) = (cx, cy)
+template <typename T>
+__global__ void nd_gs_kernel(NLevel<T> L, int colour) {
+    const NGeom &g = L.g;
+    const int cx = colour & 1, cy = colour >> 1;
+    const int hx = (g.m[0] - cx + 1) / 2, hy = (g.m[1] - cy + 1) / 2;
+    const long long total = (long long)hx * hy * g.m[2];
+    const T h2 = T(g.h * g.h);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+        const int a = 2 * int(q % hx) + cx;
+        const long long r = q / hx;
+        const int b = 2 * int(r % hy) + cy;
+        const int c = int(r / hy);
+        T s[2][2][2];
+        cell_ring(g, L.sigma, a, b, c, s);
+        T num = T(0), den = T(0);
+        for_couplings(g, a, b, c, s, [&](T coef, long long m) {
+            if (m >= 0) num += coef * L.e[m];
+            den += coef;
+        });
+        const long long n = nidx(g, a, b, c);
+        if (den > T(0)) L.e[n] = (num - T(12) * T(node_w(g, a, b, c)) * h2 * L.f[n]) / den;
+    }
+}
+
+// coarse f = full-weighting restriction of the residual f - L e (node weights)
+template <typename T>
+__global__ void nd_resid_restrict_kernel(NLevel<T> F, NLevel<T> C) {
+    const NGeom &g = F.g, &gc = C.g;
+    const T h2 = T(g.h * g.h);
+    for (long long Q = blockIdx.x * (long long)blockDim.x + threadIdx.x; Q < gc.M; Q += (long long)gridDim.x * blockDim.x) {
+        int A, B, Cc;
+        node_of(gc, Q, A, B, Cc);
+        T acc = T(0);
+        for (int oz = -1; oz <= 1; oz++)
+            for (int oy = -1; oy <= 1; oy++)
+                for (int ox = -1; ox <= 1; ox++) {
+                    const int a = node_wrap(g, 0, 2 * A + ox), b = node_wrap(g, 1, 2 * B + oy), c = node_wrap(g, 2, 2 * Cc + oz);
+                    if (a < 0 || b < 0 || c < 0) continue;
+                    const T wt = T((ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f) * (oz ? 0.5f : 1.f));
+                    T s[2][2][2];
+                    cell_ring(g, F.sigma, a, b, c, s);
+                    T num = T(0), den = T(0);
+                    for_couplings(g, a, b, c, s, [&](T coef, long long m) {
+                        if (m >= 0) num += coef * F.e[m];
+                        den += coef;
+                    });
+                    const long long n = nidx(g, a, b, c);
+                    const T w = T(node_w(g, a, b, c));
+                    const T Le = (num - den * F.e[n]) / (T(12) * w * h2);
+                    acc += wt * w * (F.f[n] - Le);
+                }
+        C.f[Q] = acc / (T(8) * T(node_w(gc, A, B, Cc)));
+        C.e[Q] = T(0);
+    }
+}
+
+// e_fine += trilinear interpolation of e_coarse
+template <typename T>
+__global__ void nd_prolong_kernel(NLevel<T> C, NLevel<T> F) {
+    const NGeom &g = F.g, &gc = C.g;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        int ia[2], ib[2], ic[2];
+        T wa[2], wb[2], wc[2];
+        int na = 1, nb = 1, nc = 1;
+        auto par = [&](int x, int d, int *ix, T *w, int &cnt) {
+            if ((x & 1) == 0) {
+                ix[0] = x / 2;
+                w[0] = T(1);
+                cnt = 1;
+            } else {
+                ix[0] = (x - 1) / 2;
+                ix[1] = (x + 1) / 2;
+                if (gc.per[d] && ix[1] == gc.m[d]) ix[1] = 0;
+                w[0] = w[1] = T(0.5);
+                cnt = 2;
+            }
+        };
+        par(a, 0, ia, wa, na);
+        par(b, 1, ib, wb, nb);
+        par(c, 2, ic, wc, nc);
+        T s = T(0);
+        for (int u = 0; u < nc; u++)
+            for (int v = 0; v < nb; v++)
+                for (int t = 0; t < na; t++) s += wa[t] * wb[v] * wc[u] * C.e[nidx(gc, ia[t], ib[v], ic[u])];
+        F.e[q] += s;
+    }
+}
+
+// y = L x
+template <typename T>
+__device__ void nd_apply_one(const NLevel<T> &L, const T *x, T *y, long long q) {
+    const NGeom &g = L.g;
+    int a, b, c;
+    node_of(g, q, a, b, c);
+    T s[2][2][2];
+    cell_ring(g, L.sigma, a, b, c, s);
+    T num = T(0), den = T(0);
+    for_couplings(g, a, b, c, s, [&](T coef, long long m) {
+        if (m >= 0) num += coef * x[m];
+        den += coef;
+    });
+    y[q] = (num - den * x[q]) / (T(12) * T(node_w(g, a, b, c)) * T(g.h * g.h));
+}
+
+template <typename T>
+__global__ void nd_apply_kernel(NLevel<T> L, const T *x, T *y) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < L.g.M; q += (long long)gridDim.x * blockDim.x)
+        nd_apply_one(L, x, y, q);
+}
+
+// BiCGStab on the coarsest nodal level (one CTA).  The nodal operator is
+// symmetric in the w-weighted inner product; singular problems (no Dirichlet
+// nodes) are projected onto weighted-mean-free vectors.
+constexpr int NBT = 256;
+
+template <typename T>
+__device__ T nd_wdot(const NGeom &g, const T *a, const T *b, int weighted) {
+    float acc = 0.f, m = 0.f, z = 0.f;
+    for (int q = threadIdx.x; q < g.M; q += NBT) {
+        int x, y, zz;
+        node_of(g, q, x, y, zz);
+        const float w = weighted ? node_w(g, x, y, zz) : 1.f;
+        acc += w * float(a[q]) * float(b[q]);
+    }
+    block_red3f(m, acc, z);
+    __shared__ float res;
+    if (threadIdx.x == 0) res = acc;
+    __syncthreads();
+    const T out = T(res);
+    __syncthreads();
+    return out;
+}
+
+template <typename T>
+__device__ void nd_wmean0(const NGeom &g, T *x) {
+    float acc = 0.f, ws = 0.f, m = 0.f;
+    for (int q = threadIdx.x; q < g.M; q += NBT) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        const float w = node_w(g, a, b, c);
+        acc += w * float(x[q]);
+        ws += w;
+    }
+    block_red3f(m, acc, ws);
+    __shared__ float mean;
+    if (threadIdx.x == 0) mean = acc / ws;
+    __syncthreads();
+    for (int q = threadIdx.x; q < g.M; q += NBT) x[q] -= T(mean);
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NBT) nd_bottom_kernel(NLevel<T> L, T *scr, int iters) {
+    const NGeom &g = L.g;
+    const int n = int(g.M);
+    T *x = L.e, *r = scr, *r0 = scr + n, *p = scr + 2 * n, *v = scr + 3 * n, *sv = scr + 4 * n, *tv = scr + 5 * n;
+    for (int q = threadIdx.x; q < n; q += NBT) r[q] = L.f[q];
+    __syncthreads();
+    nd_wmean0(g, r);  // compatibility (all nodal problems here are singular)
+    for (int q = threadIdx.x; q < n; q += NBT) {
+        x[q] = T(0);
+        r0[q] = r[q];
+        p[q] = T(0);
+        v[q] = T(0);
+    }
+    __syncthreads();
+    const T bnorm2 = nd_wdot(g, r, r, 1);
+    if (!(bnorm2 > T(0))) return;
+    const T tol2 = bnorm2 * T(1e-8);
+    T rho = T(1), alpha = T(1), omega = T(1);
+    for (int it = 0; it < iters; it++) {
+        const T rho1 = nd_wdot(g, r0, r, 1);
+        if (rho1 == T(0) || omega == T(0)) break;
+        const T beta = (rho1 / rho) * (alpha / omega);
+        for (int q = threadIdx.x; q < n; q += NBT) p[q] = r[q] + beta * (p[q] - omega * v[q]);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += NBT) nd_apply_one(L, p, v, q);
+        __syncthreads();
+        const T r0v = nd_wdot(g, r0, v, 1);
+        if (r0v == T(0)) break;
+        alpha = rho1 / r0v;
+        for (int q = threadIdx.x; q < n; q += NBT) sv[q] = r[q] - alpha * v[q];
+        __syncthreads();
+        if (nd_wdot(g, sv, sv, 1) <= tol2) {
+            for (int q = threadIdx.x; q < n; q += NBT) x[q] += alpha * p[q];
+            __syncthreads();
+            break;
+        }
+        for (int q = threadIdx.x; q < n; q += NBT) nd_apply_one(L, sv, tv, q);
+        __syncthreads();
+        const T tt = nd_wdot(g, tv, tv, 1), ts = nd_wdot(g, tv, sv, 1);
+        omega = tt > T(0) ? ts / tt : T(0);
+        for (int q = threadIdx.x; q < n; q += NBT) {
+            x[q] += alpha * p[q] + omega * sv[q];
+            r[q] = sv[q] - omega * tv[q];
+        }
+        __syncthreads();
+        rho = rho1;
+        if (nd_wdot(g, r, r, 1) <= tol2) break;
+    }
+    nd_wmean0(g, x);
+}
+
+// ---- double-float residual of the refinement loop ------------------------------------
+__device__ __forceinline__ void ts2(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// UPDATE: phi += scale e first (in place; nodes are updated by their own thread
+// only, and the residual pass is a separate launch).
+__global__ void nd_df_update_kernel(NDF D, long long M, const float *__restrict__ e, const SolveState *st) {
+    const float sh = __double2float_rn(st->scale);
+    const float sl = __double2float_rn(st->scale - double(sh));
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
+        const float ev = e[q];
+        const float t = sh * ev;
+        const float te = fmaf(sh, ev, -t) + sl * ev;
+        float h, e1;
+        ts2(D.ph[q], t, h, e1);
+        const float l = D.pl[q] + (te + e1);
+        ts2(h, l, D.ph[q], D.pl[q]);
+    }
+}
+
+// 12 w h^2 r = 12 w h^2 f - sum_m c_m (phi_m - phi_n), in double-float;
+// rhat = r / scale in FP32 (the V-cycle right-hand side), norm partials of rhat.
+__global__ void nd_df_resid_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part) {
+    const NGeom &g = L0.g;
+    const float inv = float(st->inv_scale);
+    const float ih2 = float(1.0 / (g.h * g.h));
+    float mx = 0.f, s2 = 0.f, s1 = 0.f;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        float sh[2][2][2], sl[2][2][2];
+        for (int dz = 0; dz < 2; dz++) {
+            const int k = cell_wrap(g, 2, c - 1 + dz);
+            for (int dy = 0; dy < 2; dy++) {
+                const int j = cell_wrap(g, 1, b - 1 + dy);
+                for (int dx = 0; dx < 2; dx++) {
+                    const int i = cell_wrap(g, 0, a - 1 + dx);
+                    const bool ok = i >= 0 && j >= 0 && k >= 0;
+                    const long long cc = ok ? cidx(g, i, j, k) : 0;
+                    sh[dz][dy][dx] = ok ? D.sh[cc] : 0.f;
+                    sl[dz][dy][dx] = ok ? D.sl[cc] : 0.f;
+                }
+            }
+        }
+        const float ch = D.ph[q], cl = D.pl[q];
+        float Sh = 0.f, Se = 0.f;
+        for (int oz = -1; oz <= 1; oz++)
+            for (int oy = -1; oy <= 1; oy++)
+                for (int ox = -1; ox <= 1; ox++) {
+                    if ((ox != 0) + (oy != 0) + (oz != 0) < 2) continue;
+                    float kh = 0.f, kl = 0.f;  // coefficient as double-float
+                    for (int dz = 0; dz < 2; dz++) {
+                        if (oz != 0 && dz != (oz > 0)) continue;
+                        for (int dy = 0; dy < 2; dy++) {
+                            if (oy != 0 && dy != (oy > 0)) continue;
+                            for (int dx = 0; dx < 2; dx++) {
+                                if (ox != 0 && dx != (ox > 0)) continue;
+                                float s, e1;
+                                ts2(kh, sh[dz][dy][dx], s, e1);
+                                kh = s;
+                                kl += e1 + sl[dz][dy][dx];
+                            }
+                        }
+                    }
+                    const int na = node_wrap(g, 0, a + ox), nb = node_wrap(g, 1, b + oy), nc = node_wrap(g, 2, c + oz);
+                    if (na < 0 || nb < 0 || nc < 0) continue;
+                    const long long m = nidx(g, na, nb, nc);
+                    float dh, de;
+                    ts2(D.ph[m], -ch, dh, de);
+                    de += D.pl[m] - cl;
+                    const float th = kh * dh;
+                    float te = fmaf(kh, dh, -th);
+                    te = fmaf(kh, de, te);
+                    te = fmaf(kl, dh, te);
+                    float s, e1;
+                    ts2(Sh, th, s, e1);
+                    Sh = s;
+                    Se += e1 + te;
+                }
+        float Rh, Re;
+        ts2(D.fh[q], -Sh, Rh, Re);
+        Re += D.fl[q] - Se;
+        const float R = Rh + Re;  // 12 w h^2 r
+        const float r = R * (ih2 / (12.f * node_w(g, a, b, c)));
+        const float rh = r * inv;
+        L0.f[q] = rh;
+        mx = fmaxf(mx, fabsf(rh));
+        s2 = fmaf(rh, rh, s2);
+        s1 += rh;
+    }
+    block_red3f(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = double(mx);
+        part[3 * blockIdx.x + 1] = double(s2);
+        part[3 * blockIdx.x + 2] = double(s1);
+    }
+}
+
+// FP64 residual of the plain FP64 path (and of mx_residual): r = f - L phi
+__global__ void nd_resid64_kernel(NLevel<double> L, const double *__restrict__ phi, const double *__restrict__ f,
+                                  double *__restrict__ rout, double *rhat, const SolveState *st, double *part) {
+    const NGeom &g = L.g;
+    const double inv = st ? st->inv_scale : 1.0;
+    double mx = 0.0, s2 = 0.0, s1 = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        double y;
+        {
+            int a, b, c;
+            node_of(g, q, a, b, c);
+            double s[2][2][2];
+            cell_ring(g, L.sigma, a, b, c, s);
+            double num = 0.0, den = 0.0;
+            for_couplings(g, a, b, c, s, [&](double coef, long long m) {
+                if (m >= 0) num += coef * (phi[m] - phi[q]);
+                den += coef;
+            });
+            y = num / (12.0 * node_w(g, a, b, c) * g.h * g.h);
+        }
+        const double r = f[q] - y;
+        if (rout) rout[q] = r;
+        if (rhat) rhat[q] = r * inv;
+        mx = fmax(mx, fabs(r));
+        s2 += r * r;
+        s1 += r;
+    }
+    block_red3(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = mx;
+        part[3 * blockIdx.x + 1] = s2;
+        part[3 * blockIdx.x + 2] = s1;
+    }
+}
+
+__global__ void nd_update64_kernel(double *phi, const double *e, const SolveState *st, long long M) {
+    const double sc = st->scale;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x)
+        phi[q] += sc * e[q];
+}
+
+__global__ void nd_split_kernel(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo,
+                                long long M) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
+        const float h = __double2float_rn(x[q]);
+        hi[q] = h;
+        lo[q] = __double2float_rn(x[q] - double(h));
+    }
+}
+
+// r = f - L phi with L phi from the FP32 operator (mx_residual, mixed precision)
+__global__ void nd_resid32_kernel(const double *__restrict__ f, const float *__restrict__ lphi, double *__restrict__ r,
+                                  long long M, double *part) {
+    double mx = 0.0, s2 = 0.0, s1 = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
+        const double v = double(float(f[q]) - lphi[q]);
+        r[q] = v;
+        mx = fmax(mx, fabs(v));
+    }
+    block_red3(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = mx;
+        part[3 * blockIdx.x + 1] = s2;
+        part[3 * blockIdx.x + 2] = s1;
+    }
+}
+
+__global__ void nd_df_final_kernel(NDF D, long long M, double *phi) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x)
+        phi[q] = double(D.ph[q]) + double(D.pl[q]);
+}
+
+// weighted mean of phi -> st->aux, then subtraction
+__global__ void nd_wsum_kernel(NGeom g, const double *x, double *part) {
+    double s1 = 0.0, s0 = 0.0, m = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        const double w = node_w(g, a, b, c);
+        s1 += w * x[q];
+        s0 += w;
+    }
+    block_red3(m, s1, s0);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = 0.0;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s0;
+    }
+}
+__global__ void nd_wmean_finalize_kernel(const double *part, int nb, double *dst) {
+    double a, b, c;
+    reduce_partials3(part, nb, a, b, c);
+    if (threadIdx.x == 0) *dst = b / c;
+}
+
+// U -= G phi / rho at cell centres
+__global__ void nd_correct_kernel(NGeom g, const double *__restrict__ rho, const double *__restrict__ phi,
+                                  double *__restrict__ ux, double *__restrict__ uy, double *__restrict__ uz) {
+    const double i4h = 1.0 / (4.0 * g.h);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = int(q % g.n[0]), j = int((q / g.n[0]) % g.n[1]), k = int(q / ((long long)g.n[0] * g.n[1]));
+        double p[8];
+        for (int e = 0; e < 8; e++) {
+            int a = i + (e & 1), b = j + ((e >> 1) & 1), c = k + ((e >> 2) & 1);
+            if (g.per[0] && a == g.m[0]) a = 0;
+            if (g.per[1] && b == g.m[1]) b = 0;
+            if (g.per[2] && c == g.m[2]) c = 0;
+            p[e] = phi[nidx(g, a, b, c)];
+        }
+        const double gx = ((p[1] - p[0]) + (p[3] - p[2]) + (p[5] - p[4]) + (p[7] - p[6])) * i4h;
+        const double gy = ((p[2] - p[0]) + (p[3] - p[1]) + (p[6] - p[4]) + (p[7] - p[5])) * i4h;
+        const double gz = ((p[4] - p[0]) + (p[5] - p[1]) + (p[6] - p[2]) + (p[7] - p[3])) * i4h;
+        const double ir = 1.0 / rho[q];
+        ux[q] -= gx * ir;
+        uy[q] -= gy * ir;
+        uz[q] -= gz * ir;
+    }
+}
+
+// ---- host side -------------------------------------------------------------------------
+
+static bool same_ngeom(const NGeom &a, const NGeom &b) {
+    for (int d = 0; d < 3; d++)
+        if (a.n[d] != b.n[d] || a.per[d] != b.per[d]) return false;
+    return a.h == b.h;
+}
+
+static void carve_nodal(Bump &b, NodalPlan &P) {
+    NGeom gs[MX_MAXLEV];
+    P.nlev = nodal_levels(P.g, gs);
+    for (int l = 0; l < P.nlev; l++) {
+        if (P.prec == MX_PREC_MIXED) {
+            P.L32[l].g = gs[l];
+            P.L32[l].sigma = b.take<float>(gs[l].N);
+            P.L32[l].f = b.take<float>(gs[l].M);
+            P.L32[l].e = b.take<float>(gs[l].M);
+        } else {
+            P.L64[l].g = gs[l];
+            P.L64[l].sigma = b.take<double>(gs[l].N);
+            P.L64[l].f = b.take<double>(gs[l].M);
+            P.L64[l].e = b.take<double>(gs[l].M);
+        }
+    }
+    const long long Mb = gs[P.nlev - 1].M;
+    if (P.prec == MX_PREC_MIXED) {
+        P.bot32 = b.take<float>(6 * Mb);
+        P.D.sh = P.L32[0].sigma;
+        P.D.sl = b.take<float>(P.g.N);
+        P.D.fh = b.take<float>(P.g.M);
+        P.D.fl = b.take<float>(P.g.M);
+        P.D.ph = b.take<float>(P.g.M);
+        P.D.pl = b.take<float>(P.g.M);
+        P.sigma64 = nullptr;
+    } else {
+        P.bot64 = b.take<double>(6 * Mb);
+        P.sigma64 = P.L64[0].sigma;
+    }
+    P.f64 = b.take<double>(P.g.M);
+}
+
+static void free_nodal_plan(NodalPlan *p) {
+    if (p->mem) cudaFree(p->mem);
+    delete p;
+}
+
+static NodalPlan *get_nodal_plan(mx_ctx *c, const NGeom &g, int prec, mx_status *st) {
+    *st = ensure_partials(c, 152 * 8);
+    if (*st) return nullptr;
+    for (NodalPlan *p : c->nplans)
+        if (p->prec == prec && same_ngeom(p->g, g)) {
+            p->last_use = ++c->use_counter;
+            return p;
+        }
+    if (c->nplans.size() >= 2) {
+        auto it = std::min_element(c->nplans.begin(), c->nplans.end(),
+                                   [](NodalPlan *a, NodalPlan *b) { return a->last_use < b->last_use; });
+        cudaStreamSynchronize(c->stream);
+        free_nodal_plan(*it);
+        c->nplans.erase(it);
+    }
+    NodalPlan *P = new NodalPlan();
+    P->g = g;
+    P->prec = prec;
+    Bump dry{nullptr, 0};
+    carve_nodal(dry, *P);
+    if (cudaMalloc(&P->mem, dry.off + 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        *st = set_err(c, MX_ERR_OOM, "nodal plan cudaMalloc failed");
+        return nullptr;
+    }
+    Bump real{(char *)P->mem, 0};
+    carve_nodal(real, *P);
+    P->last_use = ++c->use_counter;
+    c->nplans.push_back(P);
+    return P;
+}
+
+void destroy_nodal_plans(mx_ctx *c) {
+    for (NodalPlan *p : c->nplans) free_nodal_plan(p);
+    c->nplans.clear();
+}
+
+static int nblk(long long n) { return red_blocks(n); }
+
+template <typename T>
+static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int nu2, int bot_iters) {
+    cudaMemsetAsync(L[0].e, 0, sizeof(T) * L[0].g.M, s);
+    for (int l = 0; l < nl - 1; l++) {
+        for (int q = 0; q < nu1; q++)
+            for (int col = 0; col < 4; col++) nd_gs_kernel<T><<<nblk(L[l].g.M / 4 + 1), 256, 0, s>>>(L[l], col);
+        nd_resid_restrict_kernel<T><<<nblk(L[l + 1].g.M), 256, 0, s>>>(L[l], L[l + 1]);
+    }
+    nd_bottom_kernel<T><<<1, NBT, 0, s>>>(L[nl - 1], bot, bot_iters);
+    for (int l = nl - 2; l >= 0; l--) {
+        nd_prolong_kernel<T><<<nblk(L[l].g.M), 256, 0, s>>>(L[l + 1], L[l]);
+        for (int q = 0; q < nu2; q++)
+            for (int col = 3; col >= 0; col--) nd_gs_kernel<T><<<nblk(L[l].g.M / 4 + 1), 256, 0, s>>>(L[l], col);
+    }
+}
+
+static mx_status nodal_setup(mx_ctx *c, NodalPlan &P, const double *rho, const double *beta0) {
+    cudaStream_t s = c->stream;
+    const NGeom &g = P.g;
+    if (P.prec == MX_PREC_MIXED) {
+        nd_sigma_kernel<<<nblk(g.N), 256, 0, s>>>(g.N, rho, beta0, nullptr, P.L32[0].sigma, P.D.sl);
+        for (int l = 0; l + 1 < P.nlev; l++)
+            nd_coarsen_sigma_kernel<float><<<nblk(P.L32[l + 1].g.N), 256, 0, s>>>(P.L32[l], P.L32[l + 1]);
+    } else {
+        nd_sigma_kernel<<<nblk(g.N), 256, 0, s>>>(g.N, rho, beta0, P.L64[0].sigma, nullptr, nullptr);
+        for (int l = 0; l + 1 < P.nlev; l++)
+            nd_coarsen_sigma_kernel<double><<<nblk(P.L64[l + 1].g.N), 256, 0, s>>>(P.L64[l], P.L64[l + 1]);
+    }
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux, double *uy, double *uz,
+                                      const double *rho, const double *beta0, const double *sbar, double *phi,
+                                      const mx_opts *opts, mx_info *info) {
+    if (!c) return MX_ERR_ARG;
+    mx_status st = check_geom(c, geom, true);
+    if (st) return st;
+    if (!ux || !uy || !uz || !rho || !beta0 || !sbar || !phi) return set_err(c, MX_ERR_ARG, "nodal_project: null array");
+    mx_opts o;
+    if (opts) o = *opts;
+    else mx_default_opts(&o);
+    if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 ||
+        o.bottom_iters < 1 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED))
+        return set_err(c, MX_ERR_ARG, "invalid options");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
+    const NGeom g = make_ngeom(make_dgeom(geom));
+    NodalPlan *P = get_nodal_plan(c, g, o.prec, &st);
+    if (!P) return st;
+    cudaStream_t s = c->stream;
+    const int nb = nblk(g.M);
+    MX_CUDA(c, cudaEventRecord(c->ev0, s));
+    SolveState init = {};
+    init.tol = o.rel_tol;
+    init.maxit = std::min(o.max_outer, o.max_vcycles);
+    *c->hstate = init;
+    MX_CUDA(c, cudaMemcpyAsync(c->state, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    if ((st = nodal_setup(c, *P, rho, beta0))) return st;
+    nd_rhs_kernel<<<nb, 256, 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0, c->state);
+    nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nb, c->state, o.remove_mean, 0);
+    if (!o.remove_mean) {
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (std::fabs(c->hstate->aux) > 1e-12 * c->hstate->fnorm) {
+            if (info) {
+                std::memset(info, 0, sizeof(*info));
+                info->status = MX_ERR_INCOMPAT;
+            }
+            return set_err(c, MX_ERR_INCOMPAT, "nodal: right-hand side has non-zero weighted mean and remove_mean = 0");
+        }
+    }
+    const bool mixed = o.prec == MX_PREC_MIXED;
+    nd_rhs_final_kernel<<<nb, 256, 0, s>>>(g, P->f64, c->state, mixed ? P->D.fh : nullptr, mixed ? P->D.fl : nullptr,
+                                           c->partials);
+    nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nb, c->state, 0, 1);
+    if (mixed) {
+        if (o.use_initial_guess) {
+            nd_split_kernel<<<nb, 256, 0, s>>>(phi, P->D.ph, P->D.pl, g.M);
+        } else {
+            MX_CUDA(c, cudaMemsetAsync(P->D.ph, 0, sizeof(float) * g.M, s));
+            MX_CUDA(c, cudaMemsetAsync(P->D.pl, 0, sizeof(float) * g.M, s));
+        }
+    } else if (!o.use_initial_guess) {
+        MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.M, s));
+    }
+    // refinement loop (host-driven)
+    for (;;) {
+        if (mixed) nd_df_resid_kernel<<<nb, 256, 0, s>>>(P->L32[0], P->D, c->state, c->partials);
+        else nd_resid64_kernel<<<nb, 256, 0, s>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f, c->state, c->partials);
+        k_finalize_residual(s, c->partials, nb, c->state, mixed ? 1 : 0);
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (c->hstate->done) break;
+        if (mixed) {
+            nd_vcycle<float>(s, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters);
+            nd_df_update_kernel<<<nb, 256, 0, s>>>(P->D, g.M, P->L32[0].e, c->state);
+        } else {
+            nd_vcycle<double>(s, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters);
+            nd_update64_kernel<<<nb, 256, 0, s>>>(phi, P->L64[0].e, c->state, g.M);
+        }
+    }
+    if (mixed) nd_df_final_kernel<<<nb, 256, 0, s>>>(P->D, g.M, phi);
+    // normalise the weighted mean of phi to 0, correct U, check the divergence
+    nd_wsum_kernel<<<nb, 256, 0, s>>>(g, phi, c->partials);
+    nd_wmean_finalize_kernel<<<1, 1024, 0, s>>>(c->partials, nb, &c->state->aux);
+    k_sub_scalar(s, g.M, phi, &c->state->aux);
+    nd_correct_kernel<<<nblk(g.N), 256, 0, s>>>(g, rho, phi, ux, uy, uz);
+    // divergence of the projected velocity minus Sbar_n minus c: nd_rhs with the mean subtracted
+    nd_rhs_kernel<<<nb, 256, 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials, 1, c->state);
+    k_finalize_max(s, c->partials, nb, &c->state->div_err);
+    MX_CUDA(c, cudaEventRecord(c->ev1, s));
+    MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MX_CUDA(c, cudaStreamSynchronize(s));
+    MX_CUDA(c, cudaGetLastError());
+    const SolveState &hs = *c->hstate;
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        info->outer_iters = hs.iter;
+        info->vcycles = hs.iter;
+        info->rel_resid = hs.fnorm > 0 ? hs.rnorm / hs.fnorm : hs.rnorm;
+        info->rel_resid_l2 = 0.0;
+        info->div_err_linf = hs.div_err;
+        info->rhs_mean_removed = hs.mean;
+        info->rhs_linf = hs.fnorm;
+        info->ms = ms;
+        info->status = hs.status;
+    }
+    if (hs.status != MX_OK) return set_err(c, (mx_status)hs.status, "nodal: no convergence");
+    return MX_OK;
+}
+
+// mx_apply_op / mx_residual for the nodal operator
+mx_status nodal_apply(mx_ctx *c, const mx_geom *geom, int prec, const double *rho, const double *beta0,
+                      const double *phi, const double *f, double *out, double *rnorm) {
+    const NGeom g = make_ngeom(make_dgeom(geom));
+    mx_status st;
+    NodalPlan *P = get_nodal_plan(c, g, prec, &st);
+    if (!P) return st;
+    cudaStream_t s = c->stream;
+    if ((st = nodal_setup(c, *P, rho, beta0))) return st;
+    const int nb = nblk(g.M);
+    if (prec == MX_PREC_FP64) {
+        if (f) {
+            nd_resid64_kernel<<<nb, 256, 0, s>>>(P->L64[0], phi, f, out, nullptr, nullptr, c->partials);
+            if (rnorm) k_finalize_max(s, c->partials, nb, &c->state->rnorm);
+        } else {
+            nd_apply_kernel<double><<<nb, 256, 0, s>>>(P->L64[0], phi, out);
+        }
+    } else {
+        NLevel<float> &l0 = P->L32[0];
+        k_cast<float>(s, g.M, phi, l0.e);
+        nd_apply_kernel<float><<<nb, 256, 0, s>>>(l0, l0.e, l0.f);
+        if (f) {
+            nd_resid32_kernel<<<nb, 256, 0, s>>>(f, l0.f, out, g.M, c->partials);
+            if (rnorm) k_finalize_max(s, c->partials, nb, &c->state->rnorm);
+        } else {
+            k_uncast<float>(s, g.M, l0.f, out);
+        }
+    }
+    if (rnorm) {
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        *rnorm = c->hstate->rnorm;
+    }
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
 void destroy_batch_plan(mx_ctx *) {}
 
-extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *, double *, double *, double *, const double *,
-                                      const double *, const double *, double *, const mx_opts *, mx_info *) {
-    return set_err(c, MX_ERR_ARG, "nodal projection not built yet");
-}
 extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int, const mx_geom *, double *const *, double *const *,
                                             double *const *, const double *const *, const double *const *,
                                             const double *const *, double *const *, const mx_opts *, mx_info *) {
