@@ -4,6 +4,8 @@
 // On these levels a grid-wide launch does a few microseconds of work, so one
 // launch replaces the dozens of per-level launches (smoothing, restriction,
 // BiCGStab bottom solve, prolongation) that would otherwise dominate.
+#include <cstring>
+
 #include "mx_coarse.cuh"
 #include "mx_rbgs.cuh"
 #include "mx_stencil.cuh"
@@ -185,7 +187,7 @@ __device__ void cta_bicgstab(const Level<T> &L, T *x, const T *f, T *scr, int it
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CT) coarse_vcycle_kernel(CoarseArgs<T> A) {
+__device__ void coarse_body(const CoarseArgs<T> &A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *e[COARSE_MAX_LEVELS], *f[COARSE_MAX_LEVELS];
@@ -230,6 +232,17 @@ __global__ void __launch_bounds__(CT) coarse_vcycle_kernel(CoarseArgs<T> A) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(CT) coarse_vcycle_kernel(CoarseArgs<T> A) {
+    coarse_body(A);
+}
+
+// batched: one CTA per box (boxes already converged return at once)
+__global__ void __launch_bounds__(CT) coarse_vcycle_batch_kernel(const CoarseArgs<float> *args, const SolveState *st) {
+    if (st[blockIdx.x].done) return;
+    coarse_body(args[blockIdx.x]);
+}
+
+template <typename T>
 size_t coarse_smem_bytes(const Level<T> *levs, int nl) {
     size_t n = 0;
     for (int l = 0; l < nl; l++) n += 2 * (size_t)levs[l].g.N;
@@ -262,8 +275,31 @@ cudaError_t coarse_init() {
     cudaError_t e = cudaFuncSetAttribute(coarse_vcycle_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          COARSE_MAX_SMEM);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coarse_vcycle_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, COARSE_MAX_SMEM);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(coarse_vcycle_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 COARSE_MAX_SMEM);
+}
+
+size_t coarse_args_bytes() { return sizeof(CoarseArgs<float>); }
+
+void coarse_fill_args(void *dst, const Level<float> *levs, int nl, int nu1, int nu2, int bot_iters, int singular) {
+    CoarseArgs<float> A;
+    std::memset(&A, 0, sizeof(A));
+    A.nl = nl;
+    for (int l = 0; l < nl; l++) A.lev[l] = levs[l];
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.bot_iters = bot_iters;
+    A.singular = singular;
+    std::memcpy(dst, &A, sizeof(A));
+}
+
+size_t coarse_smem_bytes_f(const Level<float> *levs, int nl) { return coarse_smem_bytes(levs, nl); }
+
+void k_coarse_vcycle_batch(cudaStream_t s, const void *dev_args, const SolveState *st, int nbox, size_t smem) {
+    if (nbox > 0)
+        coarse_vcycle_batch_kernel<<<nbox, CT, smem, s>>>((const CoarseArgs<float> *)dev_args, st);
 }
 
 template bool coarse_fits<float>(const Level<float> *, int);

@@ -16,3 +16,9 @@ template <typename T>
 void k_coarse_vcycle(cudaStream_t s, const Level<T> *levs, int nl, int nu1, int nu2, int bot_iters, int singular);
 
 cudaError_t coarse_init();
+
+// batched coarse ends: argument blocks for one box each (host fills, device reads)
+size_t coarse_args_bytes();
+void coarse_fill_args(void *dst, const Level<float> *levs, int nl, int nu1, int nu2, int bot_iters, int singular);
+size_t coarse_smem_bytes_f(const Level<float> *levs, int nl);
+void k_coarse_vcycle_batch(cudaStream_t s, const void *dev_args, const SolveState *st, int nbox, size_t smem);

@@ -187,14 +187,13 @@ __device__ __forceinline__ int df_map(int u, int n, bool per) {
 // to the other phi buffer, and the residual is taken of phi_new.  The two phi
 // buffers alternate with the V-cycle count held on the device.
 template <bool UPDATE>
-__global__ void __launch_bounds__(DF_THREADS)
-    df_resid_tile_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const SolveState *st, float ih2,
-                         double *part) {
+__device__ __forceinline__ void df_resid_body(const Level<float> &L, const DFArrays &D, const float *__restrict__ e,
+                                              const SolveState *st, float ih2, double *p, int bx, int by, int bz) {
     __shared__ float sh_[DHZ][DHY][DHX], sl_[DHZ][DHY][DHX];
     const DGeom &g = L.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
-    const int x0 = blockIdx.x * DX, y0 = blockIdx.y * DY, z0 = blockIdx.z * DZ;
+    const int x0 = bx * DX, y0 = by * DY, z0 = bz * DZ;
     const int tid = threadIdx.x;
     const int it = st->iter;
     const int src = UPDATE ? ((it - 1) & 1) : (it & 1), dst = it & 1;
@@ -265,11 +264,43 @@ __global__ void __launch_bounds__(DF_THREADS)
     }
     block_red3f(mx, s2f, s1f);
     if (tid == 0) {
-        double *p = part + 3 * flat_bid();
         p[0] = double(mx);
         p[1] = double(s2f);
         p[2] = double(s1f);
     }
+}
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(DF_THREADS)
+    df_resid_tile_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const SolveState *st, float ih2,
+                         double *part) {
+    df_resid_body<UPDATE>(L, D, e, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// batched: work[blockIdx.x] = (box, bx, by, bz); the box's partials start at boxes[box].part_off
+template <bool UPDATE>
+__global__ void __launch_bounds__(DF_THREADS)
+    df_resid_batch_kernel(const DFBox *boxes, const int4 *work, const SolveState *st, double *part) {
+    const int4 w = work[blockIdx.x];
+    if (st[w.x].done) return;
+    const DFBox &B = boxes[w.x];
+    const Level<float> L = B.L0;
+    const DFArrays D = B.D;
+    const DGeom &g = L.g;
+    const int nbx = (g.n[0] + DX - 1) / DX, nby = (g.n[1] + DY - 1) / DY;
+    double *p = part + 3 * ((long long)B.part_off + w.y + nbx * (w.z + nby * w.w));
+    df_resid_body<UPDATE>(L, D, UPDATE ? L.e : nullptr, &st[w.x], float(1.0 / (g.h * g.h)), p, w.y, w.z, w.w);
+}
+
+void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
+                      double *partials, int update) {
+    if (nwork <= 0) return;
+    if (update) df_resid_batch_kernel<true><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
+    else df_resid_batch_kernel<false><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
+}
+
+dim3 df_resid_grid(const DGeom &g) {
+    return dim3((g.n[0] + DX - 1) / DX, (g.n[1] + DY - 1) / DY, (g.n[2] + DZ - 1) / DZ);
 }
 
 int df_resid_blocks(const DGeom &g) {

@@ -24,4 +24,14 @@ void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float 
 void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
                 double *partials);
 int df_resid_blocks(const DGeom &g);
+dim3 df_resid_grid(const DGeom &g);
+
+// one box of the batched refinement loop
+struct DFBox {
+    Level<float> L0;  // finest FP32 level (L0.e: the V-cycle correction, L0.f: rhat)
+    DFArrays D;
+    int part_off;     // first reduction partial of the box
+};
+void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
+                      double *partials, int update);
 void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x);

@@ -147,7 +147,17 @@ void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveSt
 template <typename T>
 void k_update(cudaStream_t s, const DGeom &g, double *phi, const T *e, const SolveState *st);
 template <typename T>
-void k_rbgs(cudaStream_t s, const Level<T> &L, int colour);
+void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero = 0);
+dim3 rbgs_grid(const DGeom &g);
+// batched multigrid phases over a work list of (box, bx, by, bz)
+void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
+                  int level, int colour, int zero);
+void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork,
+                            const SolveState *st, int level);
+void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
+                     int level);
+void k_finalize_residual_batch(cudaStream_t s, const double *partials, const int *off, const int *cnt, SolveState *st,
+                               int nbox);
 template <typename T>
 void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse);
 template <typename T>

@@ -102,7 +102,33 @@ void k_residual64(cudaStream_t s, const Level<double> &L64, const double *phi, c
     residual64_kernel<T><<<stencil_grid(L64.g), dim3(SX, SY), 0, s>>>(L64, phi, f, rhat, st, partials, ih2);
 }
 
-// Convergence control of the refinement loop (single block).
+// Convergence control of the refinement loop: one thread decides from the
+// reduced norms (a = max, b = sum of squares, c = sum).
+__device__ void decide(SolveState *st, double a, double b, double c) {
+    st->rnorm = a;
+    st->rnorm2 = sqrt(b);
+    st->rsum = c;
+    const int k = st->iter;
+    const bool conv = a <= st->tol * st->fnorm;
+    if (!isfinite(b) || !isfinite(a)) {
+        st->status = MX_ERR_NOCONV;
+        st->done = 1;
+    } else if (conv) {
+        st->status = MX_OK;
+        st->done = 1;
+    } else if (k >= st->maxit) {
+        st->status = MX_ERR_NOCONV;
+        st->done = 1;
+    } else if (k > 3 && a > 1e3 * st->best) {
+        st->status = MX_ERR_NOCONV;  // residual growth: divergence
+        st->done = 1;
+    } else {
+        st->done = 0;
+        st->iter = k + 1;
+    }
+    if (a < st->best) st->best = a;
+}
+
 __global__ void finalize_residual_kernel(const double *part, int nb, SolveState *st, int scaled) {
     double a, b, c;
     reduce_partials3(part, nb, a, b, c);
@@ -113,33 +139,30 @@ __global__ void finalize_residual_kernel(const double *part, int nb, SolveState 
             b *= sc * sc;
             c *= sc;
         }
-        st->rnorm = a;
-        st->rnorm2 = sqrt(b);
-        st->rsum = c;
-        const int k = st->iter;
-        const bool conv = a <= st->tol * st->fnorm;
-        if (!isfinite(b) || !isfinite(a)) {
-            st->status = MX_ERR_NOCONV;
-            st->done = 1;
-        } else if (conv) {
-            st->status = MX_OK;
-            st->done = 1;
-        } else if (k >= st->maxit) {
-            st->status = MX_ERR_NOCONV;
-            st->done = 1;
-        } else if (k > 3 && a > 1e3 * st->best) {
-            st->status = MX_ERR_NOCONV;  // residual growth: divergence
-            st->done = 1;
-        } else {
-            st->done = 0;
-            st->iter = k + 1;
-        }
-        if (a < st->best) st->best = a;
+        decide(st, a, b, c);
     }
 }
 
 void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveState *st, int scaled) {
     finalize_residual_kernel<<<1, 1024, 0, s>>>(partials, nb, st, scaled);
+}
+
+// one block per box: partials [off[b], off[b] + cnt[b]) of r / scale; boxes
+// already done skipped this residual and stay as they are
+__global__ void finalize_residual_batch_kernel(const double *part, const int *off, const int *cnt, SolveState *st) {
+    const int b = blockIdx.x;
+    if (st[b].done) return;
+    double a, s2, s1;
+    reduce_partials3(part + 3 * (long long)off[b], cnt[b], a, s2, s1);
+    if (threadIdx.x == 0) {
+        const double sc = st[b].scale;
+        decide(&st[b], a * sc, s2 * sc * sc, s1 * sc);
+    }
+}
+
+void k_finalize_residual_batch(cudaStream_t s, const double *partials, const int *off, const int *cnt, SolveState *st,
+                               int nbox) {
+    finalize_residual_batch_kernel<<<nbox, 256, 0, s>>>(partials, off, cnt, st);
 }
 
 template <typename T>
@@ -158,12 +181,15 @@ void k_update(cudaStream_t s, const DGeom &g, double *phi, const T *e, const Sol
 // V-cycle kernels
 
 // One colour of red-black Gauss-Seidel: cells with (i+j+k) % 2 == colour solve
-// their row exactly with the other colour's current values.
+// their row exactly with the other colour's current values.  zero = 1 (red
+// pass of the first sweep from a zero initial guess): the black neighbours are
+// taken as 0 without reading e.
 template <typename T>
-__global__ void rbgs_kernel(Level<T> L, int colour, T h2) {
+__device__ __forceinline__ void rbgs_body(const Level<T> &L, int colour, T h2, int zero, int bx, int by, int bz,
+                                          int tx, int ty) {
     const DGeom &g = L.g;
-    const int t = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
-    const int k0 = blockIdx.z * ZC;
+    const int t = bx * SX + tx, j = by * SY + ty;
+    const int k0 = bz * ZC;
     if (j >= g.n[1]) return;
     const int k1 = min(k0 + ZC, g.n[2]);
     for (int k = k0; k < k1; k++) {
@@ -172,24 +198,51 @@ __global__ void rbgs_kernel(Level<T> L, int colour, T h2) {
         const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
         T b[6], v[6];
         face_coefs(L, i, j, k, c, b);
-        nb_vals(g, L.e, i, j, k, c, v);
+        if (zero) {
+            for (int q = 0; q < 6; q++) v[q] = T(0);
+        } else {
+            nb_vals(g, L.e, i, j, k, c, v);
+        }
         L.e[c] = gs_update(b, v, L.f[c], h2);
     }
 }
 
 template <typename T>
-void k_rbgs(cudaStream_t s, const Level<T> &L, int colour) {
-    const DGeom &g = L.g;
-    dim3 grid(((g.n[0] + 1) / 2 + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + ZC - 1) / ZC);
-    rbgs_kernel<T><<<grid, dim3(SX, SY), 0, s>>>(L, colour, T(g.h * g.h));
+__global__ void rbgs_kernel(Level<T> L, int colour, T h2, int zero) {
+    rbgs_body(L, colour, h2, zero, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
 }
 
-// Coarse RHS = average of the 8 fine residuals f - L e; coarse e = 0.
+dim3 rbgs_grid(const DGeom &g) {
+    return dim3(((g.n[0] + 1) / 2 + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + ZC - 1) / ZC);
+}
+
+// batched: work[blockIdx.x] = (box, bx, by, bz); level descriptors levs[box * MX_MAXLEV + level]
+__global__ void rbgs_batch_kernel(const Level<float> *levs, const int4 *work, const SolveState *st, int level,
+                                  int colour, int zero) {
+    const int4 w = work[blockIdx.x];
+    if (st[w.x].done) return;
+    const Level<float> L = levs[w.x * MX_MAXLEV + level];
+    rbgs_body(L, colour, float(L.g.h * L.g.h), zero, w.y, w.z, w.w, threadIdx.x, threadIdx.y);
+}
+
+void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
+                  int level, int colour, int zero) {
+    if (nwork > 0) rbgs_batch_kernel<<<nwork, dim3(SX, SY), 0, s>>>(levs, work, st, level, colour, zero);
+}
+
 template <typename T>
-__global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2) {
+void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero) {
+    const DGeom &g = L.g;
+    rbgs_kernel<T><<<rbgs_grid(g), dim3(SX, SY), 0, s>>>(L, colour, T(g.h * g.h), zero);
+}
+
+// Coarse RHS = average of the 8 fine residuals f - L e.
+template <typename T>
+__device__ __forceinline__ void resid_restrict_body(const Level<T> &F, const Level<T> &Cl, T ih2, int bx, int by,
+                                                    int bz, int tx, int ty) {
     const DGeom &gc = Cl.g;
-    const int I = blockIdx.x * SX + threadIdx.x, J = blockIdx.y * SY + threadIdx.y;
-    const int K0 = blockIdx.z * ZC;
+    const int I = bx * SX + tx, J = by * SY + ty;
+    const int K0 = bz * ZC;
     if (I >= gc.n[0] || J >= gc.n[1]) return;
     const DGeom &g = F.g;
     const int K1 = min(K0 + ZC, gc.n[2]);
@@ -207,8 +260,26 @@ __global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2) {
                 }
         const long long C = I + (long long)gc.n[0] * (J + (long long)gc.n[1] * K);
         Cl.f[C] = s * T(0.125);
-        Cl.e[C] = T(0);
     }
+}
+
+template <typename T>
+__global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2) {
+    resid_restrict_body(F, Cl, ih2, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
+}
+
+__global__ void resid_restrict_batch_kernel(const Level<float> *levs, const int4 *work, const SolveState *st,
+                                            int level) {
+    const int4 w = work[blockIdx.x];
+    if (st[w.x].done) return;
+    const Level<float> F = levs[w.x * MX_MAXLEV + level];
+    const Level<float> C = levs[w.x * MX_MAXLEV + level + 1];
+    resid_restrict_body(F, C, float(1.0 / (F.g.h * F.g.h)), w.y, w.z, w.w, threadIdx.x, threadIdx.y);
+}
+
+void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork,
+                            const SolveState *st, int level) {
+    if (nwork > 0) resid_restrict_batch_kernel<<<nwork, dim3(SX, SY), 0, s>>>(levs, work, st, level);
 }
 
 template <typename T>
@@ -219,10 +290,11 @@ void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coar
 
 // e_fine += e_coarse(parent)
 template <typename T>
-__global__ void prolong_kernel(Level<T> Cl, Level<T> F) {
+__device__ __forceinline__ void prolong_body(const Level<T> &Cl, const Level<T> &F, int bx, int by, int bz, int tx,
+                                             int ty) {
     const DGeom &g = F.g;
-    const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
-    const int k0 = blockIdx.z * ZC;
+    const int i = bx * SX + tx, j = by * SY + ty;
+    const int k0 = bz * ZC;
     if (i >= g.n[0] || j >= g.n[1]) return;
     const int k1 = min(k0 + ZC, g.n[2]);
     for (int k = k0; k < k1; k++) {
@@ -230,6 +302,24 @@ __global__ void prolong_kernel(Level<T> Cl, Level<T> F) {
         const long long C = (i >> 1) + (long long)Cl.g.n[0] * ((j >> 1) + (long long)Cl.g.n[1] * (k >> 1));
         F.e[c] += Cl.e[C];
     }
+}
+
+template <typename T>
+__global__ void prolong_kernel(Level<T> Cl, Level<T> F) {
+    prolong_body(Cl, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
+}
+
+__global__ void prolong_batch_kernel(const Level<float> *levs, const int4 *work, const SolveState *st, int level) {
+    const int4 w = work[blockIdx.x];
+    if (st[w.x].done) return;
+    const Level<float> C = levs[w.x * MX_MAXLEV + level + 1];
+    const Level<float> F = levs[w.x * MX_MAXLEV + level];
+    prolong_body(C, F, w.y, w.z, w.w, threadIdx.x, threadIdx.y);
+}
+
+void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
+                     int level) {
+    if (nwork > 0) prolong_batch_kernel<<<nwork, dim3(SX, SY), 0, s>>>(levs, work, st, level);
 }
 
 template <typename T>
@@ -475,7 +565,7 @@ void k_residual_plain(cudaStream_t s, const Level<double> &L, const double *phi,
     template void k_residual64<T>(cudaStream_t, const Level<double> &, const double *, const double *, T *,      \
                                   const SolveState *, double *, int);                                            \
     template void k_update<T>(cudaStream_t, const DGeom &, double *, const T *, const SolveState *);            \
-    template void k_rbgs<T>(cudaStream_t, const Level<T> &, int);                                                \
+    template void k_rbgs<T>(cudaStream_t, const Level<T> &, int, int);                                           \
     template void k_resid_restrict<T>(cudaStream_t, const Level<T> &, const Level<T> &);                       \
     template void k_prolong<T>(cudaStream_t, const Level<T> &, const Level<T> &);                              \
     template void k_bottom<T>(cudaStream_t, const Level<T> &, T *, int, int);                                   \

@@ -960,10 +960,3 @@ mx_status nodal_apply(mx_ctx *c, const mx_geom *geom, int prec, const double *rh
     return MX_OK;
 }
 
-void destroy_batch_plan(mx_ctx *) {}
-
-extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int, const mx_geom *, double *const *, double *const *,
-                                            double *const *, const double *const *, const double *const *,
-                                            const double *const *, double *const *, const mx_opts *, mx_info *) {
-    return set_err(c, MX_ERR_ARG, "batched projection not built yet");
-}

@@ -90,10 +90,30 @@ static bool same_geom(const DGeom &a, const DGeom &b) {
     return a.h == b.h;
 }
 
-static void free_plan(MacPlan *p) {
+void free_mac_plan(MacPlan *p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->mem) cudaFree(p->mem);
     delete p;
+}
+
+// A plan owned by the caller (not in the context's cache).
+MacPlan *create_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st) {
+    *st = MX_OK;
+    MacPlan *P = new MacPlan();
+    P->g = g;
+    P->prec = prec;
+    Bump dry{nullptr, 0};
+    carve_plan(dry, *P);
+    P->bytes = dry.off + 256;
+    if (cudaMalloc(&P->mem, P->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        *st = set_err(c, MX_ERR_OOM, "plan workspace cudaMalloc failed");
+        return nullptr;
+    }
+    Bump real{(char *)P->mem, 0};
+    carve_plan(real, *P);
+    return P;
 }
 
 mx_status ensure_partials(mx_ctx *c, long long nblocks) {
@@ -128,30 +148,18 @@ MacPlan *get_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st) {
         auto it = std::min_element(c->plans.begin(), c->plans.end(),
                                    [](MacPlan *a, MacPlan *b) { return a->last_use < b->last_use; });
         cudaStreamSynchronize(c->stream);
-        free_plan(*it);
+        free_mac_plan(*it);
         c->plans.erase(it);
     }
-    MacPlan *P = new MacPlan();
-    P->g = g;
-    P->prec = prec;
-    Bump dry{nullptr, 0};
-    carve_plan(dry, *P);
-    P->bytes = dry.off + 256;
-    if (cudaMalloc(&P->mem, P->bytes) != cudaSuccess) {
-        cudaGetLastError();
-        delete P;
-        *st = set_err(c, MX_ERR_OOM, "plan workspace cudaMalloc failed");
-        return nullptr;
-    }
-    Bump real{(char *)P->mem, 0};
-    carve_plan(real, *P);
+    MacPlan *P = create_mac_plan(c, g, prec, st);
+    if (!P) return nullptr;
     P->last_use = ++c->use_counter;
     c->plans.push_back(P);
     return P;
 }
 
 void destroy_plans(mx_ctx *c) {
-    for (MacPlan *p : c->plans) free_plan(p);
+    for (MacPlan *p : c->plans) free_mac_plan(p);
     c->plans.clear();
     destroy_nodal_plans(c);
     destroy_batch_plan(c);
@@ -171,7 +179,7 @@ void destroy_plans(mx_ctx *c) {
 constexpr long long FUSED_MIN_CELLS = 1LL << 20;
 
 template <typename T>
-static int coarse_start(const Hier<T> &H) {
+int coarse_start(const Hier<T> &H) {
     for (int l = 0; l < H.nlev; l++)
         if (H.lev[l].g.N <= COARSE_MAX_CELLS && coarse_fits(&H.lev[l], H.nlev - l)) return l;
     return H.nlev;
@@ -185,11 +193,6 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
     const bool can_fuse = sizeof(T) == sizeof(float) && fused && nu1 >= 1 && nu2 >= 1;
     auto is_fused = [&](int l) { return can_fuse && H.lev[l].g.N >= FUSED_MIN_CELLS; };
     T *cur[MX_MAXLEV];
-    if (ldown > 0 && !is_fused(0)) {
-        prof_begin(pc, s, MX_PH_UPDATE);
-        cudaMemsetAsync(H.lev[0].e, 0, sizeof(T) * H.lev[0].g.N, s);
-        prof_end(pc, s, MX_PH_UPDATE, 1);
-    }
     for (int l = 0; l < ldown; l++) {
         Level<T> &L = H.lev[l];
         if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
@@ -204,8 +207,10 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
             }
             cur[l] = (T *)in;
         } else {
+            // the first red pass starts from e = 0 without reading e
+            if (nu1 == 0) cudaMemsetAsync(L.e, 0, sizeof(T) * L.g.N, s);
             for (int q = 0; q < nu1; q++) {
-                k_rbgs(s, L, 0);
+                k_rbgs(s, L, 0, q == 0);
                 k_rbgs(s, L, 1);
             }
             cur[l] = L.e;
@@ -251,6 +256,7 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
         if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, is_fused(0) ? nu2 : 1 + 2 * nu2);
     }
 }
+template int coarse_start<float>(const Hier<float> &);
 template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *, int);
 template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *, int);
 
@@ -391,7 +397,7 @@ static mx_status run_ir(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx
 
 // ------------------------------------------------------------------------------
 
-static mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
+mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
     if (in) o = *in;
     else mx_default_opts(&o);
     if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.max_vcycles < 0 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
@@ -404,7 +410,7 @@ static mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
     return MX_OK;
 }
 
-static void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0) {
+void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0) {
     cudaStream_t s = c->stream;
     if (P.prec == MX_PREC_MIXED) {
         k_mac_coeffs_df(s, P.H32.lev[0], P.D, rho, beta0);
