@@ -164,6 +164,26 @@ mx_status mx_mac_project_batched(mx_ctx *ctx, int nbox, const mx_geom *geoms, do
                                  const double *const *beta0, const double *const *sbar,
                                  double *const *phi, const mx_opts *opts, mx_info *infos);
 
+/* FP64 MAC residual r = f - L phi and its max norm, allocating nothing.  This
+ * entry point has no counterpart in the paper; it serves callers that may not
+ * allocate device memory at all -- code that runs inside a caller-managed pool
+ * or arena, or under a policy that forbids cudaMalloc on a hot path -- and so
+ * cannot create an mx_ctx (whose workspace is allocated).  It computes the face
+ * coefficients on the fly from rho and beta0 and keeps its per-tile partial
+ * maxima in a fixed device array built into the library (about 512 KB, held by
+ * every GPU that loads the library until the process exits).
+ * Arguments as for mx_residual (device arrays, MAC operator, FP64); work runs on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream) of the current
+ * device; rnorm_linf (host, may be NULL) is written after the stream syncs.
+ * Limit: at most 65536 tiles of 32 x 8 x 8 cells, i.e. ceil(n0/32) *
+ * ceil(n1/8) * ceil(n2/8) <= 65536 (512^3 fits); larger grids return MX_ERR_ARG
+ * before any work.  The first call on a device looks up the array's device
+ * address; make that first call before capturing a stream into a graph.  All
+ * calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
+mx_status mx_residual_noalloc(const mx_geom *geom, const double *rho, const double *beta0, const double *phi,
+                              const double *f, double *r, double *rnorm_linf, void *cuda_stream);
+
 /* Tracing: per-phase device time of mx_mac_project.  While enabled, the
  * refinement loop runs from the host (no graph) and every phase is bracketed by
  * CUDA events on the context's stream.  mx_profile_read copies, per phase, the

@@ -75,6 +75,7 @@ def load():
         "mx_nodal_project": (C.c_int, [_VP, G, _DP, _DP, _DP, _DP, _DP, _DP, _DP, O, I]),
         "mx_apply_op": (C.c_int, [_VP, G, C.c_int, C.c_int, _DP, _DP, _DP, _DP]),
         "mx_residual": (C.c_int, [_VP, G, C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP, C.POINTER(C.c_double)]),
+        "mx_residual_noalloc": (C.c_int, [G, _DP, _DP, _DP, _DP, _DP, C.POINTER(C.c_double), _VP]),
         "mx_profile_enable": (C.c_int, [_VP, C.c_int]),
         "mx_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "mx_mac_project_batched": (C.c_int, [_VP, C.c_int, G, C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP),
@@ -92,7 +93,7 @@ def exported_symbols():
     """Names declared in include/mx.h and exported by the library."""
     return ["mx_create", "mx_destroy", "mx_set_stream", "mx_last_error", "mx_default_opts", "mx_device_supported",
             "mx_fill_base_state", "mx_mac_project", "mx_nodal_project", "mx_apply_op", "mx_residual",
-            "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read"]
+            "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -265,3 +266,16 @@ def mx_profile_read(ctx):
     ln = (C.c_longlong * n)()
     _check(ctx, load().mx_profile_read(ctx, ms, ln))
     return {PHASES[i]: (ms[i], ln[i]) for i in range(n)}
+
+
+def mx_residual_noalloc(geom, rho, beta0, phi, f, r, stream=None):
+    """FP64 MAC residual r = f - L phi without any device allocation (see
+    include/mx.h); returns ||r||_inf.  Raises MXError on a non-zero status."""
+    g = make_geom(geom)
+    cs = cell_shape(geom)
+    rn = C.c_double(0.0)
+    st = load().mx_residual_noalloc(C.byref(g), _ptr(rho, cs, "rho"), _ptr(beta0, cs, "beta0"), _ptr(phi, cs, "phi"),
+                                    _ptr(f, cs, "f"), _ptr(r, cs, "r"), C.byref(rn), _stream_handle(stream))
+    if st != MX_OK:
+        raise MXError(st, "mx_residual_noalloc failed")
+    return rn.value
