@@ -42,6 +42,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the nodal and batched workloads")
+    p.add_argument("--workload", default="planar256",
+                   choices=["planar256", "star512", "nodal-sweep"],
+                   help="planar256: the headline line (+ nodal384 and batched96 extras); star512: the "
+                        "full-star line; nodal-sweep: one line per nodal size 64^3..512^3")
     p.add_argument("--no-graph", action="store_true",
                    help="run the refinement loop from the host (same kernels; for profilers that "
                         "cannot see inside conditional CUDA graphs)")
@@ -292,6 +297,12 @@ def run_mx(args):
             ems = float(t.item())
         e2e = {"value": world * ke / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- the other workloads (nodal projection, batched patches) ----
+    extras = {}
+    if not args.no_extras:
+        extras["nodal384"] = bench_nodal(mx, W, ctx, dev, stream, hbm=hbm)
+        extras["batched96"] = bench_batched(mx, W, ctx, dev, stream)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -308,13 +319,99 @@ def run_mx(args):
                    "parallelism": f"replicas x{world}"},
         "vcycles_per_solve": vcycles, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
         "fp64": fp64, "phases": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clk,
+        "gpu_launches": launches, "clocks": clk, **extras,
     }
     mx.mx_destroy(ctx)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def timed(fn, steps, stream):
+    import torch
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = [fn(i) for i in range(steps)]
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hbm=6793.4):
+    """Nodal projection (Step 11) on the planar256 stratification at n^3 cells:
+    mixed precision vs plain FP64, solves/s, time per V-cycle and the HBM
+    fraction of one V-cycle against the model's algorithmic bytes."""
+    import torch
+    w = W.nodal384(device=dev, n=n)
+    g = w.geom
+    beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=dev)
+    mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0, g.dx, (0.5, 0.5, 0.5), beta0)
+    phi = torch.zeros(mx.node_shape(g), dtype=torch.float64, device=dev)
+    us = [[t.clone() for t in w.u] for _ in range(steps + warmup)]
+    opts = mx.default_opts()
+    run = lambda u, o: mx.mx_nodal_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
+    for i in range(warmup):
+        run(us[i], opts)
+    ms, infos = timed(lambda i: run(us[warmup + i], opts), steps, stream)
+    vc = infos[-1]["vcycles"]
+    nodes = phi.numel()
+    # model bytes per V-cycle (FP32, nu = 2+2): sweeps 4w/node, residual+restriction
+    # 3.125w, prolongation 2.125w on every level (N_total = 8/7 N), + the double-float
+    # residual and update of the refinement loop (phi 8 read + 8 write, f 8, sigma 8, rhat 4)
+    model = nodes * (8.0 / 7.0) * 4 * (4 * 4 + 3.125 + 2.125) + nodes * 36
+    ms_solve = ms / steps
+    out = {"workload": f"nodal{n}", "nodes": nodes, "solves_per_s": 1e3 / ms_solve, "ms_per_solve": ms_solve,
+           "vcycles": vc, "rel_resid": infos[-1]["rel_resid"], "div_err_linf": infos[-1]["div_err_linf"],
+           "ms_per_vcycle_upper": ms_solve / max(vc, 1),
+           "hbm_frac_per_vcycle": round(model / (ms_solve / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
+           "model_bytes_per_vcycle": model}
+    if fp64:
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        u64 = [t.clone() for t in w.u]
+        run(u64, o64)
+        for d in range(3):
+            u64[d].copy_(w.u[d])
+        ms64, i64 = timed(lambda i: run(u64, o64), 1, stream)
+        out["fp64"] = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "vcycles": i64[-1]["vcycles"]}
+    return out
+
+
+def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=True):
+    """96 independent planar patches (sizes {32,48,64,96,128}^3) solved as one
+    batch (one launch per phase over all patches), vs looping single FP64 solves."""
+    import torch
+    ps = W.batched_patches(npatch, device=dev)
+    geoms = [p.geom for p in ps]
+    cells = sum(g.ncell for g in geoms)
+    b0 = []
+    for p in ps:
+        t = torch.empty(mx.cell_shape(p.geom), dtype=torch.float64, device=dev)
+        mx.mx_fill_base_state(ctx, p.geom, 0, p.prof_beta0, p.geom.dx, (0.5, 0.5, 0.5), t)
+        b0.append(t)
+    phis = [torch.zeros(mx.cell_shape(g), dtype=torch.float64, device=dev) for g in geoms]
+    sets = [[[t.clone() for t in p.u] for p in ps] for _ in range(steps + warmup)]
+
+    def run(us, o):
+        return mx.mx_mac_project_batched(ctx, geoms, [u[0] for u in us], [u[1] for u in us], [u[2] for u in us],
+                                         [p.rho for p in ps], b0, [p.sbar for p in ps], phis, o)[1]
+    opts = mx.default_opts()
+    for i in range(warmup):
+        run(sets[i], opts)
+    ms, infos = timed(lambda i: run(sets[warmup + i], opts), steps, stream)
+    last = infos[-1]
+    ms_b = ms / steps
+    out = {"workload": f"batched{npatch}", "patches": npatch, "cells": cells, "ms_per_batch": ms_b,
+           "patch_solves_per_s": npatch * 1e3 / ms_b, "cells_per_s": cells * 1e3 / ms_b,
+           "vcycles_max": max(i["vcycles"] for i in last), "vcycles_mean": statistics.mean(i["vcycles"] for i in last),
+           "rel_resid_max": max(i["rel_resid"] for i in last)}
+    if fp64:
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        us = [[t.clone() for t in p.u] for p in ps]
+        ms64, _ = timed(lambda i: run(us, o64), 1, stream)
+        out["fp64_loop"] = {"ms_per_batch": ms64, "patch_solves_per_s": npatch * 1e3 / ms64}
+    return out
 
 
 def cpu_baseline_sample(n_sample, n_full, reps=1):
@@ -366,9 +463,62 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_other(args):
+    """--workload star512 | nodal-sweep (single GPU)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1908_03634_gb300 import build as B
+    B.build()
+    import paper_1908_03634_gb300 as mx
+    from paper_1908_03634_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    ctx = mx.mx_create(0, stream)
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if args.workload == "nodal-sweep":
+        for n in (64, 128, 192, 256, 384, 512):
+            r = bench_nodal(mx, W, ctx, dev, stream, n=n, steps=2, warmup=1, fp64=(n <= 256), hbm=hbm)
+            print(json.dumps(r), flush=True)
+            torch.cuda.empty_cache()
+    else:
+        w = W.star512(device=dev)
+        g = w.geom
+        beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=dev)
+        phi = torch.zeros_like(beta0)
+        K, Wm = args.steps, args.warmup
+        us = [[t.clone() for t in w.u] for _ in range(min(K + Wm, 6))]
+
+        def step(i, o):
+            u = us[i % len(us)]
+            for d in range(3):
+                u[d].copy_(w.u[d])
+            mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
+            return mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
+        o = mx.default_opts()
+        for i in range(Wm):
+            step(i, o)
+        ms, infos = timed(lambda i: step(i, o), K, stream)
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        step(0, o64)
+        ms64, i64 = timed(lambda i: step(i, o64), 1, stream)
+        print(json.dumps({"workload": "star512", "metric": "MAC projection solves/s to 1e-10 (full star 512^3, "
+                          "Dirichlet)", "value": K * 1e3 / ms, "unit": UNIT, "ms_per_solve": ms / K,
+                          "vcycles": infos[-1]["vcycles"], "rel_resid": infos[-1]["rel_resid"],
+                          "div_err_linf": infos[-1]["div_err_linf"],
+                          "fp64": {"solves_per_s": 1e3 / ms64, "vcycles": i64[-1]["vcycles"]},
+                          "note": "includes a 3-array restore of U per solve"}), flush=True)
+    mx.mx_destroy(ctx)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != "planar256":
+        run_other(a)
     else:
         run_mx(a)

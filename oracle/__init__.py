@@ -64,6 +64,9 @@ def _load():
             "or_mac_solve": (C.c_int, [G, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P]),
             "or_mac_dense_solve": (C.c_int, [G, _P, _P, _P, _P, _P]),
             "or_mac_project": (C.c_int, [G, _P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int, _P]),
+            "or_mac_residual_sample": (None, [G, _P, _P, _P, _P, C.POINTER(C.c_long), C.c_long, _P]),
+            "or_mac_divergence_sample": (None, [G, _P, _P, _P, _P, C.POINTER(C.c_long), C.c_long, _P]),
+            "or_nd_residual_sample": (None, [G, _P, _P, _P, C.POINTER(C.c_long), C.c_long, _P]),
             "or_nd_nnode": (C.c_long, [G]),
             "or_nd_weights": (None, [G, _P]),
             "or_nd_apply": (None, [G, _P, _P, _P]),
@@ -212,6 +215,38 @@ def mac_project(geom, u, rho, beta0, sbar, tol=1e-13, maxit=200, remove_mean=Tru
                             _p(_arr(sbar)), _p(phi), float(tol), int(maxit), int(bool(remove_mean)), _p(out))
     info = dict(mean=out[0], rel_resid=out[1], div_err=out[2], iters=int(out[3]), ok=(rc == 0))
     return u, phi, info
+
+
+def _idx(idx):
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    return idx, idx.ctypes.data_as(C.POINTER(C.c_long))
+
+
+def mac_residual_sample(geom, rho, beta0, phi, f, idx):
+    """f - L phi at the flat cell indices idx, one cell at a time from rho, beta0."""
+    lib = _load()
+    idx, ip = _idx(idx)
+    out = np.empty(idx.size)
+    lib.or_mac_residual_sample(_g(geom), _p(_arr(rho)), _p(_arr(beta0)), _p(_arr(phi)), _p(_arr(f)), ip, idx.size,
+                               _p(out))
+    return out
+
+
+def mac_divergence_sample(geom, u, beta0, idx):
+    lib = _load()
+    u = [_arr(x) for x in u]
+    idx, ip = _idx(idx)
+    out = np.empty(idx.size)
+    lib.or_mac_divergence_sample(_g(geom), _p(u[0]), _p(u[1]), _p(u[2]), _p(_arr(beta0)), ip, idx.size, _p(out))
+    return out
+
+
+def nd_residual_sample(geom, sigma, phi, f, idx):
+    lib = _load()
+    idx, ip = _idx(idx)
+    out = np.empty(idx.size)
+    lib.or_nd_residual_sample(_g(geom), _p(_arr(sigma)), _p(_arr(phi)), _p(_arr(f)), ip, idx.size, _p(out))
+    return out
 
 
 # --- nodal -------------------------------------------------------------------------

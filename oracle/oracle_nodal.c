@@ -532,3 +532,34 @@ int or_nd_project(const or_geom *g, double *ux, double *uy, double *uz, const do
     free(sigma); free(f); free(d);
     return it < 0 ? -1 : 0;
 }
+
+/* Sampled nodal residual f - L phi at nodes idx[q] (same definition as
+ * or_nd_apply, evaluated node by node). */
+void or_nd_residual_sample(const or_geom *g, const double *sigma, const double *phi, const double *f,
+                           const long *idx, long n, double *r) {
+    int mx = nnodes_axis(g, 0), my = nnodes_axis(g, 1);
+    for (long q = 0; q < n; q++) {
+        long nd = idx[q];
+        int a = (int)(nd % mx), b = (int)((nd / mx) % my), c = (int)(nd / ((long)mx * my));
+        double acc = 0.0, cnt = 0.0;
+        for (int dz = -1; dz <= 0; dz++)
+            for (int dy = -1; dy <= 0; dy++)
+                for (int dx = -1; dx <= 0; dx++) {
+                    int cell[3] = {a + dx, b + dy, c + dz}, ok = 1;
+                    for (int d = 0; d < 3; d++) {
+                        if (g->lo[d] == OR_PERIODIC) {
+                            if (cell[d] < 0) cell[d] += g->n[d];
+                        } else if (cell[d] < 0 || cell[d] >= g->n[d]) ok = 0;
+                    }
+                    if (!ok) continue;
+                    cnt += 1.0;
+                    double s = sigma[ccidx(g, cell[0], cell[1], cell[2])];
+                    int e_n = (-dx) | ((-dy) << 1) | ((-dz) << 2);
+                    double inner = 0.0;
+                    for (int e = 0; e < 8; e++)
+                        inner += elem_a(e_n, e) * phi[corner_node(g, cell[0], cell[1], cell[2], e)];
+                    acc += s * inner;
+                }
+        r[q] = f[nd] - acc / ((cnt / 8.0) * g->h * g->h);
+    }
+}

@@ -1,0 +1,103 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (default options: mixed precision, CUDA-graph loop), on outputs the
+oracle computes one at a time: the residual f - L phi of the GPU's phi at
+sampled cells/nodes (f from the oracle's own full-array RHS), the divergence
+identity D(beta0 U) - beta0 Sbar - c = f - L phi of the GPU's projected U at
+the same cells, and the normalisation of phi.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1908_03634_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def mx():
+    from paper_1908_03634_gb300 import build as b
+    b.build()
+    O.build()
+    import paper_1908_03634_gb300 as m
+    return m
+
+
+def sample_cells(g, n, seed):
+    rng = np.random.default_rng(seed)
+    N = g.n[0] * g.n[1] * g.n[2]
+    idx = rng.integers(0, N, size=n)
+    # always include cells on the first and last planes (boundary closures)
+    nxy = g.n[0] * g.n[1]
+    edge = np.concatenate([rng.integers(0, nxy, size=n // 10), N - nxy + rng.integers(0, nxy, size=n // 10)])
+    return np.unique(np.concatenate([idx, edge]))
+
+
+def run_mac(mx, w):
+    g = w.geom
+    ctx = mx.mx_create(0)
+    try:
+        beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+        mx.mx_fill_base_state(ctx, g, int(w.spherical), w.prof_beta0.to(DEV), w.prof_dr, w.center, beta0)
+        u = [t.clone() for t in w.u]
+        phi = torch.zeros(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+        st, info = mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, mx.default_opts())
+        torch.cuda.synchronize()
+    finally:
+        mx.mx_destroy(ctx)
+    return info, phi.cpu().numpy(), [x.cpu().numpy() for x in u]
+
+
+@pytest.mark.parametrize("name", ["planar256", "star512"])
+def test_mac_fullsize_sampled(mx, name):
+    w = W.planar256(device=DEV) if name == "planar256" else W.star512(device=DEV)
+    g = w.geom
+    info, phi, u = run_mac(mx, w)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-10
+    rho, sbar, u0 = w.rho.cpu().numpy(), w.sbar.cpu().numpy(), [t.cpu().numpy() for t in w.u]
+    prof, spherical, dr = w.prof_beta0.cpu().numpy(), w.spherical, w.prof_dr
+    del w
+    b0 = O.fill(g, prof, spherical=spherical, dr=dr, center=(0.5, 0.5, 0.5))
+    f, c = O.mac_rhs(g, u0, b0, sbar)
+    fn = np.abs(f).max()
+    idx = sample_cells(g, 20000, 5)
+    r = O.mac_residual_sample(g, rho, b0, phi, f, idx)
+    assert np.abs(r).max() <= 1.05e-10 * fn
+    d = O.mac_divergence_sample(g, u, b0, idx) - (b0 * sbar).ravel()[idx] - c
+    assert np.abs(d - r).max() <= 1e-11 * fn
+    assert abs(info["rhs_mean_removed"] - c) <= 1e-12 * max(1.0, abs(c))
+    if O.singular(g):
+        assert abs(phi.mean()) <= 1e-12 * np.abs(phi).max()
+
+
+def test_nodal384_fullsize_sampled(mx):
+    w = W.nodal384(device=DEV)
+    g = w.geom
+    ctx = mx.mx_create(0)
+    try:
+        beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+        mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0.to(DEV), w.prof_dr, w.center, beta0)
+        u = [t.clone() for t in w.u]
+        phi = torch.zeros(mx.node_shape(g), dtype=torch.float64, device=DEV)
+        st, info = mx.mx_nodal_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, mx.default_opts())
+        torch.cuda.synchronize()
+    finally:
+        mx.mx_destroy(ctx)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-10
+    b0 = beta0.cpu().numpy()
+    rho, sbar = w.rho.cpu().numpy(), w.sbar.cpu().numpy()
+    u0 = [t.cpu().numpy() for t in w.u]
+    prof = w.prof_beta0.cpu().numpy()
+    del w
+    assert np.array_equal(b0, O.fill(g, prof))
+    f, c = O.nd_rhs(g, u0, b0, sbar)
+    fn = np.abs(f).max()
+    phi = phi.cpu().numpy()
+    M = phi.size
+    idx = np.unique(np.random.default_rng(6).integers(0, M, size=20000))
+    r = O.nd_residual_sample(g, b0 / rho, phi, f, idx)
+    assert np.abs(r).max() <= 1.05e-10 * fn
+    wts = O.nd_weights(g)
+    assert abs((wts * phi).sum()) <= 1e-12 * np.abs(phi).max() * wts.sum()

@@ -252,3 +252,21 @@ def test_remove_mean_flag_and_dirichlet_keeps_mean(oracle_lib):
     b0 = O.fill(ws.geom, ws.prof_beta0, spherical=True, dr=ws.prof_dr)
     _, cs = O.mac_rhs(ws.geom, ws.u, b0, ws.sbar, remove_mean=True)
     assert cs == 0.0
+
+
+@pytest.mark.parametrize("bc", [(P, P, N), (D, D, D), (N, P, D)])
+def test_sampled_residual_and_divergence_equal_full_arrays(oracle_lib, bc):
+    """The one-cell-at-a-time functions used for full-size checks agree with
+    the full-array definitions (coefficients from rho, beta0 directly)."""
+    rng = np.random.default_rng(21)
+    g = geom((10, 6, 8), bc)
+    cs = O.cell_shape(g)
+    rho, beta0, phi, f = np.exp(rng.standard_normal(cs)), np.exp(rng.standard_normal(cs)), \
+        rng.standard_normal(cs), rng.standard_normal(cs)
+    u = [rng.standard_normal(O.face_shape(g, d)) for d in range(3)]
+    b = O.mac_coeffs(g, rho, beta0)
+    r_full = (f - O.mac_apply(g, b, phi)).ravel()
+    d_full = O.mac_divergence(g, u, beta0).ravel()
+    idx = np.arange(r_full.size)
+    assert np.array_equal(O.mac_residual_sample(g, rho, beta0, phi, f, idx), r_full)
+    assert np.array_equal(O.mac_divergence_sample(g, u, beta0, idx), d_full)

@@ -165,3 +165,14 @@ def test_approximate_projection_error_is_second_order(oracle_lib):
         fn = np.abs(O.nd_rhs(w.geom, w.u, beta0, sbar)[0]).max()
         errs.append(info["div_err"] / fn)
     assert errs[0] / errs[1] >= 3.0 and errs[1] / errs[2] >= 3.0, errs
+
+
+@pytest.mark.parametrize("bc", [(P, P, N), (N, N, N), (P, P, P)])
+def test_sampled_nodal_residual_equals_full(oracle_lib, bc):
+    rng = np.random.default_rng(22)
+    g = geom((6, 4, 8), bc)
+    sigma = np.exp(rng.standard_normal(O.cell_shape(g)))
+    phi, f = rng.standard_normal(O.node_shape(g)), rng.standard_normal(O.node_shape(g))
+    full = (f - O.nd_apply(g, sigma, phi)).ravel()
+    got = O.nd_residual_sample(g, sigma, phi, f, np.arange(full.size))
+    assert np.abs(got - full).max() <= 1e-12 * np.abs(full).max()
