@@ -357,6 +357,12 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     ms, infos = timed(lambda i: run(us[warmup + i], opts), steps, stream)
     vc = infos[-1]["vcycles"]
     nodes = phi.numel()
+    # traced pass: per-phase device time (CUDA events on the stream)
+    mx.mx_profile_enable(ctx, True)
+    ut = [t.clone() for t in w.u]
+    run(ut, opts)
+    trace = {k: {"ms": v[0], "launches": v[1]} for k, v in mx.mx_profile_read(ctx).items()}
+    mx.mx_profile_enable(ctx, False)
     # model bytes per V-cycle (FP32, nu = 2+2): sweeps 4w/node, residual+restriction
     # 3.125w, prolongation 2.125w on every level (N_total = 8/7 N), + the double-float
     # residual and update of the refinement loop (phi 8 read + 8 write, f 8, sigma 8, rhat 4)
@@ -366,7 +372,7 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
            "vcycles": vc, "rel_resid": infos[-1]["rel_resid"], "div_err_linf": infos[-1]["div_err_linf"],
            "ms_per_vcycle_upper": ms_solve / max(vc, 1),
            "hbm_frac_per_vcycle": round(model / (ms_solve / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
-           "model_bytes_per_vcycle": model}
+           "model_bytes_per_vcycle": model, "phases": trace}
     if fp64:
         o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
         u64 = [t.clone() for t in w.u]

@@ -31,8 +31,8 @@ struct NGeom {
 template <typename T>
 struct NLevel {
     NGeom g;
-    T *sigma;  // cells
-    T *f, *e;  // nodes
+    T *sigma;     // cells
+    T *f, *e, *r; // nodes (r: residual scratch of the restriction)
 };
 
 struct NDF {             // double-float arrays of the finest level
@@ -279,36 +279,11 @@ __global__ void nd_rhs_final_kernel(NGeom g, double *__restrict__ f, const Solve
 
 // ---- multigrid kernels (T = float or double) -----------------------------------------
 
-// Gauss-Seidel on the nodes of one colour (a mod 2, b mod 2) = (cx, cy)
+// coarse f = full-weighting restriction of the fine residual (node weights):
+// f_C = (1/(8 w_C)) sum_n P(n, C) w_n r_n; coarse e = 0
 template <typename T>
-__global__ void nd_gs_kernel(NLevel<T> L, int colour) {
-    const NGeom &g = L.g;
-    const int cx = colour & 1, cy = colour >> 1;
-    const int hx = (g.m[0] - cx + 1) / 2, hy = (g.m[1] - cy + 1) / 2;
-    const long long total = (long long)hx * hy * g.m[2];
-    const T h2 = T(g.h * g.h);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
-        const int a = 2 * int(q % hx) + cx;
-        const long long r = q / hx;
-        const int b = 2 * int(r % hy) + cy;
-        const int c = int(r / hy);
-        T s[2][2][2];
-        cell_ring(g, L.sigma, a, b, c, s);
-        T num = T(0), den = T(0);
-        for_couplings(g, a, b, c, s, [&](T coef, long long m) {
-            if (m >= 0) num += coef * L.e[m];
-            den += coef;
-        });
-        const long long n = nidx(g, a, b, c);
-        if (den > T(0)) L.e[n] = (num - T(12) * T(node_w(g, a, b, c)) * h2 * L.f[n]) / den;
-    }
-}
-
-// coarse f = full-weighting restriction of the residual f - L e (node weights)
-template <typename T>
-__global__ void nd_resid_restrict_kernel(NLevel<T> F, NLevel<T> C) {
+__global__ void nd_restrict_kernel(NLevel<T> F, NLevel<T> C) {
     const NGeom &g = F.g, &gc = C.g;
-    const T h2 = T(g.h * g.h);
     for (long long Q = blockIdx.x * (long long)blockDim.x + threadIdx.x; Q < gc.M; Q += (long long)gridDim.x * blockDim.x) {
         int A, B, Cc;
         node_of(gc, Q, A, B, Cc);
@@ -319,17 +294,7 @@ __global__ void nd_resid_restrict_kernel(NLevel<T> F, NLevel<T> C) {
                     const int a = node_wrap(g, 0, 2 * A + ox), b = node_wrap(g, 1, 2 * B + oy), c = node_wrap(g, 2, 2 * Cc + oz);
                     if (a < 0 || b < 0 || c < 0) continue;
                     const T wt = T((ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f) * (oz ? 0.5f : 1.f));
-                    T s[2][2][2];
-                    cell_ring(g, F.sigma, a, b, c, s);
-                    T num = T(0), den = T(0);
-                    for_couplings(g, a, b, c, s, [&](T coef, long long m) {
-                        if (m >= 0) num += coef * F.e[m];
-                        den += coef;
-                    });
-                    const long long n = nidx(g, a, b, c);
-                    const T w = T(node_w(g, a, b, c));
-                    const T Le = (num - den * F.e[n]) / (T(12) * w * h2);
-                    acc += wt * w * (F.f[n] - Le);
+                    acc += wt * T(node_w(g, a, b, c)) * F.r[nidx(g, a, b, c)];
                 }
         C.f[Q] = acc / (T(8) * T(node_w(gc, A, B, Cc)));
         C.e[Q] = T(0);
@@ -485,6 +450,131 @@ __global__ void __launch_bounds__(NBT) nd_bottom_kernel(NLevel<T> L, T *scr, int
     nd_wmean0(g, x);
 }
 
+// ---- column-marching kernels ------------------------------------------------------------
+// A thread owns one (a, b) node column and walks up a z-chunk, keeping the
+// 3x3 neighbourhood of nodes of planes c-1, c, c+1 and the 2x2 cells below and
+// above plane c in registers, so each node costs 9 node and 4 cell loads.
+// One colour (a mod 2, b mod 2) is a set of whole columns, and nodes of one
+// column are never coupled (edge neighbours), so a column can be updated in
+// place while it is walked.
+
+struct ColMap {
+    int na[3], nb[3];  // node x / y indices of a-1, a, a+1 (-1: beyond a wall)
+    int ca[2], cb[2];  // cell x / y indices a-1, a (-1: beyond a wall)
+};
+
+__device__ __forceinline__ ColMap col_map(const NGeom &g, int a, int b) {
+    ColMap m;
+    for (int o = 0; o < 3; o++) {
+        m.na[o] = node_wrap(g, 0, a - 1 + o);
+        m.nb[o] = node_wrap(g, 1, b - 1 + o);
+    }
+    for (int o = 0; o < 2; o++) {
+        m.ca[o] = cell_wrap(g, 0, a - 1 + o);
+        m.cb[o] = cell_wrap(g, 1, b - 1 + o);
+    }
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_node_plane(const NGeom &g, const ColMap &m, const T *e, int c, T p[3][3]) {
+    const int cz = node_wrap(g, 2, c);
+    for (int y = 0; y < 3; y++)
+        for (int x = 0; x < 3; x++)
+            p[y][x] = (cz >= 0 && m.na[x] >= 0 && m.nb[y] >= 0) ? e[nidx(g, m.na[x], m.nb[y], cz)] : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_cell_plane(const NGeom &g, const ColMap &m, const T *sig, int k, T s[2][2]) {
+    const int kz = cell_wrap(g, 2, k);
+    for (int y = 0; y < 2; y++)
+        for (int x = 0; x < 2; x++)
+            s[y][x] = (kz >= 0 && m.ca[x] >= 0 && m.cb[y] >= 0) ? sig[cidx(g, m.ca[x], m.cb[y], kz)] : T(0);
+}
+
+// sum_m c_m e_m and sum_m c_m for node (.., .., c) from the planes below (pm),
+// at (p0) and above (pp) and the cells below (sl) and above (sh) the node
+template <typename T>
+__device__ __forceinline__ void couplings(const T pm[3][3], const T p0[3][3], const T pp[3][3], const T sl[2][2],
+                                          const T sh[2][2], T &num, T &den) {
+    num = T(0);
+    // face diagonals in the xy plane: both z cells
+    for (int y = 0; y < 2; y++)
+        for (int x = 0; x < 2; x++) num += (sl[y][x] + sh[y][x]) * p0[2 * y][2 * x];
+    // face diagonals in xz (oy = 0): both y cells; in yz (ox = 0): both x cells
+    for (int x = 0; x < 2; x++) {
+        num += (sl[0][x] + sl[1][x]) * pm[1][2 * x];
+        num += (sh[0][x] + sh[1][x]) * pp[1][2 * x];
+    }
+    for (int y = 0; y < 2; y++) {
+        num += (sl[y][0] + sl[y][1]) * pm[2 * y][1];
+        num += (sh[y][0] + sh[y][1]) * pp[2 * y][1];
+    }
+    // body diagonals: one cell each
+    for (int y = 0; y < 2; y++)
+        for (int x = 0; x < 2; x++) {
+            num += sl[y][x] * pm[2 * y][2 * x];
+            num += sh[y][x] * pp[2 * y][2 * x];
+        }
+    den = T(4) * (((sl[0][0] + sl[0][1]) + (sl[1][0] + sl[1][1])) + ((sh[0][0] + sh[0][1]) + (sh[1][0] + sh[1][1])));
+}
+
+constexpr int NCZ = 16;  // z-chunk of the column kernels
+
+template <typename T, int MODE>  // MODE 0: Gauss-Seidel on one colour, 1: residual r = f - L e
+__global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y) {
+    const NGeom &g = L.g;
+    const int cx = colour & 1, cy = colour >> 1;
+    const int tx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ty = blockIdx.y;
+    if (tx >= ncol_x || ty >= ncol_y) return;
+    const int a = MODE == 0 ? 2 * tx + cx : tx, b = MODE == 0 ? 2 * ty + cy : ty;
+    if (a >= g.m[0] || b >= g.m[1]) return;
+    const int c0 = blockIdx.z * NCZ, c1 = min(c0 + NCZ, g.m[2]);
+    const ColMap m = col_map(g, a, b);
+    const T h2 = T(g.h * g.h);
+    const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
+                      ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f);
+    T pm[3][3], p0[3][3], pp[3][3], sl[2][2], sh[2][2];
+    load_node_plane(g, m, L.e, c0 - 1, pm);
+    load_node_plane(g, m, L.e, c0, p0);
+    load_cell_plane(g, m, L.sigma, c0 - 1, sl);
+    for (int c = c0; c < c1; c++) {
+        load_node_plane(g, m, L.e, c + 1, pp);
+        load_cell_plane(g, m, L.sigma, c, sh);
+        T num, den;
+        couplings(pm, p0, pp, sl, sh, num, den);
+        const float w = wxy * ((!g.per[2] && (c == 0 || c == g.m[2] - 1)) ? 0.5f : 1.f);
+        const long long q = nidx(g, a, b, c);
+        if (MODE == 0) {
+            if (den > T(0)) L.e[q] = (num - T(12) * T(w) * h2 * L.f[q]) / den;
+        } else {
+            L.r[q] = L.f[q] - (num - den * p0[1][1]) / (T(12) * T(w) * h2);
+        }
+        for (int y = 0; y < 3; y++)
+            for (int x = 0; x < 3; x++) {
+                pm[y][x] = p0[y][x];
+                p0[y][x] = pp[y][x];
+            }
+        for (int y = 0; y < 2; y++)
+            for (int x = 0; x < 2; x++) sl[y][x] = sh[y][x];
+    }
+}
+
+template <typename T>
+static void k_nd_gs(cudaStream_t s, const NLevel<T> &L, int colour) {
+    const int cx = colour & 1, cy = colour >> 1;
+    const int ncx = (L.g.m[0] - cx + 1) / 2, ncy = (L.g.m[1] - cy + 1) / 2;
+    dim3 grid((ncx + 63) / 64, ncy, (L.g.m[2] + NCZ - 1) / NCZ);
+    nd_col_kernel<T, 0><<<grid, 64, 0, s>>>(L, colour, ncx, ncy);
+}
+
+template <typename T>
+static void k_nd_residual(cudaStream_t s, const NLevel<T> &L) {
+    dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + NCZ - 1) / NCZ);
+    nd_col_kernel<T, 1><<<grid, 64, 0, s>>>(L, 0, L.g.m[0], L.g.m[1]);
+}
+
 // ---- double-float residual of the refinement loop ------------------------------------
 __device__ __forceinline__ void ts2(float a, float b, float &s, float &e) {
     s = a + b;
@@ -508,116 +598,188 @@ __global__ void nd_df_update_kernel(NDF D, long long M, const float *__restrict_
     }
 }
 
-// 12 w h^2 r = 12 w h^2 f - sum_m c_m (phi_m - phi_n), in double-float;
-// rhat = r / scale in FP32 (the V-cycle right-hand side), norm partials of rhat.
-__global__ void nd_df_resid_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part) {
+// ---- column-marching residuals of the refinement loop -------------------------------
+
+// acc += coef * (q - p) in double-float, coef = (kh, kl), q = (qh, ql), p = (ch, cl)
+__device__ __forceinline__ void df_acc(float kh, float kl, float qh, float ql, float ch, float cl, float &Sh,
+                                       float &Se) {
+    float dh, de;
+    ts2(qh, -ch, dh, de);
+    de += ql - cl;
+    const float th = kh * dh;
+    float te = fmaf(kh, dh, -th);
+    te = fmaf(kh, de, te);
+    te = fmaf(kl, dh, te);
+    float s, e1;
+    ts2(Sh, th, s, e1);
+    Sh = s;
+    Se += e1 + te;
+}
+// (a + b) in double-float from two double-float values
+__device__ __forceinline__ void df_add2(float ah, float al, float bh, float bl, float &sh, float &sl) {
+    float e;
+    ts2(ah, bh, sh, e);
+    sl = e + (al + bl);
+}
+
+__device__ __forceinline__ void load_df_plane(const NGeom &g, const ColMap &m, const float *hi, const float *lo, int c,
+                                              float ph[3][3], float pl[3][3]) {
+    const int cz = node_wrap(g, 2, c);
+    for (int y = 0; y < 3; y++)
+        for (int x = 0; x < 3; x++) {
+            const bool ok = cz >= 0 && m.na[x] >= 0 && m.nb[y] >= 0;
+            const long long q = ok ? nidx(g, m.na[x], m.nb[y], cz) : 0;
+            ph[y][x] = ok ? hi[q] : 0.f;
+            pl[y][x] = ok ? lo[q] : 0.f;
+        }
+}
+__device__ __forceinline__ void load_df_cells(const NGeom &g, const ColMap &m, const float *hi, const float *lo, int k,
+                                              float sh[2][2], float sl[2][2]) {
+    const int kz = cell_wrap(g, 2, k);
+    for (int y = 0; y < 2; y++)
+        for (int x = 0; x < 2; x++) {
+            const bool ok = kz >= 0 && m.ca[x] >= 0 && m.cb[y] >= 0;
+            const long long q = ok ? cidx(g, m.ca[x], m.cb[y], kz) : 0;
+            sh[y][x] = ok ? hi[q] : 0.f;
+            sl[y][x] = ok ? lo[q] : 0.f;
+        }
+}
+
+// 12 w h^2 r = 12 w h^2 f - sum_m c_m (phi_m - phi_n) in double-float, node
+// columns marched in z; rhat = r / scale in FP32 with norm partials per block
+__global__ void nd_df_col_resid_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part) {
     const NGeom &g = L0.g;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    const int c0 = blockIdx.z * NCZ, c1 = min(c0 + NCZ, g.m[2]);
     const float inv = float(st->inv_scale);
     const float ih2 = float(1.0 / (g.h * g.h));
     float mx = 0.f, s2 = 0.f, s1 = 0.f;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
-        int a, b, c;
-        node_of(g, q, a, b, c);
-        float sh[2][2][2], sl[2][2][2];
-        for (int dz = 0; dz < 2; dz++) {
-            const int k = cell_wrap(g, 2, c - 1 + dz);
-            for (int dy = 0; dy < 2; dy++) {
-                const int j = cell_wrap(g, 1, b - 1 + dy);
-                for (int dx = 0; dx < 2; dx++) {
-                    const int i = cell_wrap(g, 0, a - 1 + dx);
-                    const bool ok = i >= 0 && j >= 0 && k >= 0;
-                    const long long cc = ok ? cidx(g, i, j, k) : 0;
-                    sh[dz][dy][dx] = ok ? D.sh[cc] : 0.f;
-                    sl[dz][dy][dx] = ok ? D.sl[cc] : 0.f;
+    if (a < g.m[0]) {
+        const ColMap m = col_map(g, a, b);
+        const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
+                          ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f);
+        float pmh[3][3], pml[3][3], p0h[3][3], p0l[3][3], pph[3][3], ppl[3][3];
+        float slh[2][2], sll[2][2], shh[2][2], shl[2][2];
+        load_df_plane(g, m, D.ph, D.pl, c0 - 1, pmh, pml);
+        load_df_plane(g, m, D.ph, D.pl, c0, p0h, p0l);
+        load_df_cells(g, m, D.sh, D.sl, c0 - 1, slh, sll);
+        for (int c = c0; c < c1; c++) {
+            load_df_plane(g, m, D.ph, D.pl, c + 1, pph, ppl);
+            load_df_cells(g, m, D.sh, D.sl, c, shh, shl);
+            const float ch = p0h[1][1], cl = p0l[1][1];
+            float Sh = 0.f, Se = 0.f, kh, kl;
+            for (int y = 0; y < 2; y++)
+                for (int x = 0; x < 2; x++) {
+                    df_add2(slh[y][x], sll[y][x], shh[y][x], shl[y][x], kh, kl);
+                    df_acc(kh, kl, p0h[2 * y][2 * x], p0l[2 * y][2 * x], ch, cl, Sh, Se);
+                    df_acc(slh[y][x], sll[y][x], pmh[2 * y][2 * x], pml[2 * y][2 * x], ch, cl, Sh, Se);
+                    df_acc(shh[y][x], shl[y][x], pph[2 * y][2 * x], ppl[2 * y][2 * x], ch, cl, Sh, Se);
                 }
+            for (int x = 0; x < 2; x++) {
+                df_add2(slh[0][x], sll[0][x], slh[1][x], sll[1][x], kh, kl);
+                df_acc(kh, kl, pmh[1][2 * x], pml[1][2 * x], ch, cl, Sh, Se);
+                df_add2(shh[0][x], shl[0][x], shh[1][x], shl[1][x], kh, kl);
+                df_acc(kh, kl, pph[1][2 * x], ppl[1][2 * x], ch, cl, Sh, Se);
             }
-        }
-        const float ch = D.ph[q], cl = D.pl[q];
-        float Sh = 0.f, Se = 0.f;
-        for (int oz = -1; oz <= 1; oz++)
-            for (int oy = -1; oy <= 1; oy++)
-                for (int ox = -1; ox <= 1; ox++) {
-                    if ((ox != 0) + (oy != 0) + (oz != 0) < 2) continue;
-                    float kh = 0.f, kl = 0.f;  // coefficient as double-float
-                    for (int dz = 0; dz < 2; dz++) {
-                        if (oz != 0 && dz != (oz > 0)) continue;
-                        for (int dy = 0; dy < 2; dy++) {
-                            if (oy != 0 && dy != (oy > 0)) continue;
-                            for (int dx = 0; dx < 2; dx++) {
-                                if (ox != 0 && dx != (ox > 0)) continue;
-                                float s, e1;
-                                ts2(kh, sh[dz][dy][dx], s, e1);
-                                kh = s;
-                                kl += e1 + sl[dz][dy][dx];
-                            }
-                        }
-                    }
-                    const int na = node_wrap(g, 0, a + ox), nb = node_wrap(g, 1, b + oy), nc = node_wrap(g, 2, c + oz);
-                    if (na < 0 || nb < 0 || nc < 0) continue;
-                    const long long m = nidx(g, na, nb, nc);
-                    float dh, de;
-                    ts2(D.ph[m], -ch, dh, de);
-                    de += D.pl[m] - cl;
-                    const float th = kh * dh;
-                    float te = fmaf(kh, dh, -th);
-                    te = fmaf(kh, de, te);
-                    te = fmaf(kl, dh, te);
-                    float s, e1;
-                    ts2(Sh, th, s, e1);
-                    Sh = s;
-                    Se += e1 + te;
+            for (int y = 0; y < 2; y++) {
+                df_add2(slh[y][0], sll[y][0], slh[y][1], sll[y][1], kh, kl);
+                df_acc(kh, kl, pmh[2 * y][1], pml[2 * y][1], ch, cl, Sh, Se);
+                df_add2(shh[y][0], shl[y][0], shh[y][1], shl[y][1], kh, kl);
+                df_acc(kh, kl, pph[2 * y][1], ppl[2 * y][1], ch, cl, Sh, Se);
+            }
+            const long long q = nidx(g, a, b, c);
+            float Rh, Re;
+            ts2(D.fh[q], -Sh, Rh, Re);
+            Re += D.fl[q] - Se;
+            const float R = Rh + Re;  // 12 w h^2 r
+            const float w = wxy * ((!g.per[2] && (c == 0 || c == g.m[2] - 1)) ? 0.5f : 1.f);
+            const float rh = R * (ih2 / (12.f * w)) * inv;
+            L0.f[q] = rh;
+            mx = fmaxf(mx, fabsf(rh));
+            s2 = fmaf(rh, rh, s2);
+            s1 += rh;
+            for (int y = 0; y < 3; y++)
+                for (int x = 0; x < 3; x++) {
+                    pmh[y][x] = p0h[y][x];
+                    pml[y][x] = p0l[y][x];
+                    p0h[y][x] = pph[y][x];
+                    p0l[y][x] = ppl[y][x];
                 }
-        float Rh, Re;
-        ts2(D.fh[q], -Sh, Rh, Re);
-        Re += D.fl[q] - Se;
-        const float R = Rh + Re;  // 12 w h^2 r
-        const float r = R * (ih2 / (12.f * node_w(g, a, b, c)));
-        const float rh = r * inv;
-        L0.f[q] = rh;
-        mx = fmaxf(mx, fabsf(rh));
-        s2 = fmaf(rh, rh, s2);
-        s1 += rh;
+            for (int y = 0; y < 2; y++)
+                for (int x = 0; x < 2; x++) {
+                    slh[y][x] = shh[y][x];
+                    sll[y][x] = shl[y][x];
+                }
+        }
     }
     block_red3f(mx, s2, s1);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x] = double(mx);
-        part[3 * blockIdx.x + 1] = double(s2);
-        part[3 * blockIdx.x + 2] = double(s1);
+        double *p = part + 3 * (blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
+        p[0] = double(mx);
+        p[1] = double(s2);
+        p[2] = double(s1);
     }
 }
 
-// FP64 residual of the plain FP64 path (and of mx_residual): r = f - L phi
-__global__ void nd_resid64_kernel(NLevel<double> L, const double *__restrict__ phi, const double *__restrict__ f,
-                                  double *__restrict__ rout, double *rhat, const SolveState *st, double *part) {
+static dim3 nd_col_grid(const NGeom &g) { return dim3((g.m[0] + 63) / 64, g.m[1], (g.m[2] + NCZ - 1) / NCZ); }
+static int nd_col_blocks(const NGeom &g) {
+    const dim3 d = nd_col_grid(g);
+    return int(d.x * d.y * d.z);
+}
+
+// FP64 residual r = f - L phi (plain FP64 path and mx_residual), columns marched in z
+__global__ void nd_col_resid64_kernel(NLevel<double> L, const double *__restrict__ phi, const double *__restrict__ f,
+                                      double *__restrict__ rout, double *__restrict__ rhat, const SolveState *st,
+                                      double *part) {
     const NGeom &g = L.g;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    const int c0 = blockIdx.z * NCZ, c1 = min(c0 + NCZ, g.m[2]);
     const double inv = st ? st->inv_scale : 1.0;
     double mx = 0.0, s2 = 0.0, s1 = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
-        double y;
-        {
-            int a, b, c;
-            node_of(g, q, a, b, c);
-            double s[2][2][2];
-            cell_ring(g, L.sigma, a, b, c, s);
-            double num = 0.0, den = 0.0;
-            for_couplings(g, a, b, c, s, [&](double coef, long long m) {
-                if (m >= 0) num += coef * (phi[m] - phi[q]);
-                den += coef;
-            });
-            y = num / (12.0 * node_w(g, a, b, c) * g.h * g.h);
+    if (a < g.m[0]) {
+        const ColMap m = col_map(g, a, b);
+        const double wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5 : 1.0) *
+                           ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5 : 1.0);
+        double pm[3][3], p0[3][3], pp[3][3], sl[2][2], sh[2][2];
+        load_node_plane(g, m, phi, c0 - 1, pm);
+        load_node_plane(g, m, phi, c0, p0);
+        load_cell_plane(g, m, L.sigma, c0 - 1, sl);
+        for (int c = c0; c < c1; c++) {
+            load_node_plane(g, m, phi, c + 1, pp);
+            load_cell_plane(g, m, L.sigma, c, sh);
+            // differences from the centre keep the cancellation exact in FP64
+            double dm[3][3], d0[3][3], dp[3][3];
+            for (int y = 0; y < 3; y++)
+                for (int x = 0; x < 3; x++) {
+                    dm[y][x] = pm[y][x] - p0[1][1];
+                    d0[y][x] = p0[y][x] - p0[1][1];
+                    dp[y][x] = pp[y][x] - p0[1][1];
+                }
+            double num, den;
+            couplings(dm, d0, dp, sl, sh, num, den);
+            const double w = wxy * ((!g.per[2] && (c == 0 || c == g.m[2] - 1)) ? 0.5 : 1.0);
+            const long long q = nidx(g, a, b, c);
+            const double r = f[q] - num / (12.0 * w * g.h * g.h);
+            if (rout) rout[q] = r;
+            if (rhat) rhat[q] = r * inv;
+            mx = fmax(mx, fabs(r));
+            s2 += r * r;
+            s1 += r;
+            for (int y = 0; y < 3; y++)
+                for (int x = 0; x < 3; x++) {
+                    pm[y][x] = p0[y][x];
+                    p0[y][x] = pp[y][x];
+                }
+            for (int y = 0; y < 2; y++)
+                for (int x = 0; x < 2; x++) sl[y][x] = sh[y][x];
         }
-        const double r = f[q] - y;
-        if (rout) rout[q] = r;
-        if (rhat) rhat[q] = r * inv;
-        mx = fmax(mx, fabs(r));
-        s2 += r * r;
-        s1 += r;
     }
     block_red3(mx, s2, s1);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x] = mx;
-        part[3 * blockIdx.x + 1] = s2;
-        part[3 * blockIdx.x + 2] = s1;
+        double *p = part + 3 * (blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
+        p[0] = mx;
+        p[1] = s2;
+        p[2] = s1;
     }
 }
 
@@ -722,11 +884,13 @@ static void carve_nodal(Bump &b, NodalPlan &P) {
             P.L32[l].sigma = b.take<float>(gs[l].N);
             P.L32[l].f = b.take<float>(gs[l].M);
             P.L32[l].e = b.take<float>(gs[l].M);
+            P.L32[l].r = b.take<float>(gs[l].M);
         } else {
             P.L64[l].g = gs[l];
             P.L64[l].sigma = b.take<double>(gs[l].N);
             P.L64[l].f = b.take<double>(gs[l].M);
             P.L64[l].e = b.take<double>(gs[l].M);
+            P.L64[l].r = b.take<double>(gs[l].M);
         }
     }
     const long long Mb = gs[P.nlev - 1].M;
@@ -752,7 +916,7 @@ static void free_nodal_plan(NodalPlan *p) {
 }
 
 static NodalPlan *get_nodal_plan(mx_ctx *c, const NGeom &g, int prec, mx_status *st) {
-    *st = ensure_partials(c, 152 * 8);
+    *st = ensure_partials(c, std::max(152 * 8, nd_col_blocks(g)));
     if (*st) return nullptr;
     for (NodalPlan *p : c->nplans)
         if (p->prec == prec && same_ngeom(p->g, g)) {
@@ -792,18 +956,41 @@ void destroy_nodal_plans(mx_ctx *c) {
 static int nblk(long long n) { return red_blocks(n); }
 
 template <typename T>
-static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int nu2, int bot_iters) {
+static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int nu2, int bot_iters, mx_ctx *pc) {
+    prof_begin(pc, s, MX_PH_UPDATE);
     cudaMemsetAsync(L[0].e, 0, sizeof(T) * L[0].g.M, s);
+    prof_end(pc, s, MX_PH_UPDATE, 1);
     for (int l = 0; l < nl - 1; l++) {
+        if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
         for (int q = 0; q < nu1; q++)
-            for (int col = 0; col < 4; col++) nd_gs_kernel<T><<<nblk(L[l].g.M / 4 + 1), 256, 0, s>>>(L[l], col);
-        nd_resid_restrict_kernel<T><<<nblk(L[l + 1].g.M), 256, 0, s>>>(L[l], L[l + 1]);
+            for (int col = 0; col < 4; col++) k_nd_gs(s, L[l], col);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_SMOOTH_FINE, 4 * nu1);
+            prof_begin(pc, s, MX_PH_RESTRICT_FINE);
+        }
+        k_nd_residual(s, L[l]);
+        nd_restrict_kernel<T><<<nblk(L[l + 1].g.M), 256, 0, s>>>(L[l], L[l + 1]);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_RESTRICT_FINE, 2);
+            prof_begin(pc, s, MX_PH_COARSE);
+        }
     }
+    if (nl == 1) prof_begin(pc, s, MX_PH_COARSE);
     nd_bottom_kernel<T><<<1, NBT, 0, s>>>(L[nl - 1], bot, bot_iters);
+    if (nl == 1) prof_end(pc, s, MX_PH_COARSE, 1);
     for (int l = nl - 2; l >= 0; l--) {
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_COARSE, 0);
+            prof_begin(pc, s, MX_PH_PROLONG_FINE);
+        }
         nd_prolong_kernel<T><<<nblk(L[l].g.M), 256, 0, s>>>(L[l + 1], L[l]);
+        if (l == 0) {
+            prof_end(pc, s, MX_PH_PROLONG_FINE, 1);
+            prof_begin(pc, s, MX_PH_SMOOTH_FINE);
+        }
         for (int q = 0; q < nu2; q++)
-            for (int col = 3; col >= 0; col--) nd_gs_kernel<T><<<nblk(L[l].g.M / 4 + 1), 256, 0, s>>>(L[l], col);
+            for (int col = 3; col >= 0; col--) k_nd_gs(s, L[l], col);
+        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, 4 * nu2);
     }
 }
 
@@ -848,6 +1035,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     init.maxit = std::min(o.max_outer, o.max_vcycles);
     *c->hstate = init;
     MX_CUDA(c, cudaMemcpyAsync(c->state, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    prof_begin(c, s, MX_PH_SETUP);
     if ((st = nodal_setup(c, *P, rho, beta0))) return st;
     nd_rhs_kernel<<<nb, 256, 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0, c->state);
     nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nb, c->state, o.remove_mean, 0);
@@ -876,22 +1064,32 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     } else if (!o.use_initial_guess) {
         MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.M, s));
     }
+    prof_end(c, s, MX_PH_SETUP, 0);
     // refinement loop (host-driven)
     for (;;) {
-        if (mixed) nd_df_resid_kernel<<<nb, 256, 0, s>>>(P->L32[0], P->D, c->state, c->partials);
-        else nd_resid64_kernel<<<nb, 256, 0, s>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f, c->state, c->partials);
-        k_finalize_residual(s, c->partials, nb, c->state, mixed ? 1 : 0);
+        prof_begin(c, s, MX_PH_RESID64);
+        if (mixed) nd_df_col_resid_kernel<<<nd_col_grid(g), 64, 0, s>>>(P->L32[0], P->D, c->state, c->partials);
+        else nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, s>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f, c->state,
+                                                                 c->partials);
+        k_finalize_residual(s, c->partials, nd_col_blocks(g), c->state, mixed ? 1 : 0);
+        prof_end(c, s, MX_PH_RESID64, 2);
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         MX_CUDA(c, cudaStreamSynchronize(s));
+        prof_flush(c);
         if (c->hstate->done) break;
         if (mixed) {
-            nd_vcycle<float>(s, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters);
+            nd_vcycle<float>(s, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, c);
+            prof_begin(c, s, MX_PH_UPDATE);
             nd_df_update_kernel<<<nb, 256, 0, s>>>(P->D, g.M, P->L32[0].e, c->state);
+            prof_end(c, s, MX_PH_UPDATE, 1);
         } else {
-            nd_vcycle<double>(s, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters);
+            nd_vcycle<double>(s, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, c);
+            prof_begin(c, s, MX_PH_UPDATE);
             nd_update64_kernel<<<nb, 256, 0, s>>>(phi, P->L64[0].e, c->state, g.M);
+            prof_end(c, s, MX_PH_UPDATE, 1);
         }
     }
+    prof_begin(c, s, MX_PH_FINISH);
     if (mixed) nd_df_final_kernel<<<nb, 256, 0, s>>>(P->D, g.M, phi);
     // normalise the weighted mean of phi to 0, correct U, check the divergence
     nd_wsum_kernel<<<nb, 256, 0, s>>>(g, phi, c->partials);
@@ -901,6 +1099,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     // divergence of the projected velocity minus Sbar_n minus c: nd_rhs with the mean subtracted
     nd_rhs_kernel<<<nb, 256, 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials, 1, c->state);
     k_finalize_max(s, c->partials, nb, &c->state->div_err);
+    prof_end(c, s, MX_PH_FINISH, 7);
     MX_CUDA(c, cudaEventRecord(c->ev1, s));
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));
@@ -935,8 +1134,8 @@ mx_status nodal_apply(mx_ctx *c, const mx_geom *geom, int prec, const double *rh
     const int nb = nblk(g.M);
     if (prec == MX_PREC_FP64) {
         if (f) {
-            nd_resid64_kernel<<<nb, 256, 0, s>>>(P->L64[0], phi, f, out, nullptr, nullptr, c->partials);
-            if (rnorm) k_finalize_max(s, c->partials, nb, &c->state->rnorm);
+            nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, s>>>(P->L64[0], phi, f, out, nullptr, nullptr, c->partials);
+            if (rnorm) k_finalize_max(s, c->partials, nd_col_blocks(g), &c->state->rnorm);
         } else {
             nd_apply_kernel<double><<<nb, 256, 0, s>>>(P->L64[0], phi, out);
         }
