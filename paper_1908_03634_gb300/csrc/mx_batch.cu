@@ -104,7 +104,7 @@ static BatchPlan *build_batch(mx_ctx *c, int nbox, const DGeom *g, const mx_opts
     for (int l = 0; l < B->maxdown; l++) {
         B->rb[l].off = int(work.size());
         for (int b = 0; b < nbox; b++)
-            if (l < B->lc[b]) add_grid(work, b, rbgs_grid(B->box[b]->H32.lev[l].g));
+            if (l < B->lc[b]) add_grid(work, b, rbgs_grid(B->box[b]->H32.lev[l].g, ZC));
         B->rb[l].n = int(work.size()) - B->rb[l].off;
         B->rr[l].off = int(work.size());
         for (int b = 0; b < nbox; b++)

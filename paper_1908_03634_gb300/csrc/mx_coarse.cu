@@ -128,11 +128,83 @@ __device__ void cta_apply(const Level<T> &L, const T *x, T *y, T ih2) {
     __syncthreads();
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// BiCGStab on a bottom level of at most 32 cells by one warp: one cell per
+// lane, dot products by shuffles, the operator's neighbour values through a
+// shared-memory vector; no block barriers.
+template <typename T>
+__device__ void warp_bicgstab(const Level<T> &L, T *x, const T *f, T *pv, int iters, int singular, T ih2) {
+    const int n = int(L.g.N), lane = threadIdx.x;
+    const bool act = lane < n;
+    int i = 0, j = 0, k = 0;
+    T b[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    if (act) {
+        cell_ijk(L.g, lane, i, j, k);
+        face_coefs(L, i, j, k, lane, b);
+    }
+    auto apply = [&](T val) -> T {  // (L val)_lane, values exchanged through pv
+        if (act) pv[lane] = val;
+        __syncwarp();
+        T y = T(0);
+        if (act) {
+            T v[6];
+            nb_vals(L.g, (const T *)pv, i, j, k, lane, v);
+            y = flux_sum(b, v, val) * ih2;
+        }
+        __syncwarp();
+        return y;
+    };
+    T rhs = act ? f[lane] : T(0);
+    if (singular) rhs -= warp_sum(rhs) / T(n);
+    if (!act) rhs = T(0);
+    T xv = T(0), r = rhs, r0 = rhs, p = T(0), v = T(0);
+    const T bnorm2 = warp_sum(rhs * rhs);
+    if (bnorm2 > T(0)) {
+        const T tol2 = bnorm2 * T(1e-8);
+        T rho = T(1), alpha = T(1), omega = T(1);
+        for (int it = 0; it < iters; it++) {
+            const T rho1 = warp_sum(r0 * r);
+            if (rho1 == T(0) || omega == T(0)) break;
+            const T beta = (rho1 / rho) * (alpha / omega);
+            p = r + beta * (p - omega * v);
+            v = apply(p);
+            const T r0v = warp_sum(r0 * v);
+            if (r0v == T(0)) break;
+            alpha = rho1 / r0v;
+            const T sv = r - alpha * v;
+            if (warp_sum(sv * sv) <= tol2) {
+                xv += alpha * p;
+                break;
+            }
+            const T tv = apply(sv);
+            const T tt = warp_sum(tv * tv), ts = warp_sum(tv * sv);
+            omega = tt > T(0) ? ts / tt : T(0);
+            xv += alpha * p + omega * sv;
+            r = sv - omega * tv;
+            rho = rho1;
+            if (warp_sum(r * r) <= tol2) break;
+        }
+    }
+    if (!act) xv = T(0);
+    if (singular) xv -= warp_sum(xv) / T(n);
+    if (act) x[lane] = xv;
+}
+
 // BiCGStab on L x = f (x starts at 0), projected onto mean-free vectors when
 // the problem is singular; stops at relative residual 1e-4 or `iters`.
 template <typename T>
 __device__ void cta_bicgstab(const Level<T> &L, T *x, const T *f, T *scr, int iters, int singular, T ih2) {
     const int n = int(L.g.N);
+    if (n <= 32) {
+        if (threadIdx.x < 32) warp_bicgstab(L, x, f, scr, iters, singular, ih2);
+        __syncthreads();
+        return;
+    }
     T *r = scr, *r0 = scr + n, *p = scr + 2 * n, *v = scr + 3 * n, *sv = scr + 4 * n, *tv = scr + 5 * n;
     const T mean = singular ? cta_sum(f, n) / T(n) : T(0);
     for (int q = threadIdx.x; q < n; q += CT) {

@@ -31,7 +31,7 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
 
 // ---- coefficients: FP64 face values, stored as hi (the FP32 level-0 array) + lo
 __device__ __forceinline__ double face_b(const double *beta0, const double *rho, long long cl, long long cr) {
-    return (beta0[cl] + beta0[cr]) / (rho[cl] + rho[cr]);
+    return (beta0[cl] + beta0[cr]) * rcp64(rho[cl] + rho[cr]);
 }
 
 __global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, const double *__restrict__ rho,
@@ -44,31 +44,31 @@ __global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, const double *_
     const int k1 = min(k0 + ZC, nz);
     for (int k = k0; k < k1; k++) {
         const long long c = i + (long long)nx * (j + (long long)ny * k);
-        const double own = 2.0 * (beta0[c] / rho[c]);  // a Dirichlet face's effective coefficient
+        auto own = [&]() { return 2.0 * (beta0[c] * rcp64(rho[c])); };  // a Dirichlet face's coefficient
         double bx, by, bz;
         if (i > 0) bx = face_b(beta0, rho, c - 1, c);
         else if (gper(g, 0)) bx = face_b(beta0, rho, c + nx - 1, c);
-        else bx = g.lo[0] == MX_BC_DIRICHLET ? own : 0.0;
+        else bx = g.lo[0] == MX_BC_DIRICHLET ? own() : 0.0;
         if (j > 0) by = face_b(beta0, rho, c - nx, c);
         else if (gper(g, 1)) by = face_b(beta0, rho, c + (long long)(ny - 1) * nx, c);
-        else by = g.lo[1] == MX_BC_DIRICHLET ? own : 0.0;
+        else by = g.lo[1] == MX_BC_DIRICHLET ? own() : 0.0;
         if (k > 0) bz = face_b(beta0, rho, c - g.nxy, c);
         else if (gper(g, 2)) bz = face_b(beta0, rho, c + (long long)(nz - 1) * g.nxy, c);
-        else bz = g.lo[2] == MX_BC_DIRICHLET ? own : 0.0;
+        else bz = g.lo[2] == MX_BC_DIRICHLET ? own() : 0.0;
         split_double(bx, L.bx[c], D.bxl[c]);
         split_double(by, L.by[c], D.byl[c]);
         split_double(bz, L.bz[c], D.bzl[c]);
         if (i == nx - 1 && L.hx) {
             const long long q = j + (long long)ny * k;
-            split_double(g.hi[0] == MX_BC_DIRICHLET ? own : 0.0, L.hx[q], D.hxl[q]);
+            split_double(g.hi[0] == MX_BC_DIRICHLET ? own() : 0.0, L.hx[q], D.hxl[q]);
         }
         if (j == ny - 1 && L.hy) {
             const long long q = i + (long long)nx * k;
-            split_double(g.hi[1] == MX_BC_DIRICHLET ? own : 0.0, L.hy[q], D.hyl[q]);
+            split_double(g.hi[1] == MX_BC_DIRICHLET ? own() : 0.0, L.hy[q], D.hyl[q]);
         }
         if (k == nz - 1 && L.hz) {
             const long long q = i + (long long)nx * j;
-            split_double(g.hi[2] == MX_BC_DIRICHLET ? own : 0.0, L.hz[q], D.hzl[q]);
+            split_double(g.hi[2] == MX_BC_DIRICHLET ? own() : 0.0, L.hz[q], D.hzl[q]);
         }
     }
 }

@@ -148,7 +148,7 @@ template <typename T>
 void k_update(cudaStream_t s, const DGeom &g, double *phi, const T *e, const SolveState *st);
 template <typename T>
 void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero = 0);
-dim3 rbgs_grid(const DGeom &g);
+dim3 rbgs_grid(const DGeom &g, int zc);
 // batched multigrid phases over a work list of (box, bx, by, bz)
 void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
                   int level, int colour, int zero);

@@ -51,26 +51,27 @@ __global__ void mac_coeffs_kernel(Level<double> L, const double *__restrict__ rh
     for (int k = k0; k < k1; k++) {
         const long long c = i + (long long)nx * (j + (long long)ny * k);
         const double bc = beta0[c], rc = rho[c];
+        auto own = [&]() { return 2.0 * (bc * rcp64(rc)); };  // a Dirichlet face's coefficient
         // x
-        if (i > 0) L.bx[c] = (beta0[c - 1] + bc) / (rho[c - 1] + rc);
-        else if (gper(g, 0)) L.bx[c] = (beta0[c + nx - 1] + bc) / (rho[c + nx - 1] + rc);
-        else L.bx[c] = g.lo[0] == MX_BC_DIRICHLET ? 2.0 * (bc / rc) : 0.0;
+        if (i > 0) L.bx[c] = (beta0[c - 1] + bc) * rcp64(rho[c - 1] + rc);
+        else if (gper(g, 0)) L.bx[c] = (beta0[c + nx - 1] + bc) * rcp64(rho[c + nx - 1] + rc);
+        else L.bx[c] = g.lo[0] == MX_BC_DIRICHLET ? own() : 0.0;
         // y
-        if (j > 0) L.by[c] = (beta0[c - nx] + bc) / (rho[c - nx] + rc);
+        if (j > 0) L.by[c] = (beta0[c - nx] + bc) * rcp64(rho[c - nx] + rc);
         else if (gper(g, 1)) {
             const long long o = c + (long long)(ny - 1) * nx;
-            L.by[c] = (beta0[o] + bc) / (rho[o] + rc);
-        } else L.by[c] = g.lo[1] == MX_BC_DIRICHLET ? 2.0 * (bc / rc) : 0.0;
+            L.by[c] = (beta0[o] + bc) * rcp64(rho[o] + rc);
+        } else L.by[c] = g.lo[1] == MX_BC_DIRICHLET ? own() : 0.0;
         // z
-        if (k > 0) L.bz[c] = (beta0[c - g.nxy] + bc) / (rho[c - g.nxy] + rc);
+        if (k > 0) L.bz[c] = (beta0[c - g.nxy] + bc) * rcp64(rho[c - g.nxy] + rc);
         else if (gper(g, 2)) {
             const long long o = c + (long long)(nz - 1) * g.nxy;
-            L.bz[c] = (beta0[o] + bc) / (rho[o] + rc);
-        } else L.bz[c] = g.lo[2] == MX_BC_DIRICHLET ? 2.0 * (bc / rc) : 0.0;
+            L.bz[c] = (beta0[o] + bc) * rcp64(rho[o] + rc);
+        } else L.bz[c] = g.lo[2] == MX_BC_DIRICHLET ? own() : 0.0;
         // high boundary planes
-        if (i == nx - 1 && L.hx) L.hx[j + (long long)ny * k] = g.hi[0] == MX_BC_DIRICHLET ? 2.0 * (bc / rc) : 0.0;
-        if (j == ny - 1 && L.hy) L.hy[i + (long long)nx * k] = g.hi[1] == MX_BC_DIRICHLET ? 2.0 * (bc / rc) : 0.0;
-        if (k == nz - 1 && L.hz) L.hz[i + (long long)nx * j] = g.hi[2] == MX_BC_DIRICHLET ? 2.0 * (bc / rc) : 0.0;
+        if (i == nx - 1 && L.hx) L.hx[j + (long long)ny * k] = g.hi[0] == MX_BC_DIRICHLET ? own() : 0.0;
+        if (j == ny - 1 && L.hy) L.hy[i + (long long)nx * k] = g.hi[1] == MX_BC_DIRICHLET ? own() : 0.0;
+        if (k == nz - 1 && L.hz) L.hz[i + (long long)nx * j] = g.hi[2] == MX_BC_DIRICHLET ? own() : 0.0;
     }
 }
 
@@ -201,55 +202,53 @@ void k_sub_mean_norm(cudaStream_t s, const DGeom &g, double *f, const SolveState
 }
 
 // ------------------------------------------------------------------------------
-// Correction U_f -= (dphi/dn)_f / rho_f on the API face layout.  The face
-// gradient is (phi_R - phi_L)/h inside and across periodic faces, one-sided
-// with phi = 0 across a Dirichlet face; wall faces are set to 0.
-__global__ void mac_correct_kernel(DGeom g, int d, const double *__restrict__ rho, const double *__restrict__ phi,
-                                   double *__restrict__ u, double ih) {
-    int m[3] = {g.n[0], g.n[1], g.n[2]};
-    m[d] += 1;
-    const long long nf = (long long)m[0] * m[1] * m[2];
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nf; q += (long long)gridDim.x * blockDim.x) {
-        int idx[3];
-        idx[0] = int(q % m[0]);
-        idx[1] = int((q / m[0]) % m[1]);
-        idx[2] = int(q / ((long long)m[0] * m[1]));
-        const int p = idx[d];
-        const int n = g.n[d];
-        long long stride = d == 0 ? 1 : (d == 1 ? g.n[0] : g.nxy);
-        // cell with the face's transverse indices and index min(p, n-1) along d
-        int cc[3] = {idx[0], idx[1], idx[2]};
-        const bool per = gper(g, d);
-        if (p > 0 && p < n) {
-            cc[d] = p;
-            const long long cr = cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]);
-            const long long cl = cr - stride;
-            const double rf = 0.5 * (rho[cl] + rho[cr]);
-            u[q] -= ((phi[cr] - phi[cl]) * ih) / rf;
-        } else if (per) {
-            cc[d] = 0;
-            const long long cr = cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]);
-            const long long cl = cr + (long long)(n - 1) * stride;
-            const double rf = 0.5 * (rho[cl] + rho[cr]);
-            u[q] -= ((phi[cr] - phi[cl]) * ih) / rf;
+// Correction U_f -= (dphi/dn)_f / rho_f on the API face layout.  One thread per
+// cell updates the cell's three low faces and, on the last cell of a row, the
+// high boundary face.  The face gradient is (phi_R - phi_L)/h inside and across
+// periodic faces (faces 0 and n then both get the same value), one-sided with
+// phi = 0 across a Dirichlet face; wall faces are set to 0.
+__device__ __forceinline__ void correct_face(const DGeom &g, int d, int p, long long cl, long long cr, long long ci,
+                                             const double *__restrict__ rho, const double *__restrict__ phi,
+                                             double *__restrict__ u, long long f, double ih) {
+    const int n = g.n[d];
+    if ((p > 0 && p < n) || gper(g, d)) {
+        const double rf = 0.5 * (rho[cl] + rho[cr]);
+        u[f] -= ((phi[cr] - phi[cl]) * ih) * rcp64(rf);
+    } else {
+        const int bc = p == 0 ? g.lo[d] : g.hi[d];
+        if (bc == MX_BC_DIRICHLET) {
+            const double grad = p == 0 ? (phi[ci] - 0.0) * (2.0 * ih) : (0.0 - phi[ci]) * (2.0 * ih);
+            u[f] -= grad * rcp64(rho[ci]);
         } else {
-            const int bc = p == 0 ? g.lo[d] : g.hi[d];
-            if (bc == MX_BC_DIRICHLET) {
-                cc[d] = p == 0 ? 0 : n - 1;
-                const long long ci = cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]);
-                const double grad = p == 0 ? (phi[ci] - 0.0) * (2.0 * ih) : (0.0 - phi[ci]) * (2.0 * ih);
-                u[q] -= grad / rho[ci];
-            } else {
-                u[q] = 0.0;
-            }
+            u[f] = 0.0;
         }
+    }
+}
+
+__global__ void mac_correct_kernel(DGeom g, const double *__restrict__ rho, const double *__restrict__ phi,
+                                   double *__restrict__ ux, double *__restrict__ uy, double *__restrict__ uz, double ih) {
+    const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
+    const int k0 = blockIdx.z * ZC;
+    if (i >= g.n[0] || j >= g.n[1]) return;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int k1 = min(k0 + ZC, nz);
+    for (int k = k0; k < k1; k++) {
+        const long long c = i + (long long)nx * (j + (long long)ny * k);
+        // x faces i (and nx on the last cell)
+        const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
+        correct_face(g, 0, i, i > 0 ? c - 1 : c + nx - 1, c, c, rho, phi, ux, fx, ih);
+        if (i == nx - 1) correct_face(g, 0, nx, c, c - (nx - 1), c, rho, phi, ux, fx + 1, ih);
+        const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
+        correct_face(g, 1, j, j > 0 ? c - nx : c + (long long)(ny - 1) * nx, c, c, rho, phi, uy, fy, ih);
+        if (j == ny - 1) correct_face(g, 1, ny, c, c - (long long)(ny - 1) * nx, c, rho, phi, uy, fy + nx, ih);
+        correct_face(g, 2, k, k > 0 ? c - g.nxy : c + (long long)(nz - 1) * g.nxy, c, c, rho, phi, uz, c, ih);
+        if (k == nz - 1) correct_face(g, 2, nz, c, c - (long long)(nz - 1) * g.nxy, c, rho, phi, uz, c + g.nxy, ih);
     }
 }
 
 void k_mac_correct(cudaStream_t s, const DGeom &g, const double *rho, const double *phi, double *ux, double *uy,
                    double *uz) {
-    double *u[3] = {ux, uy, uz};
-    for (int d = 0; d < 3; d++) mac_correct_kernel<<<red_blocks(g.N), RED_THREADS, 0, s>>>(g, d, rho, phi, u[d], 1.0 / g.h);
+    mac_correct_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, rho, phi, ux, uy, uz, 1.0 / g.h);
 }
 
 // max |D(beta0 U) - beta0 Sbar - c| of the projected velocity

@@ -186,12 +186,12 @@ void k_update(cudaStream_t s, const DGeom &g, double *phi, const T *e, const Sol
 // taken as 0 without reading e.
 template <typename T>
 __device__ __forceinline__ void rbgs_body(const Level<T> &L, int colour, T h2, int zero, int bx, int by, int bz,
-                                          int tx, int ty) {
+                                          int tx, int ty, int zc) {
     const DGeom &g = L.g;
     const int t = bx * SX + tx, j = by * SY + ty;
-    const int k0 = bz * ZC;
+    const int k0 = bz * zc;
     if (j >= g.n[1]) return;
-    const int k1 = min(k0 + ZC, g.n[2]);
+    const int k1 = min(k0 + zc, g.n[2]);
     for (int k = k0; k < k1; k++) {
         const int i = 2 * t + ((j + k + colour) & 1);
         if (i >= g.n[0]) continue;
@@ -208,12 +208,15 @@ __device__ __forceinline__ void rbgs_body(const Level<T> &L, int colour, T h2, i
 }
 
 template <typename T>
-__global__ void rbgs_kernel(Level<T> L, int colour, T h2, int zero) {
-    rbgs_body(L, colour, h2, zero, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
+__global__ void rbgs_kernel(Level<T> L, int colour, T h2, int zero, int zc) {
+    rbgs_body(L, colour, h2, zero, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, zc);
 }
 
-dim3 rbgs_grid(const DGeom &g) {
-    return dim3(((g.n[0] + 1) / 2 + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + ZC - 1) / ZC);
+dim3 rbgs_grid(const DGeom &g, int zc) {
+    return dim3(((g.n[0] + 1) / 2 + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + zc - 1) / zc);
+}
+static int rbgs_zc(const DGeom &g) {
+    return zchunk((long long)(((g.n[0] + 1) / 2 + SX - 1) / SX) * ((g.n[1] + SY - 1) / SY), g.n[2]);
 }
 
 // batched: work[blockIdx.x] = (box, bx, by, bz); level descriptors levs[box * MX_MAXLEV + level]
@@ -222,7 +225,7 @@ __global__ void rbgs_batch_kernel(const Level<float> *levs, const int4 *work, co
     const int4 w = work[blockIdx.x];
     if (st[w.x].done) return;
     const Level<float> L = levs[w.x * MX_MAXLEV + level];
-    rbgs_body(L, colour, float(L.g.h * L.g.h), zero, w.y, w.z, w.w, threadIdx.x, threadIdx.y);
+    rbgs_body(L, colour, float(L.g.h * L.g.h), zero, w.y, w.z, w.w, threadIdx.x, threadIdx.y, ZC);
 }
 
 void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
@@ -233,19 +236,20 @@ void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, in
 template <typename T>
 void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero) {
     const DGeom &g = L.g;
-    rbgs_kernel<T><<<rbgs_grid(g), dim3(SX, SY), 0, s>>>(L, colour, T(g.h * g.h), zero);
+    const int zc = rbgs_zc(g);
+    rbgs_kernel<T><<<rbgs_grid(g, zc), dim3(SX, SY), 0, s>>>(L, colour, T(g.h * g.h), zero, zc);
 }
 
 // Coarse RHS = average of the 8 fine residuals f - L e.
 template <typename T>
 __device__ __forceinline__ void resid_restrict_body(const Level<T> &F, const Level<T> &Cl, T ih2, int bx, int by,
-                                                    int bz, int tx, int ty) {
+                                                    int bz, int tx, int ty, int zc) {
     const DGeom &gc = Cl.g;
     const int I = bx * SX + tx, J = by * SY + ty;
-    const int K0 = bz * ZC;
+    const int K0 = bz * zc;
     if (I >= gc.n[0] || J >= gc.n[1]) return;
     const DGeom &g = F.g;
-    const int K1 = min(K0 + ZC, gc.n[2]);
+    const int K1 = min(K0 + zc, gc.n[2]);
     for (int K = K0; K < K1; K++) {
         T s = T(0);
         for (int dk = 0; dk < 2; dk++)
@@ -264,8 +268,8 @@ __device__ __forceinline__ void resid_restrict_body(const Level<T> &F, const Lev
 }
 
 template <typename T>
-__global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2) {
-    resid_restrict_body(F, Cl, ih2, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
+__global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2, int zc) {
+    resid_restrict_body(F, Cl, ih2, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, zc);
 }
 
 __global__ void resid_restrict_batch_kernel(const Level<float> *levs, const int4 *work, const SolveState *st,
@@ -274,7 +278,7 @@ __global__ void resid_restrict_batch_kernel(const Level<float> *levs, const int4
     if (st[w.x].done) return;
     const Level<float> F = levs[w.x * MX_MAXLEV + level];
     const Level<float> C = levs[w.x * MX_MAXLEV + level + 1];
-    resid_restrict_body(F, C, float(1.0 / (F.g.h * F.g.h)), w.y, w.z, w.w, threadIdx.x, threadIdx.y);
+    resid_restrict_body(F, C, float(1.0 / (F.g.h * F.g.h)), w.y, w.z, w.w, threadIdx.x, threadIdx.y, ZC);
 }
 
 void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork,
@@ -285,18 +289,19 @@ void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4
 template <typename T>
 void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse) {
     const double h = fine.g.h;
-    resid_restrict_kernel<T><<<stencil_grid(coarse.g), dim3(SX, SY), 0, s>>>(fine, coarse, T(1.0 / (h * h)));
+    const int zc = stencil_zc(coarse.g);
+    resid_restrict_kernel<T><<<stencil_grid_zc(coarse.g, zc), dim3(SX, SY), 0, s>>>(fine, coarse, T(1.0 / (h * h)), zc);
 }
 
 // e_fine += e_coarse(parent)
 template <typename T>
 __device__ __forceinline__ void prolong_body(const Level<T> &Cl, const Level<T> &F, int bx, int by, int bz, int tx,
-                                             int ty) {
+                                             int ty, int zc) {
     const DGeom &g = F.g;
     const int i = bx * SX + tx, j = by * SY + ty;
-    const int k0 = bz * ZC;
+    const int k0 = bz * zc;
     if (i >= g.n[0] || j >= g.n[1]) return;
-    const int k1 = min(k0 + ZC, g.n[2]);
+    const int k1 = min(k0 + zc, g.n[2]);
     for (int k = k0; k < k1; k++) {
         const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
         const long long C = (i >> 1) + (long long)Cl.g.n[0] * ((j >> 1) + (long long)Cl.g.n[1] * (k >> 1));
@@ -305,8 +310,8 @@ __device__ __forceinline__ void prolong_body(const Level<T> &Cl, const Level<T> 
 }
 
 template <typename T>
-__global__ void prolong_kernel(Level<T> Cl, Level<T> F) {
-    prolong_body(Cl, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
+__global__ void prolong_kernel(Level<T> Cl, Level<T> F, int zc) {
+    prolong_body(Cl, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, zc);
 }
 
 __global__ void prolong_batch_kernel(const Level<float> *levs, const int4 *work, const SolveState *st, int level) {
@@ -314,7 +319,7 @@ __global__ void prolong_batch_kernel(const Level<float> *levs, const int4 *work,
     if (st[w.x].done) return;
     const Level<float> C = levs[w.x * MX_MAXLEV + level + 1];
     const Level<float> F = levs[w.x * MX_MAXLEV + level];
-    prolong_body(C, F, w.y, w.z, w.w, threadIdx.x, threadIdx.y);
+    prolong_body(C, F, w.y, w.z, w.w, threadIdx.x, threadIdx.y, ZC);
 }
 
 void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
@@ -324,7 +329,8 @@ void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work,
 
 template <typename T>
 void k_prolong(cudaStream_t s, const Level<T> &coarse, const Level<T> &fine) {
-    prolong_kernel<T><<<stencil_grid(fine.g), dim3(SX, SY), 0, s>>>(coarse, fine);
+    const int zc = stencil_zc(fine.g);
+    prolong_kernel<T><<<stencil_grid_zc(fine.g, zc), dim3(SX, SY), 0, s>>>(coarse, fine, zc);
 }
 
 // y = L x on a level (unscaled by nothing: true operator, 1/h^2 included)

@@ -522,7 +522,7 @@ __device__ __forceinline__ void couplings(const T pm[3][3], const T p0[3][3], co
 constexpr int NCZ = 16;  // z-chunk of the column kernels
 
 template <typename T, int MODE>  // MODE 0: Gauss-Seidel on one colour, 1: residual r = f - L e
-__global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y) {
+__global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y, int nzc) {
     const NGeom &g = L.g;
     const int cx = colour & 1, cy = colour >> 1;
     const int tx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -530,7 +530,7 @@ __global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y) {
     if (tx >= ncol_x || ty >= ncol_y) return;
     const int a = MODE == 0 ? 2 * tx + cx : tx, b = MODE == 0 ? 2 * ty + cy : ty;
     if (a >= g.m[0] || b >= g.m[1]) return;
-    const int c0 = blockIdx.z * NCZ, c1 = min(c0 + NCZ, g.m[2]);
+    const int c0 = blockIdx.z * nzc, c1 = min(c0 + nzc, g.m[2]);
     const ColMap m = col_map(g, a, b);
     const T h2 = T(g.h * g.h);
     const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
@@ -561,18 +561,29 @@ __global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y) {
     }
 }
 
+// z-chunk of a column launch with bxy blocks per chunk: NCZ nodes per thread
+// on large levels, fewer (down to 1) until there are >= 8 blocks per SM, so
+// small levels are not latency-bound on a few long columns.
+static int nd_zchunk(long long bxy, int m2) {
+    int zc = NCZ;
+    while (zc > 1 && bxy * ((m2 + zc - 1) / zc) < 8 * 152) zc >>= 1;
+    return zc;
+}
+
 template <typename T>
 static void k_nd_gs(cudaStream_t s, const NLevel<T> &L, int colour) {
     const int cx = colour & 1, cy = colour >> 1;
     const int ncx = (L.g.m[0] - cx + 1) / 2, ncy = (L.g.m[1] - cy + 1) / 2;
-    dim3 grid((ncx + 63) / 64, ncy, (L.g.m[2] + NCZ - 1) / NCZ);
-    nd_col_kernel<T, 0><<<grid, 64, 0, s>>>(L, colour, ncx, ncy);
+    const int zc = nd_zchunk((long long)((ncx + 63) / 64) * ncy, L.g.m[2]);
+    dim3 grid((ncx + 63) / 64, ncy, (L.g.m[2] + zc - 1) / zc);
+    nd_col_kernel<T, 0><<<grid, 64, 0, s>>>(L, colour, ncx, ncy, zc);
 }
 
 template <typename T>
 static void k_nd_residual(cudaStream_t s, const NLevel<T> &L) {
-    dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + NCZ - 1) / NCZ);
-    nd_col_kernel<T, 1><<<grid, 64, 0, s>>>(L, 0, L.g.m[0], L.g.m[1]);
+    const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2]);
+    dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
+    nd_col_kernel<T, 1><<<grid, 64, 0, s>>>(L, 0, L.g.m[0], L.g.m[1], zc);
 }
 
 // ---- double-float residual of the refinement loop ------------------------------------

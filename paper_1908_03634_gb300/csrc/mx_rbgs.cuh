@@ -20,6 +20,9 @@ __device__ __forceinline__ T gs_update(const T b[6], const T v[6], T f, T h2) {
     return num / den;
 }
 
+// Whether the single-pass sweep supports this level (n_x even, periodic extents >= 2).
+bool rbgs_fused_ok(const DGeom &g);
+
 // e_out = one red+black sweep applied to e_in (mode RB_ZERO: e_in = 0;
 // RB_PROLONG: e_in + piecewise-constant prolongation of coarse->e).
 void k_rbgs_fused(cudaStream_t s, const Level<float> &L, const float *ein, float *eout, int mode,

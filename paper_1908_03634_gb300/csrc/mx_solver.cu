@@ -176,7 +176,7 @@ void destroy_plans(mx_ctx *c) {
 //  * other levels above the coarse end: two-pass colour kernels in place;
 //  * the coarse end (levels of <= COARSE_MAX_CELLS cells, down to the bottom):
 //    one single-CTA kernel; without such a level, a BiCGStab bottom kernel.
-constexpr long long FUSED_MIN_CELLS = 1LL << 20;
+constexpr long long FUSED_MIN_CELLS = 1LL << 18;
 
 template <typename T>
 int coarse_start(const Hier<T> &H) {
@@ -191,7 +191,7 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
     const int lc = coarse_start(H);
     const int ldown = lc < nl ? lc : nl - 1;  // levels with their own kernels
     const bool can_fuse = sizeof(T) == sizeof(float) && fused && nu1 >= 1 && nu2 >= 1;
-    auto is_fused = [&](int l) { return can_fuse && H.lev[l].g.N >= FUSED_MIN_CELLS; };
+    auto is_fused = [&](int l) { return can_fuse && H.lev[l].g.N >= FUSED_MIN_CELLS && rbgs_fused_ok(H.lev[l].g); };
     T *cur[MX_MAXLEV];
     for (int l = 0; l < ldown; l++) {
         Level<T> &L = H.lev[l];

@@ -41,6 +41,21 @@ __device__ __forceinline__ T flux_sum(const T b[6], const T v[6], T pc) {
     return s;
 }
 
+// 1/d in FP64 without the FP64 divide (which runs at 1/11 of the FMA rate on
+// this part): a correctly rounded FP32 reciprocal refined by two Newton-Raphson
+// steps r <- r + r (1 - d r); the result is within about 2 ulp of 1/d.
+// Values outside the FP32 range fall back to the division.
+__device__ __forceinline__ double rcp64(double d) {
+    const float df = __double2float_rn(d);
+    const float rf = __frcp_rn(df);
+    if (!(fabsf(df) > 1e-37f && fabsf(df) < 1e37f)) return 1.0 / d;
+    double r = double(rf);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 __device__ __forceinline__ int flat_tid() {
     return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
 }
@@ -131,6 +146,20 @@ __device__ __forceinline__ void reduce_partials3(const double *p, int nb, double
 constexpr int SX = 32, SY = 8, ZC = 8;
 inline dim3 stencil_grid(const DGeom &g) {
     return dim3((g.n[0] + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + ZC - 1) / ZC);
+}
+// z-chunk for a level with bxy blocks per chunk of planes: 8 planes per
+// thread on large levels, fewer (down to 1) until the grid has >= 4 blocks per
+// SM, so small levels are not latency-bound on a few long-running blocks.
+inline int zchunk(long long bxy, int nz) {
+    int zc = ZC;
+    while (zc > 1 && bxy * ((nz + zc - 1) / zc) < 4 * 152) zc >>= 1;
+    return zc;
+}
+inline dim3 stencil_grid_zc(const DGeom &g, int zc) {
+    return dim3((g.n[0] + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + zc - 1) / zc);
+}
+inline int stencil_zc(const DGeom &g) {
+    return zchunk((long long)((g.n[0] + SX - 1) / SX) * ((g.n[1] + SY - 1) / SY), g.n[2]);
 }
 inline int stencil_blocks(const DGeom &g) {
     dim3 d = stencil_grid(g);

@@ -222,11 +222,13 @@ def test_argument_errors(mx, ctx):
 
 
 FUSED_CASES = {
-    # levels of >= 2^20 cells run the single-pass kernel
+    # levels of >= 2^18 cells with even n_x run the single-pass kernel
     "planar128": lambda: W.planar(128, W.H_1E5, 0.6, 16, 3, 1),
     "ragged_136x104x96": lambda: W.planar((136, 104, 96), 0.2, 0.6, 8, 2, 7),
     "star_104": lambda: W.star(104, 32, 2),
     "planar32": lambda: W.planar32(),
+    "periodic_z_128x64x96": lambda: W.planar((128, 64, 96), 0.3, 0.6, 8, 2, 11, bc_z=W.PERIODIC),
+    "dirichlet_z_192x128x64": lambda: W.planar((192, 128, 64), 0.3, 0.6, 8, 2, 12, bc_z=W.DIRICHLET),
 }
 
 
