@@ -52,6 +52,10 @@ struct NodalPlan {
     double *sigma64 = nullptr, *f64 = nullptr;
     float *bot32 = nullptr;
     double *bot64 = nullptr;
+    // CUDA graph of the refinement loop, keyed by what it was captured with
+    cudaGraphExec_t graph = nullptr;
+    const void *graph_phi = nullptr;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1;
     long long last_use = 0;
 };
 
@@ -922,6 +926,7 @@ static void carve_nodal(Bump &b, NodalPlan &P) {
 }
 
 static void free_nodal_plan(NodalPlan *p) {
+    if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->mem) cudaFree(p->mem);
     delete p;
 }
@@ -1076,28 +1081,55 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.M, s));
     }
     prof_end(c, s, MX_PH_SETUP, 0);
-    // refinement loop (host-driven)
-    for (;;) {
-        prof_begin(c, s, MX_PH_RESID64);
-        if (mixed) nd_df_col_resid_kernel<<<nd_col_grid(g), 64, 0, s>>>(P->L32[0], P->D, c->state, c->partials);
-        else nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, s>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f, c->state,
-                                                                 c->partials);
-        k_finalize_residual(s, c->partials, nd_col_blocks(g), c->state, mixed ? 1 : 0);
-        prof_end(c, s, MX_PH_RESID64, 2);
-        MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-        MX_CUDA(c, cudaStreamSynchronize(s));
-        prof_flush(c);
-        if (c->hstate->done) break;
+    // refinement loop: residual, then while not converged {V-cycle, update, residual}
+    auto residual = [&](cudaStream_t ss, mx_ctx *pc) {
+        prof_begin(pc, ss, MX_PH_RESID64);
+        if (mixed) nd_df_col_resid_kernel<<<nd_col_grid(g), 64, 0, ss>>>(P->L32[0], P->D, c->state, c->partials);
+        else nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, ss>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f,
+                                                                  c->state, c->partials);
+        k_finalize_residual(ss, c->partials, nd_col_blocks(g), c->state, mixed ? 1 : 0);
+        prof_end(pc, ss, MX_PH_RESID64, 2);
+    };
+    auto step = [&](cudaStream_t ss, mx_ctx *pc) {
         if (mixed) {
-            nd_vcycle<float>(s, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, c);
-            prof_begin(c, s, MX_PH_UPDATE);
-            nd_df_update_kernel<<<nb, 256, 0, s>>>(P->D, g.M, P->L32[0].e, c->state);
-            prof_end(c, s, MX_PH_UPDATE, 1);
+            nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc);
+            prof_begin(pc, ss, MX_PH_UPDATE);
+            nd_df_update_kernel<<<nb, 256, 0, ss>>>(P->D, g.M, P->L32[0].e, c->state);
+            prof_end(pc, ss, MX_PH_UPDATE, 1);
         } else {
-            nd_vcycle<double>(s, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, c);
-            prof_begin(c, s, MX_PH_UPDATE);
-            nd_update64_kernel<<<nb, 256, 0, s>>>(phi, P->L64[0].e, c->state, g.M);
-            prof_end(c, s, MX_PH_UPDATE, 1);
+            nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc);
+            prof_begin(pc, ss, MX_PH_UPDATE);
+            nd_update64_kernel<<<nb, 256, 0, ss>>>(phi, P->L64[0].e, c->state, g.M);
+            prof_end(pc, ss, MX_PH_UPDATE, 1);
+        }
+        residual(ss, pc);
+    };
+    residual(s, c);
+    MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MX_CUDA(c, cudaStreamSynchronize(s));
+    prof_flush(c);
+    if (!c->hstate->done) {
+        if (o.use_graph && !c->prof) {
+            if (!P->graph || P->graph_phi != phi || P->graph_nu1 != o.nu1 || P->graph_nu2 != o.nu2 ||
+                P->graph_bot != o.bottom_iters) {
+                if (P->graph) {
+                    cudaGraphExecDestroy(P->graph);
+                    P->graph = nullptr;
+                }
+                if ((st = capture_while_graph(c, &P->graph, [&](cudaStream_t cs) { step(cs, nullptr); }))) return st;
+                P->graph_phi = phi;
+                P->graph_nu1 = o.nu1;
+                P->graph_nu2 = o.nu2;
+                P->graph_bot = o.bottom_iters;
+            }
+            MX_CUDA(c, cudaGraphLaunch(P->graph, s));
+        } else {
+            do {
+                step(s, c);
+                MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+                MX_CUDA(c, cudaStreamSynchronize(s));
+                prof_flush(c);
+            } while (!c->hstate->done);
         }
     }
     prof_begin(c, s, MX_PH_FINISH);

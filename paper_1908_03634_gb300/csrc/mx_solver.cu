@@ -317,6 +317,44 @@ __global__ void set_cond_kernel(cudaGraphConditionalHandle h, const SolveState *
     cudaGraphSetConditional(h, st->done ? 0u : 1u);
 }
 
+mx_status capture_while_graph(mx_ctx *c, cudaGraphExec_t *exec, const std::function<void(cudaStream_t)> &body) {
+    cudaGraph_t graph;
+    MX_CUDA(c, cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t inner = cp.conditional.phGraph_out[0];
+        cudaStream_t cs;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            e = cudaStreamBeginCaptureToGraph(cs, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                body(cs);
+                set_cond_kernel<<<1, 1, 0, cs>>>(handle, c->state);
+                cudaGraph_t captured;
+                e = cudaStreamEndCapture(cs, &captured);
+            }
+            cudaStreamDestroy(cs);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        return set_err(c, MX_ERR_CUDA, std::string("refinement-loop graph failed: ") + cudaGetErrorString(e));
+    }
+    return MX_OK;
+}
+
 template <typename T>
 static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular, int nb) {
     cudaStream_t s = c->stream;
@@ -326,46 +364,17 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
             cudaGraphExecDestroy(P.graph);
             P.graph = nullptr;
         }
-        cudaGraph_t graph;
-        MX_CUDA(c, cudaGraphCreate(&graph, 0));
-        cudaGraphConditionalHandle handle;
-        MX_CUDA(c, cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = handle;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        MX_CUDA(c, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        cudaStream_t cs;
-        MX_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            ir_step(cs, c, P, H, phi, o, singular, nb, nullptr);
-            set_cond_kernel<<<1, 1, 0, cs>>>(handle, c->state);
-            cudaGraph_t captured;
-            e = cudaStreamEndCapture(cs, &captured);
-        }
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(graph);
-            return set_err(c, MX_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
-        }
-        e = cudaGraphInstantiate(&P.graph, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            P.graph = nullptr;
-            return set_err(c, MX_ERR_CUDA, std::string("graph instantiate failed: ") + cudaGetErrorString(e));
-        }
+        mx_status st = capture_while_graph(
+            c, &P.graph, [&](cudaStream_t cs) { ir_step(cs, c, P, H, phi, o, singular, nb, nullptr); });
+        if (st) return st;
         P.graph_phi = phi;
         P.graph_nu1 = o.nu1;
         P.graph_nu2 = o.nu2;
         P.graph_bot = o.bottom_iters;
         P.graph_fused = o.fused;
     }
-    // the while node runs its body while the condition is 1; enter only if the
-    // first residual asked for a V-cycle
+    // the while node runs its body while the condition is 1 (the host checked
+    // that the first residual asked for a V-cycle)
     MX_CUDA(c, cudaGraphLaunch(P.graph, s));
     return MX_OK;
 }

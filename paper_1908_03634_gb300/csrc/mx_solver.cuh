@@ -2,6 +2,8 @@
 // FP64 finest-level operator and the multigrid hierarchy of the correction solve.
 #pragma once
 
+#include <functional>
+
 #include "mx_df.cuh"
 #include "mx_internal.cuh"
 
@@ -39,6 +41,11 @@ template <typename T>
 int coarse_start(const Hier<T> &H);
 void destroy_plans(mx_ctx *c);
 mx_status ensure_partials(mx_ctx *c, long long nblocks);
+
+// Capture body(stream) as the body of a conditional-while graph node and
+// instantiate it: one launch then runs body while SolveState::done is 0 (the
+// last kernel of each iteration sets the loop condition from it).
+mx_status capture_while_graph(mx_ctx *c, cudaGraphExec_t *exec, const std::function<void(cudaStream_t)> &body);
 
 template <typename T>
 void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *prof = nullptr,

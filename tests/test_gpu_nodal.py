@@ -134,3 +134,26 @@ def test_nodal_rejects_dirichlet(mx, ctx):
     with pytest.raises(mx.MXError) as e:
         mx.mx_nodal_project(ctx, g, *u, one, one, one, phi, mx.default_opts())
     assert e.value.status == mx.MX_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nodal_graph_and_host_loop_identical(mx, ctx, prec):
+    """The refinement loop captured as a conditional-while CUDA graph runs the
+    same kernels as the host-driven loop: bit-identical phi and U, twice."""
+    w = NODAL_WORKLOADS["ragged_40x24x32"]()
+    r1 = run_gpu_nodal(mx, ctx, w, prec, use_graph=1)
+    r2 = run_gpu_nodal(mx, ctx, w, prec, use_graph=0)
+    r3 = run_gpu_nodal(mx, ctx, w, prec, use_graph=1)
+    assert r1[0] == mx.MX_OK and r1[1]["vcycles"] == r2[1]["vcycles"] > 0
+    assert np.array_equal(r1[2], r2[2]) and np.array_equal(r1[2], r3[2])
+    for d in range(3):
+        assert np.array_equal(r1[3][d], r2[3][d])
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_nodal_iteration_cap_reports_noconv(mx, ctx, use_graph):
+    w = NODAL_WORKLOADS["ragged_40x24x32"]()
+    st, info, phi, _, _ = run_gpu_nodal(mx, ctx, w, 1, use_graph=use_graph, max_outer=2)
+    assert st == mx.MX_ERR_NOCONV and info["status"] == mx.MX_ERR_NOCONV
+    assert info["vcycles"] == 2 and info["rel_resid"] > 1e-10
+    assert np.isfinite(phi).all()
