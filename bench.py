@@ -44,9 +44,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the nodal and batched workloads")
     p.add_argument("--workload", default="planar256",
-                   choices=["planar256", "star512", "nodal-sweep"],
+                   choices=["planar256", "star512", "nodal-sweep", "nodal384", "batched96"],
                    help="planar256: the headline line (+ nodal384 and batched96 extras); star512: the "
-                        "full-star line; nodal-sweep: one line per nodal size 64^3..512^3")
+                        "full-star line; nodal-sweep: one line per nodal size 64^3..512^3; nodal384 / "
+                        "batched96: that extra alone (for profiling)")
     p.add_argument("--no-graph", action="store_true",
                    help="run the refinement loop from the host (same kernels; for profilers that "
                         "cannot see inside conditional CUDA graphs)")
@@ -339,7 +340,7 @@ def timed(fn, steps, stream):
     return a.elapsed_time(b), out
 
 
-def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hbm=6793.4):
+def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hbm=6793.4, graph=True):
     """Nodal projection (Step 11) on the planar256 stratification at n^3 cells:
     mixed precision vs plain FP64, solves/s, time per V-cycle and the HBM
     fraction of one V-cycle against the model's algorithmic bytes."""
@@ -350,7 +351,7 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0, g.dx, (0.5, 0.5, 0.5), beta0)
     phi = torch.zeros(mx.node_shape(g), dtype=torch.float64, device=dev)
     us = [[t.clone() for t in w.u] for _ in range(steps + warmup)]
-    opts = mx.default_opts()
+    opts = mx.default_opts(use_graph=int(graph))
     run = lambda u, o: mx.mx_nodal_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
     for i in range(warmup):
         run(us[i], opts)
@@ -374,7 +375,7 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
            "hbm_frac_per_vcycle": round(model / (ms_solve / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
            "model_bytes_per_vcycle": model, "phases": trace}
     if fp64:
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=int(graph))
         u64 = [t.clone() for t in w.u]
         run(u64, o64)
         for d in range(3):
@@ -485,7 +486,14 @@ def run_other(args):
     except (OSError, ValueError):
         peaks = {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    if args.workload == "nodal-sweep":
+    if args.workload == "nodal384":
+        r = bench_nodal(mx, W, ctx, dev, stream, n=384, steps=args.steps, warmup=args.warmup,
+                        fp64=not args.no_fp64, hbm=hbm, graph=not args.no_graph)
+        print(json.dumps(r), flush=True)
+    elif args.workload == "batched96":
+        r = bench_batched(mx, W, ctx, dev, stream, steps=args.steps, warmup=args.warmup, fp64=not args.no_fp64)
+        print(json.dumps(r), flush=True)
+    elif args.workload == "nodal-sweep":
         for n in (64, 128, 192, 256, 384, 512):
             r = bench_nodal(mx, W, ctx, dev, stream, n=n, steps=2, warmup=1, fp64=(n <= 256), hbm=hbm)
             print(json.dumps(r), flush=True)
