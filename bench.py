@@ -120,6 +120,28 @@ def algorithmic_bytes_per_cell():
     return {"smooth_fine": 12.0, "resid64": 44.0}
 
 
+def launches_per_solve(g, o, vcycles, graph):
+    """Kernels the library launches for one mixed-precision MAC solve (fill
+    included), from the solver's structure: setup 13 + first residual 2; per
+    refinement iteration the V-cycle's launches on the levels above the coarse
+    end (> 4096 cells: colour passes, residual+restriction, prolongation, or
+    single-pass sweeps), the coarse-end CTA, update+residual and its finalize
+    (+1 condition kernel inside the graph); finish 7.  It reproduces the ncu
+    launch list of the planar 256^3 solve (409 launches at 9 V-cycles, host loop)."""
+    dims = [list(g.n)]
+    while all(d % 2 == 0 and d >= 4 for d in dims[-1]):
+        dims.append([d // 2 for d in dims[-1]])
+    nlev = len(dims)
+    ncell = [d[0] * d[1] * d[2] for d in dims]
+    ldown = next((l for l in range(nlev) if ncell[l] <= 4096), nlev - 1)
+    per_iter = 1 + 2 + (1 if graph else 0)
+    for l in range(ldown):
+        fused = o.fused and ncell[l] >= (1 << 18) and dims[l][0] % 2 == 0
+        per_iter += (o.nu1 + 1 + o.nu2) if fused else (2 * o.nu1 + 1 + 1 + 2 * o.nu2)
+    setup = 1 + 1 + (nlev - 1) + 4 + 2
+    return setup + vcycles * per_iter + 7
+
+
 def setup_inputs(mx, W, dev, n, copies):
     import torch
     w = W.planar256(device=dev, n=n)
@@ -155,7 +177,17 @@ def run_mx(args):
     phi = torch.zeros_like(rho)
     stream = torch.cuda.current_stream()
     ctx = mx.mx_create(local, stream)
-    opts = mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=0 if args.no_graph else 1)
+    graph = 0 if args.no_graph else 1
+    # the library's autotuner picks sweep counts, tile depth and sweep kind on
+    # these inputs (untimed); the timed solves then run with nu1 = nu2 = 0
+    mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
+    t_tune = time.perf_counter()
+    tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar,
+                              base=mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph))
+    tuned64, _ = (None, None) if args.no_fp64 else mx.mx_autotune(
+        ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar, base=mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph))
+    t_tune = time.perf_counter() - t_tune
+    opts = mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=0, nu2=0)
 
     def step(u, o=opts):
         mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
@@ -188,21 +220,12 @@ def run_mx(args):
     assert all(i["status"] == 0 for i in infos), infos[-1]
     value = world * K / (ms_total / 1e3)
     vcycles = statistics.mean(i["vcycles"] for i in infos[Wm:])
-    # launches per step: fill 1 + setup (coeffs, round 6, coarsen L-1, rhs 4) + loop + finish
-    nlev = 0
-    m = n
-    while m % 2 == 0 and m >= 4:
-        m //= 2
-        nlev += 1
-    nlev += 1
-    per_vcycle = 1 + (nlev - 1) * (4 * 2 + 1) + 1 + (nlev - 1) * (1 + 4 * 2) + 1 + 2 + 1   # memset, sweeps, restrict, bottom, prolong, update, resid+finalize, cond
-    per_setup = 1 + 1 + 6 + (nlev - 1) + 4 + 2 + 1
-    launches = int(round(K * (per_setup + vcycles * per_vcycle + 8)))
+    launches = int(round(K * launches_per_solve(g, tuned, vcycles, graph)))
 
     # ---- plain FP64 solve (the comparison) ----
     fp64 = None
     if not args.no_fp64:
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=0 if args.no_graph else 1)
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph, nu1=0, nu2=0)
         u64 = [t.clone() for t in w.u]
         step(u64, o64)  # warm-up (plan, graph)
         kk = max(2, min(5, K // 4))
@@ -244,7 +267,10 @@ def run_mx(args):
         phases[name] = {"ms_per_step": pms / nt, "launches_per_step": pn / nt}
     sm_ms, sm_n = trace["smooth_fine"]
     per_launch_ms = sm_ms / max(sm_n, 1)
-    achieved = bpc["smooth_fine"] * ncell / (per_launch_ms * 1e-3) / 1e9
+    # the tuned smoother: two colour passes (12 B/cell each) or single-pass sweeps (24 B/cell)
+    fused0 = bool(tuned.fused) and ncell >= (1 << 18) and g.n[0] % 2 == 0
+    sweep_bytes = 2 * bpc["smooth_fine"] if fused0 else bpc["smooth_fine"]
+    achieved = sweep_bytes * ncell / (per_launch_ms * 1e-3) / 1e9
     r_ms, r_n = trace["resid64"]
     resid_per_launch = r_ms / max(r_n / 2, 1)   # resid64 phase = residual + its 1-block finalize
     traffic = None
@@ -253,10 +279,13 @@ def run_mx(args):
         traffic = tr.get("rbgs_fp32_per_launch_bytes_256")
     except (OSError, ValueError):
         pass
-    roofline = {"kernel": "rbgs_kernel<float> (finest level, one colour)", "bound": "hbm",
+    if fused0:
+        traffic = None  # the ncu figure is for the colour-pass kernel
+    roofline = {"kernel": ("rbgs_march_kernel (finest level, one red+black sweep)" if fused0 else
+                           "rbgs_kernel<float> (finest level, one colour)"), "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "peak_source": peak_src, "traffic": traffic,
-                "algorithmic_bytes_per_launch": bpc["smooth_fine"] * ncell,
+                "algorithmic_bytes_per_launch": sweep_bytes * ncell,
                 "ms_per_launch": per_launch_ms,
                 "resid64": {"ms_per_launch": resid_per_launch,
                             "achieved_GBs": round(bpc["resid64"] * ncell / (resid_per_launch * 1e-3) / 1e9, 1)}}
@@ -315,7 +344,11 @@ def run_mx(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"planar{n}", "cells": g.ncell, "bc": "periodic x,y / wall z",
                    "density_contrast": 1e5, "beta0": "rho0^(3/5)", "rel_tol": 1e-10,
-                   "precision": "FP32 V-cycles in FP64 iterative refinement", "nu1": 2, "nu2": 2,
+                   "precision": "FP32 V-cycles in FP64 iterative refinement",
+                   "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z, "fused": tuned.fused,
+                             "fp64": None if tuned64 is None else {"nu1": tuned64.nu1, "nu2": tuned64.nu2,
+                                                                   "tile_z": tuned64.tile_z},
+                             "tuning_s": round(t_tune, 2)},
                    "l2_policy": "inputs larger than L2 (fresh U copy per step, ~1.5 GB working set)",
                    "parallelism": f"replicas x{world}"},
         "vcycles_per_solve": vcycles, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
@@ -351,7 +384,9 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0, g.dx, (0.5, 0.5, 0.5), beta0)
     phi = torch.zeros(mx.node_shape(g), dtype=torch.float64, device=dev)
     us = [[t.clone() for t in w.u] for _ in range(steps + warmup)]
-    opts = mx.default_opts(use_graph=int(graph))
+    tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_NODAL, g, *w.u, w.rho, beta0, w.sbar,
+                              base=mx.default_opts(use_graph=int(graph)))
+    opts = mx.default_opts(use_graph=int(graph), nu1=0, nu2=0)
     run = lambda u, o: mx.mx_nodal_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
     for i in range(warmup):
         run(us[i], opts)
@@ -373,9 +408,11 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
            "vcycles": vc, "rel_resid": infos[-1]["rel_resid"], "div_err_linf": infos[-1]["div_err_linf"],
            "ms_per_vcycle_upper": ms_solve / max(vc, 1),
            "hbm_frac_per_vcycle": round(model / (ms_solve / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
-           "model_bytes_per_vcycle": model, "phases": trace}
+           "model_bytes_per_vcycle": model, "phases": trace,
+           "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z}}
     if fp64:
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=int(graph))
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=int(graph), nu1=tuned.nu1, nu2=tuned.nu2,
+                              tile_z=tuned.tile_z)
         u64 = [t.clone() for t in w.u]
         run(u64, o64)
         for d in range(3):

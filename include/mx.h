@@ -71,7 +71,10 @@ typedef struct {
 
 /* Solver options.  mx_default_opts() fills: rel_tol 1e-10, max_outer 100,
  * max_vcycles 100, prec MX_PREC_MIXED, remove_mean 1, use_initial_guess 0,
- * use_graph 1, nu1 = nu2 = 2 (0 = autotuned), bottom_iters 200, fused 0. */
+ * use_graph 1, nu1 = nu2 = 2, bottom_iters 200, fused 0, tile_z 0.
+ * nu1 = nu2 = 0 selects the setting mx_autotune() stored in the context for
+ * this operator, precision and geometry (nu1, nu2, fused, tile_z), or
+ * 2, 2, fused, tile_z as given when nothing is stored. */
 typedef struct {
     double rel_tol;        /* stop when ||f - L phi||_inf <= rel_tol ||f||_inf */
     int max_outer;         /* iterative-refinement iterations (one V-cycle each) */
@@ -84,6 +87,10 @@ typedef struct {
     int bottom_iters;      /* BiCGStab iteration cap on the coarsest grid */
     int fused;             /* 1: single-pass tile sweeps with the prolongation fused on load;
                               0: two-pass colour kernels (default; bit-identical results) */
+    int tile_z;            /* cells per thread along z in the stencil kernels' tiles (the
+                              largest z-chunk; smaller levels use fewer): 0 = default
+                              (8 MAC, 16 nodal), else 1, 2, 4, 8 or 16; results do not
+                              depend on it */
 } mx_opts;
 
 typedef struct {
@@ -202,6 +209,30 @@ enum {
 };
 mx_status mx_profile_enable(mx_ctx *ctx, int enable);
 mx_status mx_profile_read(mx_ctx *ctx, double *ms, long long *launches);
+
+/* Autotuner (a GPU tuning step; the paper has no counterpart).  Times the
+ * projection of the given inputs (op MX_OP_MAC: mx_mac_project, MX_OP_NODAL:
+ * mx_nodal_project, same argument layouts) under candidate smoother and tile
+ * settings -- sweep counts (nu1, nu2) in {1..4}, then tile_z in {4, 8, 16}
+ * (nodal {4, 8, 16, default}), then (MAC, mixed precision) the single-pass
+ * sweep -- one at a time from base (NULL = defaults), keeping a change only if
+ * the solve converges and is faster (CUDA-event time of a whole call, after
+ * one untimed call that builds the graph).  Candidates needing more than
+ * 3 x (the best's V-cycles) + 4 V-cycles are cut off.  The winner is stored in
+ * the context's tune cache for (op, prec, geometry) and used by later calls
+ * with nu1 = nu2 = 0.  The inputs are not modified: the tuner copies U and
+ * phi into scratch it allocates and frees (about 4 fields of device memory).
+ * best (may be NULL): the chosen options (base with nu1, nu2, fused, tile_z
+ * replaced); ms_best (may be NULL): the tuned solve's time in ms.  Returns
+ * MX_ERR_NOCONV if no candidate converges, MX_ERR_OOM if the scratch cannot
+ * be allocated, or the error of the first failing solve. */
+mx_status mx_autotune(mx_ctx *ctx, int op, const mx_geom *geom, const double *ux, const double *uy,
+                      const double *uz, const double *rho, const double *beta0, const double *sbar,
+                      const mx_opts *base, mx_opts *best, double *ms_best);
+
+/* Look up the tune cache: 1 and *out = the stored setting (base fields from
+ * *out as passed) if mx_autotune stored one for (op, prec, geometry), else 0. */
+int mx_tune_lookup(const mx_ctx *ctx, int op, int prec, const mx_geom *geom, mx_opts *out);
 
 #ifdef __cplusplus
 }

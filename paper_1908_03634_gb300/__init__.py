@@ -31,7 +31,8 @@ class mx_geom(C.Structure):
 class mx_opts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("max_outer", C.c_int), ("max_vcycles", C.c_int), ("prec", C.c_int),
                 ("remove_mean", C.c_int), ("use_initial_guess", C.c_int), ("use_graph", C.c_int),
-                ("nu1", C.c_int), ("nu2", C.c_int), ("bottom_iters", C.c_int), ("fused", C.c_int)]
+                ("nu1", C.c_int), ("nu2", C.c_int), ("bottom_iters", C.c_int), ("fused", C.c_int),
+                ("tile_z", C.c_int)]
 
 
 class mx_info(C.Structure):
@@ -78,6 +79,8 @@ def load():
         "mx_residual_noalloc": (C.c_int, [G, _DP, _DP, _DP, _DP, _DP, C.POINTER(C.c_double), _VP]),
         "mx_profile_enable": (C.c_int, [_VP, C.c_int]),
         "mx_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+        "mx_autotune": (C.c_int, [_VP, C.c_int, G, _DP, _DP, _DP, _DP, _DP, _DP, O, O, C.POINTER(C.c_double)]),
+        "mx_tune_lookup": (C.c_int, [_VP, C.c_int, C.c_int, G, O]),
         "mx_mac_project_batched": (C.c_int, [_VP, C.c_int, G, C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP),
                                              C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), O, I]),
     }
@@ -93,7 +96,8 @@ def exported_symbols():
     """Names declared in include/mx.h and exported by the library."""
     return ["mx_create", "mx_destroy", "mx_set_stream", "mx_last_error", "mx_default_opts", "mx_device_supported",
             "mx_fill_base_state", "mx_mac_project", "mx_nodal_project", "mx_apply_op", "mx_residual",
-            "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc"]
+            "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc",
+            "mx_autotune", "mx_tune_lookup"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -214,6 +218,30 @@ def mx_nodal_project(ctx, geom, ux, uy, uz, rho, beta0, sbar, phi_nodes, opts=No
                                  C.byref(opts) if opts is not None else None, C.byref(info))
     _check(ctx, st, allow)
     return st, info.as_dict()
+
+
+def mx_autotune(ctx, op, geom, ux, uy, uz, rho, beta0, sbar, base=None):
+    """Tune (nu1, nu2, tile_z, fused) on these inputs (left unmodified); returns
+    (chosen mx_opts, ms of the tuned solve).  The choice is cached in ctx for
+    calls with nu1 = nu2 = 0."""
+    g = make_geom(geom)
+    cs = cell_shape(geom)
+    us = [face_shape(geom, d) for d in range(3)] if op == MX_OP_MAC else [cs] * 3
+    best = mx_opts()
+    ms = C.c_double(0.0)
+    st = load().mx_autotune(ctx, int(op), C.byref(g), _ptr(ux, us[0], "ux"), _ptr(uy, us[1], "uy"),
+                            _ptr(uz, us[2], "uz"), _ptr(rho, cs, "rho"), _ptr(beta0, cs, "beta0"),
+                            _ptr(sbar, cs, "sbar"), C.byref(base) if base is not None else None, C.byref(best),
+                            C.byref(ms))
+    _check(ctx, st)
+    return best, ms.value
+
+
+def mx_tune_lookup(ctx, op, prec, geom):
+    """The cached tuned options for (op, prec, geom), or None."""
+    g = make_geom(geom)
+    o = default_opts()
+    return o if load().mx_tune_lookup(ctx, int(op), int(prec), C.byref(g), C.byref(o)) else None
 
 
 def mx_apply_op(ctx, geom, op, prec, rho, beta0, phi, out):

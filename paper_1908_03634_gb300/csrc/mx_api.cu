@@ -207,6 +207,7 @@ void mx_default_opts(mx_opts *o) {
     o->nu2 = 2;
     o->bottom_iters = 200;
     o->fused = 0;
+    o->tile_z = 0;
 }
 
 int mx_device_supported(int device) {

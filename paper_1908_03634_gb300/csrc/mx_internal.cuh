@@ -69,6 +69,9 @@ struct mx_ctx {
     double *partials = nullptr;   // device reduction scratch (3 doubles per block)
     int max_partials = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // tune cache (mx_autotune): the fastest setting per operator, precision and geometry
+    struct Tune { int op, prec, n[3], lo[3], hi[3], nu1, nu2, fused, tile_z; double ms; };
+    std::vector<Tune> tune;
     std::vector<MacPlan *> plans;        // cached workspaces, one per geometry/precision
     std::vector<NodalPlan *> nplans;
     BatchPlan *batch = nullptr;
@@ -81,6 +84,10 @@ struct mx_ctx {
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> ev_pool;
 };
+
+// nu1 = nu2 = 0 in o: replace nu1, nu2, fused, tile_z by the tune cache's
+// entry for (op, o.prec, geometry), or nu1 = nu2 = 2 when there is none.
+void tune_apply(const mx_ctx *c, int op, const mx_geom *g, mx_opts &o);
 
 // phase markers: no-ops unless tracing is on and the stream is not capturing
 void prof_begin(mx_ctx *c, cudaStream_t s, int phase);
@@ -147,7 +154,7 @@ void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveSt
 template <typename T>
 void k_update(cudaStream_t s, const DGeom &g, double *phi, const T *e, const SolveState *st);
 template <typename T>
-void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero = 0);
+void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero = 0, int zcap = 8);
 dim3 rbgs_grid(const DGeom &g, int zc);
 // batched multigrid phases over a work list of (box, bx, by, bz)
 void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
@@ -159,9 +166,9 @@ void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work,
 void k_finalize_residual_batch(cudaStream_t s, const double *partials, const int *off, const int *cnt, SolveState *st,
                                int nbox);
 template <typename T>
-void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse);
+void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse, int zcap = 8);
 template <typename T>
-void k_prolong(cudaStream_t s, const Level<T> &coarse, const Level<T> &fine);
+void k_prolong(cudaStream_t s, const Level<T> &coarse, const Level<T> &fine, int zcap = 8);
 template <typename T>
 void k_bottom(cudaStream_t s, const Level<T> &L, T *scratch, int iters, int singular);
 template <typename T>

@@ -215,8 +215,8 @@ __global__ void rbgs_kernel(Level<T> L, int colour, T h2, int zero, int zc) {
 dim3 rbgs_grid(const DGeom &g, int zc) {
     return dim3(((g.n[0] + 1) / 2 + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + zc - 1) / zc);
 }
-static int rbgs_zc(const DGeom &g) {
-    return zchunk((long long)(((g.n[0] + 1) / 2 + SX - 1) / SX) * ((g.n[1] + SY - 1) / SY), g.n[2]);
+static int rbgs_zc(const DGeom &g, int cap) {
+    return zchunk((long long)(((g.n[0] + 1) / 2 + SX - 1) / SX) * ((g.n[1] + SY - 1) / SY), g.n[2], cap);
 }
 
 // batched: work[blockIdx.x] = (box, bx, by, bz); level descriptors levs[box * MX_MAXLEV + level]
@@ -234,9 +234,9 @@ void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, in
 }
 
 template <typename T>
-void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero) {
+void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero, int zcap) {
     const DGeom &g = L.g;
-    const int zc = rbgs_zc(g);
+    const int zc = rbgs_zc(g, zcap);
     rbgs_kernel<T><<<rbgs_grid(g, zc), dim3(SX, SY), 0, s>>>(L, colour, T(g.h * g.h), zero, zc);
 }
 
@@ -287,9 +287,9 @@ void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4
 }
 
 template <typename T>
-void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse) {
+void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse, int zcap) {
     const double h = fine.g.h;
-    const int zc = stencil_zc(coarse.g);
+    const int zc = stencil_zc(coarse.g, zcap);
     resid_restrict_kernel<T><<<stencil_grid_zc(coarse.g, zc), dim3(SX, SY), 0, s>>>(fine, coarse, T(1.0 / (h * h)), zc);
 }
 
@@ -328,8 +328,8 @@ void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work,
 }
 
 template <typename T>
-void k_prolong(cudaStream_t s, const Level<T> &coarse, const Level<T> &fine) {
-    const int zc = stencil_zc(fine.g);
+void k_prolong(cudaStream_t s, const Level<T> &coarse, const Level<T> &fine, int zcap) {
+    const int zc = stencil_zc(fine.g, zcap);
     prolong_kernel<T><<<stencil_grid_zc(fine.g, zc), dim3(SX, SY), 0, s>>>(coarse, fine, zc);
 }
 
@@ -571,9 +571,9 @@ void k_residual_plain(cudaStream_t s, const Level<double> &L, const double *phi,
     template void k_residual64<T>(cudaStream_t, const Level<double> &, const double *, const double *, T *,      \
                                   const SolveState *, double *, int);                                            \
     template void k_update<T>(cudaStream_t, const DGeom &, double *, const T *, const SolveState *);            \
-    template void k_rbgs<T>(cudaStream_t, const Level<T> &, int, int);                                           \
-    template void k_resid_restrict<T>(cudaStream_t, const Level<T> &, const Level<T> &);                       \
-    template void k_prolong<T>(cudaStream_t, const Level<T> &, const Level<T> &);                              \
+    template void k_rbgs<T>(cudaStream_t, const Level<T> &, int, int, int);                                      \
+    template void k_resid_restrict<T>(cudaStream_t, const Level<T> &, const Level<T> &, int);                  \
+    template void k_prolong<T>(cudaStream_t, const Level<T> &, const Level<T> &, int);                         \
     template void k_bottom<T>(cudaStream_t, const Level<T> &, T *, int, int);                                   \
     template void k_apply<T>(cudaStream_t, const Level<T> &, const T *, T *);                                   \
     template void k_cast<T>(cudaStream_t, long long, const double *, T *);                                       \

@@ -55,7 +55,7 @@ struct NodalPlan {
     // CUDA graph of the refinement loop, keyed by what it was captured with
     cudaGraphExec_t graph = nullptr;
     const void *graph_phi = nullptr;
-    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_tilez = -1;
     long long last_use = 0;
 };
 
@@ -568,24 +568,24 @@ __global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y, i
 // z-chunk of a column launch with bxy blocks per chunk: NCZ nodes per thread
 // on large levels, fewer (down to 1) until there are >= 8 blocks per SM, so
 // small levels are not latency-bound on a few long columns.
-static int nd_zchunk(long long bxy, int m2) {
-    int zc = NCZ;
+static int nd_zchunk(long long bxy, int m2, int cap) {
+    int zc = cap;
     while (zc > 1 && bxy * ((m2 + zc - 1) / zc) < 8 * 152) zc >>= 1;
     return zc;
 }
 
 template <typename T>
-static void k_nd_gs(cudaStream_t s, const NLevel<T> &L, int colour) {
+static void k_nd_gs(cudaStream_t s, const NLevel<T> &L, int colour, int zcap) {
     const int cx = colour & 1, cy = colour >> 1;
     const int ncx = (L.g.m[0] - cx + 1) / 2, ncy = (L.g.m[1] - cy + 1) / 2;
-    const int zc = nd_zchunk((long long)((ncx + 63) / 64) * ncy, L.g.m[2]);
+    const int zc = nd_zchunk((long long)((ncx + 63) / 64) * ncy, L.g.m[2], zcap);
     dim3 grid((ncx + 63) / 64, ncy, (L.g.m[2] + zc - 1) / zc);
     nd_col_kernel<T, 0><<<grid, 64, 0, s>>>(L, colour, ncx, ncy, zc);
 }
 
 template <typename T>
-static void k_nd_residual(cudaStream_t s, const NLevel<T> &L) {
-    const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2]);
+static void k_nd_residual(cudaStream_t s, const NLevel<T> &L, int zcap) {
+    const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2], zcap);
     dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
     nd_col_kernel<T, 1><<<grid, 64, 0, s>>>(L, 0, L.g.m[0], L.g.m[1], zc);
 }
@@ -972,19 +972,20 @@ void destroy_nodal_plans(mx_ctx *c) {
 static int nblk(long long n) { return red_blocks(n); }
 
 template <typename T>
-static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int nu2, int bot_iters, mx_ctx *pc) {
+static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int nu2, int bot_iters, mx_ctx *pc,
+                      int zcap) {
     prof_begin(pc, s, MX_PH_UPDATE);
     cudaMemsetAsync(L[0].e, 0, sizeof(T) * L[0].g.M, s);
     prof_end(pc, s, MX_PH_UPDATE, 1);
     for (int l = 0; l < nl - 1; l++) {
         if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
         for (int q = 0; q < nu1; q++)
-            for (int col = 0; col < 4; col++) k_nd_gs(s, L[l], col);
+            for (int col = 0; col < 4; col++) k_nd_gs(s, L[l], col, zcap);
         if (l == 0) {
             prof_end(pc, s, MX_PH_SMOOTH_FINE, 4 * nu1);
             prof_begin(pc, s, MX_PH_RESTRICT_FINE);
         }
-        k_nd_residual(s, L[l]);
+        k_nd_residual(s, L[l], zcap);
         nd_restrict_kernel<T><<<nblk(L[l + 1].g.M), 256, 0, s>>>(L[l], L[l + 1]);
         if (l == 0) {
             prof_end(pc, s, MX_PH_RESTRICT_FINE, 2);
@@ -1005,7 +1006,7 @@ static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int
             prof_begin(pc, s, MX_PH_SMOOTH_FINE);
         }
         for (int q = 0; q < nu2; q++)
-            for (int col = 3; col >= 0; col--) k_nd_gs(s, L[l], col);
+            for (int col = 3; col >= 0; col--) k_nd_gs(s, L[l], col, zcap);
         if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, 4 * nu2);
     }
 }
@@ -1036,9 +1037,12 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     mx_opts o;
     if (opts) o = *opts;
     else mx_default_opts(&o);
-    if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 ||
-        o.bottom_iters < 1 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED))
+    if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 ||
+        o.bottom_iters < 1 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
+        !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16))
         return set_err(c, MX_ERR_ARG, "invalid options");
+    tune_apply(c, MX_OP_NODAL, geom, o);
+    if (o.nu1 < 1 || o.nu2 < 1) return set_err(c, MX_ERR_ARG, "nodal: nu1 and nu2 must be >= 1 (or both 0)");
     if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     const NGeom g = make_ngeom(make_dgeom(geom));
     NodalPlan *P = get_nodal_plan(c, g, o.prec, &st);
@@ -1081,6 +1085,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.M, s));
     }
     prof_end(c, s, MX_PH_SETUP, 0);
+    const int zcap = o.tile_z ? o.tile_z : NCZ;
     // refinement loop: residual, then while not converged {V-cycle, update, residual}
     auto residual = [&](cudaStream_t ss, mx_ctx *pc) {
         prof_begin(pc, ss, MX_PH_RESID64);
@@ -1092,12 +1097,12 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     };
     auto step = [&](cudaStream_t ss, mx_ctx *pc) {
         if (mixed) {
-            nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc);
+            nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc, zcap);
             prof_begin(pc, ss, MX_PH_UPDATE);
             nd_df_update_kernel<<<nb, 256, 0, ss>>>(P->D, g.M, P->L32[0].e, c->state);
             prof_end(pc, ss, MX_PH_UPDATE, 1);
         } else {
-            nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc);
+            nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc, zcap);
             prof_begin(pc, ss, MX_PH_UPDATE);
             nd_update64_kernel<<<nb, 256, 0, ss>>>(phi, P->L64[0].e, c->state, g.M);
             prof_end(pc, ss, MX_PH_UPDATE, 1);
@@ -1111,7 +1116,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     if (!c->hstate->done) {
         if (o.use_graph && !c->prof) {
             if (!P->graph || P->graph_phi != phi || P->graph_nu1 != o.nu1 || P->graph_nu2 != o.nu2 ||
-                P->graph_bot != o.bottom_iters) {
+                P->graph_bot != o.bottom_iters || P->graph_tilez != o.tile_z) {
                 if (P->graph) {
                     cudaGraphExecDestroy(P->graph);
                     P->graph = nullptr;
@@ -1121,6 +1126,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
                 P->graph_nu1 = o.nu1;
                 P->graph_nu2 = o.nu2;
                 P->graph_bot = o.bottom_iters;
+                P->graph_tilez = o.tile_z;
             }
             MX_CUDA(c, cudaGraphLaunch(P->graph, s));
         } else {

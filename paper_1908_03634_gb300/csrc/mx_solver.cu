@@ -186,7 +186,8 @@ int coarse_start(const Hier<T> &H) {
 }
 
 template <typename T>
-void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc, int fused) {
+void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *pc, int fused,
+            int zcap) {
     const int nl = H.nlev;
     const int lc = coarse_start(H);
     const int ldown = lc < nl ? lc : nl - 1;  // levels with their own kernels
@@ -210,8 +211,8 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
             // the first red pass starts from e = 0 without reading e
             if (nu1 == 0) cudaMemsetAsync(L.e, 0, sizeof(T) * L.g.N, s);
             for (int q = 0; q < nu1; q++) {
-                k_rbgs(s, L, 0, q == 0);
-                k_rbgs(s, L, 1);
+                k_rbgs(s, L, 0, q == 0, zcap);
+                k_rbgs(s, L, 1, 0, zcap);
             }
             cur[l] = L.e;
         }
@@ -221,7 +222,7 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
         }
         Level<T> Lc = L;
         Lc.e = cur[l];
-        k_resid_restrict(s, Lc, H.lev[l + 1]);
+        k_resid_restrict(s, Lc, H.lev[l + 1], zcap);
         if (l == 0) {
             prof_end(pc, s, MX_PH_RESTRICT_FINE, 1);
             prof_begin(pc, s, MX_PH_COARSE);  // everything below the finest level
@@ -247,18 +248,18 @@ void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int sin
                 out = (out == (float *)L.e) ? (float *)L.e2 : (float *)L.e;
             }
         } else {
-            k_prolong(s, H.lev[l + 1], L);
+            k_prolong(s, H.lev[l + 1], L, zcap);
             for (int q = 0; q < nu2; q++) {
-                k_rbgs(s, L, 0);
-                k_rbgs(s, L, 1);
+                k_rbgs(s, L, 0, 0, zcap);
+                k_rbgs(s, L, 1, 0, zcap);
             }
         }
         if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, is_fused(0) ? nu2 : 1 + 2 * nu2);
     }
 }
 template int coarse_start<float>(const Hier<float> &);
-template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *, int);
-template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *, int);
+template void vcycle<float>(cudaStream_t, Hier<float> &, int, int, int, int, mx_ctx *, int, int);
+template void vcycle<double>(cudaStream_t, Hier<double> &, int, int, int, int, mx_ctx *, int, int);
 
 template <typename T>
 static void build_hierarchy(cudaStream_t s, Hier<T> &H) {
@@ -269,7 +270,7 @@ static void build_hierarchy(cudaStream_t s, Hier<T> &H) {
 // Mixed precision: FP32 V-cycle, double-float update and residual.
 static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const mx_opts &o, int singular, int nb,
                     mx_ctx *pc) {
-    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused);
+    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused, o.tile_z ? o.tile_z : 8);
     prof_begin(pc, s, MX_PH_RESID64);  // update phi += scale e fused with the next residual
     k_df_resid(s, H.lev[0], P.D, H.lev[0].e, c->state, c->partials);
     k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
@@ -278,7 +279,7 @@ static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const
 // Plain FP64: FP64 V-cycle, FP64 update and residual.
 static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, const mx_opts &o, int singular, int nb,
                     mx_ctx *pc, double *phi) {
-    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc);
+    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, 0, o.tile_z ? o.tile_z : 8);
     prof_begin(pc, s, MX_PH_UPDATE);
     k_update<double>(s, P.g, phi, H.lev[0].e, c->state);
     prof_end(pc, s, MX_PH_UPDATE, 1);
@@ -359,7 +360,7 @@ template <typename T>
 static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular, int nb) {
     cudaStream_t s = c->stream;
     if (!P.graph || P.graph_phi != phi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 || P.graph_bot != o.bottom_iters ||
-        P.graph_fused != o.fused) {
+        P.graph_fused != o.fused || P.graph_tilez != o.tile_z) {
         if (P.graph) {
             cudaGraphExecDestroy(P.graph);
             P.graph = nullptr;
@@ -372,6 +373,7 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
         P.graph_nu2 = o.nu2;
         P.graph_bot = o.bottom_iters;
         P.graph_fused = o.fused;
+        P.graph_tilez = o.tile_z;
     }
     // the while node runs its body while the condition is 1 (the host checked
     // that the first residual asked for a V-cycle)
@@ -410,12 +412,9 @@ mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
     if (in) o = *in;
     else mx_default_opts(&o);
     if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.max_vcycles < 0 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
-        o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.bottom_iters < 1 || o.bottom_iters > 100000)
+        o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.bottom_iters < 1 || o.bottom_iters > 100000 ||
+        !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16))
         return set_err(c, MX_ERR_ARG, "invalid options");
-    if (o.nu1 == 0 && o.nu2 == 0) {
-        o.nu1 = 2;
-        o.nu2 = 2;
-    }
     return MX_OK;
 }
 
@@ -439,6 +438,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     if (!ux || !uy || !uz || !rho || !beta0 || !sbar || !phi) return set_err(c, MX_ERR_ARG, "mac_project: null array");
     mx_opts o;
     if ((st = check_opts(c, opts, o))) return st;
+    tune_apply(c, MX_OP_MAC, geom, o);
     if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     const DGeom g = make_dgeom(geom);
     const int singular = geom_singular(g);

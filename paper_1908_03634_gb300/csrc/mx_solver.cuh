@@ -28,7 +28,7 @@ struct MacPlan {
     // CUDA graph of the refinement loop, keyed by the pointers it was captured with
     cudaGraphExec_t graph = nullptr;
     const void *graph_phi = nullptr;
-    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_fused = -1;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_fused = -1, graph_tilez = -1;
     long long last_use = 0;
 };
 
@@ -49,4 +49,4 @@ mx_status capture_while_graph(mx_ctx *c, cudaGraphExec_t *exec, const std::funct
 
 template <typename T>
 void vcycle(cudaStream_t s, Hier<T> &H, int nu1, int nu2, int bot_iters, int singular, mx_ctx *prof = nullptr,
-            int fused = 0);
+            int fused = 0, int zcap = 8);

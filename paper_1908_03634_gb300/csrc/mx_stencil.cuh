@@ -147,19 +147,20 @@ constexpr int SX = 32, SY = 8, ZC = 8;
 inline dim3 stencil_grid(const DGeom &g) {
     return dim3((g.n[0] + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + ZC - 1) / ZC);
 }
-// z-chunk for a level with bxy blocks per chunk of planes: 8 planes per
-// thread on large levels, fewer (down to 1) until the grid has >= 4 blocks per
-// SM, so small levels are not latency-bound on a few long-running blocks.
-inline int zchunk(long long bxy, int nz) {
-    int zc = ZC;
+// z-chunk for a level with bxy blocks per chunk of planes: `cap` planes per
+// thread (8 unless tuned) on large levels, fewer (down to 1) until the grid
+// has >= 4 blocks per SM, so small levels are not latency-bound on a few
+// long-running blocks.
+inline int zchunk(long long bxy, int nz, int cap = ZC) {
+    int zc = cap;
     while (zc > 1 && bxy * ((nz + zc - 1) / zc) < 4 * 152) zc >>= 1;
     return zc;
 }
 inline dim3 stencil_grid_zc(const DGeom &g, int zc) {
     return dim3((g.n[0] + SX - 1) / SX, (g.n[1] + SY - 1) / SY, (g.n[2] + zc - 1) / zc);
 }
-inline int stencil_zc(const DGeom &g) {
-    return zchunk((long long)((g.n[0] + SX - 1) / SX) * ((g.n[1] + SY - 1) / SY), g.n[2]);
+inline int stencil_zc(const DGeom &g, int cap = ZC) {
+    return zchunk((long long)((g.n[0] + SX - 1) / SX) * ((g.n[1] + SY - 1) / SY), g.n[2], cap);
 }
 inline int stencil_blocks(const DGeom &g) {
     dim3 d = stencil_grid(g);
