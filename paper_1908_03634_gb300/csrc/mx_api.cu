@@ -52,6 +52,11 @@ mx_status check_geom(mx_ctx *ctx, const mx_geom *g, bool nodal) {
     }
     if (!(g->dx > 0.0) || !std::isfinite(g->dx)) return set_err(ctx, MX_ERR_ARG, "dx must be positive");
     if (N >= (1LL << 31)) return set_err(ctx, MX_ERR_ARG, "grid too large (>= 2^31 cells)");
+    if (nodal) {
+        long long M = 1;
+        for (int a = 0; a < 3; a++) M *= g->n[a] + (g->lo[a] == MX_BC_PERIODIC ? 0 : 1);
+        if (M >= (1LL << 31)) return set_err(ctx, MX_ERR_ARG, "grid too large (>= 2^31 nodes)");
+    }
     return MX_OK;
 }
 

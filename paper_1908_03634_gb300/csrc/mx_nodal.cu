@@ -120,10 +120,11 @@ __device__ __forceinline__ float node_w(const NGeom &g, int a, int b, int c) {
     return w;
 }
 __device__ __forceinline__ void node_of(const NGeom &g, long long q, int &a, int &b, int &c) {
-    a = int(q % g.m[0]);
-    const long long r = q / g.m[0];
-    b = int(r % g.m[1]);
-    c = int(r / g.m[1]);
+    const int qi = int(q);  // node counts are < 2^31 (checked on entry)
+    a = qi % g.m[0];
+    const int r = qi / g.m[0];
+    b = r % g.m[1];
+    c = r / g.m[1];
 }
 
 // sigma of the 8 cells around node (a,b,c): s[iz][iy][ix], index 0 = cell a-1, 1 = cell a
@@ -172,7 +173,7 @@ __device__ __forceinline__ void for_couplings(const NGeom &g, int a, int b, int 
 __global__ void nd_sigma_kernel(long long N, const double *__restrict__ rho, const double *__restrict__ beta0,
                                 double *__restrict__ s64, float *__restrict__ s32, float *__restrict__ sl) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
-        const double v = beta0[q] / rho[q];
+        const double v = beta0[q] * rcp64(rho[q]);
         if (s64) s64[q] = v;
         if (s32) {
             const float hi = __double2float_rn(v);
@@ -194,40 +195,88 @@ __global__ void nd_coarsen_sigma_kernel(NLevel<T> F, NLevel<T> C) {
 
 // ---- RHS f = D(beta0 U) - Sbar_n, with weighted sums for the mean -----------------------
 
-__global__ void nd_rhs_kernel(NGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
-                              const double *__restrict__ uz, const double *__restrict__ beta0,
-                              const double *__restrict__ sbar, double *__restrict__ f, double *part, int sub_mean,
-                              const SolveState *st) {
-    double mx = 0.0, s1 = 0.0, s0 = 0.0;  // max|f|, sum w f, sum w
-    const double cm = sub_mean ? st->mean : 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
-        int a, b, c;
-        node_of(g, q, a, b, c);
-        double div = 0.0, sb = 0.0;
-        int cnt = 0;
-        for (int e = 0; e < 8; e++) {
-            const int dx = e & 1, dy = (e >> 1) & 1, dz = (e >> 2) & 1;  // 1: cell on the + side
-            const int i = cell_wrap(g, 0, a - 1 + dx), j = cell_wrap(g, 1, b - 1 + dy), k = cell_wrap(g, 2, c - 1 + dz);
-            if (i < 0 || j < 0 || k < 0) continue;
-            const long long cc = cidx(g, i, j, k);
-            const double bt = beta0[cc];
-            div += (dx ? 1.0 : -1.0) * bt * ux[cc] + (dy ? 1.0 : -1.0) * bt * uy[cc] + (dz ? 1.0 : -1.0) * bt * uz[cc];
-            sb += bt * sbar[cc];
-            cnt++;
+// Node columns (a, b) walk up c: the divergence at node (a,b,c) sums over the
+// (up to) 8 touching cells, which form the cell layers k = c-1 and k = c.  Each
+// layer's 4 cells are reduced once into
+//   x = sum_j (beta0 U_x)(a, j) - (beta0 U_x)(a-1, j)   (cells on the +x side minus -x side)
+//   y = sum_i (beta0 U_y)(i, b) - (beta0 U_y)(i, b-1)
+//   z = sum   (beta0 U_z),  s = sum beta0 Sbar,  n = number of cells
+// and node c combines layers c-1 and c: (D_n U) = (x + x' + y + y' + z' - z)/(4 h w),
+// Sbar_n = (s + s')/n, with w = n/8 (the node weight) a power of two.
+constexpr int NRZ = 16;  // nodes per thread along z in the node-column kernels
+
+struct RhsLayer {
+    double x, y, z, s;
+    int n;
+};
+
+__device__ __forceinline__ RhsLayer rhs_layer(const NGeom &g, const double *__restrict__ ux,
+                                              const double *__restrict__ uy, const double *__restrict__ uz,
+                                              const double *__restrict__ beta0, const double *__restrict__ sbar,
+                                              int i0, int i1, int j0, int j1, int k) {
+    RhsLayer L = {0.0, 0.0, 0.0, 0.0, 0};
+    const int kk = cell_wrap(g, 2, k);
+    if (kk < 0) return L;
+    for (int jj = 0; jj < 2; jj++) {
+        const int j = jj ? j1 : j0;
+        if (j < 0) continue;
+        for (int ii = 0; ii < 2; ii++) {
+            const int i = ii ? i1 : i0;
+            if (i < 0) continue;
+            const int c = i + g.n[0] * (j + g.n[1] * kk);
+            const double bt = beta0[c];
+            const double px = bt * ux[c], py = bt * uy[c];
+            L.x += ii ? px : -px;
+            L.y += jj ? py : -py;
+            L.z = fma(bt, uz[c], L.z);
+            L.s = fma(bt, sbar[c], L.s);
+            L.n++;
         }
-        const double w = cnt / 8.0;
-        const double v = div / (4.0 * g.h * w) - sb / cnt - cm;
-        if (f) f[q] = v;
-        mx = fmax(mx, fabs(v));
-        s1 += w * v;
-        s0 += w;
+    }
+    return L;
+}
+
+// f = D_n(beta0 U) - Sbar_n - cm (cm = the weighted mean when sub_mean), with
+// per-block partials (max |f|, sum w f, sum w); f may be null (divergence check)
+__global__ void nd_rhs_col_kernel(NGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                                  const double *__restrict__ uz, const double *__restrict__ beta0,
+                                  const double *__restrict__ sbar, double *__restrict__ f, double *part, int sub_mean,
+                                  const SolveState *st, double i4h) {
+    double mx = 0.0, s1 = 0.0, s0 = 0.0;
+    const int a = blockIdx.x * 32 + threadIdx.x, b = blockIdx.y * 8 + threadIdx.y;
+    const int c0 = blockIdx.z * NRZ, c1 = min(c0 + NRZ, g.m[2]);
+    if (a < g.m[0] && b < g.m[1]) {
+        const double cm = sub_mean ? st->mean : 0.0;
+        const int i0 = cell_wrap(g, 0, a - 1), i1 = cell_wrap(g, 0, a);
+        const int j0 = cell_wrap(g, 1, b - 1), j1 = cell_wrap(g, 1, b);
+        RhsLayer lo = rhs_layer(g, ux, uy, uz, beta0, sbar, i0, i1, j0, j1, c0 - 1);
+        for (int c = c0; c < c1; c++) {
+            const RhsLayer hi = rhs_layer(g, ux, uy, uz, beta0, sbar, i0, i1, j0, j1, c);
+            const int cnt = lo.n + hi.n;  // 1, 2, 4 or 8
+            const double ic = cnt == 8 ? 0.125 : cnt == 4 ? 0.25 : cnt == 2 ? 0.5 : 1.0;
+            const double div = ((lo.x + hi.x) + (lo.y + hi.y)) + (hi.z - lo.z);
+            const double v = div * (8.0 * i4h * ic) - (lo.s + hi.s) * ic - cm;
+            const double w = 0.125 * cnt;
+            if (f) f[a + g.m[0] * (b + g.m[1] * c)] = v;
+            mx = fmax(mx, fabs(v));
+            s1 = fma(w, v, s1);
+            s0 += w;
+            lo = hi;
+        }
     }
     block_red3(mx, s1, s0);
-    if (threadIdx.x == 0) {
-        part[3 * blockIdx.x] = mx;
-        part[3 * blockIdx.x + 1] = s1;
-        part[3 * blockIdx.x + 2] = s0;
+    if (flat_tid() == 0) {
+        double *p = part + 3 * flat_bid();
+        p[0] = mx;
+        p[1] = s1;
+        p[2] = s0;
     }
+}
+
+static dim3 nd_node_grid(const NGeom &g) { return dim3((g.m[0] + 31) / 32, (g.m[1] + 7) / 8, (g.m[2] + NRZ - 1) / NRZ); }
+static int nd_node_blocks(const NGeom &g) {
+    const dim3 d = nd_node_grid(g);
+    return int(d.x * d.y * d.z);
 }
 
 // stage 0: weighted mean; stage 1: norms of the final RHS + initial state
@@ -462,20 +511,29 @@ __global__ void __launch_bounds__(NBT) nd_bottom_kernel(NLevel<T> L, T *scr, int
 // column are never coupled (edge neighbours), so a column can be updated in
 // place while it is walked.
 
+// In-plane offsets of a node column's 3 x 3 node neighbourhood and 2 x 2 cell
+// neighbourhood (-1: beyond a wall), computed once per column so each plane of
+// the march costs one plane base plus the loads.
 struct ColMap {
-    int na[3], nb[3];  // node x / y indices of a-1, a, a+1 (-1: beyond a wall)
-    int ca[2], cb[2];  // cell x / y indices a-1, a (-1: beyond a wall)
+    int no[3][3];  // node (a-1+x, b-1+y): offset within a node plane
+    int co[2][2];  // cell (a-1+x, b-1+y): offset within a cell plane
 };
 
 __device__ __forceinline__ ColMap col_map(const NGeom &g, int a, int b) {
     ColMap m;
-    for (int o = 0; o < 3; o++) {
-        m.na[o] = node_wrap(g, 0, a - 1 + o);
-        m.nb[o] = node_wrap(g, 1, b - 1 + o);
+    for (int y = 0; y < 3; y++) {
+        const int nb = node_wrap(g, 1, b - 1 + y);
+        for (int x = 0; x < 3; x++) {
+            const int na = node_wrap(g, 0, a - 1 + x);
+            m.no[y][x] = (na >= 0 && nb >= 0) ? na + g.m[0] * nb : -1;
+        }
     }
-    for (int o = 0; o < 2; o++) {
-        m.ca[o] = cell_wrap(g, 0, a - 1 + o);
-        m.cb[o] = cell_wrap(g, 1, b - 1 + o);
+    for (int y = 0; y < 2; y++) {
+        const int cb = cell_wrap(g, 1, b - 1 + y);
+        for (int x = 0; x < 2; x++) {
+            const int ca = cell_wrap(g, 0, a - 1 + x);
+            m.co[y][x] = (ca >= 0 && cb >= 0) ? ca + g.n[0] * cb : -1;
+        }
     }
     return m;
 }
@@ -483,17 +541,17 @@ __device__ __forceinline__ ColMap col_map(const NGeom &g, int a, int b) {
 template <typename T>
 __device__ __forceinline__ void load_node_plane(const NGeom &g, const ColMap &m, const T *e, int c, T p[3][3]) {
     const int cz = node_wrap(g, 2, c);
+    const T *pl = e + (cz >= 0 ? cz : 0) * (g.m[0] * g.m[1]);
     for (int y = 0; y < 3; y++)
-        for (int x = 0; x < 3; x++)
-            p[y][x] = (cz >= 0 && m.na[x] >= 0 && m.nb[y] >= 0) ? e[nidx(g, m.na[x], m.nb[y], cz)] : T(0);
+        for (int x = 0; x < 3; x++) p[y][x] = (cz >= 0 && m.no[y][x] >= 0) ? pl[m.no[y][x]] : T(0);
 }
 
 template <typename T>
 __device__ __forceinline__ void load_cell_plane(const NGeom &g, const ColMap &m, const T *sig, int k, T s[2][2]) {
     const int kz = cell_wrap(g, 2, k);
+    const T *pl = sig + (kz >= 0 ? kz : 0) * (g.n[0] * g.n[1]);
     for (int y = 0; y < 2; y++)
-        for (int x = 0; x < 2; x++)
-            s[y][x] = (kz >= 0 && m.ca[x] >= 0 && m.cb[y] >= 0) ? sig[cidx(g, m.ca[x], m.cb[y], kz)] : T(0);
+        for (int x = 0; x < 2; x++) s[y][x] = (kz >= 0 && m.co[y][x] >= 0) ? pl[m.co[y][x]] : T(0);
 }
 
 // sum_m c_m e_m and sum_m c_m for node (.., .., c) from the planes below (pm),
@@ -640,10 +698,11 @@ __device__ __forceinline__ void df_add2(float ah, float al, float bh, float bl, 
 __device__ __forceinline__ void load_df_plane(const NGeom &g, const ColMap &m, const float *hi, const float *lo, int c,
                                               float ph[3][3], float pl[3][3]) {
     const int cz = node_wrap(g, 2, c);
+    const int base = (cz >= 0 ? cz : 0) * (g.m[0] * g.m[1]);
     for (int y = 0; y < 3; y++)
         for (int x = 0; x < 3; x++) {
-            const bool ok = cz >= 0 && m.na[x] >= 0 && m.nb[y] >= 0;
-            const long long q = ok ? nidx(g, m.na[x], m.nb[y], cz) : 0;
+            const bool ok = cz >= 0 && m.no[y][x] >= 0;
+            const int q = base + (ok ? m.no[y][x] : 0);
             ph[y][x] = ok ? hi[q] : 0.f;
             pl[y][x] = ok ? lo[q] : 0.f;
         }
@@ -651,10 +710,11 @@ __device__ __forceinline__ void load_df_plane(const NGeom &g, const ColMap &m, c
 __device__ __forceinline__ void load_df_cells(const NGeom &g, const ColMap &m, const float *hi, const float *lo, int k,
                                               float sh[2][2], float sl[2][2]) {
     const int kz = cell_wrap(g, 2, k);
+    const int base = (kz >= 0 ? kz : 0) * (g.n[0] * g.n[1]);
     for (int y = 0; y < 2; y++)
         for (int x = 0; x < 2; x++) {
-            const bool ok = kz >= 0 && m.ca[x] >= 0 && m.cb[y] >= 0;
-            const long long q = ok ? cidx(g, m.ca[x], m.cb[y], kz) : 0;
+            const bool ok = kz >= 0 && m.co[y][x] >= 0;
+            const int q = base + (ok ? m.co[y][x] : 0);
             sh[y][x] = ok ? hi[q] : 0.f;
             sl[y][x] = ok ? lo[q] : 0.f;
         }
@@ -859,26 +919,40 @@ __global__ void nd_wmean_finalize_kernel(const double *part, int nb, double *dst
 }
 
 // U -= G phi / rho at cell centres
+// U -= G_c phi / rho per cell: (G_c phi)_d = (1/(4h)) sum of the 4 d-edges of
+// the cell.  Cell columns walk up k and reuse the top face's nodes as the next
+// cell's bottom face.
 __global__ void nd_correct_kernel(NGeom g, const double *__restrict__ rho, const double *__restrict__ phi,
-                                  double *__restrict__ ux, double *__restrict__ uy, double *__restrict__ uz) {
-    const double i4h = 1.0 / (4.0 * g.h);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
-        const int i = int(q % g.n[0]), j = int((q / g.n[0]) % g.n[1]), k = int(q / ((long long)g.n[0] * g.n[1]));
-        double p[8];
-        for (int e = 0; e < 8; e++) {
-            int a = i + (e & 1), b = j + ((e >> 1) & 1), c = k + ((e >> 2) & 1);
-            if (g.per[0] && a == g.m[0]) a = 0;
-            if (g.per[1] && b == g.m[1]) b = 0;
-            if (g.per[2] && c == g.m[2]) c = 0;
-            p[e] = phi[nidx(g, a, b, c)];
-        }
-        const double gx = ((p[1] - p[0]) + (p[3] - p[2]) + (p[5] - p[4]) + (p[7] - p[6])) * i4h;
-        const double gy = ((p[2] - p[0]) + (p[3] - p[1]) + (p[6] - p[4]) + (p[7] - p[5])) * i4h;
-        const double gz = ((p[4] - p[0]) + (p[5] - p[1]) + (p[6] - p[2]) + (p[7] - p[3])) * i4h;
-        const double ir = 1.0 / rho[q];
-        ux[q] -= gx * ir;
-        uy[q] -= gy * ir;
-        uz[q] -= gz * ir;
+                                  double *__restrict__ ux, double *__restrict__ uy, double *__restrict__ uz,
+                                  double i4h) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int k0 = blockIdx.z * NRZ, k1 = min(k0 + NRZ, g.n[2]);
+    if (i >= g.n[0] || j >= g.n[1]) return;
+    const int a1 = (g.per[0] && i + 1 == g.m[0]) ? 0 : i + 1;
+    const int b1 = (g.per[1] && j + 1 == g.m[1]) ? 0 : j + 1;
+    const int m01 = g.m[0] * g.m[1];
+    const int o00 = i + g.m[0] * j, o10 = a1 + g.m[0] * j, o01 = i + g.m[0] * b1, o11 = a1 + g.m[0] * b1;
+    auto face = [&](int c, double p[4]) {
+        const int cc = (g.per[2] && c == g.m[2]) ? 0 : c;
+        const double *q = phi + (long long)m01 * cc;
+        p[0] = q[o00];
+        p[1] = q[o10];
+        p[2] = q[o01];
+        p[3] = q[o11];
+    };
+    double lo[4], hi[4];
+    face(k0, lo);
+    for (int k = k0; k < k1; k++) {
+        face(k + 1, hi);
+        const double gx = ((lo[1] - lo[0]) + (lo[3] - lo[2]) + (hi[1] - hi[0]) + (hi[3] - hi[2])) * i4h;
+        const double gy = ((lo[2] - lo[0]) + (lo[3] - lo[1]) + (hi[2] - hi[0]) + (hi[3] - hi[1])) * i4h;
+        const double gz = ((hi[0] - lo[0]) + (hi[1] - lo[1]) + (hi[2] - lo[2]) + (hi[3] - lo[3])) * i4h;
+        const int c = i + g.n[0] * (j + g.n[1] * k);
+        const double ir = rcp64(rho[c]);
+        ux[c] -= gx * ir;
+        uy[c] -= gy * ir;
+        uz[c] -= gz * ir;
+        for (int e = 0; e < 4; e++) lo[e] = hi[e];
     }
 }
 
@@ -1057,8 +1131,9 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     MX_CUDA(c, cudaMemcpyAsync(c->state, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     prof_begin(c, s, MX_PH_SETUP);
     if ((st = nodal_setup(c, *P, rho, beta0))) return st;
-    nd_rhs_kernel<<<nb, 256, 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0, c->state);
-    nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nb, c->state, o.remove_mean, 0);
+    nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0,
+                                                             c->state, 0.25 / g.h);
+    nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nd_node_blocks(g), c->state, o.remove_mean, 0);
     if (!o.remove_mean) {
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         MX_CUDA(c, cudaStreamSynchronize(s));
@@ -1144,10 +1219,12 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     nd_wsum_kernel<<<nb, 256, 0, s>>>(g, phi, c->partials);
     nd_wmean_finalize_kernel<<<1, 1024, 0, s>>>(c->partials, nb, &c->state->aux);
     k_sub_scalar(s, g.M, phi, &c->state->aux);
-    nd_correct_kernel<<<nblk(g.N), 256, 0, s>>>(g, rho, phi, ux, uy, uz);
+    nd_correct_kernel<<<dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + NRZ - 1) / NRZ), dim3(32, 8), 0, s>>>(
+        g, rho, phi, ux, uy, uz, 0.25 / g.h);
     // divergence of the projected velocity minus Sbar_n minus c: nd_rhs with the mean subtracted
-    nd_rhs_kernel<<<nb, 256, 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials, 1, c->state);
-    k_finalize_max(s, c->partials, nb, &c->state->div_err);
+    nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials, 1,
+                                                             c->state, 0.25 / g.h);
+    k_finalize_max(s, c->partials, nd_node_blocks(g), &c->state->div_err);
     prof_end(c, s, MX_PH_FINISH, 7);
     MX_CUDA(c, cudaEventRecord(c->ev1, s));
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
