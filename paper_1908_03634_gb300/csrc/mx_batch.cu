@@ -361,7 +361,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
             k_finalize_sum(s, c->partials, nbr, &sb->aux, 1.0 / double(gb.N));
             k_sub_scalar(s, gb.N, phi[b], &sb->aux);
         }
-        k_mac_correct(s, gb, rho[b], phi[b], ux[b], uy[b], uz[b]);
+        k_mac_correct(s, gb, P.Q, phi[b], ux[b], uy[b], uz[b]);
         k_mac_divcheck(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], sb, c->partials, nb);
         k_finalize_max(s, c->partials, nb, &sb->div_err);
     }

@@ -29,53 +29,80 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
     lo = __double2float_rn(x - double(hi));
 }
 
-// ---- coefficients: FP64 face values, stored as hi (the FP32 level-0 array) + lo
-__device__ __forceinline__ double face_b(const double *beta0, const double *rho, long long cl, long long cr) {
-    return (beta0[cl] + beta0[cr]) * rcp64(rho[cl] + rho[cr]);
-}
-
-__global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, const double *__restrict__ rho,
-                                     const double *__restrict__ beta0) {
+// ---- coefficients: FP64 face values, stored as hi (the FP32 level-0 array) + lo,
+// and (q non-null) the correction factors q = 2/(h (rho_L + rho_R)) ------------
+__global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, FaceQ Q, const double *__restrict__ rho,
+                                     const double *__restrict__ beta0, double ih2x) {
     const DGeom &g = L.g;
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     if (i >= g.n[0] || j >= g.n[1]) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int k1 = min(k0 + ZC, nz);
+    const bool wq = Q.x != nullptr;
     for (int k = k0; k < k1; k++) {
         const long long c = i + (long long)nx * (j + (long long)ny * k);
-        auto own = [&]() { return 2.0 * (beta0[c] * rcp64(rho[c])); };  // a Dirichlet face's coefficient
-        double bx, by, bz;
-        if (i > 0) bx = face_b(beta0, rho, c - 1, c);
-        else if (gper(g, 0)) bx = face_b(beta0, rho, c + nx - 1, c);
-        else bx = g.lo[0] == MX_BC_DIRICHLET ? own() : 0.0;
-        if (j > 0) by = face_b(beta0, rho, c - nx, c);
-        else if (gper(g, 1)) by = face_b(beta0, rho, c + (long long)(ny - 1) * nx, c);
-        else by = g.lo[1] == MX_BC_DIRICHLET ? own() : 0.0;
-        if (k > 0) bz = face_b(beta0, rho, c - g.nxy, c);
-        else if (gper(g, 2)) bz = face_b(beta0, rho, c + (long long)(nz - 1) * g.nxy, c);
-        else bz = g.lo[2] == MX_BC_DIRICHLET ? own() : 0.0;
+        // face (cl, c): b = (beta0_L + beta0_R) / (rho_L + rho_R), q = 2/(h (rho_L + rho_R))
+        auto face = [&](long long cl, double &b, double &q) {
+            const double r = rcp64(rho[cl] + rho[c]);
+            b = (beta0[cl] + beta0[c]) * r;
+            q = ih2x * r;
+        };
+        // a Dirichlet face of cell c: b = 2 beta0/rho, q = 2/(h rho)
+        auto own = [&](int bc, double &b, double &q) {
+            if (bc == MX_BC_DIRICHLET) {
+                const double r = rcp64(rho[c]);
+                b = 2.0 * (beta0[c] * r);
+                q = ih2x * r;
+            } else {
+                b = 0.0;
+                q = 0.0;
+            }
+        };
+        double bx, by, bz, qx, qy, qz;
+        if (i > 0) face(c - 1, bx, qx);
+        else if (gper(g, 0)) face(c + nx - 1, bx, qx);
+        else own(g.lo[0], bx, qx);
+        if (j > 0) face(c - nx, by, qy);
+        else if (gper(g, 1)) face(c + (long long)(ny - 1) * nx, by, qy);
+        else own(g.lo[1], by, qy);
+        if (k > 0) face(c - g.nxy, bz, qz);
+        else if (gper(g, 2)) face(c + (long long)(nz - 1) * g.nxy, bz, qz);
+        else own(g.lo[2], bz, qz);
         split_double(bx, L.bx[c], D.bxl[c]);
         split_double(by, L.by[c], D.byl[c]);
         split_double(bz, L.bz[c], D.bzl[c]);
+        if (wq) {
+            Q.x[c] = qx;
+            Q.y[c] = qy;
+            Q.z[c] = qz;
+        }
+        double bh, qh;
         if (i == nx - 1 && L.hx) {
             const long long q = j + (long long)ny * k;
-            split_double(g.hi[0] == MX_BC_DIRICHLET ? own() : 0.0, L.hx[q], D.hxl[q]);
+            own(g.hi[0], bh, qh);
+            split_double(bh, L.hx[q], D.hxl[q]);
+            if (wq) Q.hx[q] = qh;
         }
         if (j == ny - 1 && L.hy) {
             const long long q = i + (long long)nx * k;
-            split_double(g.hi[1] == MX_BC_DIRICHLET ? own() : 0.0, L.hy[q], D.hyl[q]);
+            own(g.hi[1], bh, qh);
+            split_double(bh, L.hy[q], D.hyl[q]);
+            if (wq) Q.hy[q] = qh;
         }
         if (k == nz - 1 && L.hz) {
             const long long q = i + (long long)nx * j;
-            split_double(g.hi[2] == MX_BC_DIRICHLET ? own() : 0.0, L.hz[q], D.hzl[q]);
+            own(g.hi[2], bh, qh);
+            split_double(bh, L.hz[q], D.hzl[q]);
+            if (wq) Q.hz[q] = qh;
         }
     }
 }
 
 void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho,
-                     const double *beta0) {
-    mac_coeffs_df_kernel<<<stencil_grid(L0.g), dim3(SX, SY), 0, s>>>(L0, D, rho, beta0);
+                     const double *beta0, const FaceQ *q) {
+    mac_coeffs_df_kernel<<<stencil_grid(L0.g), dim3(SX, SY), 0, s>>>(L0, D, q ? *q : FaceQ{}, rho, beta0,
+                                                                       2.0 / L0.g.h);
 }
 
 // ---- RHS: f <- f - mean, stored as h^2 f in double-float; norms of f ------------

@@ -13,7 +13,8 @@ struct DFArrays {
     float *ph2, *pl2;        // phi, buffer 1 (the buffers alternate with the V-cycle count)
 };
 
-void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho, const double *beta0);
+void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho, const double *beta0,
+                     const FaceQ *q = nullptr);
 void k_sub_mean_split(cudaStream_t s, const DGeom &g, const double *f, const SolveState *st, const DFArrays &D,
                       double *partials, int nb);
 void k_df_from_double(cudaStream_t s, long long n, const double *x, const DFArrays &D);

@@ -131,13 +131,20 @@ int red_blocks(long long n);
 // MAC (FP64) pieces
 void k_fill(cudaStream_t s, const DGeom &g, int spherical, const double *prof, int nr, double dr,
             double cx, double cy, double cz, double *out);
-void k_mac_coeffs64(cudaStream_t s, const Level<double> &L, const double *rho, const double *beta0);
+// Correction factors q_f = 2/(h (rho_L + rho_R)) of the MAC faces (a Dirichlet
+// face: 2/(h rho) of the interior cell), in the coefficients' lo-face layout
+// with the high-boundary planes; written by the coefficient kernels.
+struct FaceQ {
+    double *x = nullptr, *y = nullptr, *z = nullptr, *hx = nullptr, *hy = nullptr, *hz = nullptr;
+};
+void k_mac_coeffs64(cudaStream_t s, const Level<double> &L, const double *rho, const double *beta0,
+                    const FaceQ *q = nullptr);
 void k_mac_rhs(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
                const double *beta0, const double *sbar, double *f, double *partials, int nb);
 void k_sub_mean_norm(cudaStream_t s, const DGeom &g, double *f, const SolveState *st, double *partials, int nb);
 void k_finalize_rhs(cudaStream_t s, const double *partials, int nb, SolveState *st, long long N, int remove_mean,
                     int stage);
-void k_mac_correct(cudaStream_t s, const DGeom &g, const double *rho, const double *phi, double *ux, double *uy,
+void k_mac_correct(cudaStream_t s, const DGeom &g, const FaceQ &q, const double *phi, double *ux, double *uy,
                    double *uz);
 void k_mac_divcheck(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
                     const double *beta0, const double *sbar, const SolveState *st, double *partials, int nb);

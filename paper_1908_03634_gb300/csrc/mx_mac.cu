@@ -41,99 +41,122 @@ void k_fill(cudaStream_t s, const DGeom &g, int spherical, const double *prof, i
 // ------------------------------------------------------------------------------
 // Face coefficients b_f = beta0_f / rho_f (arithmetic face averages), stored in
 // lo-face form; wall faces 0, Dirichlet faces 2 beta0/rho of the interior cell.
-__global__ void mac_coeffs_kernel(Level<double> L, const double *__restrict__ rho, const double *__restrict__ beta0) {
+// With Q: the correction factors q_f = 2/(h (rho_L + rho_R)) (Dirichlet 2/(h rho)).
+__global__ void mac_coeffs_kernel(Level<double> L, FaceQ Q, const double *__restrict__ rho,
+                                  const double *__restrict__ beta0, double ih2x) {
     const DGeom &g = L.g;
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     if (i >= g.n[0] || j >= g.n[1]) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int k1 = min(k0 + ZC, nz);
+    const bool wq = Q.x != nullptr;
     for (int k = k0; k < k1; k++) {
         const long long c = i + (long long)nx * (j + (long long)ny * k);
         const double bc = beta0[c], rc = rho[c];
-        auto own = [&]() { return 2.0 * (bc * rcp64(rc)); };  // a Dirichlet face's coefficient
+        auto face = [&](long long cl, double *b, double *q) {
+            const double r = rcp64(rho[cl] + rc);
+            *b = (beta0[cl] + bc) * r;
+            if (wq) *q = ih2x * r;
+        };
+        auto own = [&](int bcnd, double *b, double *q) {
+            if (bcnd == MX_BC_DIRICHLET) {
+                const double r = rcp64(rc);
+                *b = 2.0 * (bc * r);
+                if (wq) *q = ih2x * r;
+            } else {
+                *b = 0.0;
+                if (wq) *q = 0.0;
+            }
+        };
         // x
-        if (i > 0) L.bx[c] = (beta0[c - 1] + bc) * rcp64(rho[c - 1] + rc);
-        else if (gper(g, 0)) L.bx[c] = (beta0[c + nx - 1] + bc) * rcp64(rho[c + nx - 1] + rc);
-        else L.bx[c] = g.lo[0] == MX_BC_DIRICHLET ? own() : 0.0;
+        if (i > 0) face(c - 1, L.bx + c, Q.x + c);
+        else if (gper(g, 0)) face(c + nx - 1, L.bx + c, Q.x + c);
+        else own(g.lo[0], L.bx + c, Q.x + c);
         // y
-        if (j > 0) L.by[c] = (beta0[c - nx] + bc) * rcp64(rho[c - nx] + rc);
-        else if (gper(g, 1)) {
-            const long long o = c + (long long)(ny - 1) * nx;
-            L.by[c] = (beta0[o] + bc) * rcp64(rho[o] + rc);
-        } else L.by[c] = g.lo[1] == MX_BC_DIRICHLET ? own() : 0.0;
+        if (j > 0) face(c - nx, L.by + c, Q.y + c);
+        else if (gper(g, 1)) face(c + (long long)(ny - 1) * nx, L.by + c, Q.y + c);
+        else own(g.lo[1], L.by + c, Q.y + c);
         // z
-        if (k > 0) L.bz[c] = (beta0[c - g.nxy] + bc) * rcp64(rho[c - g.nxy] + rc);
-        else if (gper(g, 2)) {
-            const long long o = c + (long long)(nz - 1) * g.nxy;
-            L.bz[c] = (beta0[o] + bc) * rcp64(rho[o] + rc);
-        } else L.bz[c] = g.lo[2] == MX_BC_DIRICHLET ? own() : 0.0;
+        if (k > 0) face(c - g.nxy, L.bz + c, Q.z + c);
+        else if (gper(g, 2)) face(c + (long long)(nz - 1) * g.nxy, L.bz + c, Q.z + c);
+        else own(g.lo[2], L.bz + c, Q.z + c);
         // high boundary planes
-        if (i == nx - 1 && L.hx) L.hx[j + (long long)ny * k] = g.hi[0] == MX_BC_DIRICHLET ? own() : 0.0;
-        if (j == ny - 1 && L.hy) L.hy[i + (long long)nx * k] = g.hi[1] == MX_BC_DIRICHLET ? own() : 0.0;
-        if (k == nz - 1 && L.hz) L.hz[i + (long long)nx * j] = g.hi[2] == MX_BC_DIRICHLET ? own() : 0.0;
+        if (i == nx - 1 && L.hx) {
+            const long long q = j + (long long)ny * k;
+            own(g.hi[0], L.hx + q, Q.hx + q);
+        }
+        if (j == ny - 1 && L.hy) {
+            const long long q = i + (long long)nx * k;
+            own(g.hi[1], L.hy + q, Q.hy + q);
+        }
+        if (k == nz - 1 && L.hz) {
+            const long long q = i + (long long)nx * j;
+            own(g.hi[2], L.hz + q, Q.hz + q);
+        }
     }
 }
 
-void k_mac_coeffs64(cudaStream_t s, const Level<double> &L, const double *rho, const double *beta0) {
-    mac_coeffs_kernel<<<stencil_grid(L.g), dim3(SX, SY), 0, s>>>(L, rho, beta0);
+void k_mac_coeffs64(cudaStream_t s, const Level<double> &L, const double *rho, const double *beta0, const FaceQ *q) {
+    mac_coeffs_kernel<<<stencil_grid(L.g), dim3(SX, SY), 0, s>>>(L, q ? *q : FaceQ{}, rho, beta0, 2.0 / L.g.h);
 }
 
 // ------------------------------------------------------------------------------
-// D(beta0 U) at cell (i,j,k) from API-layout face velocities.
-
-__device__ __forceinline__ double face_beta_u(const DGeom &g, const double *__restrict__ beta0, int d, int p,
-                                              long long c_lo, long long c_hi, double u) {
-    // face p along d joins cells c_lo (p-1, possibly wrapped) and c_hi (p)
+// D(beta0 U) - beta0 Sbar along a cell column, from API-layout face velocities.
+// Face flux times 2: (beta0_L + beta0_R) U_f inside and across periodic faces,
+// 2 beta0 U_f of the interior cell on a Dirichlet face, 0 on a wall; the factor
+// 1/2 and 1/h are applied once per cell.  The column walks up k and carries each
+// cell's high z-face flux over as the next cell's low one.
+__device__ __forceinline__ double face_flux2(const DGeom &g, const double *__restrict__ beta0, int d, int p,
+                                             long long c_lo, long long c_hi, double u) {
     const int n = g.n[d];
-    if (p > 0 && p < n) return 0.5 * (beta0[c_lo] + beta0[c_hi]) * u;
+    if ((p > 0 && p < n) || gper(g, d)) return (beta0[c_lo] + beta0[c_hi]) * u;
     const int bc = p == 0 ? g.lo[d] : g.hi[d];
-    if (bc == MX_BC_PERIODIC) return 0.5 * (beta0[c_lo] + beta0[c_hi]) * u;
-    if (bc == MX_BC_DIRICHLET) return beta0[p == 0 ? c_hi : c_lo] * u;
+    if (bc == MX_BC_DIRICHLET) return (2.0 * beta0[p == 0 ? c_hi : c_lo]) * u;
     return 0.0;  // wall: U_n taken as 0
 }
 
-__device__ __forceinline__ double div_beta_u(const DGeom &g, const double *__restrict__ beta0,
-                                             const double *__restrict__ ux, const double *__restrict__ uy,
-                                             const double *__restrict__ uz, int i, int j, int k, long long c,
-                                             double ih) {
+template <typename F>
+__device__ __forceinline__ void div_column(const DGeom &g, const double *__restrict__ ux,
+                                           const double *__restrict__ uy, const double *__restrict__ uz,
+                                           const double *__restrict__ beta0, const double *__restrict__ sbar, int i,
+                                           int j, int k0, int k1, double hih, F fn) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    // x faces i and i+1 in the (nx+1)-wide layout
-    const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
-    const long long cw = i > 0 ? c - 1 : c + nx - 1;   // wrapped neighbour (used only if periodic)
-    const long long ce = i + 1 < nx ? c + 1 : c - (nx - 1);
-    const double fxl = face_beta_u(g, beta0, 0, i, cw, c, ux[fx]);
-    const double fxh = face_beta_u(g, beta0, 0, i + 1, c, ce, ux[fx + 1]);
-    const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
-    const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
-    const long long cn = j + 1 < ny ? c + nx : c - (long long)(ny - 1) * nx;
-    const double fyl = face_beta_u(g, beta0, 1, j, cs, c, uy[fy]);
-    const double fyh = face_beta_u(g, beta0, 1, j + 1, c, cn, uy[fy + nx]);
-    const long long fz = c;  // z faces: i + nx*(j + ny*k), k in [0, nz]
-    const long long cb = k > 0 ? c - g.nxy : c + (long long)(nz - 1) * g.nxy;
-    const long long ct = k + 1 < nz ? c + g.nxy : c - (long long)(nz - 1) * g.nxy;
-    const double fzl = face_beta_u(g, beta0, 2, k, cb, c, uz[fz]);
-    const double fzh = face_beta_u(g, beta0, 2, k + 1, c, ct, uz[fz + g.nxy]);
-    return (fxh - fxl) * ih + (fyh - fyl) * ih + (fzh - fzl) * ih;
+    const long long nxy = g.nxy;
+    long long c = i + (long long)nx * (j + (long long)ny * k0);
+    double fzl = face_flux2(g, beta0, 2, k0, k0 > 0 ? c - nxy : c + (long long)(nz - 1) * nxy, c, uz[c]);
+    for (int k = k0; k < k1; k++, c += nxy) {
+        // x faces i and i+1 in the (nx+1)-wide layout
+        const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
+        const long long cw = i > 0 ? c - 1 : c + nx - 1;  // wrapped neighbours (used only if periodic)
+        const long long ce = i + 1 < nx ? c + 1 : c - (nx - 1);
+        const double fxl = face_flux2(g, beta0, 0, i, cw, c, ux[fx]);
+        const double fxh = face_flux2(g, beta0, 0, i + 1, c, ce, ux[fx + 1]);
+        const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
+        const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
+        const long long cn = j + 1 < ny ? c + nx : c - (long long)(ny - 1) * nx;
+        const double fyl = face_flux2(g, beta0, 1, j, cs, c, uy[fy]);
+        const double fyh = face_flux2(g, beta0, 1, j + 1, c, cn, uy[fy + nx]);
+        const long long ct = k + 1 < nz ? c + nxy : c - (long long)(nz - 1) * nxy;
+        const double fzh = face_flux2(g, beta0, 2, k + 1, c, ct, uz[c + nxy]);  // z faces: c + nxy*k', k' <= nz
+        fn(c, fma(((fxh - fxl) + (fyh - fyl)) + (fzh - fzl), hih, -beta0[c] * sbar[c]));
+        fzl = fzh;
+    }
 }
 
 __global__ void mac_rhs_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
                                const double *__restrict__ uz, const double *__restrict__ beta0,
-                               const double *__restrict__ sbar, double *__restrict__ f, double *part, double ih) {
+                               const double *__restrict__ sbar, double *__restrict__ f, double *part, double hih) {
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     double mx = 0.0, s2 = 0.0, s1 = 0.0;
-    if (i < g.n[0] && j < g.n[1]) {
-        const int k1 = min(k0 + ZC, g.n[2]);
-        for (int k = k0; k < k1; k++) {
-            const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
-            const double v = div_beta_u(g, beta0, ux, uy, uz, i, j, k, c, ih) - beta0[c] * sbar[c];
+    if (i < g.n[0] && j < g.n[1])
+        div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, double v) {
             f[c] = v;
             mx = fmax(mx, fabs(v));
-            s2 += v * v;
+            s2 = fma(v, v, s2);
             s1 += v;
-        }
-    }
+        });
     block_red3(mx, s2, s1);
     if (flat_tid() == 0) {
         double *p = part + 3 * flat_bid();
@@ -146,7 +169,7 @@ __global__ void mac_rhs_kernel(DGeom g, const double *__restrict__ ux, const dou
 void k_mac_rhs(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
                const double *beta0, const double *sbar, double *f, double *partials, int nb) {
     (void)nb;
-    mac_rhs_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, f, partials, 1.0 / g.h);
+    mac_rhs_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, f, partials, 0.5 / g.h);
 }
 
 // stage 0: the RHS mean (if removed); stage 1: norms of the final RHS and the
@@ -202,31 +225,28 @@ void k_sub_mean_norm(cudaStream_t s, const DGeom &g, double *f, const SolveState
 }
 
 // ------------------------------------------------------------------------------
-// Correction U_f -= (dphi/dn)_f / rho_f on the API face layout.  One thread per
-// cell updates the cell's three low faces and, on the last cell of a row, the
-// high boundary face.  The face gradient is (phi_R - phi_L)/h inside and across
-// periodic faces (faces 0 and n then both get the same value), one-sided with
-// phi = 0 across a Dirichlet face; wall faces are set to 0.
+// Correction U_f -= (dphi/dn)_f / rho_f on the API face layout, with the face
+// factors q_f = 2/(h (rho_L + rho_R)) of the coefficient setup: inside and
+// across periodic faces U_f -= q_f (phi_R - phi_L) (faces 0 and n of a periodic
+// axis get the same value); across a Dirichlet face (phi = 0 outside, distance
+// h/2) U_f -= +-q_f phi_c; wall faces are set to 0.  One thread per cell
+// updates the cell's three low faces and, on the last cell of a row, the high
+// boundary face.
 __device__ __forceinline__ void correct_face(const DGeom &g, int d, int p, long long cl, long long cr, long long ci,
-                                             const double *__restrict__ rho, const double *__restrict__ phi,
-                                             double *__restrict__ u, long long f, double ih) {
+                                             const double *__restrict__ phi, double q, double *__restrict__ u,
+                                             long long f) {
     const int n = g.n[d];
     if ((p > 0 && p < n) || gper(g, d)) {
-        const double rf = 0.5 * (rho[cl] + rho[cr]);
-        u[f] -= ((phi[cr] - phi[cl]) * ih) * rcp64(rf);
+        u[f] = fma(-q, phi[cr] - phi[cl], u[f]);
     } else {
         const int bc = p == 0 ? g.lo[d] : g.hi[d];
-        if (bc == MX_BC_DIRICHLET) {
-            const double grad = p == 0 ? (phi[ci] - 0.0) * (2.0 * ih) : (0.0 - phi[ci]) * (2.0 * ih);
-            u[f] -= grad * rcp64(rho[ci]);
-        } else {
-            u[f] = 0.0;
-        }
+        if (bc == MX_BC_DIRICHLET) u[f] = fma(p == 0 ? -q : q, phi[ci], u[f]);
+        else u[f] = 0.0;
     }
 }
 
-__global__ void mac_correct_kernel(DGeom g, const double *__restrict__ rho, const double *__restrict__ phi,
-                                   double *__restrict__ ux, double *__restrict__ uy, double *__restrict__ uz, double ih) {
+__global__ void mac_correct_kernel(DGeom g, FaceQ Q, const double *__restrict__ phi, double *__restrict__ ux,
+                                   double *__restrict__ uy, double *__restrict__ uz) {
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     if (i >= g.n[0] || j >= g.n[1]) return;
@@ -236,38 +256,39 @@ __global__ void mac_correct_kernel(DGeom g, const double *__restrict__ rho, cons
         const long long c = i + (long long)nx * (j + (long long)ny * k);
         // x faces i (and nx on the last cell)
         const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
-        correct_face(g, 0, i, i > 0 ? c - 1 : c + nx - 1, c, c, rho, phi, ux, fx, ih);
-        if (i == nx - 1) correct_face(g, 0, nx, c, c - (nx - 1), c, rho, phi, ux, fx + 1, ih);
+        correct_face(g, 0, i, i > 0 ? c - 1 : c + nx - 1, c, c, phi, Q.x[c], ux, fx);
+        if (i == nx - 1)
+            correct_face(g, 0, nx, c, c - (nx - 1), c, phi, gper(g, 0) ? Q.x[c - (nx - 1)] : Q.hx[j + (long long)ny * k],
+                         ux, fx + 1);
         const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
-        correct_face(g, 1, j, j > 0 ? c - nx : c + (long long)(ny - 1) * nx, c, c, rho, phi, uy, fy, ih);
-        if (j == ny - 1) correct_face(g, 1, ny, c, c - (long long)(ny - 1) * nx, c, rho, phi, uy, fy + nx, ih);
-        correct_face(g, 2, k, k > 0 ? c - g.nxy : c + (long long)(nz - 1) * g.nxy, c, c, rho, phi, uz, c, ih);
-        if (k == nz - 1) correct_face(g, 2, nz, c, c - (long long)(nz - 1) * g.nxy, c, rho, phi, uz, c + g.nxy, ih);
+        correct_face(g, 1, j, j > 0 ? c - nx : c + (long long)(ny - 1) * nx, c, c, phi, Q.y[c], uy, fy);
+        if (j == ny - 1)
+            correct_face(g, 1, ny, c, c - (long long)(ny - 1) * nx, c, phi,
+                         gper(g, 1) ? Q.y[c - (long long)(ny - 1) * nx] : Q.hy[i + (long long)nx * k], uy, fy + nx);
+        correct_face(g, 2, k, k > 0 ? c - g.nxy : c + (long long)(nz - 1) * g.nxy, c, c, phi, Q.z[c], uz, c);
+        if (k == nz - 1)
+            correct_face(g, 2, nz, c, c - (long long)(nz - 1) * g.nxy, c, phi,
+                         gper(g, 2) ? Q.z[c - (long long)(nz - 1) * g.nxy] : Q.hz[i + (long long)nx * j], uz,
+                         c + g.nxy);
     }
 }
 
-void k_mac_correct(cudaStream_t s, const DGeom &g, const double *rho, const double *phi, double *ux, double *uy,
+void k_mac_correct(cudaStream_t s, const DGeom &g, const FaceQ &q, const double *phi, double *ux, double *uy,
                    double *uz) {
-    mac_correct_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, rho, phi, ux, uy, uz, 1.0 / g.h);
+    mac_correct_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, q, phi, ux, uy, uz);
 }
 
 // max |D(beta0 U) - beta0 Sbar - c| of the projected velocity
 __global__ void mac_divcheck_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
                                     const double *__restrict__ uz, const double *__restrict__ beta0,
-                                    const double *__restrict__ sbar, const SolveState *st, double *part, double ih) {
+                                    const double *__restrict__ sbar, const SolveState *st, double *part, double hih) {
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     const double cm = st->mean;
     double mx = 0.0, s2 = 0.0, s1 = 0.0;
-    if (i < g.n[0] && j < g.n[1]) {
-        const int k1 = min(k0 + ZC, g.n[2]);
-        for (int k = k0; k < k1; k++) {
-            const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
-            const double v = div_beta_u(g, beta0, ux, uy, uz, i, j, k, c, ih) - beta0[c] * sbar[c] - cm;
-            mx = fmax(mx, fabs(v));
-            s2 += v * v;
-        }
-    }
+    if (i < g.n[0] && j < g.n[1])
+        div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
+                   [&](long long, double v) { mx = fmax(mx, fabs(v - cm)); });
     block_red3(mx, s2, s1);
     if (flat_tid() == 0) {
         double *p = part + 3 * flat_bid();
@@ -280,7 +301,7 @@ __global__ void mac_divcheck_kernel(DGeom g, const double *__restrict__ ux, cons
 void k_mac_divcheck(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
                     const double *beta0, const double *sbar, const SolveState *st, double *partials, int nb) {
     (void)nb;
-    mac_divcheck_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, st, partials, 1.0 / g.h);
+    mac_divcheck_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, st, partials, 0.5 / g.h);
 }
 
 __global__ void finalize_max_kernel(const double *part, int nb, double *dst) {

@@ -81,6 +81,12 @@ static void carve_plan(Bump &b, MacPlan &P) {
         l0.hx = P.L64.hx; l0.hy = P.L64.hy; l0.hz = P.L64.hz;
         P.H32.nlev = 0;
     }
+    P.Q.x = b.take<double>(g.N);
+    P.Q.y = b.take<double>(g.N);
+    P.Q.z = b.take<double>(g.N);
+    P.Q.hx = gper(g, 0) ? nullptr : b.take<double>((size_t)g.n[1] * g.n[2]);
+    P.Q.hy = gper(g, 1) ? nullptr : b.take<double>((size_t)g.n[0] * g.n[2]);
+    P.Q.hz = gper(g, 2) ? nullptr : b.take<double>((size_t)g.n[0] * g.n[1]);
     P.tmp64 = b.take<double>(g.N);
 }
 
@@ -421,10 +427,10 @@ mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
 void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0) {
     cudaStream_t s = c->stream;
     if (P.prec == MX_PREC_MIXED) {
-        k_mac_coeffs_df(s, P.H32.lev[0], P.D, rho, beta0);
+        k_mac_coeffs_df(s, P.H32.lev[0], P.D, rho, beta0, &P.Q);
         build_hierarchy(s, P.H32);
     } else {
-        k_mac_coeffs64(s, P.L64, rho, beta0);
+        k_mac_coeffs64(s, P.L64, rho, beta0, &P.Q);
         build_hierarchy(s, P.H64);
     }
 }
@@ -499,7 +505,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
         k_finalize_sum(s, c->partials, nbr, &c->state->aux, 1.0 / double(g.N));
         k_sub_scalar(s, g.N, phi, &c->state->aux);
     }
-    k_mac_correct(s, g, rho, phi, ux, uy, uz);
+    k_mac_correct(s, g, P->Q, phi, ux, uy, uz);
     k_mac_divcheck(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials, nb);
     k_finalize_max(s, c->partials, nb, &c->state->div_err);
     prof_end(c, s, MX_PH_FINISH, singular ? 8 : 5);
