@@ -166,6 +166,7 @@ def run_mx(args):
     from paper_1908_03634_gb300 import build as B
     B.build()
     import paper_1908_03634_gb300 as mx
+    from paper_1908_03634_gb300 import sharding as S
     from paper_1908_03634_gb300 import workloads as W
 
     K, Wm = args.steps, args.warmup
@@ -211,14 +212,10 @@ def run_mx(args):
     e1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    # replicas: every rank solved K problems; the job's time is the slowest rank's
+    value, ms_total = S.job_throughput(float(K), e0.elapsed_time(e1))
     last = infos[-1]
     assert all(i["status"] == 0 for i in infos), infos[-1]
-    value = world * K / (ms_total / 1e3)
     vcycles = statistics.mean(i["vcycles"] for i in infos[Wm:])
     launches = int(round(K * launches_per_solve(g, tuned, vcycles, graph)))
 
@@ -320,18 +317,14 @@ def run_mx(args):
             e2e_step()
         q1.record(stream)
         barrier()
-        ems = q0.elapsed_time(q1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * ke / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e_value, _ = S.job_throughput(float(ke), q0.elapsed_time(q1))
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- the other workloads (nodal projection, batched patches) ----
     extras = {}
     if not args.no_extras:
         extras["nodal384"] = bench_nodal(mx, W, ctx, dev, stream, hbm=hbm)
-        extras["batched96"] = bench_batched(mx, W, ctx, dev, stream)
+        extras["batched96"] = bench_batched(mx, W, ctx, dev, stream, fp64=world == 1, rank=rank, world=world)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
@@ -422,11 +415,16 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     return out
 
 
-def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=True):
+def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=True, rank=0, world=1):
     """96 independent planar patches (sizes {32,48,64,96,128}^3) solved as one
-    batch (one launch per phase over all patches), vs looping single FP64 solves."""
+    batch (one launch per phase over all patches), vs looping single FP64 solves.
+    With several ranks each solves its shard of the patches (balanced by cells,
+    no collective) and the line reports the whole job: all patches / the
+    slowest rank's time."""
     import torch
-    ps = W.batched_patches(npatch, device=dev)
+    from paper_1908_03634_gb300 import sharding as S
+    mine = S.shard_patches([a * b * c for a, b, c in W.batched_sizes(npatch)], world)[rank]
+    ps = W.batched_patches(npatch, device=dev, only=mine)
     geoms = [p.geom for p in ps]
     cells = sum(g.ncell for g in geoms)
     b0 = []
@@ -443,11 +441,15 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
     opts = mx.default_opts()
     for i in range(warmup):
         run(sets[i], opts)
+    if world > 1:
+        torch.distributed.barrier()
     ms, infos = timed(lambda i: run(sets[warmup + i], opts), steps, stream)
     last = infos[-1]
+    _, ms = S.job_throughput(0.0, ms)  # the slowest rank's time
+    cells = int(S.sum_over_ranks(cells))
     ms_b = ms / steps
     out = {"workload": f"batched{npatch}", "patches": npatch, "cells": cells, "ms_per_batch": ms_b,
-           "patch_solves_per_s": npatch * 1e3 / ms_b, "cells_per_s": cells * 1e3 / ms_b,
+           "patch_solves_per_s": npatch * 1e3 / ms_b, "cells_per_s": cells * 1e3 / ms_b, "ranks": world,
            "vcycles_max": max(i["vcycles"] for i in last), "vcycles_mean": statistics.mean(i["vcycles"] for i in last),
            "rel_resid_max": max(i["rel_resid"] for i in last)}
     if fp64:
@@ -508,16 +510,26 @@ def run_reference(args):
 
 
 def run_other(args):
-    """--workload star512 | nodal-sweep (single GPU)."""
+    """--workload star512 | nodal-sweep | nodal384 (single GPU) | batched96
+    (patches sharded over the ranks under torchrun)."""
     import torch
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.workload != "batched96":
+        if rank != 0:
+            return
+        world = 1
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
     from paper_1908_03634_gb300 import build as B
     B.build()
     import paper_1908_03634_gb300 as mx
     from paper_1908_03634_gb300 import workloads as W
     stream = torch.cuda.current_stream()
-    ctx = mx.mx_create(0, stream)
+    ctx = mx.mx_create(local, stream)
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
@@ -528,8 +540,10 @@ def run_other(args):
                         fp64=not args.no_fp64, hbm=hbm, graph=not args.no_graph)
         print(json.dumps(r), flush=True)
     elif args.workload == "batched96":
-        r = bench_batched(mx, W, ctx, dev, stream, steps=args.steps, warmup=args.warmup, fp64=not args.no_fp64)
-        print(json.dumps(r), flush=True)
+        r = bench_batched(mx, W, ctx, dev, stream, steps=args.steps, warmup=args.warmup,
+                          fp64=not args.no_fp64 and world == 1, rank=rank, world=world)
+        if rank == 0:
+            print(json.dumps(r), flush=True)
     elif args.workload == "nodal-sweep":
         for n in (64, 128, 192, 256, 384, 512):
             r = bench_nodal(mx, W, ctx, dev, stream, n=n, steps=2, warmup=1, fp64=(n <= 256), hbm=hbm)

@@ -244,15 +244,28 @@ def nodal384(device="cpu", n=384):
 PATCH_SIZES = (32, 48, 64, 96, 128)
 
 
-def batched_patches(npatch=96, seed=3, device="cpu", sizes=PATCH_SIZES, nmodes=8):
-    """Independent planar patches: cube edge uniform from sizes, density contrast
-    log-uniform in [1e2, 1e5], each patch with its own seed stream."""
+def _batched_draws(npatch, seed, sizes):
     ss = np.random.SeedSequence(seed)
     top = np.random.default_rng(ss.spawn(1)[0])
     edges = top.choice(np.array(sizes), size=npatch)
     contrast = 10.0 ** top.uniform(2.0, 5.0, size=npatch)
+    return edges, contrast
+
+
+def batched_sizes(npatch=96, seed=3, sizes=PATCH_SIZES):
+    """The (nx, ny, nz) cell counts of batched_patches(npatch, seed, sizes),
+    without building the fields."""
+    edges, _ = _batched_draws(npatch, seed, sizes)
+    return [(int(e), int(e), int(e)) for e in edges]
+
+
+def batched_patches(npatch=96, seed=3, device="cpu", sizes=PATCH_SIZES, nmodes=8, only=None):
+    """Independent planar patches: cube edge uniform from sizes, density contrast
+    log-uniform in [1e2, 1e5], each patch with its own seed stream.  only: build
+    just these patch indices (a rank's shard), in order."""
+    edges, contrast = _batched_draws(npatch, seed, sizes)
     out = []
-    for p in range(npatch):
+    for p in (range(npatch) if only is None else only):
         H = 1.0 / math.log(contrast[p])
         out.append(planar(int(edges[p]), H, 0.6, nmodes, 1, (seed, p), device, f"patch{p}"))
     return out
