@@ -438,7 +438,10 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
     def run(us, o):
         return mx.mx_mac_project_batched(ctx, geoms, [u[0] for u in us], [u[1] for u in us], [u[2] for u in us],
                                          [p.rho for p in ps], b0, [p.sbar for p in ps], phis, o)[1]
-    opts = mx.default_opts()
+    # the batch's sweep counts from the library's autotuner (untimed), then nu1 = nu2 = 0
+    tuned, _ = mx.mx_autotune_batched(ctx, geoms, [p.u[0] for p in ps], [p.u[1] for p in ps], [p.u[2] for p in ps],
+                                      [p.rho for p in ps], b0, [p.sbar for p in ps])
+    opts = mx.default_opts(nu1=0, nu2=0)
     for i in range(warmup):
         run(sets[i], opts)
     if world > 1:
@@ -450,6 +453,7 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
     ms_b = ms / steps
     out = {"workload": f"batched{npatch}", "patches": npatch, "cells": cells, "ms_per_batch": ms_b,
            "patch_solves_per_s": npatch * 1e3 / ms_b, "cells_per_s": cells * 1e3 / ms_b, "ranks": world,
+           "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2},
            "vcycles_max": max(i["vcycles"] for i in last), "vcycles_mean": statistics.mean(i["vcycles"] for i in last),
            "rel_resid_max": max(i["rel_resid"] for i in last)}
     if fp64:
@@ -563,11 +567,13 @@ def run_other(args):
                 u[d].copy_(w.u[d])
             mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
             return mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
-        o = mx.default_opts()
+        mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
+        tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_MAC, g, *w.u, w.rho, beta0, w.sbar)
+        o = mx.default_opts(nu1=0, nu2=0)
         for i in range(Wm):
             step(i, o)
         ms, infos = timed(lambda i: step(i, o), K, stream)
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
+        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, nu1=tuned.nu1, nu2=tuned.nu2, tile_z=tuned.tile_z)
         step(0, o64)
         ms64, i64 = timed(lambda i: step(i, o64), 1, stream)
         print(json.dumps({"workload": "star512", "metric": "MAC projection solves/s to 1e-10 (full star 512^3, "
@@ -575,6 +581,8 @@ def run_other(args):
                           "vcycles": infos[-1]["vcycles"], "rel_resid": infos[-1]["rel_resid"],
                           "div_err_linf": infos[-1]["div_err_linf"],
                           "fp64": {"solves_per_s": 1e3 / ms64, "vcycles": i64[-1]["vcycles"]},
+                          "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z,
+                                    "fused": tuned.fused},
                           "note": "includes a 3-array restore of U per solve"}), flush=True)
     mx.mx_destroy(ctx)
 

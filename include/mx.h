@@ -230,6 +230,18 @@ mx_status mx_autotune(mx_ctx *ctx, int op, const mx_geom *geom, const double *ux
                       const double *uz, const double *rho, const double *beta0, const double *sbar,
                       const mx_opts *base, mx_opts *best, double *ms_best);
 
+/* Autotuner for a batch (mx_mac_project_batched arguments; mixed precision):
+ * times the whole batch under each candidate (nu1, nu2) of mx_autotune, one
+ * setting for every box, and stores the fastest converging one in the tune
+ * cache under the batch's box count and geometries; mx_mac_project_batched
+ * with nu1 = nu2 = 0 uses it.  The inputs are not modified (scratch copies of
+ * every box's U and phi are allocated and freed).  Same outputs and errors as
+ * mx_autotune. */
+mx_status mx_autotune_batched(mx_ctx *ctx, int nbox, const mx_geom *geoms, const double *const *ux,
+                              const double *const *uy, const double *const *uz, const double *const *rho,
+                              const double *const *beta0, const double *const *sbar, const mx_opts *base,
+                              mx_opts *best, double *ms_best);
+
 /* Look up the tune cache: 1 and *out = the stored setting (base fields from
  * *out as passed) if mx_autotune stored one for (op, prec, geometry), else 0. */
 int mx_tune_lookup(const mx_ctx *ctx, int op, int prec, const mx_geom *geom, mx_opts *out);

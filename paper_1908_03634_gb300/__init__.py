@@ -81,6 +81,9 @@ def load():
         "mx_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "mx_autotune": (C.c_int, [_VP, C.c_int, G, _DP, _DP, _DP, _DP, _DP, _DP, O, O, C.POINTER(C.c_double)]),
         "mx_tune_lookup": (C.c_int, [_VP, C.c_int, C.c_int, G, O]),
+        "mx_autotune_batched": (C.c_int, [_VP, C.c_int, G, C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP),
+                                          C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), O, O,
+                                          C.POINTER(C.c_double)]),
         "mx_mac_project_batched": (C.c_int, [_VP, C.c_int, G, C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP),
                                              C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), O, I]),
     }
@@ -97,7 +100,7 @@ def exported_symbols():
     return ["mx_create", "mx_destroy", "mx_set_stream", "mx_last_error", "mx_default_opts", "mx_device_supported",
             "mx_fill_base_state", "mx_mac_project", "mx_nodal_project", "mx_apply_op", "mx_residual",
             "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc",
-            "mx_autotune", "mx_tune_lookup"]
+            "mx_autotune", "mx_tune_lookup", "mx_autotune_batched"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -233,6 +236,27 @@ def mx_autotune(ctx, op, geom, ux, uy, uz, rho, beta0, sbar, base=None):
                             _ptr(uz, us[2], "uz"), _ptr(rho, cs, "rho"), _ptr(beta0, cs, "beta0"),
                             _ptr(sbar, cs, "sbar"), C.byref(base) if base is not None else None, C.byref(best),
                             C.byref(ms))
+    _check(ctx, st)
+    return best, ms.value
+
+
+def mx_autotune_batched(ctx, geoms, ux, uy, uz, rho, beta0, sbar, base=None):
+    """Tune (nu1, nu2) for a batch (lists of per-box tensors, left unmodified);
+    returns (chosen mx_opts, ms of the tuned batch); cached in ctx for batched
+    calls with nu1 = nu2 = 0 on the same boxes."""
+    n = len(geoms)
+    G = (mx_geom * n)(*[make_geom(g) for g in geoms])
+
+    def arr(ts, shapes, name):
+        return (_VP * n)(*[_ptr(t, s, name) for t, s in zip(ts, shapes)])
+
+    cs = [cell_shape(g) for g in geoms]
+    best = mx_opts()
+    ms = C.c_double(0.0)
+    st = load().mx_autotune_batched(
+        ctx, n, G, arr(ux, [face_shape(g, 0) for g in geoms], "ux"), arr(uy, [face_shape(g, 1) for g in geoms], "uy"),
+        arr(uz, [face_shape(g, 2) for g in geoms], "uz"), arr(rho, cs, "rho"), arr(beta0, cs, "beta0"),
+        arr(sbar, cs, "sbar"), C.byref(base) if base is not None else None, C.byref(best), C.byref(ms))
     _check(ctx, st)
     return best, ms.value
 

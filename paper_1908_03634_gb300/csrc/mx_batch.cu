@@ -267,7 +267,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
     mx_status st;
     mx_opts o;
     if ((st = check_opts(c, opts, o))) return st;
-    if (o.nu1 == 0 && o.nu2 == 0) o.nu1 = o.nu2 = 2;  // batches are not tuned: the default sweeps
+    tune_apply_batch(c, nbox, geoms, o);
     std::vector<DGeom> g(nbox);
     for (int b = 0; b < nbox; b++) {
         if ((st = check_geom(c, &geoms[b], false))) return st;

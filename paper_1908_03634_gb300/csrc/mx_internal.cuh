@@ -88,6 +88,8 @@ struct mx_ctx {
 // nu1 = nu2 = 0 in o: replace nu1, nu2, fused, tile_z by the tune cache's
 // entry for (op, o.prec, geometry), or nu1 = nu2 = 2 when there is none.
 void tune_apply(const mx_ctx *c, int op, const mx_geom *g, mx_opts &o);
+// the same for a batch (nu1, nu2 only), keyed by its boxes' geometries
+void tune_apply_batch(const mx_ctx *c, int nbox, const mx_geom *geoms, mx_opts &o);
 
 // phase markers: no-ops unless tracing is on and the stream is not capturing
 void prof_begin(mx_ctx *c, cudaStream_t s, int phase);

@@ -134,3 +134,37 @@ def test_invalid_tile_depth_rejected(mx, ctx, tz):
     with pytest.raises(mx.MXError) as e:
         mac_solve(mx, ctx, w, inputs, tile_z=tz)
     assert e.value.status == mx.MX_ERR_ARG
+
+
+def test_batched_autotune_choice_cached_and_reproduced(mx, ctx):
+    ws = W.batched_patches(6, seed=5, sizes=(32, 48))
+    arrs = []
+    for w in ws:
+        u, rho, beta0, sbar = mac_inputs(mx, ctx, w)
+        arrs.append((u, rho, beta0, sbar))
+    geoms = [w.geom for w in ws]
+    cols = lambda k: [a[k] for a in arrs]
+    us = cols(0)
+    before = [[t.clone() for t in u] for u in us]
+    best, ms = mx.mx_autotune_batched(ctx, geoms, [u[0] for u in us], [u[1] for u in us], [u[2] for u in us],
+                                      cols(1), cols(2), cols(3))
+    assert ms > 0 and (best.nu1, best.nu2) in NU
+    for a, b in zip(before, us):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+
+    def solve(**kw):
+        uu = [[t.clone() for t in u] for u in us]
+        phis = [torch.zeros(mx.cell_shape(g), dtype=torch.float64, device=DEV) for g in geoms]
+        st, infos = mx.mx_mac_project_batched(ctx, geoms, [u[0] for u in uu], [u[1] for u in uu],
+                                              [u[2] for u in uu], cols(1), cols(2), cols(3), phis,
+                                              mx.default_opts(**kw))
+        torch.cuda.synchronize()
+        return infos, [p.cpu().numpy() for p in phis]
+
+    auto = solve(nu1=0, nu2=0)
+    expl = solve(nu1=best.nu1, nu2=best.nu2)
+    assert all(i["status"] == 0 and i["rel_resid"] <= 1e-10 for i in auto[0])
+    assert [i["vcycles"] for i in auto[0]] == [i["vcycles"] for i in expl[0]]
+    for a, b in zip(auto[1], expl[1]):
+        assert np.array_equal(a, b)
