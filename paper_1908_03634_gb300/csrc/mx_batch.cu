@@ -310,7 +310,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
         const int nb = stencil_blocks(gb), nbr = red_blocks(gb.N);
         const int singular = geom_singular(gb);
         setup_coefficients(c, P, rho[b], beta0[b]);
-        k_mac_rhs(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], P.tmp64, c->partials, nb);
+        k_mac_rhs_df(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], P.D, c->partials);
         k_finalize_rhs(s, c->partials, nb, sb, gb.N, singular && o.remove_mean, 0);
         if (singular && !o.remove_mean) {
             MX_CUDA(c, cudaMemcpyAsync(B.h_st + b, sb, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -318,7 +318,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
             if (std::fabs(B.h_st[b].aux) > 1e-12 * B.h_st[b].fnorm)
                 return set_err(c, MX_ERR_INCOMPAT, "batched: a singular box has a right-hand side of non-zero mean");
         }
-        k_sub_mean_split(s, gb, P.tmp64, sb, P.D, c->partials, nbr);
+        k_sub_mean_scale(s, gb, sb, P.D, c->partials, nbr);
         k_finalize_rhs(s, c->partials, nbr, sb, gb.N, 0, 1);
         if (o.use_initial_guess) {
             k_df_from_double(s, gb.N, phi[b], P.D);
@@ -362,7 +362,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
             k_sub_scalar(s, gb.N, phi[b], &sb->aux);
         }
         k_mac_correct(s, gb, P.Q, phi[b], ux[b], uy[b], uz[b]);
-        k_mac_divcheck(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], sb, c->partials, nb);
+        k_mac_divcheck_df(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], sb, c->partials);
         k_finalize_max(s, c->partials, nb, &sb->div_err);
     }
     MX_CUDA(c, cudaEventRecord(c->ev1, s));

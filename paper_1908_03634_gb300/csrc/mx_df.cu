@@ -12,6 +12,7 @@
 // a few 2^-48 relative to the largest flux term, far below the 1e-10 relative
 // residual the loop converges to.
 #include "mx_df.cuh"
+#include "mx_dfmath.cuh"
 #include "mx_stencil.cuh"
 
 // ---- error-free transformations -------------------------------------------------
@@ -29,105 +30,227 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
     lo = __double2float_rn(x - double(hi));
 }
 
-// ---- coefficients: FP64 face values, stored as hi (the FP32 level-0 array) + lo,
-// and (q non-null) the correction factors q = 2/(h (rho_L + rho_R)) ------------
+// ---- coefficients b = (beta0_L + beta0_R)/(rho_L + rho_R) in double-float,
+// stored as hi (the FP32 level-0 array) + lo, and (q non-null) the correction
+// factors q = 2/(h (rho_L + rho_R)) as FP64.  rho and beta0 are split into
+// double-float once per cell (the column carries the cell below); a Dirichlet
+// face uses the interior cell: b = 2 beta0/rho, q = 2/(h rho). ----------------
 __global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, FaceQ Q, const double *__restrict__ rho,
-                                     const double *__restrict__ beta0, double ih2x) {
+                                     const double *__restrict__ beta0, dfloat ih2x) {
     const DGeom &g = L.g;
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     if (i >= g.n[0] || j >= g.n[1]) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long nxy = g.nxy;
     const int k1 = min(k0 + ZC, nz);
     const bool wq = Q.x != nullptr;
-    for (int k = k0; k < k1; k++) {
-        const long long c = i + (long long)nx * (j + (long long)ny * k);
-        // face (cl, c): b = (beta0_L + beta0_R) / (rho_L + rho_R), q = 2/(h (rho_L + rho_R))
-        auto face = [&](long long cl, double &b, double &q) {
-            const double r = rcp64(rho[cl] + rho[c]);
-            b = (beta0[cl] + beta0[c]) * r;
-            q = ih2x * r;
-        };
-        // a Dirichlet face of cell c: b = 2 beta0/rho, q = 2/(h rho)
-        auto own = [&](int bc, double &b, double &q) {
-            if (bc == MX_BC_DIRICHLET) {
-                const double r = rcp64(rho[c]);
-                b = 2.0 * (beta0[c] * r);
-                q = ih2x * r;
-            } else {
-                b = 0.0;
-                q = 0.0;
-            }
-        };
-        double bx, by, bz, qx, qy, qz;
-        if (i > 0) face(c - 1, bx, qx);
-        else if (gper(g, 0)) face(c + nx - 1, bx, qx);
-        else own(g.lo[0], bx, qx);
-        if (j > 0) face(c - nx, by, qy);
-        else if (gper(g, 1)) face(c + (long long)(ny - 1) * nx, by, qy);
-        else own(g.lo[1], by, qy);
-        if (k > 0) face(c - g.nxy, bz, qz);
-        else if (gper(g, 2)) face(c + (long long)(nz - 1) * g.nxy, bz, qz);
-        else own(g.lo[2], bz, qz);
-        split_double(bx, L.bx[c], D.bxl[c]);
-        split_double(by, L.by[c], D.byl[c]);
-        split_double(bz, L.bz[c], D.bzl[c]);
-        if (wq) {
-            Q.x[c] = qx;
-            Q.y[c] = qy;
-            Q.z[c] = qz;
+    auto store = [&](float *bh, float *bl, double *qd, long long o, dfloat b, dfloat q) {
+        bh[o] = b.h;
+        bl[o] = b.l;
+        if (wq) qd[o] = df_to_double(q);
+    };
+    auto face = [&](dfloat rl, dfloat bl, dfloat rr, dfloat br, dfloat &b, dfloat &q) {
+        const dfloat rs = df_add(rl, rr);
+        b = df_div(df_add(bl, br), rs);
+        q = df_div(ih2x, rs);
+    };
+    auto own = [&](int bc, dfloat r, dfloat be, dfloat &b, dfloat &q) {
+        if (bc == MX_BC_DIRICHLET) {
+            b = df_div(df_add(be, be), r);
+            q = df_div(ih2x, r);
+        } else {
+            b = dfloat{0.f, 0.f};
+            q = dfloat{0.f, 0.f};
         }
-        double bh, qh;
+    };
+    long long c = i + (long long)nx * (j + (long long)ny * k0);
+    // the cell below the first one (its wrap image when periodic)
+    dfloat rdn = {0.f, 0.f}, bdn = {0.f, 0.f};
+    if (k0 > 0 || gper(g, 2)) {
+        const long long cd = k0 > 0 ? c - nxy : c + (long long)(nz - 1) * nxy;
+        rdn = df_split(rho[cd]);
+        bdn = df_split(beta0[cd]);
+    }
+    for (int k = k0; k < k1; k++, c += nxy) {
+        const dfloat rc = df_split(rho[c]), bc = df_split(beta0[c]);
+        dfloat b, q;
+        if (i > 0 || gper(g, 0)) {
+            const long long cl = i > 0 ? c - 1 : c + nx - 1;
+            face(df_split(rho[cl]), df_split(beta0[cl]), rc, bc, b, q);
+        } else {
+            own(g.lo[0], rc, bc, b, q);
+        }
+        store(L.bx, D.bxl, Q.x, c, b, q);
+        if (j > 0 || gper(g, 1)) {
+            const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
+            face(df_split(rho[cs]), df_split(beta0[cs]), rc, bc, b, q);
+        } else {
+            own(g.lo[1], rc, bc, b, q);
+        }
+        store(L.by, D.byl, Q.y, c, b, q);
+        if (k > 0 || gper(g, 2)) face(rdn, bdn, rc, bc, b, q);
+        else own(g.lo[2], rc, bc, b, q);
+        store(L.bz, D.bzl, Q.z, c, b, q);
         if (i == nx - 1 && L.hx) {
-            const long long q = j + (long long)ny * k;
-            own(g.hi[0], bh, qh);
-            split_double(bh, L.hx[q], D.hxl[q]);
-            if (wq) Q.hx[q] = qh;
+            own(g.hi[0], rc, bc, b, q);
+            store(L.hx, D.hxl, Q.hx, j + (long long)ny * k, b, q);
         }
         if (j == ny - 1 && L.hy) {
-            const long long q = i + (long long)nx * k;
-            own(g.hi[1], bh, qh);
-            split_double(bh, L.hy[q], D.hyl[q]);
-            if (wq) Q.hy[q] = qh;
+            own(g.hi[1], rc, bc, b, q);
+            store(L.hy, D.hyl, Q.hy, i + (long long)nx * k, b, q);
         }
         if (k == nz - 1 && L.hz) {
-            const long long q = i + (long long)nx * j;
-            own(g.hi[2], bh, qh);
-            split_double(bh, L.hz[q], D.hzl[q]);
-            if (wq) Q.hz[q] = qh;
+            own(g.hi[2], rc, bc, b, q);
+            store(L.hz, D.hzl, Q.hz, i + (long long)nx * j, b, q);
         }
+        rdn = rc;
+        bdn = bc;
     }
 }
 
 void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho,
                      const double *beta0, const FaceQ *q) {
-    mac_coeffs_df_kernel<<<stencil_grid(L0.g), dim3(SX, SY), 0, s>>>(L0, D, q ? *q : FaceQ{}, rho, beta0,
-                                                                       2.0 / L0.g.h);
+    const double v = 2.0 / L0.g.h;
+    dfloat ih2x;
+    ih2x.h = float(v);
+    ih2x.l = float(v - double(ih2x.h));
+    mac_coeffs_df_kernel<<<stencil_grid(L0.g), dim3(SX, SY), 0, s>>>(L0, D, q ? *q : FaceQ{}, rho, beta0, ih2x);
 }
 
-// ---- RHS: f <- f - mean, stored as h^2 f in double-float; norms of f ------------
-__global__ void sub_mean_split_kernel(const double *__restrict__ f, long long n, const SolveState *st, double h2,
-                                      float *__restrict__ fh, float *__restrict__ fl, double *part) {
-    const double m = st->mean;
-    double mx = 0.0, s2 = 0.0, s1 = 0.0;
+// ---- RHS f = D(beta0 U) - beta0 Sbar in double-float ----------------------------
+// The FP64 inputs are split into double-float (integer bit operations), the
+// divergence is evaluated with double-float arithmetic on the FP32 pipe, and f
+// is stored as a double-float pair (fh, fl); no FP64 arithmetic per cell.
+// Face flux times 2: (beta0_L + beta0_R) U_f inside and across periodic faces,
+// (beta0_in + beta0_in) U_f on a Dirichlet face, 0 on a wall (operands are
+// selected, then one expression is evaluated); the factor 1/(2h) is applied
+// once per cell and the column carries the high z-face flux up.
+__device__ __forceinline__ dfloat df_face_flux2(const DGeom &g, const double *__restrict__ beta0, int d, int p,
+                                                long long c_lo, long long c_hi, double u) {
+    const int n = g.n[d];
+    const bool inner = (p > 0 && p < n) || gper(g, d);
+    const int bc = p == 0 ? g.lo[d] : g.hi[d];
+    const long long cin = p == 0 ? c_hi : c_lo;
+    const bool wall = !inner && bc != MX_BC_DIRICHLET;
+    const dfloat a = df_split(wall ? 0.0 : beta0[inner ? c_lo : cin]);
+    const dfloat b = df_split(wall ? 0.0 : beta0[inner ? c_hi : cin]);
+    return df_mul(df_add(a, b), df_split(u));
+}
+
+template <typename F>
+__device__ __forceinline__ void df_div_column(const DGeom &g, const double *__restrict__ ux,
+                                              const double *__restrict__ uy, const double *__restrict__ uz,
+                                              const double *__restrict__ beta0, const double *__restrict__ sbar,
+                                              int i, int j, int k0, int k1, dfloat hih, F fn) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long nxy = g.nxy;
+    long long c = i + (long long)nx * (j + (long long)ny * k0);
+    dfloat fzl = df_face_flux2(g, beta0, 2, k0, k0 > 0 ? c - nxy : c + (long long)(nz - 1) * nxy, c, uz[c]);
+    for (int k = k0; k < k1; k++, c += nxy) {
+        const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
+        const long long cw = i > 0 ? c - 1 : c + nx - 1;
+        const long long ce = i + 1 < nx ? c + 1 : c - (nx - 1);
+        const dfloat fxl = df_face_flux2(g, beta0, 0, i, cw, c, ux[fx]);
+        const dfloat fxh = df_face_flux2(g, beta0, 0, i + 1, c, ce, ux[fx + 1]);
+        const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
+        const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
+        const long long cn = j + 1 < ny ? c + nx : c - (long long)(ny - 1) * nx;
+        const dfloat fyl = df_face_flux2(g, beta0, 1, j, cs, c, uy[fy]);
+        const dfloat fyh = df_face_flux2(g, beta0, 1, j + 1, c, cn, uy[fy + nx]);
+        const long long ct = k + 1 < nz ? c + nxy : c - (long long)(nz - 1) * nxy;
+        const dfloat fzh = df_face_flux2(g, beta0, 2, k + 1, c, ct, uz[c + nxy]);
+        const dfloat div = df_add(df_add(df_sub(fxh, fxl), df_sub(fyh, fyl)), df_sub(fzh, fzl));
+        fn(c, df_sub(df_mul(div, hih), df_mul(df_split(beta0[c]), df_split(sbar[c]))));
+        fzl = fzh;
+    }
+}
+
+// per-block partials (max |x|, sum x^2, sum x) from per-thread float / double-float sums
+__device__ __forceinline__ void df_partials(float mx, float s2, dfloat s1, double *p) {
+    double a = mx, b = s2, c = df_to_double(s1);
+    block_red3(a, b, c);
+    if (flat_tid() == 0) {
+        p[0] = a;
+        p[1] = b;
+        p[2] = c;
+    }
+}
+
+__global__ void mac_rhs_df_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                                  const double *__restrict__ uz, const double *__restrict__ beta0,
+                                  const double *__restrict__ sbar, float *__restrict__ fh, float *__restrict__ fl,
+                                  double *part, dfloat hih) {
+    const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
+    const int k0 = blockIdx.z * ZC;
+    float mx = 0.f, s2 = 0.f;
+    dfloat s1 = {0.f, 0.f};
+    if (i < g.n[0] && j < g.n[1])
+        df_div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, dfloat v) {
+            fh[c] = v.h;
+            fl[c] = v.l;
+            mx = fmaxf(mx, fabsf(v.h));
+            s2 = fmaf(v.h, v.h, s2);
+            s1 = df_add(s1, v);
+        });
+    df_partials(mx, s2, s1, part + 3 * flat_bid());
+}
+
+// max |D(beta0 U) - beta0 Sbar - c| of the projected velocity
+__global__ void mac_divcheck_df_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                                       const double *__restrict__ uz, const double *__restrict__ beta0,
+                                       const double *__restrict__ sbar, const SolveState *st, double *part,
+                                       dfloat hih) {
+    const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
+    const int k0 = blockIdx.z * ZC;
+    const dfloat cm = df_split(st->mean);
+    float mx = 0.f;
+    if (i < g.n[0] && j < g.n[1])
+        df_div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
+                      [&](long long, dfloat v) { mx = fmaxf(mx, fabsf(df_sub(v, cm).h)); });
+    df_partials(mx, 0.f, dfloat{0.f, 0.f}, part + 3 * flat_bid());
+}
+
+static dfloat df_const(double v) {
+    dfloat r;
+    r.h = float(v);
+    r.l = float(v - double(r.h));
+    return r;
+}
+
+void k_mac_rhs_df(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
+                  const double *beta0, const double *sbar, const DFArrays &D, double *partials) {
+    mac_rhs_df_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, D.fh, D.fl, partials,
+                                                               df_const(0.5 / g.h));
+}
+
+void k_mac_divcheck_df(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
+                       const double *beta0, const double *sbar, const SolveState *st, double *partials) {
+    mac_divcheck_df_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, st, partials,
+                                                                    df_const(0.5 / g.h));
+}
+
+// ---- f <- f - mean, stored as h^2 f; norms of f - mean --------------------------------
+__global__ void sub_mean_scale_kernel(long long n, const SolveState *st, dfloat h2, float *__restrict__ fh,
+                                      float *__restrict__ fl, double *part) {
+    const dfloat m = df_split(st->mean);
+    float mx = 0.f, s2 = 0.f;
+    dfloat s1 = {0.f, 0.f};
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const double v = f[q] - m;
-        split_double(v * h2, fh[q], fl[q]);
-        mx = fmax(mx, fabs(v));
-        s2 += v * v;
-        s1 += v;
+        const dfloat v = df_sub(dfloat{fh[q], fl[q]}, m);
+        const dfloat w = df_mul(v, h2);
+        fh[q] = w.h;
+        fl[q] = w.l;
+        mx = fmaxf(mx, fabsf(v.h));
+        s2 = fmaf(v.h, v.h, s2);
+        s1 = df_add(s1, v);
     }
-    block_red3(mx, s2, s1);
-    if (threadIdx.x == 0) {
-        part[3 * blockIdx.x] = mx;
-        part[3 * blockIdx.x + 1] = s2;
-        part[3 * blockIdx.x + 2] = s1;
-    }
+    df_partials(mx, s2, s1, part + 3 * blockIdx.x);
 }
 
-void k_sub_mean_split(cudaStream_t s, const DGeom &g, const double *f, const SolveState *st, const DFArrays &D,
-                      double *partials, int nb) {
-    sub_mean_split_kernel<<<nb, RED_THREADS, 0, s>>>(f, g.N, st, g.h * g.h, D.fh, D.fl, partials);
+void k_sub_mean_scale(cudaStream_t s, const DGeom &g, const SolveState *st, const DFArrays &D, double *partials,
+                      int nb) {
+    sub_mean_scale_kernel<<<nb, RED_THREADS, 0, s>>>(g.N, st, df_const(g.h * g.h), D.fh, D.fl, partials);
 }
 
 // ---- phi conversions ----------------------------------------------------------------

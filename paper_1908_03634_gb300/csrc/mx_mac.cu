@@ -109,11 +109,18 @@ void k_mac_coeffs64(cudaStream_t s, const Level<double> &L, const double *rho, c
 // cell's high z-face flux over as the next cell's low one.
 __device__ __forceinline__ double face_flux2(const DGeom &g, const double *__restrict__ beta0, int d, int p,
                                              long long c_lo, long long c_hi, double u) {
+    // one FP64 expression for every face kind (branches with FP64 arithmetic
+    // are predicated by the compiler and would all occupy the FP64 pipe):
+    // inside / periodic (beta0_lo + beta0_hi) u; Dirichlet (beta0_in + beta0_in) u;
+    // wall 0 u
     const int n = g.n[d];
-    if ((p > 0 && p < n) || gper(g, d)) return (beta0[c_lo] + beta0[c_hi]) * u;
+    const bool inner = (p > 0 && p < n) || gper(g, d);
     const int bc = p == 0 ? g.lo[d] : g.hi[d];
-    if (bc == MX_BC_DIRICHLET) return (2.0 * beta0[p == 0 ? c_hi : c_lo]) * u;
-    return 0.0;  // wall: U_n taken as 0
+    const long long cin = p == 0 ? c_hi : c_lo;
+    const bool wall = !inner && bc != MX_BC_DIRICHLET;
+    const double a = wall ? 0.0 : beta0[inner ? c_lo : cin];
+    const double b = wall ? 0.0 : beta0[inner ? c_hi : cin];
+    return (a + b) * u;
 }
 
 template <typename F>
@@ -235,14 +242,16 @@ void k_sub_mean_norm(cudaStream_t s, const DGeom &g, double *f, const SolveState
 __device__ __forceinline__ void correct_face(const DGeom &g, int d, int p, long long cl, long long cr, long long ci,
                                              const double *__restrict__ phi, double q, double *__restrict__ u,
                                              long long f) {
+    // one FP64 expression for every face kind: U -= q (phi_R - phi_L), with
+    // phi = 0 outside a Dirichlet face and U = 0 on a wall
     const int n = g.n[d];
-    if ((p > 0 && p < n) || gper(g, d)) {
-        u[f] = fma(-q, phi[cr] - phi[cl], u[f]);
-    } else {
-        const int bc = p == 0 ? g.lo[d] : g.hi[d];
-        if (bc == MX_BC_DIRICHLET) u[f] = fma(p == 0 ? -q : q, phi[ci], u[f]);
-        else u[f] = 0.0;
-    }
+    const bool inner = (p > 0 && p < n) || gper(g, d);
+    const int bc = p == 0 ? g.lo[d] : g.hi[d];
+    const bool wall = !inner && bc != MX_BC_DIRICHLET;
+    const double pr = (inner || p == 0) ? phi[inner ? cr : ci] : 0.0;
+    const double pl = (inner || p != 0) ? phi[inner ? cl : ci] : 0.0;
+    const double un = fma(-q, pr - pl, u[f]);
+    u[f] = wall ? 0.0 : un;
 }
 
 __global__ void mac_correct_kernel(DGeom g, FaceQ Q, const double *__restrict__ phi, double *__restrict__ ux,

@@ -87,7 +87,6 @@ static void carve_plan(Bump &b, MacPlan &P) {
     P.Q.hx = gper(g, 0) ? nullptr : b.take<double>((size_t)g.n[1] * g.n[2]);
     P.Q.hy = gper(g, 1) ? nullptr : b.take<double>((size_t)g.n[0] * g.n[2]);
     P.Q.hz = gper(g, 2) ? nullptr : b.take<double>((size_t)g.n[0] * g.n[1]);
-    P.tmp64 = b.take<double>(g.N);
 }
 
 static bool same_geom(const DGeom &a, const DGeom &b) {
@@ -465,8 +464,10 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     prof_begin(c, s, MX_PH_SETUP);
     setup_coefficients(c, *P, rho, beta0);
     // right-hand side f = D(beta0 U) - beta0 Sbar, mean removal, norms
-    double *f64 = o.prec == MX_PREC_MIXED ? P->tmp64 : P->L64.f;
-    k_mac_rhs(s, g, ux, uy, uz, beta0, sbar, f64, c->partials, nb);
+    // (mixed: double-float f into the plan's (fh, fl); FP64: f into L64.f)
+    double *f64 = P->L64.f;
+    if (o.prec == MX_PREC_MIXED) k_mac_rhs_df(s, g, ux, uy, uz, beta0, sbar, P->D, c->partials);
+    else k_mac_rhs(s, g, ux, uy, uz, beta0, sbar, f64, c->partials, nb);
     k_finalize_rhs(s, c->partials, nb, c->state, g.N, singular && o.remove_mean, 0);
     if (singular && !o.remove_mean) {
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -480,7 +481,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
         }
     }
     if (o.prec == MX_PREC_MIXED) {
-        k_sub_mean_split(s, g, f64, c->state, P->D, c->partials, nbr);
+        k_sub_mean_scale(s, g, c->state, P->D, c->partials, nbr);
         if (o.use_initial_guess) {
             k_df_from_double(s, g.N, phi, P->D);
         } else {
@@ -506,7 +507,8 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
         k_sub_scalar(s, g.N, phi, &c->state->aux);
     }
     k_mac_correct(s, g, P->Q, phi, ux, uy, uz);
-    k_mac_divcheck(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials, nb);
+    if (o.prec == MX_PREC_MIXED) k_mac_divcheck_df(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials);
+    else k_mac_divcheck(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials, nb);
     k_finalize_max(s, c->partials, nb, &c->state->div_err);
     prof_end(c, s, MX_PH_FINISH, singular ? 8 : 5);
     MX_CUDA(c, cudaEventRecord(c->ev1, s));

@@ -25,7 +25,6 @@ struct MacPlan {
     Hier<double> H64;   // FP64: the FP64 correction hierarchy (level 0 shares L64's coefficients)
     FaceQ Q;            // correction factors 2/(h (rho_L + rho_R)) of the finest faces
     float *tmp32 = nullptr;
-    double *tmp64 = nullptr;
     // CUDA graph of the refinement loop, keyed by the pointers it was captured with
     cudaGraphExec_t graph = nullptr;
     const void *graph_phi = nullptr;

@@ -45,10 +45,12 @@ __device__ __forceinline__ T flux_sum(const T b[6], const T v[6], T pc) {
 // this part): a correctly rounded FP32 reciprocal refined by two Newton-Raphson
 // steps r <- r + r (1 - d r); the result is within about 2 ulp of 1/d.
 // Values outside the FP32 range fall back to the division.
+static __device__ __noinline__ double rcp64_slow(double d) { return 1.0 / d; }
 __device__ __forceinline__ double rcp64(double d) {
     const float df = __double2float_rn(d);
     const float rf = __frcp_rn(df);
-    if (!(fabsf(df) > 1e-37f && fabsf(df) < 1e37f)) return 1.0 / d;
+    // out of line: an inlined, predicated division would occupy the FP64 pipe on every call
+    if (!(fabsf(df) > 1e-37f && fabsf(df) < 1e37f)) return rcp64_slow(d);
     double r = double(rf);
     double e = fma(-d, r, 1.0);
     r = fma(r, e, r);
