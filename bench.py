@@ -48,6 +48,9 @@ def parse():
                    help="planar256: the headline line (+ nodal384 and batched96 extras); star512: the "
                         "full-star line; nodal-sweep: one line per nodal size 64^3..512^3; nodal384 / "
                         "batched96: that extra alone (for profiling)")
+    p.add_argument("--fixed", default=None, metavar="NU1,NU2,TILE_Z",
+                   help="skip the autotuner and use these smoother settings (for profiling a fixed "
+                        "configuration, e.g. the tuned one)")
     p.add_argument("--no-graph", action="store_true",
                    help="run the refinement loop from the host (same kernels; for profilers that "
                         "cannot see inside conditional CUDA graphs)")
@@ -126,8 +129,8 @@ def launches_per_solve(g, o, vcycles, graph):
     refinement iteration the V-cycle's launches on the levels above the coarse
     end (> 4096 cells: colour passes, residual+restriction, prolongation, or
     single-pass sweeps), the coarse-end CTA, update+residual and its finalize
-    (+1 condition kernel inside the graph); finish 7.  It reproduces the ncu
-    launch list of the planar 256^3 solve (409 launches at 9 V-cycles, host loop)."""
+    (+1 condition kernel inside the graph); finish 6 (4 without a mean to
+    remove).  Checked against the ncu launch list of the planar 256^3 solve."""
     dims = [list(g.n)]
     while all(d % 2 == 0 and d >= 4 for d in dims[-1]):
         dims.append([d // 2 for d in dims[-1]])
@@ -139,7 +142,9 @@ def launches_per_solve(g, o, vcycles, graph):
         fused = o.fused and ncell[l] >= (1 << 18) and dims[l][0] % 2 == 0
         per_iter += (o.nu1 + 1 + o.nu2) if fused else (2 * o.nu1 + 1 + 1 + 2 * o.nu2)
     setup = 1 + 1 + (nlev - 1) + 4 + 2
-    return setup + vcycles * per_iter + 7
+    singular = all(b != 2 for b in tuple(g.lo) + tuple(g.hi))  # no Dirichlet face
+    finish = 6 if singular else 4   # phi (+ its sums), [mean, subtract], correct, check, max
+    return setup + vcycles * per_iter + finish
 
 
 def setup_inputs(mx, W, dev, n, copies):
@@ -183,12 +188,20 @@ def run_mx(args):
     # these inputs (untimed); the timed solves then run with nu1 = nu2 = 0
     mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
     t_tune = time.perf_counter()
-    tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar,
-                              base=mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph))
-    tuned64, _ = (None, None) if args.no_fp64 else mx.mx_autotune(
-        ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar, base=mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph))
+    if args.fixed:
+        a, b, z = (int(x) for x in args.fixed.split(","))
+        tuned = mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=a, nu2=b, tile_z=z)
+        tuned64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph, nu1=a, nu2=b, tile_z=z)
+    else:
+        tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar,
+                                  base=mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph))
+        tuned64, _ = (None, None) if args.no_fp64 else mx.mx_autotune(
+            ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar,
+            base=mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph))
     t_tune = time.perf_counter() - t_tune
-    opts = mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=0, nu2=0)
+    opts = (mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=tuned.nu1, nu2=tuned.nu2,
+                            tile_z=tuned.tile_z) if args.fixed else
+            mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=0, nu2=0))
 
     def step(u, o=opts):
         mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
@@ -222,7 +235,9 @@ def run_mx(args):
     # ---- plain FP64 solve (the comparison) ----
     fp64 = None
     if not args.no_fp64:
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph, nu1=0, nu2=0)
+        o64 = (mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph, nu1=tuned64.nu1, nu2=tuned64.nu2,
+                               tile_z=tuned64.tile_z) if args.fixed else
+               mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph, nu1=0, nu2=0))
         u64 = [t.clone() for t in w.u]
         step(u64, o64)  # warm-up (plan, graph)
         kk = max(2, min(5, K // 4))
@@ -341,7 +356,7 @@ def run_mx(args):
                    "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z, "fused": tuned.fused,
                              "fp64": None if tuned64 is None else {"nu1": tuned64.nu1, "nu2": tuned64.nu2,
                                                                    "tile_z": tuned64.tile_z},
-                             "tuning_s": round(t_tune, 2)},
+                             "tuning_s": round(t_tune, 2), "source": "fixed" if args.fixed else "autotuner"},
                    "l2_policy": "inputs larger than L2 (fresh U copy per step, ~1.5 GB working set)",
                    "parallelism": f"replicas x{world}"},
         "vcycles_per_solve": vcycles, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
@@ -366,7 +381,7 @@ def timed(fn, steps, stream):
     return a.elapsed_time(b), out
 
 
-def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hbm=6793.4, graph=True):
+def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hbm=6793.4, graph=True, fixed=None):
     """Nodal projection (Step 11) on the planar256 stratification at n^3 cells:
     mixed precision vs plain FP64, solves/s, time per V-cycle and the HBM
     fraction of one V-cycle against the model's algorithmic bytes."""
@@ -377,9 +392,14 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0, g.dx, (0.5, 0.5, 0.5), beta0)
     phi = torch.zeros(mx.node_shape(g), dtype=torch.float64, device=dev)
     us = [[t.clone() for t in w.u] for _ in range(steps + warmup)]
-    tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_NODAL, g, *w.u, w.rho, beta0, w.sbar,
-                              base=mx.default_opts(use_graph=int(graph)))
-    opts = mx.default_opts(use_graph=int(graph), nu1=0, nu2=0)
+    if fixed:
+        a, b, z = (int(x) for x in fixed.split(","))
+        tuned = mx.default_opts(use_graph=int(graph), nu1=a, nu2=b, tile_z=z)
+        opts = tuned
+    else:
+        tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_NODAL, g, *w.u, w.rho, beta0, w.sbar,
+                                  base=mx.default_opts(use_graph=int(graph)))
+        opts = mx.default_opts(use_graph=int(graph), nu1=0, nu2=0)
     run = lambda u, o: mx.mx_nodal_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
     for i in range(warmup):
         run(us[i], opts)
@@ -541,7 +561,7 @@ def run_other(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     if args.workload == "nodal384":
         r = bench_nodal(mx, W, ctx, dev, stream, n=384, steps=args.steps, warmup=args.warmup,
-                        fp64=not args.no_fp64, hbm=hbm, graph=not args.no_graph)
+                        fp64=not args.no_fp64, hbm=hbm, graph=not args.no_graph, fixed=args.fixed)
         print(json.dumps(r), flush=True)
     elif args.workload == "batched96":
         r = bench_batched(mx, W, ctx, dev, stream, steps=args.steps, warmup=args.warmup,

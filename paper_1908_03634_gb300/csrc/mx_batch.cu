@@ -355,9 +355,8 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
         const DGeom &gb = g[b];
         SolveState *sb = B.d_st + b;
         const int nb = stencil_blocks(gb), nbr = red_blocks(gb.N);
-        k_df_final(s, gb.N, P.D, sb, phi[b]);
+        k_df_final(s, gb.N, P.D, sb, phi[b], geom_singular(gb) ? c->partials : nullptr);
         if (geom_singular(gb)) {
-            k_sum_partials(s, gb, phi[b], c->partials, nbr);
             k_finalize_sum(s, c->partials, nbr, &sb->aux, 1.0 / double(gb.N));
             k_sub_scalar(s, gb.N, phi[b], &sb->aux);
         }

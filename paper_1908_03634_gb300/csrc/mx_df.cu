@@ -353,8 +353,8 @@ __device__ __forceinline__ void df_resid_body(const Level<float> &L, const DFArr
     float *__restrict__ dpl = dst ? D.pl2 : D.pl;
     float sch = 0.f, scl = 0.f;
     if (UPDATE) {
-        sch = __double2float_rn(st->scale);
-        scl = __double2float_rn(st->scale - double(sch));
+        sch = st->scale_h;
+        scl = st->scale_l;
     }
     for (int q = tid; q < DHX * DHY * DHZ; q += DF_THREADS) {
         const int ax = q % DHX, ay = (q / DHX) % DHY, az = q / (DHX * DHY);
@@ -370,7 +370,7 @@ __device__ __forceinline__ void df_resid_body(const Level<float> &L, const DFArr
         sl_[az][ay][ax] = l;
     }
     __syncthreads();
-    const float c_hat = float(double(ih2) * st->inv_scale);
+    const float c_hat = ih2 * st->inv_scale_f;
     float mx = 0.f, s2f = 0.f, s1f = 0.f;
     for (int q = tid; q < DX * DY * DZ; q += DF_THREADS) {
         const int ix = q % DX, iy = (q / DX) % DY, iz = q / (DX * DY);
@@ -466,15 +466,32 @@ void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const
     else df_resid_tile_kernel<false><<<grid, DF_THREADS, 0, s>>>(L0, D, nullptr, st, ih2, partials);
 }
 
-// final phi (double) from the current double-float buffer (selected by the V-cycle count)
-__global__ void df_final_kernel(DFArrays D, const SolveState *st, double *__restrict__ x, long long n) {
+// final phi (double) from the current double-float buffer (selected by the
+// V-cycle count), formed from the float bit patterns with one FP64 addition,
+// with per-block partials (0, sum phi, 0) for the mean
+__global__ void df_final_kernel(DFArrays D, const SolveState *st, double *__restrict__ x, long long n,
+                                double *part) {
     const int b = st->iter & 1;
     const float *__restrict__ hi = b ? D.ph2 : D.ph;
     const float *__restrict__ lo = b ? D.pl2 : D.pl;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-        x[q] = double(hi[q]) + double(lo[q]);
+    dfloat s1 = {0.f, 0.f};
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const dfloat v = {hi[q], lo[q]};
+        x[q] = df_to_double(v);
+        if (part) s1 = df_add(s1, v);
+    }
+    if (part) {
+        double a = 0.0, sum = df_to_double(s1), c = 0.0;
+        block_red3(a, sum, c);
+        if (threadIdx.x == 0) {
+            double *p = part + 3 * blockIdx.x;
+            p[0] = a;
+            p[1] = sum;
+            p[2] = c;
+        }
+    }
 }
 
-void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x) {
-    df_final_kernel<<<red_blocks(n), 256, 0, s>>>(D, st, x, n);
+void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x, double *partials) {
+    df_final_kernel<<<red_blocks(n), 256, 0, s>>>(D, st, x, n, partials);
 }

@@ -44,4 +44,7 @@ struct DFBox {
 };
 void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
                       double *partials, int update);
-void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x);
+// phi (double) from the current double-float buffer; partials (may be null):
+// per-block (0, sum phi, 0) on red_blocks(n) blocks
+void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x,
+                double *partials = nullptr);

@@ -46,6 +46,8 @@ struct SolveState {
     double mean;                 // removed RHS mean
     double rnorm, rnorm2, rsum;  // last residual norms
     double scale, inv_scale;     // r is handed to the correction solve as r / scale
+    float scale_h, scale_l;      // scale as a double-float pair, and 1/scale as a float,
+    float inv_scale_f;           // for kernels that do no FP64 arithmetic
     double best;                 // smallest residual seen
     double tol;                  // relative tolerance
     double div_err;              // divergence check of the projected velocity
@@ -55,6 +57,15 @@ struct SolveState {
     int done;                    // 1: leave the refinement loop
     int status;                  // mx_status
 };
+
+// set the refinement scale (and its float forms)
+__device__ __forceinline__ void set_scale(SolveState *st, double sc) {
+    st->scale = sc;
+    st->inv_scale = 1.0 / sc;
+    st->scale_h = __double2float_rn(sc);
+    st->scale_l = __double2float_rn(sc - double(st->scale_h));
+    st->inv_scale_f = __double2float_rn(st->inv_scale);
+}
 
 struct MacPlan;
 struct NodalPlan;

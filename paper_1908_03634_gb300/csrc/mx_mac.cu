@@ -194,8 +194,7 @@ __global__ void finalize_rhs_kernel(const double *part, int nb, SolveState *st, 
             st->fnorm = a;
             st->fnorm2 = sqrt(b);
             st->fsum = c;
-            st->scale = a > 0.0 ? a : 1.0;
-            st->inv_scale = 1.0 / st->scale;
+            set_scale(st, a > 0.0 ? a : 1.0);
             st->best = INFINITY;
             st->iter = 0;
             st->done = 0;

@@ -292,8 +292,7 @@ __global__ void nd_finalize_rhs_kernel(const double *part, int nb, SolveState *s
             st->fnorm = a;
             st->fnorm2 = 0.0;
             st->fsum = b;
-            st->scale = a > 0.0 ? a : 1.0;
-            st->inv_scale = 1.0 / st->scale;
+            set_scale(st, a > 0.0 ? a : 1.0);
             st->best = INFINITY;
             st->iter = 0;
             st->done = 0;
@@ -658,8 +657,7 @@ __device__ __forceinline__ void ts2(float a, float b, float &s, float &e) {
 // UPDATE: phi += scale e first (in place; nodes are updated by their own thread
 // only, and the residual pass is a separate launch).
 __global__ void nd_df_update_kernel(NDF D, long long M, const float *__restrict__ e, const SolveState *st) {
-    const float sh = __double2float_rn(st->scale);
-    const float sl = __double2float_rn(st->scale - double(sh));
+    const float sh = st->scale_h, sl = st->scale_l;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
         const float ev = e[q];
         const float t = sh * ev;
@@ -726,7 +724,7 @@ __global__ void nd_df_col_resid_kernel(NLevel<float> L0, NDF D, const SolveState
     const NGeom &g = L0.g;
     const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     const int c0 = blockIdx.z * NCZ, c1 = min(c0 + NCZ, g.m[2]);
-    const float inv = float(st->inv_scale);
+    const float inv = st->inv_scale_f;
     const float ih2 = float(1.0 / (g.h * g.h));
     float mx = 0.f, s2 = 0.f, s1 = 0.f;
     if (a < g.m[0]) {

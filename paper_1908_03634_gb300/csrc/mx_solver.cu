@@ -498,11 +498,11 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     if (o.prec == MX_PREC_MIXED) st = run_ir<float>(c, *P, P->H32, phi, o, singular);
     else st = run_ir<double>(c, *P, P->H64, phi, o, singular);
     if (st) return st;
-    if (o.prec == MX_PREC_MIXED) k_df_final(s, g.N, P->D, c->state, phi);
-
     prof_begin(c, s, MX_PH_FINISH);
+    // mixed: phi from its double-float form, with the partial sums of phi
+    if (o.prec == MX_PREC_MIXED) k_df_final(s, g.N, P->D, c->state, phi, singular ? c->partials : nullptr);
     if (singular) {  // normalise mean(phi) = 0
-        k_sum_partials(s, g, phi, c->partials, nbr);
+        if (o.prec != MX_PREC_MIXED) k_sum_partials(s, g, phi, c->partials, nbr);
         k_finalize_sum(s, c->partials, nbr, &c->state->aux, 1.0 / double(g.N));
         k_sub_scalar(s, g.N, phi, &c->state->aux);
     }
@@ -510,7 +510,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     if (o.prec == MX_PREC_MIXED) k_mac_divcheck_df(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials);
     else k_mac_divcheck(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials, nb);
     k_finalize_max(s, c->partials, nb, &c->state->div_err);
-    prof_end(c, s, MX_PH_FINISH, singular ? 8 : 5);
+    prof_end(c, s, MX_PH_FINISH, (singular ? 3 : 0) + (o.prec == MX_PREC_MIXED ? 5 : 4));
     MX_CUDA(c, cudaEventRecord(c->ev1, s));
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));
