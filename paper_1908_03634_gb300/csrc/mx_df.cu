@@ -166,9 +166,10 @@ __device__ __forceinline__ void df_div_column(const DGeom &g, const double *__re
     }
 }
 
-// per-block partials (max |x|, sum x^2, sum x) from per-thread float / double-float sums
-__device__ __forceinline__ void df_partials(float mx, float s2, dfloat s1, double *p) {
-    double a = mx, b = s2, c = df_to_double(s1);
+// per-block partials (max |x|, sum x^2, sum x) from per-thread double-float max
+// and sum and a float sum of squares
+__device__ __forceinline__ void df_partials(dfloat mx, float s2, dfloat s1, double *p) {
+    double a = df_to_double(mx), b = s2, c = df_to_double(s1);
     block_red3(a, b, c);
     if (flat_tid() == 0) {
         p[0] = a;
@@ -183,13 +184,13 @@ __global__ void mac_rhs_df_kernel(DGeom g, const double *__restrict__ ux, const 
                                   double *part, dfloat hih) {
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
-    float mx = 0.f, s2 = 0.f;
-    dfloat s1 = {0.f, 0.f};
+    dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
+    float s2 = 0.f;
     if (i < g.n[0] && j < g.n[1])
         df_div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, dfloat v) {
             fh[c] = v.h;
             fl[c] = v.l;
-            mx = fmaxf(mx, fabsf(v.h));
+            df_absmax(mx, v);
             s2 = fmaf(v.h, v.h, s2);
             s1 = df_add(s1, v);
         });
@@ -204,10 +205,10 @@ __global__ void mac_divcheck_df_kernel(DGeom g, const double *__restrict__ ux, c
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     const dfloat cm = df_split(st->mean);
-    float mx = 0.f;
+    dfloat mx = {0.f, 0.f};
     if (i < g.n[0] && j < g.n[1])
         df_div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
-                      [&](long long, dfloat v) { mx = fmaxf(mx, fabsf(df_sub(v, cm).h)); });
+                      [&](long long, dfloat v) { df_absmax(mx, df_sub(v, cm)); });
     df_partials(mx, 0.f, dfloat{0.f, 0.f}, part + 3 * flat_bid());
 }
 
@@ -234,14 +235,14 @@ void k_mac_divcheck_df(cudaStream_t s, const DGeom &g, const double *ux, const d
 __global__ void sub_mean_scale_kernel(long long n, const SolveState *st, dfloat h2, float *__restrict__ fh,
                                       float *__restrict__ fl, double *part) {
     const dfloat m = df_split(st->mean);
-    float mx = 0.f, s2 = 0.f;
-    dfloat s1 = {0.f, 0.f};
+    dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
+    float s2 = 0.f;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const dfloat v = df_sub(dfloat{fh[q], fl[q]}, m);
         const dfloat w = df_mul(v, h2);
         fh[q] = w.h;
         fl[q] = w.l;
-        mx = fmaxf(mx, fabsf(v.h));
+        df_absmax(mx, v);
         s2 = fmaf(v.h, v.h, s2);
         s1 = df_add(s1, v);
     }

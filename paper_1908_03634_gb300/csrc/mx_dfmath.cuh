@@ -105,3 +105,11 @@ __device__ __forceinline__ dfloat df_div(dfloat a, dfloat b) {
     const float r = (((a.h - p) - pe) + a.l) - q1 * b.l;
     return df_norm(q1, r / b.h);
 }
+
+// m = the larger of m and |v| (by hi, then lo), both double-float
+__device__ __forceinline__ void df_absmax(dfloat &m, dfloat v) {
+    const bool neg = v.h < 0.f || (v.h == 0.f && v.l < 0.f);
+    const dfloat a = neg ? dfloat{-v.h, -v.l} : v;
+    const bool gt = a.h > m.h || (a.h == m.h && a.l > m.l);
+    m = gt ? a : m;
+}

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mx_dfmath.cuh"
 #include "mx_solver.cuh"
 #include "mx_stencil.cuh"
 
@@ -888,10 +889,6 @@ __global__ void nd_resid32_kernel(const double *__restrict__ f, const float *__r
     }
 }
 
-__global__ void nd_df_final_kernel(NDF D, long long M, double *phi) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x)
-        phi[q] = double(D.ph[q]) + double(D.pl[q]);
-}
 
 // weighted mean of phi -> st->aux, then subtraction
 __global__ void nd_wsum_kernel(NGeom g, const double *x, double *part) {
@@ -952,6 +949,191 @@ __global__ void nd_correct_kernel(NGeom g, const double *__restrict__ rho, const
         uz[c] -= gz * ir;
         for (int e = 0; e < 4; e++) lo[e] = hi[e];
     }
+}
+
+// ---- mixed precision: setup and finish in double-float arithmetic ----------------------
+// FP64 inputs are split into double-float pairs by integer bit operations and
+// the arithmetic runs on the FP32 pipe (GB300 executes FP64 at 1/58 of the
+// FP32 rate); results written as FP64 are formed from their pairs with one
+// FP64 addition.
+
+// sigma = beta0 / rho as (hi, lo)
+__global__ void nd_sigma_df_kernel(long long N, const double *__restrict__ rho, const double *__restrict__ beta0,
+                                   float *__restrict__ s32, float *__restrict__ sl) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const dfloat v = df_div(df_split(beta0[q]), df_split(rho[q]));
+        s32[q] = v.h;
+        sl[q] = v.l;
+    }
+}
+
+struct RhsLayerDF {
+    dfloat x, y, z, s;
+    int n;
+};
+
+__device__ __forceinline__ RhsLayerDF rhs_layer_df(const NGeom &g, const double *__restrict__ ux,
+                                                   const double *__restrict__ uy, const double *__restrict__ uz,
+                                                   const double *__restrict__ beta0, const double *__restrict__ sbar,
+                                                   int i0, int i1, int j0, int j1, int k) {
+    RhsLayerDF L = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, 0};
+    const int kk = cell_wrap(g, 2, k);
+    if (kk < 0) return L;
+    for (int jj = 0; jj < 2; jj++) {
+        const int j = jj ? j1 : j0;
+        if (j < 0) continue;
+        for (int ii = 0; ii < 2; ii++) {
+            const int i = ii ? i1 : i0;
+            if (i < 0) continue;
+            const int c = i + g.n[0] * (j + g.n[1] * kk);
+            const dfloat bt = df_split(beta0[c]);
+            const dfloat px = df_mul(bt, df_split(ux[c])), py = df_mul(bt, df_split(uy[c]));
+            L.x = df_add(L.x, ii ? px : df_neg(px));
+            L.y = df_add(L.y, jj ? py : df_neg(py));
+            L.z = df_add(L.z, df_mul(bt, df_split(uz[c])));
+            L.s = df_add(L.s, df_mul(bt, df_split(sbar[c])));
+            L.n++;
+        }
+    }
+    return L;
+}
+
+__device__ __forceinline__ dfloat df_scale(dfloat a, float p2) { return dfloat{a.h * p2, a.l * p2}; }  // p2 = 2^k
+
+// the gather of nd_rhs_col_kernel in double-float: f (may be null) as (fh, fl),
+// partials (max |f|, sum w f, sum w); i4h8 = 8/(4h)
+__global__ void nd_rhs_col_df_kernel(NGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                                     const double *__restrict__ uz, const double *__restrict__ beta0,
+                                     const double *__restrict__ sbar, float *__restrict__ fh, float *__restrict__ fl,
+                                     double *part, int sub_mean, const SolveState *st, dfloat i4h8) {
+    float s0 = 0.f;
+    dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
+    const int a = blockIdx.x * 32 + threadIdx.x, b = blockIdx.y * 8 + threadIdx.y;
+    const int c0 = blockIdx.z * NRZ, c1 = min(c0 + NRZ, g.m[2]);
+    if (a < g.m[0] && b < g.m[1]) {
+        const dfloat cm = sub_mean ? df_split(st->mean) : dfloat{0.f, 0.f};
+        const int i0 = cell_wrap(g, 0, a - 1), i1 = cell_wrap(g, 0, a);
+        const int j0 = cell_wrap(g, 1, b - 1), j1 = cell_wrap(g, 1, b);
+        RhsLayerDF lo = rhs_layer_df(g, ux, uy, uz, beta0, sbar, i0, i1, j0, j1, c0 - 1);
+        for (int c = c0; c < c1; c++) {
+            const RhsLayerDF hi = rhs_layer_df(g, ux, uy, uz, beta0, sbar, i0, i1, j0, j1, c);
+            const int cnt = lo.n + hi.n;  // 1, 2, 4 or 8
+            const float ic = cnt == 8 ? 0.125f : cnt == 4 ? 0.25f : cnt == 2 ? 0.5f : 1.f;
+            const dfloat div = df_add(df_add(df_add(lo.x, hi.x), df_add(lo.y, hi.y)), df_sub(hi.z, lo.z));
+            const dfloat v = df_sub(df_sub(df_mul(div, df_scale(i4h8, ic)), df_scale(df_add(lo.s, hi.s), ic)), cm);
+            const float w = 0.125f * cnt;
+            if (fh) {
+                const int q = a + g.m[0] * (b + g.m[1] * c);
+                fh[q] = v.h;
+                fl[q] = v.l;
+            }
+            df_absmax(mx, v);
+            s1 = df_add(s1, df_scale(v, w));
+            s0 += w;
+            lo = hi;
+        }
+    }
+    double pa = df_to_double(mx), pb = df_to_double(s1), pc = s0;
+    block_red3(pa, pb, pc);
+    if (flat_tid() == 0) {
+        double *p = part + 3 * flat_bid();
+        p[0] = pa;
+        p[1] = pb;
+        p[2] = pc;
+    }
+}
+
+// f <- 12 h^2 w (f - mean) in double-float; partials (max, sum^2, sum) of f - mean
+__global__ void nd_rhs_final_df_kernel(NGeom g, const SolveState *st, dfloat h2x12, float *__restrict__ fh,
+                                       float *__restrict__ fl, double *part) {
+    const dfloat m = df_split(st->mean);
+    dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
+    float s2 = 0.f;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        const dfloat v = df_sub(dfloat{fh[q], fl[q]}, m);
+        const dfloat sv = df_mul(df_scale(h2x12, node_w(g, a, b, c)), v);
+        fh[q] = sv.h;
+        fl[q] = sv.l;
+        df_absmax(mx, v);
+        s2 = fmaf(v.h, v.h, s2);
+        s1 = df_add(s1, v);
+    }
+    double pa = df_to_double(mx), pb = s2, pc = df_to_double(s1);
+    block_red3(pa, pb, pc);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = pa;
+        part[3 * blockIdx.x + 1] = pb;
+        part[3 * blockIdx.x + 2] = pc;
+    }
+}
+
+// phi (double) from its double-float pair, with partials (0, sum w phi, sum w)
+__global__ void nd_df_final_sum_kernel(NGeom g, NDF D, double *__restrict__ phi, double *part) {
+    dfloat s1 = {0.f, 0.f};
+    float s0 = 0.f;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        node_of(g, q, a, b, c);
+        const dfloat v = {D.ph[q], D.pl[q]};
+        phi[q] = df_to_double(v);
+        const float w = node_w(g, a, b, c);
+        s1 = df_add(s1, df_scale(v, w));
+        s0 += w;
+    }
+    double pa = 0.0, pb = df_to_double(s1), pc = s0;
+    block_red3(pa, pb, pc);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = pa;
+        part[3 * blockIdx.x + 1] = pb;
+        part[3 * blockIdx.x + 2] = pc;
+    }
+}
+
+// U -= G_c phi / rho per cell from phi's double-float pair (the weighted mean
+// of phi cancels in the edge differences), in double-float
+__global__ void nd_correct_df_kernel(NGeom g, const double *__restrict__ rho, NDF D, double *__restrict__ ux,
+                                     double *__restrict__ uy, double *__restrict__ uz, dfloat i4h) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int k0 = blockIdx.z * NRZ, k1 = min(k0 + NRZ, g.n[2]);
+    if (i >= g.n[0] || j >= g.n[1]) return;
+    const int a1 = (g.per[0] && i + 1 == g.m[0]) ? 0 : i + 1;
+    const int b1 = (g.per[1] && j + 1 == g.m[1]) ? 0 : j + 1;
+    const int m01 = g.m[0] * g.m[1];
+    const int o00 = i + g.m[0] * j, o10 = a1 + g.m[0] * j, o01 = i + g.m[0] * b1, o11 = a1 + g.m[0] * b1;
+    auto face = [&](int c, dfloat p[4]) {
+        const int cc = (g.per[2] && c == g.m[2]) ? 0 : c;
+        const int base = m01 * cc;
+        p[0] = dfloat{D.ph[base + o00], D.pl[base + o00]};
+        p[1] = dfloat{D.ph[base + o10], D.pl[base + o10]};
+        p[2] = dfloat{D.ph[base + o01], D.pl[base + o01]};
+        p[3] = dfloat{D.ph[base + o11], D.pl[base + o11]};
+    };
+    dfloat lo[4], hi[4];
+    face(k0, lo);
+    for (int k = k0; k < k1; k++) {
+        face(k + 1, hi);
+        const dfloat gx = df_add(df_add(df_sub(lo[1], lo[0]), df_sub(lo[3], lo[2])),
+                                 df_add(df_sub(hi[1], hi[0]), df_sub(hi[3], hi[2])));
+        const dfloat gy = df_add(df_add(df_sub(lo[2], lo[0]), df_sub(lo[3], lo[1])),
+                                 df_add(df_sub(hi[2], hi[0]), df_sub(hi[3], hi[1])));
+        const dfloat gz = df_add(df_add(df_sub(hi[0], lo[0]), df_sub(hi[1], lo[1])),
+                                 df_add(df_sub(hi[2], lo[2]), df_sub(hi[3], lo[3])));
+        const int c = i + g.n[0] * (j + g.n[1] * k);
+        const dfloat f = df_div(i4h, df_split(rho[c]));  // 1/(4 h rho)
+        ux[c] = df_to_double(df_sub(df_split(ux[c]), df_mul(gx, f)));
+        uy[c] = df_to_double(df_sub(df_split(uy[c]), df_mul(gy, f)));
+        uz[c] = df_to_double(df_sub(df_split(uz[c]), df_mul(gz, f)));
+        for (int e = 0; e < 4; e++) lo[e] = hi[e];
+    }
+}
+
+static dfloat df_host(double v) {
+    dfloat r;
+    r.h = float(v);
+    r.l = float(v - double(r.h));
+    return r;
 }
 
 // ---- host side -------------------------------------------------------------------------
@@ -1087,7 +1269,7 @@ static mx_status nodal_setup(mx_ctx *c, NodalPlan &P, const double *rho, const d
     cudaStream_t s = c->stream;
     const NGeom &g = P.g;
     if (P.prec == MX_PREC_MIXED) {
-        nd_sigma_kernel<<<nblk(g.N), 256, 0, s>>>(g.N, rho, beta0, nullptr, P.L32[0].sigma, P.D.sl);
+        nd_sigma_df_kernel<<<nblk(g.N), 256, 0, s>>>(g.N, rho, beta0, P.L32[0].sigma, P.D.sl);
         for (int l = 0; l + 1 < P.nlev; l++)
             nd_coarsen_sigma_kernel<float><<<nblk(P.L32[l + 1].g.N), 256, 0, s>>>(P.L32[l], P.L32[l + 1]);
     } else {
@@ -1129,8 +1311,13 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     MX_CUDA(c, cudaMemcpyAsync(c->state, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     prof_begin(c, s, MX_PH_SETUP);
     if ((st = nodal_setup(c, *P, rho, beta0))) return st;
-    nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0,
-                                                             c->state, 0.25 / g.h);
+    const bool mixed = o.prec == MX_PREC_MIXED;
+    if (mixed)
+        nd_rhs_col_df_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, P->D.fh, P->D.fl,
+                                                                    c->partials, 0, c->state, df_host(2.0 / g.h));
+    else
+        nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0,
+                                                                 c->state, 0.25 / g.h);
     nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nd_node_blocks(g), c->state, o.remove_mean, 0);
     if (!o.remove_mean) {
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -1143,9 +1330,11 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
             return set_err(c, MX_ERR_INCOMPAT, "nodal: right-hand side has non-zero weighted mean and remove_mean = 0");
         }
     }
-    const bool mixed = o.prec == MX_PREC_MIXED;
-    nd_rhs_final_kernel<<<nb, 256, 0, s>>>(g, P->f64, c->state, mixed ? P->D.fh : nullptr, mixed ? P->D.fl : nullptr,
-                                           c->partials);
+    if (mixed)
+        nd_rhs_final_df_kernel<<<nb, 256, 0, s>>>(g, c->state, df_host(12.0 * g.h * g.h), P->D.fh, P->D.fl,
+                                                  c->partials);
+    else
+        nd_rhs_final_kernel<<<nb, 256, 0, s>>>(g, P->f64, c->state, nullptr, nullptr, c->partials);
     nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nb, c->state, 0, 1);
     if (mixed) {
         if (o.use_initial_guess) {
@@ -1212,18 +1401,26 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         }
     }
     prof_begin(c, s, MX_PH_FINISH);
-    if (mixed) nd_df_final_kernel<<<nb, 256, 0, s>>>(P->D, g.M, phi);
-    // normalise the weighted mean of phi to 0, correct U, check the divergence
-    nd_wsum_kernel<<<nb, 256, 0, s>>>(g, phi, c->partials);
+    // phi with its weighted mean removed, U -= G_c phi / rho, the divergence check
+    const dim3 cgrid((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + NRZ - 1) / NRZ);
+    if (mixed) {
+        nd_df_final_sum_kernel<<<nb, 256, 0, s>>>(g, P->D, phi, c->partials);
+    } else {
+        nd_wsum_kernel<<<nb, 256, 0, s>>>(g, phi, c->partials);
+    }
     nd_wmean_finalize_kernel<<<1, 1024, 0, s>>>(c->partials, nb, &c->state->aux);
     k_sub_scalar(s, g.M, phi, &c->state->aux);
-    nd_correct_kernel<<<dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + NRZ - 1) / NRZ), dim3(32, 8), 0, s>>>(
-        g, rho, phi, ux, uy, uz, 0.25 / g.h);
-    // divergence of the projected velocity minus Sbar_n minus c: nd_rhs with the mean subtracted
-    nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials, 1,
-                                                             c->state, 0.25 / g.h);
+    if (mixed) nd_correct_df_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, P->D, ux, uy, uz, df_host(0.25 / g.h));
+    else nd_correct_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, phi, ux, uy, uz, 0.25 / g.h);
+    // divergence of the projected velocity minus Sbar_n minus c: the RHS gather with the mean subtracted
+    if (mixed)
+        nd_rhs_col_df_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, nullptr,
+                                                                    c->partials, 1, c->state, df_host(2.0 / g.h));
+    else
+        nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials,
+                                                                 1, c->state, 0.25 / g.h);
     k_finalize_max(s, c->partials, nd_node_blocks(g), &c->state->div_err);
-    prof_end(c, s, MX_PH_FINISH, 7);
+    prof_end(c, s, MX_PH_FINISH, 6);
     MX_CUDA(c, cudaEventRecord(c->ev1, s));
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));
