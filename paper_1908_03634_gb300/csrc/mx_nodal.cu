@@ -1377,14 +1377,16 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     prof_flush(c);
     if (!c->hstate->done) {
         if (o.use_graph && !c->prof) {
-            if (!P->graph || P->graph_phi != phi || P->graph_nu1 != o.nu1 || P->graph_nu2 != o.nu2 ||
+            // the FP64 loop updates phi in place; the mixed loop never touches it
+            const void *kphi = mixed ? nullptr : (const void *)phi;
+            if (!P->graph || P->graph_phi != kphi || P->graph_nu1 != o.nu1 || P->graph_nu2 != o.nu2 ||
                 P->graph_bot != o.bottom_iters || P->graph_tilez != o.tile_z) {
                 if (P->graph) {
                     cudaGraphExecDestroy(P->graph);
                     P->graph = nullptr;
                 }
                 if ((st = capture_while_graph(c, &P->graph, [&](cudaStream_t cs) { step(cs, nullptr); }))) return st;
-                P->graph_phi = phi;
+                P->graph_phi = kphi;
                 P->graph_nu1 = o.nu1;
                 P->graph_nu2 = o.nu2;
                 P->graph_bot = o.bottom_iters;

@@ -364,8 +364,10 @@ mx_status capture_while_graph(mx_ctx *c, cudaGraphExec_t *exec, const std::funct
 template <typename T>
 static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx_opts &o, int singular, int nb) {
     cudaStream_t s = c->stream;
-    if (!P.graph || P.graph_phi != phi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 || P.graph_bot != o.bottom_iters ||
-        P.graph_fused != o.fused || P.graph_tilez != o.tile_z) {
+    // the FP64 loop updates phi in place; the mixed loop never touches it
+    const void *kphi = sizeof(T) == sizeof(double) ? (const void *)phi : nullptr;
+    if (!P.graph || P.graph_phi != kphi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 ||
+        P.graph_bot != o.bottom_iters || P.graph_fused != o.fused || P.graph_tilez != o.tile_z) {
         if (P.graph) {
             cudaGraphExecDestroy(P.graph);
             P.graph = nullptr;
@@ -373,7 +375,7 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
         mx_status st = capture_while_graph(
             c, &P.graph, [&](cudaStream_t cs) { ir_step(cs, c, P, H, phi, o, singular, nb, nullptr); });
         if (st) return st;
-        P.graph_phi = phi;
+        P.graph_phi = kphi;
         P.graph_nu1 = o.nu1;
         P.graph_nu2 = o.nu2;
         P.graph_bot = o.bottom_iters;
