@@ -12,13 +12,30 @@
 
 constexpr int CT = 1024;  // threads of the coarse CTA
 
+// Exact division of x < 2^16 by d < 2^16 as a multiply-high with the
+// precomputed m = ceil(2^32 / d) (the error x (m - 2^32/d) / 2^32 stays below
+// 1/d, so the floor is exact).
+struct FastDiv {
+    unsigned d, m;
+};
+inline FastDiv fast_div(unsigned d) { return FastDiv{d, unsigned(((1ull << 32) + d - 1) / d)}; }
+__device__ __forceinline__ int fdiv(int x, FastDiv f) { return int(__umulhi(unsigned(x), f.m)); }
+
 template <typename T>
 struct CoarseArgs {
     int nl;                        // number of levels handled (the last is the bottom)
     Level<T> lev[COARSE_MAX_LEVELS];
+    FastDiv d0[COARSE_MAX_LEVELS], d1[COARSE_MAX_LEVELS], dh[COARSE_MAX_LEVELS];  // n0, n1, n0/2
     int nu1, nu2, bot_iters, singular;
 };
 
+// cell (i, j, k) of index c of a level of at most 2^16 cells
+__device__ __forceinline__ void cell_ijk(int c, FastDiv d0, FastDiv d1, int &i, int &j, int &k) {
+    const int r = fdiv(c, d0);
+    i = c - r * int(d0.d);
+    k = fdiv(r, d1);
+    j = r - k * int(d1.d);
+}
 __device__ __forceinline__ void cell_ijk(const DGeom &g, int c, int &i, int &j, int &k) {
     i = c % g.n[0];
     const int r = c / g.n[0];
@@ -26,27 +43,66 @@ __device__ __forceinline__ void cell_ijk(const DGeom &g, int c, int &i, int &j, 
     k = r / g.n[1];
 }
 
+// the 6 face coefficients and neighbour values of in-box cell (i,j,k) = c
+// with 32-bit indexing (the same values as face_coefs / nb_vals)
 template <typename T>
-__device__ void cta_colour(const Level<T> &L, T *e, const T *f, int colour, T h2) {
+__device__ __forceinline__ void coefs_nbs(const Level<T> &L, const T *p, int i, int j, int k, int c, T b[6], T v[6]) {
     const DGeom &g = L.g;
-    for (int c = threadIdx.x; c < g.N; c += CT) {
-        int i, j, k;
-        cell_ijk(g, c, i, j, k);
-        if (((i + j + k) & 1) != colour) continue;
-        T b[6], v[6];
-        face_coefs(L, i, j, k, c, b);
-        nb_vals(g, e, i, j, k, c, v);
-        e[c] = gs_update(b, v, f[c], h2);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxy = nx * ny;
+    const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
+    b[0] = L.bx[c];
+    b[1] = (i + 1 < nx) ? L.bx[c + 1] : (px ? L.bx[c - (nx - 1)] : L.hx[j + ny * k]);
+    b[2] = L.by[c];
+    b[3] = (j + 1 < ny) ? L.by[c + nx] : (py ? L.by[c - (ny - 1) * nx] : L.hy[i + nx * k]);
+    b[4] = L.bz[c];
+    b[5] = (k + 1 < nz) ? L.bz[c + nxy] : (pz ? L.bz[c - (nz - 1) * nxy] : L.hz[i + nx * j]);
+    v[0] = i > 0 ? p[c - 1] : (px ? p[c + nx - 1] : T(0));
+    v[1] = i + 1 < nx ? p[c + 1] : (px ? p[c - (nx - 1)] : T(0));
+    v[2] = j > 0 ? p[c - nx] : (py ? p[c + (ny - 1) * nx] : T(0));
+    v[3] = j + 1 < ny ? p[c + nx] : (py ? p[c - (ny - 1) * nx] : T(0));
+    v[4] = k > 0 ? p[c - nxy] : (pz ? p[c + (nz - 1) * nxy] : T(0));
+    v[5] = k + 1 < nz ? p[c + nxy] : (pz ? p[c - (nz - 1) * nxy] : T(0));
+}
+
+// One colour of red-black Gauss-Seidel: with n0 even the threads walk the
+// colour's cells only (pair m of row r: i = 2m + parity); otherwise all cells.
+template <typename T>
+__device__ void cta_colour(const Level<T> &L, T *e, const T *f, int colour, T h2, FastDiv d1, FastDiv dh) {
+    const DGeom &g = L.g;
+    const int n0 = g.n[0];
+    if (n0 % 2 == 0) {
+        const int nc = int(g.N) / 2;
+        for (int t = threadIdx.x; t < nc; t += CT) {
+            const int r = fdiv(t, dh);  // row j + n1 k
+            const int m = t - r * int(dh.d);
+            const int k = fdiv(r, d1);
+            const int j = r - k * int(d1.d);
+            const int i = 2 * m + ((j + k + colour) & 1);
+            const int c = i + n0 * r;
+            T b[6], v[6];
+            coefs_nbs(L, e, i, j, k, c, b, v);
+            e[c] = gs_update(b, v, f[c], h2);
+        }
+    } else {
+        for (int c = threadIdx.x; c < g.N; c += CT) {
+            int i, j, k;
+            cell_ijk(g, c, i, j, k);
+            if (((i + j + k) & 1) != colour) continue;
+            T b[6], v[6];
+            coefs_nbs(L, e, i, j, k, c, b, v);
+            e[c] = gs_update(b, v, f[c], h2);
+        }
     }
     __syncthreads();
 }
 
 template <typename T>
-__device__ void cta_resid_restrict(const Level<T> &F, const T *ef, const T *ff, const DGeom &gc, T *fc, T *ec, T ih2) {
+__device__ void cta_resid_restrict(const Level<T> &F, const T *ef, const T *ff, const DGeom &gc, T *fc, T *ec, T ih2,
+                                   FastDiv c0, FastDiv c1) {
     const DGeom &g = F.g;
     for (int C = threadIdx.x; C < gc.N; C += CT) {
         int I, J, K;
-        cell_ijk(gc, C, I, J, K);
+        cell_ijk(C, c0, c1, I, J, K);
         T s = T(0);
         for (int dk = 0; dk < 2; dk++)
             for (int dj = 0; dj < 2; dj++)
@@ -54,8 +110,7 @@ __device__ void cta_resid_restrict(const Level<T> &F, const T *ef, const T *ff, 
                     const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
                     const int c = i + g.n[0] * (j + g.n[1] * k);
                     T b[6], v[6];
-                    face_coefs(F, i, j, k, c, b);
-                    nb_vals(g, ef, i, j, k, c, v);
+                    coefs_nbs(F, ef, i, j, k, c, b, v);
                     s += ff[c] - flux_sum(b, v, ef[c]) * ih2;
                 }
         fc[C] = s * T(0.125);
@@ -65,10 +120,10 @@ __device__ void cta_resid_restrict(const Level<T> &F, const T *ef, const T *ff, 
 }
 
 template <typename T>
-__device__ void cta_prolong(const DGeom &gc, const T *ec, const DGeom &g, T *ef) {
+__device__ void cta_prolong(const DGeom &gc, const T *ec, const DGeom &g, T *ef, FastDiv d0, FastDiv d1) {
     for (int c = threadIdx.x; c < g.N; c += CT) {
         int i, j, k;
-        cell_ijk(g, c, i, j, k);
+        cell_ijk(c, d0, d1, i, j, k);
         ef[c] += ec[(i >> 1) + gc.n[0] * ((j >> 1) + gc.n[1] * (k >> 1))];
     }
     __syncthreads();
@@ -121,8 +176,7 @@ __device__ void cta_apply(const Level<T> &L, const T *x, T *y, T ih2) {
         int i, j, k;
         cell_ijk(g, c, i, j, k);
         T b[6], v[6];
-        face_coefs(L, i, j, k, c, b);
-        nb_vals(g, x, i, j, k, c, v);
+        coefs_nbs(L, x, i, j, k, c, b, v);
         y[c] = flux_sum(b, v, x[c]) * ih2;
     }
     __syncthreads();
@@ -282,10 +336,11 @@ __device__ void coarse_body(const CoarseArgs<T> &A) {
         const Level<T> &L = A.lev[l];
         const T h2 = T(L.g.h * L.g.h);
         for (int q = 0; q < A.nu1; q++) {
-            cta_colour(L, e[l], f[l], 0, h2);
-            cta_colour(L, e[l], f[l], 1, h2);
+            cta_colour(L, e[l], f[l], 0, h2, A.d1[l], A.dh[l]);
+            cta_colour(L, e[l], f[l], 1, h2, A.d1[l], A.dh[l]);
         }
-        cta_resid_restrict(L, e[l], f[l], A.lev[l + 1].g, f[l + 1], e[l + 1], T(1) / T(L.g.h * L.g.h));
+        cta_resid_restrict(L, e[l], f[l], A.lev[l + 1].g, f[l + 1], e[l + 1], T(1) / T(L.g.h * L.g.h), A.d0[l + 1],
+                           A.d1[l + 1]);
     }
     {
         const Level<T> &L = A.lev[nb];
@@ -294,10 +349,10 @@ __device__ void coarse_body(const CoarseArgs<T> &A) {
     for (int l = nb - 1; l >= 0; l--) {
         const Level<T> &L = A.lev[l];
         const T h2 = T(L.g.h * L.g.h);
-        cta_prolong(A.lev[l + 1].g, e[l + 1], L.g, e[l]);
+        cta_prolong(A.lev[l + 1].g, e[l + 1], L.g, e[l], A.d0[l], A.d1[l]);
         for (int q = 0; q < A.nu2; q++) {
-            cta_colour(L, e[l], f[l], 0, h2);
-            cta_colour(L, e[l], f[l], 1, h2);
+            cta_colour(L, e[l], f[l], 0, h2, A.d1[l], A.dh[l]);
+            cta_colour(L, e[l], f[l], 1, h2, A.d1[l], A.dh[l]);
         }
     }
     for (int c = threadIdx.x; c < A.lev[0].g.N; c += CT) A.lev[0].e[c] = e[0][c];
@@ -332,7 +387,12 @@ template <typename T>
 void k_coarse_vcycle(cudaStream_t s, const Level<T> *levs, int nl, int nu1, int nu2, int bot_iters, int singular) {
     CoarseArgs<T> A;
     A.nl = nl;
-    for (int l = 0; l < nl; l++) A.lev[l] = levs[l];
+    for (int l = 0; l < nl; l++) {
+        A.lev[l] = levs[l];
+        A.d0[l] = fast_div(levs[l].g.n[0]);
+        A.d1[l] = fast_div(levs[l].g.n[1]);
+        A.dh[l] = fast_div(levs[l].g.n[0] > 1 ? levs[l].g.n[0] / 2 : 1);
+    }
     A.nu1 = nu1;
     A.nu2 = nu2;
     A.bot_iters = bot_iters;
@@ -359,7 +419,12 @@ void coarse_fill_args(void *dst, const Level<float> *levs, int nl, int nu1, int 
     CoarseArgs<float> A;
     std::memset(&A, 0, sizeof(A));
     A.nl = nl;
-    for (int l = 0; l < nl; l++) A.lev[l] = levs[l];
+    for (int l = 0; l < nl; l++) {
+        A.lev[l] = levs[l];
+        A.d0[l] = fast_div(levs[l].g.n[0]);
+        A.d1[l] = fast_div(levs[l].g.n[1]);
+        A.dh[l] = fast_div(levs[l].g.n[0] > 1 ? levs[l].g.n[0] / 2 : 1);
+    }
     A.nu1 = nu1;
     A.nu2 = nu2;
     A.bot_iters = bot_iters;
