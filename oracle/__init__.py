@@ -21,20 +21,21 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_SOURCES = ["oracle.c", "oracle_nodal.c"]
+_SOURCES = ["oracle.c", "oracle_nodal.c", "oracle_base.c"]
 
 PERIODIC, NEUMANN, DIRICHLET = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/liboracle.so (portable C, -O2)."""
+    """Compile the oracle with gcc into oracle/liboracle.so (portable C, -O2, no FMA
+    contraction, so that x86 and Arm builds round every operation alike)."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     if not force and os.path.exists(_LIB_PATH):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(_LIB_PATH) >= newest:
             return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,6 +78,13 @@ def _load():
             "or_nd_solve": (C.c_int, [G, _P, _P, _P, C.c_double, C.c_int, _P]),
             "or_nd_dense_solve": (C.c_int, [G, _P, _P, _P]),
             "or_nd_project": (C.c_int, [G, _P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int, _P]),
+            "or_average_planar": (None, [G, _P, _P]),
+            "or_radial_nbins": (C.c_long, [G, _IP]),
+            "or_radial_index": (None, [G, _IP, _LP]),
+            "or_average_radial": (None, [G, _IP, _P, C.c_long, _P, _LP]),
+            "or_fill_irregular": (None, [G, _IP, _P, _P]),
+            "or_fill_quadratic": (C.c_int, [G, _P, C.c_int, C.c_double, _P, _P]),
+            "or_average_to_uniform": (C.c_int, [C.c_long, _P, _LP, C.c_double, C.c_int, C.c_double, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -104,6 +112,70 @@ def _arr(a):
 
 def _p(a):
     return a.ctypes.data_as(_P)
+
+
+_IP = C.POINTER(C.c_int)
+_LP = C.POINTER(C.c_long)
+
+
+def _corner(c):
+    return (C.c_int * 3)(*[int(x) for x in c])
+
+
+# ---- base-state mapping (Sec. 3.1: lateral average and fill) ---------------------------
+
+def average_planar(geom, field):
+    """Mean of the cells at each height: (nz,)."""
+    out = np.empty(geom.n[2])
+    _load().or_average_planar(_g(geom), _p(_arr(field)), _p(out))
+    return out
+
+
+def radial_nbins(geom, corner):
+    return int(_load().or_radial_nbins(_g(geom), _corner(corner)))
+
+
+def radial_index(geom, corner):
+    """m of every cell (radius dx sqrt(0.75 + 2m)), shape (nz, ny, nx), int64."""
+    out = np.empty(cell_shape(geom), dtype=np.int64)
+    _load().or_radial_index(_g(geom), _corner(corner), out.ctypes.data_as(_LP))
+    return out
+
+
+def average_radial(geom, corner, field, nbins=None):
+    """(mean per radius m, cell count per m) of the irregular base state."""
+    nb = radial_nbins(geom, corner) if nbins is None else int(nbins)
+    out = np.empty(nb)
+    cnt = np.empty(nb, dtype=np.int64)
+    _load().or_average_radial(_g(geom), _corner(corner), _p(_arr(field)), nb, _p(out), cnt.ctypes.data_as(_LP))
+    return out, cnt
+
+
+def fill_irregular(geom, corner, base):
+    out = np.empty(cell_shape(geom))
+    _load().or_fill_irregular(_g(geom), _corner(corner), _p(_arr(base)), _p(out))
+    return out
+
+
+def fill_quadratic(geom, prof, dr, center):
+    prof = _arr(prof)
+    out = np.empty(cell_shape(geom))
+    c = np.ascontiguousarray(center, dtype=np.float64)
+    rc = _load().or_fill_quadratic(_g(geom), _p(prof), prof.size, float(dr), _p(c), _p(out))
+    if rc:
+        raise ValueError("fill_quadratic needs at least 3 radial cells")
+    return out
+
+
+def average_to_uniform(avg, count, dx, nr, dr):
+    avg = _arr(avg)
+    cnt = np.ascontiguousarray(count, dtype=np.int64)
+    out = np.empty(int(nr))
+    rc = _load().or_average_to_uniform(avg.size, _p(avg), cnt.ctypes.data_as(_LP), float(dx), int(nr), float(dr),
+                                       _p(out))
+    if rc:
+        raise ValueError("average_to_uniform needs at least 3 non-empty radii")
+    return out
 
 
 def face_shape(geom, d):
