@@ -466,7 +466,8 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     return out
 
 
-def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=True, rank=0, world=1):
+def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=True, rank=0, world=1, graph=True,
+                  fixed=None):
     """96 independent planar patches (sizes {32,48,64,96,128}^3) solved as one
     batch (one launch per phase over all patches), vs looping single FP64 solves.
     With several ranks each solves its shard of the patches (balanced by cells,
@@ -490,9 +491,15 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
         return mx.mx_mac_project_batched(ctx, geoms, [u[0] for u in us], [u[1] for u in us], [u[2] for u in us],
                                          [p.rho for p in ps], b0, [p.sbar for p in ps], phis, o)[1]
     # the batch's sweep counts from the library's autotuner (untimed), then nu1 = nu2 = 0
-    tuned, _ = mx.mx_autotune_batched(ctx, geoms, [p.u[0] for p in ps], [p.u[1] for p in ps], [p.u[2] for p in ps],
-                                      [p.rho for p in ps], b0, [p.sbar for p in ps])
-    opts = mx.default_opts(nu1=0, nu2=0)
+    if fixed:
+        a, b, _ = (int(x) for x in fixed.split(","))
+        tuned = mx.default_opts(nu1=a, nu2=b, use_graph=int(graph))
+        opts = tuned
+    else:
+        tuned, _ = mx.mx_autotune_batched(ctx, geoms, [p.u[0] for p in ps], [p.u[1] for p in ps],
+                                          [p.u[2] for p in ps], [p.rho for p in ps], b0, [p.sbar for p in ps],
+                                          base=mx.default_opts(use_graph=int(graph)))
+        opts = mx.default_opts(nu1=0, nu2=0, use_graph=int(graph))
     for i in range(warmup):
         run(sets[i], opts)
     if world > 1:
@@ -596,7 +603,8 @@ def run_other(args):
         print(json.dumps(r), flush=True)
     elif args.workload == "batched96":
         r = bench_batched(mx, W, ctx, dev, stream, steps=args.steps, warmup=args.warmup,
-                          fp64=not args.no_fp64 and world == 1, rank=rank, world=world)
+                          fp64=not args.no_fp64 and world == 1, rank=rank, world=world, graph=not args.no_graph,
+                          fixed=args.fixed)
         if rank == 0:
             print(json.dumps(r), flush=True)
     elif args.workload == "nodal-sweep":
