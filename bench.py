@@ -39,15 +39,16 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mx", choices=["mx", "reference"])
     p.add_argument("--n", type=int, default=N, help="cube edge of the planar workload")
+    p.add_argument("--star-n", type=int, default=512, help="cube edge of the average512 workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the nodal and batched workloads")
     p.add_argument("--workload", default="planar256",
-                   choices=["planar256", "star512", "nodal-sweep", "nodal384", "batched96"],
+                   choices=["planar256", "star512", "nodal-sweep", "nodal384", "batched96", "average512"],
                    help="planar256: the headline line (+ nodal384 and batched96 extras); star512: the "
                         "full-star line; nodal-sweep: one line per nodal size 64^3..512^3; nodal384 / "
-                        "batched96: that extra alone (for profiling)")
+                        "batched96 / average512: that extra alone (for profiling)")
     p.add_argument("--fixed", default=None, metavar="NU1,NU2,TILE_Z",
                    help="skip the autotuner and use these smoother settings (for profiling a fixed "
                         "configuration, e.g. the tuned one)")
@@ -371,6 +372,7 @@ def run_mx(args):
     if not args.no_extras:
         extras["nodal384"] = bench_nodal(mx, W, ctx, dev, stream, hbm=hbm)
         extras["batched96"] = bench_batched(mx, W, ctx, dev, stream, fp64=world == 1, rank=rank, world=world)
+        extras["average512"] = bench_base(mx, W, ctx, dev, stream, hbm=hbm, cpu=rank == 0 and world == 1)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
@@ -522,6 +524,78 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
     return out
 
 
+def bench_base(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, cpu=True, n=512):
+    """Lateral Average and Fill (Sec. 3.1) on the 512^3 full star's density, centre
+    on the corner (256, 256, 256): one step = Average onto the irregular base state
+    (97,921 radial bins) + Fill back onto the cells.  Also times the planar Average
+    (planar 256^3 density), the uniform-base-state interpolations and the oracle's
+    radial average on a 256^3 sample.  The 1 GiB field is larger than L2."""
+    import torch
+    w = W.star512(device=dev, n=n)
+    g = w.geom
+    c = tuple(e // 2 for e in g.n)
+    nb = mx.mx_radial_nbins(g, c)
+    avg = torch.empty(nb, dtype=torch.float64, device=dev)
+    out = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=dev)
+    rho = w.rho
+
+    def step(i):
+        mx.mx_average_radial(ctx, g, c, rho, avg)
+        mx.mx_fill_radial(ctx, g, c, avg, out)
+    for i in range(warmup):
+        step(i)
+    ms, _ = timed(step, steps, stream)
+    ms_avg, _ = timed(lambda i: mx.mx_average_radial(ctx, g, c, rho, avg), steps, stream)
+    ms_fill, _ = timed(lambda i: mx.mx_fill_radial(ctx, g, c, avg, out), steps, stream)
+    nr = 4 * g.n[0]
+    dr = g.dx / 4
+    prof = torch.empty(nr, dtype=torch.float64, device=dev)
+    mx.mx_radial_to_uniform(ctx, g, c, avg, dr, prof)
+    ms_uni, _ = timed(lambda i: mx.mx_radial_to_uniform(ctx, g, c, avg, dr, prof), steps, stream)
+    mx.mx_fill_uniform(ctx, g, c, prof, dr, out)
+    ms_fu, _ = timed(lambda i: mx.mx_fill_uniform(ctx, g, c, prof, dr, out), steps, stream)
+    N = g.ncell
+    bytes_avg = 8.0 * N + 8.0 * nb
+    bytes_fill = 8.0 * N
+    a_avg = bytes_avg / (ms_avg / steps * 1e-3) / 1e9
+    a_fill = bytes_fill / (ms_fill / steps * 1e-3) / 1e9
+    del w, out
+    torch.cuda.empty_cache()
+    wp = W.planar256(device=dev)
+    pp = torch.empty(wp.geom.n[2], dtype=torch.float64, device=dev)
+    mx.mx_average_planar(ctx, wp.geom, wp.rho, pp)
+    ms_pl, _ = timed(lambda i: mx.mx_average_planar(ctx, wp.geom, wp.rho, pp), steps, stream)
+    a_pl = 8.0 * wp.geom.ncell / (ms_pl / steps * 1e-3) / 1e9
+    r = {"workload": f"star{n} lateral average + fill", "metric": f"Average + Fill round trips/s (full star {n}^3, "
+         "irregular base state)", "value": steps * 1e3 / ms, "unit": "round trips/s", "ms_per_step": ms / steps,
+         "cells": N, "radial_bins": nb,
+         "average_radial": {"ms": ms_avg / steps, "GB_s": a_avg, "launches": 2},
+         "fill_radial": {"ms": ms_fill / steps, "GB_s": a_fill, "frac": a_fill / hbm, "launches": 1},
+         "radial_to_uniform": {"ms": ms_uni / steps, "nr": nr, "launches": 1},
+         "fill_uniform": {"ms": ms_fu / steps, "launches": 2},
+         "average_planar_256": {"ms": ms_pl / steps, "GB_s": a_pl, "frac": a_pl / hbm, "launches": 2},
+         "roofline": {"bound": "hbm", "achieved": round(a_avg, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(a_avg / hbm, 4), "traffic": None,
+                      "kernel": "mx_average_radial (fold + bin kernels), 8 B/cell read + 8 B/bin written",
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+         "gpu_launches_per_step": 3}
+    if cpu:
+        import numpy as np
+        import oracle as O
+        O.build()
+        ns = min(n, 256)
+        ws = W.star512(device="cpu", n=ns)
+        f = ws.rho.numpy()
+        t0 = time.perf_counter()
+        O.average_radial(ws.geom, (ns // 2,) * 3, f)
+        dt = time.perf_counter() - t0
+        r["cpu_baseline"] = {"value": round((ns / n) ** 3 / dt, 4), "unit": f"averages/s of the {n}^3 field",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"oracle radial average of the star recipe at {ns}^3 ({dt:.2f} s), "
+                                       f"scaled by ({ns}/{n})^3"}
+    return r
+
+
 def cpu_baseline_sample(n_sample, n_full, reps=1):
     """The FP64 oracle (single-threaded C) solving the same recipe at n_sample^3;
     its solves/s is scaled by (n_sample/n_full)^3 to the full workload (its cost
@@ -597,7 +671,11 @@ def run_other(args):
     except (OSError, ValueError):
         peaks = {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    if args.workload == "nodal384":
+    if args.workload == "average512":
+        r = bench_base(mx, W, ctx, dev, stream, hbm=hbm, steps=args.steps, warmup=args.warmup,
+                       cpu=not args.no_cpu_baseline, n=args.star_n)
+        print(json.dumps(r), flush=True)
+    elif args.workload == "nodal384":
         r = bench_nodal(mx, W, ctx, dev, stream, n=384, steps=args.steps, warmup=args.warmup,
                         fp64=not args.no_fp64, hbm=hbm, graph=not args.no_graph, fixed=args.fixed)
         print(json.dumps(r), flush=True)

@@ -127,6 +127,58 @@ int mx_device_supported(int device);
 mx_status mx_fill_base_state(mx_ctx *ctx, const mx_geom *geom, int spherical, const double *prof,
                              int nr, double dr, const double center[3], double *out_cells);
 
+/* ---- Lateral average and fill of the base state (Sec. 3.1, Eq. radii) --------------
+ * Cell arrays are device doubles of n0 n1 n2 entries, x fastest; the boundary
+ * types in geom are not used.  The calls queue work on the context's stream and
+ * return without synchronising; sums run in double-float arithmetic in a fixed
+ * order, so repeated calls give identical bits.
+ *
+ * Spherical geometry puts the centre of the star on the cell corner corner[3]
+ * (host array of three integer corner indices, each within +-2^20; the corner
+ * may lie outside the box).  The centre of cell (i,j,k) is then at distance
+ * dx sqrt(0.75 + 2m) from it, m = T(i-c0) + T(j-c1) + T(k-c2), T(a) = a(a+1)/2:
+ * bin m of the irregularly spaced base state.  The first call for a given
+ * (n, corner) builds and caches a plan on the context (host work proportional to
+ * n1 n2 plus a device allocation of about 8 bytes per cell at most). */
+
+/* number of radial bins (largest m + 1) for the box and corner; -1 if the corner
+ * is out of range or the count reaches 2^31.  Host only. */
+long long mx_radial_nbins(const mx_geom *geom, const int corner[3]);
+
+/* Planar Average: prof[k] = mean of field over plane k (n2 doubles out). */
+mx_status mx_average_planar(mx_ctx *ctx, const mx_geom *geom, const double *field, double *prof);
+
+/* Spherical Average onto the irregular base state: avg[m] = mean of field over
+ * the cells of bin m (0 for bins without cells), count[m] = their number
+ * (int64; count may be NULL).  nbins must equal mx_radial_nbins (else
+ * MX_ERR_ARG).  MX_ERR_ARG also for n0 above 12000 or a corner whose row radii
+ * span more than 2^26 bins; MX_ERR_OOM if the plan cannot be allocated. */
+mx_status mx_average_radial(mx_ctx *ctx, const mx_geom *geom, const int corner[3], const double *field,
+                            long long nbins, double *avg, long long *count);
+
+/* Fill from the irregular base state, without interpolation: out(i,j,k) =
+ * base[m(i,j,k)] (base: nbins device doubles). */
+mx_status mx_fill_radial(mx_ctx *ctx, const mx_geom *geom, const int corner[3], const double *base,
+                         long long nbins, double *out);
+
+/* Average onto a uniform base state prof[j] at radii (j + 1/2) dr (nr >= 1
+ * doubles out) from the bin means avg (nbins doubles, as mx_average_radial
+ * writes them): the quadratic (3-point Lagrange) interpolant through the
+ * non-empty bin whose radius is nearest to (j + 1/2) dr (the smaller one on a
+ * tie) and the non-empty bins on either side, the triple kept one bin inside at
+ * either end.  MX_ERR_ARG with fewer than 3 non-empty bins. */
+mx_status mx_radial_to_uniform(mx_ctx *ctx, const mx_geom *geom, const int corner[3], const double *avg, int nr,
+                               double dr, double *prof);
+
+/* Fill from a uniform base state prof (nr >= 3 device doubles at radii
+ * (j + 1/2) dr) by quadratic interpolation: each cell takes the 3-point Lagrange
+ * interpolant at its radius through the radial cell centres jc - 1, jc, jc + 1,
+ * jc = floor(r / dr) kept within [1, nr - 2].  All cells of a bin share their
+ * radius, so the value is computed once per bin (in the context's plan) and
+ * gathered. */
+mx_status mx_fill_uniform(mx_ctx *ctx, const mx_geom *geom, const int corner[3], const double *prof, int nr,
+                          double dr, double *out);
+
 /* MAC projection (Steps 3 and 7; Eq. div1, div2; Appendix A).
  * ux, uy, uz: face velocities U^ADV,dagger (in) -> projected U^ADV (out).
  * rho, beta0, sbar: cell fields; sbar is the whole bracket of the constraint's

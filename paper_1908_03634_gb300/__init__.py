@@ -53,6 +53,7 @@ class MXError(RuntimeError):
 _lib = None
 _VP = C.c_void_p
 _DP = C.c_void_p
+_IP3 = C.c_int * 3
 
 
 def load():
@@ -86,6 +87,12 @@ def load():
                                           C.POINTER(C.c_double)]),
         "mx_mac_project_batched": (C.c_int, [_VP, C.c_int, G, C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP),
                                              C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), C.POINTER(_DP), O, I]),
+        "mx_radial_nbins": (C.c_longlong, [G, _IP3]),
+        "mx_average_planar": (C.c_int, [_VP, G, _DP, _DP]),
+        "mx_average_radial": (C.c_int, [_VP, G, _IP3, _DP, C.c_longlong, _DP, _VP]),
+        "mx_fill_radial": (C.c_int, [_VP, G, _IP3, _DP, C.c_longlong, _DP]),
+        "mx_radial_to_uniform": (C.c_int, [_VP, G, _IP3, _DP, C.c_int, C.c_double, _DP]),
+        "mx_fill_uniform": (C.c_int, [_VP, G, _IP3, _DP, C.c_int, C.c_double, _DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -100,7 +107,8 @@ def exported_symbols():
     return ["mx_create", "mx_destroy", "mx_set_stream", "mx_last_error", "mx_default_opts", "mx_device_supported",
             "mx_fill_base_state", "mx_mac_project", "mx_nodal_project", "mx_apply_op", "mx_residual",
             "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc",
-            "mx_autotune", "mx_tune_lookup", "mx_autotune_batched"]
+            "mx_autotune", "mx_tune_lookup", "mx_autotune_batched", "mx_radial_nbins", "mx_average_planar",
+            "mx_average_radial", "mx_fill_radial", "mx_radial_to_uniform", "mx_fill_uniform"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -195,6 +203,59 @@ def mx_fill_base_state(ctx, geom, spherical, prof, dr, center, out):
     c = (C.c_double * 3)(*center)
     st = load().mx_fill_base_state(ctx, C.byref(g), int(spherical), _ptr(prof, None, "prof"), int(prof.numel()),
                                    float(dr), c, _ptr(out, cell_shape(geom), "out"))
+    return _check(ctx, st)
+
+
+# ---- lateral average and fill (Sec. 3.1) ------------------------------------------------
+
+def _corner(corner):
+    return _IP3(*[int(x) for x in corner])
+
+
+def mx_radial_nbins(geom, corner):
+    n = load().mx_radial_nbins(C.byref(make_geom(geom)), _corner(corner))
+    if n < 0:
+        raise ValueError("mx_radial_nbins: corner out of range")
+    return int(n)
+
+
+def mx_average_planar(ctx, geom, field, prof):
+    st = load().mx_average_planar(ctx, C.byref(make_geom(geom)), _ptr(field, cell_shape(geom), "field"),
+                                  _ptr(prof, (geom.n[2],), "prof"))
+    return _check(ctx, st)
+
+
+def mx_average_radial(ctx, geom, corner, field, avg, count=None):
+    """avg: float64 (nbins,); count: int64 (nbins,) or None."""
+    import torch
+    nb = avg.numel()
+    cp = None
+    if count is not None:
+        if not (isinstance(count, torch.Tensor) and count.is_cuda and count.dtype == torch.int64
+                and count.is_contiguous() and count.numel() == nb):
+            raise TypeError("count: expected a contiguous int64 CUDA tensor of nbins entries")
+        cp = _VP(count.data_ptr())
+    st = load().mx_average_radial(ctx, C.byref(make_geom(geom)), _corner(corner),
+                                  _ptr(field, cell_shape(geom), "field"), nb, _ptr(avg, (nb,), "avg"), cp)
+    return _check(ctx, st)
+
+
+def mx_fill_radial(ctx, geom, corner, base, out):
+    nb = base.numel()
+    st = load().mx_fill_radial(ctx, C.byref(make_geom(geom)), _corner(corner), _ptr(base, (nb,), "base"), nb,
+                               _ptr(out, cell_shape(geom), "out"))
+    return _check(ctx, st)
+
+
+def mx_radial_to_uniform(ctx, geom, corner, avg, dr, prof):
+    st = load().mx_radial_to_uniform(ctx, C.byref(make_geom(geom)), _corner(corner), _ptr(avg, None, "avg"),
+                                     int(prof.numel()), float(dr), _ptr(prof, (prof.numel(),), "prof"))
+    return _check(ctx, st)
+
+
+def mx_fill_uniform(ctx, geom, corner, prof, dr, out):
+    st = load().mx_fill_uniform(ctx, C.byref(make_geom(geom)), _corner(corner), _ptr(prof, None, "prof"),
+                                int(prof.numel()), float(dr), _ptr(out, cell_shape(geom), "out"))
     return _check(ctx, st)
 
 

@@ -1,0 +1,673 @@
+// Base-state mapping (Sec. 3.1): the lateral Average of a cell field onto the
+// one-dimensional base state and the Fill of a base state onto the cells.
+//
+// Planar: the base state is aligned with the cell heights; Average is the
+// arithmetic mean of each z plane (Fill is injection, mx_fill_base_state).
+//
+// Spherical, with the centre of the star on the cell corner c: the centre of
+// cell (i, j, k) lies at (a + 1/2, b + 1/2, e + 1/2) dx from it, a = i - c0,
+// b = j - c1, e = k - c2, so its radius is dx sqrt(0.75 + 2m) with
+// m = T(a) + T(b) + T(e), T(a) = a (a + 1) / 2 (Eq. radii).  The irregular base
+// state holds the mean over the cells of each m; its Fill reads bin m of every
+// cell.  The uniform base state (radial cells (j + 1/2) dr) is filled by
+// quadratic interpolation in r: all cells of a bin share their radius, so the
+// interpolant is evaluated once per bin and gathered.  The Average onto the
+// uniform base state interpolates the bin means quadratically.
+//
+// The radial Average runs without atomics, in a fixed order (deterministic):
+//   1. fold: the rows (j, k) with equal s = T(b) + T(e) form a group; each CTA
+//      sums the rows of its groups column by column (one pass over the field,
+//      whole rows, coalesced) and folds the mirror columns a and -1 - a (equal
+//      T) together into G[group][t], t = (a >= 0 ? a : -1 - a);
+//   2. bins: bin m = s + T(t) sums G[group(s)][t] over t, one lane per bin.
+// Sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of FP32; the
+// fold adds row pairs in FP64 first, about half an FP64 operation per cell,
+// which the FP64 pipe keeps up with); the bin means are divided in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "mx_dfmath.cuh"
+#include "mx_internal.cuh"
+
+namespace {
+
+constexpr int FOLD_THREADS = 256;
+constexpr int BIN_THREADS = 256;
+constexpr int MAX_RADIAL_PLANS = 4;
+
+__host__ __device__ __forceinline__ long long tri(long long t) { return t * (t + 1) / 2; }
+
+// t range of T(a) over a in [lo, hi]: t = a for a >= 0, -1 - a for a < 0
+void t_range(long long lo, long long hi, long long &tmin, long long &tmax) {
+    if (lo >= 0) {
+        tmin = lo;
+        tmax = hi;
+    } else if (hi < 0) {
+        tmin = -1 - hi;
+        tmax = -1 - lo;
+    } else {
+        tmin = 0;
+        tmax = std::max(hi, -1 - lo);
+    }
+}
+
+}  // namespace
+
+struct RadialPlan {
+    int n[3], c[3];
+    long long nbins, smin, smax, nne;
+    int kmin, kmax, wt;  // column index t in [kmin, kmax], wt = kmax - kmin + 1
+    int ngroups, nbatch, nrows;
+    int *rows;           // row ids j + ny k, ordered by s
+    int *gstart;         // first row of each group (ngroups + 1)
+    int *grp;            // group of s (index s - smin), -1 where no row has that s
+    int *bstart;         // first group of each fold batch (nbatch + 1)
+    long long *count;    // cells per bin
+    long long *gsv;      // s of each group
+    int *nonempty;       // bins with cells, increasing
+    float2 *G;           // folded column sums, t-major: G[t * ngroups + g]
+    int gmax;            // most groups in one fold batch
+    double *tab;         // per-bin values of the uniform fill
+    void *mem;
+    long long last_use;
+};
+
+struct RadDev {
+    int nx, ny, c0, c1, c2, kmin, kmax, wt, ngroups;
+    long long nbins, smin, smax;
+    const int *rows, *gstart, *grp, *bstart;
+    const long long *count;
+};
+
+static RadDev rad_dev(const RadialPlan *p) {
+    RadDev d;
+    d.nx = p->n[0];
+    d.ny = p->n[1];
+    d.c0 = p->c[0];
+    d.c1 = p->c[1];
+    d.c2 = p->c[2];
+    d.kmin = p->kmin;
+    d.kmax = p->kmax;
+    d.wt = p->wt;
+    d.ngroups = p->ngroups;
+    d.nbins = p->nbins;
+    d.smin = p->smin;
+    d.smax = p->smax;
+    d.rows = p->rows;
+    d.gstart = p->gstart;
+    d.grp = p->grp;
+    d.bstart = p->bstart;
+    d.count = p->count;
+    return d;
+}
+
+// ---------------------------------------------------------------------------------------
+// kernels
+
+// Double-float accumulator with deferred renormalisation: TwoSum of the high
+// parts, the low parts and the TwoSum error gathered in l (tens of terms per
+// accumulator, each below 2^-24 of the running sum, so l stays exact to about
+// 2^-48 of it); norm() renormalises once at the end.
+struct DfAcc {
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(dfloat x) {
+        const float s = h + x.h;
+        const float bb = s - h;
+        l += ((h - (s - bb)) + (x.h - bb)) + x.l;
+        h = s;
+    }
+    __device__ __forceinline__ dfloat norm() const { return df_norm(h, l); }
+};
+
+// 1. fold: one CTA per batch of whole groups (at most gmax of them); racc holds one
+// row of column sums, gbuf the batch's folded rows, written out t-major
+// (GT[t][g], runs of the batch's consecutive groups).  V = 2: each thread takes
+// column pairs as 16-byte loads (n0 even, so every row starts on a 16-byte
+// boundary).  Rows come in batches of 8 loads per column (16 in flight per
+// thread); rows are added in pairs in FP64 (the FP64 pipe is otherwise idle) and
+// the pair sums accumulate in double-float.
+template <int V>
+__global__ void __launch_bounds__(FOLD_THREADS) rad_fold_kernel(const double *__restrict__ f, RadDev P,
+                                                                float2 *__restrict__ GT) {
+    extern __shared__ float2 smem_f2[];
+    float2 *racc = smem_f2;
+    float2 *gbuf = smem_f2 + P.nx;
+    const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
+    const int nx = P.nx, nv = nx / V, wt = P.wt;
+    for (int g = g0; g < g1; g++) {
+        const int r0 = P.gstart[g], r1 = P.gstart[g + 1];
+        for (int q = threadIdx.x; q < nv; q += FOLD_THREADS) {
+            DfAcc acc[V];
+            for (int r = r0; r < r1; r += 8) {
+                double v[8][V];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+#pragma unroll
+                    for (int w = 0; w < V; w++) v[u][w] = 0.0;
+                    if (r + u < r1) {  // uniform over the CTA
+                        const double *src = f + (long long)P.rows[r + u] * nx + (long long)q * V;
+                        if constexpr (V == 2) {
+                            const double2 t = __ldcs(reinterpret_cast<const double2 *>(src));
+                            v[u][0] = t.x;
+                            v[u][V - 1] = t.y;
+                        } else {
+                            v[u][0] = __ldcs(src);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u += 2)
+                    if (r + u < r1) {
+#pragma unroll
+                        for (int w = 0; w < V; w++) acc[w].add(df_split(v[u][w] + v[u + 1][w]));
+                    }
+            }
+#pragma unroll
+            for (int w = 0; w < V; w++) {
+                const dfloat a = acc[w].norm();
+                racc[q * V + w] = make_float2(a.h, a.l);
+            }
+        }
+        __syncthreads();
+        float2 *gb = gbuf + (long long)(g - g0) * wt;
+        for (int t = threadIdx.x; t < wt; t += FOLD_THREADS) {
+            const int k = P.kmin + t;
+            const int i1 = P.c0 + k, i2 = P.c0 - 1 - k;  // a = k and a = -1 - k
+            dfloat v{0.f, 0.f};
+            if (i1 >= 0 && i1 < nx) v = dfloat{racc[i1].x, racc[i1].y};
+            if (i2 >= 0 && i2 < nx) v = df_add(v, dfloat{racc[i2].x, racc[i2].y});
+            gb[t] = make_float2(v.h, v.l);
+        }
+        __syncthreads();
+    }
+    const int ng = g1 - g0;
+    for (int e = threadIdx.x; e < ng * wt; e += FOLD_THREADS) {
+        const int t = e / ng, j = e - t * ng;
+        GT[(long long)t * P.ngroups + g0 + j] = gbuf[(long long)j * wt + t];
+    }
+}
+
+// largest t >= 0 with T(t) <= x (-1 for x < 0), x < 2^31: a float estimate corrected
+// with exact integer tests (the estimate is within one of the answer)
+__device__ __forceinline__ long long floor_tinv(long long x) {
+    if (x < 0) return -1;
+    long long t = (long long)((sqrtf(8.0f * (float)x + 1.0f) - 1.0f) * 0.5f);
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+        if (tri(t) > x) t--;
+        else if (tri(t + 1) <= x) t++;
+    }
+    return t;
+}
+
+// 2. bins: a CTA per 32 consecutive bins, lane = bin; the t range splits into one
+// contiguous slice per warp (for each t the lanes read consecutive s in grp and
+// neighbouring groups in GT[t][.]); the warps' partial sums combine in warp order.
+constexpr int BIN_WARPS = BIN_THREADS / 32;
+__global__ void __launch_bounds__(BIN_THREADS) rad_bin_kernel(RadDev P, const float2 *__restrict__ GT,
+                                                              double *__restrict__ avg) {
+    __shared__ float2 part[BIN_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long m0 = (long long)blockIdx.x * 32, m = m0 + lane;
+    const long long mlast = min(m0 + 31, P.nbins - 1);
+    const long long tlo = max((long long)P.kmin, floor_tinv(m0 - P.smax - 1) + 1);
+    const long long thi = min((long long)P.kmax, floor_tinv(mlast - P.smin));
+    const long long chunk = (thi - tlo + BIN_WARPS) / BIN_WARPS;  // ceil(nt / warps), nt may be 0
+    const long long ta = tlo + w * chunk, tb = min(thi, ta + chunk - 1);
+    DfAcc acc;
+    for (long long t = ta; t <= tb; t += 4) {
+        int g[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long s = m - tri(t + u);
+            g[u] = (t + u <= tb && s >= P.smin && s <= P.smax && m < P.nbins) ? __ldg(P.grp + (s - P.smin)) : -1;
+        }
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            v[u] = g[u] >= 0 ? __ldg(GT + (t + u - P.kmin) * (long long)P.ngroups + g[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; u++) acc.add(dfloat{v[u].x, v[u].y});
+    }
+    const dfloat a = acc.norm();
+    part[w][lane] = make_float2(a.h, a.l);
+    __syncthreads();
+    if (w == 0 && m < P.nbins) {
+        dfloat sum{part[0][lane].x, part[0][lane].y};
+        for (int q = 1; q < BIN_WARPS; q++) sum = df_add(sum, dfloat{part[q][lane].x, part[q][lane].y});
+        const long long cnt = P.count[m];
+        avg[m] = cnt ? df_to_double(sum) / (double)cnt : 0.0;
+    }
+}
+
+// Fill from per-bin values, out(i, j, k) = v[T(a) + s], s = T(b) + T(e): the rows of a
+// group share s, so each group's row is gathered once (into smem) and stored to all
+// its rows (16-byte streaming stores for V = 2)
+template <int V>
+__global__ void __launch_bounds__(FOLD_THREADS) rad_fill_kernel(RadDev P, const long long *__restrict__ gs,
+                                                                const double *__restrict__ v,
+                                                                double *__restrict__ out) {
+    extern __shared__ double rowv[];
+    const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
+    const int nx = P.nx, nv = nx / V;
+    for (int g = g0; g < g1; g++) {
+        const long long s = gs[g];
+        for (int i = threadIdx.x; i < nx; i += FOLD_THREADS) rowv[i] = __ldg(v + tri((long long)(i - P.c0)) + s);
+        __syncthreads();
+        const int r0 = P.gstart[g], r1 = P.gstart[g + 1];
+        for (int r = r0; r < r1; r++) {
+            double *dst = out + (long long)P.rows[r] * nx;
+            for (int q = threadIdx.x; q < nv; q += FOLD_THREADS) {
+                if constexpr (V == 2) __stcs(reinterpret_cast<double2 *>(dst) + q, make_double2(rowv[2 * q], rowv[2 * q + 1]));
+                else __stcs(dst + q, rowv[q]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// 3-point Lagrange value at r, every operation rounded on its own (no contraction)
+__device__ __forceinline__ double lagrange3_rn(double r, double x0, double y0, double x1, double y1, double x2,
+                                               double y2) {
+    const double a = __ddiv_rn(__dmul_rn(__dmul_rn(y0, __dsub_rn(r, x1)), __dsub_rn(r, x2)),
+                               __dmul_rn(__dsub_rn(x0, x1), __dsub_rn(x0, x2)));
+    const double b = __ddiv_rn(__dmul_rn(__dmul_rn(y1, __dsub_rn(r, x0)), __dsub_rn(r, x2)),
+                               __dmul_rn(__dsub_rn(x1, x0), __dsub_rn(x1, x2)));
+    const double c = __ddiv_rn(__dmul_rn(__dmul_rn(y2, __dsub_rn(r, x0)), __dsub_rn(r, x1)),
+                               __dmul_rn(__dsub_rn(x2, x0), __dsub_rn(x2, x1)));
+    return __dadd_rn(__dadd_rn(a, b), c);
+}
+
+__device__ __forceinline__ double bin_radius(long long m, double dx) {
+    return __dmul_rn(dx, __dsqrt_rn(__dadd_rn(0.75, __dmul_rn(2.0, (double)m))));
+}
+
+// uniform fill, per bin: the quadratic through the radial cell centres jc-1, jc, jc+1,
+// jc the radial cell holding r (kept one cell inside either end)
+__global__ void rad_uniform_table_kernel(long long nbins, double dx, const double *__restrict__ prof, int nr,
+                                         double dr, double *__restrict__ tab) {
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nbins) return;
+    const double r = bin_radius(m, dx);
+    long long jc = (long long)floor(__ddiv_rn(r, dr));
+    jc = jc < 1 ? 1 : (jc > nr - 2 ? nr - 2 : jc);
+    tab[m] = lagrange3_rn(r, __dmul_rn((double)jc - 0.5, dr), prof[jc - 1], __dmul_rn((double)jc + 0.5, dr),
+                          prof[jc], __dmul_rn((double)jc + 1.5, dr), prof[jc + 1]);
+}
+
+// Average onto the uniform base state: at r = (j + 1/2) dr, the quadratic through the
+// non-empty bin of radius nearest to r (the smaller on a tie) and its non-empty
+// neighbours (kept one inside either end)
+__global__ void rad_to_uniform_kernel(const int *__restrict__ ne, long long nne, double dx,
+                                      const double *__restrict__ avg, int nr, double dr, double *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nr) return;
+    const double r = __dmul_rn((double)j + 0.5, dr);
+    long long lo = 0, hi = nne;  // first q with radius(ne[q]) >= r
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (bin_radius(ne[mid], dx) < r) lo = mid + 1;
+        else hi = mid;
+    }
+    long long best;
+    if (lo == 0) best = 0;
+    else if (lo == nne) best = nne - 1;
+    else {
+        const double d0 = fabs(__dsub_rn(bin_radius(ne[lo - 1], dx), r));
+        const double d1 = fabs(__dsub_rn(bin_radius(ne[lo], dx), r));
+        best = d1 < d0 ? lo : lo - 1;
+    }
+    best = best < 1 ? 1 : (best > nne - 2 ? nne - 2 : best);
+    const long long m0 = ne[best - 1], m1 = ne[best], m2 = ne[best + 1];
+    out[j] = lagrange3_rn(r, bin_radius(m0, dx), avg[m0], bin_radius(m1, dx), avg[m1], bin_radius(m2, dx), avg[m2]);
+}
+
+// planar: per-(plane, chunk) double-float sums, then one warp per plane
+constexpr int PL_THREADS = 256;
+__device__ __forceinline__ dfloat warp_df_sum(dfloat a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const dfloat b{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+        a = df_add(a, b);
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__restrict__ f, long long nxy,
+                                                               int nchunk, float2 *__restrict__ part) {
+    __shared__ float2 ws[PL_THREADS / 32];
+    const long long len = (nxy + nchunk - 1) / nchunk;
+    const long long b0 = (long long)blockIdx.x * len, b1 = min(nxy, b0 + len);
+    const double *p = f + (long long)blockIdx.y * nxy;
+    dfloat acc{0.f, 0.f};
+    long long q = b0 + threadIdx.x;
+    for (; q + 3 * PL_THREADS < b1; q += 4 * PL_THREADS) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = __ldcs(p + q + u * PL_THREADS);
+#pragma unroll
+        for (int u = 0; u < 4; u++) acc = df_add(acc, df_split(v[u]));
+    }
+    for (; q < b1; q += PL_THREADS) acc = df_add(acc, df_split(__ldcs(p + q)));
+    acc = warp_df_sum(acc);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = make_float2(acc.h, acc.l);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dfloat s{ws[0].x, ws[0].y};
+        for (int w = 1; w < PL_THREADS / 32; w++) s = df_add(s, dfloat{ws[w].x, ws[w].y});
+        part[(long long)blockIdx.y * nchunk + blockIdx.x] = make_float2(s.h, s.l);
+    }
+}
+
+__global__ void plane_final_kernel(const float2 *__restrict__ part, int nz, int nchunk, long long nxy,
+                                   double *__restrict__ out) {
+    const int k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (k >= nz) return;
+    dfloat acc{0.f, 0.f};
+    for (int c = threadIdx.x & 31; c < nchunk; c += 32) {
+        const float2 v = part[(long long)k * nchunk + c];
+        acc = df_add(acc, dfloat{v.x, v.y});
+    }
+    acc = warp_df_sum(acc);
+    if ((threadIdx.x & 31) == 0) out[k] = df_to_double(acc) / (double)nxy;
+}
+
+// ---------------------------------------------------------------------------------------
+// plans (host)
+
+static bool radial_ranges(const mx_geom *g, const int c[3], long long tmin[3], long long tmax[3], long long &nbins) {
+    for (int d = 0; d < 3; d++) {
+        if (g->n[d] < 1 || c[d] < -(1 << 20) || c[d] > (1 << 20)) return false;
+        t_range(-(long long)c[d], (long long)g->n[d] - 1 - c[d], tmin[d], tmax[d]);
+    }
+    nbins = tri(tmax[0]) + tri(tmax[1]) + tri(tmax[2]) + 1;
+    return nbins < (1LL << 31);
+}
+
+static void free_radial_plan(RadialPlan *p) {
+    if (!p) return;
+    if (p->mem) cudaFree(p->mem);
+    delete p;
+}
+
+void destroy_radial_plans(mx_ctx *c) {
+    for (RadialPlan *p : c->rplans) free_radial_plan(p);
+    c->rplans.clear();
+    if (c->base_tmp) cudaFree(c->base_tmp);
+    c->base_tmp = nullptr;
+    c->base_tmp_bytes = 0;
+}
+
+static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corner[3], RadialPlan **out) {
+    for (RadialPlan *p : c->rplans)
+        if (p->n[0] == geom->n[0] && p->n[1] == geom->n[1] && p->n[2] == geom->n[2] && p->c[0] == corner[0] &&
+            p->c[1] == corner[1] && p->c[2] == corner[2]) {
+            p->last_use = ++c->use_counter;
+            *out = p;
+            return MX_OK;
+        }
+    long long tmin[3], tmax[3], nbins;
+    if (!radial_ranges(geom, corner, tmin, tmax, nbins))
+        return set_err(c, MX_ERR_ARG, "radial: corner out of range or too many bins");
+    const int nx = geom->n[0], ny = geom->n[1], nz = geom->n[2];
+    if (nx > 12000) return set_err(c, MX_ERR_ARG, "radial: n[0] above 12000");  // row buffers in smem
+    const long long nrows = (long long)ny * nz;
+    if (nrows >= (1LL << 31)) return set_err(c, MX_ERR_ARG, "radial: too many rows");
+    const long long smin = tri(tmin[1]) + tri(tmin[2]), smax = tri(tmax[1]) + tri(tmax[2]);
+    const long long ns = smax - smin + 1;
+    if (ns > (1LL << 26)) return set_err(c, MX_ERR_ARG, "radial: corner too far from the box");
+    // rows grouped by s (counting sort, stable in the row id)
+    std::vector<int> scount(ns + 1, 0), rows(nrows), grp(ns, -1), gstart;
+    std::vector<long long> gs;
+    for (long long r = 0; r < nrows; r++) {
+        const long long j = r % ny, k = r / ny;
+        scount[tri(j - corner[1]) + tri(k - corner[2]) - smin + 1]++;
+    }
+    for (long long s = 0; s < ns; s++) scount[s + 1] += scount[s];
+    {
+        std::vector<int> pos(scount.begin(), scount.end() - 1);
+        for (long long r = 0; r < nrows; r++) {
+            const long long j = r % ny, k = r / ny;
+            rows[pos[tri(j - corner[1]) + tri(k - corner[2]) - smin]++] = int(r);
+        }
+    }
+    for (long long s = 0; s < ns; s++)
+        if (scount[s + 1] > scount[s]) {
+            grp[s] = int(gstart.size());
+            gstart.push_back(scount[s]);
+            gs.push_back(s + smin);
+        }
+    const int ngroups = int(gstart.size());
+    gstart.push_back(int(nrows));
+    // fold batches: whole groups, about rb rows and at most gmax groups each (the
+    // batch's folded rows are staged in 32 KB of shared memory, or one row)
+    const long long kmin_ = tmin[0], wt_ = tmax[0] - tmin[0] + 1;
+    const long long rb = std::min(128LL, std::max(8LL, nrows / 4096));
+    const int gmax = int(std::max(1LL, std::min(64LL, 4096 / wt_)));
+    (void)kmin_;
+    std::vector<int> bstart{0};
+    for (int g = 0; g < ngroups; g++) {
+        const long long in_batch = gstart[g] - gstart[bstart.back()];
+        if (g > bstart.back() && (in_batch >= rb || g - bstart.back() >= gmax)) bstart.push_back(g);
+    }
+    bstart.push_back(ngroups);
+    const int nbatch = int(bstart.size()) - 1;
+    // cells per bin: rows of the group times the columns of each t
+    const long long kmin = tmin[0], kmax = tmax[0], wt = kmax - kmin + 1;
+    std::vector<long long> count(nbins, 0);
+    for (int g = 0; g < ngroups; g++) {
+        const long long nr = gstart[g + 1] - gstart[g];
+        for (long long t = kmin; t <= kmax; t++) {
+            const long long i1 = corner[0] + t, i2 = corner[0] - 1 - t;
+            const long long mult = (i1 >= 0 && i1 < nx) + (i2 >= 0 && i2 < nx);
+            count[gs[g] + tri(t)] += nr * mult;
+        }
+    }
+    std::vector<int> ne;
+    for (long long m = 0; m < nbins; m++)
+        if (count[m] > 0) ne.push_back(int(m));
+
+    RadialPlan *p = new RadialPlan();
+    for (int d = 0; d < 3; d++) {
+        p->n[d] = geom->n[d];
+        p->c[d] = corner[d];
+    }
+    p->nbins = nbins;
+    p->smin = smin;
+    p->smax = smax;
+    p->kmin = int(kmin);
+    p->kmax = int(kmax);
+    p->wt = int(wt);
+    p->ngroups = ngroups;
+    p->gmax = gmax;
+    p->nbatch = nbatch;
+    p->nrows = int(nrows);
+    p->nne = (long long)ne.size();
+    Bump b{nullptr, 0};
+    auto carve = [&](Bump &bb) {
+        p->rows = bb.take<int>(nrows);
+        p->gstart = bb.take<int>(ngroups + 1);
+        p->grp = bb.take<int>(ns);
+        p->bstart = bb.take<int>(nbatch + 1);
+        p->count = bb.take<long long>(nbins);
+        p->gsv = bb.take<long long>(std::max(1, ngroups));
+        p->nonempty = bb.take<int>(std::max<size_t>(1, ne.size()));
+        p->G = bb.take<float2>((size_t)ngroups * wt);
+        p->tab = bb.take<double>(nbins);
+    };
+    carve(b);
+    if (cudaMalloc(&p->mem, b.off) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return set_err(c, MX_ERR_OOM, "radial: plan allocation failed");
+    }
+    Bump b2{(char *)p->mem, 0};
+    carve(b2);
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(p->rows, rows.data(), rows.size() * sizeof(int));
+    up(p->gstart, gstart.data(), gstart.size() * sizeof(int));
+    up(p->grp, grp.data(), grp.size() * sizeof(int));
+    up(p->bstart, bstart.data(), bstart.size() * sizeof(int));
+    up(p->count, count.data(), count.size() * sizeof(long long));
+    up(p->gsv, gs.data(), gs.size() * sizeof(long long));
+    up(p->nonempty, ne.data(), ne.size() * sizeof(int));
+    if (e != cudaSuccess) {
+        free_radial_plan(p);
+        return set_err(c, MX_ERR_CUDA, std::string("radial: plan upload: ") + cudaGetErrorString(e));
+    }
+    if ((int)c->rplans.size() >= MAX_RADIAL_PLANS) {  // evict the least recently used
+        auto it = std::min_element(c->rplans.begin(), c->rplans.end(),
+                                   [](RadialPlan *a, RadialPlan *bb) { return a->last_use < bb->last_use; });
+        cudaStreamSynchronize(c->stream);
+        free_radial_plan(*it);
+        c->rplans.erase(it);
+    }
+    p->last_use = ++c->use_counter;
+    c->rplans.push_back(p);
+    *out = p;
+    return MX_OK;
+}
+
+static mx_status launch_fill(mx_ctx *c, const RadialPlan *p, const double *v, double *out) {
+    if (p->nbatch == 0) return MX_OK;
+    const size_t smem = (size_t)p->n[0] * sizeof(double);
+    if (p->n[0] % 2 == 0) {
+        if (smem > 48 * 1024)
+            MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        rad_fill_kernel<2><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
+    } else {
+        if (smem > 48 * 1024)
+            MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        rad_fill_kernel<1><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
+    }
+    return MX_OK;
+}
+
+static mx_status check_corner_args(mx_ctx *c, const mx_geom *geom, const int corner[3]) {
+    if (!c) return MX_ERR_ARG;
+    mx_status st = check_geom(c, geom, false);
+    if (st) return st;
+    if (!corner) return set_err(c, MX_ERR_ARG, "radial: null corner");
+    return MX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+long long mx_radial_nbins(const mx_geom *geom, const int corner[3]) {
+    if (!geom || !corner) return -1;
+    long long tmin[3], tmax[3], nbins;
+    if (!radial_ranges(geom, corner, tmin, tmax, nbins)) return -1;
+    return nbins;
+}
+
+mx_status mx_average_planar(mx_ctx *c, const mx_geom *geom, const double *field, double *prof) {
+    if (!c) return MX_ERR_ARG;
+    mx_status st = check_geom(c, geom, false);
+    if (st) return st;
+    if (!field || !prof) return set_err(c, MX_ERR_ARG, "average_planar: null array");
+    const long long nxy = (long long)geom->n[0] * geom->n[1];
+    const int nz = geom->n[2];
+    long long nchunk = std::min((nxy + 1023) / 1024, (2432LL + nz - 1) / nz);
+    nchunk = std::max(1LL, nchunk);
+    const size_t need = (size_t)nz * nchunk * sizeof(float2);
+    if (need > c->base_tmp_bytes) {
+        if (c->base_tmp) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->base_tmp);
+        }
+        c->base_tmp = nullptr;
+        c->base_tmp_bytes = 0;
+        if (cudaMalloc(&c->base_tmp, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, MX_ERR_OOM, "average_planar: scratch allocation failed");
+        }
+        c->base_tmp_bytes = need;
+    }
+    float2 *part = (float2 *)c->base_tmp;
+    plane_sum_kernel<<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
+    plane_final_kernel<<<(nz + 7) / 8, 256, 0, c->stream>>>(part, nz, int(nchunk), nxy, prof);
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+mx_status mx_average_radial(mx_ctx *c, const mx_geom *geom, const int corner[3], const double *field,
+                            long long nbins, double *avg, long long *count) {
+    mx_status st = check_corner_args(c, geom, corner);
+    if (st) return st;
+    if (!field || !avg) return set_err(c, MX_ERR_ARG, "average_radial: null array");
+    RadialPlan *p;
+    if ((st = get_radial_plan(c, geom, corner, &p))) return st;
+    if (nbins != p->nbins) return set_err(c, MX_ERR_ARG, "average_radial: nbins differs from mx_radial_nbins");
+    const size_t smem = ((size_t)p->n[0] + (size_t)p->gmax * p->wt) * sizeof(float2);
+    if (p->nbatch > 0) {
+        if (p->n[0] % 2 == 0) {
+            if (smem > 48 * 1024)
+                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                int(smem)));
+            rad_fold_kernel<2><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(field, rad_dev(p), p->G);
+        } else {
+            if (smem > 48 * 1024)
+                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                int(smem)));
+            rad_fold_kernel<1><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(field, rad_dev(p), p->G);
+        }
+    }
+    const long long nb = (p->nbins + 31) / 32;
+    rad_bin_kernel<<<(unsigned)nb, BIN_THREADS, 0, c->stream>>>(rad_dev(p), p->G, avg);
+    if (count)
+        MX_CUDA(c, cudaMemcpyAsync(count, p->count, p->nbins * sizeof(long long), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+mx_status mx_fill_radial(mx_ctx *c, const mx_geom *geom, const int corner[3], const double *base,
+                         long long nbins, double *out) {
+    mx_status st = check_corner_args(c, geom, corner);
+    if (st) return st;
+    if (!base || !out) return set_err(c, MX_ERR_ARG, "fill_radial: null array");
+    RadialPlan *p;
+    if ((st = get_radial_plan(c, geom, corner, &p))) return st;
+    if (nbins != p->nbins) return set_err(c, MX_ERR_ARG, "fill_radial: nbins differs from mx_radial_nbins");
+    if ((st = launch_fill(c, p, base, out))) return st;
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+mx_status mx_radial_to_uniform(mx_ctx *c, const mx_geom *geom, const int corner[3], const double *avg, int nr,
+                               double dr, double *prof) {
+    mx_status st = check_corner_args(c, geom, corner);
+    if (st) return st;
+    if (!avg || !prof) return set_err(c, MX_ERR_ARG, "radial_to_uniform: null array");
+    if (nr < 1 || !(dr > 0.0)) return set_err(c, MX_ERR_ARG, "radial_to_uniform: needs nr >= 1 and dr > 0");
+    RadialPlan *p;
+    if ((st = get_radial_plan(c, geom, corner, &p))) return st;
+    if (p->nne < 3) return set_err(c, MX_ERR_ARG, "radial_to_uniform: fewer than 3 non-empty radii");
+    rad_to_uniform_kernel<<<(nr + 127) / 128, 128, 0, c->stream>>>(p->nonempty, p->nne, geom->dx, avg, nr, dr,
+                                                                    prof);
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+mx_status mx_fill_uniform(mx_ctx *c, const mx_geom *geom, const int corner[3], const double *prof, int nr,
+                          double dr, double *out) {
+    mx_status st = check_corner_args(c, geom, corner);
+    if (st) return st;
+    if (!prof || !out) return set_err(c, MX_ERR_ARG, "fill_uniform: null array");
+    if (nr < 3 || !(dr > 0.0)) return set_err(c, MX_ERR_ARG, "fill_uniform: needs nr >= 3 and dr > 0");
+    RadialPlan *p;
+    if ((st = get_radial_plan(c, geom, corner, &p))) return st;
+    rad_uniform_table_kernel<<<(unsigned)((p->nbins + 255) / 256), 256, 0, c->stream>>>(p->nbins, geom->dx, prof,
+                                                                                         nr, dr, p->tab);
+    if ((st = launch_fill(c, p, p->tab, out))) return st;
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+}  // extern "C"

@@ -70,6 +70,7 @@ __device__ __forceinline__ void set_scale(SolveState *st, double sc) {
 struct MacPlan;
 struct NodalPlan;
 struct BatchPlan;
+struct RadialPlan;
 
 struct mx_ctx {
     int device;
@@ -86,6 +87,9 @@ struct mx_ctx {
     std::vector<MacPlan *> plans;        // cached workspaces, one per geometry/precision
     std::vector<NodalPlan *> nplans;
     BatchPlan *batch = nullptr;
+    std::vector<RadialPlan *> rplans;    // lateral average / fill plans, one per (n, corner)
+    void *base_tmp = nullptr;            // planar-average partial sums
+    size_t base_tmp_bytes = 0;
     long long use_counter = 0;
     // tracing (mx_profile_enable)
     bool prof = false;

@@ -16,6 +16,7 @@ mx_status nodal_apply(mx_ctx *c, const mx_geom *geom, int prec, const double *rh
                       const double *phi, const double *f, double *out, double *rnorm);
 void destroy_nodal_plans(mx_ctx *c);
 void destroy_batch_plan(mx_ctx *c);
+void destroy_radial_plans(mx_ctx *c);
 
 // ------------------------------------------------------------------------------
 // plans
@@ -168,6 +169,7 @@ void destroy_plans(mx_ctx *c) {
     c->plans.clear();
     destroy_nodal_plans(c);
     destroy_batch_plan(c);
+    destroy_radial_plans(c);
 }
 
 // ------------------------------------------------------------------------------

@@ -101,3 +101,40 @@ def test_nodal384_fullsize_sampled(mx):
     assert np.abs(r).max() <= 1.05e-10 * fn
     wts = O.nd_weights(g)
     assert abs((wts * phi).sum()) <= 1e-12 * np.abs(phi).max() * wts.sum()
+
+
+def test_lateral_average_and_fill_fullsize(mx):
+    """the 512^3 full star's density: radial average onto the irregular base state
+    against the oracle on every bin, and the fill back bit for bit; the planar
+    256^3 density's plane means."""
+    w = W.star512(device=DEV)
+    g = w.geom
+    c = tuple(n // 2 for n in g.n)
+    ctx = mx.mx_create(0)
+    try:
+        nb = mx.mx_radial_nbins(g, c)
+        avg = torch.empty(nb, dtype=torch.float64, device=DEV)
+        cnt = torch.empty(nb, dtype=torch.int64, device=DEV)
+        mx.mx_average_radial(ctx, g, c, w.rho, avg, cnt)
+        out = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+        mx.mx_fill_radial(ctx, g, c, avg, out)
+        torch.cuda.synchronize()
+        f = w.rho.cpu().numpy()
+        ref, rcnt = O.average_radial(g, c, f)
+        assert np.array_equal(cnt.cpu().numpy(), rcnt)
+        absmean, _ = O.average_radial(g, c, np.abs(f))
+        tol = np.maximum(np.sqrt(rcnt), 8.0) * 2.0**-44 * absmean + 1e-300
+        a = avg.cpu().numpy()
+        assert np.all(np.abs(a - ref) <= tol)
+        assert np.array_equal(out.cpu().numpy(), O.fill_irregular(g, c, a))
+        del out, f
+        wp = W.planar256(device=DEV)
+        prof = torch.empty(wp.geom.n[2], dtype=torch.float64, device=DEV)
+        mx.mx_average_planar(ctx, wp.geom, wp.rho, prof)
+        torch.cuda.synchronize()
+        fp = wp.rho.cpu().numpy()
+        refp = O.average_planar(wp.geom, fp)
+        tolp = np.sqrt(fp[0].size) * 2.0**-44 * np.abs(fp).mean(axis=(1, 2))
+        assert np.all(np.abs(prof.cpu().numpy() - refp) <= tolp)
+    finally:
+        mx.mx_destroy(ctx)
