@@ -20,9 +20,9 @@
 //      whole rows, coalesced) and folds the mirror columns a and -1 - a (equal
 //      T) together into G[group][t], t = (a >= 0 ? a : -1 - a);
 //   2. bins: bin m = s + T(t) sums G[group(s)][t] over t, one lane per bin.
-// Sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of FP32; the
-// fold adds row pairs in FP64 first, about half an FP64 operation per cell,
-// which the FP64 pipe keeps up with); the bin means are divided in FP64.
+// Sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of FP32: even
+// one FP64 addition per two cells would cost more than the double-float
+// addition); the bin means are divided in FP64.
 #include <algorithm>
 #include <cmath>
 
@@ -73,7 +73,7 @@ struct RadialPlan {
 };
 
 struct RadDev {
-    int nx, ny, c0, c1, c2, kmin, kmax, wt, ngroups;
+    int nx, ny, c0, c1, c2, kmin, kmax, wt, ngroups, gmax;
     long long nbins, smin, smax;
     const int *rows, *gstart, *grp, *bstart;
     const long long *count;
@@ -90,6 +90,7 @@ static RadDev rad_dev(const RadialPlan *p) {
     d.kmax = p->kmax;
     d.wt = p->wt;
     d.ngroups = p->ngroups;
+    d.gmax = p->gmax;
     d.nbins = p->nbins;
     d.smin = p->smin;
     d.smax = p->smax;
@@ -119,71 +120,88 @@ struct DfAcc {
     __device__ __forceinline__ dfloat norm() const { return df_norm(h, l); }
 };
 
-// 1. fold: one CTA per batch of whole groups (at most gmax of them); racc holds one
-// row of column sums, gbuf the batch's folded rows, written out t-major
-// (GT[t][g], runs of the batch's consecutive groups).  V = 2: each thread takes
-// column pairs as 16-byte loads (n0 even, so every row starts on a 16-byte
-// boundary).  Rows come in batches of 8 loads per column (16 in flight per
-// thread); rows are added in pairs in FP64 (the FP64 pipe is otherwise idle) and
-// the pair sums accumulate in double-float.
+// 1. fold: one CTA per batch of whole groups (at most gmax of them).  Each thread
+// owns a column (V = 2: a column pair, 16-byte loads; n0 even, so every row
+// starts on a 16-byte boundary) and walks all rows of the batch in rounds of 8
+// loads, across group boundaries (16 loads in flight per thread, no barrier
+// between groups).  At a
+// group's last row the column sum goes to racc[group][column].  After one
+// barrier the mirror columns a and -1 - a fold together and G is written
+// t-major (G[t][g], runs of the batch's consecutive groups).
 template <int V>
 __global__ void __launch_bounds__(FOLD_THREADS) rad_fold_kernel(const double *__restrict__ f, RadDev P,
                                                                 float2 *__restrict__ GT) {
-    extern __shared__ float2 smem_f2[];
-    float2 *racc = smem_f2;
-    float2 *gbuf = smem_f2 + P.nx;
+    extern __shared__ float2 racc[];
     const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
+    const int R0 = P.gstart[g0], R1 = P.gstart[g1];
     const int nx = P.nx, nv = nx / V, wt = P.wt;
-    for (int g = g0; g < g1; g++) {
-        const int r0 = P.gstart[g], r1 = P.gstart[g + 1];
-        for (int q = threadIdx.x; q < nv; q += FOLD_THREADS) {
-            DfAcc acc[V];
-            for (int r = r0; r < r1; r += 8) {
-                double v[8][V];
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-#pragma unroll
-                    for (int w = 0; w < V; w++) v[u][w] = 0.0;
-                    if (r + u < r1) {  // uniform over the CTA
-                        const double *src = f + (long long)P.rows[r + u] * nx + (long long)q * V;
-                        if constexpr (V == 2) {
-                            const double2 t = __ldcs(reinterpret_cast<const double2 *>(src));
-                            v[u][0] = t.x;
-                            v[u][V - 1] = t.y;
-                        } else {
-                            v[u][0] = __ldcs(src);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; u += 2)
-                    if (r + u < r1) {
-#pragma unroll
-                        for (int w = 0; w < V; w++) acc[w].add(df_split(v[u][w] + v[u + 1][w]));
-                    }
-            }
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        DfAcc acc[V];
+        int cur = g0, gend = P.gstart[g0 + 1];
+        auto flush = [&]() {
 #pragma unroll
             for (int w = 0; w < V; w++) {
                 const dfloat a = acc[w].norm();
-                racc[q * V + w] = make_float2(a.h, a.l);
+                racc[(long long)(cur - g0) * nx + q * V + w] = make_float2(a.h, a.l);
+                acc[w] = DfAcc();
+            }
+            cur++;
+            if (cur < g1) gend = P.gstart[cur + 1];
+        };
+        for (int r = R0; r < R1; r += 8) {
+            double v[8][V];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+#pragma unroll
+                for (int w = 0; w < V; w++) v[u][w] = 0.0;
+                if (r + u < R1) {  // uniform over the CTA
+                    const double *src = f + (long long)P.rows[r + u] * nx + (long long)q * V;
+                    if constexpr (V == 2) {
+                        const double2 t = __ldcs(reinterpret_cast<const double2 *>(src));
+                        v[u][0] = t.x;
+                        v[u][V - 1] = t.y;
+                    } else {
+                        v[u][0] = __ldcs(src);
+                    }
+                }
+            }
+            // rows of the same group add in FP64 pairs before the double-float
+            // accumulation (moves about a third of the work to the FP64 pipe,
+            // which the double-float operations leave idle); group boundaries are
+            // uniform over the CTA, so are these branches
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                const int ra = r + u, rb = ra + 1;
+                if (ra < R1) {
+                    if (rb < gend) {  // both rows in the current group
+#pragma unroll
+                        for (int w = 0; w < V; w++) acc[w].add(df_split(v[u][w] + v[u + 1][w]));
+                        if (rb + 1 == gend) flush();
+                    } else {  // ra ends the group
+#pragma unroll
+                        for (int w = 0; w < V; w++) acc[w].add(df_split(v[u][w]));
+                        flush();
+                        if (rb < R1) {
+#pragma unroll
+                            for (int w = 0; w < V; w++) acc[w].add(df_split(v[u + 1][w]));
+                            if (rb + 1 == gend) flush();
+                        }
+                    }
+                }
             }
         }
-        __syncthreads();
-        float2 *gb = gbuf + (long long)(g - g0) * wt;
-        for (int t = threadIdx.x; t < wt; t += FOLD_THREADS) {
-            const int k = P.kmin + t;
-            const int i1 = P.c0 + k, i2 = P.c0 - 1 - k;  // a = k and a = -1 - k
-            dfloat v{0.f, 0.f};
-            if (i1 >= 0 && i1 < nx) v = dfloat{racc[i1].x, racc[i1].y};
-            if (i2 >= 0 && i2 < nx) v = df_add(v, dfloat{racc[i2].x, racc[i2].y});
-            gb[t] = make_float2(v.h, v.l);
-        }
-        __syncthreads();
     }
+    __syncthreads();
     const int ng = g1 - g0;
-    for (int e = threadIdx.x; e < ng * wt; e += FOLD_THREADS) {
+    for (int e = threadIdx.x; e < ng * wt; e += blockDim.x) {
         const int t = e / ng, j = e - t * ng;
-        GT[(long long)t * P.ngroups + g0 + j] = gbuf[(long long)j * wt + t];
+        const int k = P.kmin + t;
+        const int i1 = P.c0 + k, i2 = P.c0 - 1 - k;  // a = k and a = -1 - k
+        const float2 *ra = racc + (long long)j * nx;
+        dfloat v{0.f, 0.f};
+        if (i1 >= 0 && i1 < nx) v = dfloat{ra[i1].x, ra[i1].y};
+        if (i2 >= 0 && i2 < nx) v = df_add(v, dfloat{ra[i2].x, ra[i2].y});
+        GT[(long long)t * P.ngroups + g0 + j] = make_float2(v.h, v.l);
     }
 }
 
@@ -215,19 +233,26 @@ __global__ void __launch_bounds__(BIN_THREADS) rad_bin_kernel(RadDev P, const fl
     const long long chunk = (thi - tlo + BIN_WARPS) / BIN_WARPS;  // ceil(nt / warps), nt may be 0
     const long long ta = tlo + w * chunk, tb = min(thi, ta + chunk - 1);
     DfAcc acc;
-    for (long long t = ta; t <= tb; t += 4) {
-        int g[4];
+    if (ta <= tb) {
+        // s = m - T(t) falls by t + 1 from t to t + 1; the G row advances by ngroups
+        long long s = m - tri(ta);
+        const float2 *gt = GT + (ta - P.kmin) * (long long)P.ngroups;
+        const bool live = m < P.nbins;
+        for (long long t = ta; t <= tb; t += 4) {
+            int g[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const long long s = m - tri(t + u);
-            g[u] = (t + u <= tb && s >= P.smin && s <= P.smax && m < P.nbins) ? __ldg(P.grp + (s - P.smin)) : -1;
+            for (int u = 0; u < 4; u++) {
+                g[u] = (live && t + u <= tb && s >= P.smin && s <= P.smax) ? __ldg(P.grp + (s - P.smin)) : -1;
+                s -= t + u + 1;
+            }
+            float2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                v[u] = g[u] >= 0 ? __ldg(gt + (long long)u * P.ngroups + g[u]) : make_float2(0.f, 0.f);
+            gt += 4LL * P.ngroups;
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc.add(dfloat{v[u].x, v[u].y});
         }
-        float2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-            v[u] = g[u] >= 0 ? __ldg(GT + (t + u - P.kmin) * (long long)P.ngroups + g[u]) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < 4; u++) acc.add(dfloat{v[u].x, v[u].y});
     }
     const dfloat a = acc.norm();
     part[w][lane] = make_float2(a.h, a.l);
@@ -252,12 +277,12 @@ __global__ void __launch_bounds__(FOLD_THREADS) rad_fill_kernel(RadDev P, const 
     const int nx = P.nx, nv = nx / V;
     for (int g = g0; g < g1; g++) {
         const long long s = gs[g];
-        for (int i = threadIdx.x; i < nx; i += FOLD_THREADS) rowv[i] = __ldg(v + tri((long long)(i - P.c0)) + s);
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) rowv[i] = __ldg(v + tri((long long)(i - P.c0)) + s);
         __syncthreads();
         const int r0 = P.gstart[g], r1 = P.gstart[g + 1];
         for (int r = r0; r < r1; r++) {
             double *dst = out + (long long)P.rows[r] * nx;
-            for (int q = threadIdx.x; q < nv; q += FOLD_THREADS) {
+            for (int q = threadIdx.x; q < nv; q += blockDim.x) {
                 if constexpr (V == 2) __stcs(reinterpret_cast<double2 *>(dst) + q, make_double2(rowv[2 * q], rowv[2 * q + 1]));
                 else __stcs(dst + q, rowv[q]);
             }
@@ -440,11 +465,10 @@ static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corne
     const int ngroups = int(gstart.size());
     gstart.push_back(int(nrows));
     // fold batches: whole groups, about rb rows and at most gmax groups each (the
-    // batch's folded rows are staged in 32 KB of shared memory, or one row)
-    const long long kmin_ = tmin[0], wt_ = tmax[0] - tmin[0] + 1;
+    // batch's column sums, gmax rows of n0 double-floats, stay in about 48 KB of
+    // shared memory)
     const long long rb = std::min(128LL, std::max(8LL, nrows / 4096));
-    const int gmax = int(std::max(1LL, std::min(64LL, 4096 / wt_)));
-    (void)kmin_;
+    const int gmax = int(std::max(1LL, std::min(64LL, 6144LL / nx)));
     std::vector<int> bstart{0};
     for (int g = 0; g < ngroups; g++) {
         const long long in_batch = gstart[g] - gstart[bstart.back()];
@@ -466,7 +490,6 @@ static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corne
     std::vector<int> ne;
     for (long long m = 0; m < nbins; m++)
         if (count[m] > 0) ne.push_back(int(m));
-
     RadialPlan *p = new RadialPlan();
     for (int d = 0; d < 3; d++) {
         p->n[d] = geom->n[d];
@@ -531,17 +554,24 @@ static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corne
     return MX_OK;
 }
 
+// threads of the fold and fill CTAs: one per column pair of a row, 64 to 256
+static int fold_threads(int nx) {
+    const int nv = (nx + 1) / 2;
+    return std::min(FOLD_THREADS, std::max(64, (nv + 31) / 32 * 32));
+}
+
 static mx_status launch_fill(mx_ctx *c, const RadialPlan *p, const double *v, double *out) {
     if (p->nbatch == 0) return MX_OK;
     const size_t smem = (size_t)p->n[0] * sizeof(double);
-    if (p->n[0] % 2 == 0) {
+    // 16-byte stores need an even row length and a 16-byte aligned array
+    if (p->n[0] % 2 == 0 && ((uintptr_t)out & 15) == 0) {
         if (smem > 48 * 1024)
             MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        rad_fill_kernel<2><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
+        rad_fill_kernel<2><<<p->nbatch, fold_threads(p->n[0]), smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
     } else {
         if (smem > 48 * 1024)
             MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        rad_fill_kernel<1><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
+        rad_fill_kernel<1><<<p->nbatch, fold_threads(p->n[0]), smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
     }
     return MX_OK;
 }
@@ -604,18 +634,19 @@ mx_status mx_average_radial(mx_ctx *c, const mx_geom *geom, const int corner[3],
     RadialPlan *p;
     if ((st = get_radial_plan(c, geom, corner, &p))) return st;
     if (nbins != p->nbins) return set_err(c, MX_ERR_ARG, "average_radial: nbins differs from mx_radial_nbins");
-    const size_t smem = ((size_t)p->n[0] + (size_t)p->gmax * p->wt) * sizeof(float2);
+    const size_t smem = (size_t)p->gmax * p->n[0] * sizeof(float2);
+    const int nthr = fold_threads(p->n[0]);
     if (p->nbatch > 0) {
-        if (p->n[0] % 2 == 0) {
+        if (p->n[0] % 2 == 0 && ((uintptr_t)field & 15) == 0) {  // 16-byte loads
             if (smem > 48 * 1024)
                 MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 int(smem)));
-            rad_fold_kernel<2><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(field, rad_dev(p), p->G);
+            rad_fold_kernel<2><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
         } else {
             if (smem > 48 * 1024)
                 MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 int(smem)));
-            rad_fold_kernel<1><<<p->nbatch, FOLD_THREADS, smem, c->stream>>>(field, rad_dev(p), p->G);
+            rad_fold_kernel<1><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
         }
     }
     const long long nb = (p->nbins + 31) / 32;

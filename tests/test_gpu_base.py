@@ -73,6 +73,7 @@ RADIAL = [
     ((16, 9, 11), (-5, 4, 14)),        # corner outside the box
     ((1, 1, 1), (0, 0, 0)),            # one cell
     ((64, 48, 40), (32, 24, 20)),
+    ((1030, 3, 4), (515, 1, 2)),       # even rows too long for the copy-engine fold
 ]
 
 
@@ -97,6 +98,33 @@ def test_average_radial_parity(mx, ctx, n, c, kind):
     again = torch.empty_like(avg)
     mx.mx_average_radial(ctx, g, c, dev(f), again)
     assert torch.equal(avg, again)  # fixed summation order
+
+
+def test_average_radial_unaligned_field(mx, ctx):
+    """a field 8 bytes off a 16-byte boundary takes the scalar-load fold (same bits as
+    the 16-byte-load fold); an output 8 bytes off takes the scalar-store fill"""
+    g = geom((64, 40, 36))
+    c = (32, 20, 18)
+    f = field(g, 11)
+    buf = torch.empty(f.size + 1, dtype=torch.float64, device=DEV)
+    off = buf[1:].view(f.shape)
+    off.copy_(dev(f))
+    nb = mx.mx_radial_nbins(g, c)
+    a = torch.empty(nb, dtype=torch.float64, device=DEV)
+    b = torch.empty(nb, dtype=torch.float64, device=DEV)
+    mx.mx_average_radial(ctx, g, c, off, a)
+    mx.mx_average_radial(ctx, g, c, dev(f), b)
+    torch.cuda.synchronize()
+    ref, cnt = O.average_radial(g, c, f)
+    absmean, _ = O.average_radial(g, c, np.abs(f))
+    for x in (a, b):
+        assert np.all(np.abs(x.cpu().numpy() - ref) <= tol_bins(absmean, cnt))
+    assert torch.equal(a, b)
+    obuf = torch.empty(f.size + 1, dtype=torch.float64, device=DEV)
+    out = obuf[1:].view(f.shape)
+    mx.mx_fill_radial(ctx, g, c, a, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), O.fill_irregular(g, c, a.cpu().numpy()))
 
 
 @pytest.mark.parametrize("n,c", RADIAL)
