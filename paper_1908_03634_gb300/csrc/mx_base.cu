@@ -358,24 +358,49 @@ __device__ __forceinline__ dfloat warp_df_sum(dfloat a) {
     return a;
 }
 
+// V = 2: 16-byte loads (n0 n1 even and a 16-byte aligned field); 4 loads in
+// flight per thread; neighbouring values add in FP64 pairs, the pair sums in
+// double-float (as in the radial fold)
+template <int V>
 __global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__restrict__ f, long long nxy,
                                                                int nchunk, float2 *__restrict__ part) {
     __shared__ float2 ws[PL_THREADS / 32];
-    const long long len = (nxy + nchunk - 1) / nchunk;
-    const long long b0 = (long long)blockIdx.x * len, b1 = min(nxy, b0 + len);
+    const long long nv = nxy / V;
+    const long long len = (nv + nchunk - 1) / nchunk;
+    const long long b0 = (long long)blockIdx.x * len, b1 = min(nv, b0 + len);
     const double *p = f + (long long)blockIdx.y * nxy;
-    dfloat acc{0.f, 0.f};
+    DfAcc acc;
     long long q = b0 + threadIdx.x;
     for (; q + 3 * PL_THREADS < b1; q += 4 * PL_THREADS) {
-        double v[4];
+        double v[4][2];
 #pragma unroll
-        for (int u = 0; u < 4; u++) v[u] = __ldcs(p + q + u * PL_THREADS);
+        for (int u = 0; u < 4; u++) {
+            if constexpr (V == 2) {
+                const double2 t = __ldcs(reinterpret_cast<const double2 *>(p) + q + u * PL_THREADS);
+                v[u][0] = t.x;
+                v[u][1] = t.y;
+            } else {
+                v[u][0] = __ldcs(p + q + u * PL_THREADS);
+            }
+        }
+        if constexpr (V == 2) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) acc = df_add(acc, df_split(v[u]));
+            for (int u = 0; u < 4; u++) acc.add(df_split(v[u][0] + v[u][1]));
+        } else {
+            acc.add(df_split(v[0][0] + v[1][0]));
+            acc.add(df_split(v[2][0] + v[3][0]));
+        }
     }
-    for (; q < b1; q += PL_THREADS) acc = df_add(acc, df_split(__ldcs(p + q)));
-    acc = warp_df_sum(acc);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = make_float2(acc.h, acc.l);
+    for (; q < b1; q += PL_THREADS) {
+        if constexpr (V == 2) {
+            const double2 t = __ldcs(reinterpret_cast<const double2 *>(p) + q);
+            acc.add(df_split(t.x + t.y));
+        } else {
+            acc.add(df_split(__ldcs(p + q)));
+        }
+    }
+    dfloat a = warp_df_sum(acc.norm());
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = make_float2(a.h, a.l);
     __syncthreads();
     if (threadIdx.x == 0) {
         dfloat s{ws[0].x, ws[0].y};
@@ -620,7 +645,10 @@ mx_status mx_average_planar(mx_ctx *c, const mx_geom *geom, const double *field,
         c->base_tmp_bytes = need;
     }
     float2 *part = (float2 *)c->base_tmp;
-    plane_sum_kernel<<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
+    if (nxy % 2 == 0 && ((uintptr_t)field & 15) == 0)
+        plane_sum_kernel<2><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
+    else
+        plane_sum_kernel<1><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
     plane_final_kernel<<<(nz + 7) / 8, 256, 0, c->stream>>>(part, nz, int(nchunk), nxy, prof);
     MX_CUDA(c, cudaGetLastError());
     return MX_OK;

@@ -154,12 +154,18 @@ def test_round_trip_radial_function(mx, ctx):
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (37, 23, 11), (256, 3, 5), (1, 1, 1), (130, 70, 3)])
-@pytest.mark.parametrize("kind", ["star", "signed"])
+@pytest.mark.parametrize("kind", ["star", "signed", "offset"])
 def test_average_planar_parity(mx, ctx, shape, kind):
+    """kind offset: the field 8 bytes off a 16-byte boundary (scalar loads)"""
     g = geom(shape)
-    f = field(g, 4, kind)
+    f = field(g, 4, "star" if kind == "offset" else kind)
     out = torch.empty(g.n[2], dtype=torch.float64, device=DEV)
-    mx.mx_average_planar(ctx, g, dev(f), out)
+    fd = dev(f)
+    if kind == "offset":
+        buf = torch.empty(f.size + 1, dtype=torch.float64, device=DEV)
+        fd = buf[1:].view(f.shape)
+        fd.copy_(dev(f))
+    mx.mx_average_planar(ctx, g, fd, out)
     torch.cuda.synchronize()
     ref = O.average_planar(g, f)
     nxy = g.n[0] * g.n[1]
