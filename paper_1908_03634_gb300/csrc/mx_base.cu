@@ -129,7 +129,7 @@ struct DfAcc {
 // barrier the mirror columns a and -1 - a fold together and G is written
 // t-major (G[t][g], runs of the batch's consecutive groups).
 template <int V>
-__global__ void __launch_bounds__(FOLD_THREADS) rad_fold_kernel(const double *__restrict__ f, RadDev P,
+__global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_kernel(const double *__restrict__ f, RadDev P,
                                                                 float2 *__restrict__ GT) {
     extern __shared__ float2 racc[];
     const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
@@ -490,10 +490,10 @@ static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corne
     const int ngroups = int(gstart.size());
     gstart.push_back(int(nrows));
     // fold batches: whole groups, about rb rows and at most gmax groups each (the
-    // batch's column sums, gmax rows of n0 double-floats, stay in about 48 KB of
-    // shared memory)
+    // batch's column sums, gmax rows of n0 double-floats, stay in about 16 KB of
+    // shared memory, so that shared memory does not limit the CTAs per SM)
     const long long rb = std::min(128LL, std::max(8LL, nrows / 4096));
-    const int gmax = int(std::max(1LL, std::min(64LL, 6144LL / nx)));
+    const int gmax = int(std::max(1LL, std::min(64LL, 2048LL / nx)));
     std::vector<int> bstart{0};
     for (int g = 0; g < ngroups; g++) {
         const long long in_batch = gstart[g] - gstart[bstart.back()];
