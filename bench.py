@@ -524,6 +524,16 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
     return out
 
 
+def _avg_traffic(ncell):
+    """DRAM bytes of one mx_average_radial call, scaled by the cell count from the
+    ncu capture recorded in profiles/traffic.json (None if absent)."""
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        return round(tr["average_radial_call_per_cell_bytes"] * ncell)
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def bench_base(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, cpu=True, n=512):
     """Lateral Average and Fill (Sec. 3.1) on the 512^3 full star's density, centre
     on the corner (256, 256, 256): one step = Average onto the irregular base state
@@ -575,7 +585,7 @@ def bench_base(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, cpu=True
          "fill_uniform": {"ms": ms_fu / steps, "launches": 2},
          "average_planar_256": {"ms": ms_pl / steps, "GB_s": a_pl, "frac": a_pl / hbm, "launches": 2},
          "roofline": {"bound": "hbm", "achieved": round(a_avg, 1), "peak": hbm, "unit": "GB/s",
-                      "frac": round(a_avg / hbm, 4), "traffic": None,
+                      "frac": round(a_avg / hbm, 4), "traffic": _avg_traffic(N),
                       "kernel": "mx_average_radial (fold + bin kernels), 8 B/cell read + 8 B/bin written",
                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
          "gpu_launches_per_step": 3}
