@@ -85,6 +85,9 @@ def _load():
             "or_fill_irregular": (None, [G, _IP, _P, _P]),
             "or_fill_quadratic": (C.c_int, [G, _P, C.c_int, C.c_double, _P, _P]),
             "or_average_to_uniform": (C.c_int, [C.c_long, _P, _LP, C.c_double, C.c_int, C.c_double, _P]),
+            "or_w0_integrate": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, C.c_int, _P]),
+            "or_add_w0_faces": (None, [G, C.c_int, _IP, C.c_int, _P, _P, _P, _P, _P]),
+            "or_subtract_lateral_average": (None, [G, C.c_int, _IP, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -164,6 +167,34 @@ def fill_quadratic(geom, prof, dr, center):
     rc = _load().or_fill_quadratic(_g(geom), _p(prof), prof.size, float(dr), _p(c), _p(out))
     if rc:
         raise ValueError("fill_quadratic needs at least 3 radial cells")
+    return out
+
+
+def w0_integrate(spherical, r_edge, beta0, src, cutoff=-1):
+    """w0 on the nr + 1 base-state edges (Appendix A velocity split)."""
+    r_edge, beta0, src = _arr(r_edge), _arr(beta0), _arr(src)
+    nr = beta0.size
+    assert r_edge.size == nr + 1 and src.size == nr
+    out = np.empty(nr + 1)
+    if _load().or_w0_integrate(int(spherical), nr, _p(r_edge), _p(beta0), _p(src), int(cutoff), _p(out)):
+        raise ValueError("w0_integrate needs nr >= 1")
+    return out
+
+
+def add_w0_faces(geom, spherical, corner, r_edge, w0, u):
+    """returns copies of the three face arrays with w0 e_r added"""
+    r_edge, w0 = _arr(r_edge), _arr(w0)
+    out = [np.array(x, dtype=np.float64, copy=True, order="C") for x in u]
+    c = _corner(corner if corner is not None else (0, 0, 0))
+    _load().or_add_w0_faces(_g(geom), int(spherical), c, w0.size - 1, _p(r_edge), _p(w0), _p(out[0]), _p(out[1]),
+                            _p(out[2]))
+    return out
+
+
+def subtract_lateral_average(geom, spherical, corner, S):
+    out = np.empty(cell_shape(geom))
+    c = _corner(corner if corner is not None else (0, 0, 0))
+    _load().or_subtract_lateral_average(_g(geom), int(spherical), c, _p(_arr(S)), _p(out))
     return out
 
 

@@ -1,7 +1,8 @@
 /*
  * FP64 CPU oracle for the base-state mapping modules of MAESTROeX (Sec. 3.1):
  * the lateral average (Cartesian cells -> 1D base state) and the fill
- * (1D base state -> Cartesian cells).
+ * (1D base state -> Cartesian cells); and for the velocity split of Appendix A
+ * (the w0 integration, w0 e_r on the MAC faces, the S - Sbar bracket).
  *
  * TEST INFRASTRUCTURE ONLY (the tests, the smoke check and the benchmark's CPU
  * legs load it).  Shares nothing with the CUDA library.  Plain loops, double
@@ -162,4 +163,108 @@ int or_average_to_uniform(long nbins, const double *avg, const long *count, doub
     free(rr);
     free(vv);
     return 0;
+}
+
+/* ---- velocity split: w0 and the lateral-average constraint (Appendix A) -------------
+ * U = U~ + w0 e_r.  U~ satisfies div(beta0 U~) = beta0 (S - Sbar) (Sbar: the lateral
+ * average of S, filled back onto the cells); w0 satisfies
+ *     div(beta0 w0 e_r) = beta0 (Sbar - psi),   psi = dp0/dt / (Gamma1bar p0),
+ * integrated in one dimension over base-state cells j (edges e = j and j + 1):
+ *     Q_0 = 0,  Q_{j+1} = Q_j + V_j beta0_j src_j,  src_j = Sbar_j - psi_j,
+ *     w0_e = Q_e / (A_e beta0e_e)      (w0_0 = 0),
+ * planar: A = 1, V_j = r_{j+1} - r_j; spherical: A = r^2, V_j = (r_{j+1}^3 - r_j^3)/3
+ * (the exact shell integral of r^2).  beta0 on an interior edge is the mean of its two
+ * cells, on the last edge that of the last cell.  With a cutoff edge c >= 0 the
+ * edges beyond it keep A w0 constant: w0_e = w0_c A_c / A_e. */
+int or_w0_integrate(int spherical, int nr, const double *r_edge, const double *beta0, const double *src,
+                    int cutoff, double *w0) {
+    if (nr < 1) return -1;
+    double Q = 0.0;
+    w0[0] = 0.0;
+    for (int j = 0; j < nr; j++) {
+        const double r0 = r_edge[j], r1 = r_edge[j + 1];
+        const double V = spherical ? (r1 * r1 * r1 - r0 * r0 * r0) / 3.0 : r1 - r0;
+        Q += V * beta0[j] * src[j];
+        const double be = j + 1 < nr ? 0.5 * (beta0[j] + beta0[j + 1]) : beta0[j];
+        const double A = spherical ? r1 * r1 : 1.0;
+        w0[j + 1] = Q / (A * be);
+    }
+    if (cutoff >= 0 && cutoff < nr) {
+        const double rc = r_edge[cutoff];
+        for (int e = cutoff + 1; e <= nr; e++) {
+            const double re = r_edge[e];
+            w0[e] = spherical ? w0[cutoff] * (rc * rc) / (re * re) : w0[cutoff];
+        }
+    }
+    return 0;
+}
+
+/* w0 at radius r: linear between the edges around it; beyond the last edge A w0 is
+ * held constant (planar: w0 constant) */
+static double w0_at(int spherical, int nr, const double *r_edge, const double *w0, double r) {
+    if (r >= r_edge[nr]) {
+        const double rl = r_edge[nr];
+        return spherical ? w0[nr] * (rl * rl) / (r * r) : w0[nr];
+    }
+    if (r <= r_edge[0]) return w0[0];
+    int e = 0;
+    while (r_edge[e + 1] < r) e++;
+    const double t = (r - r_edge[e]) / (r_edge[e + 1] - r_edge[e]);
+    return w0[e] + t * (w0[e + 1] - w0[e]);
+}
+
+/* U_f += w0(r_f) (e_r . n_f) on every MAC face (API face layout: n_d + 1 faces along d).
+ * planar: e_r = e_z; the base-state cells are the cell layers, so z-face k gets w0_k.
+ * spherical: the star's centre on corner c; face centre x_f, r_f = |x_f - c dx|. */
+void or_add_w0_faces(const or_geom *g, int spherical, const int *corner, int nr, const double *r_edge,
+                     const double *w0, double *ux, double *uy, double *uz) {
+    const double h = g->dx;
+    double *u[3] = {ux, uy, uz};
+    for (int d = 0; d < 3; d++) {
+        if (!spherical && d != 2) continue;
+        const int m0 = g->n[0] + (d == 0), m1 = g->n[1] + (d == 1), m2 = g->n[2] + (d == 2);
+        long c = 0;
+        for (int k = 0; k < m2; k++)
+            for (int j = 0; j < m1; j++)
+                for (int i = 0; i < m0; i++, c++) {
+                    if (!spherical) {  /* base-state edges are the z faces: needs nr >= n2 */
+                        u[2][c] += w0[k];
+                        continue;
+                    }
+                    /* face centre: integer position along d, half-integer along the others */
+                    const double x = (d == 0 ? i : i + 0.5) * h - corner[0] * h;
+                    const double y = (d == 1 ? j : j + 0.5) * h - corner[1] * h;
+                    const double z = (d == 2 ? k : k + 0.5) * h - corner[2] * h;
+                    const double r = sqrt(x * x + y * y + z * z);
+                    const double comp = d == 0 ? x : (d == 1 ? y : z);
+                    u[d][c] += w0_at(1, nr, r_edge, w0, r) * comp / r;
+                }
+    }
+}
+
+/* the right-hand-side bracket of the U~ constraint: out = S - Sbar on every cell, Sbar
+ * the lateral average of S (planar: plane means; spherical: the irregular radial
+ * means of the corner-centred star) filled back without interpolation */
+void or_subtract_lateral_average(const or_geom *g, int spherical, const int *corner, const double *S,
+                                 double *out) {
+    const long n = (long)g->n[0] * g->n[1] * g->n[2];
+    double *fillv = (double *)malloc(sizeof(double) * n);
+    if (!spherical) {
+        double *prof = (double *)malloc(sizeof(double) * g->n[2]);
+        or_average_planar(g, S, prof);
+        long c = 0;
+        for (int k = 0; k < g->n[2]; k++)
+            for (long q = 0; q < (long)g->n[0] * g->n[1]; q++, c++) fillv[c] = prof[k];
+        free(prof);
+    } else {
+        const long nb = or_radial_nbins(g, corner);
+        double *avg = (double *)malloc(sizeof(double) * nb);
+        long *cnt = (long *)malloc(sizeof(long) * nb);
+        or_average_radial(g, corner, S, nb, avg, cnt);
+        or_fill_irregular(g, corner, avg, fillv);
+        free(avg);
+        free(cnt);
+    }
+    for (long c = 0; c < n; c++) out[c] = S[c] - fillv[c];
+    free(fillv);
 }

@@ -12,7 +12,15 @@ against facts fixed by geometry and algebra, not by the oracle itself:
 - quadratic interpolation reproduces quadratics exactly and, on a cubic, equals
   numpy's degree-2 fit through the three points the stencil rule selects,
   written out independently here (nearest radial centre, shifted inward at the
-  ends)."""
+  ends);
+- the w0 integration of the velocity split (Appendix A): closed forms (w0 = s z
+  for constant beta0 and source; a geometric beta0 profile; r^2 w0 = s r^3/3 in
+  spherical geometry, on uniform and irregular edges; r^2 w0 held beyond a
+  cutoff), and, in planar geometry, the MAC divergence of beta0 w0 e_z, computed
+  by the projection oracle's own divergence, returning beta0 (Sbar - psi);
+- w0 = a r on the faces gives the linear flow a (x - c) component by component;
+- S - Sbar has zero lateral means and S - (S - Sbar) is constant on each
+  plane / radius."""
 import numpy as np
 import pytest
 
@@ -152,3 +160,89 @@ def test_average_to_uniform_exact_on_quadratics_and_stencil_on_cubic():
         assert got[jj] == pytest.approx(fit3(r, rn[s], cub(rn[s])), rel=1e-9, abs=1e-12)
     with pytest.raises(ValueError):
         O.average_to_uniform(np.ones(3), np.array([1, 0, 1]), g.dx, 4, dr)
+
+
+# ---- velocity split (Appendix A) -------------------------------------------------------
+
+def test_w0_planar_closed_forms():
+    nr, h = 24, 0.05
+    r = np.arange(nr + 1) * h
+    # constant beta0 and source: w0 = s z on every edge
+    w = O.w0_integrate(False, r, np.full(nr, 2.5), np.full(nr, 0.3))
+    np.testing.assert_allclose(w, 0.3 * r, rtol=1e-13, atol=1e-16)
+    # geometric beta0_k = q^k: Q_{j+1} = h s (1 - q^(j+1)) / (1 - q), beta0 on an edge the mean
+    q, s = 0.8, -1.7
+    b = q ** np.arange(nr)
+    w = O.w0_integrate(False, r, b, np.full(nr, s))
+    j = np.arange(nr)
+    Q = h * s * (1 - q ** (j + 1)) / (1 - q)
+    be = np.where(j + 1 < nr, 0.5 * (q ** j + q ** np.minimum(j + 1, nr - 1)), q ** j)
+    np.testing.assert_allclose(w[1:], Q / be, rtol=1e-12)
+    assert w[0] == 0.0
+
+
+def test_w0_spherical_closed_form_and_cutoff():
+    nr, dr = 40, 0.01
+    r = np.arange(nr + 1) * dr
+    # constant beta0 and source: r^2 w0 = s r^3 / 3 exactly (the shell integrals telescope)
+    w = O.w0_integrate(True, r, np.full(nr, 0.7), np.full(nr, 1.2))
+    np.testing.assert_allclose(w[1:], 1.2 * r[1:] / 3.0, rtol=1e-12)
+    # irregular edges (the rule does not assume uniform spacing)
+    ri = np.concatenate([[0.0], np.cumsum(np.linspace(0.5, 1.5, nr)) * dr])
+    wi = O.w0_integrate(True, ri, np.full(nr, 0.7), np.full(nr, 1.2))
+    np.testing.assert_allclose(wi[1:], 1.2 * ri[1:] / 3.0, rtol=1e-11)
+    # beyond the cutoff edge r^2 w0 stays at its cutoff value
+    cut = 25
+    wc = O.w0_integrate(True, r, np.linspace(1.0, 0.2, nr), np.linspace(0.5, -0.5, nr), cutoff=cut)
+    wn = O.w0_integrate(True, r, np.linspace(1.0, 0.2, nr), np.linspace(0.5, -0.5, nr))
+    assert np.array_equal(wc[:cut + 1], wn[:cut + 1])
+    np.testing.assert_allclose(wc[cut + 1:] * r[cut + 1:] ** 2, wn[cut] * r[cut] ** 2, rtol=1e-14)
+
+
+def test_w0_planar_matches_the_mac_divergence():
+    """D(beta0_f w0 e_z) of the MAC discretisation returns beta0 (Sbar - psi) on every
+    cell (wall bottom, outflow top): the 1D integration is the discrete inverse of the
+    projection's divergence"""
+    D, P = W.DIRICHLET, W.PERIODIC
+    g = W.Geom((6, 5, 16), 1.0 / 16, (P, P, N), (P, P, D))
+    rng = np.random.default_rng(4)
+    b = np.exp(-np.arange(16) / 5.0)
+    src = rng.standard_normal(16)
+    w = O.w0_integrate(False, np.arange(17) * g.dx, b, src)
+    u = [np.zeros(O.face_shape(g, d)) for d in range(3)]
+    u = O.add_w0_faces(g, False, None, np.arange(17) * g.dx, w, u)
+    beta0 = np.broadcast_to(b[:, None, None], O.cell_shape(g)).copy()
+    div = O.mac_divergence(g, u, beta0)
+    np.testing.assert_allclose(div, (b * src)[:, None, None] * np.ones(O.cell_shape(g)), rtol=1e-11, atol=1e-13)
+    assert np.all(u[0] == 0) and np.all(u[1] == 0)
+
+
+def test_add_w0_faces_spherical_linear_flow():
+    """w0 = a r gives U += a (x - c) on every face, component by component"""
+    g = geom((9, 8, 7), 0.1)
+    c = (4, 5, 2)
+    r = np.arange(0, 40) * 0.05
+    a = 0.9
+    u = O.add_w0_faces(g, True, c, r, a * r, [np.zeros(O.face_shape(g, d)) for d in range(3)])
+    for d in range(3):
+        sh = O.face_shape(g, d)
+        idx = np.meshgrid(*[np.arange(n) for n in sh], indexing="ij")  # (z, y, x) order
+        pos = [idx[2], idx[1], idx[0]]
+        comp = pos[d] * g.dx - c[d] * g.dx  # a d-face sits at an integer position along d
+        np.testing.assert_allclose(u[d], a * comp, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,c", CASES[:3])
+def test_subtract_lateral_average(n, c):
+    g = geom(n)
+    rng = np.random.default_rng(8)
+    S = rng.standard_normal(g.n[::-1]) + 3.0
+    out = O.subtract_lateral_average(g, True, c, S)
+    avg, cnt = O.average_radial(g, c, out)
+    assert np.all(np.abs(avg) < 1e-13)
+    m = O.radial_index(g, c)
+    sb = S - out  # constant on each bin: its bin mean
+    np.testing.assert_allclose(sb, O.average_radial(g, c, S)[0][m], rtol=1e-14, atol=1e-14)
+    outp = O.subtract_lateral_average(g, False, None, S)
+    np.testing.assert_allclose(outp.mean(axis=(1, 2)), 0.0, atol=1e-13)
+    np.testing.assert_allclose(S - outp, np.broadcast_to(S.mean(axis=(1, 2))[:, None, None], S.shape), rtol=1e-13)
