@@ -179,6 +179,48 @@ mx_status mx_radial_to_uniform(mx_ctx *ctx, const mx_geom *geom, const int corne
 mx_status mx_fill_uniform(mx_ctx *ctx, const mx_geom *geom, const int corner[3], const double *prof, int nr,
                           double dr, double *out);
 
+/* ---- Velocity split (Appendix A): U = U~ + w0 e_r --------------------------------------
+ * U~ is projected with div(beta0 U~) = beta0 (S - Sbar), Sbar the lateral average of S;
+ * w0 solves div(beta0 w0 e_r) = beta0 (Sbar - psi), psi = dp0/dt / (Gamma1bar p0),
+ * in one dimension.  Base-state arrays: nr cells between nr + 1 edges r_edge
+ * (device, strictly increasing; spherical: r_edge[0] = 0, the star's centre). */
+
+/* w0 on the nr + 1 edges (device out) from beta0 and src = Sbar - psi on the nr
+ * cells (device):  Q_0 = 0, Q_{j+1} = Q_j + V_j beta0_j src_j, w0_e = Q_e / (A_e
+ * beta0_e); planar A = 1 and V_j = r_{j+1} - r_j, spherical A = r^2 and V_j =
+ * (r_{j+1}^3 - r_j^3)/3; beta0 on an interior edge is the mean of its two cells, on
+ * the last edge the last cell's.  cutoff >= 0: beyond that edge A w0 keeps its
+ * cutoff value (the outer boundary condition at the edge of the star); -1: none.
+ * One CTA, FP64; MX_ERR_ARG for nr < 1 or cutoff outside [-1, nr]. */
+mx_status mx_w0_integrate(mx_ctx *ctx, int spherical, int nr, const double *r_edge, const double *beta0,
+                          const double *src, int cutoff, double *w0);
+
+/* U_f += w0(r_f) (e_r . n_f) on the MAC faces (ux, uy, uz: API face arrays, in/out).
+ * planar (spherical = 0): the base-state cells are the cell layers, z-face k takes
+ *   w0[k] (needs nr >= n2; r_edge, corner, ux, uy may be NULL).
+ * spherical: the star's centre on the cell corner corner[3] (host); w0 linear in r
+ *   between the edges, A w0 held beyond the last edge.  The factor dx w0(r)/r is
+ *   tabulated once per distinct face radius (4 r^2/dx^2 is an integer K) in context
+ *   scratch of 8 (K_max + 1) bytes; MX_ERR_ARG when K_max reaches 2^26. */
+mx_status mx_add_w0_faces(mx_ctx *ctx, const mx_geom *geom, int spherical, const int corner[3], int nr,
+                          const double *r_edge, const double *w0, double *ux, double *uy, double *uz);
+
+/* out = S - Sbar on the cells (device), Sbar the lateral average of S filled back:
+ * plane means (spherical = 0) or the irregular radial means of the star centred on
+ * corner (spherical = 1). */
+mx_status mx_subtract_lateral_average(mx_ctx *ctx, const mx_geom *geom, int spherical, const int corner[3],
+                                      const double *S, double *out);
+
+/* The split MAC projection: the bracket S - Sbar (in context scratch of one cell
+ * array), mx_mac_project of U~ (ux, uy, uz in: U~ predicted; phi, opts, info as
+ * mx_mac_project), then mx_add_w0_faces with the caller's w0 (from
+ * mx_w0_integrate).  Returns the solve's status (MX_ERR_NOCONV still adds w0);
+ * synchronises the stream before returning. */
+mx_status mx_mac_project_split(mx_ctx *ctx, const mx_geom *geom, int spherical, const int corner[3], double *ux,
+                               double *uy, double *uz, const double *rho, const double *beta0, const double *S,
+                               int nr, const double *r_edge, const double *w0, double *phi, const mx_opts *opts,
+                               mx_info *info);
+
 /* MAC projection (Steps 3 and 7; Eq. div1, div2; Appendix A).
  * ux, uy, uz: face velocities U^ADV,dagger (in) -> projected U^ADV (out).
  * rho, beta0, sbar: cell fields; sbar is the whole bracket of the constraint's

@@ -93,6 +93,11 @@ def load():
         "mx_fill_radial": (C.c_int, [_VP, G, _IP3, _DP, C.c_longlong, _DP]),
         "mx_radial_to_uniform": (C.c_int, [_VP, G, _IP3, _DP, C.c_int, C.c_double, _DP]),
         "mx_fill_uniform": (C.c_int, [_VP, G, _IP3, _DP, C.c_int, C.c_double, _DP]),
+        "mx_w0_integrate": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP, _DP, C.c_int, _DP]),
+        "mx_add_w0_faces": (C.c_int, [_VP, G, C.c_int, _IP3, C.c_int, _DP, _DP, _DP, _DP, _DP]),
+        "mx_subtract_lateral_average": (C.c_int, [_VP, G, C.c_int, _IP3, _DP, _DP]),
+        "mx_mac_project_split": (C.c_int, [_VP, G, C.c_int, _IP3, _DP, _DP, _DP, _DP, _DP, _DP, C.c_int, _DP, _DP,
+                                           _DP, O, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -108,7 +113,8 @@ def exported_symbols():
             "mx_fill_base_state", "mx_mac_project", "mx_nodal_project", "mx_apply_op", "mx_residual",
             "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc",
             "mx_autotune", "mx_tune_lookup", "mx_autotune_batched", "mx_radial_nbins", "mx_average_planar",
-            "mx_average_radial", "mx_fill_radial", "mx_radial_to_uniform", "mx_fill_uniform"]
+            "mx_average_radial", "mx_fill_radial", "mx_radial_to_uniform", "mx_fill_uniform", "mx_w0_integrate",
+            "mx_add_w0_faces", "mx_subtract_lateral_average", "mx_mac_project_split"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -257,6 +263,50 @@ def mx_fill_uniform(ctx, geom, corner, prof, dr, out):
     st = load().mx_fill_uniform(ctx, C.byref(make_geom(geom)), _corner(corner), _ptr(prof, None, "prof"),
                                 int(prof.numel()), float(dr), _ptr(out, cell_shape(geom), "out"))
     return _check(ctx, st)
+
+
+# ---- velocity split (Appendix A) ---------------------------------------------------------
+
+def mx_w0_integrate(ctx, spherical, r_edge, beta0, src, w0, cutoff=-1):
+    """w0 (nr + 1 edges) from the base-state beta0 and src = Sbar - psi (nr cells)."""
+    nr = beta0.numel()
+    st = load().mx_w0_integrate(ctx, int(spherical), nr, _ptr(r_edge, (nr + 1,), "r_edge"), _ptr(beta0, (nr,), "beta0"),
+                                _ptr(src, (nr,), "src"), int(cutoff), _ptr(w0, (nr + 1,), "w0"))
+    return _check(ctx, st)
+
+
+def mx_add_w0_faces(ctx, geom, spherical, corner, r_edge, w0, ux, uy, uz):
+    nr = w0.numel() - 1
+    st = load().mx_add_w0_faces(ctx, C.byref(make_geom(geom)), int(spherical), _corner(corner or (0, 0, 0)), nr,
+                                _ptr(r_edge, (nr + 1,), "r_edge") if r_edge is not None else None, _ptr(w0, None, "w0"),
+                                _ptr(ux, face_shape(geom, 0), "ux"), _ptr(uy, face_shape(geom, 1), "uy"),
+                                _ptr(uz, face_shape(geom, 2), "uz"))
+    return _check(ctx, st)
+
+
+def mx_subtract_lateral_average(ctx, geom, spherical, corner, S, out):
+    st = load().mx_subtract_lateral_average(ctx, C.byref(make_geom(geom)), int(spherical),
+                                            _corner(corner or (0, 0, 0)), _ptr(S, cell_shape(geom), "S"),
+                                            _ptr(out, cell_shape(geom), "out"))
+    return _check(ctx, st)
+
+
+def mx_mac_project_split(ctx, geom, spherical, corner, ux, uy, uz, rho, beta0, S, r_edge, w0, phi, opts=None,
+                         allow=(MX_OK,)):
+    """U~ projected with the bracket S - Sbar, then w0 e_r added: (status, info)."""
+    g = make_geom(geom)
+    info = mx_info()
+    cs = cell_shape(geom)
+    nr = w0.numel() - 1
+    st = load().mx_mac_project_split(ctx, C.byref(g), int(spherical), _corner(corner or (0, 0, 0)),
+                                     _ptr(ux, face_shape(geom, 0), "ux"), _ptr(uy, face_shape(geom, 1), "uy"),
+                                     _ptr(uz, face_shape(geom, 2), "uz"), _ptr(rho, cs, "rho"),
+                                     _ptr(beta0, cs, "beta0"), _ptr(S, cs, "S"), nr,
+                                     _ptr(r_edge, (nr + 1,), "r_edge") if r_edge is not None else None,
+                                     _ptr(w0, None, "w0"), _ptr(phi, cs, "phi"),
+                                     C.byref(opts) if opts is not None else None, C.byref(info))
+    _check(ctx, st, allow)
+    return st, info.as_dict()
 
 
 def mx_mac_project(ctx, geom, ux, uy, uz, rho, beta0, sbar, phi, opts=None, allow=(MX_OK,)):

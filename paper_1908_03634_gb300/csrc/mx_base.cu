@@ -68,6 +68,7 @@ struct RadialPlan {
     float2 *G;           // folded column sums, t-major: G[t * ngroups + g]
     int gmax;            // most groups in one fold batch
     double *tab;         // per-bin values of the uniform fill
+    double *avg_tmp;     // per-bin means (scratch of the velocity-split bracket)
     void *mem;
     long long last_use;
 };
@@ -267,10 +268,12 @@ __global__ void __launch_bounds__(BIN_THREADS) rad_bin_kernel(RadDev P, const fl
 
 // Fill from per-bin values, out(i, j, k) = v[T(a) + s], s = T(b) + T(e): the rows of a
 // group share s, so each group's row is gathered once (into smem) and stored to all
-// its rows (16-byte streaming stores for V = 2)
-template <int V>
+// its rows (16-byte streaming stores for V = 2).  SUB: out = src - v[m] instead
+// (the bracket S - Sbar of the velocity split).
+template <int V, bool SUB>
 __global__ void __launch_bounds__(FOLD_THREADS) rad_fill_kernel(RadDev P, const long long *__restrict__ gs,
                                                                 const double *__restrict__ v,
+                                                                const double *__restrict__ src,
                                                                 double *__restrict__ out) {
     extern __shared__ double rowv[];
     const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
@@ -281,10 +284,20 @@ __global__ void __launch_bounds__(FOLD_THREADS) rad_fill_kernel(RadDev P, const 
         __syncthreads();
         const int r0 = P.gstart[g], r1 = P.gstart[g + 1];
         for (int r = r0; r < r1; r++) {
-            double *dst = out + (long long)P.rows[r] * nx;
+            const long long base = (long long)P.rows[r] * nx;
             for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-                if constexpr (V == 2) __stcs(reinterpret_cast<double2 *>(dst) + q, make_double2(rowv[2 * q], rowv[2 * q + 1]));
-                else __stcs(dst + q, rowv[q]);
+                if constexpr (V == 2) {
+                    double2 val = make_double2(rowv[2 * q], rowv[2 * q + 1]);
+                    if constexpr (SUB) {
+                        const double2 x = __ldcs(reinterpret_cast<const double2 *>(src + base) + q);
+                        val = make_double2(x.x - val.x, x.y - val.y);
+                    }
+                    __stcs(reinterpret_cast<double2 *>(out + base) + q, val);
+                } else {
+                    double val = rowv[q];
+                    if constexpr (SUB) val = __ldcs(src + base + q) - val;
+                    __stcs(out + base + q, val);
+                }
             }
         }
         __syncthreads();
@@ -407,6 +420,15 @@ __global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__r
         for (int w = 1; w < PL_THREADS / 32; w++) s = df_add(s, dfloat{ws[w].x, ws[w].y});
         part[(long long)blockIdx.y * nchunk + blockIdx.x] = make_float2(s.h, s.l);
     }
+}
+
+// out = S - prof[k] on plane k (grid: x over the plane, y over planes)
+__global__ void plane_sub_kernel(const double *__restrict__ S, const double *__restrict__ prof, long long nxy,
+                                 double *__restrict__ out) {
+    const long long k = blockIdx.y;
+    const double p = prof[k];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nxy; q += (long long)gridDim.x * blockDim.x)
+        out[k * nxy + q] = S[k * nxy + q] - p;
 }
 
 __global__ void plane_final_kernel(const float2 *__restrict__ part, int nz, int nchunk, long long nxy,
@@ -542,6 +564,7 @@ static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corne
         p->nonempty = bb.take<int>(std::max<size_t>(1, ne.size()));
         p->G = bb.take<float2>((size_t)ngroups * wt);
         p->tab = bb.take<double>(nbins);
+        p->avg_tmp = bb.take<double>(nbins);
     };
     carve(b);
     if (cudaMalloc(&p->mem, b.off) != cudaSuccess) {
@@ -585,20 +608,23 @@ static int fold_threads(int nx) {
     return std::min(FOLD_THREADS, std::max(64, (nv + 31) / 32 * 32));
 }
 
-static mx_status launch_fill(mx_ctx *c, const RadialPlan *p, const double *v, double *out) {
-    if (p->nbatch == 0) return MX_OK;
+template <int V, bool SUB>
+static mx_status launch_fill_t(mx_ctx *c, const RadialPlan *p, const double *v, const double *src, double *out) {
     const size_t smem = (size_t)p->n[0] * sizeof(double);
-    // 16-byte stores need an even row length and a 16-byte aligned array
-    if (p->n[0] % 2 == 0 && ((uintptr_t)out & 15) == 0) {
-        if (smem > 48 * 1024)
-            MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        rad_fill_kernel<2><<<p->nbatch, fold_threads(p->n[0]), smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
-    } else {
-        if (smem > 48 * 1024)
-            MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        rad_fill_kernel<1><<<p->nbatch, fold_threads(p->n[0]), smem, c->stream>>>(rad_dev(p), p->gsv, v, out);
-    }
+    if (smem > 48 * 1024)
+        MX_CUDA(c, cudaFuncSetAttribute(rad_fill_kernel<V, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    rad_fill_kernel<V, SUB><<<p->nbatch, fold_threads(p->n[0]), smem, c->stream>>>(rad_dev(p), p->gsv, v, src, out);
     return MX_OK;
+}
+
+// out = v[m] on every cell, or out = src - v[m] with src
+static mx_status launch_fill(mx_ctx *c, const RadialPlan *p, const double *v, double *out,
+                             const double *src = nullptr) {
+    if (p->nbatch == 0) return MX_OK;
+    // 16-byte accesses need an even row length and 16-byte aligned arrays
+    const bool vec = p->n[0] % 2 == 0 && ((uintptr_t)out & 15) == 0 && ((uintptr_t)src & 15) == 0;
+    if (src) return vec ? launch_fill_t<2, true>(c, p, v, src, out) : launch_fill_t<1, true>(c, p, v, src, out);
+    return vec ? launch_fill_t<2, false>(c, p, v, src, out) : launch_fill_t<1, false>(c, p, v, src, out);
 }
 
 static mx_status check_corner_args(mx_ctx *c, const mx_geom *geom, const int corner[3]) {
@@ -606,6 +632,83 @@ static mx_status check_corner_args(mx_ctx *c, const mx_geom *geom, const int cor
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
     if (!corner) return set_err(c, MX_ERR_ARG, "radial: null corner");
+    return MX_OK;
+}
+
+// the two passes of the radial Average into avg (nbins doubles)
+static mx_status rad_average(mx_ctx *c, const RadialPlan *p, const double *field, double *avg) {
+    const size_t smem = (size_t)p->gmax * p->n[0] * sizeof(float2);
+    const int nthr = fold_threads(p->n[0]);
+    if (p->nbatch > 0) {
+        if (p->n[0] % 2 == 0 && ((uintptr_t)field & 15) == 0) {  // 16-byte loads
+            if (smem > 48 * 1024)
+                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                int(smem)));
+            rad_fold_kernel<2><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
+        } else {
+            if (smem > 48 * 1024)
+                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                int(smem)));
+            rad_fold_kernel<1><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
+        }
+    }
+    const long long nb = (p->nbins + 31) / 32;
+    rad_bin_kernel<<<(unsigned)nb, BIN_THREADS, 0, c->stream>>>(rad_dev(p), p->G, avg);
+    return MX_OK;
+}
+
+// the plane means of field into prof (n2 doubles); scratch: nz * nchunk partial
+// pairs, then n2 doubles (*prof_tmp, for callers that need a profile of their own)
+static mx_status planar_average(mx_ctx *c, const mx_geom *geom, const double *field, double *prof,
+                                double **prof_tmp = nullptr) {
+    const long long nxy = (long long)geom->n[0] * geom->n[1];
+    const int nz = geom->n[2];
+    long long nchunk = std::min((nxy + 1023) / 1024, (2432LL + nz - 1) / nz);
+    nchunk = std::max(1LL, nchunk);
+    const size_t part_b = ((size_t)nz * nchunk * sizeof(float2) + 255) & ~size_t(255);
+    const size_t need = part_b + (size_t)nz * sizeof(double);
+    if (need > c->base_tmp_bytes) {
+        if (c->base_tmp) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->base_tmp);
+        }
+        c->base_tmp = nullptr;
+        c->base_tmp_bytes = 0;
+        if (cudaMalloc(&c->base_tmp, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, MX_ERR_OOM, "average_planar: scratch allocation failed");
+        }
+        c->base_tmp_bytes = need;
+    }
+    float2 *part = (float2 *)c->base_tmp;
+    if (prof_tmp) *prof_tmp = prof = (double *)((char *)c->base_tmp + part_b);
+    if (nxy % 2 == 0 && ((uintptr_t)field & 15) == 0)
+        plane_sum_kernel<2><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
+    else
+        plane_sum_kernel<1><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
+    plane_final_kernel<<<(nz + 7) / 8, 256, 0, c->stream>>>(part, nz, int(nchunk), nxy, prof);
+    MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+// out = S - Sbar, Sbar the lateral average of S filled back onto the cells (plane
+// means, or the irregular radial means of the star centred on corner)
+mx_status base_subtract_average(mx_ctx *c, const mx_geom *geom, int spherical, const int corner[3], const double *S,
+                                double *out) {
+    mx_status st;
+    if (spherical) {
+        RadialPlan *p;
+        if ((st = get_radial_plan(c, geom, corner, &p))) return st;
+        if ((st = rad_average(c, p, S, p->avg_tmp))) return st;
+        if ((st = launch_fill(c, p, p->avg_tmp, out, S))) return st;
+    } else {
+        double *prof = nullptr;
+        if ((st = planar_average(c, geom, S, nullptr, &prof))) return st;
+        const long long nxy = (long long)geom->n[0] * geom->n[1];
+        const long long gx = std::min((nxy + 255) / 256, 64LL);
+        plane_sub_kernel<<<dim3((unsigned)gx, geom->n[2]), 256, 0, c->stream>>>(S, prof, nxy, out);
+    }
+    MX_CUDA(c, cudaGetLastError());
     return MX_OK;
 }
 
@@ -626,32 +729,7 @@ mx_status mx_average_planar(mx_ctx *c, const mx_geom *geom, const double *field,
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
     if (!field || !prof) return set_err(c, MX_ERR_ARG, "average_planar: null array");
-    const long long nxy = (long long)geom->n[0] * geom->n[1];
-    const int nz = geom->n[2];
-    long long nchunk = std::min((nxy + 1023) / 1024, (2432LL + nz - 1) / nz);
-    nchunk = std::max(1LL, nchunk);
-    const size_t need = (size_t)nz * nchunk * sizeof(float2);
-    if (need > c->base_tmp_bytes) {
-        if (c->base_tmp) {
-            cudaStreamSynchronize(c->stream);
-            cudaFree(c->base_tmp);
-        }
-        c->base_tmp = nullptr;
-        c->base_tmp_bytes = 0;
-        if (cudaMalloc(&c->base_tmp, need) != cudaSuccess) {
-            cudaGetLastError();
-            return set_err(c, MX_ERR_OOM, "average_planar: scratch allocation failed");
-        }
-        c->base_tmp_bytes = need;
-    }
-    float2 *part = (float2 *)c->base_tmp;
-    if (nxy % 2 == 0 && ((uintptr_t)field & 15) == 0)
-        plane_sum_kernel<2><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
-    else
-        plane_sum_kernel<1><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
-    plane_final_kernel<<<(nz + 7) / 8, 256, 0, c->stream>>>(part, nz, int(nchunk), nxy, prof);
-    MX_CUDA(c, cudaGetLastError());
-    return MX_OK;
+    return planar_average(c, geom, field, prof);
 }
 
 mx_status mx_average_radial(mx_ctx *c, const mx_geom *geom, const int corner[3], const double *field,
@@ -662,23 +740,7 @@ mx_status mx_average_radial(mx_ctx *c, const mx_geom *geom, const int corner[3],
     RadialPlan *p;
     if ((st = get_radial_plan(c, geom, corner, &p))) return st;
     if (nbins != p->nbins) return set_err(c, MX_ERR_ARG, "average_radial: nbins differs from mx_radial_nbins");
-    const size_t smem = (size_t)p->gmax * p->n[0] * sizeof(float2);
-    const int nthr = fold_threads(p->n[0]);
-    if (p->nbatch > 0) {
-        if (p->n[0] % 2 == 0 && ((uintptr_t)field & 15) == 0) {  // 16-byte loads
-            if (smem > 48 * 1024)
-                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                int(smem)));
-            rad_fold_kernel<2><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
-        } else {
-            if (smem > 48 * 1024)
-                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                int(smem)));
-            rad_fold_kernel<1><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
-        }
-    }
-    const long long nb = (p->nbins + 31) / 32;
-    rad_bin_kernel<<<(unsigned)nb, BIN_THREADS, 0, c->stream>>>(rad_dev(p), p->G, avg);
+    if ((st = rad_average(c, p, field, avg))) return st;
     if (count)
         MX_CUDA(c, cudaMemcpyAsync(count, p->count, p->nbins * sizeof(long long), cudaMemcpyDeviceToDevice,
                                    c->stream));

@@ -90,6 +90,10 @@ struct mx_ctx {
     std::vector<RadialPlan *> rplans;    // lateral average / fill plans, one per (n, corner)
     void *base_tmp = nullptr;            // planar-average partial sums
     size_t base_tmp_bytes = 0;
+    void *split_tab = nullptr;           // velocity split: per-radius face factors
+    size_t split_tab_bytes = 0;
+    void *split_cells = nullptr;         // velocity split: the S - Sbar bracket
+    size_t split_cells_bytes = 0;
     long long use_counter = 0;
     // tracing (mx_profile_enable)
     bool prof = false;
@@ -105,6 +109,10 @@ struct mx_ctx {
 void tune_apply(const mx_ctx *c, int op, const mx_geom *g, mx_opts &o);
 // the same for a batch (nu1, nu2 only), keyed by its boxes' geometries
 void tune_apply_batch(const mx_ctx *c, int nbox, const mx_geom *geoms, mx_opts &o);
+
+// out = S - Sbar (the velocity split's bracket; mx_base.cu)
+mx_status base_subtract_average(mx_ctx *c, const mx_geom *geom, int spherical, const int corner[3], const double *S,
+                                double *out);
 
 // phase markers: no-ops unless tracing is on and the stream is not capturing
 void prof_begin(mx_ctx *c, cudaStream_t s, int phase);

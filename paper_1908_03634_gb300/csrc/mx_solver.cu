@@ -17,6 +17,7 @@ mx_status nodal_apply(mx_ctx *c, const mx_geom *geom, int prec, const double *rh
 void destroy_nodal_plans(mx_ctx *c);
 void destroy_batch_plan(mx_ctx *c);
 void destroy_radial_plans(mx_ctx *c);
+void destroy_split_scratch(mx_ctx *c);
 
 // ------------------------------------------------------------------------------
 // plans
@@ -170,6 +171,7 @@ void destroy_plans(mx_ctx *c) {
     destroy_nodal_plans(c);
     destroy_batch_plan(c);
     destroy_radial_plans(c);
+    destroy_split_scratch(c);
 }
 
 // ------------------------------------------------------------------------------
