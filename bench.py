@@ -564,6 +564,27 @@ def bench_base(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, cpu=True
     ms_uni, _ = timed(lambda i: mx.mx_radial_to_uniform(ctx, g, c, avg, dr, prof), steps, stream)
     mx.mx_fill_uniform(ctx, g, c, prof, dr, out)
     ms_fu, _ = timed(lambda i: mx.mx_fill_uniform(ctx, g, c, prof, dr, out), steps, stream)
+    # velocity split (Appendix A) on the same star: the S - Sbar bracket, the Sbar profile
+    # on the uniform base state (dr = dx/4), w0 from it, and w0 e_r on the MAC faces
+    S = w.sbar
+    bracket = torch.empty_like(S)
+    mx.mx_subtract_lateral_average(ctx, g, 1, c, S, bracket)
+    ms_sub, _ = timed(lambda i: mx.mx_subtract_lateral_average(ctx, g, 1, c, S, bracket), steps, stream)
+    nru = 4 * g.n[0]
+    dru = g.dx / 4
+    r_edge = torch.arange(nru + 1, dtype=torch.float64, device=dev) * dru
+    sbar_u = torch.empty(nru, dtype=torch.float64, device=dev)
+    savg = torch.empty(nb, dtype=torch.float64, device=dev)
+    mx.mx_average_radial(ctx, g, c, S, savg)
+    mx.mx_radial_to_uniform(ctx, g, c, savg, dru, sbar_u)
+    b0u = w.prof_beta0[:nru].contiguous()
+    w0 = torch.empty(nru + 1, dtype=torch.float64, device=dev)
+    mx.mx_w0_integrate(ctx, 1, r_edge, b0u, sbar_u, w0)
+    ms_w0, _ = timed(lambda i: mx.mx_w0_integrate(ctx, 1, r_edge, b0u, sbar_u, w0), steps, stream)
+    mx.mx_add_w0_faces(ctx, g, 1, c, r_edge, w0, *w.u)
+    ms_faces, _ = timed(lambda i: mx.mx_add_w0_faces(ctx, g, 1, c, r_edge, w0, *w.u), steps, stream)
+    nfaces = sum(t.numel() for t in w.u)
+    del bracket
     N = g.ncell
     bytes_avg = 8.0 * N + 8.0 * nb
     bytes_fill = 8.0 * N
@@ -584,6 +605,15 @@ def bench_base(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, cpu=True
          "radial_to_uniform": {"ms": ms_uni / steps, "nr": nr, "launches": 1},
          "fill_uniform": {"ms": ms_fu / steps, "launches": 2},
          "average_planar_256": {"ms": ms_pl / steps, "GB_s": a_pl, "frac": a_pl / hbm, "launches": 2},
+         "velocity_split": {
+             "subtract_lateral_average": {"ms": ms_sub / steps, "launches": 3,
+                                          "GB_s": 24.0 * N / (ms_sub / steps * 1e-3) / 1e9,
+                                          "bytes": "8 B/cell read (average) + 8 read + 8 written (fill-subtract)"},
+             "w0_integrate": {"ms": ms_w0 / steps, "nr": nru, "launches": 1},
+             "add_w0_faces": {"ms": ms_faces / steps, "launches": 4,
+                              "GB_s": 16.0 * nfaces / (ms_faces / steps * 1e-3) / 1e9,
+                              "frac": 16.0 * nfaces / (ms_faces / steps * 1e-3) / 1e9 / hbm,
+                              "bytes": "8 B read + 8 B written per face"}},
          "roofline": {"bound": "hbm", "achieved": round(a_avg, 1), "peak": hbm, "unit": "GB/s",
                       "frac": round(a_avg / hbm, 4), "traffic": _avg_traffic(N),
                       "kernel": "mx_average_radial (fold + bin kernels), 8 B/cell read + 8 B/bin written",

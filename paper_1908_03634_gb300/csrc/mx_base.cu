@@ -20,9 +20,10 @@
 //      whole rows, coalesced) and folds the mirror columns a and -1 - a (equal
 //      T) together into G[group][t], t = (a >= 0 ? a : -1 - a);
 //   2. bins: bin m = s + T(t) sums G[group(s)][t] over t, one lane per bin.
-// Sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of FP32: even
-// one FP64 addition per two cells would cost more than the double-float
-// addition); the bin means are divided in FP64.
+// Per-cell sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of
+// FP32), over the whole double range (WideAcc); the fold adds row pairs in FP64
+// first, which moves about a third of the work to the otherwise idle FP64 pipe.
+// Group column sums, G and the bin sums are doubles (8 bytes like a pair).
 #include <algorithm>
 #include <cmath>
 
@@ -65,7 +66,7 @@ struct RadialPlan {
     long long *count;    // cells per bin
     long long *gsv;      // s of each group
     int *nonempty;       // bins with cells, increasing
-    float2 *G;           // folded column sums, t-major: G[t * ngroups + g]
+    double *G;           // folded column sums, t-major: G[t * ngroups + g]
     int gmax;            // most groups in one fold batch
     double *tab;         // per-bin values of the uniform fill
     double *avg_tmp;     // per-bin means (scratch of the velocity-split bracket)
@@ -121,7 +122,88 @@ struct DfAcc {
     __device__ __forceinline__ dfloat norm() const { return df_norm(h, l); }
 };
 
-// 1. fold: one CTA per batch of whole groups (at most gmax of them).  Each thread
+
+// Sums over the whole double range: a double-float accumulator on the FP32 pipe
+// that holds the values scaled by 2^shift, the shift fixed by the first value
+// (which lands at 2^0; the values of one accumulator, one column of a row group or
+// one bin, share their radius and usually their magnitude).  Values within
+// 2^-73..2^77 of the scale go through the double-float lane (its sums keep 2^50 of
+// headroom below the FP32 range); others, subnormals and non-finite values are
+// added in FP64, out of line.  Zeros are skipped.  Fields such as mass fractions
+// (1e-30) or energies (1e50) stay on the fast lane.
+static __device__ __noinline__ double wide_add(double a, double v) { return a + v; }
+static __device__ __noinline__ double wide_total(double t, double x) { return t + x; }
+struct WideAcc {
+    DfAcc a;
+    double x = 0.0;
+    int shift = 1 << 20;  // unset
+    __device__ __forceinline__ void add(double v) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const unsigned E = (unsigned)(b >> 52) & 0x7ffu;
+        if ((b << 1) == 0ull) return;
+        if (shift == (1 << 20)) shift = (E == 0u || E == 0x7ffu) ? 0 : 1023 - (int)E;
+        const unsigned Es = (unsigned)((int)E + shift);
+        if (Es - 950u < 150u && E - 1u < 0x7feu) a.add(df_split_bits(b, Es));
+        else x = wide_add(x, v);
+    }
+    __device__ __forceinline__ double total() const {
+        double t = 0.0;
+        if (shift != (1 << 20)) {  // 2^-shift (the first value's exponent), exact
+            const double scale = __longlong_as_double((long long)(unsigned long long)(1023 - shift) << 52);
+            t = df_to_double(a.norm()) * scale;
+        }
+        return x != 0.0 ? wide_total(t, x) : t;
+    }
+};
+
+// df_split for the fast passes: magnitudes 2^-73..2^97 (sums of up to 2^27 of them
+// stay below 2^124, inside the FP32 range of the pair's high part); zero gives
+// (0, 0); any other value contributes nothing here and raises *wide (the
+// full-range passes then redo the sum): once per thread (the flag `seen`), one
+// atomic per warp, out of line (kept out of line, the common path compiles to a
+// tighter loop).
+static __device__ __noinline__ void mark_wide(int *wide) {
+    const unsigned m = __activemask();
+    if ((threadIdx.x & 31u) == (unsigned)(__ffs(m) - 1)) atomicOr(wide, 1);
+}
+__device__ __forceinline__ dfloat df_split_mark(double x, bool &seen, int *wide) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned E = (unsigned)(b >> 52) & 0x7ffu;
+    if (E - 950u < 170u) return df_split_bits(b, E);
+    if ((b << 1) != 0ull && !seen) {
+        seen = true;
+        mark_wide(wide);
+    }
+    return dfloat{0.f, 0.f};
+}
+
+// The same with the shift fixed in advance (uniform over a CTA): no per-value
+// initialisation.  shift = 1023 - E0 puts values of exponent E0 at 2^0.
+struct FixedWideAcc {
+    DfAcc a;
+    double x = 0.0;
+    __device__ __forceinline__ void add(double v, int shift) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const unsigned E = (unsigned)(b >> 52) & 0x7ffu;
+        const unsigned Es = (unsigned)((int)E + shift);
+        if (Es - 950u < 150u && E - 1u < 0x7feu) a.add(df_split_bits(b, Es));
+        else if ((b << 1) != 0ull) x = wide_add(x, v);
+    }
+    __device__ __forceinline__ double total(int shift) const {
+        const double scale = __longlong_as_double((long long)(unsigned long long)(1023 - shift) << 52);
+        const double t = df_to_double(a.norm()) * scale;
+        return x != 0.0 ? wide_total(t, x) : t;
+    }
+};
+
+// shift placing the exponent of v at 2^0 (0 for zero, subnormal or non-finite v)
+__device__ __forceinline__ int scale_shift(double v) {
+    const unsigned E = (unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu;
+    return (E == 0u || E == 0x7ffu) ? 0 : 1023 - (int)E;
+}
+
+// 1. fold (the fast pass, values of magnitude 2^-73..2^97; any other value sets
+// *wide and the full-range pass below redoes the Average): one CTA per batch of whole groups (at most gmax of them).  Each thread
 // owns a column (V = 2: a column pair, 16-byte loads; n0 even, so every row
 // starts on a 16-byte boundary) and walks all rows of the batch in rounds of 8
 // loads, across group boundaries (16 loads in flight per thread, no barrier
@@ -131,8 +213,9 @@ struct DfAcc {
 // t-major (G[t][g], runs of the batch's consecutive groups).
 template <int V>
 __global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_kernel(const double *__restrict__ f, RadDev P,
-                                                                float2 *__restrict__ GT) {
+                                                                   float2 *__restrict__ GT, int *__restrict__ wide) {
     extern __shared__ float2 racc[];
+    bool seen = false;
     const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
     const int R0 = P.gstart[g0], R1 = P.gstart[g1];
     const int nx = P.nx, nv = nx / V, wt = P.wt;
@@ -176,15 +259,15 @@ __global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_kernel(const double 
                 if (ra < R1) {
                     if (rb < gend) {  // both rows in the current group
 #pragma unroll
-                        for (int w = 0; w < V; w++) acc[w].add(df_split(v[u][w] + v[u + 1][w]));
+                        for (int w = 0; w < V; w++) acc[w].add(df_split_mark(v[u][w] + v[u + 1][w], seen, wide));
                         if (rb + 1 == gend) flush();
                     } else {  // ra ends the group
 #pragma unroll
-                        for (int w = 0; w < V; w++) acc[w].add(df_split(v[u][w]));
+                        for (int w = 0; w < V; w++) acc[w].add(df_split_mark(v[u][w], seen, wide));
                         flush();
                         if (rb < R1) {
 #pragma unroll
-                            for (int w = 0; w < V; w++) acc[w].add(df_split(v[u + 1][w]));
+                            for (int w = 0; w < V; w++) acc[w].add(df_split_mark(v[u + 1][w], seen, wide));
                             if (rb + 1 == gend) flush();
                         }
                     }
@@ -206,6 +289,107 @@ __global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_kernel(const double 
     }
 }
 
+// 1'. fold, full-range pass (runs only when the fast pass met a value outside its
+// window): as the fast fold, with a wide accumulator whose scale is fixed per CTA
+// and doubles for the column sums and G.  One CTA per batch of whole groups (at most gmax of them).  Each thread
+// owns a column (V = 2: a column pair, 16-byte loads; n0 even, so every row
+// starts on a 16-byte boundary) and walks all rows of the batch in rounds of 8
+// loads, across group boundaries (16 loads in flight per thread, no barrier
+// between groups).  At a
+// group's last row the column sum goes to racc[group][column].  After one
+// barrier the mirror columns a and -1 - a fold together and G is written
+// t-major (G[t][g], runs of the batch's consecutive groups).
+template <int V>
+__global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_wide_kernel(const double *__restrict__ f, RadDev P,
+                                                                        double *__restrict__ GT,
+                                                                        const int *__restrict__ wide) {
+    if (*wide == 0) return;  // the fast pass covered every value
+    extern __shared__ double raccw[];
+    double *racc = raccw;
+    const int g0 = P.bstart[blockIdx.x], g1 = P.bstart[blockIdx.x + 1];
+    const int R0 = P.gstart[g0], R1 = P.gstart[g1];
+    const int nx = P.nx, nv = nx / V, wt = P.wt;
+    // the CTA's scale: the largest magnitude in the middle of its first row (one
+    // warp's reduction, uniform over the CTA)
+    __shared__ int s_shift;
+    if (threadIdx.x < 32) {
+        const int i = min(nx - 1, nx / 2 - 16 + (int)threadIdx.x);
+        double m = fabs(f[(long long)P.rows[R0] * nx + max(0, i)]);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) s_shift = scale_shift(m);
+    }
+    __syncthreads();
+    const int shift = s_shift;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        FixedWideAcc acc[V];
+        int cur = g0, gend = P.gstart[g0 + 1];
+        auto flush = [&]() {
+#pragma unroll
+            for (int w = 0; w < V; w++) {
+                racc[(long long)(cur - g0) * nx + q * V + w] = acc[w].total(shift);
+                acc[w] = FixedWideAcc();
+            }
+            cur++;
+            if (cur < g1) gend = P.gstart[cur + 1];
+        };
+        for (int r = R0; r < R1; r += 8) {
+            double v[8][V];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+#pragma unroll
+                for (int w = 0; w < V; w++) v[u][w] = 0.0;
+                if (r + u < R1) {  // uniform over the CTA
+                    const double *src = f + (long long)P.rows[r + u] * nx + (long long)q * V;
+                    if constexpr (V == 2) {
+                        const double2 t = __ldcs(reinterpret_cast<const double2 *>(src));
+                        v[u][0] = t.x;
+                        v[u][V - 1] = t.y;
+                    } else {
+                        v[u][0] = __ldcs(src);
+                    }
+                }
+            }
+            // rows of the same group add in FP64 pairs before the double-float
+            // accumulation (moves about a third of the work to the FP64 pipe,
+            // which the double-float operations leave idle); group boundaries are
+            // uniform over the CTA, so are these branches
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                const int ra = r + u, rb = ra + 1;
+                if (ra < R1) {
+                    if (rb < gend) {  // both rows in the current group
+#pragma unroll
+                        for (int w = 0; w < V; w++) acc[w].add(v[u][w] + v[u + 1][w], shift);
+                        if (rb + 1 == gend) flush();
+                    } else {  // ra ends the group
+#pragma unroll
+                        for (int w = 0; w < V; w++) acc[w].add(v[u][w], shift);
+                        flush();
+                        if (rb < R1) {
+#pragma unroll
+                            for (int w = 0; w < V; w++) acc[w].add(v[u + 1][w], shift);
+                            if (rb + 1 == gend) flush();
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int ng = g1 - g0;
+    for (int e = threadIdx.x; e < ng * wt; e += blockDim.x) {
+        const int t = e / ng, j = e - t * ng;
+        const int k = P.kmin + t;
+        const int i1 = P.c0 + k, i2 = P.c0 - 1 - k;  // a = k and a = -1 - k
+        const double *ra = racc + (long long)j * nx;
+        double v = 0.0;
+        if (i1 >= 0 && i1 < nx) v = ra[i1];
+        if (i2 >= 0 && i2 < nx) v += ra[i2];
+        GT[(long long)t * P.ngroups + g0 + j] = v;
+    }
+}
+
 // largest t >= 0 with T(t) <= x (-1 for x < 0), x < 2^31: a float estimate corrected
 // with exact integer tests (the estimate is within one of the answer)
 __device__ __forceinline__ long long floor_tinv(long long x) {
@@ -219,7 +403,7 @@ __device__ __forceinline__ long long floor_tinv(long long x) {
     return t;
 }
 
-// 2. bins: a CTA per 32 consecutive bins, lane = bin; the t range splits into one
+// 2. bins, fast pass (reads the fast fold's double-float G): a CTA per 32 consecutive bins, lane = bin; the t range splits into one
 // contiguous slice per warp (for each t the lanes read consecutive s in grp and
 // neighbouring groups in GT[t][.]); the warps' partial sums combine in warp order.
 constexpr int BIN_WARPS = BIN_THREADS / 32;
@@ -263,6 +447,52 @@ __global__ void __launch_bounds__(BIN_THREADS) rad_bin_kernel(RadDev P, const fl
         for (int q = 1; q < BIN_WARPS; q++) sum = df_add(sum, dfloat{part[q][lane].x, part[q][lane].y});
         const long long cnt = P.count[m];
         avg[m] = cnt ? df_to_double(sum) / (double)cnt : 0.0;
+    }
+}
+
+// 2'. bins, full-range pass (after the full-range fold): a CTA per 32 consecutive bins, lane = bin; the t range splits into one
+// contiguous slice per warp (for each t the lanes read consecutive s in grp and
+// neighbouring groups in GT[t][.]); the warps' partial sums combine in warp order.
+__global__ void __launch_bounds__(BIN_THREADS) rad_bin_wide_kernel(RadDev P, const double *__restrict__ GT,
+                                                                   const int *__restrict__ wide,
+                                                                   double *__restrict__ avg) {
+    if (*wide == 0) return;
+    __shared__ double part[BIN_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long m0 = (long long)blockIdx.x * 32, m = m0 + lane;
+    const long long mlast = min(m0 + 31, P.nbins - 1);
+    const long long tlo = max((long long)P.kmin, floor_tinv(m0 - P.smax - 1) + 1);
+    const long long thi = min((long long)P.kmax, floor_tinv(mlast - P.smin));
+    const long long chunk = (thi - tlo + BIN_WARPS) / BIN_WARPS;  // ceil(nt / warps), nt may be 0
+    const long long ta = tlo + w * chunk, tb = min(thi, ta + chunk - 1);
+    WideAcc acc;
+    if (ta <= tb) {
+        // s = m - T(t) falls by t + 1 from t to t + 1; the G row advances by ngroups
+        long long s = m - tri(ta);
+        const double *gt = GT + (ta - P.kmin) * (long long)P.ngroups;
+        const bool live = m < P.nbins;
+        for (long long t = ta; t <= tb; t += 4) {
+            int g[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                g[u] = (live && t + u <= tb && s >= P.smin && s <= P.smax) ? __ldg(P.grp + (s - P.smin)) : -1;
+                s -= t + u + 1;
+            }
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = g[u] >= 0 ? __ldg(gt + (long long)u * P.ngroups + g[u]) : 0.0;
+            gt += 4LL * P.ngroups;
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc.add(v[u]);
+        }
+    }
+    part[w][lane] = acc.total();
+    __syncthreads();
+    if (w == 0 && m < P.nbins) {
+        double sum = part[0][lane];
+        for (int q = 1; q < BIN_WARPS; q++) sum += part[q][lane];
+        const long long cnt = P.count[m];
+        avg[m] = cnt ? sum / (double)cnt : 0.0;
     }
 }
 
@@ -360,7 +590,7 @@ __global__ void rad_to_uniform_kernel(const int *__restrict__ ne, long long nne,
     out[j] = lagrange3_rn(r, bin_radius(m0, dx), avg[m0], bin_radius(m1, dx), avg[m1], bin_radius(m2, dx), avg[m2]);
 }
 
-// planar: per-(plane, chunk) double-float sums, then one warp per plane
+// planar: per-(plane, chunk) sums, then one warp per plane
 constexpr int PL_THREADS = 256;
 __device__ __forceinline__ dfloat warp_df_sum(dfloat a) {
 #pragma unroll
@@ -370,14 +600,21 @@ __device__ __forceinline__ dfloat warp_df_sum(dfloat a) {
     }
     return a;
 }
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
 
-// V = 2: 16-byte loads (n0 n1 even and a 16-byte aligned field); 4 loads in
+// The fast pass (values of magnitude 2^-73..2^97, else *wide is set).  V = 2: 16-byte loads (n0 n1 even and a 16-byte aligned field); 4 loads in
 // flight per thread; neighbouring values add in FP64 pairs, the pair sums in
 // double-float (as in the radial fold)
 template <int V>
 __global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__restrict__ f, long long nxy,
-                                                               int nchunk, float2 *__restrict__ part) {
+                                                               int nchunk, double *__restrict__ part,
+                                                               int *__restrict__ wide) {
     __shared__ float2 ws[PL_THREADS / 32];
+    bool seen = false;
     const long long nv = nxy / V;
     const long long len = (nv + nchunk - 1) / nchunk;
     const long long b0 = (long long)blockIdx.x * len, b1 = min(nv, b0 + len);
@@ -398,18 +635,18 @@ __global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__r
         }
         if constexpr (V == 2) {
 #pragma unroll
-            for (int u = 0; u < 4; u++) acc.add(df_split(v[u][0] + v[u][1]));
+            for (int u = 0; u < 4; u++) acc.add(df_split_mark(v[u][0] + v[u][1], seen, wide));
         } else {
-            acc.add(df_split(v[0][0] + v[1][0]));
-            acc.add(df_split(v[2][0] + v[3][0]));
+            acc.add(df_split_mark(v[0][0] + v[1][0], seen, wide));
+            acc.add(df_split_mark(v[2][0] + v[3][0], seen, wide));
         }
     }
     for (; q < b1; q += PL_THREADS) {
         if constexpr (V == 2) {
             const double2 t = __ldcs(reinterpret_cast<const double2 *>(p) + q);
-            acc.add(df_split(t.x + t.y));
+            acc.add(df_split_mark(t.x + t.y, seen, wide));
         } else {
-            acc.add(df_split(__ldcs(p + q)));
+            acc.add(df_split_mark(__ldcs(p + q), seen, wide));
         }
     }
     dfloat a = warp_df_sum(acc.norm());
@@ -418,7 +655,62 @@ __global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__r
     if (threadIdx.x == 0) {
         dfloat s{ws[0].x, ws[0].y};
         for (int w = 1; w < PL_THREADS / 32; w++) s = df_add(s, dfloat{ws[w].x, ws[w].y});
-        part[(long long)blockIdx.y * nchunk + blockIdx.x] = make_float2(s.h, s.l);
+        part[(long long)blockIdx.y * nchunk + blockIdx.x] = df_to_double(s);
+    }
+}
+
+// Full-range pass of the planar sums (runs when the fast pass set *wide).
+// V = 2: 16-byte loads (n0 n1 even and a 16-byte aligned field); 4 loads in
+// flight per thread; neighbouring values add in FP64 pairs, the pair sums in the
+// wide double-float accumulator (as in the radial fold); per-thread totals reduce
+// in FP64 (a few operations per thread)
+template <int V>
+__global__ void __launch_bounds__(PL_THREADS) plane_sum_wide_kernel(const double *__restrict__ f, long long nxy,
+                                                                    int nchunk, double *__restrict__ part,
+                                                                    const int *__restrict__ wide) {
+    if (*wide == 0) return;
+    __shared__ double ws[PL_THREADS / 32];
+    const long long nv = nxy / V;
+    const long long len = (nv + nchunk - 1) / nchunk;
+    const long long b0 = (long long)blockIdx.x * len, b1 = min(nv, b0 + len);
+    const double *p = f + (long long)blockIdx.y * nxy;
+    WideAcc acc;
+    long long q = b0 + threadIdx.x;
+    for (; q + 3 * PL_THREADS < b1; q += 4 * PL_THREADS) {
+        double v[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if constexpr (V == 2) {
+                const double2 t = __ldcs(reinterpret_cast<const double2 *>(p) + q + u * PL_THREADS);
+                v[u][0] = t.x;
+                v[u][1] = t.y;
+            } else {
+                v[u][0] = __ldcs(p + q + u * PL_THREADS);
+            }
+        }
+        if constexpr (V == 2) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc.add(v[u][0] + v[u][1]);
+        } else {
+            acc.add(v[0][0] + v[1][0]);
+            acc.add(v[2][0] + v[3][0]);
+        }
+    }
+    for (; q < b1; q += PL_THREADS) {
+        if constexpr (V == 2) {
+            const double2 t = __ldcs(reinterpret_cast<const double2 *>(p) + q);
+            acc.add(t.x + t.y);
+        } else {
+            acc.add(__ldcs(p + q));
+        }
+    }
+    const double a = warp_sum(acc.total());
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = ws[0];
+        for (int w = 1; w < PL_THREADS / 32; w++) t += ws[w];
+        part[(long long)blockIdx.y * nchunk + blockIdx.x] = t;
     }
 }
 
@@ -431,17 +723,14 @@ __global__ void plane_sub_kernel(const double *__restrict__ S, const double *__r
         out[k * nxy + q] = S[k * nxy + q] - p;
 }
 
-__global__ void plane_final_kernel(const float2 *__restrict__ part, int nz, int nchunk, long long nxy,
+__global__ void plane_final_kernel(const double *__restrict__ part, int nz, int nchunk, long long nxy,
                                    double *__restrict__ out) {
     const int k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (k >= nz) return;
-    dfloat acc{0.f, 0.f};
-    for (int c = threadIdx.x & 31; c < nchunk; c += 32) {
-        const float2 v = part[(long long)k * nchunk + c];
-        acc = df_add(acc, dfloat{v.x, v.y});
-    }
-    acc = warp_df_sum(acc);
-    if ((threadIdx.x & 31) == 0) out[k] = df_to_double(acc) / (double)nxy;
+    double acc = 0.0;
+    for (int c = threadIdx.x & 31; c < nchunk; c += 32) acc += part[(long long)k * nchunk + c];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) out[k] = acc / (double)nxy;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -468,6 +757,8 @@ void destroy_radial_plans(mx_ctx *c) {
     if (c->base_tmp) cudaFree(c->base_tmp);
     c->base_tmp = nullptr;
     c->base_tmp_bytes = 0;
+    if (c->base_flag) cudaFree(c->base_flag);
+    c->base_flag = nullptr;
 }
 
 static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corner[3], RadialPlan **out) {
@@ -562,7 +853,7 @@ static mx_status get_radial_plan(mx_ctx *c, const mx_geom *geom, const int corne
         p->count = bb.take<long long>(nbins);
         p->gsv = bb.take<long long>(std::max(1, ngroups));
         p->nonempty = bb.take<int>(std::max<size_t>(1, ne.size()));
-        p->G = bb.take<float2>((size_t)ngroups * wt);
+        p->G = bb.take<double>((size_t)ngroups * wt);
         p->tab = bb.take<double>(nbins);
         p->avg_tmp = bb.take<double>(nbins);
     };
@@ -635,25 +926,52 @@ static mx_status check_corner_args(mx_ctx *c, const mx_geom *geom, const int cor
     return MX_OK;
 }
 
-// the two passes of the radial Average into avg (nbins doubles)
-static mx_status rad_average(mx_ctx *c, const RadialPlan *p, const double *field, double *avg) {
-    const size_t smem = (size_t)p->gmax * p->n[0] * sizeof(float2);
-    const int nthr = fold_threads(p->n[0]);
-    if (p->nbatch > 0) {
-        if (p->n[0] % 2 == 0 && ((uintptr_t)field & 15) == 0) {  // 16-byte loads
-            if (smem > 48 * 1024)
-                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                int(smem)));
-            rad_fold_kernel<2><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
-        } else {
-            if (smem > 48 * 1024)
-                MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                int(smem)));
-            rad_fold_kernel<1><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G);
+// the flag the fast passes set when a value lies outside their window (one int per
+// context, cleared at the start of each Average)
+static mx_status wide_flag(mx_ctx *c, int **flag) {
+    if (!c->base_flag) {
+        if (cudaMalloc(&c->base_flag, 256) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, MX_ERR_OOM, "average: flag allocation failed");
         }
     }
+    *flag = (int *)c->base_flag;
+    MX_CUDA(c, cudaMemsetAsync(*flag, 0, sizeof(int), c->stream));
+    return MX_OK;
+}
+
+template <int V>
+static mx_status launch_fold(mx_ctx *c, const RadialPlan *p, const double *field, int *flag, size_t smem, int nthr) {
+    if (smem > 48 * 1024) {
+        MX_CUDA(c, cudaFuncSetAttribute(rad_fold_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        MX_CUDA(c, cudaFuncSetAttribute(rad_fold_wide_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(smem)));
+    }
+    rad_fold_kernel<V><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), (float2 *)p->G, flag);
+    return MX_OK;
+}
+
+// the radial Average into avg (nbins doubles): the fast passes, then the full-range
+// passes, which return at once unless the fast fold flagged a value
+static mx_status rad_average(mx_ctx *c, const RadialPlan *p, const double *field, double *avg) {
+    if (p->nbatch == 0) return MX_OK;
+    int *flag;
+    mx_status st = wide_flag(c, &flag);
+    if (st) return st;
+    const bool vec = p->n[0] % 2 == 0 && ((uintptr_t)field & 15) == 0;  // 16-byte loads
+    const size_t smem = (size_t)p->gmax * p->n[0] * sizeof(double);
+    const int nthr = fold_threads(p->n[0]);
     const long long nb = (p->nbins + 31) / 32;
-    rad_bin_kernel<<<(unsigned)nb, BIN_THREADS, 0, c->stream>>>(rad_dev(p), p->G, avg);
+    if (vec) {
+        if ((st = launch_fold<2>(c, p, field, flag, smem, nthr))) return st;
+    } else {
+        if ((st = launch_fold<1>(c, p, field, flag, smem, nthr))) return st;
+    }
+    rad_bin_kernel<<<(unsigned)nb, BIN_THREADS, 0, c->stream>>>(rad_dev(p), (const float2 *)p->G, avg);
+    if (vec) rad_fold_wide_kernel<2><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G, flag);
+    else rad_fold_wide_kernel<1><<<p->nbatch, nthr, smem, c->stream>>>(field, rad_dev(p), p->G, flag);
+    rad_bin_wide_kernel<<<(unsigned)nb, BIN_THREADS, 0, c->stream>>>(rad_dev(p), p->G, flag, avg);
+    MX_CUDA(c, cudaGetLastError());
     return MX_OK;
 }
 
@@ -665,7 +983,7 @@ static mx_status planar_average(mx_ctx *c, const mx_geom *geom, const double *fi
     const int nz = geom->n[2];
     long long nchunk = std::min((nxy + 1023) / 1024, (2432LL + nz - 1) / nz);
     nchunk = std::max(1LL, nchunk);
-    const size_t part_b = ((size_t)nz * nchunk * sizeof(float2) + 255) & ~size_t(255);
+    const size_t part_b = ((size_t)nz * nchunk * sizeof(double) + 255) & ~size_t(255);
     const size_t need = part_b + (size_t)nz * sizeof(double);
     if (need > c->base_tmp_bytes) {
         if (c->base_tmp) {
@@ -680,12 +998,19 @@ static mx_status planar_average(mx_ctx *c, const mx_geom *geom, const double *fi
         }
         c->base_tmp_bytes = need;
     }
-    float2 *part = (float2 *)c->base_tmp;
+    double *part = (double *)c->base_tmp;
     if (prof_tmp) *prof_tmp = prof = (double *)((char *)c->base_tmp + part_b);
-    if (nxy % 2 == 0 && ((uintptr_t)field & 15) == 0)
-        plane_sum_kernel<2><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
-    else
-        plane_sum_kernel<1><<<dim3((unsigned)nchunk, nz), PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part);
+    int *flag;
+    mx_status st = wide_flag(c, &flag);
+    if (st) return st;
+    const dim3 grid((unsigned)nchunk, nz);
+    if (nxy % 2 == 0 && ((uintptr_t)field & 15) == 0) {
+        plane_sum_kernel<2><<<grid, PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part, flag);
+        plane_sum_wide_kernel<2><<<grid, PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part, flag);
+    } else {
+        plane_sum_kernel<1><<<grid, PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part, flag);
+        plane_sum_wide_kernel<1><<<grid, PL_THREADS, 0, c->stream>>>(field, nxy, int(nchunk), part, flag);
+    }
     plane_final_kernel<<<(nz + 7) / 8, 256, 0, c->stream>>>(part, nz, int(nchunk), nxy, prof);
     MX_CUDA(c, cudaGetLastError());
     return MX_OK;

@@ -34,20 +34,13 @@ static __device__ __noinline__ dfloat df_split_slow(double x) {
 }
 static __device__ __noinline__ double df_f2d_slow(float f) { return double(f); }
 
-// x = hi + lo: hi keeps the top 24 significand bits of x (truncated), lo the
-// next 24 of the remaining 29 (the pair is exact to 2^-48 relative).  Built
-// from the bit pattern with integer operations; zero gives (0, 0) and other
-// exponents outside [2^-73, 2^127) (tiny, huge, non-finite) take the
-// conversion path.
-__device__ __forceinline__ dfloat df_split(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+// The pair of the double with bit pattern b, taken with exponent field E (E equal
+// to b's own field, or shifted to scale the value by a power of two); E must lie in
+// [950, 1150].  hi keeps the top 24 significand bits (truncated), lo the next 24 of
+// the remaining 29 (the pair is exact to 2^-48 relative).
+__device__ __forceinline__ dfloat df_split_bits(unsigned long long b, unsigned E) {
     const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
-    const unsigned E = (hi32 >> 20) & 0x7ffu;
     dfloat r;
-    if (E < 950u || E > 1150u) {
-        if ((b << 1) == 0ull) return dfloat{__uint_as_float(hi32 & 0x80000000u), 0.f};  // +-0
-        return df_split_slow(x);
-    }
     const unsigned sgn = hi32 & 0x80000000u;
     const unsigned mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);  // top 23 fraction bits
     r.h = __uint_as_float(sgn | ((E - 896u) << 23) | mh);
@@ -59,6 +52,19 @@ __device__ __forceinline__ dfloat df_split(double x) {
         r.l = __uint_as_float(sgn | ((unsigned)(k + (int)E - 948) << 23) | (sig & 0x7fffffu));
     }
     return r;
+}
+
+// x = hi + lo from the bit pattern with integer operations; zero gives (0, 0) and
+// other exponents outside [2^-73, 2^127) (tiny, huge, non-finite) take the
+// conversion path.
+__device__ __forceinline__ dfloat df_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned E = (unsigned)(b >> 52) & 0x7ffu;
+    if (E < 950u || E > 1150u) {
+        if ((b << 1) == 0ull) return dfloat{__uint_as_float((unsigned)(b >> 32) & 0x80000000u), 0.f};  // +-0
+        return df_split_slow(x);
+    }
+    return df_split_bits(b, E);
 }
 
 // the float's value as a double, from its bit pattern (normal floats; zero,

@@ -89,6 +89,7 @@ struct mx_ctx {
     BatchPlan *batch = nullptr;
     std::vector<RadialPlan *> rplans;    // lateral average / fill plans, one per (n, corner)
     void *base_tmp = nullptr;            // planar-average partial sums
+    void *base_flag = nullptr;           // averages: a value outside the fast passes' window
     size_t base_tmp_bytes = 0;
     void *split_tab = nullptr;           // velocity split: per-radius face factors
     size_t split_tab_bytes = 0;

@@ -54,6 +54,10 @@ def field(g, seed, kind="star"):
     f = np.exp(-8.0 * r) * (1.0 + 0.1 * np.sin(7 * x) * np.cos(5 * y)) + 1e-3 * rng.standard_normal(r.shape)
     if kind == "signed":
         f = f - f.mean()
+    if kind == "wide":
+        # magnitudes from 1e200 down to 1e-300 (below 2^-73 the sums take the scaled and
+        # FP64 lanes of the accumulator), signs mixed on one side
+        f = 10.0 ** (200.0 - 500.0 * r / max(r.max(), 1e-30)) * (1.0 + 0.5 * rng.standard_normal(r.shape) * (x < 0.3))
     return np.ascontiguousarray(f)
 
 
@@ -78,7 +82,7 @@ RADIAL = [
 
 
 @pytest.mark.parametrize("n,c", RADIAL)
-@pytest.mark.parametrize("kind", ["star", "signed"])
+@pytest.mark.parametrize("kind", ["star", "signed", "wide"])
 def test_average_radial_parity(mx, ctx, n, c, kind):
     g = geom(n)
     f = field(g, 7, kind)
@@ -154,9 +158,10 @@ def test_round_trip_radial_function(mx, ctx):
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (37, 23, 11), (256, 3, 5), (1, 1, 1), (130, 70, 3)])
-@pytest.mark.parametrize("kind", ["star", "signed", "offset"])
+@pytest.mark.parametrize("kind", ["star", "signed", "offset", "wide"])
 def test_average_planar_parity(mx, ctx, shape, kind):
-    """kind offset: the field 8 bytes off a 16-byte boundary (scalar loads)"""
+    """kind offset: the field 8 bytes off a 16-byte boundary (scalar loads); wide:
+    magnitudes from 1e200 to 1e-300"""
     g = geom(shape)
     f = field(g, 4, "star" if kind == "offset" else kind)
     out = torch.empty(g.n[2], dtype=torch.float64, device=DEV)
