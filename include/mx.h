@@ -131,7 +131,9 @@ mx_status mx_fill_base_state(mx_ctx *ctx, const mx_geom *geom, int spherical, co
  * Cell arrays are device doubles of n0 n1 n2 entries, x fastest; the boundary
  * types in geom are not used.  The calls queue work on the context's stream and
  * return without synchronising; sums run in double-float arithmetic in a fixed
- * order, so repeated calls give identical bits.
+ * order, so repeated calls give identical bits.  Fields with magnitudes outside
+ * 2^-73..2^97 are summed exactly as well, by full-range passes that run only
+ * when such a value is present (slower: FP64 for the outliers).
  *
  * Spherical geometry puts the centre of the star on the cell corner corner[3]
  * (host array of three integer corner indices, each within +-2^20; the corner
@@ -200,8 +202,8 @@ mx_status mx_w0_integrate(mx_ctx *ctx, int spherical, int nr, const double *r_ed
  *   w0[k] (needs nr >= n2; r_edge, corner, ux, uy may be NULL).
  * spherical: the star's centre on the cell corner corner[3] (host); w0 linear in r
  *   between the edges, A w0 held beyond the last edge.  The factor dx w0(r)/r is
- *   tabulated once per distinct face radius (4 r^2/dx^2 is an integer K) in context
- *   scratch of 8 (K_max + 1) bytes; MX_ERR_ARG when K_max reaches 2^26. */
+ *   tabulated once per face radius (4 r^2/dx^2 is an integer K, 2 mod 4) in context
+ *   scratch of 2 K_max + 8 bytes; MX_ERR_ARG when K_max / 4 reaches 2^26. */
 mx_status mx_add_w0_faces(mx_ctx *ctx, const mx_geom *geom, int spherical, const int corner[3], int nr,
                           const double *r_edge, const double *w0, double *ux, double *uy, double *uz);
 

@@ -10,9 +10,9 @@
 // cell layers).  Spherical, the centre on the corner c: a d-face sits at integer
 // offset a along d and half-integer offsets along the other two axes, so
 // 4 r^2 / dx^2 = K = 4 a^2 + B^2 + E^2 with B, E odd integers.  The factor
-// dx w0(r) / r is tabulated once per K (FP64, w0 linear in r between edges, A w0
-// held beyond the last edge) and every face takes u += tab[K] a: one FP64 FMA per
-// face, so the pass runs at the HBM rate of its read-modify-write.
+// dx w0(r) / r is tabulated once per K (K is 2 mod 4, so a quarter of the integers
+// up to the largest; FP64, w0 linear in r between edges, A w0 held beyond the last
+// edge) and every face takes u += tab[K >> 2] a: one FP64 FMA per face.
 #include <algorithm>
 #include <cmath>
 
@@ -27,28 +27,38 @@ __device__ __forceinline__ double shell(int sph, double r0, double r1) {
     return sph ? (r1 * r1 * r1 - r0 * r0 * r0) / 3.0 : r1 - r0;
 }
 
-// one CTA: per-thread contiguous chunks, their sums scanned in thread order
+// inclusive scan over the warp's lanes, a fixed shuffle pattern (deterministic)
+__device__ __forceinline__ double warp_scan(double v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// one CTA: per-thread contiguous chunks, their sums scanned in thread order (lanes
+// within a warp, then the warps' totals)
 __global__ void __launch_bounds__(W0_THREADS) w0_kernel(int sph, int nr, const double *__restrict__ re,
                                                         const double *__restrict__ b, const double *__restrict__ src,
                                                         int cutoff, double *__restrict__ w0) {
-    __shared__ double part[W0_THREADS];
+    __shared__ double wsum[W0_THREADS / 32];
     const int chunk = (nr + W0_THREADS - 1) / W0_THREADS;
-    const int j0 = min(nr, threadIdx.x * chunk), j1 = min(nr, j0 + chunk);
+    const int j0 = min(nr, (int)threadIdx.x * chunk), j1 = min(nr, j0 + chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double s = 0.0;
     for (int j = j0; j < j1; j++) s += shell(sph, re[j], re[j + 1]) * b[j] * src[j];
-    part[threadIdx.x] = s;
+    const double incl = warp_scan(s);
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int t = 0; t < W0_THREADS; t++) {
-            const double v = part[t];
-            part[t] = acc;
-            acc += v;
-        }
-        w0[0] = 0.0;
+    if (warp == 0) {
+        const double wi = warp_scan(wsum[lane]);
+        wsum[lane] = wi - wsum[lane];  // exclusive: the warps before this one
     }
     __syncthreads();
-    double Q = part[threadIdx.x];
+    double Q = wsum[warp] + (incl - s);  // everything before this thread's chunk
+    if (threadIdx.x == 0) w0[0] = 0.0;
     for (int j = j0; j < j1; j++) {
         Q += shell(sph, re[j], re[j + 1]) * b[j] * src[j];
         const double be = j + 1 < nr ? 0.5 * (b[j] + b[j + 1]) : b[j];
@@ -64,15 +74,13 @@ __global__ void __launch_bounds__(W0_THREADS) w0_kernel(int sph, int nr, const d
     }
 }
 
-// tab[K] = dx w0(r_K) / r_K, r_K = (dx / 2) sqrt(K)
-__global__ void w0_table_kernel(long long kmax, double dx, int nr, const double *__restrict__ re,
+// tab[q] = dx w0(r_K) / r_K for K = 4q + 2, r_K = (dx / 2) sqrt(K): a face's K is
+// 2 mod 4 (two odd squares sum to 2 mod 8, 4 a^2 is 0 or 4 mod 8)
+__global__ void w0_table_kernel(long long qmax, double dx, int nr, const double *__restrict__ re,
                                 const double *__restrict__ w0, double *__restrict__ tab) {
-    const long long K = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (K > kmax) return;
-    if (K == 0) {
-        tab[0] = 0.0;
-        return;
-    }
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q > qmax) return;
+    const long long K = 4 * q + 2;
     const double r = 0.5 * dx * sqrt((double)K);
     double w;
     if (r >= re[nr]) {
@@ -90,7 +98,7 @@ __global__ void w0_table_kernel(long long kmax, double dx, int nr, const double 
         const double t = (r - re[lo]) / (re[lo + 1] - re[lo]);
         w = w0[lo] + t * (w0[lo + 1] - w0[lo]);
     }
-    tab[K] = dx * w / r;
+    tab[q] = dx * w / r;
 }
 
 // u += tab[K] a on the D-faces (array m0 x m1 x m2, x fastest)
@@ -108,7 +116,7 @@ __global__ void w0_faces_kernel(int m0, int m1, int m2, int c0, int c1, int c2, 
         const long long a = D == 0 ? x : (D == 1 ? y : z);
         const long long K = (D == 0 ? 4 * x * x : x * x) + (D == 1 ? 4 * y * y : y * y) + (D == 2 ? 4 * z * z : z * z);
         const long long f = i + (long long)m0 * (j + (long long)m1 * k);
-        u[f] = fma(__ldg(tab + K), (double)a, u[f]);
+        u[f] = fma(__ldg(tab + (K >> 2)), (double)a, u[f]);  // K = 4q + 2
     }
 }
 
@@ -195,11 +203,12 @@ mx_status mx_add_w0_faces(mx_ctx *c, const mx_geom *geom, int spherical, const i
         if (corner[d] < -(1 << 20) || corner[d] > (1 << 20)) return set_err(c, MX_ERR_ARG, "add_w0_faces: corner out of range");
     long long kmax = 0;
     for (int d = 0; d < 3; d++) kmax = std::max(kmax, kmax_dir(geom, corner, d));
-    if (kmax + 1 > MAX_TAB) return set_err(c, MX_ERR_ARG, "add_w0_faces: corner too far from the box (radius table)");
-    if ((st = grow(c, &c->split_tab, &c->split_tab_bytes, (size_t)(kmax + 1) * sizeof(double), "add_w0_faces")))
+    const long long qmax = kmax >> 2;  // entries for K = 2, 6, ..., kmax
+    if (qmax + 1 > MAX_TAB) return set_err(c, MX_ERR_ARG, "add_w0_faces: corner too far from the box (radius table)");
+    if ((st = grow(c, &c->split_tab, &c->split_tab_bytes, (size_t)(qmax + 1) * sizeof(double), "add_w0_faces")))
         return st;
     double *tab = (double *)c->split_tab;
-    w0_table_kernel<<<(unsigned)((kmax + 256) / 256), 256, 0, c->stream>>>(kmax, geom->dx, nr, r_edge, w0, tab);
+    w0_table_kernel<<<(unsigned)((qmax + 256) / 256), 256, 0, c->stream>>>(qmax, geom->dx, nr, r_edge, w0, tab);
     const dim3 blk(128, 2);
     auto grid = [&](int m0, int m1, int m2) {
         return dim3((m0 + 127) / 128, (m1 + 1) / 2, std::min(m2, 64));
