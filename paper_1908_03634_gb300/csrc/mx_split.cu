@@ -108,6 +108,7 @@ __global__ void w0_faces_kernel(int m0, int m1, int m2, int c0, int c1, int c2, 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= m0 || j >= m1) return;
+#pragma unroll 4
     for (int k = blockIdx.z; k < m2; k += gridDim.z) {
         // integer offset along D, odd half-offsets (times 2) along the others
         const long long x = D == 0 ? (long long)(i - c0) : 2LL * (i - c0) + 1;
@@ -211,7 +212,7 @@ mx_status mx_add_w0_faces(mx_ctx *c, const mx_geom *geom, int spherical, const i
     w0_table_kernel<<<(unsigned)((qmax + 256) / 256), 256, 0, c->stream>>>(qmax, geom->dx, nr, r_edge, w0, tab);
     const dim3 blk(128, 2);
     auto grid = [&](int m0, int m1, int m2) {
-        return dim3((m0 + 127) / 128, (m1 + 1) / 2, std::min(m2, 64));
+        return dim3((m0 + 127) / 128, (m1 + 1) / 2, std::min(m2, 32));
     };
     w0_faces_kernel<0><<<grid(n0 + 1, n1, n2), blk, 0, c->stream>>>(n0 + 1, n1, n2, corner[0], corner[1], corner[2],
                                                                     tab, ux);
