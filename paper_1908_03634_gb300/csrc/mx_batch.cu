@@ -43,10 +43,19 @@ struct BatchPlan {
     // graph of the loop
     cudaGraphExec_t graph = nullptr;
     int g_nu1 = -1, g_nu2 = -1, g_bot = -1;
+    // side streams for the per-box setup and finish (small kernels of different
+    // boxes overlap), each with its own slice of the reduction scratch
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t fork = nullptr;
+    long long part_stride = 0;  // doubles per side stream in the partials
 };
 
 static void free_batch(BatchPlan *B) {
     if (!B) return;
+    for (cudaStream_t q : B->side) cudaStreamDestroy(q);
+    for (cudaEvent_t e : B->side_done) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
     if (B->graph) cudaGraphExecDestroy(B->graph);
     for (MacPlan *p : B->box) free_mac_plan(p);
     if (B->mem) cudaFree(B->mem);
@@ -127,7 +136,24 @@ static BatchPlan *build_batch(mx_ctx *c, int nbox, const DGeom *g, const mx_opts
     }
     B->df.n = int(work.size()) - B->df.off;
     B->nparts = parts;
-    if ((*st = ensure_partials(c, std::max(parts, 152 * 8)))) {
+    // side streams: NSIDE slices of the partials, each large enough for any box
+    constexpr int NSIDE = 8;
+    long long maxblk = 0;
+    for (int b = 0; b < nbox; b++) maxblk = std::max<long long>(maxblk, std::max(stencil_blocks(g[b]), red_blocks(g[b].N)));
+    B->part_stride = 3 * maxblk;
+    if ((*st = ensure_partials(c, std::max<long long>(std::max(parts, 152 * 8), NSIDE * maxblk)))) {
+        free_batch(B);
+        return nullptr;
+    }
+    B->side.resize(NSIDE, nullptr);
+    B->side_done.resize(NSIDE, nullptr);
+    bool ok = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int q = 0; q < NSIDE && ok; q++)
+        ok = cudaStreamCreateWithFlags(&B->side[q], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&B->side_done[q], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        *st = set_err(c, MX_ERR_CUDA, "batched: side stream creation failed");
         free_batch(B);
         return nullptr;
     }
@@ -302,31 +328,52 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
         B.h_st[b] = init;
     }
     MX_CUDA(c, cudaMemcpyAsync(B.d_st, B.h_st, sizeof(SolveState) * nbox, cudaMemcpyHostToDevice, s));
+    // the per-box setup and finish run on the side streams (box b on stream b mod
+    // NSIDE, its partials in that stream's slice), joined back by events
+    const int ns = int(B.side.size());
+    auto fork = [&]() -> mx_status {
+        MX_CUDA(c, cudaEventRecord(B.fork, s));
+        for (int q = 0; q < ns; q++) MX_CUDA(c, cudaStreamWaitEvent(B.side[q], B.fork, 0));
+        return MX_OK;
+    };
+    auto join = [&]() -> mx_status {
+        for (int q = 0; q < ns; q++) {
+            MX_CUDA(c, cudaEventRecord(B.side_done[q], B.side[q]));
+            MX_CUDA(c, cudaStreamWaitEvent(s, B.side_done[q], 0));
+        }
+        return MX_OK;
+    };
     // setup of every box: coefficients and hierarchy, RHS, mean, initial phi
+    if ((st = fork())) return st;
     for (int b = 0; b < nbox; b++) {
         MacPlan &P = *B.box[b];
         const DGeom &gb = g[b];
         SolveState *sb = B.d_st + b;
+        cudaStream_t ss = B.side[b % ns];
+        double *part = c->partials + (b % ns) * B.part_stride;
         const int nb = stencil_blocks(gb), nbr = red_blocks(gb.N);
         const int singular = geom_singular(gb);
-        setup_coefficients(c, P, rho[b], beta0[b]);
-        k_mac_rhs_df(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], P.D, c->partials);
-        k_finalize_rhs(s, c->partials, nb, sb, gb.N, singular && o.remove_mean, 0);
+        setup_coefficients_on(ss, P, rho[b], beta0[b]);
+        k_mac_rhs_df(ss, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], P.D, part);
+        k_finalize_rhs(ss, part, nb, sb, gb.N, singular && o.remove_mean, 0);
         if (singular && !o.remove_mean) {
-            MX_CUDA(c, cudaMemcpyAsync(B.h_st + b, sb, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-            MX_CUDA(c, cudaStreamSynchronize(s));
-            if (std::fabs(B.h_st[b].aux) > 1e-12 * B.h_st[b].fnorm)
+            MX_CUDA(c, cudaMemcpyAsync(B.h_st + b, sb, sizeof(SolveState), cudaMemcpyDeviceToHost, ss));
+            MX_CUDA(c, cudaStreamSynchronize(ss));
+            if (std::fabs(B.h_st[b].aux) > 1e-12 * B.h_st[b].fnorm) {
+                join();
                 return set_err(c, MX_ERR_INCOMPAT, "batched: a singular box has a right-hand side of non-zero mean");
+            }
         }
-        k_sub_mean_scale(s, gb, sb, P.D, c->partials, nbr);
-        k_finalize_rhs(s, c->partials, nbr, sb, gb.N, 0, 1);
+        k_sub_mean_scale(ss, gb, sb, P.D, part, nbr);
+        k_finalize_rhs(ss, part, nbr, sb, gb.N, 0, 1);
         if (o.use_initial_guess) {
-            k_df_from_double(s, gb.N, phi[b], P.D);
+            k_df_from_double(ss, gb.N, phi[b], P.D);
         } else {
-            MX_CUDA(c, cudaMemsetAsync(P.D.ph, 0, sizeof(float) * gb.N, s));
-            MX_CUDA(c, cudaMemsetAsync(P.D.pl, 0, sizeof(float) * gb.N, s));
+            MX_CUDA(c, cudaMemsetAsync(P.D.ph, 0, sizeof(float) * gb.N, ss));
+            MX_CUDA(c, cudaMemsetAsync(P.D.pl, 0, sizeof(float) * gb.N, ss));
         }
     }
+    if ((st = join())) return st;
     // refinement loop over all boxes
     k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 0);
     k_finalize_residual_batch(s, c->partials, B.d_off, B.d_cnt, B.d_st, nbox);
@@ -350,20 +397,24 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
         }
     }
     // finish every box: phi, mean, correction, divergence check
+    if ((st = fork())) return st;
     for (int b = 0; b < nbox; b++) {
         MacPlan &P = *B.box[b];
         const DGeom &gb = g[b];
         SolveState *sb = B.d_st + b;
+        cudaStream_t ss = B.side[b % ns];
+        double *part = c->partials + (b % ns) * B.part_stride;
         const int nb = stencil_blocks(gb), nbr = red_blocks(gb.N);
-        k_df_final(s, gb.N, P.D, sb, phi[b], geom_singular(gb) ? c->partials : nullptr);
+        k_df_final(ss, gb.N, P.D, sb, phi[b], geom_singular(gb) ? part : nullptr);
         if (geom_singular(gb)) {
-            k_finalize_sum(s, c->partials, nbr, &sb->aux, 1.0 / double(gb.N));
-            k_sub_scalar(s, gb.N, phi[b], &sb->aux);
+            k_finalize_sum(ss, part, nbr, &sb->aux, 1.0 / double(gb.N));
+            k_sub_scalar(ss, gb.N, phi[b], &sb->aux);
         }
-        k_mac_correct(s, gb, P.Q, phi[b], ux[b], uy[b], uz[b]);
-        k_mac_divcheck_df(s, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], sb, c->partials);
-        k_finalize_max(s, c->partials, nb, &sb->div_err);
+        k_mac_correct(ss, gb, P.Q, phi[b], ux[b], uy[b], uz[b]);
+        k_mac_divcheck_df(ss, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], sb, part);
+        k_finalize_max(ss, part, nb, &sb->div_err);
     }
+    if ((st = join())) return st;
     MX_CUDA(c, cudaEventRecord(c->ev1, s));
     MX_CUDA(c, cudaMemcpyAsync(B.h_st, B.d_st, sizeof(SolveState) * nbox, cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));

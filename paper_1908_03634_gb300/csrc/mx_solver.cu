@@ -430,7 +430,10 @@ mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
 }
 
 void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0) {
-    cudaStream_t s = c->stream;
+    setup_coefficients_on(c->stream, P, rho, beta0);
+}
+
+void setup_coefficients_on(cudaStream_t s, MacPlan &P, const double *rho, const double *beta0) {
     if (P.prec == MX_PREC_MIXED) {
         k_mac_coeffs_df(s, P.H32.lev[0], P.D, rho, beta0, &P.Q);
         build_hierarchy(s, P.H32);

@@ -36,6 +36,7 @@ MacPlan *get_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st);
 MacPlan *create_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st);
 void free_mac_plan(MacPlan *p);
 void setup_coefficients(mx_ctx *c, MacPlan &P, const double *rho, const double *beta0);
+void setup_coefficients_on(cudaStream_t s, MacPlan &P, const double *rho, const double *beta0);
 mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o);
 template <typename T>
 int coarse_start(const Hier<T> &H);
