@@ -20,10 +20,13 @@
 //      whole rows, coalesced) and folds the mirror columns a and -1 - a (equal
 //      T) together into G[group][t], t = (a >= 0 ? a : -1 - a);
 //   2. bins: bin m = s + T(t) sums G[group(s)][t] over t, one lane per bin.
-// Per-cell sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of
-// FP32), over the whole double range (WideAcc); the fold adds row pairs in FP64
-// first, which moves about a third of the work to the otherwise idle FP64 pipe.
-// Group column sums, G and the bin sums are doubles (8 bytes like a pair).
+// Sums are double-float on the FP32 pipe (GB300 runs FP64 at 1/58 of FP32); the
+// fold adds row pairs in FP64 first, which moves about a third of the work to
+// the otherwise idle FP64 pipe.  The fast passes keep their sums as float pairs
+// and accept magnitudes 2^-73..2^97; a value outside raises a flag, and
+// full-range passes (launched after them, returning at once otherwise) redo the
+// Average with scaled double-float accumulators, FP64 for outliers, and doubles
+// for the staged sums.  The planar Average works the same way.
 #include <algorithm>
 #include <cmath>
 
@@ -202,15 +205,15 @@ __device__ __forceinline__ int scale_shift(double v) {
     return (E == 0u || E == 0x7ffu) ? 0 : 1023 - (int)E;
 }
 
-// 1. fold (the fast pass, values of magnitude 2^-73..2^97; any other value sets
-// *wide and the full-range pass below redoes the Average): one CTA per batch of whole groups (at most gmax of them).  Each thread
-// owns a column (V = 2: a column pair, 16-byte loads; n0 even, so every row
-// starts on a 16-byte boundary) and walks all rows of the batch in rounds of 8
-// loads, across group boundaries (16 loads in flight per thread, no barrier
-// between groups).  At a
-// group's last row the column sum goes to racc[group][column].  After one
-// barrier the mirror columns a and -1 - a fold together and G is written
-// t-major (G[t][g], runs of the batch's consecutive groups).
+// 1. fold, fast pass (magnitudes 2^-73..2^97; any other value raises *wide and
+// the full-range pass below redoes the Average).  One CTA per batch of whole
+// groups (at most gmax of them).  Each thread owns a column (V = 2: a column
+// pair, 16-byte loads; n0 even, so every row starts on a 16-byte boundary) and
+// walks all rows of the batch in rounds of 8 loads, across group boundaries (16
+// loads in flight per thread, no barrier between groups).  At a group's last row
+// the column sum goes to racc[group][column].  After one barrier the mirror
+// columns a and -1 - a fold together and G is written t-major (G[t][g], runs of
+// the batch's consecutive groups).
 template <int V>
 __global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_kernel(const double *__restrict__ f, RadDev P,
                                                                    float2 *__restrict__ GT, int *__restrict__ wide) {
@@ -289,16 +292,10 @@ __global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_kernel(const double 
     }
 }
 
-// 1'. fold, full-range pass (runs only when the fast pass met a value outside its
-// window): as the fast fold, with a wide accumulator whose scale is fixed per CTA
-// and doubles for the column sums and G.  One CTA per batch of whole groups (at most gmax of them).  Each thread
-// owns a column (V = 2: a column pair, 16-byte loads; n0 even, so every row
-// starts on a 16-byte boundary) and walks all rows of the batch in rounds of 8
-// loads, across group boundaries (16 loads in flight per thread, no barrier
-// between groups).  At a
-// group's last row the column sum goes to racc[group][column].  After one
-// barrier the mirror columns a and -1 - a fold together and G is written
-// t-major (G[t][g], runs of the batch's consecutive groups).
+// 1'. fold, full-range pass (returns at once unless the fast pass met a value
+// outside its window): the fast fold's structure, with an accumulator scaled by
+// a power of two fixed per CTA (FP64 for values far from it) and doubles for
+// the column sums and G.
 template <int V>
 __global__ void __launch_bounds__(FOLD_THREADS, 4) rad_fold_wide_kernel(const double *__restrict__ f, RadDev P,
                                                                         double *__restrict__ GT,
@@ -403,9 +400,10 @@ __device__ __forceinline__ long long floor_tinv(long long x) {
     return t;
 }
 
-// 2. bins, fast pass (reads the fast fold's double-float G): a CTA per 32 consecutive bins, lane = bin; the t range splits into one
-// contiguous slice per warp (for each t the lanes read consecutive s in grp and
-// neighbouring groups in GT[t][.]); the warps' partial sums combine in warp order.
+// 2. bins, fast pass (reads the fast fold's double-float G): a CTA per 32
+// consecutive bins, lane = bin; the t range splits into one contiguous slice per
+// warp (for each t the lanes read consecutive s in grp and neighbouring groups in
+// GT[t][.]); the warps' partial sums combine in warp order.
 constexpr int BIN_WARPS = BIN_THREADS / 32;
 __global__ void __launch_bounds__(BIN_THREADS) rad_bin_kernel(RadDev P, const float2 *__restrict__ GT,
                                                               double *__restrict__ avg) {
@@ -450,9 +448,8 @@ __global__ void __launch_bounds__(BIN_THREADS) rad_bin_kernel(RadDev P, const fl
     }
 }
 
-// 2'. bins, full-range pass (after the full-range fold): a CTA per 32 consecutive bins, lane = bin; the t range splits into one
-// contiguous slice per warp (for each t the lanes read consecutive s in grp and
-// neighbouring groups in GT[t][.]); the warps' partial sums combine in warp order.
+// 2'. bins, full-range pass (after the full-range fold; returns at once unless
+// flagged): as the fast bins, over the doubles of G with the wide accumulator.
 __global__ void __launch_bounds__(BIN_THREADS) rad_bin_wide_kernel(RadDev P, const double *__restrict__ GT,
                                                                    const int *__restrict__ wide,
                                                                    double *__restrict__ avg) {
@@ -606,9 +603,10 @@ __device__ __forceinline__ double warp_sum(double a) {
     return a;
 }
 
-// The fast pass (values of magnitude 2^-73..2^97, else *wide is set).  V = 2: 16-byte loads (n0 n1 even and a 16-byte aligned field); 4 loads in
-// flight per thread; neighbouring values add in FP64 pairs, the pair sums in
-// double-float (as in the radial fold)
+// Planar sums, fast pass (magnitudes 2^-73..2^97, else *wide is raised).  V = 2:
+// 16-byte loads (n0 n1 even and a 16-byte aligned field); 4 loads in flight per
+// thread; neighbouring values add in FP64 pairs, the pair sums in double-float
+// (as in the radial fold); one double per block.
 template <int V>
 __global__ void __launch_bounds__(PL_THREADS) plane_sum_kernel(const double *__restrict__ f, long long nxy,
                                                                int nchunk, double *__restrict__ part,
