@@ -207,9 +207,14 @@ __device__ __forceinline__ void rbgs_body(const Level<T> &L, int colour, T h2, i
     }
 }
 
+// The black pass walks z downwards (blocks are dispatched in index order): it
+// starts on the planes the red pass touched last, still in L2, and ends where the
+// next red pass starts.  The cells of one colour update independently, so the
+// order changes no result.
 template <typename T>
 __global__ void rbgs_kernel(Level<T> L, int colour, T h2, int zero, int zc) {
-    rbgs_body(L, colour, h2, zero, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, zc);
+    const int bz = colour ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    rbgs_body(L, colour, h2, zero, blockIdx.x, blockIdx.y, bz, threadIdx.x, threadIdx.y, zc);
 }
 
 dim3 rbgs_grid(const DGeom &g, int zc) {
