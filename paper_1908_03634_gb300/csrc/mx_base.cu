@@ -921,6 +921,7 @@ static mx_status check_corner_args(mx_ctx *c, const mx_geom *geom, const int cor
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
     if (!corner) return set_err(c, MX_ERR_ARG, "radial: null corner");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     return MX_OK;
 }
 
@@ -1052,6 +1053,7 @@ mx_status mx_average_planar(mx_ctx *c, const mx_geom *geom, const double *field,
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
     if (!field || !prof) return set_err(c, MX_ERR_ARG, "average_planar: null array");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     return planar_average(c, geom, field, prof);
 }
 

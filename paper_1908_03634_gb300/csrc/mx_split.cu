@@ -177,8 +177,9 @@ extern "C" {
 mx_status mx_w0_integrate(mx_ctx *c, int spherical, int nr, const double *r_edge, const double *beta0,
                           const double *src, int cutoff, double *w0) {
     if (!c) return MX_ERR_ARG;
-    if (nr < 1 || !r_edge || !beta0 || !src || !w0) return set_err(c, MX_ERR_ARG, "w0_integrate: needs nr >= 1 and arrays");
+    if (nr < 1 || !r_edge || !beta0 || !src || !w0) return set_err(c, MX_ERR_ARG, "w0_integrate: null array or nr < 1");
     if (cutoff < -1 || cutoff > nr) return set_err(c, MX_ERR_ARG, "w0_integrate: cutoff outside [-1, nr]");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     w0_kernel<<<1, W0_THREADS, 0, c->stream>>>(spherical ? 1 : 0, nr, r_edge, beta0, src, cutoff, w0);
     MX_CUDA(c, cudaGetLastError());
     return MX_OK;
@@ -191,6 +192,7 @@ mx_status mx_add_w0_faces(mx_ctx *c, const mx_geom *geom, int spherical, const i
     if (st) return st;
     if (nr < 1 || !w0 || !uz || (spherical && (!ux || !uy || !r_edge || !corner)))
         return set_err(c, MX_ERR_ARG, "add_w0_faces: null array or nr < 1");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     const int n0 = geom->n[0], n1 = geom->n[1], n2 = geom->n[2];
     if (!spherical) {
         if (nr < n2) return set_err(c, MX_ERR_ARG, "add_w0_faces: planar needs nr >= n2 (w0 on the z faces)");
@@ -230,6 +232,7 @@ mx_status mx_subtract_lateral_average(mx_ctx *c, const mx_geom *geom, int spheri
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
     if (!S || !out || (spherical && !corner)) return set_err(c, MX_ERR_ARG, "subtract_lateral_average: null array");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     return base_subtract_average(c, geom, spherical, corner, S, out);
 }
 
@@ -241,6 +244,7 @@ mx_status mx_mac_project_split(mx_ctx *c, const mx_geom *geom, int spherical, co
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
     if (!S) return set_err(c, MX_ERR_ARG, "mac_project_split: null S");
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     const size_t ncell = (size_t)geom->n[0] * geom->n[1] * geom->n[2];
     if ((st = grow(c, &c->split_cells, &c->split_cells_bytes, ncell * sizeof(double), "mac_project_split"))) return st;
     double *bracket = (double *)c->split_cells;

@@ -220,6 +220,23 @@ def test_fill_uniform_parity(mx, ctx, n, c, nr, drf):
     np.testing.assert_allclose(got[~near], want[~near], rtol=0, atol=1e-12 * np.abs(prof).max())
 
 
+def test_null_arrays_rejected(mx, ctx):
+    """the C entry points check their pointers (the binding passes NULL for None)"""
+    lib = mx.load()
+    g = geom((8, 8, 8))
+    gg = mx.make_geom(g)
+    import ctypes as C
+    c3 = (C.c_int * 3)(4, 4, 4)
+    out = torch.zeros(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+    nb = mx.mx_radial_nbins(g, (4, 4, 4))
+    assert lib.mx_average_radial(ctx, C.byref(gg), c3, None, nb, C.c_void_p(out.data_ptr()), None) == mx.MX_ERR_ARG
+    assert lib.mx_fill_radial(ctx, C.byref(gg), c3, None, nb, C.c_void_p(out.data_ptr())) == mx.MX_ERR_ARG
+    assert lib.mx_average_planar(ctx, C.byref(gg), None, C.c_void_p(out.data_ptr())) == mx.MX_ERR_ARG
+    assert lib.mx_subtract_lateral_average(ctx, C.byref(gg), 1, c3, None, C.c_void_p(out.data_ptr())) == mx.MX_ERR_ARG
+    assert lib.mx_w0_integrate(ctx, 1, 4, None, None, None, -1, None) == mx.MX_ERR_ARG
+    assert "null" in mx.mx_last_error(ctx)
+
+
 def test_errors(mx, ctx):
     g = geom((8, 8, 8))
     c = (4, 4, 4)
