@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--star-n", type=int, default=512, help="cube edge of the average512 workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-fcg", action="store_true", help="skip the krylov = 1 comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the nodal and batched workloads")
     p.add_argument("--workload", default="planar256",
@@ -256,6 +257,34 @@ def run_mx(args):
         fp64 = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "vcycles": i64[-1]["vcycles"],
                 "rel_resid": i64[-1]["rel_resid"], "note": "includes a 3-array restore of U per solve"}
 
+    # ---- FCG(1) (krylov = 1) against refinement, both timed in the same loop ----
+    fcg = None
+    if not args.no_fcg:
+        def variant(o, kk):
+            uv = [t.clone() for t in w.u]
+            step(uv, o)  # warm-up (plan, graph)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            iv = []
+            v0.record(stream)
+            for s in range(kk):
+                for d in range(3):
+                    uv[d].copy_(w.u[d])
+                iv.append(step(uv, o)[1])
+            v1.record(stream)
+            torch.cuda.synchronize()
+            assert all(i["status"] == 0 for i in iv), iv[-1]
+            return v0.elapsed_time(v1) / kk, iv[-1]
+        kk = max(3, min(8, K // 2))
+        o_k = mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=opts.nu1, nu2=opts.nu2,
+                              tile_z=opts.tile_z, fused=opts.fused, krylov=1)
+        ms_k, i_k = variant(o_k, kk)
+        ms_r, i_r = variant(opts, kk)
+        fcg = {"solves_per_s": 1e3 / ms_k, "ms_per_solve": ms_k, "vcycles": i_k["vcycles"],
+               "rel_resid": i_k["rel_resid"],
+               "refinement_same_loop": {"solves_per_s": 1e3 / ms_r, "ms_per_solve": ms_r, "vcycles": i_r["vcycles"]},
+               "note": "both include a 3-array restore of U per solve"}
+
     # ---- traced pass: per-phase device time with CUDA events on the launching stream ----
     mx.mx_profile_enable(ctx, True)
     ut = [t.clone() for t in w.u]
@@ -393,7 +422,7 @@ def run_mx(args):
                    "l2_policy": "inputs larger than L2 (fresh U copy per step, ~1.5 GB working set)",
                    "parallelism": f"replicas x{world}"},
         "vcycles_per_solve": vcycles, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
-        "fp64": fp64, "phases": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "fp64": fp64, "fcg": fcg, "phases": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, **extras,
     }
     mx.mx_destroy(ctx)
@@ -753,11 +782,16 @@ def run_other(args):
         o64 = mx.default_opts(prec=mx.MX_PREC_FP64, nu1=tuned.nu1, nu2=tuned.nu2, tile_z=tuned.tile_z)
         step(0, o64)
         ms64, i64 = timed(lambda i: step(i, o64), 1, stream)
+        ok = mx.default_opts(nu1=0, nu2=0, krylov=1)
+        step(0, ok)
+        msk, ik = timed(lambda i: step(i, ok), K, stream)
         print(json.dumps({"workload": "star512", "metric": "MAC projection solves/s to 1e-10 (full star 512^3, "
                           "Dirichlet)", "value": K * 1e3 / ms, "unit": UNIT, "ms_per_solve": ms / K,
                           "vcycles": infos[-1]["vcycles"], "rel_resid": infos[-1]["rel_resid"],
                           "div_err_linf": infos[-1]["div_err_linf"],
                           "fp64": {"solves_per_s": 1e3 / ms64, "vcycles": i64[-1]["vcycles"]},
+                          "fcg": {"solves_per_s": K * 1e3 / msk, "ms_per_solve": msk / K,
+                                  "vcycles": ik[-1]["vcycles"], "rel_resid": ik[-1]["rel_resid"]},
                           "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z,
                                     "fused": tuned.fused},
                           "note": "includes a 3-array restore of U per solve"}), flush=True)

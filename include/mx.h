@@ -71,7 +71,7 @@ typedef struct {
 
 /* Solver options.  mx_default_opts() fills: rel_tol 1e-10, max_outer 100,
  * max_vcycles 100, prec MX_PREC_MIXED, remove_mean 1, use_initial_guess 0,
- * use_graph 1, nu1 = nu2 = 2, bottom_iters 200, fused 0, tile_z 0.
+ * use_graph 1, nu1 = nu2 = 2, bottom_iters 200, fused 0, tile_z 0, krylov 0.
  * nu1 = nu2 = 0 selects the setting mx_autotune() stored in the context for
  * this operator, precision and geometry (nu1, nu2, fused, tile_z), or
  * 2, 2, fused, tile_z as given when nothing is stored. */
@@ -91,6 +91,15 @@ typedef struct {
                               largest z-chunk; smaller levels use fewer): 0 = default
                               (8 MAC, 16 nodal), else 1, 2, 4, 8 or 16; results do not
                               depend on it */
+    int krylov;            /* MAC, MX_PREC_MIXED only: 0 = iterative refinement (phi +=
+                              scale e after each V-cycle); 1 = flexible conjugate
+                              gradients FCG(1) with the FP32 V-cycle as preconditioner:
+                              the direction p = e + beta p_prev is made L-conjugate to
+                              the previous one and phi += t p with the exact line-search
+                              step t, while the residual is still recomputed from phi in
+                              double-float after every step, so the attainable accuracy is
+                              that of refinement.  Other solves reject krylov = 1
+                              (MX_ERR_ARG). */
 } mx_opts;
 
 typedef struct {
@@ -299,7 +308,8 @@ enum {
     MX_PH_RESTRICT_FINE = 3,  /* residual + restriction from the finest level */
     MX_PH_PROLONG_FINE = 4,   /* prolongation onto the finest level */
     MX_PH_COARSE = 5,         /* all coarser levels and the bottom solve */
-    MX_PH_UPDATE = 6,         /* zeroing of the correction and phi += scale e */
+    MX_PH_UPDATE = 6,         /* zeroing of the correction and phi += scale e; with
+                                 krylov = 1 the conjugation and line search */
     MX_PH_FINISH = 7,         /* mean normalisation, velocity correction, divergence check */
     MX_PH_COUNT = 8
 };

@@ -32,7 +32,7 @@ class mx_opts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("max_outer", C.c_int), ("max_vcycles", C.c_int), ("prec", C.c_int),
                 ("remove_mean", C.c_int), ("use_initial_guess", C.c_int), ("use_graph", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("bottom_iters", C.c_int), ("fused", C.c_int),
-                ("tile_z", C.c_int)]
+                ("tile_z", C.c_int), ("krylov", C.c_int)]
 
 
 class mx_info(C.Structure):

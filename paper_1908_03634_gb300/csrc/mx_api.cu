@@ -213,6 +213,7 @@ void mx_default_opts(mx_opts *o) {
     o->bottom_iters = 200;
     o->fused = 0;
     o->tile_z = 0;
+    o->krylov = 0;
 }
 
 int mx_device_supported(int device) {

@@ -333,7 +333,7 @@ __device__ __forceinline__ int df_map(int u, int n, bool per) {
     return u < 0 ? u + n : u - n;
 }
 
-// UPDATE: phi_new = phi_old + scale * e is formed while staging (for the halo
+// UPDATE: phi_new = phi_old + step * e is formed while staging (for the halo
 // too, from the same inputs, so neighbouring tiles agree bit for bit), written
 // to the other phi buffer, and the residual is taken of phi_new.  The two phi
 // buffers alternate with the V-cycle count held on the device.
@@ -354,8 +354,8 @@ __device__ __forceinline__ void df_resid_body(const Level<float> &L, const DFArr
     float *__restrict__ dpl = dst ? D.pl2 : D.pl;
     float sch = 0.f, scl = 0.f;
     if (UPDATE) {
-        sch = st->scale_h;
-        scl = st->scale_l;
+        sch = st->upd_h;
+        scl = st->upd_l;
     }
     for (int q = tid; q < DHX * DHY * DHZ; q += DF_THREADS) {
         const int ax = q % DHX, ay = (q / DHX) % DHY, az = q / (DHX * DHY);
@@ -421,11 +421,14 @@ __device__ __forceinline__ void df_resid_body(const Level<float> &L, const DFArr
     }
 }
 
+// e_odd (may be null): the update direction when the V-cycle count is odd
+// (FCG keeps its two directions in alternating buffers)
 template <bool UPDATE>
 __global__ void __launch_bounds__(DF_THREADS)
-    df_resid_tile_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const SolveState *st, float ih2,
-                         double *part) {
-    df_resid_body<UPDATE>(L, D, e, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z);
+    df_resid_tile_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
+                         const SolveState *st, float ih2, double *part) {
+    const float *ee = (UPDATE && e_odd && (st->iter & 1)) ? e_odd : e;
+    df_resid_body<UPDATE>(L, D, ee, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // batched: work[blockIdx.x] = (box, bx, by, bz); the box's partials start at boxes[box].part_off
@@ -459,12 +462,12 @@ int df_resid_blocks(const DGeom &g) {
 }
 
 void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
-                double *partials) {
+                double *partials, const float *e_odd) {
     const DGeom &g = L0.g;
     const float ih2 = float(1.0 / (g.h * g.h));
     dim3 grid((g.n[0] + DX - 1) / DX, (g.n[1] + DY - 1) / DY, (g.n[2] + DZ - 1) / DZ);
-    if (e) df_resid_tile_kernel<true><<<grid, DF_THREADS, 0, s>>>(L0, D, e, st, ih2, partials);
-    else df_resid_tile_kernel<false><<<grid, DF_THREADS, 0, s>>>(L0, D, nullptr, st, ih2, partials);
+    if (e) df_resid_tile_kernel<true><<<grid, DF_THREADS, 0, s>>>(L0, D, e, e_odd, st, ih2, partials);
+    else df_resid_tile_kernel<false><<<grid, DF_THREADS, 0, s>>>(L0, D, nullptr, nullptr, st, ih2, partials);
 }
 
 // final phi (double) from the current double-float buffer (selected by the

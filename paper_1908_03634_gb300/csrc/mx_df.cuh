@@ -30,9 +30,11 @@ void k_df_from_double(cudaStream_t s, long long n, const double *x, const DFArra
 void k_df_to_double(cudaStream_t s, long long n, const DFArrays &D, double *x);
 void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float *e, const SolveState *st);
 // r = f - L phi (e == nullptr: phi in buffer iter&1) or, with e, phi_new = phi +
-// scale e (read from buffer (iter-1)&1, written to buffer iter&1) and its residual.
+// step e (step = SolveState::upd; phi read from buffer (iter-1)&1, written to
+// buffer iter&1) and its residual.  e_odd (optional): the direction to use
+// instead of e when iter is odd.
 void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
-                double *partials);
+                double *partials, const float *e_odd = nullptr);
 int df_resid_blocks(const DGeom &g);
 dim3 df_resid_grid(const DGeom &g);
 

@@ -48,6 +48,11 @@ struct SolveState {
     double scale, inv_scale;     // r is handed to the correction solve as r / scale
     float scale_h, scale_l;      // scale as a double-float pair, and 1/scale as a float,
     float inv_scale_f;           // for kernels that do no FP64 arithmetic
+    float upd_h, upd_l;          // step of the double-float update phi += step e: the scale
+                                 // (refinement) or the line-search step (FCG)
+    double kry_beta;             // FCG: conjugation coefficient of this iteration
+    double kry_pq;               // FCG: p . (h^2 L p) of the previous direction
+    int kry_restart;             // FCG: 1 = no previous direction (p = e)
     double best;                 // smallest residual seen
     double tol;                  // relative tolerance
     double div_err;              // divergence check of the projected velocity
@@ -65,6 +70,8 @@ __device__ __forceinline__ void set_scale(SolveState *st, double sc) {
     st->scale_h = __double2float_rn(sc);
     st->scale_l = __double2float_rn(sc - double(st->scale_h));
     st->inv_scale_f = __double2float_rn(st->inv_scale);
+    st->upd_h = st->scale_h;
+    st->upd_l = st->scale_l;
 }
 
 struct MacPlan;

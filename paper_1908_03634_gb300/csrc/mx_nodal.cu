@@ -1295,6 +1295,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         o.bottom_iters < 1 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
         !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16))
         return set_err(c, MX_ERR_ARG, "invalid options");
+    if (o.krylov) return set_err(c, MX_ERR_ARG, "nodal: krylov = 1 is for MAC solves");
     tune_apply(c, MX_OP_NODAL, geom, o);
     if (o.nu1 < 1 || o.nu2 < 1) return set_err(c, MX_ERR_ARG, "nodal: nu1 and nu2 must be >= 1 (or both 0)");
     if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "mx_coarse.cuh"
+#include "mx_krylov.cuh"
 #include "mx_rbgs.cuh"
 #include "mx_solver.cuh"
 #include "mx_stencil.cuh"
@@ -100,6 +101,7 @@ static bool same_geom(const DGeom &a, const DGeom &b) {
 void free_mac_plan(MacPlan *p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->mem) cudaFree(p->mem);
+    if (p->kry_mem) cudaFree(p->kry_mem);
     delete p;
 }
 
@@ -143,7 +145,7 @@ mx_status ensure_partials(mx_ctx *c, long long nblocks) {
 }
 
 MacPlan *get_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st) {
-    *st = ensure_partials(c, std::max<long long>(stencil_blocks(g), red_blocks(g.N)));
+    *st = ensure_partials(c, std::max<long long>(std::max(stencil_blocks(g), kry_dir_blocks(g)), red_blocks(g.N)));
     if (*st) return nullptr;
     for (MacPlan *p : c->plans)
         if (p->prec == prec && same_geom(p->g, g)) {
@@ -285,6 +287,21 @@ static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const
     k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
     prof_end(pc, s, MX_PH_RESID64, 2);
 }
+// One FCG(1) iteration after the residual (mx_krylov.cu): V-cycle, conjugate
+// direction and line-search step, phi += t p fused with the next residual.
+static void fcg_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const mx_opts &o, int singular,
+                     mx_ctx *pc) {
+    vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused, o.tile_z ? o.tile_z : 8);
+    Level<float> &L0 = H.lev[0];
+    prof_begin(pc, s, MX_PH_UPDATE);
+    k_kry_dot(s, P.g.N, L0.e, P.kq, c->state, c->partials);
+    k_kry_dir(s, L0, L0.e, P.kp0, P.kp1, P.kq, c->state, c->partials);
+    prof_end(pc, s, MX_PH_UPDATE, 4);
+    prof_begin(pc, s, MX_PH_RESID64);
+    k_df_resid(s, L0, P.D, P.kp0, c->state, c->partials, P.kp1);
+    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
+    prof_end(pc, s, MX_PH_RESID64, 2);
+}
 // Plain FP64: FP64 V-cycle, FP64 update and residual.
 static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, const mx_opts &o, int singular, int nb,
                     mx_ctx *pc, double *phi) {
@@ -314,7 +331,8 @@ void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<doubl
 
 static void ir_step(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, const mx_opts &o, int singular,
                     int nb, mx_ctx *pc) {
-    ir_body(s, c, P, H, o, singular, nb, pc);
+    if (o.krylov) fcg_body(s, c, P, H, o, singular, pc);
+    else ir_body(s, c, P, H, o, singular, nb, pc);
 }
 static void ir_step(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, const mx_opts &o,
                     int singular, int nb, mx_ctx *pc) {
@@ -371,7 +389,8 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
     // the FP64 loop updates phi in place; the mixed loop never touches it
     const void *kphi = sizeof(T) == sizeof(double) ? (const void *)phi : nullptr;
     if (!P.graph || P.graph_phi != kphi || P.graph_nu1 != o.nu1 || P.graph_nu2 != o.nu2 ||
-        P.graph_bot != o.bottom_iters || P.graph_fused != o.fused || P.graph_tilez != o.tile_z) {
+        P.graph_bot != o.bottom_iters || P.graph_fused != o.fused || P.graph_tilez != o.tile_z ||
+        P.graph_krylov != o.krylov) {
         if (P.graph) {
             cudaGraphExecDestroy(P.graph);
             P.graph = nullptr;
@@ -385,6 +404,7 @@ static mx_status run_loop_graph(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, 
         P.graph_bot = o.bottom_iters;
         P.graph_fused = o.fused;
         P.graph_tilez = o.tile_z;
+        P.graph_krylov = o.krylov;
     }
     // the while node runs its body while the condition is 1 (the host checked
     // that the first residual asked for a V-cycle)
@@ -424,8 +444,25 @@ mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
     else mx_default_opts(&o);
     if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.max_vcycles < 0 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
         o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.bottom_iters < 1 || o.bottom_iters > 100000 ||
-        !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16))
+        !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16) ||
+        (o.krylov != 0 && o.krylov != 1))
         return set_err(c, MX_ERR_ARG, "invalid options");
+    if (o.krylov && o.prec != MX_PREC_MIXED) return set_err(c, MX_ERR_ARG, "krylov = 1 needs prec = MX_PREC_MIXED");
+    return MX_OK;
+}
+
+// FCG buffers of a mixed plan: two directions and q, N floats each
+static mx_status ensure_krylov(mx_ctx *c, MacPlan &P) {
+    if (P.kry_mem) return MX_OK;
+    const size_t per = ((size_t)P.g.N * sizeof(float) + 255) & ~size_t(255);
+    if (cudaMalloc(&P.kry_mem, 3 * per) != cudaSuccess) {
+        cudaGetLastError();
+        P.kry_mem = nullptr;
+        return set_err(c, MX_ERR_OOM, "krylov buffers: cudaMalloc failed");
+    }
+    P.kp0 = P.kry_mem;
+    P.kp1 = (float *)((char *)P.kry_mem + per);
+    P.kq = (float *)((char *)P.kry_mem + 2 * per);
     return MX_OK;
 }
 
@@ -458,6 +495,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     const int singular = geom_singular(g);
     MacPlan *P = get_mac_plan(c, g, o.prec, &st);
     if (!P) return st;
+    if (o.krylov && (st = ensure_krylov(c, *P))) return st;
     cudaStream_t s = c->stream;
     const int nb = stencil_blocks(g);
     const int nbr = red_blocks(g.N);
@@ -467,6 +505,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     SolveState init = {};
     init.tol = o.rel_tol;
     init.maxit = std::min(o.max_outer, o.max_vcycles);
+    init.kry_restart = 1;
     *c->hstate = init;
     MX_CUDA(c, cudaMemcpyAsync(c->state, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
 

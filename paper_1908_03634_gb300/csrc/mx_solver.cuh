@@ -25,10 +25,13 @@ struct MacPlan {
     Hier<double> H64;   // FP64: the FP64 correction hierarchy (level 0 shares L64's coefficients)
     FaceQ Q;            // correction factors 2/(h (rho_L + rho_R)) of the finest faces
     float *tmp32 = nullptr;
+    // FCG (mx_opts::krylov): two direction buffers and q = h^2 L p, allocated on first use
+    float *kry_mem = nullptr;
+    float *kp0 = nullptr, *kp1 = nullptr, *kq = nullptr;
     // CUDA graph of the refinement loop, keyed by the pointers it was captured with
     cudaGraphExec_t graph = nullptr;
     const void *graph_phi = nullptr;
-    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_fused = -1, graph_tilez = -1;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_fused = -1, graph_tilez = -1, graph_krylov = -1;
     long long last_use = 0;
 };
 
