@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-fcg", action="store_true", help="skip the krylov = 1 comparison")
+    p.add_argument("--krylov", action="store_true",
+                   help="run the headline solves with krylov = 1 (FCG around the V-cycle; for profiling)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the nodal and batched workloads")
     p.add_argument("--workload", default="planar256",
@@ -125,21 +127,23 @@ def algorithmic_bytes_per_cell():
     return {"smooth_fine": 12.0, "resid64": 44.0}
 
 
-def launches_per_solve(g, o, vcycles, graph):
+def launches_per_solve(g, o, vcycles, graph, krylov=0):
     """Kernels the library launches for one mixed-precision MAC solve (fill
     included), from the solver's structure: setup 13 + first residual 2; per
     refinement iteration the V-cycle's launches on the levels above the coarse
     end (> 4096 cells: colour passes, residual+restriction, prolongation, or
     single-pass sweeps), the coarse-end CTA, update+residual and its finalize
     (+1 condition kernel inside the graph); finish 6 (4 without a mean to
-    remove).  Checked against the ncu launch list of the planar 256^3 solve."""
+    remove).  FCG (krylov = 1) adds 4 per iteration: the dot product, its
+    finalize, the direction/stencil pass and the step finalize.  Checked against
+    the ncu launch lists of the planar 256^3 solve."""
     dims = [list(g.n)]
     while all(d % 2 == 0 and d >= 4 for d in dims[-1]):
         dims.append([d // 2 for d in dims[-1]])
     nlev = len(dims)
     ncell = [d[0] * d[1] * d[2] for d in dims]
     ldown = next((l for l in range(nlev) if ncell[l] <= 4096), nlev - 1)
-    per_iter = 1 + 2 + (1 if graph else 0)
+    per_iter = 1 + 2 + (1 if graph else 0) + (4 if krylov else 0)
     for l in range(ldown):
         fused = o.fused and ncell[l] >= (1 << 18) and dims[l][0] % 2 == 0
         per_iter += (o.nu1 + 1 + o.nu2) if fused else (2 * o.nu1 + 1 + 1 + 2 * o.nu2)
@@ -201,9 +205,10 @@ def run_mx(args):
             ctx, mx.MX_OP_MAC, g, *w.u, rho, beta0, sbar,
             base=mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=graph))
     t_tune = time.perf_counter() - t_tune
+    kry = 1 if args.krylov else 0
     opts = (mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=tuned.nu1, nu2=tuned.nu2,
-                            tile_z=tuned.tile_z) if args.fixed else
-            mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=0, nu2=0))
+                            tile_z=tuned.tile_z, krylov=kry) if args.fixed else
+            mx.default_opts(prec=mx.MX_PREC_MIXED, use_graph=graph, nu1=0, nu2=0, krylov=kry))
 
     def step(u, o=opts):
         mx.mx_fill_base_state(ctx, g, 0, prof, g.dx, (0.5, 0.5, 0.5), beta0)
@@ -232,7 +237,7 @@ def run_mx(args):
     last = infos[-1]
     assert all(i["status"] == 0 for i in infos), infos[-1]
     vcycles = statistics.mean(i["vcycles"] for i in infos[Wm:])
-    launches = int(round(K * launches_per_solve(g, tuned, vcycles, graph)))
+    launches = int(round(K * launches_per_solve(g, tuned, vcycles, graph, kry)))
 
     # ---- plain FP64 solve (the comparison) ----
     fp64 = None
@@ -414,7 +419,8 @@ def run_mx(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"planar{n}", "cells": g.ncell, "bc": "periodic x,y / wall z",
                    "density_contrast": 1e5, "beta0": "rho0^(3/5)", "rel_tol": 1e-10,
-                   "precision": "FP32 V-cycles in FP64 iterative refinement",
+                   "precision": ("FP32 V-cycles as the FCG(1) preconditioner, double-float residual" if kry else
+                                 "FP32 V-cycles in FP64 iterative refinement"),
                    "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z, "fused": tuned.fused,
                              "fp64": None if tuned64 is None else {"nu1": tuned64.nu1, "nu2": tuned64.nu2,
                                                                    "tile_z": tuned64.tile_z},

@@ -7,10 +7,10 @@
 // GB300 executes FP64 at 1/58 of its FP32 rate, so an FP64 residual is bound
 // by the FP64 pipe while these kernels stay bound by memory bandwidth.
 //
-// Accuracy: the coefficients and RHS are the FP64 values rounded to 48 bits
-// (relative 2^-48); the residual of the stored phi is computed with an error of
-// a few 2^-48 relative to the largest flux term, far below the 1e-10 relative
-// residual the loop converges to.
+// Accuracy: the RHS is the FP64 value rounded to 48 bits (relative 2^-48) and
+// the coefficients are within a few 2^-48; the residual of the stored phi is
+// computed with an error of a few 2^-48 relative to the largest flux term, far
+// below the 1e-10 relative residual the loop converges to.
 #include "mx_df.cuh"
 #include "mx_dfmath.cuh"
 #include "mx_stencil.cuh"
@@ -32,80 +32,124 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
 
 // ---- coefficients b = (beta0_L + beta0_R)/(rho_L + rho_R) in double-float,
 // stored as hi (the FP32 level-0 array) + lo, and (q non-null) the correction
-// factors q = 2/(h (rho_L + rho_R)) as FP64.  rho and beta0 are split into
-// double-float once per cell (the column carries the cell below); a Dirichlet
-// face uses the interior cell: b = 2 beta0/rho, q = 2/(h rho). ----------------
+// factors q = 2/(h (rho_L + rho_R)) as FP64; a Dirichlet face uses the interior
+// cell: b = 2 beta0/rho, q = 2/(h rho).  Both come from one double-float
+// reciprocal of the face's rho sum (a few 2^-48 relative).  rho and beta0 are
+// split into double-float once per cell: the split goes to the +x neighbour by
+// warp shuffle and to the +y neighbour through shared memory, and the column
+// carries the cell below; so every thread of the block runs the plane loop. ----
+__device__ __forceinline__ dfloat df_recip(dfloat a) {
+    const float r0 = __frcp_rn(a.h);
+    float e = fmaf(-a.h, r0, 1.0f);
+    e = fmaf(-a.l, r0, e);
+    return df_norm(r0, r0 * e);
+}
+
 __global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, FaceQ Q, const double *__restrict__ rho,
                                      const double *__restrict__ beta0, dfloat ih2x) {
+    __shared__ dfloat sr[2][SY][SX], sbt[2][SY][SX];
     const DGeom &g = L.g;
-    const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * SX + tx, j = blockIdx.y * SY + ty;
     const int k0 = blockIdx.z * ZC;
-    if (i >= g.n[0] || j >= g.n[1]) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long long nxy = g.nxy;
     const int k1 = min(k0 + ZC, nz);
+    const bool act = i < nx && j < ny;
     const bool wq = Q.x != nullptr;
+    const dfloat zero = {0.f, 0.f};
     auto store = [&](float *bh, float *bl, double *qd, long long o, dfloat b, dfloat q) {
         bh[o] = b.h;
         bl[o] = b.l;
         if (wq) qd[o] = df_to_double(q);
     };
     auto face = [&](dfloat rl, dfloat bl, dfloat rr, dfloat br, dfloat &b, dfloat &q) {
-        const dfloat rs = df_add(rl, rr);
-        b = df_div(df_add(bl, br), rs);
-        q = df_div(ih2x, rs);
+        const dfloat inv = df_recip(df_add(rl, rr));
+        b = df_mul(df_add(bl, br), inv);
+        q = df_mul(ih2x, inv);
     };
     auto own = [&](int bc, dfloat r, dfloat be, dfloat &b, dfloat &q) {
         if (bc == MX_BC_DIRICHLET) {
-            b = df_div(df_add(be, be), r);
-            q = df_div(ih2x, r);
+            const dfloat inv = df_recip(r);
+            b = df_mul(df_add(be, be), inv);
+            q = df_mul(ih2x, inv);
         } else {
-            b = dfloat{0.f, 0.f};
-            q = dfloat{0.f, 0.f};
+            b = zero;
+            q = zero;
         }
     };
-    long long c = i + (long long)nx * (j + (long long)ny * k0);
-    // the cell below the first one (its wrap image when periodic)
-    dfloat rdn = {0.f, 0.f}, bdn = {0.f, 0.f};
-    if (k0 > 0 || gper(g, 2)) {
-        const long long cd = k0 > 0 ? c - nxy : c + (long long)(nz - 1) * nxy;
-        rdn = df_split(rho[cd]);
-        bdn = df_split(beta0[cd]);
+    long long c = act ? i + (long long)nx * (j + (long long)ny * k0) : 0;
+    dfloat rc = zero, bc = zero, rdn = zero, bdn = zero;
+    if (act) {
+        rc = df_split(rho[c]);
+        bc = df_split(beta0[c]);
+        // the cell below the first one (its wrap image when periodic)
+        if (k0 > 0 || gper(g, 2)) {
+            const long long cd = k0 > 0 ? c - nxy : c + (long long)(nz - 1) * nxy;
+            rdn = df_split(rho[cd]);
+            bdn = df_split(beta0[cd]);
+        }
     }
-    for (int k = k0; k < k1; k++, c += nxy) {
-        const dfloat rc = df_split(rho[c]), bc = df_split(beta0[c]);
-        dfloat b, q;
-        if (i > 0 || gper(g, 0)) {
-            const long long cl = i > 0 ? c - 1 : c + nx - 1;
-            face(df_split(rho[cl]), df_split(beta0[cl]), rc, bc, b, q);
-        } else {
-            own(g.lo[0], rc, bc, b, q);
+    int buf = 0;
+    for (int k = k0; k < k1; k++, c += nxy, buf ^= 1) {
+        sr[buf][ty][tx] = rc;
+        sbt[buf][ty][tx] = bc;
+        dfloat rw, bw;
+        rw.h = __shfl_up_sync(0xffffffffu, rc.h, 1);
+        rw.l = __shfl_up_sync(0xffffffffu, rc.l, 1);
+        bw.h = __shfl_up_sync(0xffffffffu, bc.h, 1);
+        bw.l = __shfl_up_sync(0xffffffffu, bc.l, 1);
+        __syncthreads();
+        if (act) {
+            dfloat b, q;
+            if (i > 0 || gper(g, 0)) {
+                if (tx == 0) {
+                    const long long cl = i > 0 ? c - 1 : c + nx - 1;
+                    rw = df_split(rho[cl]);
+                    bw = df_split(beta0[cl]);
+                }
+                face(rw, bw, rc, bc, b, q);
+            } else {
+                own(g.lo[0], rc, bc, b, q);
+            }
+            store(L.bx, D.bxl, Q.x, c, b, q);
+            if (j > 0 || gper(g, 1)) {
+                dfloat rs, bs;
+                if (ty > 0) {
+                    rs = sr[buf][ty - 1][tx];
+                    bs = sbt[buf][ty - 1][tx];
+                } else {
+                    const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
+                    rs = df_split(rho[cs]);
+                    bs = df_split(beta0[cs]);
+                }
+                face(rs, bs, rc, bc, b, q);
+            } else {
+                own(g.lo[1], rc, bc, b, q);
+            }
+            store(L.by, D.byl, Q.y, c, b, q);
+            if (k > 0 || gper(g, 2)) face(rdn, bdn, rc, bc, b, q);
+            else own(g.lo[2], rc, bc, b, q);
+            store(L.bz, D.bzl, Q.z, c, b, q);
+            if (i == nx - 1 && L.hx) {
+                own(g.hi[0], rc, bc, b, q);
+                store(L.hx, D.hxl, Q.hx, j + (long long)ny * k, b, q);
+            }
+            if (j == ny - 1 && L.hy) {
+                own(g.hi[1], rc, bc, b, q);
+                store(L.hy, D.hyl, Q.hy, i + (long long)nx * k, b, q);
+            }
+            if (k == nz - 1 && L.hz) {
+                own(g.hi[2], rc, bc, b, q);
+                store(L.hz, D.hzl, Q.hz, i + (long long)nx * j, b, q);
+            }
+            rdn = rc;
+            bdn = bc;
+            if (k + 1 < k1) {
+                rc = df_split(rho[c + nxy]);
+                bc = df_split(beta0[c + nxy]);
+            }
         }
-        store(L.bx, D.bxl, Q.x, c, b, q);
-        if (j > 0 || gper(g, 1)) {
-            const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
-            face(df_split(rho[cs]), df_split(beta0[cs]), rc, bc, b, q);
-        } else {
-            own(g.lo[1], rc, bc, b, q);
-        }
-        store(L.by, D.byl, Q.y, c, b, q);
-        if (k > 0 || gper(g, 2)) face(rdn, bdn, rc, bc, b, q);
-        else own(g.lo[2], rc, bc, b, q);
-        store(L.bz, D.bzl, Q.z, c, b, q);
-        if (i == nx - 1 && L.hx) {
-            own(g.hi[0], rc, bc, b, q);
-            store(L.hx, D.hxl, Q.hx, j + (long long)ny * k, b, q);
-        }
-        if (j == ny - 1 && L.hy) {
-            own(g.hi[1], rc, bc, b, q);
-            store(L.hy, D.hyl, Q.hy, i + (long long)nx * k, b, q);
-        }
-        if (k == nz - 1 && L.hz) {
-            own(g.hi[2], rc, bc, b, q);
-            store(L.hz, D.hzl, Q.hz, i + (long long)nx * j, b, q);
-        }
-        rdn = rc;
-        bdn = bc;
     }
 }
 
@@ -125,44 +169,78 @@ void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, 
 // Face flux times 2: (beta0_L + beta0_R) U_f inside and across periodic faces,
 // (beta0_in + beta0_in) U_f on a Dirichlet face, 0 on a wall (operands are
 // selected, then one expression is evaluated); the factor 1/(2h) is applied
-// once per cell and the column carries the high z-face flux up.
-__device__ __forceinline__ dfloat df_face_flux2(const DGeom &g, const double *__restrict__ beta0, int d, int p,
-                                                long long c_lo, long long c_hi, double u) {
-    const int n = g.n[d];
-    const bool inner = (p > 0 && p < n) || gper(g, d);
-    const int bc = p == 0 ? g.lo[d] : g.hi[d];
-    const long long cin = p == 0 ? c_hi : c_lo;
-    const bool wall = !inner && bc != MX_BC_DIRICHLET;
-    const dfloat a = df_split(wall ? 0.0 : beta0[inner ? c_lo : cin]);
-    const dfloat b = df_split(wall ? 0.0 : beta0[inner ? c_hi : cin]);
-    return df_mul(df_add(a, b), df_split(u));
-}
-
+// once per cell.
+// The cells of a thread's column, plane by plane.  Along x the warp's lanes
+// are neighbouring cells: a cell's beta0 split goes to its +x neighbour by
+// shuffle and its x-low face flux back as that neighbour's x-high flux, so
+// every x face is evaluated once (lane 31, and the cell on the box's high x
+// edge, evaluate their own high face).  The y faces are evaluated per cell,
+// and the z-high flux with the split above carries to the next plane.  The
+// arithmetic per face is the same wherever it is evaluated.  Every lane of a
+// warp calls this (act = false outside the box): the shuffles take the warp.
 template <typename F>
-__device__ __forceinline__ void df_div_column(const DGeom &g, const double *__restrict__ ux,
-                                              const double *__restrict__ uy, const double *__restrict__ uz,
-                                              const double *__restrict__ beta0, const double *__restrict__ sbar,
-                                              int i, int j, int k0, int k1, dfloat hih, F fn) {
+__device__ __forceinline__ void df_div_block(const DGeom &g, const double *__restrict__ ux,
+                                             const double *__restrict__ uy, const double *__restrict__ uz,
+                                             const double *__restrict__ beta0, const double *__restrict__ sbar,
+                                             int i, int j, int k0, int k1, dfloat hih, F fn) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long long nxy = g.nxy;
-    long long c = i + (long long)nx * (j + (long long)ny * k0);
-    dfloat fzl = df_face_flux2(g, beta0, 2, k0, k0 > 0 ? c - nxy : c + (long long)(nz - 1) * nxy, c, uz[c]);
+    static_assert(SX == 32, "one warp per row of the block");
+    const int lane = threadIdx.x;
+    const bool act = i < nx && j < ny;
+    const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
+    const dfloat zero = {0.f, 0.f};
+    // twice the flux at face p of axis d from the split beta0 of its low (bl)
+    // and high (bh) cells: the face mean inside and across periodic faces, the
+    // interior cell's value on a Dirichlet face, 0 on a wall
+    auto flux2 = [&](int d, int p, dfloat bl, dfloat bh, double u) -> dfloat {
+        dfloat a = bl, b = bh;
+        if (!((p > 0 && p < g.n[d]) || gper(g, d))) {
+            const int bc = p == 0 ? g.lo[d] : g.hi[d];
+            a = bc == MX_BC_DIRICHLET ? (p == 0 ? bh : bl) : zero;
+            b = a;
+        }
+        return df_mul(df_add(a, b), df_split(u));
+    };
+    long long c = act ? i + (long long)nx * (j + (long long)ny * k0) : 0;
+    dfloat bo = zero, fzl = zero;
+    if (act) {
+        bo = df_split(beta0[c]);
+        const dfloat bd = k0 > 0 ? df_split(beta0[c - nxy]) : (pz ? df_split(beta0[c + (long long)(nz - 1) * nxy]) : zero);
+        fzl = flux2(2, k0, bd, bo, uz[c]);
+    }
     for (int k = k0; k < k1; k++, c += nxy) {
+        dfloat bw;
+        bw.h = __shfl_up_sync(0xffffffffu, bo.h, 1);
+        bw.l = __shfl_up_sync(0xffffffffu, bo.l, 1);
         const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
-        const long long cw = i > 0 ? c - 1 : c + nx - 1;
-        const long long ce = i + 1 < nx ? c + 1 : c - (nx - 1);
-        const dfloat fxl = df_face_flux2(g, beta0, 0, i, cw, c, ux[fx]);
-        const dfloat fxh = df_face_flux2(g, beta0, 0, i + 1, c, ce, ux[fx + 1]);
-        const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
-        const long long cs = j > 0 ? c - nx : c + (long long)(ny - 1) * nx;
-        const long long cn = j + 1 < ny ? c + nx : c - (long long)(ny - 1) * nx;
-        const dfloat fyl = df_face_flux2(g, beta0, 1, j, cs, c, uy[fy]);
-        const dfloat fyh = df_face_flux2(g, beta0, 1, j + 1, c, cn, uy[fy + nx]);
-        const long long ct = k + 1 < nz ? c + nxy : c - (long long)(nz - 1) * nxy;
-        const dfloat fzh = df_face_flux2(g, beta0, 2, k + 1, c, ct, uz[c + nxy]);
-        const dfloat div = df_add(df_add(df_sub(fxh, fxl), df_sub(fyh, fyl)), df_sub(fzh, fzl));
-        fn(c, df_sub(df_mul(div, hih), df_mul(df_split(beta0[c]), df_split(sbar[c]))));
-        fzl = fzh;
+        dfloat fxl = zero;
+        if (act) {
+            if (lane == 0) bw = i > 0 ? df_split(beta0[c - 1]) : (px ? df_split(beta0[c + nx - 1]) : zero);
+            fxl = flux2(0, i, bw, bo, ux[fx]);
+        }
+        dfloat fxh;
+        fxh.h = __shfl_down_sync(0xffffffffu, fxl.h, 1);
+        fxh.l = __shfl_down_sync(0xffffffffu, fxl.l, 1);
+        if (act) {
+            if (lane == SX - 1 || i + 1 >= nx) {
+                const dfloat be = i + 1 < nx ? df_split(beta0[c + 1]) : (px ? df_split(beta0[c - (nx - 1)]) : zero);
+                fxh = flux2(0, i + 1, bo, be, ux[fx + 1]);
+            }
+            const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
+            const dfloat bs = j > 0 ? df_split(beta0[c - nx]) : (py ? df_split(beta0[c + (long long)(ny - 1) * nx]) : zero);
+            const dfloat bn = j + 1 < ny ? df_split(beta0[c + nx])
+                                         : (py ? df_split(beta0[c - (long long)(ny - 1) * nx]) : zero);
+            const dfloat fyl = flux2(1, j, bs, bo, uy[fy]);
+            const dfloat fyh = flux2(1, j + 1, bo, bn, uy[fy + nx]);
+            const dfloat bu = k + 1 < nz ? df_split(beta0[c + nxy])
+                                         : (pz ? df_split(beta0[c - (long long)(nz - 1) * nxy]) : zero);
+            const dfloat fzh = flux2(2, k + 1, bo, bu, uz[c + nxy]);
+            const dfloat div = df_add(df_add(df_sub(fxh, fxl), df_sub(fyh, fyl)), df_sub(fzh, fzl));
+            fn(c, df_sub(df_mul(div, hih), df_mul(bo, df_split(sbar[c]))));
+            fzl = fzh;
+            bo = bu;
+        }
     }
 }
 
@@ -186,8 +264,7 @@ __global__ void mac_rhs_df_kernel(DGeom g, const double *__restrict__ ux, const 
     const int k0 = blockIdx.z * ZC;
     dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
     float s2 = 0.f;
-    if (i < g.n[0] && j < g.n[1])
-        df_div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, dfloat v) {
+    df_div_block(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, dfloat v) {
             fh[c] = v.h;
             fl[c] = v.l;
             df_absmax(mx, v);
@@ -206,9 +283,8 @@ __global__ void mac_divcheck_df_kernel(DGeom g, const double *__restrict__ ux, c
     const int k0 = blockIdx.z * ZC;
     const dfloat cm = df_split(st->mean);
     dfloat mx = {0.f, 0.f};
-    if (i < g.n[0] && j < g.n[1])
-        df_div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
-                      [&](long long, dfloat v) { df_absmax(mx, df_sub(v, cm)); });
+    df_div_block(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
+                 [&](long long, dfloat v) { df_absmax(mx, df_sub(v, cm)); });
     df_partials(mx, 0.f, dfloat{0.f, 0.f}, part + 3 * flat_bid());
 }
 
