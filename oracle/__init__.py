@@ -8,8 +8,11 @@ Arrays are float64 numpy arrays in x-fastest order (numpy shape (nz, ny, nx));
 MAC face arrays carry n_d + 1 entries along their own direction, nodal arrays
 have n nodes on a periodic axis and n + 1 on a wall axis.
 
+``composite.py`` (numpy / scipy.sparse) holds the two-level composite MAC
+operator and projection (refinement ratio 2) with a sparse direct solve.
+
 Functions without a pin in the CPU tests: none.  Readings of the paper are
-listed in the C sources' headers.
+listed in the C sources' headers and in ``composite.py``'s.
 """
 from __future__ import annotations
 

@@ -1,0 +1,193 @@
+"""Pins of the two-level composite MAC oracle (refinement ratio 2; the paper
+keeps its AMR as in its Paper V, end of Sec. 3.2).  Each pin is fixed by the
+mathematics, not by the oracle itself:
+
+  * conservation: with flux matching, the volume-weighted sum of L phi over the
+    composite cells telescopes to the domain-boundary flux, 0 with walls and
+    periodic faces, for any phi and any coefficients;
+  * constants are in the null space (the ghost weights sum to 1);
+  * a linear phi with constant coefficients gives L phi = 0 on every fine cell
+    and every coarse cell off the domain faces (the ghost interpolation is
+    exact for linear functions);
+  * away from the patch, the composite rows are the single-level operator's
+    (coarse grid, and the fine grid inside the patch);
+  * the projection identity D(beta0 U_new) - beta0 Sbar - c = f - L phi;
+  * second order: a manufactured solution's error falls by >= 3.5 when h halves;
+  * planted mistakes in the ghost weights break the linear pin.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import composite as CP
+from paper_1908_03634_gb300 import workloads as W
+
+P, N, D = CP.PERIODIC, CP.NEUMANN, CP.DIRICHLET
+
+
+def rand_case(G, seed):
+    rng = np.random.default_rng(seed)
+    cs = tuple(reversed(G.n))
+    fs = tuple(reversed(G.nf))
+    return (np.exp(rng.standard_normal(cs)), np.exp(rng.standard_normal(cs)), np.exp(rng.standard_normal(fs)),
+            np.exp(rng.standard_normal(fs)), rng)
+
+
+def centres(G):
+    H = G.H
+    fs = tuple(reversed(G.nf))
+    zc, yc, xc = np.meshgrid(*[(np.arange(m) + 0.5) * H for m in reversed(G.n)], indexing="ij")
+    zf, yf, xf = np.meshgrid(*[(G.plo[2 - q] + (np.arange(fs[q]) + 0.5) / 2) * H for q in range(3)], indexing="ij")
+    return (xc, yc, zc), (xf, yf, zf)
+
+
+CASES = [
+    ((8, 8, 8), (N, N, N), (N, N, N), (2, 3, 2), (6, 6, 5)),
+    ((8, 6, 10), (P, P, N), (P, P, N), (1, 1, 3), (4, 5, 9)),
+    ((6, 6, 6), (P, P, P), (P, P, P), (2, 2, 2), (3, 3, 3)),  # one coarse cell: the thinnest patch
+    ((9, 7, 8), (N, P, N), (N, P, N), (3, 1, 1), (8, 6, 7)),
+]
+
+
+@pytest.mark.parametrize("n,lo,hi,plo,phi", CASES)
+def test_composite_conservation_and_constants(n, lo, hi, plo, phi):
+    G = CP.Composite(n, 1.0 / n[0], lo, hi, plo, phi)
+    rc, bc, rf, bf, rng = rand_case(G, 1)
+    A = CP.operator_matrix(G, rc, bc, rf, bf)
+    v = CP.volumes(G)
+    for _ in range(3):
+        y = A @ rng.standard_normal(G.nunk)
+        assert abs(v @ y) <= 1e-12 * (v @ np.abs(y))
+    assert np.abs(A @ np.ones(G.nunk)).max() <= 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("n,lo,hi,plo,phi", CASES)
+def test_composite_linear_exact(n, lo, hi, plo, phi):
+    G = CP.Composite(n, 1.0 / n[0], lo, hi, plo, phi)
+    (xc, yc, zc), (xf, yf, zf) = centres(G)
+    A = CP.operator_matrix(G, np.ones(xc.shape), np.ones(xc.shape), np.ones(xf.shape), np.ones(xf.shape))
+    # off the non-periodic domain faces only (walls break a non-periodic linear field)
+    inner = ~G.covered.copy()
+    for d in range(3):
+        if G.lo[d] != P:
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            inner[tuple(sl)] = False
+            sl[2 - d] = -1
+            inner[tuple(sl)] = False
+    for a in [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (0.3, -0.7, 1.1)]:
+        # a periodic axis takes no linear component
+        a = tuple(0.0 if G.lo[d] == P else a[d] for d in range(3))
+        pc = a[0] * xc + a[1] * yc + a[2] * zc
+        pf = a[0] * xf + a[1] * yf + a[2] * zf
+        yc_, yf_ = CP.unpack(G, A @ CP.pack(G, pc, pf))
+        scale = 1.0 / G.h ** 2
+        assert np.abs(yf_).max() <= 1e-12 * scale
+        assert np.abs(yc_[inner]).max() <= 1e-12 * scale
+
+
+def test_composite_planted_ghost_weights_break_the_linear_pin(monkeypatch):
+    G = CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, (2, 3, 2), (6, 6, 5))
+    (xc, yc, zc), (xf, yf, zf) = centres(G)
+    ones = (np.ones(xc.shape), np.ones(xc.shape), np.ones(xf.shape), np.ones(xf.shape))
+    # the ghost as the plain mean of C and F1 (as if C sat at the ghost's mirror
+    # image): the weights sum to 1, so constants survive, but a linear field does
+    # not (the linear interpolation 2/3 C + 1/3 F1 would, like the quadratic)
+    monkeypatch.setattr(CP, "W_C", 0.5)
+    monkeypatch.setattr(CP, "W_F1", 0.5)
+    monkeypatch.setattr(CP, "W_F2", 0.0)
+    A = CP.operator_matrix(G, *ones)
+    assert np.abs(A @ np.ones(G.nunk)).max() <= 1e-9
+    _, yf_ = CP.unpack(G, A @ CP.pack(G, xc, xf))
+    assert np.abs(yf_).max() > 1.0
+
+
+@pytest.mark.parametrize("n,lo,hi,plo,phi", CASES[:2])
+def test_composite_rows_away_from_the_patch_are_single_level(n, lo, hi, plo, phi):
+    G = CP.Composite(n, 1.0 / n[0], lo, hi, plo, phi)
+    rc, bc, rf, bf, rng = rand_case(G, 2)
+    pc = rng.standard_normal(rc.shape)
+    pf = rng.standard_normal(rf.shape)
+    yc_, yf_ = CP.apply(G, rc, bc, rf, bf, pc, pf)
+    gc = W.Geom(G.n, G.H, G.lo, G.hi)
+    ref_c = O.mac_apply(gc, O.mac_coeffs(gc, rc, bc), pc)
+    far = np.ones(rc.shape, bool)  # coarse cells whose stencil misses the patch
+    z0, z1 = max(plo[2] - 1, 0), phi[2] + 1
+    y0, y1 = max(plo[1] - 1, 0), phi[1] + 1
+    x0, x1 = max(plo[0] - 1, 0), phi[0] + 1
+    far[z0:z1, y0:y1, x0:x1] = False
+    assert far.sum() > 0
+    assert np.abs(yc_[far] - ref_c[far]).max() <= 1e-12 * np.abs(ref_c).max()
+    gf = W.Geom(G.nf, G.h, (N,) * 3, (N,) * 3)
+    ref_f = O.mac_apply(gf, O.mac_coeffs(gf, rf, bf), pf)
+    inner = np.zeros(rf.shape, bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    assert np.abs(yf_[inner] - ref_f[inner]).max() <= 1e-12 * np.abs(ref_f).max()
+
+
+def face_fields(G, rng):
+    cs = [tuple(reversed([G.n[e] + (1 if e == d else 0) for e in range(3)])) for d in range(3)]
+    fs = [tuple(reversed([G.nf[e] + (1 if e == d else 0) for e in range(3)])) for d in range(3)]
+    return [rng.standard_normal(s) for s in cs], [rng.standard_normal(s) for s in fs]
+
+
+@pytest.mark.parametrize("n,lo,hi,plo,phi", CASES + [((8, 8, 8), (P, P, D), (P, P, D), (2, 2, 2), (6, 5, 6))])
+def test_composite_projection_identity(n, lo, hi, plo, phi):
+    G = CP.Composite(n, 1.0 / n[0], lo, hi, plo, phi)
+    rc, bc, rf, bf, rng = rand_case(G, 3)
+    uc, uf = face_fields(G, rng)
+    sc = rng.standard_normal(rc.shape)
+    sf = rng.standard_normal(rf.shape)
+    uc2, uf2, pc, pf, info = CP.project(G, uc, uf, rc, bc, sc, rf, bf, sf)
+    assert info["rel_resid"] <= 1e-12
+    f = info["f"]
+    dv = CP.divergence(G, uc2, uf2, bc, bf) - CP.pack(G, bc * sc, bf * sf) - info["mean"]
+    assert np.abs(dv - info["resid"]).max() <= 1e-11 * np.abs(f).max()
+    assert np.abs(dv).max() <= 1e-11 * np.abs(f).max()
+    # walls carry no flow; coarse faces on the patch are the means of their fine faces
+    for d in range(3):
+        if G.lo[d] == N:
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            assert np.all(uc2[d][tuple(sl)] == 0.0)
+        t1, t2 = [t for t in range(3) if t != d]
+        for p in (G.plo[d], G.phi[d]):
+            face = [0, 0, 0]
+            face[d], face[t1], face[t2] = p, G.plo[t1], G.plo[t2]
+            ff = [0, 0, 0]
+            ff[d] = 2 * (p - G.plo[d])
+            want = 0.25 * sum(uf2[d][tuple(reversed([ff[0] + (e1 if t1 == 0 else 0) + (e2 if t2 == 0 else 0),
+                                                      ff[1] + (e1 if t1 == 1 else 0) + (e2 if t2 == 1 else 0),
+                                                      ff[2] + (e1 if t1 == 2 else 0) + (e2 if t2 == 2 else 0)]))]
+                              for e1 in range(2) for e2 in range(2))
+            assert uc2[d][face[2], face[1], face[0]] == pytest.approx(want, rel=1e-14, abs=1e-14)
+    if G.singular:
+        v = CP.volumes(G)
+        x = CP.pack(G, pc, pf)
+        assert abs(v @ x) <= 1e-12 * (v @ np.abs(x))
+
+
+def test_composite_second_order():
+    """walls all round, constant coefficients, phi* = cos(pi x) cos(pi y) cos(pi z)
+    (zero normal derivative on the walls), f = -3 pi^2 phi* at the centres"""
+    errs = []
+    for n in (8, 16):
+        G = CP.Composite((n,) * 3, 1.0 / n, (N,) * 3, (N,) * 3, (n // 4,) * 3, (3 * n // 4 - n // 8,) * 3)
+        (xc, yc, zc), (xf, yf, zf) = centres(G)
+        ex = lambda x, y, z: np.cos(np.pi * x) * np.cos(np.pi * y) * np.cos(np.pi * z)
+        A = CP.operator_matrix(G, np.ones(xc.shape), np.ones(xc.shape), np.ones(xf.shape), np.ones(xf.shape))
+        v = CP.volumes(G)
+        f = CP.pack(G, -3 * np.pi ** 2 * ex(xc, yc, zc), -3 * np.pi ** 2 * ex(xf, yf, zf))
+        f -= v @ f / v.sum()
+        x = CP.solve(G, A, f)
+        xs = CP.pack(G, ex(xc, yc, zc), ex(xf, yf, zf))
+        xs -= v @ xs / v.sum()
+        errs.append(np.abs(x - xs).max())
+    assert errs[0] / errs[1] >= 3.5, errs
+
+
+def test_composite_rejects_bad_patches():
+    with pytest.raises(ValueError):
+        CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, (0, 2, 2), (4, 4, 4))  # touches a domain face
+    with pytest.raises(ValueError):
+        CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, (2, 2, 2), (2, 4, 4))  # empty
