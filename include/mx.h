@@ -348,6 +348,36 @@ mx_status mx_autotune_batched(mx_ctx *ctx, int nbox, const mx_geom *geoms, const
                               const double *const *beta0, const double *const *sbar, const mx_opts *base,
                               mx_opts *best, double *ms_best);
 
+/* ---- Two-level composite (AMR) operator, refinement ratio 2 (end of Sec. 3.2:
+ * AMR as in the paper's Paper V, ratio 2 between levels) -------------------------
+ * geom: the coarse level (cells, dx = H, domain boundary types).  plo, phi (host):
+ * the fine patch as the coarse-index box [plo, phi), at least one coarse cell from
+ * every domain face and at least one coarse cell thick (else MX_ERR_ARG); the fine
+ * level has 2 (phi - plo) cells per axis of width H/2.  Coarse arrays cover the
+ * whole coarse grid (values on covered cells are not read); fine arrays cover the
+ * patch; face arrays carry n_d + 1 entries along their own direction.  All arrays
+ * are device pointers, x fastest.  Discretisation: fine ghost values across the
+ * patch boundary by linear tangential interpolation of the coarse value across
+ * and the normal quadratic 8/15 C~ + 2/3 F1 - 1/5 F2; coarse fluxes through
+ * coarse-fine faces are the means of the four fine fluxes (flux matching); face
+ * coefficients beta0_f / rho_f by arithmetic face means (of the fine cell and
+ * the coarse cell across on a coarse-fine face).  FP64; both calls synchronise
+ * the stream before returning. */
+
+/* out = L phi on the uncovered coarse cells (0 on covered ones) and the fine cells */
+mx_status mx_composite_apply(mx_ctx *ctx, const mx_geom *geom, const int plo[3], const int phi[3],
+                             const double *rho_c, const double *beta0_c, const double *rho_f, const double *beta0_f,
+                             const double *phi_c, const double *phi_f, double *out_c, double *out_f);
+
+/* out = D(beta0 U) on the uncovered coarse cells (0 on covered ones) and the fine
+ * cells; U on a wall face is taken as 0, beta0 of the interior cell on a Dirichlet
+ * face, and a coarse cell's coarse-fine flux is the mean of the four fine
+ * beta0_f U_f on its face. */
+mx_status mx_composite_divergence(mx_ctx *ctx, const mx_geom *geom, const int plo[3], const int phi[3],
+                                  const double *ux_c, const double *uy_c, const double *uz_c, const double *ux_f,
+                                  const double *uy_f, const double *uz_f, const double *beta0_c,
+                                  const double *beta0_f, double *out_c, double *out_f);
+
 /* Look up the tune cache: 1 and *out = the stored setting (base fields from
  * *out as passed) if mx_autotune stored one for (op, prec, geometry), else 0. */
 int mx_tune_lookup(const mx_ctx *ctx, int op, int prec, const mx_geom *geom, mx_opts *out);

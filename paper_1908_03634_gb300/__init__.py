@@ -96,6 +96,8 @@ def load():
         "mx_w0_integrate": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP, _DP, C.c_int, _DP]),
         "mx_add_w0_faces": (C.c_int, [_VP, G, C.c_int, _IP3, C.c_int, _DP, _DP, _DP, _DP, _DP]),
         "mx_subtract_lateral_average": (C.c_int, [_VP, G, C.c_int, _IP3, _DP, _DP]),
+        "mx_composite_apply": (C.c_int, [_VP, G, _IP3, _IP3] + [_DP] * 8),
+        "mx_composite_divergence": (C.c_int, [_VP, G, _IP3, _IP3] + [_DP] * 10),
         "mx_mac_project_split": (C.c_int, [_VP, G, C.c_int, _IP3, _DP, _DP, _DP, _DP, _DP, _DP, C.c_int, _DP, _DP,
                                            _DP, O, I]),
     }
@@ -114,7 +116,8 @@ def exported_symbols():
             "mx_mac_project_batched", "mx_profile_enable", "mx_profile_read", "mx_residual_noalloc",
             "mx_autotune", "mx_tune_lookup", "mx_autotune_batched", "mx_radial_nbins", "mx_average_planar",
             "mx_average_radial", "mx_fill_radial", "mx_radial_to_uniform", "mx_fill_uniform", "mx_w0_integrate",
-            "mx_add_w0_faces", "mx_subtract_lateral_average", "mx_mac_project_split"]
+            "mx_add_w0_faces", "mx_subtract_lateral_average", "mx_mac_project_split", "mx_composite_apply",
+            "mx_composite_divergence"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -288,6 +291,35 @@ def mx_subtract_lateral_average(ctx, geom, spherical, corner, S, out):
     st = load().mx_subtract_lateral_average(ctx, C.byref(make_geom(geom)), int(spherical),
                                             _corner(corner or (0, 0, 0)), _ptr(S, cell_shape(geom), "S"),
                                             _ptr(out, cell_shape(geom), "out"))
+    return _check(ctx, st)
+
+
+def _fine_shapes(geom, plo, phi):
+    nf = [2 * (int(phi[d]) - int(plo[d])) for d in range(3)]
+    cells = (nf[2], nf[1], nf[0])
+    faces = [tuple(reversed([nf[e] + (1 if e == d else 0) for e in range(3)])) for d in range(3)]
+    return cells, faces
+
+
+def mx_composite_apply(ctx, geom, plo, phi, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, out_c, out_f):
+    """L phi of the two-level composite operator (coarse geom + the fine patch [plo, phi))."""
+    cs = cell_shape(geom)
+    fs, _ = _fine_shapes(geom, plo, phi)
+    st = load().mx_composite_apply(ctx, C.byref(make_geom(geom)), _corner(plo), _corner(phi),
+                                   _ptr(rho_c, cs, "rho_c"), _ptr(beta0_c, cs, "beta0_c"), _ptr(rho_f, fs, "rho_f"),
+                                   _ptr(beta0_f, fs, "beta0_f"), _ptr(phi_c, cs, "phi_c"), _ptr(phi_f, fs, "phi_f"),
+                                   _ptr(out_c, cs, "out_c"), _ptr(out_f, fs, "out_f"))
+    return _check(ctx, st)
+
+
+def mx_composite_divergence(ctx, geom, plo, phi, uc, uf, beta0_c, beta0_f, out_c, out_f):
+    """D(beta0 U) on the composite grid; uc, uf: lists of the three coarse / fine face arrays."""
+    cs = cell_shape(geom)
+    fs, ffs = _fine_shapes(geom, plo, phi)
+    st = load().mx_composite_divergence(
+        ctx, C.byref(make_geom(geom)), _corner(plo), _corner(phi),
+        *[_ptr(uc[d], face_shape(geom, d), "uc") for d in range(3)], *[_ptr(uf[d], ffs[d], "uf") for d in range(3)],
+        _ptr(beta0_c, cs, "beta0_c"), _ptr(beta0_f, fs, "beta0_f"), _ptr(out_c, cs, "out_c"), _ptr(out_f, fs, "out_f"))
     return _check(ctx, st)
 
 
