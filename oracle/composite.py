@@ -10,12 +10,14 @@ a reading, chosen as the standard cell-centred ratio-2 scheme and consistent
 with the single-level oracle (oracle.c):
 
   * Layout: a coarse level of n cells per axis (cell width H) with the domain's
-    boundary conditions, and one fine patch covering the coarse box
-    [plo, phi) (cell width h = H/2, 2 (phi - plo) cells per axis).  The patch
+    boundary conditions, and fine patches, each covering a coarse box
+    [plo, phi) (cell width h = H/2, 2 (phi - plo) cells per axis).  A patch
     keeps at least one coarse cell from every face of the domain (so its
-    boundary is a coarse-fine interface only) and is at least one coarse cell
-    thick.  Unknowns: phi on the coarse cells not covered by the patch and on
-    all fine cells.
+    boundary is a coarse-fine interface only), is at least one coarse cell
+    thick, and keeps at least one coarse cell from every other patch (so no
+    two fine cells of different patches touch and the coarse cells a ghost
+    value reads are never covered).  Unknowns: phi on the coarse cells not
+    covered by a patch, then on the fine cells patch by patch.
   * Face coefficients b = beta0_f / rho_f with arithmetic face means, as on one
     level; on a coarse-fine face, of the fine cell and the coarse cell across.
   * Fine ghost value across a coarse-fine face (normal direction d, fine cell F1
@@ -40,6 +42,8 @@ with the single-level oracle (oracle.c):
 
 Arrays are numpy float64 in x-fastest order (shape (nz, ny, nx)); face arrays
 carry n_d + 1 entries along their own direction, as elsewhere in the oracle.
+Fine fields are one array per patch (a list), or a plain array with a single
+patch.
 """
 from __future__ import annotations
 
@@ -56,36 +60,74 @@ W_C, W_F1, W_F2 = 8.0 / 15.0, 2.0 / 3.0, -1.0 / 5.0
 
 
 class Composite:
-    """Index maps of a coarse level with one ratio-2 fine patch.
+    """Index maps of a coarse level with ratio-2 fine patches.
 
     n: coarse cells per axis (x, y, z); dx: coarse cell width; lo, hi: boundary
-    type per axis; plo, phi: the patch as a coarse-index box [plo, phi)."""
+    type per axis; plo, phi: one patch as the coarse-index box [plo, phi), or
+    patches: a list of such (plo, phi) boxes."""
 
-    def __init__(self, n, dx, lo, hi, plo, phi):
+    def __init__(self, n, dx, lo, hi, plo=None, phi=None, patches=None):
         self.n = tuple(int(v) for v in n)
         self.H = float(dx)
         self.h = self.H / 2.0
         self.lo = tuple(lo)
         self.hi = tuple(hi)
-        self.plo = tuple(int(v) for v in plo)
-        self.phi = tuple(int(v) for v in phi)
+        if patches is None:
+            patches = [(plo, phi)]
+        self.boxes = [(tuple(int(v) for v in a), tuple(int(v) for v in b)) for a, b in patches]
+        if not self.boxes:
+            raise ValueError("no patch")
         for d in range(3):
             if self.lo[d] == PERIODIC and self.hi[d] != PERIODIC or self.hi[d] == PERIODIC and self.lo[d] != PERIODIC:
                 raise ValueError("periodic on one side only")
-            if not (1 <= self.plo[d] and self.phi[d] <= self.n[d] - 1 and self.phi[d] - self.plo[d] >= 1):
-                raise ValueError("the patch must keep one coarse cell from the domain faces and be one cell thick")
-        self.nf = tuple(2 * (self.phi[d] - self.plo[d]) for d in range(3))
+        for a, b in self.boxes:
+            for d in range(3):
+                if not (1 <= a[d] and b[d] <= self.n[d] - 1 and b[d] - a[d] >= 1):
+                    raise ValueError("a patch must keep one coarse cell from the domain faces and be one cell thick")
+        for p in range(len(self.boxes)):
+            for q in range(p):
+                (a0, a1), (b0, b1) = self.boxes[p], self.boxes[q]
+                if all(a0[d] - 1 < b1[d] and b0[d] < a1[d] + 1 for d in range(3)):
+                    raise ValueError("patches must keep one coarse cell apart")
         nx, ny, nz = self.n
-        cov = np.zeros((nz, ny, nx), dtype=bool)
-        cov[self.plo[2]:self.phi[2], self.plo[1]:self.phi[1], self.plo[0]:self.phi[0]] = True
+        self.owner = -np.ones((nz, ny, nx), dtype=np.int64)  # patch covering each coarse cell
+        for p, (a, b) in enumerate(self.boxes):
+            self.owner[a[2]:b[2], a[1]:b[1], a[0]:b[0]] = p
+        cov = self.owner >= 0
         self.covered = cov
         self.cid = -np.ones((nz, ny, nx), dtype=np.int64)
         self.cid[~cov] = np.arange(int((~cov).sum()))
         self.nc = int((~cov).sum())
-        fx, fy, fz = self.nf
-        self.fid = self.nc + np.arange(fx * fy * fz, dtype=np.int64).reshape(fz, fy, fx)
-        self.nunk = self.nc + fx * fy * fz
-        self.singular = all(b != DIRICHLET for b in self.lo + self.hi)
+        self.nfs, self.fids = [], []
+        off = self.nc
+        for a, b in self.boxes:
+            nf = tuple(2 * (b[d] - a[d]) for d in range(3))
+            self.nfs.append(nf)
+            self.fids.append(off + np.arange(nf[0] * nf[1] * nf[2], dtype=np.int64).reshape(nf[2], nf[1], nf[0]))
+            off += nf[0] * nf[1] * nf[2]
+        self.nunk = off
+        self.singular = all(bc != DIRICHLET for bc in self.lo + self.hi)
+
+    # the single-patch view
+    @property
+    def plo(self):
+        return self.boxes[0][0]
+
+    @property
+    def phi(self):
+        return self.boxes[0][1]
+
+    @property
+    def nf(self):
+        return self.nfs[0]
+
+    @property
+    def fid(self):
+        return self.fids[0]
+
+    @property
+    def npatch(self):
+        return len(self.boxes)
 
     # ---- small helpers (index tuples are (x, y, z)) ----
     def coarse_nb(self, c, d, s):
@@ -103,25 +145,49 @@ class Composite:
     def domain_bc(self, d, s):
         return self.lo[d] if s < 0 else self.hi[d]
 
+    def patch_of(self, c):
+        """the patch covering coarse cell c, or -1"""
+        return int(self.owner[c[2], c[1], c[0]])
+
     def in_patch(self, c):
-        return all(self.plo[d] <= c[d] < self.phi[d] for d in range(3))
+        return self.patch_of(c) >= 0
 
-    def parent(self, F):
-        """coarse cell containing fine cell F (fine-local index)"""
-        return tuple(self.plo[d] + F[d] // 2 for d in range(3))
+    def parent(self, F, p=0):
+        """coarse cell containing fine cell F (patch-local index) of patch p"""
+        return tuple(self.boxes[p][0][d] + F[d] // 2 for d in range(3))
 
-    def fine_inside(self, F):
-        return all(0 <= F[d] < self.nf[d] for d in range(3))
+    def fine_inside(self, F, p=0):
+        return all(0 <= F[d] < self.nfs[p][d] for d in range(3))
+
+
+def _fine_list(G, a):
+    """a fine field as one array per patch"""
+    if isinstance(a, (list, tuple)):
+        if len(a) != G.npatch:
+            raise ValueError("one fine array per patch")
+        return [np.asarray(x) for x in a]
+    if G.npatch != 1:
+        raise ValueError("one fine array per patch")
+    return [np.asarray(a)]
+
+
+def _fine_faces(G, uf):
+    """fine face fields as [patch][direction]"""
+    if G.npatch == 1 and len(uf) == 3 and not isinstance(uf[0], (list, tuple)):
+        return [list(uf)]
+    if len(uf) != G.npatch:
+        raise ValueError("one list of three face arrays per patch")
+    return [list(x) for x in uf]
 
 
 def _at(a, c):
     return a[c[2], c[1], c[0]]
 
 
-def ghost_terms(G, F, d, s):
-    """phi_g of fine cell F (fine-local) across its patch face along d on side s,
-    as a list of (unknown index, weight)"""
-    C = list(G.parent(F))
+def ghost_terms(G, F, d, s, p=0):
+    """phi_g of fine cell F (patch-local, patch p) across its patch face along d
+    on side s, as a list of (unknown index, weight); and the coarse cell across"""
+    C = list(G.parent(F, p))
     C[d] += s
     C = tuple(C)
     terms = [(int(_at(G.cid, C)), W_C)]
@@ -137,8 +203,8 @@ def ghost_terms(G, F, d, s):
         terms.append((int(_at(G.cid, tuple(cm))), -W_C * sig / 8.0))
     F2 = list(F)
     F2[d] -= s
-    terms.append((int(_at(G.fid, F)), W_F1))
-    terms.append((int(_at(G.fid, tuple(F2))), W_F2))
+    terms.append((int(_at(G.fids[p], F)), W_F1))
+    terms.append((int(_at(G.fids[p], tuple(F2))), W_F2))
     return C, terms
 
 
@@ -146,9 +212,27 @@ def _bmean(beta_a, rho_a, beta_b, rho_b):
     return (0.5 * (beta_a + beta_b)) / (0.5 * (rho_a + rho_b))
 
 
+def _cf_cells(G, c, nb, d, s, q):
+    """the four fine cells of patch q on the coarse-fine face between coarse cell c
+    (outside) and coarse cell nb (covered by q), c + s e_d = nb"""
+    plo = G.boxes[q][0]
+    t1, t2 = [t for t in range(3) if t != d]
+    Fd = 2 * (nb[d] - plo[d]) + (0 if s > 0 else 1)
+    out = []
+    for a in range(2):
+        for bb in range(2):
+            F = [0, 0, 0]
+            F[d] = Fd
+            F[t1] = 2 * (c[t1] - plo[t1]) + a
+            F[t2] = 2 * (c[t2] - plo[t2]) + bb
+            out.append(tuple(F))
+    return out
+
+
 def operator_matrix(G, rho_c, beta0_c, rho_f, beta0_f):
     """The composite operator L as a sparse matrix on the unknown vector (coarse
-    uncovered cells in x-fastest order, then the fine cells)."""
+    uncovered cells in x-fastest order, then the fine cells patch by patch)."""
+    rho_f, beta0_f = _fine_list(G, rho_f), _fine_list(G, beta0_f)
     rows, cols, vals = [], [], []
     H, h = G.H, G.h
 
@@ -173,49 +257,43 @@ def operator_matrix(G, rho_c, beta0_c, rho_f, beta0_f):
                             if G.domain_bc(d, s) == DIRICHLET:  # phi = 0 at the face: (0 - phi)/(H/2)
                                 add(r, r, -2.0 * (bc / rc) / (H * H))
                             continue
-                        if not G.in_patch(nb):
+                        q = G.patch_of(nb)
+                        if q < 0:
                             b = _bmean(bc, rc, _at(beta0_c, nb), _at(rho_c, nb))
                             add(r, int(_at(G.cid, nb)), b / (H * H))
                             add(r, r, -b / (H * H))
                             continue
                         # coarse-fine face: the mean of the four fine fluxes b (phi_F1 - phi_g)/h
-                        t1, t2 = [t for t in range(3) if t != d]
-                        Fd = 2 * (nb[d] - G.plo[d]) + (0 if s > 0 else 1)
-                        for a in range(2):
-                            for bb in range(2):
-                                F = [0, 0, 0]
-                                F[d] = Fd
-                                F[t1] = 2 * (c[t1] - G.plo[t1]) + a
-                                F[t2] = 2 * (c[t2] - G.plo[t2]) + bb
-                                F = tuple(F)
-                                bf = _bmean(_at(beta0_f, F), _at(rho_f, F), bc, rc)
-                                w = 0.25 * bf / (h * H)
-                                add(r, int(_at(G.fid, F)), w)
-                                _, terms = ghost_terms(G, F, d, -s)
-                                for col, wt in terms:
-                                    add(r, col, -w * wt)
-    fx, fy, fz = G.nf
-    for K in range(fz):
-        for J in range(fy):
-            for I in range(fx):
-                F = (I, J, K)
-                r = int(_at(G.fid, F))
-                rf, bf_ = _at(rho_f, F), _at(beta0_f, F)
-                for d in range(3):
-                    for s in (-1, 1):
-                        N = list(F)
-                        N[d] += s
-                        N = tuple(N)
-                        if G.fine_inside(N):
-                            b = _bmean(bf_, rf, _at(beta0_f, N), _at(rho_f, N))
-                            add(r, int(_at(G.fid, N)), b / (h * h))
-                            add(r, r, -b / (h * h))
-                        else:
-                            C, terms = ghost_terms(G, F, d, s)
-                            b = _bmean(bf_, rf, _at(beta0_c, C), _at(rho_c, C))
+                        for F in _cf_cells(G, c, nb, d, s, q):
+                            bf = _bmean(_at(beta0_f[q], F), _at(rho_f[q], F), bc, rc)
+                            w = 0.25 * bf / (h * H)
+                            add(r, int(_at(G.fids[q], F)), w)
+                            _, terms = ghost_terms(G, F, d, -s, q)
                             for col, wt in terms:
-                                add(r, col, b * wt / (h * h))
-                            add(r, r, -b / (h * h))
+                                add(r, col, -w * wt)
+    for p in range(G.npatch):
+        fx, fy, fz = G.nfs[p]
+        for K in range(fz):
+            for J in range(fy):
+                for I in range(fx):
+                    F = (I, J, K)
+                    r = int(_at(G.fids[p], F))
+                    rf, bf_ = _at(rho_f[p], F), _at(beta0_f[p], F)
+                    for d in range(3):
+                        for s in (-1, 1):
+                            N = list(F)
+                            N[d] += s
+                            N = tuple(N)
+                            if G.fine_inside(N, p):
+                                b = _bmean(bf_, rf, _at(beta0_f[p], N), _at(rho_f[p], N))
+                                add(r, int(_at(G.fids[p], N)), b / (h * h))
+                                add(r, r, -b / (h * h))
+                            else:
+                                C, terms = ghost_terms(G, F, d, s, p)
+                                b = _bmean(bf_, rf, _at(beta0_c, C), _at(rho_c, C))
+                                for col, wt in terms:
+                                    add(r, col, b * wt / (h * h))
+                                add(r, r, -b / (h * h))
     return sp.csr_matrix((vals, (rows, cols)), shape=(G.nunk, G.nunk))
 
 
@@ -229,20 +307,28 @@ def volumes(G):
 def pack(G, phi_c, phi_f):
     x = np.empty(G.nunk)
     x[:G.nc] = np.asarray(phi_c)[~G.covered]
-    x[G.nc:] = np.asarray(phi_f).ravel()
+    off = G.nc
+    for a in _fine_list(G, phi_f):
+        x[off:off + a.size] = a.ravel()
+        off += a.size
     return x
 
 
 def unpack(G, x):
-    """(coarse array with covered cells = mean of their 8 fine cells, fine array)"""
+    """(coarse array with covered cells = mean of their 8 fine cells, fine array
+    (one patch) or list of fine arrays)"""
     nx, ny, nz = G.n
-    fx, fy, fz = G.nf
-    pf = np.asarray(x[G.nc:]).reshape(fz, fy, fx)
     pc = np.zeros((nz, ny, nx))
     pc[~G.covered] = x[:G.nc]
-    avg = pf.reshape(fz // 2, 2, fy // 2, 2, fx // 2, 2).mean(axis=(1, 3, 5))
-    pc[G.plo[2]:G.phi[2], G.plo[1]:G.phi[1], G.plo[0]:G.phi[0]] = avg
-    return pc, pf
+    pfs = []
+    off = G.nc
+    for (a, b), (fx, fy, fz) in zip(G.boxes, G.nfs):
+        pf = np.asarray(x[off:off + fx * fy * fz]).reshape(fz, fy, fx)
+        off += fx * fy * fz
+        avg = pf.reshape(fz // 2, 2, fy // 2, 2, fx // 2, 2).mean(axis=(1, 3, 5))
+        pc[a[2]:b[2], a[1]:b[1], a[0]:b[0]] = avg
+        pfs.append(pf)
+    return pc, (pfs[0] if G.npatch == 1 else pfs)
 
 
 def apply(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f):
@@ -262,7 +348,10 @@ def divergence(G, uc, uf, beta0_c, beta0_f):
     single-level rules (U taken as 0 on walls, beta0 of the interior cell on a
     Dirichlet face) except the coarse-fine faces, whose flux is the mean of the
     four fine beta0_f U_f; fine faces with beta0_f the mean of the fine cell and,
-    on the patch boundary, the coarse cell across."""
+    on the patch boundary, the coarse cell across.  uf: three face arrays (one
+    patch) or one such list per patch."""
+    uf = _fine_faces(G, uf)
+    beta0_f = _fine_list(G, beta0_f)
     out = np.zeros(G.nunk)
     H, h = G.H, G.h
     nx, ny, nz = G.n
@@ -286,52 +375,47 @@ def divergence(G, uc, uf, beta0_c, beta0_f):
                             if G.domain_bc(d, s) == DIRICHLET:
                                 acc += s * bc * _at(uc[d], face)
                             continue
-                        if not G.in_patch(nb):
+                        q = G.patch_of(nb)
+                        if q < 0:
                             acc += s * 0.5 * (bc + _at(beta0_c, nb)) * _at(uc[d], face)
                             continue
-                        t1, t2 = [t for t in range(3) if t != d]
-                        Fd = 2 * (nb[d] - G.plo[d]) + (0 if s > 0 else 1)
                         m = 0.0
-                        for a in range(2):
-                            for bb in range(2):
-                                F = [0, 0, 0]
-                                F[d] = Fd
-                                F[t1] = 2 * (c[t1] - G.plo[t1]) + a
-                                F[t2] = 2 * (c[t2] - G.plo[t2]) + bb
-                                F = tuple(F)
-                                ff = _fface(F, d, 0 if s > 0 else 1)
-                                m += 0.25 * 0.5 * (_at(beta0_f, F) + bc) * _at(uf[d], ff)
+                        for F in _cf_cells(G, c, nb, d, s, q):
+                            ff = _fface(F, d, 0 if s > 0 else 1)
+                            m += 0.25 * 0.5 * (_at(beta0_f[q], F) + bc) * _at(uf[q][d], ff)
                         acc += s * m
                 out[r] = acc / H
-    fx, fy, fz = G.nf
-    for K in range(fz):
-        for J in range(fy):
-            for I in range(fx):
-                F = (I, J, K)
-                r = int(_at(G.fid, F))
-                bf_ = _at(beta0_f, F)
-                acc = 0.0
-                for d in range(3):
-                    for s in (-1, 1):
-                        N = list(F)
-                        N[d] += s
-                        N = tuple(N)
-                        ff = _fface(F, d, 1 if s > 0 else 0)
-                        if G.fine_inside(N):
-                            bn = _at(beta0_f, N)
-                        else:
-                            C = list(G.parent(F))
-                            C[d] += s
-                            bn = _at(beta0_c, tuple(C))
-                        acc += s * 0.5 * (bf_ + bn) * _at(uf[d], ff)
-                out[r] = acc / h
+    for p in range(G.npatch):
+        fx, fy, fz = G.nfs[p]
+        for K in range(fz):
+            for J in range(fy):
+                for I in range(fx):
+                    F = (I, J, K)
+                    r = int(_at(G.fids[p], F))
+                    bf_ = _at(beta0_f[p], F)
+                    acc = 0.0
+                    for d in range(3):
+                        for s in (-1, 1):
+                            N = list(F)
+                            N[d] += s
+                            N = tuple(N)
+                            ff = _fface(F, d, 1 if s > 0 else 0)
+                            if G.fine_inside(N, p):
+                                bn = _at(beta0_f[p], N)
+                            else:
+                                C = list(G.parent(F, p))
+                                C[d] += s
+                                bn = _at(beta0_c, tuple(C))
+                            acc += s * 0.5 * (bf_ + bn) * _at(uf[p][d], ff)
+                    out[r] = acc / h
     return out
 
 
 def rhs(G, uc, uf, beta0_c, beta0_f, sbar_c, sbar_f, remove_mean=True):
     """f = D(beta0 U) - beta0 Sbar (unknown-ordered) and the removed mean c"""
     f = divergence(G, uc, uf, beta0_c, beta0_f)
-    f -= pack(G, np.asarray(beta0_c) * np.asarray(sbar_c), np.asarray(beta0_f) * np.asarray(sbar_f))
+    bsf = [np.asarray(b) * np.asarray(s_) for b, s_ in zip(_fine_list(G, beta0_f), _fine_list(G, sbar_f))]
+    f -= pack(G, np.asarray(beta0_c) * np.asarray(sbar_c), bsf)
     c = 0.0
     if G.singular and remove_mean:
         v = volumes(G)
@@ -354,14 +438,18 @@ def solve(G, A, f):
 
 def correct(G, uc, uf, rho_c, rho_f, x):
     """U <- U - (dphi/dn)/rho_f on both levels (x: unknown-ordered phi); the
-    coarse faces on and inside the patch then take the mean of their four fine
-    faces.  Returns new (uc, uf) lists."""
+    coarse faces on and inside the patches then take the mean of their four
+    fine faces.  Returns new (uc, uf): uf as three arrays (one patch) or one
+    such list per patch."""
+    single = G.npatch == 1 and len(uf) == 3 and not isinstance(uf[0], (list, tuple))
     uc = [np.array(a, dtype=np.float64, copy=True) for a in uc]
-    uf = [np.array(a, dtype=np.float64, copy=True) for a in uf]
+    uf = [[np.array(a, dtype=np.float64, copy=True) for a in u3] for u3 in _fine_faces(G, uf)]
+    rho_f = _fine_list(G, rho_f)
     H, h = G.H, G.h
-    pc, pf = unpack(G, x)
-    nx, ny, nz = G.n
-    # coarse faces outside the patch closure: single-level rules
+    pc, pfs = unpack(G, x)
+    if G.npatch == 1:
+        pfs = [pfs]
+    # coarse faces off the patches: single-level rules
     for d in range(3):
         shp = uc[d].shape  # (z, y, x)
         for k in range(shp[0]):
@@ -390,48 +478,50 @@ def correct(G, uc, uf, rho_c, rho_f, x):
                         continue  # set from the fine faces below
                     g = (_at(pc, R) - _at(pc, L)) / H
                     uc[d][k, j, i] -= g / (0.5 * (_at(rho_c, L) + _at(rho_c, R)))
-    # fine faces
-    fx, fy, fz = G.nf
-    for d in range(3):
-        shp = uf[d].shape
-        for K in range(shp[0]):
-            for J in range(shp[1]):
-                for I in range(shp[2]):
-                    face = [I, J, K]
-                    p = face[d]
-                    L = list(face)
-                    L[d] = p - 1
-                    R = list(face)
-                    L, R = tuple(L), tuple(R)
-                    if 0 < p < G.nf[d]:
-                        g = (_at(pf, R) - _at(pf, L)) / h
-                        rf = 0.5 * (_at(rho_f, L) + _at(rho_f, R))
-                    else:
-                        F = R if p == 0 else L
-                        s = -1 if p == 0 else 1
-                        C, terms = ghost_terms(G, F, d, s)
-                        pg = sum(w * x[col] for col, w in terms)
-                        g = (_at(pf, F) - pg) / h if p == 0 else (pg - _at(pf, F)) / h
-                        rf = 0.5 * (_at(rho_f, F) + _at(rho_c, C))
-                    uf[d][K, J, I] -= g / rf
-    # coarse faces on and inside the patch: mean of the four fine faces
-    for d in range(3):
-        t1, t2 = [t for t in range(3) if t != d]
-        for p in range(G.plo[d], G.phi[d] + 1):
-            for a in range(G.plo[t1], G.phi[t1]):
-                for b in range(G.plo[t2], G.phi[t2]):
-                    face = [0, 0, 0]
-                    face[d], face[t1], face[t2] = p, a, b
-                    m = 0.0
-                    for e1 in range(2):
-                        for e2 in range(2):
-                            ff = [0, 0, 0]
-                            ff[d] = 2 * (p - G.plo[d])
-                            ff[t1] = 2 * (a - G.plo[t1]) + e1
-                            ff[t2] = 2 * (b - G.plo[t2]) + e2
-                            m += 0.25 * uf[d][ff[2], ff[1], ff[0]]
-                    uc[d][face[2], face[1], face[0]] = m
-    return uc, uf
+    for q in range(G.npatch):
+        pf, nf = pfs[q], G.nfs[q]
+        # fine faces
+        for d in range(3):
+            shp = uf[q][d].shape
+            for K in range(shp[0]):
+                for J in range(shp[1]):
+                    for I in range(shp[2]):
+                        face = [I, J, K]
+                        p = face[d]
+                        L = list(face)
+                        L[d] = p - 1
+                        R = list(face)
+                        L, R = tuple(L), tuple(R)
+                        if 0 < p < nf[d]:
+                            g = (_at(pf, R) - _at(pf, L)) / h
+                            rf = 0.5 * (_at(rho_f[q], L) + _at(rho_f[q], R))
+                        else:
+                            F = R if p == 0 else L
+                            s = -1 if p == 0 else 1
+                            C, terms = ghost_terms(G, F, d, s, q)
+                            pg = sum(w * x[col] for col, w in terms)
+                            g = (_at(pf, F) - pg) / h if p == 0 else (pg - _at(pf, F)) / h
+                            rf = 0.5 * (_at(rho_f[q], F) + _at(rho_c, C))
+                        uf[q][d][K, J, I] -= g / rf
+        # coarse faces on and inside the patch: mean of the four fine faces
+        plo, phi = G.boxes[q]
+        for d in range(3):
+            t1, t2 = [t for t in range(3) if t != d]
+            for p in range(plo[d], phi[d] + 1):
+                for a in range(plo[t1], phi[t1]):
+                    for b in range(plo[t2], phi[t2]):
+                        face = [0, 0, 0]
+                        face[d], face[t1], face[t2] = p, a, b
+                        m = 0.0
+                        for e1 in range(2):
+                            for e2 in range(2):
+                                ff = [0, 0, 0]
+                                ff[d] = 2 * (p - plo[d])
+                                ff[t1] = 2 * (a - plo[t1]) + e1
+                                ff[t2] = 2 * (b - plo[t2]) + e2
+                                m += 0.25 * uf[q][d][ff[2], ff[1], ff[0]]
+                        uc[d][face[2], face[1], face[0]] = m
+    return uc, (uf[0] if single else uf)
 
 
 def project(G, uc, uf, rho_c, beta0_c, sbar_c, rho_f, beta0_f, sbar_f, remove_mean=True):

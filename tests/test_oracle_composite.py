@@ -191,3 +191,103 @@ def test_composite_rejects_bad_patches():
         CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, (0, 2, 2), (4, 4, 4))  # touches a domain face
     with pytest.raises(ValueError):
         CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, (2, 2, 2), (2, 4, 4))  # empty
+
+
+# ---- several patches on the fine level (the batched layout with coarse-fine interfaces) ----
+
+MULTI = [
+    ((12, 10, 10), (N, N, N), (N, N, N), [((1, 1, 1), (4, 5, 4)), ((6, 2, 2), (11, 8, 9))]),
+    # one coarse cell between the patches along x: its two x faces both match fine fluxes
+    ((12, 8, 10), (P, P, N), (P, P, N), [((1, 1, 1), (5, 4, 4)), ((6, 1, 5), (10, 7, 9))]),
+    ((10, 10, 10), (P, P, D), (P, P, D), [((2, 2, 2), (4, 4, 4)), ((6, 6, 6), (8, 8, 8)), ((2, 6, 2), (4, 8, 5))]),
+]
+
+
+def multi_case(case, seed):
+    n, lo, hi, boxes = case
+    G = CP.Composite(n, 1.0 / n[0], lo, hi, patches=boxes)
+    rng = np.random.default_rng(seed)
+    cs = tuple(reversed(G.n))
+    fss = [tuple(reversed(nf)) for nf in G.nfs]
+    e = lambda s: np.exp(rng.standard_normal(s))
+    return G, rng, e(cs), e(cs), [e(s) for s in fss], [e(s) for s in fss]
+
+
+def multi_centres(G):
+    H = G.H
+    zc, yc, xc = np.meshgrid(*[(np.arange(m) + 0.5) * H for m in reversed(G.n)], indexing="ij")
+    fine = []
+    for (plo, _), nf in zip(G.boxes, G.nfs):
+        fine.append(np.meshgrid(*[(plo[2 - q] + (np.arange(nf[2 - q]) + 0.5) / 2) * H for q in range(3)],
+                                indexing="ij")[::-1])
+    return (xc, yc, zc), fine
+
+
+@pytest.mark.parametrize("case", MULTI)
+def test_multi_patch_conservation_null_space_and_linear(case):
+    G, rng, rc, bc, rfs, bfs = multi_case(case, 7)
+    A = CP.operator_matrix(G, rc, bc, rfs, bfs)
+    v = CP.volumes(G)
+    if G.singular:
+        for _ in range(3):
+            y = A @ rng.standard_normal(G.nunk)
+            assert abs(v @ y) <= 1e-12 * (v @ np.abs(y))
+        assert np.abs(A @ np.ones(G.nunk)).max() <= 1e-12 * np.abs(A).max()
+    (xc, yc, zc), fine = multi_centres(G)
+    ones_c = np.ones(xc.shape)
+    ones_f = [np.ones(f[0].shape) for f in fine]
+    A1 = CP.operator_matrix(G, ones_c, ones_c, ones_f, ones_f)
+    inner = ~G.covered.copy()
+    for d in range(3):
+        if G.lo[d] != P:
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            inner[tuple(sl)] = False
+            sl[2 - d] = -1
+            inner[tuple(sl)] = False
+    for a in [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (0.3, -0.7, 1.1)]:
+        a = tuple(0.0 if G.lo[d] == P else a[d] for d in range(3))
+        pc = a[0] * xc + a[1] * yc + a[2] * zc
+        pf = [a[0] * f[0] + a[1] * f[1] + a[2] * f[2] for f in fine]
+        yc_, yf_ = CP.unpack(G, A1 @ CP.pack(G, pc, pf))
+        for y in yf_:
+            assert np.abs(y).max() <= 1e-12 / G.h ** 2
+        assert np.abs(yc_[inner]).max() <= 1e-12 / G.h ** 2
+
+
+@pytest.mark.parametrize("case", MULTI)
+def test_multi_patch_rows_away_and_projection_identity(case):
+    G, rng, rc, bc, rfs, bfs = multi_case(case, 8)
+    pc = rng.standard_normal(rc.shape)
+    pfs = [rng.standard_normal(r.shape) for r in rfs]
+    yc_, _ = CP.apply(G, rc, bc, rfs, bfs, pc, pfs)
+    gc = W.Geom(G.n, G.H, G.lo, G.hi)
+    ref_c = O.mac_apply(gc, O.mac_coeffs(gc, rc, bc), pc)
+    far = np.ones(rc.shape, bool)
+    for plo, phi in G.boxes:
+        far[max(plo[2] - 1, 0):phi[2] + 1, max(plo[1] - 1, 0):phi[1] + 1, max(plo[0] - 1, 0):phi[0] + 1] = False
+    assert far.sum() > 0
+    assert np.abs(yc_[far] - ref_c[far]).max() <= 1e-12 * np.abs(ref_c).max()
+    # the projection identity with every patch's faces
+    uc = [rng.standard_normal(tuple(reversed([G.n[e] + (1 if e == d else 0) for e in range(3)]))) for d in range(3)]
+    ufs = [[rng.standard_normal(tuple(reversed([nf[e] + (1 if e == d else 0) for e in range(3)]))) for d in range(3)]
+           for nf in G.nfs]
+    sc = rng.standard_normal(rc.shape)
+    sfs = [rng.standard_normal(r.shape) for r in rfs]
+    uc2, uf2, _, _, info = CP.project(G, uc, ufs, rc, bc, sc, rfs, bfs, sfs)
+    assert info["rel_resid"] <= 1e-12
+    bsf = [b * s_ for b, s_ in zip(bfs, sfs)]
+    dv = CP.divergence(G, uc2, uf2, bc, bfs) - CP.pack(G, bc * sc, bsf) - info["mean"]
+    assert np.abs(dv).max() <= 1e-11 * np.abs(info["f"]).max()
+
+
+def test_multi_patch_layout_rules():
+    with pytest.raises(ValueError):  # touching patches (no coarse cell between)
+        CP.Composite((12, 8, 8), 1.0 / 12, (N,) * 3, (N,) * 3, patches=[((1, 1, 1), (5, 4, 4)), ((5, 1, 1), (9, 4, 4))])
+    with pytest.raises(ValueError):  # diagonal neighbours: the ghost stencils would read covered cells
+        CP.Composite((12, 12, 8), 1.0 / 12, (N,) * 3, (N,) * 3,
+                     patches=[((1, 1, 1), (5, 5, 4)), ((5, 5, 1), (9, 9, 4))])
+    with pytest.raises(ValueError):
+        CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, patches=[])
+    G = CP.Composite((12, 8, 8), 1.0 / 12, (N,) * 3, (N,) * 3, patches=[((1, 1, 1), (5, 4, 4)), ((6, 1, 1), (10, 4, 4))])
+    assert G.npatch == 2 and G.nunk == G.nc + 2 * 8 * 6 * 6
