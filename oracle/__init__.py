@@ -9,7 +9,9 @@ MAC face arrays carry n_d + 1 entries along their own direction, nodal arrays
 have n nodes on a periodic axis and n + 1 on a wall axis.
 
 ``composite.py`` (numpy / scipy.sparse) holds the two-level composite MAC
-operator and projection (refinement ratio 2) with a sparse direct solve.
+operator and projection (refinement ratio 2, any number of fine patches) with a
+sparse direct solve; ``composite_ml.py`` the composite operator on any number
+of levels, written separately and equal to it on two.
 
 Functions without a pin in the CPU tests: none.  Readings of the paper are
 listed in the C sources' headers and in ``composite.py``'s.
