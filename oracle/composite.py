@@ -229,18 +229,65 @@ def _cf_cells(G, c, nb, d, s, q):
     return out
 
 
+def _coarse_row(G, c, rho_c, beta0_c, rho_f, beta0_f):
+    """(column, value) entries of the row of uncovered coarse cell c"""
+    H, h = G.H, G.h
+    out = []
+    r = int(_at(G.cid, c))
+    rc, bc = _at(rho_c, c), _at(beta0_c, c)
+    for d in range(3):
+        for s in (-1, 1):
+            nb = G.coarse_nb(c, d, s)
+            if nb is None:
+                if G.domain_bc(d, s) == DIRICHLET:  # phi = 0 at the face: (0 - phi)/(H/2)
+                    out.append((r, -2.0 * (bc / rc) / (H * H)))
+                continue
+            q = G.patch_of(nb)
+            if q < 0:
+                b = _bmean(bc, rc, _at(beta0_c, nb), _at(rho_c, nb))
+                out.append((int(_at(G.cid, nb)), b / (H * H)))
+                out.append((r, -b / (H * H)))
+                continue
+            # coarse-fine face: the mean of the four fine fluxes b (phi_F1 - phi_g)/h
+            for F in _cf_cells(G, c, nb, d, s, q):
+                bf = _bmean(_at(beta0_f[q], F), _at(rho_f[q], F), bc, rc)
+                w = 0.25 * bf / (h * H)
+                out.append((int(_at(G.fids[q], F)), w))
+                _, terms = ghost_terms(G, F, d, -s, q)
+                for col, wt in terms:
+                    out.append((col, -w * wt))
+    return r, out
+
+
+def _fine_row(G, p, F, rho_c, beta0_c, rho_f, beta0_f):
+    """(column, value) entries of the row of fine cell F of patch p"""
+    h = G.h
+    out = []
+    r = int(_at(G.fids[p], F))
+    rf, bf_ = _at(rho_f[p], F), _at(beta0_f[p], F)
+    for d in range(3):
+        for s in (-1, 1):
+            N = list(F)
+            N[d] += s
+            N = tuple(N)
+            if G.fine_inside(N, p):
+                b = _bmean(bf_, rf, _at(beta0_f[p], N), _at(rho_f[p], N))
+                out.append((int(_at(G.fids[p], N)), b / (h * h)))
+                out.append((r, -b / (h * h)))
+            else:
+                C, terms = ghost_terms(G, F, d, s, p)
+                b = _bmean(bf_, rf, _at(beta0_c, C), _at(rho_c, C))
+                for col, wt in terms:
+                    out.append((col, b * wt / (h * h)))
+                out.append((r, -b / (h * h)))
+    return r, out
+
+
 def operator_matrix(G, rho_c, beta0_c, rho_f, beta0_f):
     """The composite operator L as a sparse matrix on the unknown vector (coarse
     uncovered cells in x-fastest order, then the fine cells patch by patch)."""
     rho_f, beta0_f = _fine_list(G, rho_f), _fine_list(G, beta0_f)
     rows, cols, vals = [], [], []
-    H, h = G.H, G.h
-
-    def add(r, c, v):
-        rows.append(r)
-        cols.append(c)
-        vals.append(v)
-
     nx, ny, nz = G.n
     for k in range(nz):
         for j in range(ny):
@@ -248,53 +295,40 @@ def operator_matrix(G, rho_c, beta0_c, rho_f, beta0_f):
                 c = (i, j, k)
                 if G.in_patch(c):
                     continue
-                r = int(_at(G.cid, c))
-                rc, bc = _at(rho_c, c), _at(beta0_c, c)
-                for d in range(3):
-                    for s in (-1, 1):
-                        nb = G.coarse_nb(c, d, s)
-                        if nb is None:
-                            if G.domain_bc(d, s) == DIRICHLET:  # phi = 0 at the face: (0 - phi)/(H/2)
-                                add(r, r, -2.0 * (bc / rc) / (H * H))
-                            continue
-                        q = G.patch_of(nb)
-                        if q < 0:
-                            b = _bmean(bc, rc, _at(beta0_c, nb), _at(rho_c, nb))
-                            add(r, int(_at(G.cid, nb)), b / (H * H))
-                            add(r, r, -b / (H * H))
-                            continue
-                        # coarse-fine face: the mean of the four fine fluxes b (phi_F1 - phi_g)/h
-                        for F in _cf_cells(G, c, nb, d, s, q):
-                            bf = _bmean(_at(beta0_f[q], F), _at(rho_f[q], F), bc, rc)
-                            w = 0.25 * bf / (h * H)
-                            add(r, int(_at(G.fids[q], F)), w)
-                            _, terms = ghost_terms(G, F, d, -s, q)
-                            for col, wt in terms:
-                                add(r, col, -w * wt)
+                r, ent = _coarse_row(G, c, rho_c, beta0_c, rho_f, beta0_f)
+                for col, v in ent:
+                    rows.append(r)
+                    cols.append(col)
+                    vals.append(v)
     for p in range(G.npatch):
         fx, fy, fz = G.nfs[p]
         for K in range(fz):
             for J in range(fy):
                 for I in range(fx):
-                    F = (I, J, K)
-                    r = int(_at(G.fids[p], F))
-                    rf, bf_ = _at(rho_f[p], F), _at(beta0_f[p], F)
-                    for d in range(3):
-                        for s in (-1, 1):
-                            N = list(F)
-                            N[d] += s
-                            N = tuple(N)
-                            if G.fine_inside(N, p):
-                                b = _bmean(bf_, rf, _at(beta0_f[p], N), _at(rho_f[p], N))
-                                add(r, int(_at(G.fids[p], N)), b / (h * h))
-                                add(r, r, -b / (h * h))
-                            else:
-                                C, terms = ghost_terms(G, F, d, s, p)
-                                b = _bmean(bf_, rf, _at(beta0_c, C), _at(rho_c, C))
-                                for col, wt in terms:
-                                    add(r, col, b * wt / (h * h))
-                                add(r, r, -b / (h * h))
+                    r, ent = _fine_row(G, p, (I, J, K), rho_c, beta0_c, rho_f, beta0_f)
+                    for col, v in ent:
+                        rows.append(r)
+                        cols.append(col)
+                        vals.append(v)
     return sp.csr_matrix((vals, (rows, cols)), shape=(G.nunk, G.nunk))
+
+
+def apply_at(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, cells):
+    """L phi at the listed cells only, one row at a time (for sampled checks of
+    large composite grids): cells as ("c", (i, j, k)) for an uncovered coarse
+    cell or ("f", p, (I, J, K)) for a fine cell of patch p."""
+    rho_f, beta0_f = _fine_list(G, rho_f), _fine_list(G, beta0_f)
+    x = pack(G, phi_c, phi_f)
+    out = np.empty(len(cells))
+    for q, cell in enumerate(cells):
+        if cell[0] == "c":
+            if G.in_patch(cell[1]):
+                raise ValueError("a covered coarse cell has no row")
+            _, ent = _coarse_row(G, tuple(cell[1]), rho_c, beta0_c, rho_f, beta0_f)
+        else:
+            _, ent = _fine_row(G, int(cell[1]), tuple(cell[2]), rho_c, beta0_c, rho_f, beta0_f)
+        out[q] = sum(v * x[col] for col, v in ent)
+    return out
 
 
 def volumes(G):

@@ -291,3 +291,50 @@ def test_multi_patch_layout_rules():
         CP.Composite((8, 8, 8), 1.0 / 8, (N,) * 3, (N,) * 3, patches=[])
     G = CP.Composite((12, 8, 8), 1.0 / 12, (N,) * 3, (N,) * 3, patches=[((1, 1, 1), (5, 4, 4)), ((6, 1, 1), (10, 4, 4))])
     assert G.npatch == 2 and G.nunk == G.nc + 2 * 8 * 6 * 6
+
+
+def test_apply_at_rows_match_the_matrix():
+    """sampled rows, one at a time, equal the assembled operator's (the form the
+    full-size GPU checks will use)"""
+    G, rng, rc, bc, rfs, bfs = multi_case(MULTI[1], 9)
+    pc = rng.standard_normal(rc.shape)
+    pfs = [rng.standard_normal(r.shape) for r in rfs]
+    full = CP.operator_matrix(G, rc, bc, rfs, bfs) @ CP.pack(G, pc, pfs)
+    cells, want = [], []
+    for _ in range(60):
+        if rng.random() < 0.5:
+            while True:
+                c = tuple(int(rng.integers(0, G.n[d])) for d in range(3))
+                if not G.in_patch(c):
+                    break
+            cells.append(("c", c))
+            want.append(full[int(G.cid[c[2], c[1], c[0]])])
+        else:
+            p = int(rng.integers(0, G.npatch))
+            F = tuple(int(rng.integers(0, G.nfs[p][d])) for d in range(3))
+            cells.append(("f", p, F))
+            want.append(full[int(G.fids[p][F[2], F[1], F[0]])])
+    got = CP.apply_at(G, rc, bc, rfs, bfs, pc, pfs, cells)
+    assert np.abs(got - np.array(want)).max() <= 1e-13 * np.abs(full).max()
+
+
+def test_apply_at_large_grid_far_rows_are_single_level():
+    """a grid too large to assemble quickly here: coarse rows away from the patch
+    equal the single-level oracle's at the same cells"""
+    n = (64, 48, 40)
+    G = CP.Composite(n, 1.0 / 64, (P, P, N), (P, P, N), (20, 12, 10), (44, 36, 30))
+    rng = np.random.default_rng(10)
+    cs, fs = tuple(reversed(G.n)), tuple(reversed(G.nf))
+    rc, bc = np.exp(rng.standard_normal(cs)), np.exp(rng.standard_normal(cs))
+    rf, bf = np.exp(rng.standard_normal(fs)), np.exp(rng.standard_normal(fs))
+    pc, pf = rng.standard_normal(cs), rng.standard_normal(fs)
+    gc = W.Geom(G.n, G.H, G.lo, G.hi)
+    ref = O.mac_apply(gc, O.mac_coeffs(gc, rc, bc), pc)
+    cells = []
+    while len(cells) < 50:
+        c = tuple(int(rng.integers(0, G.n[d])) for d in range(3))
+        if all(c[d] < G.plo[d] - 1 or c[d] > G.phi[d] for d in range(3)):
+            cells.append(("c", c))
+    got = CP.apply_at(G, rc, bc, rf, bf, pc, pf, cells)
+    want = np.array([ref[c[1][2], c[1][1], c[1][0]] for c in cells])
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(ref).max()
