@@ -269,3 +269,106 @@ def batched_patches(npatch=96, seed=3, device="cpu", sizes=PATCH_SIZES, nmodes=8
         H = 1.0 / math.log(contrast[p])
         out.append(planar(int(edges[p]), H, 0.6, nmodes, 1, (seed, p), device, f"patch{p}"))
     return out
+
+
+# ---- two-level composite (AMR) inputs -------------------------------------------------
+
+@dataclass
+class CompositeWorkload:
+    """A coarse level and one ratio-2 fine patch over the coarse box [plo, phi):
+    the same closed-form fields evaluated at each level's cell and face centres
+    (each level with its own density noise).  beta0 is given per cell on both
+    levels (closed form at the cell centres)."""
+
+    name: str
+    geom: Geom
+    plo: tuple
+    phi: tuple
+    rho_c: torch.Tensor
+    beta0_c: torch.Tensor
+    sbar_c: torch.Tensor
+    u_c: list
+    rho_f: torch.Tensor
+    beta0_f: torch.Tensor
+    sbar_f: torch.Tensor
+    u_f: list
+    meta: dict = field(default_factory=dict)
+
+
+def _patch_points(geom: Geom, plo, phi, d, device):
+    """1D coordinates of the fine patch's d-face centres (d=None: cell centres)"""
+    h = geom.dx / 2.0
+    out = []
+    for a in range(3):
+        m = 2 * (phi[a] - plo[a])
+        i = torch.arange(m + (1 if d == a else 0), dtype=torch.float64, device=device)
+        out.append(plo[a] * geom.dx + (i * h if d == a else (i + 0.5) * h))
+    return out
+
+
+def composite_planar(n, plo, phi, H, beta_exp, nmodes, spots, seed, device="cpu", name="composite_planar"):
+    """The planar box of planar() (periodic x, y; walls in z) with a fine patch
+    over the coarse box [plo, phi): rho0(z) = exp(-z/H), beta0 = rho0**p,
+    rho = rho0 (1 + 0.01 xi) per level, the same Fourier-mode U and hotspot Sbar
+    on both levels.  The patch keeps one coarse cell from the domain faces."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    g = Geom(tuple(n), 1.0 / n[0], (PERIODIC, PERIODIC, NEUMANN), (PERIODIC, PERIODIC, NEUMANN))
+    ss = np.random.SeedSequence(seed)
+    r_noise_c, r_noise_f, r_modes, r_spots = [np.random.default_rng(s) for s in ss.spawn(4)]
+    modes = draw_modes(r_modes, nmodes)
+    centres = [(0.5, 0.5, 0.5)] if spots == "center" else list(r_spots.uniform(0.2, 0.8, size=(spots, 3)))
+
+    def level(pts_c, pts_f, rng, shape):
+        z = pts_c[2]
+        rho0 = torch.exp(-z / H)
+        xi = torch.from_numpy(rng.uniform(-1.0, 1.0, size=int(np.prod(shape)))).reshape(shape).to(device)
+        rho = (rho0[:, None, None] * (1.0 + 0.01 * xi)).contiguous()
+        beta0 = (rho0 ** beta_exp)[:, None, None].expand(shape).contiguous()
+        sbar = eval_hotspots(centres, 0.05, pts_c)
+        u = [eval_modes(modes, d, pts_f[d]) for d in range(3)]
+        return rho, beta0, sbar, u
+
+    cshape = (n[2], n[1], n[0])
+    rc, bc, sc, uc = level(_points(g, None, device), [_points(g, d, device) for d in range(3)], r_noise_c, cshape)
+    uc = _periodic_faces(g, uc)
+    nf = [2 * (phi[a] - plo[a]) for a in range(3)]
+    fshape = (nf[2], nf[1], nf[0])
+    rf, bf, sf, uf = level(_patch_points(g, plo, phi, None, device),
+                           [_patch_points(g, plo, phi, d, device) for d in range(3)], r_noise_f, fshape)
+    return CompositeWorkload(name, g, tuple(plo), tuple(phi), rc, bc, sc, uc, rf, bf, sf, uf,
+                             dict(H=H, beta_exp=beta_exp, modes=nmodes, seed=seed, centres=centres))
+
+
+def composite_star(n, plo, phi, nmodes, seed, device="cpu", name="composite_star"):
+    """The full star of star() (Dirichlet faces) with a fine patch over the
+    coarse box [plo, phi) (the core): rho0(r) as star_rho0, beta0 = rho0**0.6
+    at the cell centres of each level, rho = rho0 (1 + 0.01 xi) per level, the
+    same Fourier-mode U and central hotspot on both levels."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    Dd = DIRICHLET
+    g = Geom(tuple(n), 1.0 / n[0], (Dd, Dd, Dd), (Dd, Dd, Dd))
+    ss = np.random.SeedSequence(seed)
+    r_noise_c, r_noise_f, r_modes = [np.random.default_rng(s) for s in ss.spawn(3)]
+    modes = draw_modes(r_modes, nmodes)
+
+    def level(pts_c, pts_f, rng, shape):
+        x, y, z = pts_c
+        r = torch.sqrt((z[:, None, None] - 0.5) ** 2 + (y[None, :, None] - 0.5) ** 2 + (x[None, None, :] - 0.5) ** 2)
+        rho0 = star_rho0(r)
+        xi = torch.from_numpy(rng.uniform(-1.0, 1.0, size=int(np.prod(shape)))).reshape(shape).to(device)
+        rho = (rho0 * (1.0 + 0.01 * xi)).contiguous()
+        beta0 = (rho0 ** 0.6).contiguous()
+        sbar = eval_hotspots([(0.5, 0.5, 0.5)], 0.05, pts_c)
+        u = [eval_modes(modes, d, pts_f[d]) for d in range(3)]
+        return rho, beta0, sbar, u
+
+    cshape = (n[2], n[1], n[0])
+    rc, bc, sc, uc = level(_points(g, None, device), [_points(g, d, device) for d in range(3)], r_noise_c, cshape)
+    nf = [2 * (phi[a] - plo[a]) for a in range(3)]
+    fshape = (nf[2], nf[1], nf[0])
+    rf, bf, sf, uf = level(_patch_points(g, plo, phi, None, device),
+                           [_patch_points(g, plo, phi, d, device) for d in range(3)], r_noise_f, fshape)
+    return CompositeWorkload(name, g, tuple(plo), tuple(phi), rc, bc, sc, uc, rf, bf, sf, uf,
+                             dict(modes=nmodes, seed=seed))

@@ -43,3 +43,32 @@ def test_batched_patch_recipe():
     assert len(ps) == 6
     for p in ps:
         assert p.geom.n[0] in (8, 12, 16)
+
+
+def test_composite_workloads_shapes_and_recipe():
+    import numpy as np
+    from oracle import composite as CP
+    for make in (lambda: W.composite_planar(12, (3, 3, 3), (9, 9, 9), 0.2, 0.6, 4, "center", 5),
+                 lambda: W.composite_star(12, (4, 4, 4), (8, 8, 8), 4, 6)):
+        a, b = make(), make()
+        assert torch.equal(a.rho_f, b.rho_f) and torch.equal(a.u_f[2], b.u_f[2])  # seeded
+        nf = [2 * (a.phi[d] - a.plo[d]) for d in range(3)]
+        assert tuple(a.rho_f.shape) == (nf[2], nf[1], nf[0]) == tuple(a.beta0_f.shape) == tuple(a.sbar_f.shape)
+        for d in range(3):
+            want = [nf[2], nf[1], nf[0]]
+            want[2 - d] += 1
+            assert tuple(a.u_f[d].shape) == tuple(want)
+            assert tuple(a.u_c[d].shape) == a.geom.face_shape(d)
+        # the hotspot at the domain centre lies in the patch, whose centres sample
+        # its peak more closely than the coarse ones
+        assert float(a.sbar_f.max()) > float(a.sbar_c.max())
+        # a valid composite problem: the oracle's projection meets its identity
+        G = CP.Composite(a.geom.n, a.geom.dx, a.geom.lo, a.geom.hi, a.plo, a.phi)
+        npy = lambda t: t.numpy()
+        uc2, uf2, _, _, info = CP.project(G, [npy(x) for x in a.u_c], [npy(x) for x in a.u_f], npy(a.rho_c),
+                                          npy(a.beta0_c), npy(a.sbar_c), npy(a.rho_f), npy(a.beta0_f),
+                                          npy(a.sbar_f))
+        assert info["rel_resid"] <= 1e-12
+        dv = (CP.divergence(G, uc2, uf2, npy(a.beta0_c), npy(a.beta0_f))
+              - CP.pack(G, npy(a.beta0_c * a.sbar_c), npy(a.beta0_f * a.sbar_f)) - info["mean"])
+        assert np.abs(dv).max() <= 1e-11 * np.abs(info["f"]).max()
