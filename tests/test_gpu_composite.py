@@ -113,3 +113,33 @@ def test_composite_errors(mx, ctx):
     p = C.c_void_p(z.data_ptr())
     assert lib.mx_composite_apply(ctx, C.byref(gg), b, t, None, p, p, p, p, p, p, p) == mx.MX_ERR_ARG
     assert lib.mx_composite_divergence(ctx, C.byref(gg), b, t, p, p, p, p, p, p, p, p, p, None) == mx.MX_ERR_ARG
+
+
+@pytest.mark.parametrize("which", ["planar", "star"])
+def test_composite_on_the_composite_workloads(mx, ctx, which):
+    """the stratified box with a patch around its heating spot and the star with
+    a patch over its core: operator (on the workload's phi-like field Sbar) and
+    divergence of the workload's U, against the oracle"""
+    if which == "planar":
+        w = W.composite_planar(32, (8, 8, 8), (24, 24, 24), 0.2, 0.6, 8, "center", 7)
+    else:
+        w = W.composite_star(32, (12, 12, 12), (20, 20, 20), 8, 8)
+    G = CP.Composite(w.geom.n, w.geom.dx, w.geom.lo, w.geom.hi, w.plo, w.phi)
+    npy = lambda t: t.numpy()
+    want_c, want_f = CP.apply(G, npy(w.rho_c), npy(w.beta0_c), npy(w.rho_f), npy(w.beta0_f), npy(w.sbar_c),
+                              npy(w.sbar_f))
+    oc = torch.full(tuple(w.rho_c.shape), np.nan, dtype=torch.float64, device=DEV)
+    of = torch.full(tuple(w.rho_f.shape), np.nan, dtype=torch.float64, device=DEV)
+    d = lambda t: t.to(DEV)
+    mx.mx_composite_apply(ctx, w.geom, w.plo, w.phi, d(w.rho_c), d(w.beta0_c), d(w.rho_f), d(w.beta0_f),
+                          d(w.sbar_c), d(w.sbar_f), oc, of)
+    scale = max(np.abs(want_c[~G.covered]).max(), np.abs(want_f).max())
+    assert np.abs(oc.cpu().numpy()[~G.covered] - want_c[~G.covered]).max() <= 1e-12 * scale
+    assert np.abs(of.cpu().numpy() - want_f).max() <= 1e-12 * scale
+    dv_c, dv_f = CP.unpack(G, CP.divergence(G, [npy(x) for x in w.u_c], [npy(x) for x in w.u_f], npy(w.beta0_c),
+                                            npy(w.beta0_f)))
+    mx.mx_composite_divergence(ctx, w.geom, w.plo, w.phi, [d(x) for x in w.u_c], [d(x) for x in w.u_f],
+                               d(w.beta0_c), d(w.beta0_f), oc, of)
+    scale = max(np.abs(dv_c[~G.covered]).max(), np.abs(dv_f).max())
+    assert np.abs(oc.cpu().numpy()[~G.covered] - dv_c[~G.covered]).max() <= 1e-12 * scale
+    assert np.abs(of.cpu().numpy() - dv_f).max() <= 1e-12 * scale
