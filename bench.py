@@ -127,6 +127,45 @@ def algorithmic_bytes_per_cell():
     return {"smooth_fine": 12.0, "resid64": 44.0}
 
 
+def mac_iteration_bytes_per_cell(nu1, nu2, w):
+    """Algorithmic bytes per finest-level cell of one refinement iteration of the
+    MAC solve (the fixed model of the measurement plan): a V-cycle(nu1, nu2) on
+    all levels (N_total = 8/7 N) moves w (6 (nu1 + nu2) + 7.25) bytes per cell
+    (a sweep reads phi, f, b_x, b_y, b_z and writes phi: 6w; residual +
+    restriction 5.125w; prolongation + correction 2.125w), and the outer step
+    adds the high-precision residual (5 reads x 8 B + 4 B written) and the
+    update (20 B): 64 B/cell.  w = 4 (FP32 V-cycle) or 8 (plain FP64)."""
+    return (8.0 / 7.0) * w * (6.0 * (nu1 + nu2) + 7.25) + 64.0
+
+
+def mac_iteration_fp64_flops_per_cell(nu1, nu2):
+    """FP64 flops per finest-level cell of one iteration of the plain FP64 solve:
+    a Gauss-Seidel update 19 (6 products and sums of the neighbours, h^2 f, the
+    5-term diagonal, one division counted as 1 flop), residual + restriction 22,
+    prolongation 1 per level cell (8/7 N in all), and the outer FP64 residual
+    with its norms and the update, 26."""
+    return (8.0 / 7.0) * (19.0 * (nu1 + nu2) + 22.0 + 1.0) + 26.0
+
+
+def roofline_per_vcycle(ncell, nu1, nu2, w, ms_solve, vcycles, hbm, loop_ms=None):
+    """Fraction of the HBM roofline per refinement iteration: the model's bytes
+    of one iteration over (solve time / iterations), against the measured copy
+    peak.  The solve time includes the setup and finish passes, so this is the
+    conservative figure; loop_ms (the traced time of the refinement loop alone)
+    gives the loop-only one."""
+    b = mac_iteration_bytes_per_cell(nu1, nu2, w) * ncell
+    v = max(vcycles, 1)
+    out = {"model_bytes_per_vcycle": b, "nu1": nu1, "nu2": nu2, "word_bytes": w,
+           "ms_per_vcycle": ms_solve / v,
+           "achieved_GBs": round(b / (ms_solve / v * 1e-3) / 1e9, 1),
+           "frac": round(b / (ms_solve / v * 1e-3) / 1e9 / hbm, 4),
+           "time": "whole solve / V-cycles (setup and finish included)"}
+    if loop_ms:
+        out["loop_only"] = {"ms_per_vcycle": loop_ms / v,
+                            "frac": round(b / (loop_ms / v * 1e-3) / 1e9 / hbm, 4)}
+    return out
+
+
 def launches_per_solve(g, o, vcycles, graph, krylov=0):
     """Kernels the library launches for one mixed-precision MAC solve (fill
     included), from the solver's structure: setup 13 + first residual 2; per
@@ -260,7 +299,9 @@ def run_mx(args):
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / kk
         fp64 = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "vcycles": i64[-1]["vcycles"],
-                "rel_resid": i64[-1]["rel_resid"], "note": "includes a 3-array restore of U per solve"}
+                "rel_resid": i64[-1]["rel_resid"],
+                "div_err_rel": i64[-1]["div_err_linf"] / max(i64[-1]["rhs_linf"], 1e-300),
+                "note": "includes a 3-array restore of U per solve"}
 
     # ---- FCG(1) (krylov = 1) against refinement, both timed in the same loop ----
     fcg = None
@@ -337,6 +378,28 @@ def run_mx(args):
                 "resid64": {"ms_per_launch": resid_per_launch,
                             "achieved_GBs": round(bpc["resid64"] * ncell / (resid_per_launch * 1e-3) / 1e9, 1)}}
 
+    # ---- per refinement iteration (the model's bytes per V-cycle over the time per
+    # V-cycle), for the mixed solve and the plain FP64 one; for the FP64 solve also
+    # the FP64-ALU bound from the measured FMA rate of the FP64 pipe ----
+    loop_ms = sum(v["ms_per_step"] for k, v in phases.items() if k not in ("setup", "finish"))
+    per_vc = {"mixed": roofline_per_vcycle(ncell, tuned.nu1, tuned.nu2, 4, ms_total / K, vcycles, hbm,
+                                           loop_ms=loop_ms)}
+    if fp64 is not None:
+        n1, n2 = tuned64.nu1, tuned64.nu2
+        per_vc["fp64"] = roofline_per_vcycle(ncell, n1, n2, 8, fp64["ms_per_solve"], fp64["vcycles"], hbm)
+        try:
+            p64 = mx.mx_probe_fma_peak(local, True)
+            fl = mac_iteration_fp64_flops_per_cell(n1, n2) * ncell
+            ach = fl / (fp64["ms_per_solve"] / max(fp64["vcycles"], 1) * 1e-3) / 1e12
+            fp64["alu_bound"] = {"bound": "fp64_alu", "peak_tflops": round(p64, 3), "unit": "TFLOP/s",
+                                 "peak_source": "measured FP64 FMA rate of this GPU (mx_probe_fma_peak)",
+                                 "model_flops_per_vcycle": fl, "achieved_tflops": round(ach, 4),
+                                 "frac": round(ach / p64, 4)}
+        except Exception as e:  # noqa: BLE001 - the probe is a measurement extra
+            fp64["alu_bound"] = {"error": str(e)}
+        fp64["hbm_frac_per_vcycle"] = per_vc["fp64"]["frac"]
+    roofline["per_vcycle"] = per_vc
+
     # ---- end to end through the C ABI with host buffers ----
     # Every step copies its inputs (rho, Sbar, the base-state profile, U) from
     # pinned host memory and reads its outputs (U, phi) back, all inside the
@@ -407,6 +470,10 @@ def run_mx(args):
         extras["nodal384"] = bench_nodal(mx, W, ctx, dev, stream, hbm=hbm)
         extras["batched96"] = bench_batched(mx, W, ctx, dev, stream, fp64=world == 1, rank=rank, world=world)
         extras["average512"] = bench_base(mx, W, ctx, dev, stream, hbm=hbm, cpu=rank == 0 and world == 1)
+        torch.cuda.empty_cache()
+        extras["star512"] = bench_star(mx, W, ctx, dev, stream, hbm=hbm)
+        extras["planar32_fp64"] = bench_planar32_fp64(mx, W, ctx, dev, stream)
+        extras["nodal_sweep"] = bench_nodal_sweep(mx, W, ctx, dev, stream, hbm)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
@@ -428,6 +495,8 @@ def run_mx(args):
                    "l2_policy": "inputs larger than L2 (fresh U copy per step, ~1.5 GB working set)",
                    "parallelism": f"replicas x{world}"},
         "vcycles_per_solve": vcycles, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
+        "rhs_linf": last["rhs_linf"], "div_err_rel": last["div_err_linf"] / max(last["rhs_linf"], 1e-300),
+        "hbm_frac_per_vcycle": per_vc["mixed"]["frac"],
         "fp64": fp64, "fcg": fcg, "phases": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, **extras,
     }
@@ -480,16 +549,22 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     run(ut, opts)
     trace = {k: {"ms": v[0], "launches": v[1]} for k, v in mx.mx_profile_read(ctx).items()}
     mx.mx_profile_enable(ctx, False)
-    # model bytes per V-cycle (FP32, nu = 2+2): sweeps 4w/node, residual+restriction
-    # 3.125w, prolongation 2.125w on every level (N_total = 8/7 N), + the double-float
-    # residual and update of the refinement loop (phi 8 read + 8 write, f 8, sigma 8, rhat 4)
-    model = nodes * (8.0 / 7.0) * 4 * (4 * 4 + 3.125 + 2.125) + nodes * 36
+    # model bytes per V-cycle at the timed sweep counts (FP32): a sweep reads phi, f,
+    # sigma and writes phi (4w/node), residual+restriction 3.125w, prolongation
+    # 2.125w on every level (N_total = 8/7 N), + the double-float residual and update
+    # of the refinement loop (phi 8 read + 8 write, f 8, sigma 8, rhat 4)
+    nu1, nu2 = tuned.nu1, tuned.nu2
+    model = nodes * (8.0 / 7.0) * 4 * (4 * (nu1 + nu2) + 3.125 + 2.125) + nodes * 36
     ms_solve = ms / steps
+    loop_ms = sum(v["ms"] for k, v in trace.items() if k not in ("setup", "finish"))
+    last = infos[-1]
     out = {"workload": f"nodal{n}", "nodes": nodes, "solves_per_s": 1e3 / ms_solve, "ms_per_solve": ms_solve,
-           "vcycles": vc, "rel_resid": infos[-1]["rel_resid"], "div_err_linf": infos[-1]["div_err_linf"],
+           "vcycles": vc, "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"],
+           "rhs_linf": last["rhs_linf"], "div_err_rel": last["div_err_linf"] / max(last["rhs_linf"], 1e-300),
            "ms_per_vcycle_upper": ms_solve / max(vc, 1),
            "hbm_frac_per_vcycle": round(model / (ms_solve / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
-           "model_bytes_per_vcycle": model, "phases": trace,
+           "hbm_frac_per_vcycle_loop_only": round(model / (loop_ms / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
+           "model_bytes_per_vcycle": model, "model_nu": [nu1, nu2], "phases": trace,
            "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z}}
     if fp64:
         o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=int(graph), nu1=tuned.nu1, nu2=tuned.nu2,
@@ -550,7 +625,8 @@ def bench_batched(mx, W, ctx, dev, stream, npatch=96, steps=2, warmup=1, fp64=Tr
            "patch_solves_per_s": npatch * 1e3 / ms_b, "cells_per_s": cells * 1e3 / ms_b, "ranks": world,
            "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2},
            "vcycles_max": max(i["vcycles"] for i in last), "vcycles_mean": statistics.mean(i["vcycles"] for i in last),
-           "rel_resid_max": max(i["rel_resid"] for i in last)}
+           "rel_resid_max": max(i["rel_resid"] for i in last),
+           "div_err_rel_max": max(i["div_err_linf"] / max(i["rhs_linf"], 1e-300) for i in last)}
     if fp64:
         o64 = mx.default_opts(prec=mx.MX_PREC_FP64)
         us = [[t.clone() for t in p.u] for p in ps]
@@ -671,28 +747,58 @@ def bench_base(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, cpu=True
     return r
 
 
-def cpu_baseline_sample(n_sample, n_full, reps=1):
-    """The FP64 oracle (single-threaded C) solving the same recipe at n_sample^3;
-    its solves/s is scaled by (n_sample/n_full)^3 to the full workload (its cost
-    per solve grows linearly with the cell count at a fixed iteration count)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_solves(w, b0, nthreads, tol=1e-10):
+    """nthreads independent oracle solves of the same inputs, run at the same time
+    in host threads (the oracle's C code releases the GIL; each solve works on its
+    own copies of U and phi).  Returns (wall seconds, infos)."""
+    import concurrent.futures as cf
+
+    import oracle as O
+
+    def one(_):
+        return O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=tol)[2]
+    t0 = time.perf_counter()
+    if nthreads == 1:
+        infos = [one(0)]
+    else:
+        with cf.ThreadPoolExecutor(nthreads) as ex:
+            infos = list(ex.map(one, range(nthreads)))
+    return time.perf_counter() - t0, infos
+
+
+def cpu_baseline_sample(n_sample, n_full):
+    """The FP64 oracle (plain C) solving the same recipe at n_sample^3, scaled by
+    (n_sample/n_full)^3 to the full workload (its cost per solve grows linearly
+    with the cell count at a fixed iteration count): once on one core, and as
+    throughput of one concurrent solve per host core (the reported value)."""
     import oracle as O
     from paper_1908_03634_gb300 import workloads as W
     O.build()
     w = W.planar256(device="cpu", n=n_sample)
     b0 = O.fill(w.geom, w.prof_beta0)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        _, _, info = O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-10)
-    dt = (time.perf_counter() - t0) / reps
     scale = (n_sample / n_full) ** 3
-    return {"value": round(scale / dt, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle solve of the planar{n_full} recipe at {n_sample}^3 "
-                      f"({dt:.2f} s, {info['iters']} MG-PCG iterations), scaled by ({n_sample}/{n_full})^3"}
+    dt1, i1 = oracle_solves(w, b0, 1)
+    nc = host_cores()
+    dtn, _ = oracle_solves(w, b0, nc)
+    return {"value": round(scale * nc / dtn, 6), "unit": UNIT, "cores": nc, "kind": "oracle",
+            "sample": f"{nc} concurrent oracle solves (one per host core) of the planar{n_full} recipe at "
+                      f"{n_sample}^3 in {dtn:.2f} s wall, each {i1[0]['iters']} MG-PCG iterations to 1e-10, "
+                      f"scaled by ({n_sample}/{n_full})^3",
+            "one_core": {"value": round(scale / dt1, 6), "cores": 1, "sample": f"one solve at {n_sample}^3 "
+                         f"({dt1:.2f} s), scaled by ({n_sample}/{n_full})^3"}}
 
 
 def run_reference(args):
     """The CPU oracle as the reference arm: each step solves the planar recipe at
-    64^3 (bounded sample), reported in solves/s of the full workload."""
+    64^3 (a bounded sample) once per host core, concurrently; reported in solves/s
+    of the full workload."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
     import oracle as O
@@ -701,23 +807,115 @@ def run_reference(args):
     ns = 64
     w = W.planar256(device="cpu", n=ns)
     b0 = O.fill(w.geom, w.prof_beta0)
+    nc = host_cores()
     for _ in range(args.warmup):
-        O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-10)
-    t0 = time.perf_counter()
+        oracle_solves(w, b0, nc)
+    t = 0.0
     for _ in range(args.steps):
-        _, _, info = O.mac_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-10)
-    dt = (time.perf_counter() - t0) / args.steps
+        dt, infos = oracle_solves(w, b0, nc)
+        t += dt
+    dt = t / args.steps
     scale = (ns / args.n) ** 3
-    v = scale / dt
-    sample = (f"oracle solve of the planar{args.n} recipe at {ns}^3 per step ({dt:.3f} s, "
-              f"{info['iters']} MG-PCG iterations), scaled by ({ns}/{args.n})^3")
+    v = scale * nc / dt
+    sample = (f"{nc} concurrent oracle solves (one per host core) of the planar{args.n} recipe at {ns}^3 per "
+              f"step ({dt:.3f} s wall, {infos[0]['iters']} MG-PCG iterations each), scaled by ({ns}/{args.n})^3")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"planar{args.n}", "rel_tol": 1e-10},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def bench_star(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, n=512):
+    """Full-star MAC projection (Dirichlet walls, radial base state with the 1e-6
+    floor beyond r = 0.45, 1e6 contrast) at n^3: mixed precision at the autotuned
+    settings, the plain FP64 solve and FCG(1) beside it; solves/s, V-cycles and
+    the HBM fraction per V-cycle (the same model as the planar line)."""
+    import torch
+    w = W.star512(device=dev, n=n)
+    g = w.geom
+    beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=dev)
+    phi = torch.zeros_like(beta0)
+    us = [[t.clone() for t in w.u] for _ in range(min(steps + warmup, 4))]
+
+    def step(i, o):
+        u = us[i % len(us)]
+        for d in range(3):
+            u[d].copy_(w.u[d])
+        mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
+        return mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
+    mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
+    tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_MAC, g, *w.u, w.rho, beta0, w.sbar)
+    o = mx.default_opts(nu1=0, nu2=0)
+    for i in range(warmup):
+        step(i, o)
+    ms, infos = timed(lambda i: step(i, o), steps, stream)
+    o64 = mx.default_opts(prec=mx.MX_PREC_FP64, nu1=tuned.nu1, nu2=tuned.nu2, tile_z=tuned.tile_z)
+    step(0, o64)
+    k64 = 2
+    ms64, i64 = timed(lambda i: step(i, o64), k64, stream)
+    ok = mx.default_opts(nu1=0, nu2=0, krylov=1)
+    step(0, ok)
+    kk = max(2, steps // 2)
+    msk, ik = timed(lambda i: step(i, ok), kk, stream)
+    last = infos[-1]
+    vc = last["vcycles"]
+    ms_s = ms / steps
+    out = {"workload": f"star{n}", "metric": f"MAC projection solves/s to 1e-10 (full star {n}^3, Dirichlet)",
+           "value": 1e3 / ms_s, "unit": "solves/s", "ms_per_solve": ms_s, "vcycles": vc,
+           "rel_resid": last["rel_resid"], "div_err_linf": last["div_err_linf"], "rhs_linf": last["rhs_linf"],
+           "div_err_rel": last["div_err_linf"] / max(last["rhs_linf"], 1e-300),
+           "per_vcycle": roofline_per_vcycle(g.ncell, tuned.nu1, tuned.nu2, 4, ms_s, vc, hbm),
+           "fp64": {"solves_per_s": k64 * 1e3 / ms64, "ms_per_solve": ms64 / k64, "vcycles": i64[-1]["vcycles"],
+                    "per_vcycle": roofline_per_vcycle(g.ncell, tuned.nu1, tuned.nu2, 8, ms64 / k64,
+                                                      i64[-1]["vcycles"], hbm)},
+           "fcg": {"solves_per_s": kk * 1e3 / msk, "ms_per_solve": msk / kk, "vcycles": ik[-1]["vcycles"],
+                   "rel_resid": ik[-1]["rel_resid"]},
+           "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z, "fused": tuned.fused},
+           "note": "each solve includes a 3-array restore of U and the Fill of beta0"}
+    del w, us, beta0, phi
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_planar32_fp64(mx, W, ctx, dev, stream, steps=20, warmup=3):
+    """The 32^3 planar smoke configuration (H = 0.1, beta0 = rho0): plain FP64
+    projection to 1e-10, solves/s (launch-latency bound at this size)."""
+    import torch
+    w = W.planar32(device=dev)
+    g = w.geom
+    beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=dev)
+    mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0, g.dx, (0.5, 0.5, 0.5), beta0)
+    phi = torch.zeros_like(beta0)
+    u = [t.clone() for t in w.u]
+    o = mx.default_opts(prec=mx.MX_PREC_FP64)
+
+    def step(i):
+        for d in range(3):
+            u[d].copy_(w.u[d])
+        return mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
+    for i in range(warmup):
+        step(i)
+    ms, infos = timed(step, steps, stream)
+    last = infos[-1]
+    return {"workload": "planar32", "prec": "fp64", "solves_per_s": steps * 1e3 / ms, "ms_per_solve": ms / steps,
+            "vcycles": last["vcycles"], "rel_resid": last["rel_resid"],
+            "div_err_rel": last["div_err_linf"] / max(last["rhs_linf"], 1e-300)}
+
+
+def bench_nodal_sweep(mx, W, ctx, dev, stream, hbm, sizes=(64, 128, 192, 256, 384, 512)):
+    """The nodal projection's size sweep: per size the tuned mixed solve, its
+    time per V-cycle and HBM fraction per V-cycle (FP64 beside it up to 256^3)."""
+    import torch
+    out = []
+    for n in sizes:
+        r = bench_nodal(mx, W, ctx, dev, stream, n=n, steps=2, warmup=1, fp64=(n <= 256), hbm=hbm)
+        r.pop("phases", None)
+        out.append(r)
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_other(args):
@@ -761,46 +959,11 @@ def run_other(args):
         if rank == 0:
             print(json.dumps(r), flush=True)
     elif args.workload == "nodal-sweep":
-        for n in (64, 128, 192, 256, 384, 512):
-            r = bench_nodal(mx, W, ctx, dev, stream, n=n, steps=2, warmup=1, fp64=(n <= 256), hbm=hbm)
+        for r in bench_nodal_sweep(mx, W, ctx, dev, stream, hbm):
             print(json.dumps(r), flush=True)
-            torch.cuda.empty_cache()
     else:
-        w = W.star512(device=dev)
-        g = w.geom
-        beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=dev)
-        phi = torch.zeros_like(beta0)
-        K, Wm = args.steps, args.warmup
-        us = [[t.clone() for t in w.u] for _ in range(min(K + Wm, 6))]
-
-        def step(i, o):
-            u = us[i % len(us)]
-            for d in range(3):
-                u[d].copy_(w.u[d])
-            mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
-            return mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi, o)[1]
-        mx.mx_fill_base_state(ctx, g, 1, w.prof_beta0, w.prof_dr, w.center, beta0)
-        tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_MAC, g, *w.u, w.rho, beta0, w.sbar)
-        o = mx.default_opts(nu1=0, nu2=0)
-        for i in range(Wm):
-            step(i, o)
-        ms, infos = timed(lambda i: step(i, o), K, stream)
-        o64 = mx.default_opts(prec=mx.MX_PREC_FP64, nu1=tuned.nu1, nu2=tuned.nu2, tile_z=tuned.tile_z)
-        step(0, o64)
-        ms64, i64 = timed(lambda i: step(i, o64), 1, stream)
-        ok = mx.default_opts(nu1=0, nu2=0, krylov=1)
-        step(0, ok)
-        msk, ik = timed(lambda i: step(i, ok), K, stream)
-        print(json.dumps({"workload": "star512", "metric": "MAC projection solves/s to 1e-10 (full star 512^3, "
-                          "Dirichlet)", "value": K * 1e3 / ms, "unit": UNIT, "ms_per_solve": ms / K,
-                          "vcycles": infos[-1]["vcycles"], "rel_resid": infos[-1]["rel_resid"],
-                          "div_err_linf": infos[-1]["div_err_linf"],
-                          "fp64": {"solves_per_s": 1e3 / ms64, "vcycles": i64[-1]["vcycles"]},
-                          "fcg": {"solves_per_s": K * 1e3 / msk, "ms_per_solve": msk / K,
-                                  "vcycles": ik[-1]["vcycles"], "rel_resid": ik[-1]["rel_resid"]},
-                          "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z,
-                                    "fused": tuned.fused},
-                          "note": "includes a 3-array restore of U per solve"}), flush=True)
+        print(json.dumps(bench_star(mx, W, ctx, dev, stream, hbm=hbm, steps=args.steps, warmup=args.warmup)),
+              flush=True)
     mx.mx_destroy(ctx)
 
 

@@ -114,9 +114,19 @@ typedef struct {
     int status;               /* mx_status of the solve */
 } mx_info;
 
-/* Create a context on CUDA device `device`, enqueuing work on `cuda_stream`
- * (a cudaStream_t; NULL = the legacy default stream).  The context owns its
- * device workspace (multigrid hierarchy, reduction scratch, graphs). */
+/* Context calls (no counterpart in the paper: they hold the GPU state that the
+ * projections of Appendix A run on).
+ * mx_create: a context on CUDA device `device`, enqueuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream); *ctx receives it.  The
+ * context owns its device workspace (multigrid hierarchy, reduction scratch,
+ * graphs), allocated on first use per geometry and precision.  MX_ERR_ARG for a
+ * NULL ctx; MX_ERR_CUDA for a device that does not exist or cannot be used, or
+ * when the context's small fixed allocations fail.
+ * mx_destroy: synchronises the context's stream and frees everything it owns
+ * (never the caller's arrays); NULL is accepted.
+ * mx_set_stream: later calls enqueue on cuda_stream; cached CUDA graphs stay
+ * valid (graphs are launched on whatever stream is current).
+ * mx_last_error: one-line description of the last failure ("" if none). */
 mx_status mx_create(mx_ctx **ctx, int device, void *cuda_stream);
 mx_status mx_destroy(mx_ctx *ctx);
 mx_status mx_set_stream(mx_ctx *ctx, void *cuda_stream);
@@ -253,15 +263,24 @@ mx_status mx_nodal_project(mx_ctx *ctx, const mx_geom *geom, double *ux, double 
                            const double *rho, const double *beta0, const double *sbar,
                            double *phi_nodes, const mx_opts *opts, mx_info *info);
 
-/* Apply the operator L = div((beta0/rho) grad .) to phi (MAC: cells -> cells;
- * nodal: nodes -> nodes).  prec = MX_PREC_FP64 computes in FP64;
- * MX_PREC_MIXED rounds the coefficients and phi to FP32 and computes in FP32
- * (the arithmetic of the V-cycle), still writing doubles. */
+/* Apply the operator L = div((beta0/rho) grad .) of the projection's elliptic
+ * equation (Appendix A; the MAC form of Steps 3 and 7, Eq. div1/div2, and the
+ * nodal form of Step 11, Eq. div3) to phi (MAC: cells -> cells; nodal: nodes ->
+ * nodes), with the face coefficients and boundary closures of mx_mac_project /
+ * mx_nodal_project.  rho, beta0: cell arrays; phi, Lphi: device arrays in the
+ * layout of phi (Lphi written, never read).  prec = MX_PREC_FP64 computes in
+ * FP64; MX_PREC_MIXED rounds the coefficients and phi to FP32 and computes in
+ * FP32 (the arithmetic of the V-cycle), still writing doubles.  Work is queued
+ * on the context's stream (no synchronisation).  MX_ERR_ARG for an unknown op
+ * or prec, invalid geometry or a NULL array. */
 mx_status mx_apply_op(mx_ctx *ctx, const mx_geom *geom, int op, int prec, const double *rho,
                       const double *beta0, const double *phi, double *Lphi);
 
-/* r = f - L phi (device, same layout as phi) and, if rnorm_linf is not NULL,
- * its max norm to the host. */
+/* Residual of the projection's elliptic equation L phi = f (Appendix A; the
+ * convergence measure of the solves): r = f - L phi (device, same layout as
+ * phi; L as for mx_apply_op) and, if rnorm_linf is not NULL, its max norm to
+ * the host after the stream synchronises (NaN if r holds a NaN).  Errors as for
+ * mx_apply_op. */
 mx_status mx_residual(mx_ctx *ctx, const mx_geom *geom, int op, int prec, const double *rho,
                       const double *beta0, const double *phi, const double *f, double *r,
                       double *rnorm_linf);
@@ -288,11 +307,14 @@ mx_status mx_mac_project_batched(mx_ctx *ctx, int nbox, const mx_geom *geoms, do
  * cuda_stream (a cudaStream_t, NULL = legacy default stream) of the current
  * device; rnorm_linf (host, may be NULL) is written after the stream syncs.
  * Limit: at most 65536 tiles of 32 x 8 x 8 cells, i.e. ceil(n0/32) *
- * ceil(n1/8) * ceil(n2/8) <= 65536 (512^3 fits); larger grids return MX_ERR_ARG
- * before any work.  The first call on a device looks up the array's device
+ * ceil(n1/8) * ceil(n2/8) <= 65536 (512^3 fits), and ceil(n1/8), ceil(n2/8)
+ * <= 65535; larger grids return MX_ERR_ARG before any work.  The first call on a device looks up the array's device
  * address; make that first call before capturing a stream into a graph.  All
  * calls share the one array: calls that overlap on the GPU (other streams,
- * other threads) race and must be serialised by the caller. */
+ * other threads) race and must be serialised by the caller.  The first-call
+ * lookup itself is safe from several host threads.  The looked-up address
+ * belongs to the device's primary context: after cudaDeviceReset the library
+ * must be unloaded and loaded again.  The norm is NaN if r holds a NaN. */
 mx_status mx_residual_noalloc(const mx_geom *geom, const double *rho, const double *beta0, const double *phi,
                               const double *f, double *r, double *rnorm_linf, void *cuda_stream);
 
@@ -361,8 +383,9 @@ mx_status mx_autotune_batched(mx_ctx *ctx, int nbox, const mx_geom *geoms, const
  * and the normal quadratic 8/15 C~ + 2/3 F1 - 1/5 F2; coarse fluxes through
  * coarse-fine faces are the means of the four fine fluxes (flux matching); face
  * coefficients beta0_f / rho_f by arithmetic face means (of the fine cell and
- * the coarse cell across on a coarse-fine face).  FP64; both calls synchronise
- * the stream before returning. */
+ * the coarse cell across on a coarse-fine face).  FP64; both calls queue their
+ * work on the context's stream and return without synchronising (the outputs
+ * are ready in stream order, as for mx_apply_op). */
 
 /* out = L phi on the uncovered coarse cells (0 on covered ones) and the fine cells */
 mx_status mx_composite_apply(mx_ctx *ctx, const mx_geom *geom, const int plo[3], const int phi[3],
@@ -377,6 +400,16 @@ mx_status mx_composite_divergence(mx_ctx *ctx, const mx_geom *geom, const int pl
                                   const double *ux_c, const double *uy_c, const double *uz_c, const double *ux_f,
                                   const double *uy_f, const double *uz_f, const double *beta0_c,
                                   const double *beta0_f, double *out_c, double *out_f);
+
+/* Measurement helper (no counterpart in the paper): the FMA rate of the
+ * device's FP64 (fp64 = 1) or FP32 (fp64 = 0) pipe in TFLOP/s (2 flops per
+ * FMA), the best of three CUDA-event-timed launches of independent FMA chains
+ * on every SM (after one warm-up launch).  It is the arithmetic bound beside the
+ * HBM bound for the plain FP64 solve.  Runs on the legacy default stream of
+ * `device` (made current), allocates and frees a small device buffer and
+ * synchronises; *tflops is written on MX_OK.  MX_ERR_ARG for a NULL tflops,
+ * MX_ERR_CUDA if the device cannot run it. */
+mx_status mx_probe_fma_peak(int device, int fp64, double *tflops);
 
 /* Look up the tune cache: 1 and *out = the stored setting (base fields from
  * *out as passed) if mx_autotune stored one for (op, prec, geometry), else 0. */

@@ -100,6 +100,7 @@ def load():
         "mx_composite_divergence": (C.c_int, [_VP, G, _IP3, _IP3] + [_DP] * 10),
         "mx_mac_project_split": (C.c_int, [_VP, G, C.c_int, _IP3, _DP, _DP, _DP, _DP, _DP, _DP, C.c_int, _DP, _DP,
                                            _DP, O, I]),
+        "mx_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -117,7 +118,7 @@ def exported_symbols():
             "mx_autotune", "mx_tune_lookup", "mx_autotune_batched", "mx_radial_nbins", "mx_average_planar",
             "mx_average_radial", "mx_fill_radial", "mx_radial_to_uniform", "mx_fill_uniform", "mx_w0_integrate",
             "mx_add_w0_faces", "mx_subtract_lateral_average", "mx_mac_project_split", "mx_composite_apply",
-            "mx_composite_divergence"]
+            "mx_composite_divergence", "mx_probe_fma_peak"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -474,3 +475,12 @@ def mx_residual_noalloc(geom, rho, beta0, phi, f, r, stream=None):
     if st != MX_OK:
         raise MXError(st, "mx_residual_noalloc failed")
     return rn.value
+
+
+def mx_probe_fma_peak(device: int = 0, fp64: bool = True) -> float:
+    """Measured FMA rate of the FP64 (or FP32) pipe in TFLOP/s (see include/mx.h)."""
+    t = C.c_double(0.0)
+    st = load().mx_probe_fma_peak(int(device), int(bool(fp64)), C.byref(t))
+    if st != MX_OK:
+        raise MXError(st, "mx_probe_fma_peak failed")
+    return t.value

@@ -287,7 +287,6 @@ extern "C" mx_status mx_composite_apply(mx_ctx *c, const mx_geom *geom, const in
     comp_apply_fine_kernel<<<red_blocks(Nf), 256, 0, c->stream>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f,
                                                                    out_f);
     MX_CUDA(c, cudaGetLastError());
-    MX_CUDA(c, cudaStreamSynchronize(c->stream));
     return MX_OK;
 }
 
@@ -307,6 +306,5 @@ extern "C" mx_status mx_composite_divergence(mx_ctx *c, const mx_geom *geom, con
                                                                    beta0_f, out_c);
     comp_div_fine_kernel<<<red_blocks(Nf), 256, 0, c->stream>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, out_f);
     MX_CUDA(c, cudaGetLastError());
-    MX_CUDA(c, cudaStreamSynchronize(c->stream));
     return MX_OK;
 }

@@ -485,7 +485,7 @@ __device__ __forceinline__ void df_resid_body(const Level<float> &L, const DFArr
         const float R = Rh + Re;
         const float rh = R * c_hat;  // r / scale: O(1), so its FP32 norms neither over- nor underflow
         L.f[c] = rh;
-        mx = fmaxf(mx, fabsf(rh));
+        mx = nmaxf(mx, fabsf(rh));
         s2f = fmaf(rh, rh, s2f);
         s1f += rh;
     }

@@ -112,10 +112,11 @@ __device__ __forceinline__ dfloat df_div(dfloat a, dfloat b) {
     return df_norm(q1, r / b.h);
 }
 
-// m = the larger of m and |v| (by hi, then lo), both double-float
+// m = the larger of m and |v| (by hi, then lo), both double-float; NaN propagates
 __device__ __forceinline__ void df_absmax(dfloat &m, dfloat v) {
     const bool neg = v.h < 0.f || (v.h == 0.f && v.l < 0.f);
     const dfloat a = neg ? dfloat{-v.h, -v.l} : v;
-    const bool gt = a.h > m.h || (a.h == m.h && a.l > m.l);
+    // a NaN value wins and then stays (every comparison with it is false)
+    const bool gt = a.h > m.h || (a.h == m.h && a.l > m.l) || a.h != a.h;
     m = gt ? a : m;
 }

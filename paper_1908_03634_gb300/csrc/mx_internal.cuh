@@ -74,6 +74,16 @@ __device__ __forceinline__ void set_scale(SolveState *st, double sc) {
     st->upd_l = st->scale_l;
 }
 
+// Maxima that propagate NaN.  fmax/fmaxf return the other operand when one is
+// NaN, so a norm built from them would report a finite value for a residual
+// holding NaN; every norm and its block and grid reductions use these instead.
+__device__ __forceinline__ double nmax(double a, double b) { return (a > b || a != a) ? a : b; }
+__device__ __forceinline__ float nmaxf(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 struct MacPlan;
 struct NodalPlan;
 struct BatchPlan;

@@ -160,7 +160,7 @@ __global__ void mac_rhs_kernel(DGeom g, const double *__restrict__ ux, const dou
     if (i < g.n[0] && j < g.n[1])
         div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, double v) {
             f[c] = v;
-            mx = fmax(mx, fabs(v));
+            mx = nmax(mx, fabs(v));
             s2 = fma(v, v, s2);
             s1 += v;
         });
@@ -214,7 +214,7 @@ __global__ void sub_mean_norm_kernel(double *f, long long n, const SolveState *s
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const double v = f[q] - m;
         f[q] = v;
-        mx = fmax(mx, fabs(v));
+        mx = nmax(mx, fabs(v));
         s2 += v * v;
         s1 += v;
     }
@@ -296,7 +296,7 @@ __global__ void mac_divcheck_kernel(DGeom g, const double *__restrict__ ux, cons
     double mx = 0.0, s2 = 0.0, s1 = 0.0;
     if (i < g.n[0] && j < g.n[1])
         div_column(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
-                   [&](long long, double v) { mx = fmax(mx, fabs(v - cm)); });
+                   [&](long long, double v) { mx = nmax(mx, fabs(v - cm)); });
     block_red3(mx, s2, s1);
     if (flat_tid() == 0) {
         double *p = part + 3 * flat_bid();

@@ -80,7 +80,7 @@ __global__ void residual64_kernel(Level<double> L, const double *__restrict__ ph
             nb_vals(g, phi, i, j, k, c, v);
             const double r = f[c] - flux_sum(b, v, phi[c]) * ih2;
             rhat[c] = T(r * inv);
-            mx = fmax(mx, fabs(r));
+            mx = nmax(mx, fabs(r));
             s2 += r * r;
             s1 += r;
         }
@@ -498,7 +498,7 @@ __global__ void sum_partials_kernel(const double *x, long long n, double *part) 
     double s = 0.0, m = 0.0, z = 0.0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         s += x[q];
-        m = fmax(m, fabs(x[q]));
+        m = nmax(m, fabs(x[q]));
     }
     block_red3(m, s, z);
     if (threadIdx.x == 0) {
@@ -549,7 +549,7 @@ __global__ void residual_plain_kernel(Level<double> L, const double *__restrict_
             nb_vals(g, phi, i, j, k, c, v);
             const double rr = f[c] - flux_sum(b, v, phi[c]) * ih2;
             r[c] = rr;
-            mx = fmax(mx, fabs(rr));
+            mx = nmax(mx, fabs(rr));
             s2 += rr * rr;
             s1 += rr;
         }

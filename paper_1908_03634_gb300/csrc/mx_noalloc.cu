@@ -5,7 +5,9 @@
 // computed on the fly from rho and beta0, and the per-block partial maxima
 // live in a file-scope device array of fixed size that every GPU loading the
 // library holds until the process exits.
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "mx_stencil.cuh"
 
@@ -56,7 +58,7 @@ __global__ void na_residual_kernel(DGeom g, const double *__restrict__ rho, cons
             nb_vals(g, phi, i, j, k, c, v);
             const double rr = f[c] - flux_sum(b, v, phi[c]) * ih2;
             r[c] = rr;
-            mx = fmax(mx, fabs(rr));
+            mx = nmax(mx, fabs(rr));
         }
     }
     block_red3(mx, s2, s1);
@@ -65,14 +67,32 @@ __global__ void na_residual_kernel(DGeom g, const double *__restrict__ rho, cons
 
 __global__ void na_reduce_kernel(double *part, int nb) {
     double mx = 0.0, s2 = 0.0, s1 = 0.0;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) mx = fmax(mx, part[q]);
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) mx = nmax(mx, part[q]);
     block_red3(mx, s2, s1);
     if (threadIdx.x == 0) part[NA_MAX_TILES] = mx;
 }
 
-// Device address of the scratch array, looked up once per device.
-static double *na_ptr[64];
-static bool na_ready[64];
+// Device address of the scratch array, looked up once per device (under a lock,
+// so that threads making their first call at the same time do not race).  The
+// address belongs to the device's primary context: a cudaDeviceReset discards
+// it, and this library must then be unloaded and loaded again.
+static std::atomic<double *> na_ptr[64];
+static std::mutex na_mu;
+
+static double *na_scratch_addr(int dev) {
+    double *p = na_ptr[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    std::lock_guard<std::mutex> lock(na_mu);
+    p = na_ptr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+        if (cudaGetSymbolAddress((void **)&p, na_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        na_ptr[dev].store(p, std::memory_order_release);
+    }
+    return p;
+}
 
 extern "C" mx_status mx_residual_noalloc(const mx_geom *geom, const double *rho, const double *beta0,
                                          const double *phi, const double *f, double *r, double *rnorm_linf,
@@ -82,18 +102,12 @@ extern "C" mx_status mx_residual_noalloc(const mx_geom *geom, const double *rho,
     const DGeom g = make_dgeom(geom);
     const dim3 grid = stencil_grid(g);
     const long long nb = (long long)grid.x * grid.y * grid.z;
-    if (nb > NA_MAX_TILES) return MX_ERR_ARG;  // more tiles than the fixed scratch holds
+    // more tiles than the fixed scratch holds, or a grid beyond the launch limits
+    if (nb > NA_MAX_TILES || grid.y > 65535 || grid.z > 65535) return MX_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MX_ERR_CUDA;
-    if (!na_ready[dev]) {
-        // first call on this device: resolve the array's device address
-        if (cudaGetSymbolAddress((void **)&na_ptr[dev], na_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return MX_ERR_CUDA;
-        }
-        na_ready[dev] = true;
-    }
-    double *part = na_ptr[dev];
+    double *part = na_scratch_addr(dev);  // the first call on a device looks it up
+    if (!part) return MX_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     na_residual_kernel<<<grid, dim3(SX, SY), 0, s>>>(g, rho, beta0, phi, f, r, part, 1.0 / (g.h * g.h));
     na_reduce_kernel<<<1, 1024, 0, s>>>(part, int(nb));

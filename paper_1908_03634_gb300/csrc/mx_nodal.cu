@@ -259,7 +259,7 @@ __global__ void nd_rhs_col_kernel(NGeom g, const double *__restrict__ ux, const 
             const double v = div * (8.0 * i4h * ic) - (lo.s + hi.s) * ic - cm;
             const double w = 0.125 * cnt;
             if (f) f[a + g.m[0] * (b + g.m[1] * c)] = v;
-            mx = fmax(mx, fabs(v));
+            mx = nmax(mx, fabs(v));
             s1 = fma(w, v, s1);
             s0 += w;
             lo = hi;
@@ -318,7 +318,7 @@ __global__ void nd_rhs_final_kernel(NGeom g, double *__restrict__ f, const Solve
             fh[q] = hi;
             fl[q] = __double2float_rn(sv - double(hi));
         }
-        mx = fmax(mx, fabs(v));
+        mx = nmax(mx, fabs(v));
         s2 += v * v;
         s1 += v;
     }
@@ -769,7 +769,7 @@ __global__ void nd_df_col_resid_kernel(NLevel<float> L0, NDF D, const SolveState
             const float w = wxy * ((!g.per[2] && (c == 0 || c == g.m[2] - 1)) ? 0.5f : 1.f);
             const float rh = R * (ih2 / (12.f * w)) * inv;
             L0.f[q] = rh;
-            mx = fmaxf(mx, fabsf(rh));
+            mx = nmaxf(mx, fabsf(rh));
             s2 = fmaf(rh, rh, s2);
             s1 += rh;
             for (int y = 0; y < 3; y++)
@@ -836,7 +836,7 @@ __global__ void nd_col_resid64_kernel(NLevel<double> L, const double *__restrict
             const double r = f[q] - num / (12.0 * w * g.h * g.h);
             if (rout) rout[q] = r;
             if (rhat) rhat[q] = r * inv;
-            mx = fmax(mx, fabs(r));
+            mx = nmax(mx, fabs(r));
             s2 += r * r;
             s1 += r;
             for (int y = 0; y < 3; y++)
@@ -879,7 +879,7 @@ __global__ void nd_resid32_kernel(const double *__restrict__ f, const float *__r
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
         const double v = double(float(f[q]) - lphi[q]);
         r[q] = v;
-        mx = fmax(mx, fabs(v));
+        mx = nmax(mx, fabs(v));
     }
     block_red3(mx, s2, s1);
     if (threadIdx.x == 0) {

@@ -593,7 +593,7 @@ __global__ void resid_combine_kernel(const double *f, const float *lphi, double 
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const float v = float(f[q]) - lphi[q];
         r[q] = double(v);
-        mx = fmax(mx, fabs(double(v)));
+        mx = nmax(mx, fabs(double(v)));
         s2 += double(v) * double(v);
         s1 += double(v);
     }

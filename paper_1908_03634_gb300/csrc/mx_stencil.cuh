@@ -72,7 +72,7 @@ __device__ __forceinline__ void block_red3(double &a, double &b, double &c) {
     const int t = flat_tid();
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
     for (int o = 16; o > 0; o >>= 1) {
-        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        a = nmax(a, __shfl_xor_sync(0xffffffffu, a, o));
         b += __shfl_xor_sync(0xffffffffu, b, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
     }
@@ -89,7 +89,7 @@ __device__ __forceinline__ void block_red3(double &a, double &b, double &c) {
         b = lane < nw ? sh[32 + lane] : 0.0;
         c = lane < nw ? sh[64 + lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) {
-            a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+            a = nmax(a, __shfl_xor_sync(0xffffffffu, a, o));
             b += __shfl_xor_sync(0xffffffffu, b, o);
             c += __shfl_xor_sync(0xffffffffu, c, o);
         }
@@ -105,7 +105,7 @@ __device__ __forceinline__ void block_red3f(float &a, float &b, float &c) {
     const int t = flat_tid();
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
     for (int o = 16; o > 0; o >>= 1) {
-        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        a = nmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
         b += __shfl_xor_sync(0xffffffffu, b, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
     }
@@ -122,7 +122,7 @@ __device__ __forceinline__ void block_red3f(float &a, float &b, float &c) {
         b = lane < nw ? shf[32 + lane] : 0.f;
         c = lane < nw ? shf[64 + lane] : 0.f;
         for (int o = 16; o > 0; o >>= 1) {
-            a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            a = nmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
             b += __shfl_xor_sync(0xffffffffu, b, o);
             c += __shfl_xor_sync(0xffffffffu, c, o);
         }
@@ -136,7 +136,7 @@ __device__ __forceinline__ void reduce_partials3(const double *p, int nb, double
     b = 0.0;
     c = 0.0;
     for (int q = flat_tid(); q < nb; q += blockDim.x * blockDim.y * blockDim.z) {
-        a = fmax(a, p[3 * q]);
+        a = nmax(a, p[3 * q]);
         b += p[3 * q + 1];
         c += p[3 * q + 2];
     }
