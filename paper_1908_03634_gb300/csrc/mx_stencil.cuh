@@ -155,7 +155,7 @@ inline dim3 stencil_grid(const DGeom &g) {
 // long-running blocks.
 inline int zchunk(long long bxy, int nz, int cap = ZC) {
     int zc = cap;
-    while (zc > 1 && bxy * ((nz + zc - 1) / zc) < 4 * 152) zc >>= 1;
+    while (zc > 1 && bxy * ((nz + zc - 1) / zc) < 16 * 152) zc >>= 1;
     return zc;
 }
 inline dim3 stencil_grid_zc(const DGeom &g, int zc) {
