@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the nodal and batched workloads")
     p.add_argument("--workload", default="planar256",
-                   choices=["planar256", "star512", "nodal-sweep", "nodal384", "batched96", "average512"],
+                   choices=["planar256", "star512", "nodal-sweep", "nodal384", "batched96", "average512",
+                            "composite"],
                    help="planar256: the headline line (+ nodal384 and batched96 extras); star512: the "
                         "full-star line; nodal-sweep: one line per nodal size 64^3..512^3; nodal384 / "
                         "batched96 / average512: that extra alone (for profiling)")
@@ -474,6 +475,7 @@ def run_mx(args):
         extras["star512"] = bench_star(mx, W, ctx, dev, stream, hbm=hbm)
         extras["planar32_fp64"] = bench_planar32_fp64(mx, W, ctx, dev, stream)
         extras["nodal_sweep"] = bench_nodal_sweep(mx, W, ctx, dev, stream, hbm)
+        extras["composite"] = bench_composite(mx, W, ctx, dev, stream, hbm=hbm)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
@@ -880,6 +882,59 @@ def bench_star(mx, W, ctx, dev, stream, hbm=6793.4, steps=10, warmup=3, n=512):
     return out
 
 
+def composite_iteration_bytes(nc, nf, nu1, nu2):
+    """Algorithmic bytes of one refinement iteration of the composite projection
+    (coarse level of nc cells, patch of nf cells): the FP64 composite residual
+    (phi, rho, beta0, f read, r written: 40 B per cell; on the patch twice, before
+    and after the coarse correction), the FP32 right-hand sides (r read, rhat
+    written: 12 B per cell, and the fine residual read once more for the covered
+    coarse cells: 8 B per fine cell), one V-cycle of each grid (the single-level
+    model: 8/7 x 4 x (6 (nu1 + nu2) + 7.25) B per cell) and the FP64 updates (phi
+    read and written, e read: 20 B per cell; the patch takes two)."""
+    v = (8.0 / 7.0) * 4 * (6.0 * (nu1 + nu2) + 7.25)
+    return nc * (40 + 12 + v + 20) + nf * (2 * 40 + 8 + 12 + v + 2 * 20)
+
+
+def bench_composite(mx, W, ctx, dev, stream, hbm=6793.4, n=128, steps=5, warmup=2):
+    """The two-level composite MAC projection on the planar workload with a
+    ratio-2 patch over the middle half of the box (coarse n^3, patch n^3 fine
+    cells): solves/s, refinement iterations and the HBM fraction per iteration."""
+    import torch
+    q = n // 4
+    w = W.composite_planar(n, (q, q, q), (3 * q, 3 * q, 3 * q), W.H_1E5, 0.6, 16, 3, 1, device=dev)
+    g = w.geom
+    pc = torch.zeros_like(w.rho_c)
+    pf = torch.zeros_like(w.rho_f)
+    uc = [t.clone() for t in w.u_c]
+    uf = [t.clone() for t in w.u_f]
+    o = mx.default_opts()
+
+    def step(i):
+        for d in range(3):
+            uc[d].copy_(w.u_c[d])
+            uf[d].copy_(w.u_f[d])
+        return mx.mx_mac_project_composite(ctx, g, w.plo, w.phi, uc, w.rho_c, w.beta0_c, w.sbar_c, pc, uf, w.rho_f,
+                                           w.beta0_f, w.sbar_f, pf, o)[1]
+    for i in range(warmup):
+        step(i)
+    ms, infos = timed(step, steps, stream)
+    last = infos[-1]
+    nc, nf = g.ncell, pf.numel()
+    ms_s = ms / steps
+    it = max(last["outer_iters"], 1)
+    b = composite_iteration_bytes(nc, nf, 2, 2)
+    out = {"workload": f"composite_planar{n}", "coarse_cells": nc, "fine_cells": nf, "patch": [w.plo, w.phi],
+           "solves_per_s": 1e3 / ms_s, "ms_per_solve": ms_s, "iterations": last["outer_iters"],
+           "vcycles": last["vcycles"], "rel_resid": last["rel_resid"],
+           "div_err_rel": last["div_err_linf"] / max(last["rhs_linf"], 1e-300),
+           "model_bytes_per_iteration": b, "ms_per_iteration": ms_s / it,
+           "hbm_frac_per_iteration": round(b / (ms_s / it * 1e-3) / 1e9 / hbm, 4),
+           "note": "each solve includes the restore of U on both levels; the call allocates its workspace"}
+    del w, uc, uf, pc, pf
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_planar32_fp64(mx, W, ctx, dev, stream, steps=20, warmup=3):
     """The 32^3 planar smoke configuration (H = 0.1, beta0 = rho0): plain FP64
     projection to 1e-10, solves/s (launch-latency bound at this size)."""
@@ -958,6 +1013,9 @@ def run_other(args):
                           fixed=args.fixed)
         if rank == 0:
             print(json.dumps(r), flush=True)
+    elif args.workload == "composite":
+        print(json.dumps(bench_composite(mx, W, ctx, dev, stream, hbm=hbm, n=args.n if args.n != N else 128,
+                                         steps=args.steps, warmup=args.warmup)), flush=True)
     elif args.workload == "nodal-sweep":
         for r in bench_nodal_sweep(mx, W, ctx, dev, stream, hbm):
             print(json.dumps(r), flush=True)

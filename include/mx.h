@@ -411,6 +411,35 @@ mx_status mx_composite_divergence(mx_ctx *ctx, const mx_geom *geom, const int pl
  * MX_ERR_CUDA if the device cannot run it. */
 mx_status mx_probe_fma_peak(int device, int fp64, double *tflops);
 
+/* Composite (two-level, ratio 2) MAC projection (Steps 3 and 7, Eq. div1/div2,
+ * Appendix A, on the AMR levels of the end of Sec. 3.2): the projection of the
+ * coarse level and one fine patch together, with the composite operator and
+ * divergence of mx_composite_apply / mx_composite_divergence (ghost values,
+ * flux matching at the coarse-fine faces).  Solves L phi = f, f = D(beta0 U) -
+ * beta0 Sbar on the uncovered coarse cells and the fine cells, the
+ * volume-weighted mean removed when no face is Dirichlet, to ||f - L phi||_inf
+ * <= rel_tol ||f||_inf (FP64 composite residual); then U -= grad(phi)/rho_f on
+ * both levels (the fine coarse-fine faces with the ghost value), the coarse
+ * faces on and inside the patch take the mean of the four fine faces on them,
+ * and the covered coarse phi the mean of its eight fine cells.  phi has zero
+ * volume-weighted mean over the uncovered coarse and the fine cells on singular
+ * problems.
+ * Arguments: geom, plo, phi as for mx_composite_apply (phi[3] is the patch's
+ * high corner, phi_c / phi_f the potentials); coarse arrays cover the whole
+ * coarse grid (U faces in/out, rho, beta0, sbar in; rho and beta0 on covered
+ * cells are not read), fine arrays cover the patch; all device pointers.
+ * opts: prec must be MX_PREC_MIXED (FP32 V-cycles as the corrections inside the
+ * FP64 refinement) and krylov 0 (else MX_ERR_ARG); nu1 = nu2 = 0 means 2, 2;
+ * max_outer / max_vcycles cap the refinement iterations (each runs one V-cycle
+ * of the coarse grid and one of the patch; info->vcycles counts both).
+ * Allocates its workspace (two multigrid plans and six FP64 scratch fields) for
+ * the call and frees it before returning; synchronises the stream. */
+mx_status mx_mac_project_composite(mx_ctx *ctx, const mx_geom *geom, const int plo[3], const int phi[3],
+                                   double *ux_c, double *uy_c, double *uz_c, const double *rho_c,
+                                   const double *beta0_c, const double *sbar_c, double *phi_c, double *ux_f,
+                                   double *uy_f, double *uz_f, const double *rho_f, const double *beta0_f,
+                                   const double *sbar_f, double *phi_f, const mx_opts *opts, mx_info *info);
+
 /* Look up the tune cache: 1 and *out = the stored setting (base fields from
  * *out as passed) if mx_autotune stored one for (op, prec, geometry), else 0. */
 int mx_tune_lookup(const mx_ctx *ctx, int op, int prec, const mx_geom *geom, mx_opts *out);

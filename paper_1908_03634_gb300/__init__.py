@@ -101,6 +101,7 @@ def load():
         "mx_mac_project_split": (C.c_int, [_VP, G, C.c_int, _IP3, _DP, _DP, _DP, _DP, _DP, _DP, C.c_int, _DP, _DP,
                                            _DP, O, I]),
         "mx_probe_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+        "mx_mac_project_composite": (C.c_int, [_VP, G, _IP3, _IP3] + [_DP] * 14 + [O, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -118,7 +119,7 @@ def exported_symbols():
             "mx_autotune", "mx_tune_lookup", "mx_autotune_batched", "mx_radial_nbins", "mx_average_planar",
             "mx_average_radial", "mx_fill_radial", "mx_radial_to_uniform", "mx_fill_uniform", "mx_w0_integrate",
             "mx_add_w0_faces", "mx_subtract_lateral_average", "mx_mac_project_split", "mx_composite_apply",
-            "mx_composite_divergence", "mx_probe_fma_peak"]
+            "mx_composite_divergence", "mx_probe_fma_peak", "mx_mac_project_composite"]
 
 
 # --- marshalling helpers ---------------------------------------------------------------
@@ -322,6 +323,24 @@ def mx_composite_divergence(ctx, geom, plo, phi, uc, uf, beta0_c, beta0_f, out_c
         *[_ptr(uc[d], face_shape(geom, d), "uc") for d in range(3)], *[_ptr(uf[d], ffs[d], "uf") for d in range(3)],
         _ptr(beta0_c, cs, "beta0_c"), _ptr(beta0_f, fs, "beta0_f"), _ptr(out_c, cs, "out_c"), _ptr(out_f, fs, "out_f"))
     return _check(ctx, st)
+
+
+def mx_mac_project_composite(ctx, geom, plo, phi, uc, rho_c, beta0_c, sbar_c, phi_c, uf, rho_f, beta0_f, sbar_f,
+                             phi_f, opts=None, allow=(MX_OK,)):
+    """Composite (coarse + one ratio-2 patch [plo, phi)) MAC projection; uc, uf:
+    lists of the three coarse / fine face arrays (in/out).  Returns (status, info)."""
+    cs = cell_shape(geom)
+    fs, ffs = _fine_shapes(geom, plo, phi)
+    info = mx_info()
+    st = load().mx_mac_project_composite(
+        ctx, C.byref(make_geom(geom)), _corner(plo), _corner(phi),
+        *[_ptr(uc[d], face_shape(geom, d), "uc") for d in range(3)], _ptr(rho_c, cs, "rho_c"),
+        _ptr(beta0_c, cs, "beta0_c"), _ptr(sbar_c, cs, "sbar_c"), _ptr(phi_c, cs, "phi_c"),
+        *[_ptr(uf[d], ffs[d], "uf") for d in range(3)], _ptr(rho_f, fs, "rho_f"), _ptr(beta0_f, fs, "beta0_f"),
+        _ptr(sbar_f, fs, "sbar_f"), _ptr(phi_f, fs, "phi_f"), C.byref(opts) if opts is not None else None,
+        C.byref(info))
+    _check(ctx, st, allow)
+    return st, info.as_dict()
 
 
 def mx_mac_project_split(ctx, geom, spherical, corner, ux, uy, uz, rho, beta0, S, r_edge, w0, phi, opts=None,

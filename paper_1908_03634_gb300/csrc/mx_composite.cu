@@ -16,12 +16,18 @@
 //     fine cell and the coarse cell across on a coarse-fine face; the domain
 //     faces as on one level (wall: no flux; Dirichlet phi = 0: (0 - phi)/(H/2)).
 //
-// FP64, one thread per cell: the operator and divergence of a composite
-// solve, checked element by element against the oracle; the composite solver
-// itself is not built on them yet.
+// FP64, one thread per cell: the operator and divergence, and on them the
+// composite projection (mx_mac_project_composite): refinement on the composite
+// residual with a two-level correction per iteration (a V-cycle of the whole
+// coarse grid, then a V-cycle of the patch).
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "mx_internal.cuh"
+#include "mx_solver.cuh"
 #include "mx_stencil.cuh"
 
 namespace {
@@ -69,10 +75,14 @@ __device__ double ghost(const CompGeom &G, const double *__restrict__ pc, const 
     return (8.0 / 15.0) * ct + (2.0 / 3.0) * pf[fix_(G, F[0], F[1], F[2])] - 0.2 * pf[fix_(G, F2[0], F2[1], F2[2])];
 }
 
+// out = L phi on the uncovered coarse cells (0 on covered ones), or with f
+// non-null the residual f - L phi and per-block maxima of its magnitude in part
 __global__ void comp_apply_coarse_kernel(CompGeom G, const double *__restrict__ rc, const double *__restrict__ bc,
                                          const double *__restrict__ rf, const double *__restrict__ bf,
                                          const double *__restrict__ pc, const double *__restrict__ pf,
-                                         double *__restrict__ out) {
+                                         double *__restrict__ out, const double *__restrict__ f = nullptr,
+                                         double *part = nullptr) {
+    double rmax = 0.0;
     const long long N = (long long)G.n[0] * G.n[1] * G.n[2];
     const double iH2 = 1.0 / (G.H * G.H), ihH = 1.0 / (G.h * G.H);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
@@ -118,14 +128,25 @@ __global__ void comp_apply_coarse_kernel(CompGeom G, const double *__restrict__ 
                 acc += 0.25 * m * ihH;
             }
         }
+        if (f) {
+            acc = f[q] - acc;
+            rmax = nmax(rmax, fabs(acc));
+        }
         out[q] = acc;
+    }
+    if (part) {
+        double z1 = 0.0, z2 = 0.0;
+        block_red3(rmax, z1, z2);
+        if (threadIdx.x == 0) part[3 * blockIdx.x] = rmax;
     }
 }
 
 __global__ void comp_apply_fine_kernel(CompGeom G, const double *__restrict__ rc, const double *__restrict__ bc,
                                        const double *__restrict__ rf, const double *__restrict__ bf,
                                        const double *__restrict__ pc, const double *__restrict__ pf,
-                                       double *__restrict__ out) {
+                                       double *__restrict__ out, const double *__restrict__ f = nullptr,
+                                       double *part = nullptr) {
+    double rmax = 0.0;
     const long long N = (long long)G.nf[0] * G.nf[1] * G.nf[2];
     const double ih2 = 1.0 / (G.h * G.h);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
@@ -147,7 +168,16 @@ __global__ void comp_apply_fine_kernel(CompGeom G, const double *__restrict__ rc
                 }
             }
         }
+        if (f) {
+            acc = f[q] - acc;
+            rmax = nmax(rmax, fabs(acc));
+        }
         out[q] = acc;
+    }
+    if (part) {
+        double z1 = 0.0, z2 = 0.0;
+        block_red3(rmax, z1, z2);
+        if (threadIdx.x == 0) part[3 * blockIdx.x] = rmax;
     }
 }
 
@@ -248,6 +278,382 @@ __global__ void comp_div_fine_kernel(CompGeom G, const double *__restrict__ fx, 
     }
 }
 
+// ---- composite projection ---------------------------------------------------------------
+// grid-stride launch shape of the per-cell kernels below
+inline int gs_blocks(long long n) { return red_blocks(n); }
+
+__device__ __forceinline__ void coarse_ijk(const CompGeom &G, long long q, int c[3]) {
+    c[0] = int(q % G.n[0]);
+    c[1] = int((q / G.n[0]) % G.n[1]);
+    c[2] = int(q / ((long long)G.n[0] * G.n[1]));
+}
+__device__ __forceinline__ void fine_ijk(const CompGeom &G, long long q, int F[3]) {
+    F[0] = int(q % G.nf[0]);
+    F[1] = int((q / G.nf[0]) % G.nf[1]);
+    F[2] = int(q / ((long long)G.nf[0] * G.nf[1]));
+}
+// the fine cell (patch-local) of child (a, b, e) of covered coarse cell c
+__device__ __forceinline__ long long child(const CompGeom &G, const int c[3], int a, int b, int e) {
+    return fix_(G, 2 * (c[0] - G.plo[0]) + a, 2 * (c[1] - G.plo[1]) + b, 2 * (c[2] - G.plo[2]) + e);
+}
+__device__ __forceinline__ double mean8(const CompGeom &G, const double *__restrict__ xf, const int c[3]) {
+    double s = 0.0;
+    for (int e = 0; e < 2; e++)
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) s += xf[child(G, c, a, b, e)];
+    return 0.125 * s;
+}
+
+// f = D(beta0 U) - beta0 Sbar on the uncovered coarse cells (0 on covered ones)
+// and the fine cells, in place over the divergence; partials (max |f|,
+// volume-weighted sum of f, volume) per block, the coarse level's blocks first
+__global__ void comp_rhs_kernel(CompGeom G, double *__restrict__ fc, double *__restrict__ ff,
+                                const double *__restrict__ bc, const double *__restrict__ sc,
+                                const double *__restrict__ bf, const double *__restrict__ sf, double *part,
+                                int nbc) {
+    const bool fine = blockIdx.x >= nbc;
+    const long long N = fine ? (long long)G.nf[0] * G.nf[1] * G.nf[2] : (long long)G.n[0] * G.n[1] * G.n[2];
+    const int b0 = fine ? blockIdx.x - nbc : blockIdx.x, nb = fine ? gridDim.x - nbc : nbc;
+    const double vol = fine ? G.h * G.h * G.h : G.H * G.H * G.H;
+    double mx = 0.0, sum = 0.0, v = 0.0;
+    for (long long q = b0 * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)nb * blockDim.x) {
+        if (fine) {
+            const double x = ff[q] - bf[q] * sf[q];
+            ff[q] = x;
+            mx = nmax(mx, fabs(x));
+            sum += vol * x;
+            v += vol;
+        } else {
+            int c[3];
+            coarse_ijk(G, q, c);
+            if (in_patch(G, c)) {
+                fc[q] = 0.0;
+                continue;
+            }
+            const double x = fc[q] - bc[q] * sc[q];
+            fc[q] = x;
+            mx = nmax(mx, fabs(x));
+            sum += vol * x;
+            v += vol;
+        }
+    }
+    block_red3(mx, sum, v);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = mx;
+        part[3 * blockIdx.x + 1] = sum;
+        part[3 * blockIdx.x + 2] = v;
+    }
+}
+
+// one block: st->mean = volume-weighted mean (when singular and asked), st->fnorm = max |f|
+__global__ void comp_rhs_final_kernel(const double *part, int nb, SolveState *st, int remove_mean) {
+    double a, b, c;
+    reduce_partials3(part, nb, a, b, c);
+    if (threadIdx.x == 0) {
+        st->mean = remove_mean ? b / c : 0.0;
+        st->fnorm = a;
+        st->aux = b / c;
+    }
+}
+
+// f -= mean on the uncovered coarse and the fine cells; partials of max |f|
+__global__ void comp_sub_mean_kernel(CompGeom G, double *__restrict__ fc, double *__restrict__ ff,
+                                     const SolveState *st, double *part, int nbc) {
+    const bool fine = blockIdx.x >= nbc;
+    const long long N = fine ? (long long)G.nf[0] * G.nf[1] * G.nf[2] : (long long)G.n[0] * G.n[1] * G.n[2];
+    const int b0 = fine ? blockIdx.x - nbc : blockIdx.x, nb = fine ? gridDim.x - nbc : nbc;
+    const double m = st->mean;
+    double mx = 0.0, z1 = 0.0, z2 = 0.0;
+    for (long long q = b0 * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)nb * blockDim.x) {
+        double *x = fine ? ff : fc;
+        if (!fine) {
+            int c[3];
+            coarse_ijk(G, q, c);
+            if (in_patch(G, c)) continue;
+        }
+        x[q] -= m;
+        mx = nmax(mx, fabs(x[q]));
+    }
+    block_red3(mx, z1, z2);
+    if (threadIdx.x == 0) part[3 * blockIdx.x] = mx;
+}
+
+// one block: convergence decision from the partial maxima of the residual
+__global__ void comp_decide_kernel(const double *part, int nb, SolveState *st) {
+    double mx = 0.0, z1 = 0.0, z2 = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) mx = nmax(mx, part[3 * q]);
+    block_red3(mx, z1, z2);
+    if (threadIdx.x == 0) {
+        st->rnorm = mx;
+        const bool conv = mx <= st->tol * st->fnorm;
+        if (!(mx == mx) || isinf(mx)) {
+            st->status = MX_ERR_NOCONV;
+            st->done = 1;
+        } else if (conv) {
+            st->status = MX_OK;
+            st->done = 1;
+        } else if (st->iter >= st->maxit) {
+            st->status = MX_ERR_NOCONV;
+            st->done = 1;
+        } else if (st->iter > 3 && mx > 1e3 * st->best) {
+            st->status = MX_ERR_NOCONV;
+            st->done = 1;
+        } else {
+            st->done = 0;
+            st->iter += 1;
+        }
+        if (mx < st->best) st->best = mx;
+    }
+}
+__global__ void comp_scale_kernel(SolveState *st) { set_scale(st, st->fnorm > 0.0 ? st->fnorm : 1.0); }
+__global__ void comp_rmax_kernel(const double *part, int nb, double *dst) {
+    double mx = 0.0, z1 = 0.0, z2 = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) mx = nmax(mx, part[3 * q]);
+    block_red3(mx, z1, z2);
+    if (threadIdx.x == 0) *dst = mx;
+}
+
+// right-hand side of the coarse correction: r / scale on the uncovered cells,
+// the mean of the eight fine residuals on the covered ones (FP32)
+__global__ void comp_coarse_rhs_kernel(CompGeom G, const double *__restrict__ rc, const double *__restrict__ rf,
+                                       const SolveState *st, float *__restrict__ out) {
+    const long long N = (long long)G.n[0] * G.n[1] * G.n[2];
+    const double is = st->inv_scale;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coarse_ijk(G, q, c);
+        out[q] = float((in_patch(G, c) ? mean8(G, rf, c) : rc[q]) * is);
+    }
+}
+__global__ void comp_fine_rhs_kernel(long long n, const double *__restrict__ rf, const SolveState *st,
+                                     float *__restrict__ out) {
+    const double is = st->inv_scale;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        out[q] = float(rf[q] * is);
+}
+// phi_c += scale e_c on the uncovered cells, phi_f += scale e_c(parent)
+__global__ void comp_coarse_update_kernel(CompGeom G, double *__restrict__ pc, double *__restrict__ pf,
+                                          const float *__restrict__ ec, const SolveState *st, int nbc) {
+    const double sc = st->scale;
+    const bool fine = blockIdx.x >= nbc;
+    const int b0 = fine ? blockIdx.x - nbc : blockIdx.x, nb = fine ? gridDim.x - nbc : nbc;
+    if (fine) {
+        const long long N = (long long)G.nf[0] * G.nf[1] * G.nf[2];
+        for (long long q = b0 * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)nb * blockDim.x) {
+            int F[3];
+            fine_ijk(G, q, F);
+            pf[q] += sc * double(ec[cix(G, G.plo[0] + F[0] / 2, G.plo[1] + F[1] / 2, G.plo[2] + F[2] / 2)]);
+        }
+    } else {
+        const long long N = (long long)G.n[0] * G.n[1] * G.n[2];
+        for (long long q = b0 * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)nb * blockDim.x) {
+            int c[3];
+            coarse_ijk(G, q, c);
+            if (!in_patch(G, c)) pc[q] += sc * double(ec[q]);
+        }
+    }
+}
+__global__ void comp_fine_update_kernel(long long n, double *__restrict__ pf, const float *__restrict__ ef,
+                                        const SolveState *st) {
+    const double sc = st->scale;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        pf[q] += sc * double(ef[q]);
+}
+
+// coefficient inputs of the coarse correction operator: rho, beta0 of the coarse
+// level with the covered cells replaced by the means of their fine cells
+__global__ void comp_coarse_fields_kernel(CompGeom G, const double *__restrict__ rc, const double *__restrict__ bc,
+                                          const double *__restrict__ rf, const double *__restrict__ bf,
+                                          double *__restrict__ rm, double *__restrict__ bm) {
+    const long long N = (long long)G.n[0] * G.n[1] * G.n[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coarse_ijk(G, q, c);
+        const bool cov = in_patch(G, c);
+        rm[q] = cov ? mean8(G, rf, c) : rc[q];
+        bm[q] = cov ? mean8(G, bf, c) : bc[q];
+    }
+}
+
+// The patch's correction operator: the patch as a box with phi = 0 beyond its
+// faces, whose boundary faces (stored as the Dirichlet coefficient 2 b of the
+// boundary cell) get the weight the ghost gives the boundary cell when the
+// coarse correction is held at 0 and the next cell inward is taken equal to it:
+// phi_g - phi_F1 = (2/3 - 1/5 - 1) phi_F1, i.e. 8/15 b instead of 2 b.
+__global__ void comp_patch_bnd_kernel(Level<float> L, float w) {
+    const DGeom &g = L.g;
+    const long long N = g.N;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const int i = int(q % g.n[0]), j = int((q / g.n[0]) % g.n[1]), k = int(q / g.nxy);
+        if (i == 0) L.bx[q] *= w;
+        if (j == 0) L.by[q] *= w;
+        if (k == 0) L.bz[q] *= w;
+        if (i == g.n[0] - 1) L.hx[j + (long long)g.n[1] * k] *= w;
+        if (j == g.n[1] - 1) L.hy[i + (long long)g.n[0] * k] *= w;
+        if (k == g.n[2] - 1) L.hz[i + (long long)g.n[0] * j] *= w;
+    }
+}
+
+// volume-weighted sum of phi over the unknowns (uncovered coarse, fine): partials (0, sum, volume)
+__global__ void comp_phi_sum_kernel(CompGeom G, const double *__restrict__ pc, const double *__restrict__ pf,
+                                    double *part, int nbc) {
+    const bool fine = blockIdx.x >= nbc;
+    const long long N = fine ? (long long)G.nf[0] * G.nf[1] * G.nf[2] : (long long)G.n[0] * G.n[1] * G.n[2];
+    const int b0 = fine ? blockIdx.x - nbc : blockIdx.x, nb = fine ? gridDim.x - nbc : nbc;
+    const double vol = fine ? G.h * G.h * G.h : G.H * G.H * G.H;
+    double z = 0.0, sum = 0.0, v = 0.0;
+    for (long long q = b0 * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)nb * blockDim.x) {
+        if (!fine) {
+            int c[3];
+            coarse_ijk(G, q, c);
+            if (in_patch(G, c)) continue;
+        }
+        sum += vol * (fine ? pf[q] : pc[q]);
+        v += vol;
+    }
+    block_red3(z, sum, v);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = 0.0;
+        part[3 * blockIdx.x + 1] = sum;
+        part[3 * blockIdx.x + 2] = v;
+    }
+}
+__global__ void comp_phi_mean_kernel(const double *part, int nb, double *dst) {
+    double a, b, c;
+    reduce_partials3(part, nb, a, b, c);
+    if (threadIdx.x == 0) *dst = b / c;
+}
+// phi -= mean (singular problems) on both levels, then the covered coarse phi = mean of its fine cells
+__global__ void comp_phi_fine_shift_kernel(long long n, double *__restrict__ pf, const double *mean) {
+    const double m = mean ? *mean : 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        pf[q] -= m;
+}
+__global__ void comp_phi_coarse_final_kernel(CompGeom G, double *__restrict__ pc, const double *__restrict__ pf,
+                                             const double *mean) {
+    const double m = mean ? *mean : 0.0;
+    const long long N = (long long)G.n[0] * G.n[1] * G.n[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coarse_ijk(G, q, c);
+        pc[q] = in_patch(G, c) ? mean8(G, pf, c) : pc[q] - m;
+    }
+}
+
+// U <- U - (dphi/dn)/rho_f on the coarse faces off the patch (single-level rules:
+// periodic faces wrap, a wall face keeps U = 0, a Dirichlet face uses (0 - phi)
+// over H/2); faces touching a covered cell are left to comp_face_mean_kernel
+__global__ void comp_correct_coarse_kernel(CompGeom G, int d, double *__restrict__ u, const double *__restrict__ pc,
+                                           const double *__restrict__ rc) {
+    int m[3] = {G.n[0], G.n[1], G.n[2]};
+    m[d] += 1;
+    const long long N = (long long)m[0] * m[1] * m[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int f[3] = {int(q % m[0]), int((q / m[0]) % m[1]), int(q / ((long long)m[0] * m[1]))};
+        const int p = f[d];
+        int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
+        L[d] = p - 1;
+        if (p == 0 || p == G.n[d]) {
+            if (G.lo[d] == MX_BC_PERIODIC) {
+                L[d] = (L[d] + G.n[d]) % G.n[d];
+                R[d] = R[d] % G.n[d];
+            } else {
+                const int bc = p == 0 ? G.lo[d] : G.hi[d];
+                const int *in = p == 0 ? R : L;
+                const long long qi = cix(G, in[0], in[1], in[2]);
+                if (bc == MX_BC_DIRICHLET) {
+                    const double g = p == 0 ? pc[qi] / (0.5 * G.H) : -pc[qi] / (0.5 * G.H);
+                    u[q] -= g / rc[qi];
+                } else {
+                    u[q] = 0.0;
+                }
+                continue;
+            }
+        }
+        if (in_patch(G, L) || in_patch(G, R)) continue;
+        const long long ql = cix(G, L[0], L[1], L[2]), qr = cix(G, R[0], R[1], R[2]);
+        u[q] -= ((pc[qr] - pc[ql]) / G.H) / (0.5 * (rc[ql] + rc[qr]));
+    }
+}
+// the fine faces: interior ones by the fine difference, patch-boundary ones with the ghost value
+__global__ void comp_correct_fine_kernel(CompGeom G, int d, double *__restrict__ u, const double *__restrict__ pc,
+                                         const double *__restrict__ pf, const double *__restrict__ rc,
+                                         const double *__restrict__ rf) {
+    int m[3] = {G.nf[0], G.nf[1], G.nf[2]};
+    m[d] += 1;
+    const long long N = (long long)m[0] * m[1] * m[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int f[3] = {int(q % m[0]), int((q / m[0]) % m[1]), int(q / ((long long)m[0] * m[1]))};
+        const int p = f[d];
+        int L[3] = {f[0], f[1], f[2]};
+        L[d] = p - 1;
+        if (p > 0 && p < G.nf[d]) {
+            const long long ql = fix_(G, L[0], L[1], L[2]), qr = fix_(G, f[0], f[1], f[2]);
+            u[q] -= ((pf[qr] - pf[ql]) / G.h) / (0.5 * (rf[ql] + rf[qr]));
+        } else {
+            const int *F = p == 0 ? f : L;
+            const int s = p == 0 ? -1 : 1;
+            int C[3];
+            const double pg = ghost(G, pc, pf, F, d, s, C);
+            const long long qf = fix_(G, F[0], F[1], F[2]);
+            const double g = p == 0 ? (pf[qf] - pg) / G.h : (pg - pf[qf]) / G.h;
+            u[q] -= g / (0.5 * (rf[qf] + rc[cix(G, C[0], C[1], C[2])]));
+        }
+    }
+}
+// coarse faces on and inside the patch: the mean of the four fine faces on them
+__global__ void comp_face_mean_kernel(CompGeom G, int d, double *__restrict__ uc, const double *__restrict__ uf) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int np = G.phi[d] - G.plo[d] + 1, na = G.phi[t1] - G.plo[t1], nb = G.phi[t2] - G.plo[t2];
+    int mc[3] = {G.n[0], G.n[1], G.n[2]}, mf[3] = {G.nf[0], G.nf[1], G.nf[2]};
+    mc[d] += 1;
+    mf[d] += 1;
+    const long long N = (long long)np * na * nb;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const int p = G.plo[d] + int(q % np), a = G.plo[t1] + int((q / np) % na), b = G.plo[t2] + int(q / ((long long)np * na));
+        int face[3];
+        face[d] = p;
+        face[t1] = a;
+        face[t2] = b;
+        double m = 0.0;
+        for (int e2 = 0; e2 < 2; e2++)
+            for (int e1 = 0; e1 < 2; e1++) {
+                int ff[3];
+                ff[d] = 2 * (p - G.plo[d]);
+                ff[t1] = 2 * (a - G.plo[t1]) + e1;
+                ff[t2] = 2 * (b - G.plo[t2]) + e2;
+                m += 0.25 * uf[ff[0] + (long long)mf[0] * (ff[1] + (long long)mf[1] * ff[2])];
+            }
+        uc[face[0] + (long long)mc[0] * (face[1] + (long long)mc[1] * face[2])] = m;
+    }
+}
+
+// max |D(beta0 U) - beta0 Sbar - c| over the unknowns (the divergence in place in dc, df)
+__global__ void comp_divcheck_kernel(CompGeom G, const double *__restrict__ dc, const double *__restrict__ df,
+                                     const double *__restrict__ bc, const double *__restrict__ sc,
+                                     const double *__restrict__ bf, const double *__restrict__ sf,
+                                     const SolveState *st, double *part, int nbc) {
+    const bool fine = blockIdx.x >= nbc;
+    const long long N = fine ? (long long)G.nf[0] * G.nf[1] * G.nf[2] : (long long)G.n[0] * G.n[1] * G.n[2];
+    const int b0 = fine ? blockIdx.x - nbc : blockIdx.x, nb = fine ? gridDim.x - nbc : nbc;
+    const double cm = st->mean;
+    double mx = 0.0, z1 = 0.0, z2 = 0.0;
+    for (long long q = b0 * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)nb * blockDim.x) {
+        double x;
+        if (fine) {
+            x = df[q] - bf[q] * sf[q] - cm;
+        } else {
+            int c[3];
+            coarse_ijk(G, q, c);
+            if (in_patch(G, c)) continue;
+            x = dc[q] - bc[q] * sc[q] - cm;
+        }
+        mx = nmax(mx, fabs(x));
+    }
+    block_red3(mx, z1, z2);
+    if (threadIdx.x == 0) part[3 * blockIdx.x] = mx;
+}
+
 mx_status make_comp(mx_ctx *c, const mx_geom *geom, const int plo[3], const int phi[3], CompGeom &G) {
     mx_status st = check_geom(c, geom, false);
     if (st) return st;
@@ -306,5 +712,182 @@ extern "C" mx_status mx_composite_divergence(mx_ctx *c, const mx_geom *geom, con
                                                                    beta0_f, out_c);
     comp_div_fine_kernel<<<red_blocks(Nf), 256, 0, c->stream>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, out_f);
     MX_CUDA(c, cudaGetLastError());
+    return MX_OK;
+}
+
+// ---- composite projection (mx_mac_project_composite) ------------------------------------
+// Refinement on the composite residual: r = f - L phi (FP64, the exact composite
+// operator), then per iteration a coarse correction (one FP32 V-cycle of the whole
+// coarse grid; its right-hand side the coarse residual on uncovered cells and the
+// mean of the eight fine residuals on covered ones, its coefficients from rho,
+// beta0 with the covered cells replaced by their fine means), added to the
+// uncovered coarse cells and, piecewise constant, to the patch; the fine
+// residual again; a fine correction (one FP32 V-cycle of the patch with phi = 0
+// beyond its faces, the boundary faces weighted 8/15 b as the ghost weighs the
+// boundary cell with the coarse correction held), added to the patch.  The
+// iteration stops when the FP64 composite residual meets the tolerance.
+namespace {
+struct CompScratch {
+    void *mem = nullptr;
+    MacPlan *pc = nullptr, *pf = nullptr;
+    ~CompScratch() {
+        if (mem) cudaFree(mem);
+        if (pc) free_mac_plan(pc);
+        if (pf) free_mac_plan(pf);
+    }
+};
+}  // namespace
+
+extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, const int plo[3], const int phi[3],
+                                              double *ux_c, double *uy_c, double *uz_c, const double *rho_c,
+                                              const double *beta0_c, const double *sbar_c, double *phi_c,
+                                              double *ux_f, double *uy_f, double *uz_f, const double *rho_f,
+                                              const double *beta0_f, const double *sbar_f, double *phi_f,
+                                              const mx_opts *opts, mx_info *info) {
+    if (!c) return MX_ERR_ARG;
+    CompGeom G;
+    mx_status st = make_comp(c, geom, plo, phi, G);
+    if (st) return st;
+    if (!ux_c || !uy_c || !uz_c || !rho_c || !beta0_c || !sbar_c || !phi_c || !ux_f || !uy_f || !uz_f || !rho_f ||
+        !beta0_f || !sbar_f || !phi_f)
+        return set_err(c, MX_ERR_ARG, "mac_project_composite: null array");
+    mx_opts o;
+    if ((st = check_opts(c, opts, o))) return st;
+    if (o.prec != MX_PREC_MIXED || o.krylov)
+        return set_err(c, MX_ERR_ARG, "mac_project_composite: prec must be MX_PREC_MIXED and krylov 0");
+    if (o.nu1 == 0 && o.nu2 == 0) o.nu1 = o.nu2 = 2;
+    const int zcap = o.tile_z ? o.tile_z : 8;
+    cudaStream_t s = c->stream;
+    const DGeom gc = make_dgeom(geom);
+    DGeom gf;
+    for (int d = 0; d < 3; d++) {
+        gf.n[d] = G.nf[d];
+        gf.lo[d] = gf.hi[d] = MX_BC_DIRICHLET;
+    }
+    gf.nxy = (long long)gf.n[0] * gf.n[1];
+    gf.N = gf.nxy * gf.n[2];
+    gf.h = G.h;
+    const long long Nc = gc.N, Nf = gf.N;
+    const int singular = geom_singular(gc);
+    const int nbc = gs_blocks(Nc), nbf = gs_blocks(Nf), nb = nbc + nbf;
+    if ((st = ensure_partials(c, nb))) return st;
+    CompScratch S;
+    S.pc = create_mac_plan(c, gc, MX_PREC_MIXED, &st);
+    if (!S.pc) return st;
+    S.pf = create_mac_plan(c, gf, MX_PREC_MIXED, &st);
+    if (!S.pf) return st;
+    if (cudaMalloc(&S.mem, sizeof(double) * (4 * Nc + 2 * Nf)) != cudaSuccess) {
+        cudaGetLastError();
+        S.mem = nullptr;
+        return set_err(c, MX_ERR_OOM, "mac_project_composite: scratch cudaMalloc failed");
+    }
+    double *fc = (double *)S.mem, *rcb = fc + Nc, *rm = rcb + Nc, *bm = rm + Nc, *ff = bm + Nc, *rfb = ff + Nf;
+    double *part = c->partials;
+    SolveState *dst = c->state;
+    MX_CUDA(c, cudaEventRecord(c->ev0, s));
+    SolveState init = {};
+    init.tol = o.rel_tol;
+    init.maxit = std::min(o.max_outer, o.max_vcycles);
+    init.best = INFINITY;
+    *c->hstate = init;
+    MX_CUDA(c, cudaMemcpyAsync(dst, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+
+    // correction operators
+    comp_coarse_fields_kernel<<<nbc, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, rm, bm);
+    setup_coefficients_on(s, *S.pc, rm, bm);
+    Hier<float> &HF = S.pf->H32;
+    k_mac_coeffs_df(s, HF.lev[0], S.pf->D, rho_f, beta0_f, nullptr);
+    comp_patch_bnd_kernel<<<nbf, 256, 0, s>>>(HF.lev[0], float(4.0 / 15.0));
+    for (int l = 0; l + 1 < HF.nlev; l++) k_coarsen_coeffs(s, HF.lev[l], HF.lev[l + 1]);
+
+    // right-hand side, mean removal, scale
+    comp_div_coarse_kernel<<<nbc, 256, 0, s>>>(G, ux_c, uy_c, uz_c, ux_f, uy_f, uz_f, beta0_c, beta0_f, fc);
+    comp_div_fine_kernel<<<nbf, 256, 0, s>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, ff);
+    comp_rhs_kernel<<<nb, 256, 0, s>>>(G, fc, ff, beta0_c, sbar_c, beta0_f, sbar_f, part, nbc);
+    comp_rhs_final_kernel<<<1, 1024, 0, s>>>(part, nb, dst, singular && o.remove_mean);
+    if (singular && !o.remove_mean) {
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (std::fabs(c->hstate->aux) > 1e-12 * c->hstate->fnorm) {
+            if (info) {
+                std::memset(info, 0, sizeof(*info));
+                info->status = MX_ERR_INCOMPAT;
+            }
+            return set_err(c, MX_ERR_INCOMPAT, "singular problem: right-hand side has non-zero mean and remove_mean = 0");
+        }
+    }
+    if (singular && o.remove_mean) {
+        comp_sub_mean_kernel<<<nb, 256, 0, s>>>(G, fc, ff, dst, part, nbc);
+        comp_rmax_kernel<<<1, 1024, 0, s>>>(part, nb, &dst->fnorm);
+    }
+    comp_scale_kernel<<<1, 1, 0, s>>>(dst);
+    if (!o.use_initial_guess) {
+        MX_CUDA(c, cudaMemsetAsync(phi_c, 0, sizeof(double) * Nc, s));
+        MX_CUDA(c, cudaMemsetAsync(phi_f, 0, sizeof(double) * Nf, s));
+    }
+
+    // refinement loop
+    Hier<float> &HC = S.pc->H32;
+    for (;;) {
+        comp_apply_coarse_kernel<<<nbc, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, rcb, fc, part);
+        comp_apply_fine_kernel<<<nbf, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, rfb, ff,
+                                                   part + 3 * nbc);
+        comp_decide_kernel<<<1, 1024, 0, s>>>(part, nb, dst);
+        MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MX_CUDA(c, cudaStreamSynchronize(s));
+        if (c->hstate->done) break;
+        // coarse correction
+        comp_coarse_rhs_kernel<<<nbc, 256, 0, s>>>(G, rcb, rfb, dst, HC.lev[0].f);
+        vcycle(s, HC, o.nu1, o.nu2, o.bottom_iters, singular, nullptr, 0, zcap);
+        comp_coarse_update_kernel<<<nb, 256, 0, s>>>(G, phi_c, phi_f, HC.lev[0].e, dst, nbc);
+        // fine correction from the fine residual after it
+        comp_apply_fine_kernel<<<nbf, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, rfb, ff, nullptr);
+        comp_fine_rhs_kernel<<<nbf, 256, 0, s>>>(Nf, rfb, dst, HF.lev[0].f);
+        vcycle(s, HF, o.nu1, o.nu2, o.bottom_iters, 0, nullptr, 0, zcap);
+        comp_fine_update_kernel<<<nbf, 256, 0, s>>>(Nf, phi_f, HF.lev[0].e, dst);
+    }
+
+    // normalisation (zero volume-weighted mean of the unknowns when singular), the
+    // covered coarse phi, the velocity correction on both levels, the check
+    if (singular) {
+        comp_phi_sum_kernel<<<nb, 256, 0, s>>>(G, phi_c, phi_f, part, nbc);
+        comp_phi_mean_kernel<<<1, 1024, 0, s>>>(part, nb, &dst->aux);
+        comp_phi_fine_shift_kernel<<<nbf, 256, 0, s>>>(Nf, phi_f, &dst->aux);
+    }
+    comp_phi_coarse_final_kernel<<<nbc, 256, 0, s>>>(G, phi_c, phi_f, singular ? &dst->aux : nullptr);
+    double *uc[3] = {ux_c, uy_c, uz_c}, *uf[3] = {ux_f, uy_f, uz_f};
+    for (int d = 0; d < 3; d++) {
+        comp_correct_coarse_kernel<<<nbc, 256, 0, s>>>(G, d, uc[d], phi_c, rho_c);
+        comp_correct_fine_kernel<<<nbf, 256, 0, s>>>(G, d, uf[d], phi_c, phi_f, rho_c, rho_f);
+    }
+    for (int d = 0; d < 3; d++) comp_face_mean_kernel<<<nbc, 256, 0, s>>>(G, d, uc[d], uf[d]);
+    comp_div_coarse_kernel<<<nbc, 256, 0, s>>>(G, ux_c, uy_c, uz_c, ux_f, uy_f, uz_f, beta0_c, beta0_f, rcb);
+    comp_div_fine_kernel<<<nbf, 256, 0, s>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, rfb);
+    comp_divcheck_kernel<<<nb, 256, 0, s>>>(G, rcb, rfb, beta0_c, sbar_c, beta0_f, sbar_f, dst, part, nbc);
+    comp_rmax_kernel<<<1, 1024, 0, s>>>(part, nb, &dst->div_err);
+    MX_CUDA(c, cudaEventRecord(c->ev1, s));
+    MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MX_CUDA(c, cudaStreamSynchronize(s));
+    MX_CUDA(c, cudaGetLastError());
+    const SolveState &hs = *c->hstate;
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        info->outer_iters = hs.iter;
+        info->vcycles = 2 * hs.iter;
+        info->rel_resid = hs.fnorm > 0 ? hs.rnorm / hs.fnorm : hs.rnorm;
+        info->rel_resid_l2 = 0.0;
+        info->div_err_linf = hs.div_err;
+        info->rhs_mean_removed = hs.mean;
+        info->rhs_linf = hs.fnorm;
+        info->ms = ms;
+        info->status = hs.status;
+    }
+    if (hs.status != MX_OK) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "composite: no convergence, relative residual %.3e after %d iterations",
+                      hs.rnorm / (hs.fnorm > 0 ? hs.fnorm : 1.0), hs.iter);
+        return set_err(c, (mx_status)hs.status, buf);
+    }
     return MX_OK;
 }
