@@ -432,8 +432,10 @@ mx_status mx_probe_fma_peak(int device, int fp64, double *tflops);
  * FP64 refinement) and krylov 0 (else MX_ERR_ARG); nu1 = nu2 = 0 means 2, 2;
  * max_outer / max_vcycles cap the refinement iterations (each runs one V-cycle
  * of the coarse grid and one of the patch; info->vcycles counts both).
- * Allocates its workspace (two multigrid plans and six FP64 scratch fields) for
- * the call and frees it before returning; synchronises the stream. */
+ * The context keeps the workspace of the last composite geometry (two multigrid
+ * plans, six FP64 cell fields and the FP64 face coefficients of both levels) and
+ * the CUDA graph of its refinement loop (use_graph = 1; keyed by phi_c, phi_f and
+ * the smoother options); a new geometry replaces them.  Synchronises the stream. */
 mx_status mx_mac_project_composite(mx_ctx *ctx, const mx_geom *geom, const int plo[3], const int phi[3],
                                    double *ux_c, double *uy_c, double *uz_c, const double *rho_c,
                                    const double *beta0_c, const double *sbar_c, double *phi_c, double *ux_f,

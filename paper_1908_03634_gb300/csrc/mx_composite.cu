@@ -278,7 +278,6 @@ __global__ void comp_div_fine_kernel(CompGeom G, const double *__restrict__ fx, 
     }
 }
 
-// ---- composite projection ---------------------------------------------------------------
 // grid-stride launch shape of the per-cell kernels below
 inline int gs_blocks(long long n) { return red_blocks(n); }
 
@@ -303,6 +302,182 @@ __device__ __forceinline__ double mean8(const CompGeom &G, const double *__restr
             for (int a = 0; a < 2; a++) s += xf[child(G, c, a, b, e)];
     return 0.125 * s;
 }
+
+// ---- composite projection ---------------------------------------------------------------
+// Face coefficients of both levels, computed once per solve (the iteration then
+// does no FP64 division): API face layout, n_d + 1 faces along d.
+//   coarse: faces between two uncovered cells (periodic images included) the
+//   arithmetic face mean, a Dirichlet domain face 2 beta0/rho of its cell, a wall
+//   0; faces touching a covered cell 0 (their fluxes come from the fine faces);
+//   fine: the face mean inside the patch, on the patch boundary of the fine cell
+//   and the coarse cell across.
+__device__ __forceinline__ long long face_ix(const int m[3], const int f[3]) {
+    return f[0] + (long long)m[0] * (f[1] + (long long)m[1] * f[2]);
+}
+__global__ void comp_coef_coarse_kernel(CompGeom G, int d, double *__restrict__ B, const double *__restrict__ rc,
+                                        const double *__restrict__ bc) {
+    int m[3] = {G.n[0], G.n[1], G.n[2]};
+    m[d] += 1;
+    const long long N = (long long)m[0] * m[1] * m[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int f[3] = {int(q % m[0]), int((q / m[0]) % m[1]), int(q / ((long long)m[0] * m[1]))};
+        const int p = f[d];
+        int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
+        L[d] = p - 1;
+        double b = 0.0;
+        if (p == 0 || p == G.n[d]) {
+            if (G.lo[d] == MX_BC_PERIODIC) {
+                L[d] = (L[d] + G.n[d]) % G.n[d];
+                R[d] = R[d] % G.n[d];
+                const long long ql = cix(G, L[0], L[1], L[2]), qr = cix(G, R[0], R[1], R[2]);
+                b = bmean(bc[ql], rc[ql], bc[qr], rc[qr]);
+            } else if ((p == 0 ? G.lo[d] : G.hi[d]) == MX_BC_DIRICHLET) {
+                const int *in = p == 0 ? R : L;
+                const long long qi = cix(G, in[0], in[1], in[2]);
+                b = 2.0 * (bc[qi] / rc[qi]);
+            }
+        } else if (!in_patch(G, L) && !in_patch(G, R)) {
+            const long long ql = cix(G, L[0], L[1], L[2]), qr = cix(G, R[0], R[1], R[2]);
+            b = bmean(bc[ql], rc[ql], bc[qr], rc[qr]);
+        }
+        B[q] = b;
+    }
+}
+__global__ void comp_coef_fine_kernel(CompGeom G, int d, double *__restrict__ B, const double *__restrict__ rc,
+                                      const double *__restrict__ bc, const double *__restrict__ rf,
+                                      const double *__restrict__ bf) {
+    int m[3] = {G.nf[0], G.nf[1], G.nf[2]};
+    m[d] += 1;
+    const long long N = (long long)m[0] * m[1] * m[2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int f[3] = {int(q % m[0]), int((q / m[0]) % m[1]), int(q / ((long long)m[0] * m[1]))};
+        const int p = f[d];
+        int L[3] = {f[0], f[1], f[2]};
+        L[d] = p - 1;
+        if (p > 0 && p < G.nf[d]) {
+            const long long ql = fix_(G, L[0], L[1], L[2]), qr = fix_(G, f[0], f[1], f[2]);
+            B[q] = bmean(bf[ql], rf[ql], bf[qr], rf[qr]);
+        } else {
+            const int *F = p == 0 ? f : L;
+            int C[3];
+            for (int a = 0; a < 3; a++) C[a] = G.plo[a] + F[a] / 2;
+            C[d] += p == 0 ? -1 : 1;
+            const long long qf = fix_(G, F[0], F[1], F[2]), qc = cix(G, C[0], C[1], C[2]);
+            B[q] = bmean(bf[qf], rf[qf], bc[qc], rc[qc]);
+        }
+    }
+}
+struct CompCoefs {
+    const double *c[3], *f[3];
+};
+// r = f - L phi with the cached face coefficients (the operator of
+// comp_apply_*_kernel), and per-block maxima of |r| in part (if non-null)
+__global__ void comp_resid_coarse_kernel(CompGeom G, CompCoefs B, const double *__restrict__ pc,
+                                         const double *__restrict__ pf, const double *__restrict__ f,
+                                         double *__restrict__ out, double *part) {
+    const long long N = (long long)G.n[0] * G.n[1] * G.n[2];
+    const double iH2 = 1.0 / (G.H * G.H), ihH = 1.0 / (G.h * G.H);
+    double rmax = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        coarse_ijk(G, q, c);
+        if (in_patch(G, c)) {
+            out[q] = 0.0;
+            continue;
+        }
+        const double p0 = pc[q];
+        double acc = 0.0;
+        for (int d = 0; d < 3; d++) {
+            int m[3] = {G.n[0], G.n[1], G.n[2]};
+            m[d] += 1;
+            for (int s = -1; s <= 1; s += 2) {
+                int face[3] = {c[0], c[1], c[2]};
+                if (s > 0) face[d] += 1;
+                const double b = B.c[d][face_ix(m, face)];
+                int nb[3] = {c[0], c[1], c[2]};
+                nb[d] += s;
+                if (nb[d] < 0 || nb[d] >= G.n[d]) {
+                    if (G.lo[d] != MX_BC_PERIODIC) {
+                        acc -= b * p0 * iH2;  // Dirichlet (b = 2 beta0/rho) or wall (b = 0)
+                        continue;
+                    }
+                    nb[d] = (nb[d] + G.n[d]) % G.n[d];
+                }
+                if (!in_patch(G, nb)) {
+                    acc += b * (pc[cix(G, nb[0], nb[1], nb[2])] - p0) * iH2;
+                    continue;
+                }
+                // coarse-fine face: the mean of the four fine fluxes
+                const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+                const int Fd = 2 * (nb[d] - G.plo[d]) + (s > 0 ? 0 : 1);
+                int mf[3] = {G.nf[0], G.nf[1], G.nf[2]};
+                mf[d] += 1;
+                double mm = 0.0;
+                for (int a = 0; a < 2; a++)
+                    for (int e = 0; e < 2; e++) {
+                        int F[3];
+                        F[d] = Fd;
+                        F[t1] = 2 * (c[t1] - G.plo[t1]) + a;
+                        F[t2] = 2 * (c[t2] - G.plo[t2]) + e;
+                        int ff[3] = {F[0], F[1], F[2]};
+                        if (s < 0) ff[d] += 1;  // the fine cell's high face
+                        int C[3];
+                        const double g = ghost(G, pc, pf, F, d, -s, C);
+                        mm += B.f[d][face_ix(mf, ff)] * (pf[fix_(G, F[0], F[1], F[2])] - g);
+                    }
+                acc += 0.25 * mm * ihH;
+            }
+        }
+        acc = f[q] - acc;
+        rmax = nmax(rmax, fabs(acc));
+        out[q] = acc;
+    }
+    if (part) {
+        double z1 = 0.0, z2 = 0.0;
+        block_red3(rmax, z1, z2);
+        if (threadIdx.x == 0) part[3 * blockIdx.x] = rmax;
+    }
+}
+__global__ void comp_resid_fine_kernel(CompGeom G, CompCoefs B, const double *__restrict__ pc,
+                                       const double *__restrict__ pf, const double *__restrict__ f,
+                                       double *__restrict__ out, double *part) {
+    const long long N = (long long)G.nf[0] * G.nf[1] * G.nf[2];
+    const double ih2 = 1.0 / (G.h * G.h);
+    double rmax = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int F[3];
+        fine_ijk(G, q, F);
+        const double p0 = pf[q];
+        double acc = 0.0;
+        for (int d = 0; d < 3; d++) {
+            int m[3] = {G.nf[0], G.nf[1], G.nf[2]};
+            m[d] += 1;
+            for (int s = -1; s <= 1; s += 2) {
+                int face[3] = {F[0], F[1], F[2]};
+                if (s > 0) face[d] += 1;
+                const double b = B.f[d][face_ix(m, face)];
+                int nb[3] = {F[0], F[1], F[2]};
+                nb[d] += s;
+                if (nb[d] >= 0 && nb[d] < G.nf[d]) {
+                    acc += b * (pf[fix_(G, nb[0], nb[1], nb[2])] - p0) * ih2;
+                } else {
+                    int C[3];
+                    acc += b * (ghost(G, pc, pf, F, d, s, C) - p0) * ih2;
+                }
+            }
+        }
+        acc = f[q] - acc;
+        rmax = nmax(rmax, fabs(acc));
+        out[q] = acc;
+    }
+    if (part) {
+        double z1 = 0.0, z2 = 0.0;
+        block_red3(rmax, z1, z2);
+        if (threadIdx.x == 0) part[3 * blockIdx.x] = rmax;
+    }
+}
+
+
 
 // f = D(beta0 U) - beta0 Sbar on the uncovered coarse cells (0 on covered ones)
 // and the fine cells, in place over the divergence; partials (max |f|,
@@ -717,26 +892,137 @@ extern "C" mx_status mx_composite_divergence(mx_ctx *c, const mx_geom *geom, con
 
 // ---- composite projection (mx_mac_project_composite) ------------------------------------
 // Refinement on the composite residual: r = f - L phi (FP64, the exact composite
-// operator), then per iteration a coarse correction (one FP32 V-cycle of the whole
-// coarse grid; its right-hand side the coarse residual on uncovered cells and the
-// mean of the eight fine residuals on covered ones, its coefficients from rho,
-// beta0 with the covered cells replaced by their fine means), added to the
-// uncovered coarse cells and, piecewise constant, to the patch; the fine
-// residual again; a fine correction (one FP32 V-cycle of the patch with phi = 0
-// beyond its faces, the boundary faces weighted 8/15 b as the ghost weighs the
-// boundary cell with the coarse correction held), added to the patch.  The
-// iteration stops when the FP64 composite residual meets the tolerance.
+// operator with face coefficients computed once per call), then per iteration a
+// coarse correction (one FP32 V-cycle of the whole coarse grid; its right-hand
+// side the coarse residual on uncovered cells and the mean of the eight fine
+// residuals on covered ones, its coefficients from rho, beta0 with the covered
+// cells replaced by their fine means), added to the uncovered coarse cells and,
+// piecewise constant, to the patch; the fine residual again; a fine correction
+// (one FP32 V-cycle of the patch with phi = 0 beyond its faces, the boundary
+// faces weighted 8/15 b as the ghost weighs the boundary cell with the coarse
+// correction held), added to the patch; the composite residual and its norm.
+// The loop runs as one conditional CUDA graph (or from the host), stopping when
+// the FP64 composite residual meets the tolerance.
 namespace {
-struct CompScratch {
-    void *mem = nullptr;
+struct CompPlan {
+    CompGeom G;
+    int singular = 0;
     MacPlan *pc = nullptr, *pf = nullptr;
-    ~CompScratch() {
+    void *mem = nullptr;
+    double *fc, *rcb, *rm, *bm, *ff, *rfb;
+    CompCoefs B;
+    // the refinement loop's graph and what it was captured with
+    cudaGraphExec_t graph = nullptr;
+    const void *k_pc = nullptr, *k_pf = nullptr, *k_part = nullptr;
+    int k_nu1 = -1, k_nu2 = -1, k_bot = -1, k_zcap = -1;
+    ~CompPlan() {
+        if (graph) cudaGraphExecDestroy(graph);
         if (mem) cudaFree(mem);
         if (pc) free_mac_plan(pc);
         if (pf) free_mac_plan(pf);
     }
 };
+
+bool same_comp(const CompGeom &a, const CompGeom &b) {
+    for (int d = 0; d < 3; d++)
+        if (a.n[d] != b.n[d] || a.lo[d] != b.lo[d] || a.hi[d] != b.hi[d] || a.plo[d] != b.plo[d] || a.phi[d] != b.phi[d])
+            return false;
+    return a.H == b.H;
+}
+
+// the context's composite plan for G (one kept: the last geometry)
+CompPlan *get_comp_plan(mx_ctx *c, const CompGeom &G, const mx_geom *geom, mx_status *st) {
+    *st = MX_OK;
+    CompPlan *P = (CompPlan *)c->comp;
+    if (P && same_comp(P->G, G)) return P;
+    if (P) {
+        cudaStreamSynchronize(c->stream);
+        delete P;
+        c->comp = nullptr;
+    }
+    P = new CompPlan();
+    P->G = G;
+    const DGeom gc = make_dgeom(geom);
+    DGeom gf;
+    for (int d = 0; d < 3; d++) {
+        gf.n[d] = G.nf[d];
+        gf.lo[d] = gf.hi[d] = MX_BC_DIRICHLET;
+    }
+    gf.nxy = (long long)gf.n[0] * gf.n[1];
+    gf.N = gf.nxy * gf.n[2];
+    gf.h = G.h;
+    P->singular = geom_singular(gc);
+    P->pc = create_mac_plan(c, gc, MX_PREC_MIXED, st);
+    if (P->pc) P->pf = create_mac_plan(c, gf, MX_PREC_MIXED, st);
+    if (!P->pc || !P->pf) {
+        delete P;
+        return nullptr;
+    }
+    const long long Nc = gc.N, Nf = gf.N;
+    long long nface_c[3], nface_f[3], tot = 4 * Nc + 2 * Nf;
+    for (int d = 0; d < 3; d++) {
+        nface_c[d] = (Nc / G.n[d]) * (G.n[d] + 1);
+        nface_f[d] = (Nf / G.nf[d]) * (G.nf[d] + 1);
+        tot += nface_c[d] + nface_f[d];
+    }
+    if (cudaMalloc(&P->mem, sizeof(double) * tot) != cudaSuccess) {
+        cudaGetLastError();
+        P->mem = nullptr;
+        delete P;
+        *st = set_err(c, MX_ERR_OOM, "mac_project_composite: workspace cudaMalloc failed");
+        return nullptr;
+    }
+    double *x = (double *)P->mem;
+    P->fc = x;
+    P->rcb = x + Nc;
+    P->rm = x + 2 * Nc;
+    P->bm = x + 3 * Nc;
+    P->ff = x + 4 * Nc;
+    P->rfb = P->ff + Nf;
+    x = P->rfb + Nf;
+    double *bcoef[6];
+    for (int d = 0; d < 3; d++) {
+        bcoef[d] = x;
+        x += nface_c[d];
+    }
+    for (int d = 0; d < 3; d++) {
+        bcoef[3 + d] = x;
+        x += nface_f[d];
+    }
+    for (int d = 0; d < 3; d++) {
+        P->B.c[d] = bcoef[d];
+        P->B.f[d] = bcoef[3 + d];
+    }
+    c->comp = P;
+    return P;
+}
+
+// one refinement iteration after the composite residual: the two corrections,
+// then the residual and the convergence decision
+void comp_body(cudaStream_t s, mx_ctx *c, CompPlan &P, double *phi_c, double *phi_f, const mx_opts &o, int zcap) {
+    const CompGeom &G = P.G;
+    const long long Nf = (long long)G.nf[0] * G.nf[1] * G.nf[2];
+    const int nbc = gs_blocks((long long)G.n[0] * G.n[1] * G.n[2]), nbf = gs_blocks(Nf), nb = nbc + nbf;
+    Hier<float> &HC = P.pc->H32, &HF = P.pf->H32;
+    SolveState *dst = c->state;
+    double *part = c->partials;
+    comp_coarse_rhs_kernel<<<nbc, 256, 0, s>>>(G, P.rcb, P.rfb, dst, HC.lev[0].f);
+    vcycle(s, HC, o.nu1, o.nu2, o.bottom_iters, P.singular, nullptr, 0, zcap);
+    comp_coarse_update_kernel<<<nb, 256, 0, s>>>(G, phi_c, phi_f, HC.lev[0].e, dst, nbc);
+    comp_resid_fine_kernel<<<nbf, 256, 0, s>>>(G, P.B, phi_c, phi_f, P.ff, P.rfb, nullptr);
+    comp_fine_rhs_kernel<<<nbf, 256, 0, s>>>(Nf, P.rfb, dst, HF.lev[0].f);
+    vcycle(s, HF, o.nu1, o.nu2, o.bottom_iters, 0, nullptr, 0, zcap);
+    comp_fine_update_kernel<<<nbf, 256, 0, s>>>(Nf, phi_f, HF.lev[0].e, dst);
+    comp_resid_coarse_kernel<<<nbc, 256, 0, s>>>(G, P.B, phi_c, phi_f, P.fc, P.rcb, part);
+    comp_resid_fine_kernel<<<nbf, 256, 0, s>>>(G, P.B, phi_c, phi_f, P.ff, P.rfb, part + 3 * nbc);
+    comp_decide_kernel<<<1, 1024, 0, s>>>(part, nb, dst);
+}
 }  // namespace
+
+void destroy_comp_plan(mx_ctx *c) {
+    delete (CompPlan *)c->comp;
+    c->comp = nullptr;
+}
 
 extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, const int plo[3], const int phi[3],
                                               double *ux_c, double *uy_c, double *uz_c, const double *rho_c,
@@ -758,30 +1044,13 @@ extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, co
     if (o.nu1 == 0 && o.nu2 == 0) o.nu1 = o.nu2 = 2;
     const int zcap = o.tile_z ? o.tile_z : 8;
     cudaStream_t s = c->stream;
-    const DGeom gc = make_dgeom(geom);
-    DGeom gf;
-    for (int d = 0; d < 3; d++) {
-        gf.n[d] = G.nf[d];
-        gf.lo[d] = gf.hi[d] = MX_BC_DIRICHLET;
-    }
-    gf.nxy = (long long)gf.n[0] * gf.n[1];
-    gf.N = gf.nxy * gf.n[2];
-    gf.h = G.h;
-    const long long Nc = gc.N, Nf = gf.N;
-    const int singular = geom_singular(gc);
+    const long long Nc = (long long)G.n[0] * G.n[1] * G.n[2], Nf = (long long)G.nf[0] * G.nf[1] * G.nf[2];
     const int nbc = gs_blocks(Nc), nbf = gs_blocks(Nf), nb = nbc + nbf;
     if ((st = ensure_partials(c, nb))) return st;
-    CompScratch S;
-    S.pc = create_mac_plan(c, gc, MX_PREC_MIXED, &st);
-    if (!S.pc) return st;
-    S.pf = create_mac_plan(c, gf, MX_PREC_MIXED, &st);
-    if (!S.pf) return st;
-    if (cudaMalloc(&S.mem, sizeof(double) * (4 * Nc + 2 * Nf)) != cudaSuccess) {
-        cudaGetLastError();
-        S.mem = nullptr;
-        return set_err(c, MX_ERR_OOM, "mac_project_composite: scratch cudaMalloc failed");
-    }
-    double *fc = (double *)S.mem, *rcb = fc + Nc, *rm = rcb + Nc, *bm = rm + Nc, *ff = bm + Nc, *rfb = ff + Nf;
+    CompPlan *Pp = get_comp_plan(c, G, geom, &st);
+    if (!Pp) return st;
+    CompPlan &P = *Pp;
+    const int singular = P.singular;
     double *part = c->partials;
     SolveState *dst = c->state;
     MX_CUDA(c, cudaEventRecord(c->ev0, s));
@@ -792,18 +1061,23 @@ extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, co
     *c->hstate = init;
     MX_CUDA(c, cudaMemcpyAsync(dst, c->hstate, sizeof(SolveState), cudaMemcpyHostToDevice, s));
 
-    // correction operators
-    comp_coarse_fields_kernel<<<nbc, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, rm, bm);
-    setup_coefficients_on(s, *S.pc, rm, bm);
-    Hier<float> &HF = S.pf->H32;
-    k_mac_coeffs_df(s, HF.lev[0], S.pf->D, rho_f, beta0_f, nullptr);
+    // face coefficients of the composite operator and the correction operators
+    double *uc[3] = {ux_c, uy_c, uz_c}, *uf[3] = {ux_f, uy_f, uz_f};
+    for (int d = 0; d < 3; d++) {
+        comp_coef_coarse_kernel<<<nbc, 256, 0, s>>>(G, d, (double *)P.B.c[d], rho_c, beta0_c);
+        comp_coef_fine_kernel<<<nbf, 256, 0, s>>>(G, d, (double *)P.B.f[d], rho_c, beta0_c, rho_f, beta0_f);
+    }
+    comp_coarse_fields_kernel<<<nbc, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, P.rm, P.bm);
+    setup_coefficients_on(s, *P.pc, P.rm, P.bm);
+    Hier<float> &HF = P.pf->H32;
+    k_mac_coeffs_df(s, HF.lev[0], P.pf->D, rho_f, beta0_f, nullptr);
     comp_patch_bnd_kernel<<<nbf, 256, 0, s>>>(HF.lev[0], float(4.0 / 15.0));
     for (int l = 0; l + 1 < HF.nlev; l++) k_coarsen_coeffs(s, HF.lev[l], HF.lev[l + 1]);
 
     // right-hand side, mean removal, scale
-    comp_div_coarse_kernel<<<nbc, 256, 0, s>>>(G, ux_c, uy_c, uz_c, ux_f, uy_f, uz_f, beta0_c, beta0_f, fc);
-    comp_div_fine_kernel<<<nbf, 256, 0, s>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, ff);
-    comp_rhs_kernel<<<nb, 256, 0, s>>>(G, fc, ff, beta0_c, sbar_c, beta0_f, sbar_f, part, nbc);
+    comp_div_coarse_kernel<<<nbc, 256, 0, s>>>(G, ux_c, uy_c, uz_c, ux_f, uy_f, uz_f, beta0_c, beta0_f, P.fc);
+    comp_div_fine_kernel<<<nbf, 256, 0, s>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, P.ff);
+    comp_rhs_kernel<<<nb, 256, 0, s>>>(G, P.fc, P.ff, beta0_c, sbar_c, beta0_f, sbar_f, part, nbc);
     comp_rhs_final_kernel<<<1, 1024, 0, s>>>(part, nb, dst, singular && o.remove_mean);
     if (singular && !o.remove_mean) {
         MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -817,7 +1091,7 @@ extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, co
         }
     }
     if (singular && o.remove_mean) {
-        comp_sub_mean_kernel<<<nb, 256, 0, s>>>(G, fc, ff, dst, part, nbc);
+        comp_sub_mean_kernel<<<nb, 256, 0, s>>>(G, P.fc, P.ff, dst, part, nbc);
         comp_rmax_kernel<<<1, 1024, 0, s>>>(part, nb, &dst->fnorm);
     }
     comp_scale_kernel<<<1, 1, 0, s>>>(dst);
@@ -826,25 +1100,39 @@ extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, co
         MX_CUDA(c, cudaMemsetAsync(phi_f, 0, sizeof(double) * Nf, s));
     }
 
-    // refinement loop
-    Hier<float> &HC = S.pc->H32;
-    for (;;) {
-        comp_apply_coarse_kernel<<<nbc, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, rcb, fc, part);
-        comp_apply_fine_kernel<<<nbf, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, rfb, ff,
-                                                   part + 3 * nbc);
-        comp_decide_kernel<<<1, 1024, 0, s>>>(part, nb, dst);
-        MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-        MX_CUDA(c, cudaStreamSynchronize(s));
-        if (c->hstate->done) break;
-        // coarse correction
-        comp_coarse_rhs_kernel<<<nbc, 256, 0, s>>>(G, rcb, rfb, dst, HC.lev[0].f);
-        vcycle(s, HC, o.nu1, o.nu2, o.bottom_iters, singular, nullptr, 0, zcap);
-        comp_coarse_update_kernel<<<nb, 256, 0, s>>>(G, phi_c, phi_f, HC.lev[0].e, dst, nbc);
-        // fine correction from the fine residual after it
-        comp_apply_fine_kernel<<<nbf, 256, 0, s>>>(G, rho_c, beta0_c, rho_f, beta0_f, phi_c, phi_f, rfb, ff, nullptr);
-        comp_fine_rhs_kernel<<<nbf, 256, 0, s>>>(Nf, rfb, dst, HF.lev[0].f);
-        vcycle(s, HF, o.nu1, o.nu2, o.bottom_iters, 0, nullptr, 0, zcap);
-        comp_fine_update_kernel<<<nbf, 256, 0, s>>>(Nf, phi_f, HF.lev[0].e, dst);
+    // first residual, then the refinement loop (a conditional graph, or from the host)
+    comp_resid_coarse_kernel<<<nbc, 256, 0, s>>>(G, P.B, phi_c, phi_f, P.fc, P.rcb, part);
+    comp_resid_fine_kernel<<<nbf, 256, 0, s>>>(G, P.B, phi_c, phi_f, P.ff, P.rfb, part + 3 * nbc);
+    comp_decide_kernel<<<1, 1024, 0, s>>>(part, nb, dst);
+    MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MX_CUDA(c, cudaStreamSynchronize(s));
+    if (!c->hstate->done) {
+        if (o.use_graph) {
+            if (!P.graph || P.k_pc != phi_c || P.k_pf != phi_f || P.k_part != part || P.k_nu1 != o.nu1 ||
+                P.k_nu2 != o.nu2 || P.k_bot != o.bottom_iters || P.k_zcap != zcap) {
+                if (P.graph) {
+                    cudaGraphExecDestroy(P.graph);
+                    P.graph = nullptr;
+                }
+                st = capture_while_graph(c, &P.graph, [&](cudaStream_t cs) { comp_body(cs, c, P, phi_c, phi_f, o, zcap); });
+                if (st) return st;
+                P.k_pc = phi_c;
+                P.k_pf = phi_f;
+                P.k_part = part;
+                P.k_nu1 = o.nu1;
+                P.k_nu2 = o.nu2;
+                P.k_bot = o.bottom_iters;
+                P.k_zcap = zcap;
+            }
+            MX_CUDA(c, cudaGraphLaunch(P.graph, s));
+        } else {
+            for (;;) {
+                comp_body(s, c, P, phi_c, phi_f, o, zcap);
+                MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+                MX_CUDA(c, cudaStreamSynchronize(s));
+                if (c->hstate->done) break;
+            }
+        }
     }
 
     // normalisation (zero volume-weighted mean of the unknowns when singular), the
@@ -855,15 +1143,14 @@ extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, co
         comp_phi_fine_shift_kernel<<<nbf, 256, 0, s>>>(Nf, phi_f, &dst->aux);
     }
     comp_phi_coarse_final_kernel<<<nbc, 256, 0, s>>>(G, phi_c, phi_f, singular ? &dst->aux : nullptr);
-    double *uc[3] = {ux_c, uy_c, uz_c}, *uf[3] = {ux_f, uy_f, uz_f};
     for (int d = 0; d < 3; d++) {
         comp_correct_coarse_kernel<<<nbc, 256, 0, s>>>(G, d, uc[d], phi_c, rho_c);
         comp_correct_fine_kernel<<<nbf, 256, 0, s>>>(G, d, uf[d], phi_c, phi_f, rho_c, rho_f);
     }
     for (int d = 0; d < 3; d++) comp_face_mean_kernel<<<nbc, 256, 0, s>>>(G, d, uc[d], uf[d]);
-    comp_div_coarse_kernel<<<nbc, 256, 0, s>>>(G, ux_c, uy_c, uz_c, ux_f, uy_f, uz_f, beta0_c, beta0_f, rcb);
-    comp_div_fine_kernel<<<nbf, 256, 0, s>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, rfb);
-    comp_divcheck_kernel<<<nb, 256, 0, s>>>(G, rcb, rfb, beta0_c, sbar_c, beta0_f, sbar_f, dst, part, nbc);
+    comp_div_coarse_kernel<<<nbc, 256, 0, s>>>(G, ux_c, uy_c, uz_c, ux_f, uy_f, uz_f, beta0_c, beta0_f, P.rcb);
+    comp_div_fine_kernel<<<nbf, 256, 0, s>>>(G, ux_f, uy_f, uz_f, beta0_c, beta0_f, P.rfb);
+    comp_divcheck_kernel<<<nb, 256, 0, s>>>(G, P.rcb, P.rfb, beta0_c, sbar_c, beta0_f, sbar_f, dst, part, nbc);
     comp_rmax_kernel<<<1, 1024, 0, s>>>(part, nb, &dst->div_err);
     MX_CUDA(c, cudaEventRecord(c->ev1, s));
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, dst, sizeof(SolveState), cudaMemcpyDeviceToHost, s));

@@ -112,6 +112,7 @@ struct mx_ctx {
     size_t split_tab_bytes = 0;
     void *split_cells = nullptr;         // velocity split: the S - Sbar bracket
     size_t split_cells_bytes = 0;
+    void *comp = nullptr;                // composite projection: the last geometry's plans and graph
     long long use_counter = 0;
     // tracing (mx_profile_enable)
     bool prof = false;

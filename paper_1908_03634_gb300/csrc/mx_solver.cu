@@ -19,6 +19,7 @@ void destroy_nodal_plans(mx_ctx *c);
 void destroy_batch_plan(mx_ctx *c);
 void destroy_radial_plans(mx_ctx *c);
 void destroy_split_scratch(mx_ctx *c);
+void destroy_comp_plan(mx_ctx *c);
 
 // ------------------------------------------------------------------------------
 // plans
@@ -174,6 +175,7 @@ void destroy_plans(mx_ctx *c) {
     destroy_batch_plan(c);
     destroy_radial_plans(c);
     destroy_split_scratch(c);
+    destroy_comp_plan(c);
 }
 
 // ------------------------------------------------------------------------------
