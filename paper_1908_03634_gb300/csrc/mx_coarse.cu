@@ -360,6 +360,8 @@ __device__ void coarse_body(const CoarseArgs<T> &A) {
 
 template <typename T>
 __global__ void __launch_bounds__(CT) coarse_vcycle_kernel(CoarseArgs<T> A) {
+    pdl_trigger();
+    pdl_wait();
     coarse_body(A);
 }
 
@@ -398,7 +400,7 @@ void k_coarse_vcycle(cudaStream_t s, const Level<T> *levs, int nl, int nu1, int 
     A.bot_iters = bot_iters;
     A.singular = singular;
     const size_t smem = coarse_smem_bytes(levs, nl);
-    coarse_vcycle_kernel<T><<<1, CT, smem, s>>>(A);
+    launch_pdl(coarse_vcycle_kernel<T>, dim3(1), dim3(CT), smem, s, A);
 }
 
 // Allow the coarse kernels more than the default 48 KB of dynamic shared

@@ -503,6 +503,8 @@ template <bool UPDATE>
 __global__ void __launch_bounds__(DF_THREADS)
     df_resid_tile_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
                          const SolveState *st, float ih2, double *part) {
+    pdl_trigger();
+    pdl_wait();
     const float *ee = (UPDATE && e_odd && (st->iter & 1)) ? e_odd : e;
     df_resid_body<UPDATE>(L, D, ee, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -542,8 +544,41 @@ void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const
     const DGeom &g = L0.g;
     const float ih2 = float(1.0 / (g.h * g.h));
     dim3 grid((g.n[0] + DX - 1) / DX, (g.n[1] + DY - 1) / DY, (g.n[2] + DZ - 1) / DZ);
-    if (e) df_resid_tile_kernel<true><<<grid, DF_THREADS, 0, s>>>(L0, D, e, e_odd, st, ih2, partials);
-    else df_resid_tile_kernel<false><<<grid, DF_THREADS, 0, s>>>(L0, D, nullptr, nullptr, st, ih2, partials);
+    if (e) launch_pdl(df_resid_tile_kernel<true>, grid, dim3(DF_THREADS), 0, s, L0, D, e, e_odd, st, ih2, partials);
+    else launch_pdl(df_resid_tile_kernel<false>, grid, dim3(DF_THREADS), 0, s, L0, D, (const float *)nullptr,
+                    (const float *)nullptr, st, ih2, partials);
+}
+
+// The first residual of a solve from phi = 0 is f itself: rhat = (h^2 f) c_hat
+// evaluated as the residual kernel would (every flux term is exactly 0 there),
+// so the results are bit-identical without the stencil pass; partials on
+// df_resid_blocks blocks like the residual kernel's.
+__global__ void df_resid_zero_kernel(long long n, const float *__restrict__ fh, const float *__restrict__ fl,
+                                     float *__restrict__ rhat, const SolveState *st, float ih2, double *part) {
+    const float c_hat = ih2 * st->inv_scale_f;
+    float mx = 0.f, s2f = 0.f, s1f = 0.f;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        float Rh, Re;
+        two_sum(fh[q], -0.f, Rh, Re);
+        Re += fl[q] - 0.f;
+        const float rh = (Rh + Re) * c_hat;
+        rhat[q] = rh;
+        mx = nmaxf(mx, fabsf(rh));
+        s2f = fmaf(rh, rh, s2f);
+        s1f += rh;
+    }
+    block_red3f(mx, s2f, s1f);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = double(mx);
+        part[3 * blockIdx.x + 1] = double(s2f);
+        part[3 * blockIdx.x + 2] = double(s1f);
+    }
+}
+
+void k_df_resid_zero(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials) {
+    const DGeom &g = L0.g;
+    df_resid_zero_kernel<<<df_resid_blocks(g), DF_THREADS, 0, s>>>(g.N, D.fh, D.fl, L0.f, st, float(1.0 / (g.h * g.h)),
+                                                                  partials);
 }
 
 // final phi (double) from the current double-float buffer (selected by the

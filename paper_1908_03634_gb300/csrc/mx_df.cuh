@@ -36,6 +36,8 @@ void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float 
 void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
                 double *partials, const float *e_odd = nullptr);
 int df_resid_blocks(const DGeom &g);
+// the residual of phi = 0 (r = f), bit-identical to k_df_resid's there, without the stencil
+void k_df_resid_zero(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials);
 dim3 df_resid_grid(const DGeom &g);
 
 // one box of the batched refinement loop

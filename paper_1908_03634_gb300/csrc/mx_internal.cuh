@@ -84,6 +84,30 @@ __device__ __forceinline__ float nmaxf(float a, float b) {
     return r;
 }
 
+// Programmatic dependent launch.  The V-cycle's kernels are launched with
+// launch_pdl: the next kernel of the stream may be scheduled while the current
+// one drains (its blocks become resident once every block of the current one
+// has called pdl_trigger), and waits in pdl_wait -- its first statement -- until
+// the current kernel has finished and its writes are visible.  Results are
+// those of plain stream order; the launch gaps between the short kernels of the
+// coarse levels shrink.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct MacPlan;
 struct NodalPlan;
 struct BatchPlan;

@@ -130,6 +130,8 @@ __device__ void decide(SolveState *st, double a, double b, double c) {
 }
 
 __global__ void finalize_residual_kernel(const double *part, int nb, SolveState *st, int scaled) {
+    pdl_trigger();
+    pdl_wait();
     double a, b, c;
     reduce_partials3(part, nb, a, b, c);
     if (flat_tid() == 0) {
@@ -144,7 +146,7 @@ __global__ void finalize_residual_kernel(const double *part, int nb, SolveState 
 }
 
 void k_finalize_residual(cudaStream_t s, const double *partials, int nb, SolveState *st, int scaled) {
-    finalize_residual_kernel<<<1, 1024, 0, s>>>(partials, nb, st, scaled);
+    launch_pdl(finalize_residual_kernel, dim3(1), dim3(1024), 0, s, partials, nb, st, scaled);
 }
 
 // one block per box: partials [off[b], off[b] + cnt[b]) of r / scale; boxes
@@ -213,6 +215,8 @@ __device__ __forceinline__ void rbgs_body(const Level<T> &L, int colour, T h2, i
 // order changes no result.
 template <typename T>
 __global__ void rbgs_kernel(Level<T> L, int colour, T h2, int zero, int zc) {
+    pdl_trigger();
+    pdl_wait();
     const int bz = colour ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
     rbgs_body(L, colour, h2, zero, blockIdx.x, blockIdx.y, bz, threadIdx.x, threadIdx.y, zc);
 }
@@ -242,7 +246,7 @@ template <typename T>
 void k_rbgs(cudaStream_t s, const Level<T> &L, int colour, int zero, int zcap) {
     const DGeom &g = L.g;
     const int zc = rbgs_zc(g, zcap);
-    rbgs_kernel<T><<<rbgs_grid(g, zc), dim3(SX, SY), 0, s>>>(L, colour, T(g.h * g.h), zero, zc);
+    launch_pdl(rbgs_kernel<T>, rbgs_grid(g, zc), dim3(SX, SY), 0, s, L, colour, T(g.h * g.h), zero, zc);
 }
 
 // Coarse RHS = average of the 8 fine residuals f - L e.
@@ -274,6 +278,8 @@ __device__ __forceinline__ void resid_restrict_body(const Level<T> &F, const Lev
 
 template <typename T>
 __global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2, int zc) {
+    pdl_trigger();
+    pdl_wait();
     resid_restrict_body(F, Cl, ih2, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, zc);
 }
 
@@ -295,7 +301,8 @@ template <typename T>
 void k_resid_restrict(cudaStream_t s, const Level<T> &fine, const Level<T> &coarse, int zcap) {
     const double h = fine.g.h;
     const int zc = stencil_zc(coarse.g, zcap);
-    resid_restrict_kernel<T><<<stencil_grid_zc(coarse.g, zc), dim3(SX, SY), 0, s>>>(fine, coarse, T(1.0 / (h * h)), zc);
+    launch_pdl(resid_restrict_kernel<T>, stencil_grid_zc(coarse.g, zc), dim3(SX, SY), 0, s, fine, coarse,
+               T(1.0 / (h * h)), zc);
 }
 
 // e_fine += e_coarse(parent)
@@ -316,6 +323,8 @@ __device__ __forceinline__ void prolong_body(const Level<T> &Cl, const Level<T> 
 
 template <typename T>
 __global__ void prolong_kernel(Level<T> Cl, Level<T> F, int zc) {
+    pdl_trigger();
+    pdl_wait();
     prolong_body(Cl, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, zc);
 }
 
@@ -335,7 +344,7 @@ void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work,
 template <typename T>
 void k_prolong(cudaStream_t s, const Level<T> &coarse, const Level<T> &fine, int zcap) {
     const int zc = stencil_zc(fine.g, zcap);
-    prolong_kernel<T><<<stencil_grid_zc(fine.g, zc), dim3(SX, SY), 0, s>>>(coarse, fine, zc);
+    launch_pdl(prolong_kernel<T>, stencil_grid_zc(fine.g, zc), dim3(SX, SY), 0, s, coarse, fine, zc);
 }
 
 // y = L x on a level (unscaled by nothing: true operator, 1/h^2 included)
@@ -393,6 +402,8 @@ __device__ void bot_apply(const Level<T> &L, const T *x, T *y, T ih2) {
 
 template <typename T>
 __global__ void __launch_bounds__(BOT_THREADS) bottom_kernel(Level<T> L, T *scr, int iters, int singular, T ih2) {
+    pdl_trigger();
+    pdl_wait();
     const int n = int(L.g.N);
     T *x = L.e, *r = scr, *r0 = scr + n, *p = scr + 2 * n, *v = scr + 3 * n, *sv = scr + 4 * n, *tv = scr + 5 * n;
     T *bvec = scr + 6 * n;
@@ -469,7 +480,7 @@ __global__ void __launch_bounds__(BOT_THREADS) bottom_kernel(Level<T> L, T *scr,
 template <typename T>
 void k_bottom(cudaStream_t s, const Level<T> &L, T *scratch, int iters, int singular) {
     const double h = L.g.h;
-    bottom_kernel<T><<<1, BOT_THREADS, 0, s>>>(L, scratch, iters, singular, T(1.0 / (h * h)));
+    launch_pdl(bottom_kernel<T>, dim3(1), dim3(BOT_THREADS), 0, s, L, scratch, iters, singular, T(1.0 / (h * h)));
 }
 
 // ------------------------------------------------------------------------------

@@ -71,6 +71,8 @@ template <int MODE>
 __global__ void __launch_bounds__(RB_THREADS, 4)
     rbgs_march_kernel(Level<float> L, const float *__restrict__ ein, float *__restrict__ eout,
                       const float *__restrict__ ecoarse, int ncx, int ncy, float h2) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ __align__(16) float sp[NSLOT][PH][PW];
     const DGeom &g = L.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxy = nx * ny;
@@ -209,10 +211,7 @@ void k_rbgs_fused(cudaStream_t s, const Level<float> &L, const float *ein, float
     const float h2 = float(g.h * g.h);
     const float *ec = coarse ? coarse->e : nullptr;
     const int ncx = coarse ? coarse->g.n[0] : 0, ncy = coarse ? coarse->g.n[1] : 0;
-    if (mode == RB_ZERO)
-        rbgs_march_kernel<RB_ZERO><<<grid, RB_THREADS, 0, s>>>(L, ein, eout, ec, ncx, ncy, h2);
-    else if (mode == RB_PROLONG)
-        rbgs_march_kernel<RB_PROLONG><<<grid, RB_THREADS, 0, s>>>(L, ein, eout, ec, ncx, ncy, h2);
-    else
-        rbgs_march_kernel<RB_PLAIN><<<grid, RB_THREADS, 0, s>>>(L, ein, eout, ec, ncx, ncy, h2);
+    auto k = mode == RB_ZERO ? rbgs_march_kernel<RB_ZERO>
+             : mode == RB_PROLONG ? rbgs_march_kernel<RB_PROLONG> : rbgs_march_kernel<RB_PLAIN>;
+    launch_pdl(k, grid, dim3(RB_THREADS), 0, s, L, ein, eout, ec, ncx, ncy, h2);
 }

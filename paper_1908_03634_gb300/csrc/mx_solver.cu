@@ -318,15 +318,16 @@ static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, cons
 }
 
 template <typename T>
-static void ir_first_residual(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, int nb);
+static void ir_first_residual(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, int nb, int zero_phi);
 template <>
-void ir_first_residual<float>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, int nb) {
+void ir_first_residual<float>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, int nb, int zero_phi) {
     (void)nb;
-    k_df_resid(s, H.lev[0], P.D, nullptr, c->state, c->partials);
+    if (zero_phi) k_df_resid_zero(s, H.lev[0], P.D, c->state, c->partials);  // r = f
+    else k_df_resid(s, H.lev[0], P.D, nullptr, c->state, c->partials);
     k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
 }
 template <>
-void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, int nb) {
+void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, int nb, int) {
     k_residual64<double>(s, P.L64, phi, P.L64.f, H.lev[0].f, c->state, c->partials, nb);
     k_finalize_residual(s, c->partials, nb, c->state);
 }
@@ -419,7 +420,7 @@ static mx_status run_ir(mx_ctx *c, MacPlan &P, Hier<T> &H, double *phi, const mx
     cudaStream_t s = c->stream;
     const int nb = stencil_blocks(P.g);
     prof_begin(c, s, MX_PH_RESID64);
-    ir_first_residual<T>(s, c, P, H, phi, nb);
+    ir_first_residual<T>(s, c, P, H, phi, nb, !o.use_initial_guess);
     prof_end(c, s, MX_PH_RESID64, 2);
     if (o.use_graph && !c->prof) {
         // the loop is entered unconditionally by the while node; a first
