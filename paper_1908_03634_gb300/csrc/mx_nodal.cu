@@ -336,6 +336,8 @@ __global__ void nd_rhs_final_kernel(NGeom g, double *__restrict__ f, const Solve
 // f_C = (1/(8 w_C)) sum_n P(n, C) w_n r_n; coarse e = 0
 template <typename T>
 __global__ void nd_restrict_kernel(NLevel<T> F, NLevel<T> C) {
+    pdl_trigger();
+    pdl_wait();
     const NGeom &g = F.g, &gc = C.g;
     for (long long Q = blockIdx.x * (long long)blockDim.x + threadIdx.x; Q < gc.M; Q += (long long)gridDim.x * blockDim.x) {
         int A, B, Cc;
@@ -357,6 +359,8 @@ __global__ void nd_restrict_kernel(NLevel<T> F, NLevel<T> C) {
 // e_fine += trilinear interpolation of e_coarse
 template <typename T>
 __global__ void nd_prolong_kernel(NLevel<T> C, NLevel<T> F) {
+    pdl_trigger();
+    pdl_wait();
     const NGeom &g = F.g, &gc = C.g;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
         int a, b, c;
@@ -453,6 +457,8 @@ __device__ void nd_wmean0(const NGeom &g, T *x) {
 
 template <typename T>
 __global__ void __launch_bounds__(NBT) nd_bottom_kernel(NLevel<T> L, T *scr, int iters) {
+    pdl_trigger();
+    pdl_wait();
     const NGeom &g = L.g;
     const int n = int(g.M);
     T *x = L.e, *r = scr, *r0 = scr + n, *p = scr + 2 * n, *v = scr + 3 * n, *sv = scr + 4 * n, *tv = scr + 5 * n;
@@ -585,6 +591,8 @@ constexpr int NCZ = 16;  // z-chunk of the column kernels
 
 template <typename T, int MODE>  // MODE 0: Gauss-Seidel on one colour, 1: residual r = f - L e
 __global__ void nd_col_kernel(NLevel<T> L, int colour, int ncol_x, int ncol_y, int nzc) {
+    pdl_trigger();
+    pdl_wait();
     const NGeom &g = L.g;
     const int cx = colour & 1, cy = colour >> 1;
     const int tx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -638,14 +646,14 @@ static void k_nd_gs(cudaStream_t s, const NLevel<T> &L, int colour, int zcap) {
     const int ncx = (L.g.m[0] - cx + 1) / 2, ncy = (L.g.m[1] - cy + 1) / 2;
     const int zc = nd_zchunk((long long)((ncx + 63) / 64) * ncy, L.g.m[2], zcap);
     dim3 grid((ncx + 63) / 64, ncy, (L.g.m[2] + zc - 1) / zc);
-    nd_col_kernel<T, 0><<<grid, 64, 0, s>>>(L, colour, ncx, ncy, zc);
+    launch_pdl(nd_col_kernel<T, 0>, grid, dim3(64), 0, s, L, colour, ncx, ncy, zc);
 }
 
 template <typename T>
 static void k_nd_residual(cudaStream_t s, const NLevel<T> &L, int zcap) {
     const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2], zcap);
     dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
-    nd_col_kernel<T, 1><<<grid, 64, 0, s>>>(L, 0, L.g.m[0], L.g.m[1], zc);
+    launch_pdl(nd_col_kernel<T, 1>, grid, dim3(64), 0, s, L, 0, L.g.m[0], L.g.m[1], zc);
 }
 
 // ---- double-float residual of the refinement loop ------------------------------------
@@ -658,6 +666,8 @@ __device__ __forceinline__ void ts2(float a, float b, float &s, float &e) {
 // UPDATE: phi += scale e first (in place; nodes are updated by their own thread
 // only, and the residual pass is a separate launch).
 __global__ void nd_df_update_kernel(NDF D, long long M, const float *__restrict__ e, const SolveState *st) {
+    pdl_trigger();
+    pdl_wait();
     const float sh = st->scale_h, sl = st->scale_l;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
         const float ev = e[q];
@@ -722,6 +732,8 @@ __device__ __forceinline__ void load_df_cells(const NGeom &g, const ColMap &m, c
 // 12 w h^2 r = 12 w h^2 f - sum_m c_m (phi_m - phi_n) in double-float, node
 // columns marched in z; rhat = r / scale in FP32 with norm partials per block
 __global__ void nd_df_col_resid_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part) {
+    pdl_trigger();
+    pdl_wait();
     const NGeom &g = L0.g;
     const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     const int c0 = blockIdx.z * NCZ, c1 = min(c0 + NCZ, g.m[2]);
@@ -1240,21 +1252,21 @@ static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int
             prof_begin(pc, s, MX_PH_RESTRICT_FINE);
         }
         k_nd_residual(s, L[l], zcap);
-        nd_restrict_kernel<T><<<nblk(L[l + 1].g.M), 256, 0, s>>>(L[l], L[l + 1]);
+        launch_pdl(nd_restrict_kernel<T>, dim3(nblk(L[l + 1].g.M)), dim3(256), 0, s, L[l], L[l + 1]);
         if (l == 0) {
             prof_end(pc, s, MX_PH_RESTRICT_FINE, 2);
             prof_begin(pc, s, MX_PH_COARSE);
         }
     }
     if (nl == 1) prof_begin(pc, s, MX_PH_COARSE);
-    nd_bottom_kernel<T><<<1, NBT, 0, s>>>(L[nl - 1], bot, bot_iters);
+    launch_pdl(nd_bottom_kernel<T>, dim3(1), dim3(NBT), 0, s, L[nl - 1], bot, bot_iters);
     if (nl == 1) prof_end(pc, s, MX_PH_COARSE, 1);
     for (int l = nl - 2; l >= 0; l--) {
         if (l == 0) {
             prof_end(pc, s, MX_PH_COARSE, 0);
             prof_begin(pc, s, MX_PH_PROLONG_FINE);
         }
-        nd_prolong_kernel<T><<<nblk(L[l].g.M), 256, 0, s>>>(L[l + 1], L[l]);
+        launch_pdl(nd_prolong_kernel<T>, dim3(nblk(L[l].g.M)), dim3(256), 0, s, L[l + 1], L[l]);
         if (l == 0) {
             prof_end(pc, s, MX_PH_PROLONG_FINE, 1);
             prof_begin(pc, s, MX_PH_SMOOTH_FINE);
@@ -1352,7 +1364,8 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     // refinement loop: residual, then while not converged {V-cycle, update, residual}
     auto residual = [&](cudaStream_t ss, mx_ctx *pc) {
         prof_begin(pc, ss, MX_PH_RESID64);
-        if (mixed) nd_df_col_resid_kernel<<<nd_col_grid(g), 64, 0, ss>>>(P->L32[0], P->D, c->state, c->partials);
+        if (mixed) launch_pdl(nd_df_col_resid_kernel, nd_col_grid(g), dim3(64), 0, ss, P->L32[0], P->D,
+                              (const SolveState *)c->state, c->partials);
         else nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, ss>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f,
                                                                   c->state, c->partials);
         k_finalize_residual(ss, c->partials, nd_col_blocks(g), c->state, mixed ? 1 : 0);
@@ -1362,7 +1375,8 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         if (mixed) {
             nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc, zcap);
             prof_begin(pc, ss, MX_PH_UPDATE);
-            nd_df_update_kernel<<<nb, 256, 0, ss>>>(P->D, g.M, P->L32[0].e, c->state);
+            launch_pdl(nd_df_update_kernel, dim3(nb), dim3(256), 0, ss, P->D, (long long)g.M,
+                       (const float *)P->L32[0].e, (const SolveState *)c->state);
             prof_end(pc, ss, MX_PH_UPDATE, 1);
         } else {
             nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc, zcap);
