@@ -239,3 +239,27 @@ def test_nodal192_phi_parity_at_tuned_settings(mx):
     for d in range(3):
         scale = np.abs(u0[d]).max() + np.abs(u_pred[d] - u0[d]).max()
         assert np.abs(u[d] - u_pred[d]).max() <= 1e-12 * scale
+
+
+def test_planar256_two_pass_sweeps_bit_identical_to_single_pass(mx):
+    """At full size the solve with the two colour passes per sweep equals, bit
+    for bit, the one with the single-pass sweep kernel (red then black in one
+    pass over memory, with the prolongation applied on load)."""
+    w = W.planar256(device=DEV)
+    g = w.geom
+    ctx = mx.mx_create(0)
+    try:
+        beta0 = torch.empty(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+        mx.mx_fill_base_state(ctx, g, 0, w.prof_beta0, g.dx, (0.5, 0.5, 0.5), beta0)
+        out = []
+        for fused in (0, 1):
+            u = [t.clone() for t in w.u]
+            phi = torch.zeros(mx.cell_shape(g), dtype=torch.float64, device=DEV)
+            st, info = mx.mx_mac_project(ctx, g, *u, w.rho, beta0, w.sbar, phi,
+                                         mx.default_opts(nu1=2, nu2=3, fused=fused))
+            out.append((info["vcycles"], phi))
+        torch.cuda.synchronize()
+    finally:
+        mx.mx_destroy(ctx)
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1])
