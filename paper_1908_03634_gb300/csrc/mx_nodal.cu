@@ -51,6 +51,7 @@ struct NodalPlan {
     NLevel<double> L64[MX_MAXLEV];
     NDF D;
     double *sigma64 = nullptr, *f64 = nullptr;
+    float4 *cellp = nullptr;  // mixed: per cell beta0 (ux, uy, uz, Sbar) as double-float pairs (two float4)
     float *bot32 = nullptr;
     double *bot64 = nullptr;
     // CUDA graph of the refinement loop, keyed by what it was captured with
@@ -984,10 +985,28 @@ struct RhsLayerDF {
     int n;
 };
 
-__device__ __forceinline__ RhsLayerDF rhs_layer_df(const NGeom &g, const double *__restrict__ ux,
-                                                   const double *__restrict__ uy, const double *__restrict__ uz,
-                                                   const double *__restrict__ beta0, const double *__restrict__ sbar,
-                                                   int i0, int i1, int j0, int j1, int k) {
+// The products beta0 (ux, uy, uz, Sbar) of every cell in double-float, formed once
+// per cell (the node gather below adds them; forming them inside the gather did
+// the same work for each of the cell's four node columns): P[2c] = (beta0 ux,
+// beta0 uy), P[2c+1] = (beta0 uz, beta0 Sbar), each as (hi, lo).
+__device__ __forceinline__ void cell_products(const double *__restrict__ ux, const double *__restrict__ uy,
+                                              const double *__restrict__ uz, const double *__restrict__ beta0,
+                                              const double *__restrict__ sbar, long long c, float4 *__restrict__ P) {
+    const dfloat bt = df_split(beta0[c]);
+    const dfloat px = df_mul(bt, df_split(ux[c])), py = df_mul(bt, df_split(uy[c]));
+    const dfloat pz = df_mul(bt, df_split(uz[c])), ps = df_mul(bt, df_split(sbar[c]));
+    P[2 * c] = make_float4(px.h, px.l, py.h, py.l);
+    P[2 * c + 1] = make_float4(pz.h, pz.l, ps.h, ps.l);
+}
+__global__ void nd_cell_prod_kernel(long long N, const double *__restrict__ ux, const double *__restrict__ uy,
+                                    const double *__restrict__ uz, const double *__restrict__ beta0,
+                                    const double *__restrict__ sbar, float4 *__restrict__ P) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x)
+        cell_products(ux, uy, uz, beta0, sbar, q, P);
+}
+// rhs_layer_df from the formed products: the same additions in the same order
+__device__ __forceinline__ RhsLayerDF rhs_layer_pre(const NGeom &g, const float4 *__restrict__ P, int i0, int i1,
+                                                    int j0, int j1, int k) {
     RhsLayerDF L = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, 0};
     const int kk = cell_wrap(g, 2, k);
     if (kk < 0) return L;
@@ -997,13 +1016,13 @@ __device__ __forceinline__ RhsLayerDF rhs_layer_df(const NGeom &g, const double 
         for (int ii = 0; ii < 2; ii++) {
             const int i = ii ? i1 : i0;
             if (i < 0) continue;
-            const int c = i + g.n[0] * (j + g.n[1] * kk);
-            const dfloat bt = df_split(beta0[c]);
-            const dfloat px = df_mul(bt, df_split(ux[c])), py = df_mul(bt, df_split(uy[c]));
+            const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * kk);
+            const float4 a = P[2 * c], b = P[2 * c + 1];
+            const dfloat px = {a.x, a.y}, py = {a.z, a.w}, pz = {b.x, b.y}, ps = {b.z, b.w};
             L.x = df_add(L.x, ii ? px : df_neg(px));
             L.y = df_add(L.y, jj ? py : df_neg(py));
-            L.z = df_add(L.z, df_mul(bt, df_split(uz[c])));
-            L.s = df_add(L.s, df_mul(bt, df_split(sbar[c])));
+            L.z = df_add(L.z, pz);
+            L.s = df_add(L.s, ps);
             L.n++;
         }
     }
@@ -1014,10 +1033,9 @@ __device__ __forceinline__ dfloat df_scale(dfloat a, float p2) { return dfloat{a
 
 // the gather of nd_rhs_col_kernel in double-float: f (may be null) as (fh, fl),
 // partials (max |f|, sum w f, sum w); i4h8 = 8/(4h)
-__global__ void nd_rhs_col_df_kernel(NGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
-                                     const double *__restrict__ uz, const double *__restrict__ beta0,
-                                     const double *__restrict__ sbar, float *__restrict__ fh, float *__restrict__ fl,
-                                     double *part, int sub_mean, const SolveState *st, dfloat i4h8) {
+__global__ void nd_rhs_col_df_kernel(NGeom g, const float4 *__restrict__ P, float *__restrict__ fh,
+                                     float *__restrict__ fl, double *part, int sub_mean, const SolveState *st,
+                                     dfloat i4h8) {
     float s0 = 0.f;
     dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
     const int a = blockIdx.x * 32 + threadIdx.x, b = blockIdx.y * 8 + threadIdx.y;
@@ -1026,9 +1044,9 @@ __global__ void nd_rhs_col_df_kernel(NGeom g, const double *__restrict__ ux, con
         const dfloat cm = sub_mean ? df_split(st->mean) : dfloat{0.f, 0.f};
         const int i0 = cell_wrap(g, 0, a - 1), i1 = cell_wrap(g, 0, a);
         const int j0 = cell_wrap(g, 1, b - 1), j1 = cell_wrap(g, 1, b);
-        RhsLayerDF lo = rhs_layer_df(g, ux, uy, uz, beta0, sbar, i0, i1, j0, j1, c0 - 1);
+        RhsLayerDF lo = rhs_layer_pre(g, P, i0, i1, j0, j1, c0 - 1);
         for (int c = c0; c < c1; c++) {
-            const RhsLayerDF hi = rhs_layer_df(g, ux, uy, uz, beta0, sbar, i0, i1, j0, j1, c);
+            const RhsLayerDF hi = rhs_layer_pre(g, P, i0, i1, j0, j1, c);
             const int cnt = lo.n + hi.n;  // 1, 2, 4 or 8
             const float ic = cnt == 8 ? 0.125f : cnt == 4 ? 0.25f : cnt == 2 ? 0.5f : 1.f;
             const dfloat div = df_add(df_add(df_add(lo.x, hi.x), df_add(lo.y, hi.y)), df_sub(hi.z, lo.z));
@@ -1105,8 +1123,11 @@ __global__ void nd_df_final_sum_kernel(NGeom g, NDF D, double *__restrict__ phi,
 
 // U -= G_c phi / rho per cell from phi's double-float pair (the weighted mean
 // of phi cancels in the edge differences), in double-float
+// (also forms the cell products of the corrected U for the divergence check)
 __global__ void nd_correct_df_kernel(NGeom g, const double *__restrict__ rho, NDF D, double *__restrict__ ux,
-                                     double *__restrict__ uy, double *__restrict__ uz, dfloat i4h) {
+                                     double *__restrict__ uy, double *__restrict__ uz, dfloat i4h,
+                                     const double *__restrict__ beta0, const double *__restrict__ sbar,
+                                     float4 *__restrict__ P) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     const int k0 = blockIdx.z * NRZ, k1 = min(k0 + NRZ, g.n[2]);
     if (i >= g.n[0] || j >= g.n[1]) return;
@@ -1137,6 +1158,7 @@ __global__ void nd_correct_df_kernel(NGeom g, const double *__restrict__ rho, ND
         ux[c] = df_to_double(df_sub(df_split(ux[c]), df_mul(gx, f)));
         uy[c] = df_to_double(df_sub(df_split(uy[c]), df_mul(gy, f)));
         uz[c] = df_to_double(df_sub(df_split(uz[c]), df_mul(gz, f)));
+        cell_products(ux, uy, uz, beta0, sbar, c, P);
         for (int e = 0; e < 4; e++) lo[e] = hi[e];
     }
 }
@@ -1183,6 +1205,7 @@ static void carve_nodal(Bump &b, NodalPlan &P) {
         P.D.fl = b.take<float>(P.g.M);
         P.D.ph = b.take<float>(P.g.M);
         P.D.pl = b.take<float>(P.g.M);
+        P.cellp = b.take<float4>(2 * P.g.N);
         P.sigma64 = nullptr;
     } else {
         P.bot64 = b.take<double>(6 * Mb);
@@ -1325,10 +1348,11 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     prof_begin(c, s, MX_PH_SETUP);
     if ((st = nodal_setup(c, *P, rho, beta0))) return st;
     const bool mixed = o.prec == MX_PREC_MIXED;
-    if (mixed)
-        nd_rhs_col_df_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, P->D.fh, P->D.fl,
-                                                                    c->partials, 0, c->state, df_host(2.0 / g.h));
-    else
+    if (mixed) {
+        nd_cell_prod_kernel<<<nblk(g.N), 256, 0, s>>>(g.N, ux, uy, uz, beta0, sbar, P->cellp);
+        nd_rhs_col_df_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, P->cellp, P->D.fh, P->D.fl, c->partials, 0,
+                                                                    c->state, df_host(2.0 / g.h));
+    } else
         nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, P->f64, c->partials, 0,
                                                                  c->state, 0.25 / g.h);
     nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nd_node_blocks(g), c->state, o.remove_mean, 0);
@@ -1427,12 +1451,14 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     }
     nd_wmean_finalize_kernel<<<1, 1024, 0, s>>>(c->partials, nb, &c->state->aux);
     k_sub_scalar(s, g.M, phi, &c->state->aux);
-    if (mixed) nd_correct_df_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, P->D, ux, uy, uz, df_host(0.25 / g.h));
+    if (mixed)
+        nd_correct_df_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, P->D, ux, uy, uz, df_host(0.25 / g.h), beta0, sbar,
+                                                          P->cellp);
     else nd_correct_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, phi, ux, uy, uz, 0.25 / g.h);
     // divergence of the projected velocity minus Sbar_n minus c: the RHS gather with the mean subtracted
     if (mixed)
-        nd_rhs_col_df_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, nullptr,
-                                                                    c->partials, 1, c->state, df_host(2.0 / g.h));
+        nd_rhs_col_df_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, P->cellp, nullptr, nullptr, c->partials, 1,
+                                                                    c->state, df_host(2.0 / g.h));
     else
         nd_rhs_col_kernel<<<nd_node_grid(g), dim3(32, 8), 0, s>>>(g, ux, uy, uz, beta0, sbar, nullptr, c->partials,
                                                                  1, c->state, 0.25 / g.h);
