@@ -54,9 +54,10 @@ def parse():
                    help="planar256: the headline line (+ nodal384 and batched96 extras); star512: the "
                         "full-star line; nodal-sweep: one line per nodal size 64^3..512^3; nodal384 / "
                         "batched96 / average512: that extra alone (for profiling)")
-    p.add_argument("--fixed", default=None, metavar="NU1,NU2,TILE_Z",
+    p.add_argument("--fixed", default=None, metavar="NU1,NU2,TILE_Z[,SMOOTHER]",
                    help="skip the autotuner and use these smoother settings (for profiling a fixed "
-                        "configuration, e.g. the tuned one)")
+                        "configuration, e.g. the tuned one); SMOOTHER (nodal384 only): 0 four-colour "
+                        "Gauss-Seidel, 1 Chebyshev")
     p.add_argument("--no-graph", action="store_true",
                    help="run the refinement loop from the host (same kernels; for profilers that "
                         "cannot see inside conditional CUDA graphs)")
@@ -533,8 +534,8 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     phi = torch.zeros(mx.node_shape(g), dtype=torch.float64, device=dev)
     us = [[t.clone() for t in w.u] for _ in range(steps + warmup)]
     if fixed:
-        a, b, z = (int(x) for x in fixed.split(","))
-        tuned = mx.default_opts(use_graph=int(graph), nu1=a, nu2=b, tile_z=z)
+        a, b, z, *sm = (int(x) for x in fixed.split(","))
+        tuned = mx.default_opts(use_graph=int(graph), nu1=a, nu2=b, tile_z=z, smoother=sm[0] if sm else 0)
         opts = tuned
     else:
         tuned, _ = mx.mx_autotune(ctx, mx.MX_OP_NODAL, g, *w.u, w.rho, beta0, w.sbar,
@@ -552,10 +553,11 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
     run(ut, opts)
     trace = {k: {"ms": v[0], "launches": v[1]} for k, v in mx.mx_profile_read(ctx).items()}
     mx.mx_profile_enable(ctx, False)
-    # model bytes per V-cycle at the timed sweep counts (FP32): a sweep reads phi, f,
-    # sigma and writes phi (4w/node), residual+restriction 3.125w, prolongation
-    # 2.125w on every level (N_total = 8/7 N), + the double-float residual and update
-    # of the refinement loop (phi 8 read + 8 write, f 8, sigma 8, rhat 4)
+    # model bytes per V-cycle at the timed sweep counts (FP32): a sweep (four-colour
+    # Gauss-Seidel) or a step (Chebyshev) reads phi, f, sigma and writes phi
+    # (4w/node), residual+restriction 3.125w, prolongation 2.125w on every level
+    # (N_total = 8/7 N), + the double-float residual and update of the refinement
+    # loop (phi 8 read + 8 write, f 8, sigma 8, rhat 4)
     nu1, nu2 = tuned.nu1, tuned.nu2
     model = nodes * (8.0 / 7.0) * 4 * (4 * (nu1 + nu2) + 3.125 + 2.125) + nodes * 36
     ms_solve = ms / steps
@@ -568,10 +570,11 @@ def bench_nodal(mx, W, ctx, dev, stream, n=384, steps=3, warmup=2, fp64=True, hb
            "hbm_frac_per_vcycle": round(model / (ms_solve / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
            "hbm_frac_per_vcycle_loop_only": round(model / (loop_ms / max(vc, 1) * 1e-3) / 1e9 / hbm, 4),
            "model_bytes_per_vcycle": model, "model_nu": [nu1, nu2], "phases": trace,
-           "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z}}
+           "tuned": {"nu1": tuned.nu1, "nu2": tuned.nu2, "tile_z": tuned.tile_z,
+                     "smoother": "chebyshev" if tuned.smoother else "gauss-seidel-4colour"}}
     if fp64:
         o64 = mx.default_opts(prec=mx.MX_PREC_FP64, use_graph=int(graph), nu1=tuned.nu1, nu2=tuned.nu2,
-                              tile_z=tuned.tile_z)
+                              tile_z=tuned.tile_z, smoother=tuned.smoother)
         u64 = [t.clone() for t in w.u]
         run(u64, o64)
         for d in range(3):

@@ -71,9 +71,10 @@ typedef struct {
 
 /* Solver options.  mx_default_opts() fills: rel_tol 1e-10, max_outer 100,
  * max_vcycles 100, prec MX_PREC_MIXED, remove_mean 1, use_initial_guess 0,
- * use_graph 1, nu1 = nu2 = 2, bottom_iters 200, fused 0, tile_z 0, krylov 0.
+ * use_graph 1, nu1 = nu2 = 2, bottom_iters 200, fused 0, tile_z 0, krylov 0, smoother 0.
  * nu1 = nu2 = 0 selects the setting mx_autotune() stored in the context for
- * this operator, precision and geometry (nu1, nu2, fused, tile_z), or
+ * this operator, precision and geometry (nu1, nu2, fused, tile_z; nodal: also
+ * smoother), or
  * 2, 2, fused, tile_z as given when nothing is stored. */
 typedef struct {
     double rel_tol;        /* stop when ||f - L phi||_inf <= rel_tol ||f||_inf */
@@ -100,6 +101,14 @@ typedef struct {
                               double-float after every step, so the attainable accuracy is
                               that of refinement.  Other solves reject krylov = 1
                               (MX_ERR_ARG). */
+    int smoother;          /* nodal solves: 0 = four-colour Gauss-Seidel (default; nu1, nu2
+                              sweeps of four colour passes); 1 = Chebyshev smoothing:
+                              nu1 / nu2 steps e <- e + w_k D^-1 (f - L e) of one pass each,
+                              the weights w_k the inverse roots of one Chebyshev polynomial
+                              of degree nu1 + nu2 on [0.4, 1.5] (post-smoothing the nu2
+                              largest roots, pre-smoothing the others); 1.5 bounds the
+                              spectrum of D^-1 L for every positive coefficient field.
+                              MAC, batched and composite solves reject 1 (MX_ERR_ARG). */
 } mx_opts;
 
 typedef struct {
@@ -343,15 +352,16 @@ mx_status mx_profile_read(mx_ctx *ctx, double *ms, long long *launches);
  * mx_nodal_project, same argument layouts) under candidate smoother and tile
  * settings -- sweep counts (nu1, nu2) in {1..4}, then tile_z in {4, 8, 16}
  * (nodal {4, 8, 16, default}), then (MAC, mixed precision) the single-pass
- * sweep -- one at a time from base (NULL = defaults), keeping a change only if
+ * sweep or (nodal, base smoother 0) the Chebyshev smoother at degrees (nu1,
+ * nu2) in {1..3} -- one at a time from base (NULL = defaults), keeping a change only if
  * the solve converges and is faster (CUDA-event time of a whole call, after
  * one untimed call that builds the graph).  Candidates needing more than
  * 3 x (the best's V-cycles) + 4 V-cycles are cut off.  The winner is stored in
  * the context's tune cache for (op, prec, geometry) and used by later calls
  * with nu1 = nu2 = 0.  The inputs are not modified: the tuner copies U and
  * phi into scratch it allocates and frees (about 4 fields of device memory).
- * best (may be NULL): the chosen options (base with nu1, nu2, fused, tile_z
- * replaced); ms_best (may be NULL): the tuned solve's time in ms.  Returns
+ * best (may be NULL): the chosen options (base with nu1, nu2, fused, tile_z,
+ * smoother replaced); ms_best (may be NULL): the tuned solve's time in ms.  Returns
  * MX_ERR_NOCONV if no candidate converges, MX_ERR_OOM if the scratch cannot
  * be allocated, or the error of the first failing solve. */
 mx_status mx_autotune(mx_ctx *ctx, int op, const mx_geom *geom, const double *ux, const double *uy,

@@ -32,7 +32,7 @@ class mx_opts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("max_outer", C.c_int), ("max_vcycles", C.c_int), ("prec", C.c_int),
                 ("remove_mean", C.c_int), ("use_initial_guess", C.c_int), ("use_graph", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("bottom_iters", C.c_int), ("fused", C.c_int),
-                ("tile_z", C.c_int), ("krylov", C.c_int)]
+                ("tile_z", C.c_int), ("krylov", C.c_int), ("smoother", C.c_int)]
 
 
 class mx_info(C.Structure):
@@ -387,7 +387,7 @@ def mx_nodal_project(ctx, geom, ux, uy, uz, rho, beta0, sbar, phi_nodes, opts=No
 
 
 def mx_autotune(ctx, op, geom, ux, uy, uz, rho, beta0, sbar, base=None):
-    """Tune (nu1, nu2, tile_z, fused) on these inputs (left unmodified); returns
+    """Tune (nu1, nu2, tile_z, fused; nodal: smoother) on these inputs (left unmodified); returns
     (chosen mx_opts, ms of the tuned solve).  The choice is cached in ctx for
     calls with nu1 = nu2 = 0."""
     g = make_geom(geom)

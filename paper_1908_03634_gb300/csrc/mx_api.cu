@@ -214,6 +214,7 @@ void mx_default_opts(mx_opts *o) {
     o->fused = 0;
     o->tile_z = 0;
     o->krylov = 0;
+    o->smoother = 0;
 }
 
 int mx_device_supported(int device) {

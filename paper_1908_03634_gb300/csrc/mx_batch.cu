@@ -294,6 +294,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
     mx_opts o;
     if ((st = check_opts(c, opts, o))) return st;
     if (o.krylov) return set_err(c, MX_ERR_ARG, "batched: krylov = 1 is for single MAC solves");
+    if (o.smoother) return set_err(c, MX_ERR_ARG, "batched: smoother = 1 (Chebyshev) is for nodal solves");
     tune_apply_batch(c, nbox, geoms, o);
     std::vector<DGeom> g(nbox);
     for (int b = 0; b < nbox; b++) {

@@ -1039,8 +1039,8 @@ extern "C" mx_status mx_mac_project_composite(mx_ctx *c, const mx_geom *geom, co
         return set_err(c, MX_ERR_ARG, "mac_project_composite: null array");
     mx_opts o;
     if ((st = check_opts(c, opts, o))) return st;
-    if (o.prec != MX_PREC_MIXED || o.krylov)
-        return set_err(c, MX_ERR_ARG, "mac_project_composite: prec must be MX_PREC_MIXED and krylov 0");
+    if (o.prec != MX_PREC_MIXED || o.krylov || o.smoother)
+        return set_err(c, MX_ERR_ARG, "mac_project_composite: prec must be MX_PREC_MIXED, krylov and smoother 0");
     if (o.nu1 == 0 && o.nu2 == 0) o.nu1 = o.nu2 = 2;
     const int zcap = o.tile_z ? o.tile_z : 8;
     cudaStream_t s = c->stream;

@@ -123,7 +123,7 @@ struct mx_ctx {
     int max_partials = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // tune cache (mx_autotune): the fastest setting per operator, precision and geometry
-    struct Tune { int op, prec, n[3], lo[3], hi[3], nu1, nu2, fused, tile_z; double ms; };
+    struct Tune { int op, prec, n[3], lo[3], hi[3], nu1, nu2, fused, tile_z, smoother; double ms; };
     std::vector<Tune> tune;
     std::vector<MacPlan *> plans;        // cached workspaces, one per geometry/precision
     std::vector<NodalPlan *> nplans;

@@ -34,6 +34,7 @@ struct NLevel {
     NGeom g;
     T *sigma;     // cells
     T *f, *e, *r; // nodes (r: residual scratch of the restriction)
+    T *e2;        // second correction buffer (the Chebyshev steps alternate e <-> e2)
 };
 
 struct NDF {             // double-float arrays of the finest level
@@ -57,7 +58,7 @@ struct NodalPlan {
     // CUDA graph of the refinement loop, keyed by what it was captured with
     cudaGraphExec_t graph = nullptr;
     const void *graph_phi = nullptr;
-    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_tilez = -1;
+    int graph_nu1 = -1, graph_nu2 = -1, graph_bot = -1, graph_tilez = -1, graph_smoother = -1;
     long long last_use = 0;
 };
 
@@ -357,9 +358,9 @@ __global__ void nd_restrict_kernel(NLevel<T> F, NLevel<T> C) {
     }
 }
 
-// e_fine += trilinear interpolation of e_coarse
+// e_fine += trilinear interpolation of e_coarse (out non-null: out = e_fine + it)
 template <typename T>
-__global__ void nd_prolong_kernel(NLevel<T> C, NLevel<T> F) {
+__global__ void nd_prolong_kernel(NLevel<T> C, NLevel<T> F, T *out) {
     pdl_trigger();
     pdl_wait();
     const NGeom &g = F.g, &gc = C.g;
@@ -389,7 +390,8 @@ __global__ void nd_prolong_kernel(NLevel<T> C, NLevel<T> F) {
         for (int u = 0; u < nc; u++)
             for (int v = 0; v < nb; v++)
                 for (int t = 0; t < na; t++) s += wa[t] * wb[v] * wc[u] * C.e[nidx(gc, ia[t], ib[v], ic[u])];
-        F.e[q] += s;
+        if (out) out[q] = F.e[q] + s;
+        else F.e[q] += s;
     }
 }
 
@@ -656,6 +658,78 @@ static void k_nd_residual(cudaStream_t s, const NLevel<T> &L, int zcap) {
     dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
     launch_pdl(nd_col_kernel<T, 1>, grid, dim3(64), 0, s, L, 0, L.g.m[0], L.g.m[1], zc);
 }
+
+// One Chebyshev smoothing step e_out = e_in + w D^-1 (f - L e_in), D the diagonal of
+// L (its coefficient sum: 12 w h^2 (L e)_n = sum_m c_m (e_m - e_n)), node columns
+// marched in z like the colour kernel; zero = 1: e_in is identically 0 (not read).
+// The updated nodes go to a second buffer (the stencil reads old neighbours).
+template <typename T>
+__global__ void nd_cheb_kernel(NLevel<T> L, const T *__restrict__ ein, T *__restrict__ eout, T omega, int zero,
+                               int nzc) {
+    pdl_trigger();
+    pdl_wait();
+    const NGeom &g = L.g;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= g.m[0] || b >= g.m[1]) return;
+    const int c0 = blockIdx.z * nzc, c1 = min(c0 + nzc, g.m[2]);
+    const ColMap m = col_map(g, a, b);
+    const T h2 = T(g.h * g.h);
+    const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
+                      ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f);
+    T pm[3][3], p0[3][3], pp[3][3], sl[2][2], sh[2][2];
+    for (int y = 0; y < 3; y++)
+        for (int x = 0; x < 3; x++) pm[y][x] = p0[y][x] = pp[y][x] = T(0);
+    if (!zero) {
+        load_node_plane(g, m, ein, c0 - 1, pm);
+        load_node_plane(g, m, ein, c0, p0);
+    }
+    load_cell_plane(g, m, L.sigma, c0 - 1, sl);
+    for (int c = c0; c < c1; c++) {
+        if (!zero) load_node_plane(g, m, ein, c + 1, pp);
+        load_cell_plane(g, m, L.sigma, c, sh);
+        T num, den;
+        couplings(pm, p0, pp, sl, sh, num, den);
+        const float w = wxy * ((!g.per[2] && (c == 0 || c == g.m[2] - 1)) ? 0.5f : 1.f);
+        const long long q = nidx(g, a, b, c);
+        const T e0 = p0[1][1];
+        eout[q] = den > T(0) ? e0 + omega * ((num - den * e0) - T(12) * T(w) * h2 * L.f[q]) / den : e0;
+        for (int y = 0; y < 3; y++)
+            for (int x = 0; x < 3; x++) {
+                pm[y][x] = p0[y][x];
+                p0[y][x] = pp[y][x];
+            }
+        for (int y = 0; y < 2; y++)
+            for (int x = 0; x < 2; x++) sl[y][x] = sh[y][x];
+    }
+}
+
+template <typename T>
+static void k_nd_cheb(cudaStream_t s, const NLevel<T> &L, const T *ein, T *eout, T omega, int zcap) {
+    const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2], zcap);
+    dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
+    launch_pdl(nd_cheb_kernel<T>, grid, dim3(64), 0, s, L, ein, eout, omega, ein ? 0 : 1, zc);
+}
+
+// weights of a degree-m Chebyshev smoother: the inverses of the roots of the
+// degree-m Chebyshev polynomial mapped onto [lo, hi] of the spectrum of D^-1 L,
+// largest root first.  The error factor prod_k (1 - lambda / root_k) is at most
+// 1 / T_m((hi + lo) / (hi - lo)) on [lo, hi] and at most 1 on [0, lo].
+static void cheb_weights(int m, double lo, double hi, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < m; k++) {
+        const double lam = 0.5 * (hi + lo) + 0.5 * (hi - lo) * std::cos(pi * (2 * k + 1) / (2.0 * m));
+        w[k] = 1.0 / lam;
+    }
+}
+// The interval.  hi: the operator is the trilinear finite-element Laplacian
+// sum_cells sigma_c K_c, and each cell matrix K_c (8 x 8) has eigenvalues
+// {0, h/2, h/3, h/6} (tensor products of the 1-D stiffness and mass matrices)
+// and diagonal h/3, so v'K_c v <= 1.5 v'diag(K_c) v; summing over cells with
+// sigma_c > 0 gives lambda_max(D^-1 L) <= 1.5 for any coefficient field (on the
+// coarser levels too, which are rediscretised).  lo: the smoother's share of the
+// spectrum; the modes below it are left to the coarse grid (0.4 converged in
+// the fewest V-cycles on the stratified workloads at 192^3..512^3).
+constexpr double CHEB_LO = 0.4, CHEB_HI = 1.5;
 
 // ---- double-float residual of the refinement loop ------------------------------------
 __device__ __forceinline__ void ts2(float a, float b, float &s, float &e) {
@@ -1188,12 +1262,14 @@ static void carve_nodal(Bump &b, NodalPlan &P) {
             P.L32[l].f = b.take<float>(gs[l].M);
             P.L32[l].e = b.take<float>(gs[l].M);
             P.L32[l].r = b.take<float>(gs[l].M);
+            P.L32[l].e2 = b.take<float>(gs[l].M);
         } else {
             P.L64[l].g = gs[l];
             P.L64[l].sigma = b.take<double>(gs[l].N);
             P.L64[l].f = b.take<double>(gs[l].M);
             P.L64[l].e = b.take<double>(gs[l].M);
             P.L64[l].r = b.take<double>(gs[l].M);
+            P.L64[l].e2 = b.take<double>(gs[l].M);
         }
     }
     const long long Mb = gs[P.nlev - 1].M;
@@ -1260,18 +1336,44 @@ void destroy_nodal_plans(mx_ctx *c) {
 
 static int nblk(long long n) { return red_blocks(n); }
 
+// Chebyshev: pre-smoothing from e = 0 starts writing in the buffer that leaves the
+// result in e; post-smoothing starts from the prolonged e, put in e2 (the
+// prolongation writes out of place) when the step count is odd, in e otherwise,
+// so every level's final correction is in e as with the colour sweeps.
 template <typename T>
 static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int nu2, int bot_iters, mx_ctx *pc,
-                      int zcap) {
+                      int zcap, int cheb = 0) {
+    double w1[16], w2[16];
+    if (cheb) {
+        // one Chebyshev polynomial of degree nu1 + nu2 per V-cycle, its roots split:
+        // post-smoothing takes the nu2 largest, pre-smoothing the nu1 smallest (of
+        // the splits tried -- this one, the reverse, alternating -- the one that
+        // converged in the fewest V-cycles)
+        double w[32];
+        cheb_weights(nu1 + nu2, CHEB_LO, CHEB_HI, w);
+        for (int k = 0; k < nu2; k++) w2[k] = w[k];
+        for (int k = 0; k < nu1; k++) w1[k] = w[nu2 + k];
+    }
     prof_begin(pc, s, MX_PH_UPDATE);
-    cudaMemsetAsync(L[0].e, 0, sizeof(T) * L[0].g.M, s);
-    prof_end(pc, s, MX_PH_UPDATE, 1);
+    if (!cheb) cudaMemsetAsync(L[0].e, 0, sizeof(T) * L[0].g.M, s);
+    prof_end(pc, s, MX_PH_UPDATE, cheb ? 0 : 1);
     for (int l = 0; l < nl - 1; l++) {
         if (l == 0) prof_begin(pc, s, MX_PH_SMOOTH_FINE);
-        for (int q = 0; q < nu1; q++)
-            for (int col = 0; col < 4; col++) k_nd_gs(s, L[l], col, zcap);
+        if (cheb) {
+            T *bufs[2] = {L[l].e, L[l].e2};
+            int o = nu1 % 2 == 1 ? 0 : 1;
+            const T *in = nullptr;
+            for (int q = 0; q < nu1; q++) {
+                k_nd_cheb(s, L[l], in, bufs[o], T(w1[q]), zcap);
+                in = bufs[o];
+                o ^= 1;
+            }
+        } else {
+            for (int q = 0; q < nu1; q++)
+                for (int col = 0; col < 4; col++) k_nd_gs(s, L[l], col, zcap);
+        }
         if (l == 0) {
-            prof_end(pc, s, MX_PH_SMOOTH_FINE, 4 * nu1);
+            prof_end(pc, s, MX_PH_SMOOTH_FINE, cheb ? nu1 : 4 * nu1);
             prof_begin(pc, s, MX_PH_RESTRICT_FINE);
         }
         k_nd_residual(s, L[l], zcap);
@@ -1289,14 +1391,25 @@ static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int
             prof_end(pc, s, MX_PH_COARSE, 0);
             prof_begin(pc, s, MX_PH_PROLONG_FINE);
         }
-        launch_pdl(nd_prolong_kernel<T>, dim3(nblk(L[l].g.M)), dim3(256), 0, s, L[l + 1], L[l]);
+        const bool odd = cheb && nu2 % 2 == 1;
+        launch_pdl(nd_prolong_kernel<T>, dim3(nblk(L[l].g.M)), dim3(256), 0, s, L[l + 1], L[l],
+                   odd ? L[l].e2 : (T *)nullptr);
         if (l == 0) {
             prof_end(pc, s, MX_PH_PROLONG_FINE, 1);
             prof_begin(pc, s, MX_PH_SMOOTH_FINE);
         }
-        for (int q = 0; q < nu2; q++)
-            for (int col = 3; col >= 0; col--) k_nd_gs(s, L[l], col, zcap);
-        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, 4 * nu2);
+        if (cheb) {
+            T *in = odd ? L[l].e2 : L[l].e;
+            for (int q = 0; q < nu2; q++) {
+                T *out = in == L[l].e ? L[l].e2 : L[l].e;
+                k_nd_cheb(s, L[l], (const T *)in, out, T(w2[q]), zcap);
+                in = out;
+            }
+        } else {
+            for (int q = 0; q < nu2; q++)
+                for (int col = 3; col >= 0; col--) k_nd_gs(s, L[l], col, zcap);
+        }
+        if (l == 0) prof_end(pc, s, MX_PH_SMOOTH_FINE, cheb ? nu2 : 4 * nu2);
     }
 }
 
@@ -1328,7 +1441,8 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     else mx_default_opts(&o);
     if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 ||
         o.bottom_iters < 1 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
-        !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16))
+        !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16) ||
+        (o.smoother != 0 && o.smoother != 1))
         return set_err(c, MX_ERR_ARG, "invalid options");
     if (o.krylov) return set_err(c, MX_ERR_ARG, "nodal: krylov = 1 is for MAC solves");
     tune_apply(c, MX_OP_NODAL, geom, o);
@@ -1397,13 +1511,13 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     };
     auto step = [&](cudaStream_t ss, mx_ctx *pc) {
         if (mixed) {
-            nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc, zcap);
+            nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc, zcap, o.smoother);
             prof_begin(pc, ss, MX_PH_UPDATE);
             launch_pdl(nd_df_update_kernel, dim3(nb), dim3(256), 0, ss, P->D, (long long)g.M,
                        (const float *)P->L32[0].e, (const SolveState *)c->state);
             prof_end(pc, ss, MX_PH_UPDATE, 1);
         } else {
-            nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc, zcap);
+            nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc, zcap, o.smoother);
             prof_begin(pc, ss, MX_PH_UPDATE);
             nd_update64_kernel<<<nb, 256, 0, ss>>>(phi, P->L64[0].e, c->state, g.M);
             prof_end(pc, ss, MX_PH_UPDATE, 1);
@@ -1419,7 +1533,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
             // the FP64 loop updates phi in place; the mixed loop never touches it
             const void *kphi = mixed ? nullptr : (const void *)phi;
             if (!P->graph || P->graph_phi != kphi || P->graph_nu1 != o.nu1 || P->graph_nu2 != o.nu2 ||
-                P->graph_bot != o.bottom_iters || P->graph_tilez != o.tile_z) {
+                P->graph_bot != o.bottom_iters || P->graph_tilez != o.tile_z || P->graph_smoother != o.smoother) {
                 if (P->graph) {
                     cudaGraphExecDestroy(P->graph);
                     P->graph = nullptr;
@@ -1430,6 +1544,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
                 P->graph_nu2 = o.nu2;
                 P->graph_bot = o.bottom_iters;
                 P->graph_tilez = o.tile_z;
+                P->graph_smoother = o.smoother;
             }
             MX_CUDA(c, cudaGraphLaunch(P->graph, s));
         } else {

@@ -448,7 +448,7 @@ mx_status check_opts(mx_ctx *c, const mx_opts *in, mx_opts &o) {
     if (!(o.rel_tol >= 0.0) || o.max_outer < 0 || o.max_vcycles < 0 || (o.prec != MX_PREC_FP64 && o.prec != MX_PREC_MIXED) ||
         o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.bottom_iters < 1 || o.bottom_iters > 100000 ||
         !(o.tile_z == 0 || o.tile_z == 1 || o.tile_z == 2 || o.tile_z == 4 || o.tile_z == 8 || o.tile_z == 16) ||
-        (o.krylov != 0 && o.krylov != 1))
+        (o.krylov != 0 && o.krylov != 1) || (o.smoother != 0 && o.smoother != 1))
         return set_err(c, MX_ERR_ARG, "invalid options");
     if (o.krylov && o.prec != MX_PREC_MIXED) return set_err(c, MX_ERR_ARG, "krylov = 1 needs prec = MX_PREC_MIXED");
     return MX_OK;
@@ -492,6 +492,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     if (!ux || !uy || !uz || !rho || !beta0 || !sbar || !phi) return set_err(c, MX_ERR_ARG, "mac_project: null array");
     mx_opts o;
     if ((st = check_opts(c, opts, o))) return st;
+    if (o.smoother) return set_err(c, MX_ERR_ARG, "smoother = 1 (Chebyshev) is for nodal solves");
     tune_apply(c, MX_OP_MAC, geom, o);
     if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, MX_ERR_CUDA, "cudaSetDevice failed");
     const DGeom g = make_dgeom(geom);

@@ -4,7 +4,8 @@
 // mx_autotune times whole solves of the caller's inputs on scratch copies of
 // U and phi, changing one setting at a time from the base options: the sweep
 // counts (nu1, nu2), then the z-depth of the stencil tiles (tile_z), then (MAC,
-// mixed precision) the single-pass sweep.  A change is kept when the solve
+// mixed precision) the single-pass sweep, or (nodal) the Chebyshev smoother
+// with its own degree candidates.  A change is kept when the solve
 // converges and its CUDA-event time (second of two calls: the first one builds
 // the plan and the loop graph) beats the best so far.  The winner is stored in
 // the context's tune cache, which calls with nu1 = nu2 = 0 read.
@@ -67,6 +68,7 @@ void store(mx_ctx *c, int op, int prec, const mx_geom *g, const mx_opts &cur, do
     t.nu2 = cur.nu2;
     t.fused = cur.fused;
     t.tile_z = cur.tile_z;
+    t.smoother = cur.smoother;
     t.ms = ms;
     for (auto &e : c->tune)
         if (same_key(e, op, prec, g)) {
@@ -99,6 +101,7 @@ void tune_apply(const mx_ctx *c, int op, const mx_geom *g, mx_opts &o) {
         o.nu2 = t->nu2;
         o.fused = t->fused;
         o.tile_z = t->tile_z;
+        if (op == MX_OP_NODAL) o.smoother = t->smoother;
     } else {
         o.nu1 = 2;
         o.nu2 = 2;
@@ -114,6 +117,7 @@ extern "C" int mx_tune_lookup(const mx_ctx *c, int op, int prec, const mx_geom *
     out->nu2 = t->nu2;
     out->fused = t->fused;
     out->tile_z = t->tile_z;
+    out->smoother = t->smoother;
     return 1;
 }
 
@@ -232,6 +236,19 @@ extern "C" mx_status mx_autotune(mx_ctx *c, int op, const mx_geom *geom, const d
         mx_opts cand = cur;
         cand.fused = cur.fused ? 0 : 1;
         st = consider(cand);
+    }
+    // 3'. the Chebyshev smoother (nodal) at the chosen tile depth: a step is one
+    // pass over the nodes where a colour sweep is four, so its degrees run higher
+    if (!st && have && op == MX_OP_NODAL && o.smoother == 0) {
+        const int CH_CAND[][2] = {{1, 1}, {1, 2}, {2, 1}, {2, 2}, {1, 3}, {2, 3}, {3, 2}, {3, 3}};
+        const mx_opts at = cur;
+        for (const auto &nu : CH_CAND) {
+            mx_opts cand = at;
+            cand.smoother = 1;
+            cand.nu1 = nu[0];
+            cand.nu2 = nu[1];
+            if ((st = consider(cand))) break;
+        }
     }
     cudaStreamSynchronize(c->stream);
     release();

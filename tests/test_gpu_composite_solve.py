@@ -142,7 +142,7 @@ def test_composite_projection_errors(mx, ctx):
     f = torch.zeros((8, 8, 8), dtype=torch.float64, device=DEV)
     uc = [torch.zeros(s, dtype=torch.float64, device=DEV) for s in face_shapes(G.n)]
     uf = [torch.zeros(s, dtype=torch.float64, device=DEV) for s in face_shapes(G.nf)]
-    for kw in ({"prec": mx.MX_PREC_FP64}, {"krylov": 1}):
+    for kw in ({"prec": mx.MX_PREC_FP64}, {"krylov": 1}, {"smoother": 1}):
         with pytest.raises(mx.MXError) as e:
             mx.mx_mac_project_composite(ctx, g, G.plo, G.phi, uc, z + 1, z + 1, z, z.clone(), uf, f + 1, f + 1, f,
                                         f.clone(), mx.default_opts(**kw))

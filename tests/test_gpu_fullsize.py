@@ -234,7 +234,7 @@ def test_nodal192_phi_parity_at_tuned_settings(mx):
     del w
     phi_ref = ref()
     err = np.abs(phi - phi_ref).max() / np.abs(phi_ref).max()
-    assert err <= 1e-8, (err, tuned.nu1, tuned.nu2, tuned.tile_z)
+    assert err <= 1e-8, (err, tuned.nu1, tuned.nu2, tuned.tile_z, tuned.smoother)
     u_pred = O.nd_correct(g, rho_h, phi, u0)
     for d in range(3):
         scale = np.abs(u0[d]).max() + np.abs(u_pred[d] - u0[d]).max()

@@ -4,7 +4,9 @@ oracle through the C ABI.
 Tolerances: FP64 operator/residual 1e-12 of the terms' scale (rounding order
 only); FP32 operator 3e-6 of the scale (20 FP32 terms); projection: phi within
 1e-8 relative max norm of the oracle solved to 1e-13, U equal to the oracle's
-correction of the GPU phi to 1e-12, GPU residual <= 1e-10.
+correction of the GPU phi to 1e-12, GPU residual <= 1e-10.  The same bars hold
+with either smoother (four-colour Gauss-Seidel or Chebyshev): the smoother
+changes the iterates, not the converged answer.
 """
 import numpy as np
 import pytest
@@ -93,12 +95,13 @@ def run_gpu_nodal(mx, ctx, w, prec, **kw):
     return st, info, phi.cpu().numpy(), [x.cpu().numpy() for x in u], beta0.cpu().numpy()
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("name", list(NODAL_WORKLOADS))
-def test_nodal_project_parity(mx, ctx, name, prec):
+def test_nodal_project_parity(mx, ctx, name, prec, smoother):
     w = NODAL_WORKLOADS[name]()
     g = w.geom
-    st, info, phi, u, b0 = run_gpu_nodal(mx, ctx, w, prec)
+    st, info, phi, u, b0 = run_gpu_nodal(mx, ctx, w, prec, smoother=smoother)
     assert st == mx.MX_OK, info
     assert info["rel_resid"] <= 1e-10
     u_ref, phi_ref, oinfo = O.nd_project(g, w.u, w.rho, b0, w.sbar, tol=1e-13, maxit=400)
@@ -136,14 +139,18 @@ def test_nodal_rejects_dirichlet(mx, ctx):
     assert e.value.status == mx.MX_ERR_ARG
 
 
+@pytest.mark.parametrize("cheb", [None, (1, 2), (2, 3)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_nodal_graph_and_host_loop_identical(mx, ctx, prec):
+def test_nodal_graph_and_host_loop_identical(mx, ctx, prec, cheb):
     """The refinement loop captured as a conditional-while CUDA graph runs the
-    same kernels as the host-driven loop: bit-identical phi and U, twice."""
+    same kernels as the host-driven loop: bit-identical phi and U, twice (with
+    the Chebyshev smoother at odd step counts too, where the steps ping-pong
+    between two correction buffers)."""
     w = NODAL_WORKLOADS["ragged_40x24x32"]()
-    r1 = run_gpu_nodal(mx, ctx, w, prec, use_graph=1)
-    r2 = run_gpu_nodal(mx, ctx, w, prec, use_graph=0)
-    r3 = run_gpu_nodal(mx, ctx, w, prec, use_graph=1)
+    kw = {} if cheb is None else {"smoother": 1, "nu1": cheb[0], "nu2": cheb[1]}
+    r1 = run_gpu_nodal(mx, ctx, w, prec, use_graph=1, **kw)
+    r2 = run_gpu_nodal(mx, ctx, w, prec, use_graph=0, **kw)
+    r3 = run_gpu_nodal(mx, ctx, w, prec, use_graph=1, **kw)
     assert r1[0] == mx.MX_OK and r1[1]["vcycles"] == r2[1]["vcycles"] > 0
     assert np.array_equal(r1[2], r2[2]) and np.array_equal(r1[2], r3[2])
     for d in range(3):
@@ -157,3 +164,38 @@ def test_nodal_iteration_cap_reports_noconv(mx, ctx, use_graph):
     assert st == mx.MX_ERR_NOCONV and info["status"] == mx.MX_ERR_NOCONV
     assert info["vcycles"] == 2 and info["rel_resid"] > 1e-10
     assert np.isfinite(phi).all()
+
+
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1), (1, 3), (3, 3), (4, 2)])
+def test_nodal_chebyshev_degrees_converge_to_the_oracle(mx, ctx, nu):
+    """Every split of the Chebyshev roots between pre- and post-smoothing
+    converges to the oracle's phi."""
+    w = NODAL_WORKLOADS["nodal384_at_24"]()
+    st, info, phi, u, b0 = run_gpu_nodal(mx, ctx, w, 1, smoother=1, nu1=nu[0], nu2=nu[1])
+    assert st == mx.MX_OK and info["rel_resid"] <= 1e-10, info
+    _, phi_ref, oinfo = O.nd_project(w.geom, w.u, w.rho, b0, w.sbar, tol=1e-13, maxit=400)
+    assert np.abs(phi - phi_ref).max() <= 1e-8 * np.abs(phi_ref).max()
+
+
+def test_smoother_option_rejected_where_not_offered(mx, ctx):
+    """smoother = 1 is a nodal option; the MAC and batched solves reject it, and
+    every solve rejects an unknown smoother."""
+    g = geom((8, 8, 8), (P, P, N))
+    cs = O.cell_shape(g)
+    one = torch.ones(cs, dtype=torch.float64, device=DEV)
+    z = torch.zeros(cs, dtype=torch.float64, device=DEV)
+    uf = [torch.zeros(tuple(reversed([g.n[e] + (1 if e == d else 0) for e in range(3)])), dtype=torch.float64,
+                      device=DEV) for d in range(3)]
+    with pytest.raises(mx.MXError) as e:
+        mx.mx_mac_project(ctx, g, *uf, one, one, z, z.clone(), mx.default_opts(smoother=1))
+    assert e.value.status == mx.MX_ERR_ARG
+    with pytest.raises(mx.MXError) as e:
+        mx.mx_mac_project_batched(ctx, [g], [uf[0]], [uf[1]], [uf[2]], [one], [one], [z], [z.clone()],
+                                  mx.default_opts(smoother=1))
+    assert e.value.status == mx.MX_ERR_ARG
+    u = [z.clone() for _ in range(3)]
+    phi = torch.zeros(O.node_shape(g), dtype=torch.float64, device=DEV)
+    for bad in (2, -1):
+        with pytest.raises(mx.MXError) as e:
+            mx.mx_nodal_project(ctx, g, *u, one, one, z, phi, mx.default_opts(smoother=bad))
+        assert e.value.status == mx.MX_ERR_ARG

@@ -62,6 +62,7 @@ def nodal_solve(mx, ctx, w, inputs, **kw):
 
 
 NU = {(2, 2), (1, 1), (2, 1), (1, 2), (3, 2), (2, 3), (3, 3), (4, 4)}
+NU_CHEB = {(1, 1), (1, 2), (2, 1), (2, 2), (1, 3), (2, 3), (3, 2), (3, 3)}
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -96,11 +97,14 @@ def test_nodal_autotune_choice_cached_and_reproduced(mx, ctx):
     inputs = nodal_inputs(mx, ctx, w)
     before = [t.clone() for t in inputs[0]]
     best, ms = mx.mx_autotune(ctx, mx.MX_OP_NODAL, w.geom, *inputs[0], *inputs[1:])
-    assert (best.nu1, best.nu2) in NU and best.tile_z in (0, 4, 8, 16) and best.fused == 0
+    assert best.smoother in (0, 1)
+    assert (best.nu1, best.nu2) in (NU if best.smoother == 0 else NU_CHEB)
+    assert best.tile_z in (0, 4, 8, 16) and best.fused == 0
+    assert mx.mx_tune_lookup(ctx, mx.MX_OP_NODAL, 1, w.geom).smoother == best.smoother
     for a, b in zip(before, inputs[0]):
         assert torch.equal(a, b)
     auto = nodal_solve(mx, ctx, w, inputs, nu1=0, nu2=0)
-    expl = nodal_solve(mx, ctx, w, inputs, nu1=best.nu1, nu2=best.nu2, tile_z=best.tile_z)
+    expl = nodal_solve(mx, ctx, w, inputs, nu1=best.nu1, nu2=best.nu2, tile_z=best.tile_z, smoother=best.smoother)
     assert auto[0]["status"] == 0 and auto[0]["rel_resid"] <= 1e-10
     assert np.array_equal(auto[1], expl[1])
 

@@ -176,3 +176,30 @@ def test_sampled_nodal_residual_equals_full(oracle_lib, bc):
     full = (f - O.nd_apply(g, sigma, phi)).ravel()
     got = O.nd_residual_sample(g, sigma, phi, f, np.arange(full.size))
     assert np.abs(got - full).max() <= 1e-12 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("bc", [(P, P, P), (P, P, N), (N, N, N)])
+def test_jacobi_spectrum_within_one_and_a_half(oracle_lib, bc):
+    """The spectrum of D^-1 L (D the diagonal of the nodal operator) lies in
+    [-1.5, 0] for any positive coefficient field: each cell's trilinear
+    stiffness matrix is at most 1.5 times its diagonal.  The Chebyshev smoother
+    of the nodal solve takes 1.5 as the top of its interval.  Constant sigma
+    on a grid that holds the mode (-1)^i reaches the bound."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(3)
+    g = geom((6, 4, 8), bc)
+    ns = O.node_shape(g)
+    w = O.nd_weights(g).ravel()
+    for sigma in (np.full(O.cell_shape(g), 2.3), np.exp(2.0 * rng.standard_normal(O.cell_shape(g)))):
+        cols = []
+        for k in range(int(np.prod(ns))):
+            e = np.zeros(int(np.prod(ns)))
+            e[k] = 1.0
+            cols.append(O.nd_apply(g, sigma, e.reshape(ns)).ravel())
+        M = np.stack(cols, axis=1)
+        A = -(w[:, None] * M)                   # symmetric positive semidefinite
+        assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+        lam = sl.eigh(A, np.diag(np.diag(A)), eigvals_only=True)
+        assert lam.min() >= -1e-10 and lam.max() <= 1.5 * (1 + 1e-12), (lam.min(), lam.max())
+        if np.ptp(sigma) == 0 and bc[0] == P:
+            assert lam.max() >= 1.5 * (1 - 1e-12)
