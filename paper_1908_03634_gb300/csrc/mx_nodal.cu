@@ -652,8 +652,19 @@ static void k_nd_gs(cudaStream_t s, const NLevel<T> &L, int colour, int zcap) {
     launch_pdl(nd_col_kernel<T, 0>, grid, dim3(64), 0, s, L, colour, ncx, ncy, zc);
 }
 
+template <typename T, int MODE>
+static void k_nd_tile(cudaStream_t s, const NLevel<T> &L, const T *ein, T *eout, T omega, int zcap);
+// levels at least this many nodes wide take the tiled kernels (x is covered by
+// one tile width per block; narrower levels keep the column kernels)
+constexpr int ND_TILE_MIN = 32;
+static bool nd_tiled(const NGeom &g);
+
 template <typename T>
 static void k_nd_residual(cudaStream_t s, const NLevel<T> &L, int zcap) {
+    if (nd_tiled(L.g)) {
+        k_nd_tile<T, 1>(s, L, L.e, (T *)nullptr, T(0), zcap);
+        return;
+    }
     const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2], zcap);
     dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
     launch_pdl(nd_col_kernel<T, 1>, grid, dim3(64), 0, s, L, 0, L.g.m[0], L.g.m[1], zc);
@@ -703,8 +714,250 @@ __global__ void nd_cheb_kernel(NLevel<T> L, const T *__restrict__ ein, T *__rest
     }
 }
 
+// ---- out-of-place stencil passes, tiled in x-y and marched in z ----------------------
+// A block of TBX x TTY threads owns a TBX x TNY tile of node columns (each
+// thread two y-adjacent columns, sharing their neighbourhood loads) over nzc
+// planes.  Step k of the march (node plane c0 + k) needs node plane c0 + k + 1
+// (with its one-node halo: periodic images, zeros beyond a wall), cell layer
+// c0 + k of sigma (with its halo) and f at plane c0 + k: one "stage", copied
+// global -> shared by cp.async (element copies, zero-filled where there is no
+// node or cell) into a ring of ND_NS slots, ND_NS - 1 stages ahead of the step
+// that reads it, so the DRAM latency hides behind three planes of arithmetic;
+// one barrier per plane.  Each thread keeps its 4 x 3 x 3 node and 3 x 2 x 2
+// cell neighbourhood in registers, rotated by unrolling the march six planes
+// deep.
+// MODE 0: Chebyshev step eout = e + omega D^-1 (f - L e) (e = ein); MODE 2: the
+// same from e = 0 (no node is read); MODE 1: residual L.r = L.f - L e (ein =
+// L.e).  The couplings are the column
+// kernels' (same terms, same order); the step divides with the fast FP32
+// division and the residual multiplies by 1 / (12 w h^2).
+constexpr int TBX = 32, TTY = 8, TNT = TBX * TTY, TNY = 2 * TTY;
+constexpr int THX = TBX + 2, THN = THX * (TNY + 2);  // node plane with halo
+constexpr int TCX = TBX + 1, TCN = TCX * (TNY + 1);  // cell layer with halo
+constexpr int ND_NS = 4;                             // ring slots
+constexpr int ND_HS = 3;                             // halo slots of each kind per thread
+static_assert(THN <= ND_HS * TNT && TCN <= ND_HS * TNT, "halo slots per thread");
+
+__device__ __forceinline__ float nd_fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double nd_fdiv(double a, double b) { return a / b; }
+
+// sizeof(T)-byte global -> shared copy of the first n bytes, the rest zero
+// filled (n = 0: src names a valid address but no byte is read)
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T *dst, const T *src, int n) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T>
+struct NdStage {
+    T p[THN];  // node plane
+    T s[TCN];  // cell layer
+    T f[TNY * TBX];  // f of the tile's nodes
+};
+
+// couplings() of the node in rows R..R+2 of a 4-row neighbourhood (same terms,
+// same order)
+template <int R, typename T>
+__device__ __forceinline__ void couplings_r(const T pm[4][3], const T p0[4][3], const T pp[4][3], const T sl[3][2],
+                                            const T sh[3][2], T &num, T &den) {
+    num = T(0);
+    for (int y = 0; y < 2; y++)
+        for (int x = 0; x < 2; x++) num += (sl[R + y][x] + sh[R + y][x]) * p0[R + 2 * y][2 * x];
+    for (int x = 0; x < 2; x++) {
+        num += (sl[R][x] + sl[R + 1][x]) * pm[R + 1][2 * x];
+        num += (sh[R][x] + sh[R + 1][x]) * pp[R + 1][2 * x];
+    }
+    for (int y = 0; y < 2; y++) {
+        num += (sl[R + y][0] + sl[R + y][1]) * pm[R + 2 * y][1];
+        num += (sh[R + y][0] + sh[R + y][1]) * pp[R + 2 * y][1];
+    }
+    for (int y = 0; y < 2; y++)
+        for (int x = 0; x < 2; x++) {
+            num += sl[R + y][x] * pm[R + 2 * y][2 * x];
+            num += sh[R + y][x] * pp[R + 2 * y][2 * x];
+        }
+    den = T(4) * (((sl[R][0] + sl[R][1]) + (sl[R + 1][0] + sl[R + 1][1])) +
+                  ((sh[R][0] + sh[R][1]) + (sh[R + 1][0] + sh[R + 1][1])));
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(TNT, sizeof(T) == 4 ? 3 : 1)
+    nd_tile_kernel(NLevel<T> L, const T *__restrict__ ein, T *__restrict__ eout, T omega, int nzc) {
+    pdl_trigger();
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char nd_smem[];
+    NdStage<T> *st = reinterpret_cast<NdStage<T> *>(nd_smem);
+    const NGeom &g = L.g;
+    const int tid = threadIdx.x, tx = tid % TBX, ty = tid / TBX;
+    const int a0 = blockIdx.x * TBX, b0 = blockIdx.y * TNY;
+    const int a = a0 + tx, b = b0 + 2 * ty;  // this thread's nodes: (a, b) and (a, b + 1)
+    const bool own0 = a < g.m[0] && b < g.m[1], own1 = a < g.m[0] && b + 1 < g.m[1];
+    const int c0 = blockIdx.z * nzc, c1 = min(c0 + nzc, g.m[2]);
+    const int np = g.m[0] * g.m[1], ncp = g.n[0] * g.n[1];  // 32-bit indices: M, N < 2^31 (host check)
+    // the tile's halo slots reach at most one node or cell past either end of
+    // the nodes the tile owns, which one periodic wrap maps into the box;
+    // beyond a wall or past that reach nw / cw give -1
+    auto nw = [&](int d, int x) { return x > g.m[d] ? -1 : node_wrap(g, d, x); };
+    auto cw = [&](int d, int x) { return x > g.m[d] - 1 ? -1 : cell_wrap(g, d, x); };
+    // per slot: the in-plane offset; slots 0 and 1 exist for every thread.
+    // A node beyond a wall couples only through cells beyond that wall, whose
+    // sigma is zero-filled (cmask bit clear: a 0-byte copy), so its slot may
+    // hold any finite node: it copies node 0 of the plane (the products are +-0
+    // either way, and adding a zero leaves the sum's bits unchanged).
+    static_assert(THN >= 2 * TNT && TCN >= 2 * TNT, "two full slot rows");
+    int no[ND_HS], co[ND_HS], cmask = 0;
+    for (int k = 0; k < ND_HS; k++) {
+        const int sl = tid + k * TNT;
+        no[k] = co[k] = 0;
+        if (sl < THN) {
+            const int na = nw(0, a0 - 1 + sl % THX), nb = nw(1, b0 - 1 + sl / THX);
+            if (na >= 0 && nb >= 0) no[k] = na + g.m[0] * nb;
+        }
+        if (sl < TCN) {
+            const int ca = cw(0, a0 - 1 + sl % TCX), cb = cw(1, b0 - 1 + sl / TCX);
+            if (ca >= 0 && cb >= 0) {
+                co[k] = ca + g.n[0] * cb;
+                cmask |= 1 << k;
+            }
+        }
+    }
+    const bool slot2n = tid + 2 * TNT < THN, slot2c = tid + 2 * TNT < TCN;
+    const int qa = own0 ? a + g.m[0] * b : 0;  // this thread's first node at plane 0
+    // stage k: node plane c0 + 1 + k, cell layer c0 + k, f at plane c0 + k; any
+    // part outside [c0 - 1, c1] (planes), [c0 - 1, c1 - 1] (layers) or
+    // [c0, c1 - 1] (f) is not copied (nothing reads it)
+    auto issue = [&](int k) {
+        NdStage<T> &S = st[(k + 2) % ND_NS];
+        const int c = c0 + 1 + k, kl = c0 + k;
+        if (MODE != 2 && c <= c1) {
+            const int cz = node_wrap(g, 2, c);  // beyond a z wall: any plane (see above)
+            const T *base = ein + (cz >= 0 ? cz * np : 0);
+            cp_async_el(&S.p[tid], base + no[0], (int)sizeof(T));
+            cp_async_el(&S.p[tid + TNT], base + no[1], (int)sizeof(T));
+            if (slot2n) cp_async_el(&S.p[tid + 2 * TNT], base + no[2], (int)sizeof(T));
+        }
+        if (kl >= c0 - 1 && kl <= c1 - 1) {
+            const int kz = cell_wrap(g, 2, kl);
+            const T *base = L.sigma + (kz >= 0 ? kz * ncp : 0);
+            const int m = kz >= 0 ? cmask : 0;
+            cp_async_el(&S.s[tid], base + co[0], (m & 1) ? (int)sizeof(T) : 0);
+            cp_async_el(&S.s[tid + TNT], base + co[1], (m & 2) ? (int)sizeof(T) : 0);
+            if (slot2c) cp_async_el(&S.s[tid + 2 * TNT], base + co[2], (m & 4) ? (int)sizeof(T) : 0);
+        }
+        if (kl >= c0 && kl < c1) {
+            if (own0) cp_async_el(&S.f[2 * ty * TBX + tx], L.f + (qa + kl * np), (int)sizeof(T));
+            if (own1) cp_async_el(&S.f[(2 * ty + 1) * TBX + tx], L.f + (qa + g.m[0] + kl * np), (int)sizeof(T));
+        }
+        cp_async_commit();
+    };
+    auto get_nodes = [&](int k, T p[4][3]) {
+        const T *sp = st[(k + 2) % ND_NS].p + 2 * ty * THX + tx;
+        for (int y = 0; y < 4; y++)
+            for (int x = 0; x < 3; x++) p[y][x] = MODE == 2 ? T(0) : sp[y * THX + x];
+    };
+    auto get_cells = [&](int k, T s[3][2]) {
+        const T *sc = st[(k + 2) % ND_NS].s + 2 * ty * TCX + tx;
+        for (int y = 0; y < 3; y++)
+            for (int x = 0; x < 2; x++) s[y][x] = sc[y * TCX + x];
+    };
+    const T h2 = T(g.h * g.h);
+    const float wx = (!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f;
+    const float wy0 = (!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f;
+    const float wy1 = (!g.per[1] && (b + 1 == 0 || b + 1 == g.m[1] - 1)) ? 0.5f : 1.f;
+    const T f12a = T(12) * T(wx * wy0) * h2, f12b = T(12) * T(wx * wy1) * h2;  // 12 w h^2 off the z walls
+    const T inva = T(1) / f12a, invb = T(1) / f12b;
+    T P0[4][3], P1[4][3], P2[4][3], S0[3][2], S1[3][2];
+    // prologue: stages -2 (plane c0 - 1) and -1 (plane c0, layer c0 - 1) into
+    // registers; then stages 0, 1, 2 in flight
+    issue(-2);
+    issue(-1);
+    cp_async_wait<0>();
+    __syncthreads();
+    get_nodes(-2, P0);
+    get_nodes(-1, P1);
+    get_cells(-1, S0);
+    __syncthreads();
+    issue(0);
+    issue(1);
+    issue(2);
+    auto one = [&](int R, const T num, const T den, const T e0, const T f, const T f12, const T inv, bool wall,
+                   int q) {
+        if (MODE != 1) {
+            const T t = (num - den * e0) - (wall ? T(0.5) * f12 : f12) * f;
+            eout[q] = den > T(0) ? e0 + nd_fdiv(omega * t, den) : e0;
+        } else {
+            L.r[q] = f - (num - den * e0) * (wall ? T(2) * inv : inv);
+        }
+    };
+    auto step = [&](int k, T pm[4][3], T p0[4][3], T pp[4][3], T sl[3][2], T sh[3][2]) {
+        cp_async_wait<2>();  // this thread's copies of stage k
+        __syncthreads();     // everyone's; and stage k - 1 is free for stage k + 3
+        get_nodes(k, pp);
+        get_cells(k, sh);
+        const int c = c0 + k;
+        const bool wall = !g.per[2] && (c == 0 || c == g.m[2] - 1);
+        const T *fs = st[(k + 2) % ND_NS].f + 2 * ty * TBX + tx;
+        const int q = qa + c * np;
+        if (own0) {
+            T num, den;
+            couplings_r<0>(pm, p0, pp, sl, sh, num, den);
+            one(0, num, den, p0[1][1], fs[0], f12a, inva, wall, q);
+        }
+        if (own1) {
+            T num, den;
+            couplings_r<1>(pm, p0, pp, sl, sh, num, den);
+            one(1, num, den, p0[2][1], fs[TBX], f12b, invb, wall, q + g.m[0]);
+        }
+        issue(k + 3);
+    };
+    const int nk = c1 - c0;
+    for (int k = 0; k < nk; k += 6) {
+        step(k, P0, P1, P2, S0, S1);
+        if (k + 1 >= nk) break;
+        step(k + 1, P1, P2, P0, S1, S0);
+        if (k + 2 >= nk) break;
+        step(k + 2, P2, P0, P1, S0, S1);
+        if (k + 3 >= nk) break;
+        step(k + 3, P0, P1, P2, S1, S0);
+        if (k + 4 >= nk) break;
+        step(k + 4, P1, P2, P0, S0, S1);
+        if (k + 5 >= nk) break;
+        step(k + 5, P2, P0, P1, S1, S0);
+    }
+    cp_async_wait<0>();  // no copy outlives the block
+}
+
+template <typename T, int MODE>
+static void k_nd_tile(cudaStream_t s, const NLevel<T> &L, const T *ein, T *eout, T omega, int zcap) {
+    const long long bxy = (long long)((L.g.m[0] + TBX - 1) / TBX) * ((L.g.m[1] + TNY - 1) / TNY);
+    // deep chunks (the halo planes are re-read once per chunk), halved until the
+    // grid fills every SM a few times over
+    int zc = 4 * (zcap > 0 ? zcap : NCZ);
+    while (zc > 4 && bxy * ((L.g.m[2] + zc - 1) / zc) < 4 * 3 * 152) zc >>= 1;
+    dim3 grid((L.g.m[0] + TBX - 1) / TBX, (L.g.m[1] + TNY - 1) / TNY, (L.g.m[2] + zc - 1) / zc);
+    const size_t smem = sizeof(NdStage<T>) * ND_NS;  // FP64: above the 48 KB default, opted in
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(nd_tile_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    launch_pdl(nd_tile_kernel<T, MODE>, grid, dim3(TNT), smem, s, L, ein, eout, omega, zc);
+}
+
+// the tiled kernels index with 32-bit integers
+static bool nd_tiled(const NGeom &g) { return g.m[0] >= ND_TILE_MIN && g.M < (1LL << 31) && g.N < (1LL << 31); }
+
 template <typename T>
 static void k_nd_cheb(cudaStream_t s, const NLevel<T> &L, const T *ein, T *eout, T omega, int zcap) {
+    if (nd_tiled(L.g)) {
+        if (ein) k_nd_tile<T, 0>(s, L, ein, eout, omega, zcap);
+        else k_nd_tile<T, 2>(s, L, ein, eout, omega, zcap);
+        return;
+    }
     const int zc = nd_zchunk((long long)((L.g.m[0] + 63) / 64) * L.g.m[1], L.g.m[2], zcap);
     dim3 grid((L.g.m[0] + 63) / 64, L.g.m[1], (L.g.m[2] + zc - 1) / zc);
     launch_pdl(nd_cheb_kernel<T>, grid, dim3(64), 0, s, L, ein, eout, omega, ein ? 0 : 1, zc);
