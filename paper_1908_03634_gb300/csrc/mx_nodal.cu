@@ -1135,6 +1135,211 @@ __global__ void nd_df_col_resid_kernel(NLevel<float> L0, NDF D, const SolveState
     }
 }
 
+// The double-float residual tiled like nd_tile_kernel (one node per thread,
+// a 32 x 8 tile of columns, the halo planes of phi (hi, lo), the cell layers of
+// sigma (hi, lo) and f (hi, lo) staged by cp.async in a ring of ND_NS slots):
+// the couplings, their order and the final scaling are the column kernel's, so
+// the result is the same bit for bit; the sums of sigma over the two cells of
+// an upper face (x-z and y-z pairs) are kept for the next plane, where they are
+// the lower face's.
+constexpr int DBX = 32, DBY = 8, DNT = DBX * DBY;
+constexpr int DHX = DBX + 2, DHN = DHX * (DBY + 2);
+constexpr int DCX = DBX + 1, DCN = DCX * (DBY + 1);
+static_assert(DHN <= 2 * DNT && DCN <= 2 * DNT && DHN > DNT && DCN > DNT, "two halo slots per thread");
+
+struct NdDfStage {
+    float ph[DHN], pl[DHN];
+    float sh[DCN], sl[DCN];
+    float fh[DNT], fl[DNT];
+};
+
+static int nd_df_zchunk(const NGeom &g) {
+    const long long bxy = (long long)((g.m[0] + DBX - 1) / DBX) * ((g.m[1] + DBY - 1) / DBY);
+    int zc = 64;
+    while (zc > 4 && bxy * ((g.m[2] + zc - 1) / zc) < 4 * 2 * 152) zc >>= 1;
+    return zc;
+}
+static dim3 nd_df_tile_grid(const NGeom &g) {
+    const int zc = nd_df_zchunk(g);
+    return dim3((g.m[0] + DBX - 1) / DBX, (g.m[1] + DBY - 1) / DBY, (g.m[2] + zc - 1) / zc);
+}
+
+__global__ void __launch_bounds__(DNT, 2)
+    nd_df_tile_resid_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part, int nzc) {
+    pdl_trigger();
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char nd_smem[];
+    NdDfStage *sg = reinterpret_cast<NdDfStage *>(nd_smem);
+    const NGeom &g = L0.g;
+    const int tid = threadIdx.x, tx = tid % DBX, ty = tid / DBX;
+    const int a0 = blockIdx.x * DBX, b0 = blockIdx.y * DBY;
+    const int a = a0 + tx, b = b0 + ty;
+    const bool own = a < g.m[0] && b < g.m[1];
+    const int c0 = blockIdx.z * nzc, c1 = min(c0 + nzc, g.m[2]);
+    const int np = g.m[0] * g.m[1], ncp = g.n[0] * g.n[1];
+    // halo slots (see nd_tile_kernel): nodes beyond a wall read node 0 of the
+    // plane (their couplings' sigma is zero-filled), cells beyond one are zero
+    auto nw = [&](int d, int x) { return x > g.m[d] ? -1 : node_wrap(g, d, x); };
+    auto cw = [&](int d, int x) { return x > g.m[d] - 1 ? -1 : cell_wrap(g, d, x); };
+    int no[2], co[2], cmask = 0;
+    for (int k = 0; k < 2; k++) {
+        const int sl = tid + k * DNT;
+        no[k] = co[k] = 0;
+        if (sl < DHN) {
+            const int na = nw(0, a0 - 1 + sl % DHX), nb = nw(1, b0 - 1 + sl / DHX);
+            if (na >= 0 && nb >= 0) no[k] = na + g.m[0] * nb;
+        }
+        if (sl < DCN) {
+            const int ca = cw(0, a0 - 1 + sl % DCX), cb = cw(1, b0 - 1 + sl / DCX);
+            if (ca >= 0 && cb >= 0) {
+                co[k] = ca + g.n[0] * cb;
+                cmask |= 1 << k;
+            }
+        }
+    }
+    const bool slot1n = tid + DNT < DHN, slot1c = tid + DNT < DCN;
+    const int qa = own ? a + g.m[0] * b : 0;
+    // stage k: phi plane c0 + 1 + k, sigma layer c0 + k, f at plane c0 + k
+    auto issue = [&](int k) {
+        NdDfStage &S = sg[(k + 2) % ND_NS];
+        const int c = c0 + 1 + k, kl = c0 + k;
+        if (c <= c1) {
+            const int cz = node_wrap(g, 2, c);
+            const int o = cz >= 0 ? cz * np : 0;
+            cp_async_el(&S.ph[tid], D.ph + o + no[0], 4);
+            cp_async_el(&S.pl[tid], D.pl + o + no[0], 4);
+            if (slot1n) {
+                cp_async_el(&S.ph[tid + DNT], D.ph + o + no[1], 4);
+                cp_async_el(&S.pl[tid + DNT], D.pl + o + no[1], 4);
+            }
+        }
+        if (kl >= c0 - 1 && kl <= c1 - 1) {
+            const int kz = cell_wrap(g, 2, kl);
+            const int o = kz >= 0 ? kz * ncp : 0;
+            const int m = kz >= 0 ? cmask : 0;
+            cp_async_el(&S.sh[tid], D.sh + o + co[0], (m & 1) ? 4 : 0);
+            cp_async_el(&S.sl[tid], D.sl + o + co[0], (m & 1) ? 4 : 0);
+            if (slot1c) {
+                cp_async_el(&S.sh[tid + DNT], D.sh + o + co[1], (m & 2) ? 4 : 0);
+                cp_async_el(&S.sl[tid + DNT], D.sl + o + co[1], (m & 2) ? 4 : 0);
+            }
+        }
+        if (own && kl >= c0 && kl < c1) {
+            cp_async_el(&S.fh[tid], D.fh + qa + kl * np, 4);
+            cp_async_el(&S.fl[tid], D.fl + qa + kl * np, 4);
+        }
+        cp_async_commit();
+    };
+    auto get_nodes = [&](int k, float h[3][3], float l[3][3]) {
+        const NdDfStage &S = sg[(k + 2) % ND_NS];
+        const int o = ty * DHX + tx;
+        for (int y = 0; y < 3; y++)
+            for (int x = 0; x < 3; x++) {
+                h[y][x] = S.ph[o + y * DHX + x];
+                l[y][x] = S.pl[o + y * DHX + x];
+            }
+    };
+    auto get_cells = [&](int k, float h[2][2], float l[2][2]) {
+        const NdDfStage &S = sg[(k + 2) % ND_NS];
+        const int o = ty * DCX + tx;
+        for (int y = 0; y < 2; y++)
+            for (int x = 0; x < 2; x++) {
+                h[y][x] = S.sh[o + y * DCX + x];
+                l[y][x] = S.sl[o + y * DCX + x];
+            }
+    };
+    const float inv = st->inv_scale_f;
+    const float ih2 = float(1.0 / (g.h * g.h));
+    const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
+                      ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f);
+    const float sc_in = ih2 / (12.f * wxy), sc_wall = ih2 / (12.f * (wxy * 0.5f));
+    float mx = 0.f, s2 = 0.f, s1 = 0.f;
+    float PH0[3][3], PL0[3][3], PH1[3][3], PL1[3][3], PH2[3][3], PL2[3][3];
+    float SH0[2][2], SL0[2][2], SH1[2][2], SL1[2][2];
+    float xzh[2], xzl[2], yzh[2], yzl[2];  // lower-face sigma pair sums of the current plane
+    issue(-2);
+    issue(-1);
+    cp_async_wait<0>();
+    __syncthreads();
+    get_nodes(-2, PH0, PL0);
+    get_nodes(-1, PH1, PL1);
+    get_cells(-1, SH0, SL0);
+    __syncthreads();
+    for (int x = 0; x < 2; x++) df_add2(SH0[0][x], SL0[0][x], SH0[1][x], SL0[1][x], xzh[x], xzl[x]);
+    for (int y = 0; y < 2; y++) df_add2(SH0[y][0], SL0[y][0], SH0[y][1], SL0[y][1], yzh[y], yzl[y]);
+    issue(0);
+    issue(1);
+    issue(2);
+    auto step = [&](int k, float pmh[3][3], float pml[3][3], float p0h[3][3], float p0l[3][3], float pph[3][3],
+                    float ppl[3][3], float slh[2][2], float sll[2][2], float shh[2][2], float shl[2][2]) {
+        cp_async_wait<2>();
+        __syncthreads();
+        get_nodes(k, pph, ppl);
+        get_cells(k, shh, shl);
+        const int c = c0 + k;
+        const NdDfStage &S = sg[(k + 2) % ND_NS];
+        const float ch = p0h[1][1], cl = p0l[1][1];
+        float Sh = 0.f, Se = 0.f, kh, kl;
+        for (int y = 0; y < 2; y++)
+            for (int x = 0; x < 2; x++) {
+                df_add2(slh[y][x], sll[y][x], shh[y][x], shl[y][x], kh, kl);
+                df_acc(kh, kl, p0h[2 * y][2 * x], p0l[2 * y][2 * x], ch, cl, Sh, Se);
+                df_acc(slh[y][x], sll[y][x], pmh[2 * y][2 * x], pml[2 * y][2 * x], ch, cl, Sh, Se);
+                df_acc(shh[y][x], shl[y][x], pph[2 * y][2 * x], ppl[2 * y][2 * x], ch, cl, Sh, Se);
+            }
+        for (int x = 0; x < 2; x++) {
+            df_acc(xzh[x], xzl[x], pmh[1][2 * x], pml[1][2 * x], ch, cl, Sh, Se);
+            df_add2(shh[0][x], shl[0][x], shh[1][x], shl[1][x], kh, kl);
+            df_acc(kh, kl, pph[1][2 * x], ppl[1][2 * x], ch, cl, Sh, Se);
+            xzh[x] = kh;
+            xzl[x] = kl;
+        }
+        for (int y = 0; y < 2; y++) {
+            df_acc(yzh[y], yzl[y], pmh[2 * y][1], pml[2 * y][1], ch, cl, Sh, Se);
+            df_add2(shh[y][0], shl[y][0], shh[y][1], shl[y][1], kh, kl);
+            df_acc(kh, kl, pph[2 * y][1], ppl[2 * y][1], ch, cl, Sh, Se);
+            yzh[y] = kh;
+            yzl[y] = kl;
+        }
+        if (own) {
+            const int q = qa + c * np;
+            float Rh, Re;
+            ts2(S.fh[tid], -Sh, Rh, Re);
+            Re += S.fl[tid] - Se;
+            const float R = Rh + Re;  // 12 w h^2 r
+            const bool wall = !g.per[2] && (c == 0 || c == g.m[2] - 1);
+            const float rh = R * (wall ? sc_wall : sc_in) * inv;
+            L0.f[q] = rh;
+            mx = nmaxf(mx, fabsf(rh));
+            s2 = fmaf(rh, rh, s2);
+            s1 += rh;
+        }
+        issue(k + 3);
+    };
+    const int nk = c1 - c0;
+    for (int k = 0; k < nk; k += 6) {
+        step(k, PH0, PL0, PH1, PL1, PH2, PL2, SH0, SL0, SH1, SL1);
+        if (k + 1 >= nk) break;
+        step(k + 1, PH1, PL1, PH2, PL2, PH0, PL0, SH1, SL1, SH0, SL0);
+        if (k + 2 >= nk) break;
+        step(k + 2, PH2, PL2, PH0, PL0, PH1, PL1, SH0, SL0, SH1, SL1);
+        if (k + 3 >= nk) break;
+        step(k + 3, PH0, PL0, PH1, PL1, PH2, PL2, SH1, SL1, SH0, SL0);
+        if (k + 4 >= nk) break;
+        step(k + 4, PH1, PL1, PH2, PL2, PH0, PL0, SH0, SL0, SH1, SL1);
+        if (k + 5 >= nk) break;
+        step(k + 5, PH2, PL2, PH0, PL0, PH1, PL1, SH1, SL1, SH0, SL0);
+    }
+    cp_async_wait<0>();
+    block_red3f(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        double *p = part + 3 * (blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z));
+        p[0] = double(mx);
+        p[1] = double(s2);
+        p[2] = double(s1);
+    }
+}
+
 static dim3 nd_col_grid(const NGeom &g) { return dim3((g.m[0] + 63) / 64, g.m[1], (g.m[2] + NCZ - 1) / NCZ); }
 static int nd_col_blocks(const NGeom &g) {
     const dim3 d = nd_col_grid(g);
@@ -1550,7 +1755,8 @@ static void free_nodal_plan(NodalPlan *p) {
 }
 
 static NodalPlan *get_nodal_plan(mx_ctx *c, const NGeom &g, int prec, mx_status *st) {
-    *st = ensure_partials(c, std::max(152 * 8, nd_col_blocks(g)));
+    const dim3 tg = nd_df_tile_grid(g);
+    *st = ensure_partials(c, std::max<long long>(std::max(152 * 8, nd_col_blocks(g)), (long long)tg.x * tg.y * tg.z));
     if (*st) return nullptr;
     for (NodalPlan *p : c->nplans)
         if (p->prec == prec && same_ngeom(p->g, g)) {
@@ -1755,11 +1961,20 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     // refinement loop: residual, then while not converged {V-cycle, update, residual}
     auto residual = [&](cudaStream_t ss, mx_ctx *pc) {
         prof_begin(pc, ss, MX_PH_RESID64);
-        if (mixed) launch_pdl(nd_df_col_resid_kernel, nd_col_grid(g), dim3(64), 0, ss, P->L32[0], P->D,
-                              (const SolveState *)c->state, c->partials);
-        else nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, ss>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f,
-                                                                  c->state, c->partials);
-        k_finalize_residual(ss, c->partials, nd_col_blocks(g), c->state, mixed ? 1 : 0);
+        int nparts = nd_col_blocks(g);
+        if (mixed && nd_tiled(g)) {
+            const dim3 grid = nd_df_tile_grid(g);
+            nparts = int(grid.x * grid.y * grid.z);
+            launch_pdl(nd_df_tile_resid_kernel, grid, dim3(DNT), sizeof(NdDfStage) * ND_NS, ss, P->L32[0], P->D,
+                       (const SolveState *)c->state, c->partials, nd_df_zchunk(g));
+        } else if (mixed) {
+            launch_pdl(nd_df_col_resid_kernel, nd_col_grid(g), dim3(64), 0, ss, P->L32[0], P->D,
+                       (const SolveState *)c->state, c->partials);
+        } else {
+            nd_col_resid64_kernel<<<nd_col_grid(g), 64, 0, ss>>>(P->L64[0], phi, P->f64, nullptr, P->L64[0].f,
+                                                                 c->state, c->partials);
+        }
+        k_finalize_residual(ss, c->partials, nparts, c->state, mixed ? 1 : 0);
         prof_end(pc, ss, MX_PH_RESID64, 2);
     };
     auto step = [&](cudaStream_t ss, mx_ctx *pc) {
