@@ -11,6 +11,7 @@
 // the coefficients are within a few 2^-48; the residual of the stored phi is
 // computed with an error of a few 2^-48 relative to the largest flux term, far
 // below the 1e-10 relative residual the loop converges to.
+#include "mx_async.cuh"
 #include "mx_df.cuh"
 #include "mx_dfmath.cuh"
 #include "mx_stencil.cuh"
@@ -531,6 +532,262 @@ void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int 
     else df_resid_batch_kernel<false><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
 }
 
+// ---- the same residual as a z-march --------------------------------------------
+// A block of 32 x 8 threads owns a 32 x 8 tile of cell columns over nzc planes.
+// Step k (cell plane c0 + k) reads one "stage" (this block's slice of the
+// inputs, copied global -> shared by cp.async into a ring of DM_NS slots, two
+// stages ahead): the old phi (hi, lo) and e of plane c0 + k + 1 with a one-cell
+// x-y halo (zero beyond a wall), the x and y face coefficients (hi, lo) of plane
+// c0 + k with the tile's high faces, the low z faces of plane c0 + k (stage k + 1
+// gives the high ones) and h^2 f.  phi_new = phi + step e is formed once per
+// staged value (into one of two shared planes) and once more by each thread for
+// its own column, so a column's z neighbours stay in registers.  The flux terms,
+// their order and the update arithmetic are the tile kernel's: the results are
+// the same bit for bit.  32-bit indices (N < 2^31, checked by the caller).
+constexpr int DM_X = 32, DM_Y = 8, DM_T = DM_X * DM_Y;
+constexpr int DM_HX = DM_X + 2, DM_HN = DM_HX * (DM_Y + 2);  // phi plane with halo
+constexpr int DM_BXX = DM_X + 1, DM_BXN = DM_BXX * DM_Y;    // x faces (with the tile's high column)
+constexpr int DM_BYN = DM_X * (DM_Y + 1);                   // y faces (with the tile's high row)
+constexpr int DM_NS = 4;
+static_assert(DM_HN <= 2 * DM_T && DM_BXN <= 2 * DM_T && DM_BYN <= 2 * DM_T, "two slots per thread");
+
+struct DmStage {
+    float ph[DM_HN], pl[DM_HN], pe[DM_HN];
+    float bxh[DM_BXN], bxl[DM_BXN];
+    float byh[DM_BYN], byl[DM_BYN];
+    float bzh[DM_T], bzl[DM_T];
+    float fh[DM_T], fl[DM_T];
+};
+struct DmShared {
+    DmStage st[DM_NS];
+    float ch[2][DM_HN], cl[2][DM_HN];  // phi_new of plane c0 + k (buffer k & 1)
+};
+
+static int df_march_zchunk(const DGeom &g) {
+    const long long bxy = (long long)((g.n[0] + DM_X - 1) / DM_X) * ((g.n[1] + DM_Y - 1) / DM_Y);
+    int zc = 64;
+    while (zc > 4 && bxy * ((g.n[2] + zc - 1) / zc) < 4 * 3 * 152) zc >>= 1;
+    return zc;
+}
+static dim3 df_march_grid(const DGeom &g) {
+    const int zc = df_march_zchunk(g);
+    return dim3((g.n[0] + DM_X - 1) / DM_X, (g.n[1] + DM_Y - 1) / DM_Y, (g.n[2] + zc - 1) / zc);
+}
+static bool df_march_ok(const DGeom &g) { return g.n[0] >= DM_X && g.N < (1LL << 31); }
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(DM_T, 2)
+    df_march_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
+                    const SolveState *st, float ih2, double *part, int nzc) {
+    pdl_trigger();
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char dm_smem[];
+    DmShared &sm = *reinterpret_cast<DmShared *>(dm_smem);
+    const DGeom &g = L.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxy = nx * ny;
+    const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
+    const int tid = threadIdx.x, tx = tid % DM_X, ty = tid / DM_X;
+    const int x0 = blockIdx.x * DM_X, y0 = blockIdx.y * DM_Y;
+    const int i = x0 + tx, j = y0 + ty;
+    const bool own = i < nx && j < ny;
+    const int c0 = blockIdx.z * nzc, c1 = min(c0 + nzc, nz);
+    const int nk = c1 - c0;
+    const int it = st->iter;
+    const int src = UPDATE ? ((it - 1) & 1) : (it & 1), dst = it & 1;
+    const float *__restrict__ sph = src ? D.ph2 : D.ph;
+    const float *__restrict__ spl = src ? D.pl2 : D.pl;
+    float *__restrict__ dph = dst ? D.ph2 : D.ph;
+    float *__restrict__ dpl = dst ? D.pl2 : D.pl;
+    const float *__restrict__ ee = (UPDATE && e_odd && (it & 1)) ? e_odd : e;
+    float sch = 0.f, scl = 0.f;
+    if (UPDATE) {
+        sch = st->upd_h;
+        scl = st->upd_l;
+    }
+    // this thread's slots.  phi: in-plane offset (po, bit k of pmask: a cell
+    // there).  x faces: kind 1 = bx at (offset, plane stride nxy), kind 2 = the
+    // high plane hx at (offset, plane stride ny), 0 = no copy; y faces alike
+    // (hy: plane stride nx).
+    int po[2], xo[2], yo[2], pmask = 0, xk = 0, yk = 0;
+    for (int s = 0; s < 2; s++) {
+        const int q = tid + s * DM_T;
+        po[s] = xo[s] = yo[s] = 0;
+        if (q < DM_HN) {
+            const int lx = df_map(x0 - 1 + q % DM_HX, nx, px), ly = df_map(y0 - 1 + q / DM_HX, ny, py);
+            if (lx >= 0 && ly >= 0) {
+                po[s] = lx + nx * ly;
+                pmask |= 1 << s;
+            }
+        }
+        if (q < DM_BXN) {
+            const int x = x0 + q % DM_BXX, y = y0 + q / DM_BXX;
+            if (y < ny && x < nx) {
+                xo[s] = x + nx * y;
+                xk |= 1 << (2 * s);
+            } else if (y < ny && x == nx) {
+                if (px) {
+                    xo[s] = nx * y;
+                    xk |= 1 << (2 * s);
+                } else {
+                    xo[s] = y;
+                    xk |= 2 << (2 * s);
+                }
+            }
+        }
+        if (q < DM_BYN) {
+            const int x = x0 + q % DM_X, y = y0 + q / DM_X;
+            if (x < nx && y < ny) {
+                yo[s] = x + nx * y;
+                yk |= 1 << (2 * s);
+            } else if (x < nx && y == ny) {
+                if (py) {
+                    yo[s] = x;
+                    yk |= 1 << (2 * s);
+                } else {
+                    yo[s] = x;
+                    yk |= 2 << (2 * s);
+                }
+            }
+        }
+    }
+    const bool slot1 = tid + DM_T < DM_HN, slot1x = tid + DM_T < DM_BXN, slot1y = tid + DM_T < DM_BYN;
+    const int oc = own ? i + nx * j : 0;  // own column, in-plane
+    // stage k: phi raw of plane c0 + k + 1 (k in [-2, nk - 1]); faces and f of
+    // plane c0 + k (k in [0, nk - 1]); low z faces of plane c0 + k (k in [0, nk])
+    auto issue = [&](int k) {
+        DmStage &S = sm.st[(k + 2) % DM_NS];
+        if (k <= nk - 1) {
+            const int p = df_map(c0 + k + 1, nz, pz);
+            const int base = p >= 0 ? p * nxy : 0;
+            const int m = p >= 0 ? pmask : 0;
+            for (int s = 0; s < 2; s++) {
+                if (s == 1 && !slot1) break;
+                const int q = tid + s * DM_T, n = ((m >> s) & 1) ? 4 : 0;
+                cp_async_el(&S.ph[q], sph + base + po[s], n);
+                cp_async_el(&S.pl[q], spl + base + po[s], n);
+                if (UPDATE) cp_async_el(&S.pe[q], ee + base + po[s], n);
+            }
+        }
+        const int c = c0 + k;
+        if (k >= 0 && k <= nk - 1) {
+            for (int s = 0; s < 2; s++) {
+                const int q = tid + s * DM_T;
+                const int kx = (xk >> (2 * s)) & 3, ky = (yk >> (2 * s)) & 3;
+                if (kx && (s == 0 || slot1x)) {
+                    const float *hh = kx == 1 ? L.bx + c * nxy : L.hx + c * ny;
+                    const float *hl = kx == 1 ? D.bxl + c * nxy : D.hxl + c * ny;
+                    cp_async_el(&S.bxh[q], hh + xo[s], 4);
+                    cp_async_el(&S.bxl[q], hl + xo[s], 4);
+                }
+                if (ky && (s == 0 || slot1y)) {
+                    const float *hh = ky == 1 ? L.by + c * nxy : L.hy + c * nx;
+                    const float *hl = ky == 1 ? D.byl + c * nxy : D.hyl + c * nx;
+                    cp_async_el(&S.byh[q], hh + yo[s], 4);
+                    cp_async_el(&S.byl[q], hl + yo[s], 4);
+                }
+            }
+            if (own) {
+                cp_async_el(&S.fh[tid], D.fh + c * nxy + oc, 4);
+                cp_async_el(&S.fl[tid], D.fl + c * nxy + oc, 4);
+            }
+        }
+        if (k >= 0 && k <= nk && own) {
+            if (c < nz) {
+                cp_async_el(&S.bzh[tid], L.bz + c * nxy + oc, 4);
+                cp_async_el(&S.bzl[tid], D.bzl + c * nxy + oc, 4);
+            } else if (pz) {  // the top face of the last plane: plane 0's low face
+                cp_async_el(&S.bzh[tid], L.bz + oc, 4);
+                cp_async_el(&S.bzl[tid], D.bzl + oc, 4);
+            } else {          // or the high boundary plane
+                cp_async_el(&S.bzh[tid], L.hz + oc, 4);
+                cp_async_el(&S.bzl[tid], D.hzl + oc, 4);
+            }
+        }
+        cp_async_commit();
+    };
+    auto newval = [&](const DmStage &S, int q, float &h, float &l) {
+        h = S.ph[q];
+        l = S.pl[q];
+        if (UPDATE) df_axpy(h, l, sch, scl, S.pe[q]);
+    };
+    auto convert = [&](const DmStage &S, int b) {  // this thread's slots of the stage's plane into buffer b
+        for (int s = 0; s < 2; s++) {
+            if (s == 1 && !slot1) break;
+            const int q = tid + s * DM_T;
+            float h, l;
+            newval(S, q, h, l);
+            sm.ch[b][q] = h;
+            sm.cl[b][q] = l;
+        }
+    };
+    const int qo = (ty + 1) * DM_HX + tx + 1;  // own column in the halo plane
+    float pmh, pml, p0h, p0l;
+    issue(-2);
+    issue(-1);
+    cp_async_wait<0>();
+    __syncthreads();
+    newval(sm.st[0], qo, pmh, pml);  // plane c0 - 1
+    newval(sm.st[1], qo, p0h, p0l);  // plane c0
+    if (UPDATE && own) {
+        dph[c0 * nxy + oc] = p0h;
+        dpl[c0 * nxy + oc] = p0l;
+    }
+    convert(sm.st[1], 0);
+    __syncthreads();
+    issue(0);
+    issue(1);
+    issue(2);
+    const float c_hat = ih2 * st->inv_scale_f;
+    float mx = 0.f, s2f = 0.f, s1f = 0.f;
+    for (int k = 0; k < nk; k++) {
+        cp_async_wait<1>();  // stages k and k + 1
+        __syncthreads();
+        const DmStage &S = sm.st[(k + 2) % DM_NS];
+        const DmStage &S1 = sm.st[(k + 3) % DM_NS];
+        float puh, pul;
+        newval(S, qo, puh, pul);  // plane c0 + k + 1, own column
+        const int c = c0 + k;
+        if (UPDATE && own && c + 1 < c1) {
+            dph[(c + 1) * nxy + oc] = puh;
+            dpl[(c + 1) * nxy + oc] = pul;
+        }
+        if (k + 1 < nk) convert(S, (k + 1) & 1);
+        if (own) {
+            const float *h = sm.ch[k & 1], *l = sm.cl[k & 1];
+            const int bxq = ty * DM_BXX + tx, byq = ty * DM_X + tx;
+            float Sh = 0.f, Se = 0.f;
+            df_term(S.bxh[bxq], S.bxl[bxq], h[qo - 1], l[qo - 1], p0h, p0l, Sh, Se);
+            df_term(S.bxh[bxq + 1], S.bxl[bxq + 1], h[qo + 1], l[qo + 1], p0h, p0l, Sh, Se);
+            df_term(S.byh[byq], S.byl[byq], h[qo - DM_HX], l[qo - DM_HX], p0h, p0l, Sh, Se);
+            df_term(S.byh[byq + DM_X], S.byl[byq + DM_X], h[qo + DM_HX], l[qo + DM_HX], p0h, p0l, Sh, Se);
+            df_term(S.bzh[tid], S.bzl[tid], pmh, pml, p0h, p0l, Sh, Se);
+            df_term(S1.bzh[tid], S1.bzl[tid], puh, pul, p0h, p0l, Sh, Se);
+            float Rh, Re;
+            two_sum(S.fh[tid], -Sh, Rh, Re);
+            Re += S.fl[tid] - Se;
+            const float R = Rh + Re;
+            const float rh = R * c_hat;
+            L.f[c * nxy + oc] = rh;
+            mx = nmaxf(mx, fabsf(rh));
+            s2f = fmaf(rh, rh, s2f);
+            s1f += rh;
+        }
+        issue(k + 3);
+        pmh = p0h;
+        pml = p0l;
+        p0h = puh;
+        p0l = pul;
+    }
+    cp_async_wait<0>();
+    block_red3f(mx, s2f, s1f);
+    if (tid == 0) {
+        double *p = part + 3 * flat_bid();
+        p[0] = double(mx);
+        p[1] = double(s2f);
+        p[2] = double(s1f);
+    }
+}
+
 dim3 df_resid_grid(const DGeom &g) {
     return dim3((g.n[0] + DX - 1) / DX, (g.n[1] + DY - 1) / DY, (g.n[2] + DZ - 1) / DZ);
 }
@@ -539,14 +796,37 @@ int df_resid_blocks(const DGeom &g) {
     return ((g.n[0] + DX - 1) / DX) * ((g.n[1] + DY - 1) / DY) * ((g.n[2] + DZ - 1) / DZ);
 }
 
-void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
-                double *partials, const float *e_odd) {
+int k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
+               double *partials, const float *e_odd) {
     const DGeom &g = L0.g;
     const float ih2 = float(1.0 / (g.h * g.h));
+    if (df_march_ok(g)) {
+        const dim3 grid = df_march_grid(g);
+        const int zc = df_march_zchunk(g);
+        const size_t smem = sizeof(DmShared);
+        if (e) {
+            cudaFuncSetAttribute(df_march_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            launch_pdl(df_march_kernel<true>, grid, dim3(DM_T), smem, s, L0, D, e, e_odd, st, ih2, partials, zc);
+        } else {
+            cudaFuncSetAttribute(df_march_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            launch_pdl(df_march_kernel<false>, grid, dim3(DM_T), smem, s, L0, D, (const float *)nullptr,
+                       (const float *)nullptr, st, ih2, partials, zc);
+        }
+        return int(grid.x * grid.y * grid.z);
+    }
     dim3 grid((g.n[0] + DX - 1) / DX, (g.n[1] + DY - 1) / DY, (g.n[2] + DZ - 1) / DZ);
     if (e) launch_pdl(df_resid_tile_kernel<true>, grid, dim3(DF_THREADS), 0, s, L0, D, e, e_odd, st, ih2, partials);
     else launch_pdl(df_resid_tile_kernel<false>, grid, dim3(DF_THREADS), 0, s, L0, D, (const float *)nullptr,
                     (const float *)nullptr, st, ih2, partials);
+    return int(grid.x * grid.y * grid.z);
+}
+
+int df_resid_parts(const DGeom &g) {
+    if (df_march_ok(g)) {
+        const dim3 d = df_march_grid(g);
+        return int(d.x * d.y * d.z);
+    }
+    return df_resid_blocks(g);
 }
 
 // The first residual of a solve from phi = 0 is f itself: rhat = (h^2 f) c_hat

@@ -33,8 +33,11 @@ void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float 
 // step e (step = SolveState::upd; phi read from buffer (iter-1)&1, written to
 // buffer iter&1) and its residual.  e_odd (optional): the direction to use
 // instead of e when iter is odd.
-void k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
-                double *partials, const float *e_odd = nullptr);
+// Returns the number of partial triples written (one per block).
+int k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
+               double *partials, const float *e_odd = nullptr);
+// the number of partial triples k_df_resid writes for geometry g
+int df_resid_parts(const DGeom &g);
 int df_resid_blocks(const DGeom &g);
 // the residual of phi = 0 (r = f), bit-identical to k_df_resid's there, without the stencil
 void k_df_resid_zero(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials);

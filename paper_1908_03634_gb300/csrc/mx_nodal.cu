@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mx_async.cuh"
 #include "mx_dfmath.cuh"
 #include "mx_solver.cuh"
 #include "mx_stencil.cuh"
@@ -741,19 +742,6 @@ static_assert(THN <= ND_HS * TNT && TCN <= ND_HS * TNT, "halo slots per thread")
 __device__ __forceinline__ float nd_fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double nd_fdiv(double a, double b) { return a / b; }
 
-// sizeof(T)-byte global -> shared copy of the first n bytes, the rest zero
-// filled (n = 0: src names a valid address but no byte is read)
-template <typename T>
-__device__ __forceinline__ void cp_async_el(T *dst, const T *src, int n) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T>
 struct NdStage {

@@ -146,7 +146,8 @@ mx_status ensure_partials(mx_ctx *c, long long nblocks) {
 }
 
 MacPlan *get_mac_plan(mx_ctx *c, const DGeom &g, int prec, mx_status *st) {
-    *st = ensure_partials(c, std::max<long long>(std::max(stencil_blocks(g), kry_dir_blocks(g)), red_blocks(g.N)));
+    *st = ensure_partials(c, std::max<long long>(std::max(std::max(stencil_blocks(g), kry_dir_blocks(g)), red_blocks(g.N)),
+                                                 std::max(df_resid_blocks(g), df_resid_parts(g))));
     if (*st) return nullptr;
     for (MacPlan *p : c->plans)
         if (p->prec == prec && same_geom(p->g, g)) {
@@ -285,8 +286,8 @@ static void ir_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, const
                     mx_ctx *pc) {
     vcycle(s, H, o.nu1, o.nu2, o.bottom_iters, singular, pc, o.fused, o.tile_z ? o.tile_z : 8);
     prof_begin(pc, s, MX_PH_RESID64);  // update phi += scale e fused with the next residual
-    k_df_resid(s, H.lev[0], P.D, H.lev[0].e, c->state, c->partials);
-    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
+    const int np = k_df_resid(s, H.lev[0], P.D, H.lev[0].e, c->state, c->partials);
+    k_finalize_residual(s, c->partials, np, c->state, 1);
     prof_end(pc, s, MX_PH_RESID64, 2);
 }
 // One FCG(1) iteration after the residual (mx_krylov.cu): V-cycle, conjugate
@@ -300,8 +301,8 @@ static void fcg_body(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, cons
     k_kry_dir(s, L0, L0.e, P.kp0, P.kp1, P.kq, c->state, c->partials);
     prof_end(pc, s, MX_PH_UPDATE, 4);
     prof_begin(pc, s, MX_PH_RESID64);
-    k_df_resid(s, L0, P.D, P.kp0, c->state, c->partials, P.kp1);
-    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
+    const int np = k_df_resid(s, L0, P.D, P.kp0, c->state, c->partials, P.kp1);
+    k_finalize_residual(s, c->partials, np, c->state, 1);
     prof_end(pc, s, MX_PH_RESID64, 2);
 }
 // Plain FP64: FP64 V-cycle, FP64 update and residual.
@@ -322,9 +323,10 @@ static void ir_first_residual(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<T> &H,
 template <>
 void ir_first_residual<float>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<float> &H, double *, int nb, int zero_phi) {
     (void)nb;
+    int np = df_resid_blocks(P.g);
     if (zero_phi) k_df_resid_zero(s, H.lev[0], P.D, c->state, c->partials);  // r = f
-    else k_df_resid(s, H.lev[0], P.D, nullptr, c->state, c->partials);
-    k_finalize_residual(s, c->partials, df_resid_blocks(P.g), c->state, 1);
+    else np = k_df_resid(s, H.lev[0], P.D, nullptr, c->state, c->partials);
+    k_finalize_residual(s, c->partials, np, c->state, 1);
 }
 template <>
 void ir_first_residual<double>(cudaStream_t s, mx_ctx *c, MacPlan &P, Hier<double> &H, double *phi, int nb, int) {
