@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--n", type=int, default=N, help="cube edge of the planar workload")
     p.add_argument("--star-n", type=int, default=512, help="cube edge of the average512 workload")
     p.add_argument("--comp-n", type=int, default=128, help="coarse cube edge of the composite workload")
+    p.add_argument("--nodal-n", type=int, default=384,
+                   help="cube edge of --workload nodal384 (smaller cases for profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-fcg", action="store_true", help="skip the krylov = 1 comparison")
@@ -1008,7 +1010,7 @@ def run_other(args):
                        cpu=not args.no_cpu_baseline, n=args.star_n)
         print(json.dumps(r), flush=True)
     elif args.workload == "nodal384":
-        r = bench_nodal(mx, W, ctx, dev, stream, n=384, steps=args.steps, warmup=args.warmup,
+        r = bench_nodal(mx, W, ctx, dev, stream, n=args.nodal_n, steps=args.steps, warmup=args.warmup,
                         fp64=not args.no_fp64, hbm=hbm, graph=not args.no_graph, fixed=args.fixed)
         print(json.dumps(r), flush=True)
     elif args.workload == "batched96":
