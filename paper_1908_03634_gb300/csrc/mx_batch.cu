@@ -27,6 +27,7 @@ struct BatchPlan {
     std::vector<MacPlan *> box;
     std::vector<int> lc;       // first level of each box's coarse end
     int maxdown = 0;           // deepest per-level phase over all boxes
+    int march = 0;             // the double-float residual's work list is of z-march blocks
     // device-side descriptors
     void *mem = nullptr;
     Level<float> *d_levs = nullptr;  // [nbox * MX_MAXLEV]
@@ -125,10 +126,13 @@ static BatchPlan *build_batch(mx_ctx *c, int nbox, const DGeom *g, const mx_opts
         B->pr[l].n = int(work.size()) - B->pr[l].off;
     }
     B->df.off = int(work.size());
-    std::vector<int> off(nbox), cnt(nbox);
+    std::vector<int> off(nbox), cnt(nbox), zcs(nbox);
+    B->march = 1;  // the residual as a z-march when every box allows it
+    for (int b = 0; b < nbox; b++)
+        if (!df_march_usable(g[b])) B->march = 0;
     int parts = 0;
     for (int b = 0; b < nbox; b++) {
-        const dim3 gr = df_resid_grid(g[b]);
+        const dim3 gr = df_resid_batch_grid(g[b], B->march, &zcs[b]);
         add_grid(work, b, gr);
         off[b] = parts;
         cnt[b] = int(gr.x * gr.y * gr.z);
@@ -168,6 +172,7 @@ static BatchPlan *build_batch(mx_ctx *c, int nbox, const DGeom *g, const mx_opts
         dfb[b].L0 = H.lev[0];
         dfb[b].D = B->box[b]->D;
         dfb[b].part_off = off[b];
+        dfb[b].zc = zcs[b];
         const int lc = B->lc[b];
         coarse_fill_args(cargs.data() + cab * b, &H.lev[lc], H.nlev - lc, o.nu1, o.nu2, o.bottom_iters,
                          geom_singular(g[b]));
@@ -229,7 +234,7 @@ static void batch_body(cudaStream_t s, mx_ctx *c, BatchPlan &B, const mx_opts &o
             k_rbgs_batch(s, B.d_levs, B.d_work + B.rb[l].off, B.rb[l].n, B.d_st, l, 1, 0);
         }
     }
-    k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 1);
+    k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 1, B.march);
     k_finalize_residual_batch(s, c->partials, B.d_off, B.d_cnt, B.d_st, B.nbox);
 }
 
@@ -377,7 +382,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
     }
     if ((st = join())) return st;
     // refinement loop over all boxes
-    k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 0);
+    k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 0, B.march);
     k_finalize_residual_batch(s, c->partials, B.d_off, B.d_cnt, B.d_st, nbox);
     MX_CUDA(c, cudaMemcpyAsync(B.h_st, B.d_st, sizeof(SolveState) * nbox, cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));

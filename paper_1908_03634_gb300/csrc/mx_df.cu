@@ -525,13 +525,6 @@ __global__ void __launch_bounds__(DF_THREADS)
     df_resid_body<UPDATE>(L, D, UPDATE ? L.e : nullptr, &st[w.x], float(1.0 / (g.h * g.h)), p, w.y, w.z, w.w);
 }
 
-void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
-                      double *partials, int update) {
-    if (nwork <= 0) return;
-    if (update) df_resid_batch_kernel<true><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
-    else df_resid_batch_kernel<false><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
-}
-
 // ---- the same residual as a z-march --------------------------------------------
 // A block of 32 x 8 threads owns a 32 x 8 tile of cell columns over nzc planes.
 // Step k (cell plane c0 + k) reads one "stage" (this block's slice of the
@@ -575,22 +568,21 @@ static dim3 df_march_grid(const DGeom &g) {
 }
 static bool df_march_ok(const DGeom &g) { return g.n[0] >= DM_X && g.N < (1LL << 31); }
 
+// one block's march: tile (bx, by), z-chunk bz of nzc planes; partials to p
 template <bool UPDATE>
-__global__ void __launch_bounds__(DM_T, 2)
-    df_march_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
-                    const SolveState *st, float ih2, double *part, int nzc) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArrays &D, const float *__restrict__ e,
+                                              const float *__restrict__ e_odd, const SolveState *st, float ih2,
+                                              double *p, int bx, int by, int bz, int nzc) {
     extern __shared__ __align__(16) unsigned char dm_smem[];
     DmShared &sm = *reinterpret_cast<DmShared *>(dm_smem);
     const DGeom &g = L.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxy = nx * ny;
     const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
     const int tid = threadIdx.x, tx = tid % DM_X, ty = tid / DM_X;
-    const int x0 = blockIdx.x * DM_X, y0 = blockIdx.y * DM_Y;
+    const int x0 = bx * DM_X, y0 = by * DM_Y;
     const int i = x0 + tx, j = y0 + ty;
     const bool own = i < nx && j < ny;
-    const int c0 = blockIdx.z * nzc, c1 = min(c0 + nzc, nz);
+    const int c0 = bz * nzc, c1 = min(c0 + nzc, nz);
     const int nk = c1 - c0;
     const int it = st->iter;
     const int src = UPDATE ? ((it - 1) & 1) : (it & 1), dst = it & 1;
@@ -781,11 +773,36 @@ __global__ void __launch_bounds__(DM_T, 2)
     cp_async_wait<0>();
     block_red3f(mx, s2f, s1f);
     if (tid == 0) {
-        double *p = part + 3 * flat_bid();
         p[0] = double(mx);
         p[1] = double(s2f);
         p[2] = double(s1f);
     }
+}
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(DM_T, 2)
+    df_march_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
+                    const SolveState *st, float ih2, double *part, int nzc) {
+    pdl_trigger();
+    pdl_wait();
+    df_march_body<UPDATE>(L, D, e, e_odd, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z, nzc);
+}
+
+// batched: work[blockIdx.x] = (box, bx, by, z-chunk) over each box's march grid;
+// the box's partials start at boxes[box].part_off (block bx + nbx (by + nby bz))
+template <bool UPDATE>
+__global__ void __launch_bounds__(DM_T, 2)
+    df_march_batch_kernel(const DFBox *boxes, const int4 *work, const SolveState *st, double *part) {
+    const int4 w = work[blockIdx.x];
+    if (st[w.x].done) return;
+    const DFBox &B = boxes[w.x];
+    const Level<float> L = B.L0;
+    const DFArrays D = B.D;
+    const DGeom &g = L.g;
+    const int nbx = (g.n[0] + DM_X - 1) / DM_X, nby = (g.n[1] + DM_Y - 1) / DM_Y;
+    double *p = part + 3 * ((long long)B.part_off + w.y + nbx * (w.z + nby * w.w));
+    df_march_body<UPDATE>(L, D, UPDATE ? L.e : nullptr, nullptr, &st[w.x], float(1.0 / (g.h * g.h)), p, w.y, w.z, w.w,
+                          B.zc);
 }
 
 dim3 df_resid_grid(const DGeom &g) {
@@ -795,6 +812,36 @@ dim3 df_resid_grid(const DGeom &g) {
 int df_resid_blocks(const DGeom &g) {
     return ((g.n[0] + DX - 1) / DX) * ((g.n[1] + DY - 1) / DY) * ((g.n[2] + DZ - 1) / DZ);
 }
+
+void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
+                      double *partials, int update, int march) {
+    if (nwork <= 0) return;
+    if (march) {
+        const size_t smem = sizeof(DmShared);
+        if (update) {
+            cudaFuncSetAttribute(df_march_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            df_march_batch_kernel<true><<<nwork, DM_T, smem, s>>>(boxes, work, st, partials);
+        } else {
+            cudaFuncSetAttribute(df_march_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            df_march_batch_kernel<false><<<nwork, DM_T, smem, s>>>(boxes, work, st, partials);
+        }
+        return;
+    }
+    if (update) df_resid_batch_kernel<true><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
+    else df_resid_batch_kernel<false><<<nwork, DF_THREADS, 0, s>>>(boxes, work, st, partials);
+}
+
+dim3 df_resid_batch_grid(const DGeom &g, int march, int *zc) {
+    if (march) {
+        // deep chunks: the blocks of all boxes fill the GPU together, so no box
+        // needs to be cut finer (each chunk re-reads two halo planes)
+        *zc = 64;
+        return dim3((g.n[0] + DM_X - 1) / DM_X, (g.n[1] + DM_Y - 1) / DM_Y, (g.n[2] + 63) / 64);
+    }
+    *zc = 0;
+    return df_resid_grid(g);
+}
+bool df_march_usable(const DGeom &g) { return df_march_ok(g); }
 
 int k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
                double *partials, const float *e_odd) {

@@ -48,9 +48,14 @@ struct DFBox {
     Level<float> L0;  // finest FP32 level (L0.e: the V-cycle correction, L0.f: rhat)
     DFArrays D;
     int part_off;     // first reduction partial of the box
+    int zc;           // z-chunk of the box's march grid (march work lists)
 };
+// the batched residual over a work list of df_resid_batch_grid entries: the
+// z-march (march = 1, every box df_march_usable) or the 3D-tile kernel
 void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
-                      double *partials, int update);
+                      double *partials, int update, int march);
+dim3 df_resid_batch_grid(const DGeom &g, int march, int *zc);
+bool df_march_usable(const DGeom &g);
 // phi (double) from the current double-float buffer; partials (may be null):
 // per-block (0, sum phi, 0) on red_blocks(n) blocks
 void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x,
