@@ -336,65 +336,144 @@ __global__ void nd_rhs_final_kernel(NGeom g, double *__restrict__ f, const Solve
 // ---- multigrid kernels (T = float or double) -----------------------------------------
 
 // coarse f = full-weighting restriction of the fine residual (node weights):
-// f_C = (1/(8 w_C)) sum_n P(n, C) w_n r_n; coarse e = 0
+// f_C = (1/(8 w_C)) sum_n P(n, C) w_n r_n; coarse e = 0.  One coarse node column
+// per thread, marched in z: the 3 x 3 fine neighbourhood of plane 2C + 1 is kept
+// for the next coarse plane (where it is plane 2C' - 1); the in-plane positions
+// and weights are computed once per column.  Every weight is a power of two, so
+// each term is exact; they are summed in the order oz, oy, ox.
 template <typename T>
-__global__ void nd_restrict_kernel(NLevel<T> F, NLevel<T> C) {
+__global__ void __launch_bounds__(256) nd_restrict_march_kernel(NLevel<T> F, NLevel<T> C, int zc) {
     pdl_trigger();
     pdl_wait();
     const NGeom &g = F.g, &gc = C.g;
-    for (long long Q = blockIdx.x * (long long)blockDim.x + threadIdx.x; Q < gc.M; Q += (long long)gridDim.x * blockDim.x) {
-        int A, B, Cc;
-        node_of(gc, Q, A, B, Cc);
+    const int A = blockIdx.x * 32 + threadIdx.x, B = blockIdx.y * 8 + threadIdx.y;
+    if (A >= gc.m[0] || B >= gc.m[1]) return;
+    const int C0 = blockIdx.z * zc, C1 = min(C0 + zc, gc.m[2]);
+    int fa[3], fb[3];
+    float wx[3], wy[3];
+    for (int o = 0; o < 3; o++) {
+        fa[o] = node_wrap(g, 0, 2 * A + o - 1);
+        fb[o] = node_wrap(g, 1, 2 * B + o - 1);
+        wx[o] = (o != 1 ? 0.5f : 1.f) * ((fa[o] >= 0 && !g.per[0] && (fa[o] == 0 || fa[o] == g.m[0] - 1)) ? 0.5f : 1.f);
+        wy[o] = (o != 1 ? 0.5f : 1.f) * ((fb[o] >= 0 && !g.per[1] && (fb[o] == 0 || fb[o] == g.m[1] - 1)) ? 0.5f : 1.f);
+    }
+    const float wxyC = ((!gc.per[0] && (A == 0 || A == gc.m[0] - 1)) ? 0.5f : 1.f) *
+                       ((!gc.per[1] && (B == 0 || B == gc.m[1] - 1)) ? 0.5f : 1.f);
+    T v[3][3][3];  // [oz][oy][ox]
+    auto load = [&](int c, T p[3][3]) {
+        const int cz = node_wrap(g, 2, c);
+        for (int y = 0; y < 3; y++)
+            for (int x = 0; x < 3; x++)
+                p[y][x] = (cz >= 0 && fa[x] >= 0 && fb[y] >= 0) ? F.r[nidx(g, fa[x], fb[y], cz)] : T(0);
+    };
+    load(2 * C0 - 1, v[0]);
+    for (int Cz = C0; Cz < C1; Cz++) {
+        load(2 * Cz, v[1]);
+        load(2 * Cz + 1, v[2]);
         T acc = T(0);
-        for (int oz = -1; oz <= 1; oz++)
-            for (int oy = -1; oy <= 1; oy++)
-                for (int ox = -1; ox <= 1; ox++) {
-                    const int a = node_wrap(g, 0, 2 * A + ox), b = node_wrap(g, 1, 2 * B + oy), c = node_wrap(g, 2, 2 * Cc + oz);
-                    if (a < 0 || b < 0 || c < 0) continue;
-                    const T wt = T((ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f) * (oz ? 0.5f : 1.f));
-                    acc += wt * T(node_w(g, a, b, c)) * F.r[nidx(g, a, b, c)];
+        for (int oz = 0; oz < 3; oz++) {
+            const int cz = node_wrap(g, 2, 2 * Cz + oz - 1);
+            if (cz < 0) continue;
+            const float wz = (oz != 1 ? 0.5f : 1.f) * ((!g.per[2] && (cz == 0 || cz == g.m[2] - 1)) ? 0.5f : 1.f);
+            for (int oy = 0; oy < 3; oy++) {
+                if (fb[oy] < 0) continue;
+                for (int ox = 0; ox < 3; ox++) {
+                    if (fa[ox] < 0) continue;
+                    // the offset factors times the fine node's weight
+                    acc += T(wx[ox] * wy[oy] * wz) * v[oz][oy][ox];
                 }
-        C.f[Q] = acc / (T(8) * T(node_w(gc, A, B, Cc)));
+            }
+        }
+        const long long Q = nidx(gc, A, B, Cz);
+        const float wC = wxyC * ((!gc.per[2] && (Cz == 0 || Cz == gc.m[2] - 1)) ? 0.5f : 1.f);
+        C.f[Q] = acc / (T(8) * T(wC));
         C.e[Q] = T(0);
+        for (int y = 0; y < 3; y++)
+            for (int x = 0; x < 3; x++) v[0][y][x] = v[2][y][x];
     }
 }
 
-// e_fine += trilinear interpolation of e_coarse (out non-null: out = e_fine + it)
+// e_fine += trilinear interpolation of e_coarse (out non-null: out = e_fine +
+// it), one fine node column per thread, marched in z: the in-plane parents and
+// weights are computed once per column and the parents' values of a coarse
+// plane are loaded once for the (up to three) fine planes that use them; the
+// terms (every weight a power of two) are added coarse plane by plane, then
+// along y, then x.
 template <typename T>
-__global__ void nd_prolong_kernel(NLevel<T> C, NLevel<T> F, T *out) {
+__global__ void __launch_bounds__(256) nd_prolong_march_kernel(NLevel<T> C, NLevel<T> F, T *out, int zc) {
     pdl_trigger();
     pdl_wait();
     const NGeom &g = F.g, &gc = C.g;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
-        int a, b, c;
-        node_of(g, q, a, b, c);
-        int ia[2], ib[2], ic[2];
-        T wa[2], wb[2], wc[2];
-        int na = 1, nb = 1, nc = 1;
-        auto par = [&](int x, int d, int *ix, T *w, int &cnt) {
-            if ((x & 1) == 0) {
-                ix[0] = x / 2;
-                w[0] = T(1);
-                cnt = 1;
-            } else {
-                ix[0] = (x - 1) / 2;
-                ix[1] = (x + 1) / 2;
-                if (gc.per[d] && ix[1] == gc.m[d]) ix[1] = 0;
-                w[0] = w[1] = T(0.5);
-                cnt = 2;
-            }
-        };
-        par(a, 0, ia, wa, na);
-        par(b, 1, ib, wb, nb);
-        par(c, 2, ic, wc, nc);
+    const int a = blockIdx.x * 32 + threadIdx.x, b = blockIdx.y * 8 + threadIdx.y;
+    if (a >= g.m[0] || b >= g.m[1]) return;
+    const int c0 = blockIdx.z * zc, c1 = min(c0 + zc, g.m[2]);
+    int ia[2], ib[2], na, nb;
+    T wa[2], wb[2];
+    auto par = [&](int x, int d, int *ix, T *w, int &cnt) {
+        if ((x & 1) == 0) {
+            ix[0] = ix[1] = x / 2;
+            w[0] = T(1);
+            w[1] = T(0);
+            cnt = 1;
+        } else {
+            ix[0] = (x - 1) / 2;
+            ix[1] = (x + 1) / 2;
+            if (gc.per[d] && ix[1] == gc.m[d]) ix[1] = 0;
+            w[0] = w[1] = T(0.5);
+            cnt = 2;
+        }
+    };
+    par(a, 0, ia, wa, na);
+    par(b, 1, ib, wb, nb);
+    // the parents' values of coarse plane Cz: p[v][t]
+    auto load = [&](int Cz, T p[2][2]) {
+        for (int v = 0; v < 2; v++)
+            for (int t = 0; t < 2; t++) p[v][t] = (v < nb && t < na) ? C.e[nidx(gc, ia[t], ib[v], Cz)] : T(0);
+    };
+    auto terms = [&](T &s, const T p[2][2], T wc) {
+        for (int v = 0; v < nb; v++)
+            for (int t = 0; t < na; t++) s += wa[t] * wb[v] * wc * p[v][t];
+    };
+    T lo[2][2], hi[2][2];
+    int Clo = c0 / 2;  // the coarse plane at or below the first fine plane
+    load(Clo, lo);
+    int Chi = -1;      // coarse plane held in hi (-1: none)
+    for (int c = c0; c < c1; c++) {
+        const long long q = nidx(g, a, b, c);
         T s = T(0);
-        for (int u = 0; u < nc; u++)
-            for (int v = 0; v < nb; v++)
-                for (int t = 0; t < na; t++) s += wa[t] * wb[v] * wc[u] * C.e[nidx(gc, ia[t], ib[v], ic[u])];
+        if ((c & 1) == 0) {
+            if (c / 2 != Clo) {  // advance: the plane above becomes the plane below
+                if (Chi == c / 2) {
+                    for (int v = 0; v < 2; v++)
+                        for (int t = 0; t < 2; t++) lo[v][t] = hi[v][t];
+                } else {
+                    load(c / 2, lo);
+                }
+                Clo = c / 2;
+            }
+            terms(s, lo, T(1));
+        } else {
+            int Cu = (c + 1) / 2;
+            if (gc.per[2] && Cu == gc.m[2]) Cu = 0;
+            if (Chi != Cu) {
+                load(Cu, hi);
+                Chi = Cu;
+            }
+            terms(s, lo, T(0.5));
+            terms(s, hi, T(0.5));
+        }
         if (out) out[q] = F.e[q] + s;
         else F.e[q] += s;
     }
 }
+
+static int nd_xfer_zc(const NGeom &g) {
+    const long long bxy = (long long)((g.m[0] + 31) / 32) * ((g.m[1] + 7) / 8);
+    int zc = 32;
+    while (zc > 2 && bxy * ((g.m[2] + zc - 1) / zc) < 8 * 152) zc >>= 1;
+    return zc;
+}
+
 
 // y = L x
 template <typename T>
@@ -1824,7 +1903,12 @@ static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int
             prof_begin(pc, s, MX_PH_RESTRICT_FINE);
         }
         k_nd_residual(s, L[l], zcap);
-        launch_pdl(nd_restrict_kernel<T>, dim3(nblk(L[l + 1].g.M)), dim3(256), 0, s, L[l], L[l + 1]);
+        {
+            const NGeom &gc = L[l + 1].g;
+            const int zc = nd_xfer_zc(gc);
+            launch_pdl(nd_restrict_march_kernel<T>, dim3((gc.m[0] + 31) / 32, (gc.m[1] + 7) / 8, (gc.m[2] + zc - 1) / zc),
+                       dim3(32, 8), 0, s, L[l], L[l + 1], zc);
+        }
         if (l == 0) {
             prof_end(pc, s, MX_PH_RESTRICT_FINE, 2);
             prof_begin(pc, s, MX_PH_COARSE);
@@ -1839,8 +1923,12 @@ static void nd_vcycle(cudaStream_t s, NLevel<T> *L, int nl, T *bot, int nu1, int
             prof_begin(pc, s, MX_PH_PROLONG_FINE);
         }
         const bool odd = cheb && nu2 % 2 == 1;
-        launch_pdl(nd_prolong_kernel<T>, dim3(nblk(L[l].g.M)), dim3(256), 0, s, L[l + 1], L[l],
-                   odd ? L[l].e2 : (T *)nullptr);
+        {
+            const NGeom &gf = L[l].g;
+            const int zc = nd_xfer_zc(gf);
+            launch_pdl(nd_prolong_march_kernel<T>, dim3((gf.m[0] + 31) / 32, (gf.m[1] + 7) / 8, (gf.m[2] + zc - 1) / zc),
+                       dim3(32, 8), 0, s, L[l + 1], L[l], odd ? L[l].e2 : (T *)nullptr, zc);
+        }
         if (l == 0) {
             prof_end(pc, s, MX_PH_PROLONG_FINE, 1);
             prof_begin(pc, s, MX_PH_SMOOTH_FINE);
