@@ -241,16 +241,7 @@ void k_sub_mean_norm(cudaStream_t s, const DGeom &g, double *f, const SolveState
 __device__ __forceinline__ void correct_face(const DGeom &g, int d, int p, long long cl, long long cr, long long ci,
                                              const double *__restrict__ phi, double q, double *__restrict__ u,
                                              long long f) {
-    // one FP64 expression for every face kind: U -= q (phi_R - phi_L), with
-    // phi = 0 outside a Dirichlet face and U = 0 on a wall
-    const int n = g.n[d];
-    const bool inner = (p > 0 && p < n) || gper(g, d);
-    const int bc = p == 0 ? g.lo[d] : g.hi[d];
-    const bool wall = !inner && bc != MX_BC_DIRICHLET;
-    const double pr = (inner || p == 0) ? phi[inner ? cr : ci] : 0.0;
-    const double pl = (inner || p != 0) ? phi[inner ? cl : ci] : 0.0;
-    const double un = fma(-q, pr - pl, u[f]);
-    u[f] = wall ? 0.0 : un;
+    u[f] = corr_face_value(g, d, p, cl, cr, ci, phi, q, u[f]);
 }
 
 __global__ void mac_correct_kernel(DGeom g, FaceQ Q, const double *__restrict__ phi, double *__restrict__ ux,

@@ -17,6 +17,22 @@ __device__ __forceinline__ void face_coefs(const Level<T> &L, int i, int j, int 
     b[5] = (k + 1 < nz) ? L.bz[c + g.nxy] : (gper(g, 2) ? L.bz[c - (long long)(nz - 1) * g.nxy] : L.hz[i + (long long)nx * j]);
 }
 
+// The corrected MAC face velocity U_f - q_f (phi_R - phi_L) (Appendix A's
+// correction): face p of axis d between cells cl and cr (ci: the interior cell
+// of a boundary face), phi = 0 outside a Dirichlet face, U = 0 on a wall face.
+// One FP64 expression for every face kind, shared by the correction kernels.
+__device__ __forceinline__ double corr_face_value(const DGeom &g, int d, int p, long long cl, long long cr,
+                                                  long long ci, const double *__restrict__ phi, double q, double u) {
+    const int n = g.n[d];
+    const bool inner = (p > 0 && p < n) || gper(g, d);
+    const int bc = p == 0 ? g.lo[d] : g.hi[d];
+    const bool wall = !inner && bc != MX_BC_DIRICHLET;
+    const double pr = (inner || p == 0) ? phi[inner ? cr : ci] : 0.0;
+    const double pl = (inner || p != 0) ? phi[inner ? cl : ci] : 0.0;
+    const double un = fma(-q, pr - pl, u);
+    return wall ? 0.0 : un;
+}
+
 // The 6 neighbour values of cell (i,j,k); 0 beyond a non-periodic face.
 template <typename T>
 __device__ __forceinline__ void nb_vals(const DGeom &g, const T *p, int i, int j, int k, long long c, T v[6]) {
