@@ -16,3 +16,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most N of this thread's most recent groups are in flight
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// 16-byte global -> shared copy (both addresses 16-byte aligned) of the first n
+// bytes (0 or 16), the rest zero filled; cached in L2 only
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int n) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}

@@ -127,9 +127,8 @@ static BatchPlan *build_batch(mx_ctx *c, int nbox, const DGeom *g, const mx_opts
     }
     B->df.off = int(work.size());
     std::vector<int> off(nbox), cnt(nbox), zcs(nbox);
-    B->march = 1;  // the residual as a z-march when every box allows it
-    for (int b = 0; b < nbox; b++)
-        if (!df_march_usable(g[b])) B->march = 0;
+    B->march = 2;  // the residual as a z-march (2: with row chunks) when every box allows it
+    for (int b = 0; b < nbox; b++) B->march = std::min(B->march, df_march_usable(g[b]));
     int parts = 0;
     for (int b = 0; b < nbox; b++) {
         const dim3 gr = df_resid_batch_grid(g[b], B->march, &zcs[b]);

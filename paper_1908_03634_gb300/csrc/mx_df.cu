@@ -543,17 +543,25 @@ constexpr int DM_BXX = DM_X + 1, DM_BXN = DM_BXX * DM_Y;    // x faces (with the
 constexpr int DM_BYN = DM_X * (DM_Y + 1);                   // y faces (with the tile's high row)
 constexpr int DM_NS = 4;
 static_assert(DM_HN <= 2 * DM_T && DM_BXN <= 2 * DM_T && DM_BYN <= 2 * DM_T, "two slots per thread");
+// The wide variant (n_x a multiple of 4) stages whole rows in 16-byte chunks:
+// the phi plane from x0 - 4 (pitch 40), the x faces from x0 (pitch 36).
+constexpr int DW_PX = 40, DW_PN = DW_PX * (DM_Y + 2);
+constexpr int DW_BXP = 36, DW_BXN = DW_BXP * DM_Y;
+constexpr int DW_ITEMS = 100 + 72 + 72 + 64 + 64;  // chunk positions: phi, x faces, y faces, z faces, f
+static_assert(DW_ITEMS <= 2 * DM_T, "two chunk items per thread");
 
 struct DmStage {
-    float ph[DM_HN], pl[DM_HN], pe[DM_HN];
-    float bxh[DM_BXN], bxl[DM_BXN];
+    float ph[DW_PN], pl[DW_PN], pe[DW_PN];
+    float bxh[DW_BXN], bxl[DW_BXN];
     float byh[DM_BYN], byl[DM_BYN];
     float bzh[DM_T], bzl[DM_T];
     float fh[DM_T], fl[DM_T];
 };
+static_assert(DW_PN >= DM_HN && DW_BXN >= DM_BXN && (DW_PN % 4) == 0 && (DW_BXN % 4) == 0 && (DM_BYN % 4) == 0,
+              "both layouts fit; 16-byte aligned arrays");
 struct DmShared {
     DmStage st[DM_NS];
-    float ch[2][DM_HN], cl[2][DM_HN];  // phi_new of plane c0 + k (buffer k & 1)
+    float ch[2][DW_PN], cl[2][DW_PN];  // phi_new of plane c0 + k (buffer k & 1)
 };
 
 static int df_march_zchunk(const DGeom &g) {
@@ -567,9 +575,10 @@ static dim3 df_march_grid(const DGeom &g) {
     return dim3((g.n[0] + DM_X - 1) / DM_X, (g.n[1] + DM_Y - 1) / DM_Y, (g.n[2] + zc - 1) / zc);
 }
 static bool df_march_ok(const DGeom &g) { return g.n[0] >= DM_X && g.N < (1LL << 31); }
+static bool df_march_wide(const DGeom &g) { return g.n[0] % 4 == 0; }
 
 // one block's march: tile (bx, by), z-chunk bz of nzc planes; partials to p
-template <bool UPDATE>
+template <bool UPDATE, bool WIDE>
 __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArrays &D, const float *__restrict__ e,
                                               const float *__restrict__ e_odd, const SolveState *st, float ih2,
                                               double *p, int bx, int by, int bz, int nzc) {
@@ -600,8 +609,54 @@ __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArr
     // there).  x faces: kind 1 = bx at (offset, plane stride nxy), kind 2 = the
     // high plane hx at (offset, plane stride ny), 0 = no copy; y faces alike
     // (hy: plane stride nx).
+    constexpr int PX = WIDE ? DW_PX : DM_HX, XO = WIDE ? 4 : 1, BXP = WIDE ? DW_BXP : DM_BXX;
     int po[2], xo[2], yo[2], pmask = 0, xk = 0, yk = 0;
-    for (int s = 0; s < 2; s++) {
+    // wide: this thread's chunk items (wtyp: 0 phi, 1 x faces, 2 y faces, 3 z
+    // faces, 4 f; wkind: 0 none (phi: zero fill), 1 main array, 2 high boundary
+    // plane; wdst: float offset in the stage array; woff: in-plane offset)
+    int wtyp[2] = {-1, -1}, wkind[2] = {0, 0}, wdst[2] = {0, 0}, woff[2] = {0, 0};
+    for (int s = 0; s < 2 && WIDE; s++) {
+        const int q = tid + s * DM_T;
+        if (q >= DW_ITEMS) break;
+        if (q < 100) {  // phi: 10 rows x 10 chunks from x0 - 4
+            const int yy = q / 10, cc = q % 10, xs = x0 - 4 + 4 * cc;
+            const int ly = df_map(y0 - 1 + yy, ny, py);
+            const int lx = (xs >= 0 && xs + 4 <= nx) ? xs : (xs == -4 && px) ? nx - 4 : (xs == nx && px) ? 0 : -1;
+            wtyp[s] = 0;
+            wdst[s] = yy * DW_PX + 4 * cc;
+            wkind[s] = (lx >= 0 && ly >= 0) ? 1 : 0;
+            woff[s] = wkind[s] ? lx + nx * ly : 0;
+        } else if (q < 172) {  // x faces: 8 rows x 9 chunks from x0
+            const int r = q - 100, yy = r / 9, cc = r % 9, x = x0 + 4 * cc, y = y0 + yy;
+            wtyp[s] = 1;
+            wdst[s] = yy * DW_BXP + 4 * cc;
+            if (y < ny && x + 4 <= nx) {
+                wkind[s] = 1;
+                woff[s] = x + nx * y;
+            } else if (y < ny && x == nx) {
+                wkind[s] = px ? 1 : 2;  // periodic: the row's first faces; else hx (one face)
+                woff[s] = px ? nx * y : y;
+            }
+        } else if (q < 244) {  // y faces: 9 rows x 8 chunks
+            const int r = q - 172, yy = r / 8, cc = r % 8, x = x0 + 4 * cc, y = y0 + yy;
+            wtyp[s] = 2;
+            wdst[s] = yy * DM_X + 4 * cc;
+            if (x < nx && y < ny) {
+                wkind[s] = 1;
+                woff[s] = x + nx * y;
+            } else if (x < nx && y == ny) {
+                wkind[s] = py ? 1 : 2;
+                woff[s] = x;
+            }
+        } else {  // z faces or f: 8 rows x 8 chunks of the tile
+            const int r = q < 308 ? q - 244 : q - 308, yy = r / 8, cc = r % 8, x = x0 + 4 * cc, y = y0 + yy;
+            wtyp[s] = q < 308 ? 3 : 4;
+            wdst[s] = yy * DM_X + 4 * cc;
+            wkind[s] = (x < nx && y < ny) ? 1 : 0;
+            woff[s] = wkind[s] ? x + nx * y : 0;
+        }
+    }
+    for (int s = 0; s < 2 && !WIDE; s++) {
         const int q = tid + s * DM_T;
         po[s] = xo[s] = yo[s] = 0;
         if (q < DM_HN) {
@@ -646,7 +701,56 @@ __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArr
     const int oc = own ? i + nx * j : 0;  // own column, in-plane
     // stage k: phi raw of plane c0 + k + 1 (k in [-2, nk - 1]); faces and f of
     // plane c0 + k (k in [0, nk - 1]); low z faces of plane c0 + k (k in [0, nk])
+    auto issue_wide = [&](int k) {
+        DmStage &S = sm.st[(k + 2) % DM_NS];
+        const int c = c0 + k;
+        for (int s = 0; s < 2; s++) {
+            const int t = wtyp[s], kd = wkind[s], d = wdst[s], o = woff[s];
+            if (t == 0) {
+                if (k <= nk - 1) {
+                    const int p = df_map(c0 + k + 1, nz, pz);
+                    const int n = (p >= 0 && kd) ? 16 : 0;
+                    const int base = (p >= 0 && kd) ? p * nxy + o : 0;
+                    cp_async16(&S.ph[d], sph + base, n);
+                    cp_async16(&S.pl[d], spl + base, n);
+                    if (UPDATE) cp_async16(&S.pe[d], ee + base, n);
+                }
+            } else if (t == 1) {
+                if (k >= 0 && k <= nk - 1 && kd == 1) {
+                    cp_async16(&S.bxh[d], L.bx + c * nxy + o, 16);
+                    cp_async16(&S.bxl[d], D.bxl + c * nxy + o, 16);
+                } else if (k >= 0 && k <= nk - 1 && kd == 2) {
+                    cp_async_el(&S.bxh[d], L.hx + c * ny + o, 4);
+                    cp_async_el(&S.bxl[d], D.hxl + c * ny + o, 4);
+                }
+            } else if (t == 2) {
+                if (k >= 0 && k <= nk - 1 && kd) {
+                    const float *hh = kd == 1 ? L.by + c * nxy : L.hy + c * nx;
+                    const float *hl = kd == 1 ? D.byl + c * nxy : D.hyl + c * nx;
+                    cp_async16(&S.byh[d], hh + o, 16);
+                    cp_async16(&S.byl[d], hl + o, 16);
+                }
+            } else if (t == 3) {
+                if (k >= 0 && k <= nk && kd) {
+                    const float *hh = c < nz ? L.bz + c * nxy : (pz ? L.bz : L.hz);
+                    const float *hl = c < nz ? D.bzl + c * nxy : (pz ? D.bzl : D.hzl);
+                    cp_async16(&S.bzh[d], hh + o, 16);
+                    cp_async16(&S.bzl[d], hl + o, 16);
+                }
+            } else if (t == 4) {
+                if (k >= 0 && k <= nk - 1 && kd) {
+                    cp_async16(&S.fh[d], D.fh + c * nxy + o, 16);
+                    cp_async16(&S.fl[d], D.fl + c * nxy + o, 16);
+                }
+            }
+        }
+        cp_async_commit();
+    };
     auto issue = [&](int k) {
+        if (WIDE) {
+            issue_wide(k);
+            return;
+        }
         DmStage &S = sm.st[(k + 2) % DM_NS];
         if (k <= nk - 1) {
             const int p = df_map(c0 + k + 1, nz, pz);
@@ -702,17 +806,18 @@ __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArr
         l = S.pl[q];
         if (UPDATE) df_axpy(h, l, sch, scl, S.pe[q]);
     };
-    auto convert = [&](const DmStage &S, int b) {  // this thread's slots of the stage's plane into buffer b
+    auto convert = [&](const DmStage &S, int b) {  // this thread's window slots of the stage's plane into buffer b
         for (int s = 0; s < 2; s++) {
             if (s == 1 && !slot1) break;
-            const int q = tid + s * DM_T;
+            const int q = tid + s * DM_T;                           // the 34 x 10 window around the tile
+            const int w = (q / DM_HX) * PX + (q % DM_HX) + XO - 1;  // its place in the staged plane
             float h, l;
-            newval(S, q, h, l);
-            sm.ch[b][q] = h;
-            sm.cl[b][q] = l;
+            newval(S, w, h, l);
+            sm.ch[b][w] = h;
+            sm.cl[b][w] = l;
         }
     };
-    const int qo = (ty + 1) * DM_HX + tx + 1;  // own column in the halo plane
+    const int qo = (ty + 1) * PX + tx + XO;  // own column in the halo plane
     float pmh, pml, p0h, p0l;
     issue(-2);
     issue(-1);
@@ -746,12 +851,12 @@ __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArr
         if (k + 1 < nk) convert(S, (k + 1) & 1);
         if (own) {
             const float *h = sm.ch[k & 1], *l = sm.cl[k & 1];
-            const int bxq = ty * DM_BXX + tx, byq = ty * DM_X + tx;
+            const int bxq = ty * BXP + tx, byq = ty * DM_X + tx;
             float Sh = 0.f, Se = 0.f;
             df_term(S.bxh[bxq], S.bxl[bxq], h[qo - 1], l[qo - 1], p0h, p0l, Sh, Se);
             df_term(S.bxh[bxq + 1], S.bxl[bxq + 1], h[qo + 1], l[qo + 1], p0h, p0l, Sh, Se);
-            df_term(S.byh[byq], S.byl[byq], h[qo - DM_HX], l[qo - DM_HX], p0h, p0l, Sh, Se);
-            df_term(S.byh[byq + DM_X], S.byl[byq + DM_X], h[qo + DM_HX], l[qo + DM_HX], p0h, p0l, Sh, Se);
+            df_term(S.byh[byq], S.byl[byq], h[qo - PX], l[qo - PX], p0h, p0l, Sh, Se);
+            df_term(S.byh[byq + DM_X], S.byl[byq + DM_X], h[qo + PX], l[qo + PX], p0h, p0l, Sh, Se);
             df_term(S.bzh[tid], S.bzl[tid], pmh, pml, p0h, p0l, Sh, Se);
             df_term(S1.bzh[tid], S1.bzl[tid], puh, pul, p0h, p0l, Sh, Se);
             float Rh, Re;
@@ -779,18 +884,19 @@ __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArr
     }
 }
 
-template <bool UPDATE>
+template <bool UPDATE, bool WIDE>
 __global__ void __launch_bounds__(DM_T, 2)
     df_march_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
                     const SolveState *st, float ih2, double *part, int nzc) {
     pdl_trigger();
     pdl_wait();
-    df_march_body<UPDATE>(L, D, e, e_odd, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z, nzc);
+    df_march_body<UPDATE, WIDE>(L, D, e, e_odd, st, ih2, part + 3 * flat_bid(), blockIdx.x, blockIdx.y, blockIdx.z,
+                                nzc);
 }
 
 // batched: work[blockIdx.x] = (box, bx, by, z-chunk) over each box's march grid;
 // the box's partials start at boxes[box].part_off (block bx + nbx (by + nby bz))
-template <bool UPDATE>
+template <bool UPDATE, bool WIDE>
 __global__ void __launch_bounds__(DM_T, 2)
     df_march_batch_kernel(const DFBox *boxes, const int4 *work, const SolveState *st, double *part) {
     const int4 w = work[blockIdx.x];
@@ -801,8 +907,8 @@ __global__ void __launch_bounds__(DM_T, 2)
     const DGeom &g = L.g;
     const int nbx = (g.n[0] + DM_X - 1) / DM_X, nby = (g.n[1] + DM_Y - 1) / DM_Y;
     double *p = part + 3 * ((long long)B.part_off + w.y + nbx * (w.z + nby * w.w));
-    df_march_body<UPDATE>(L, D, UPDATE ? L.e : nullptr, nullptr, &st[w.x], float(1.0 / (g.h * g.h)), p, w.y, w.z, w.w,
-                          B.zc);
+    df_march_body<UPDATE, WIDE>(L, D, UPDATE ? L.e : nullptr, nullptr, &st[w.x], float(1.0 / (g.h * g.h)), p, w.y, w.z,
+                                w.w, B.zc);
 }
 
 dim3 df_resid_grid(const DGeom &g) {
@@ -818,12 +924,16 @@ void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int 
     if (nwork <= 0) return;
     if (march) {
         const size_t smem = sizeof(DmShared);
-        if (update) {
-            cudaFuncSetAttribute(df_march_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            df_march_batch_kernel<true><<<nwork, DM_T, smem, s>>>(boxes, work, st, partials);
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<nwork, DM_T, smem, s>>>(boxes, work, st, partials);
+        };
+        if (march == 2) {
+            if (update) go(df_march_batch_kernel<true, true>);
+            else go(df_march_batch_kernel<false, true>);
         } else {
-            cudaFuncSetAttribute(df_march_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            df_march_batch_kernel<false><<<nwork, DM_T, smem, s>>>(boxes, work, st, partials);
+            if (update) go(df_march_batch_kernel<true, false>);
+            else go(df_march_batch_kernel<false, false>);
         }
         return;
     }
@@ -841,7 +951,7 @@ dim3 df_resid_batch_grid(const DGeom &g, int march, int *zc) {
     *zc = 0;
     return df_resid_grid(g);
 }
-bool df_march_usable(const DGeom &g) { return df_march_ok(g); }
+int df_march_usable(const DGeom &g) { return df_march_ok(g) ? (df_march_wide(g) ? 2 : 1) : 0; }
 
 int k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const float *e, const SolveState *st,
                double *partials, const float *e_odd) {
@@ -851,13 +961,17 @@ int k_df_resid(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const 
         const dim3 grid = df_march_grid(g);
         const int zc = df_march_zchunk(g);
         const size_t smem = sizeof(DmShared);
+        auto go = [&](auto kern, const float *ea, const float *eb) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            launch_pdl(kern, grid, dim3(DM_T), smem, s, L0, D, ea, eb, st, ih2, partials, zc);
+        };
+        const bool wide = df_march_wide(g);
         if (e) {
-            cudaFuncSetAttribute(df_march_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            launch_pdl(df_march_kernel<true>, grid, dim3(DM_T), smem, s, L0, D, e, e_odd, st, ih2, partials, zc);
+            if (wide) go(df_march_kernel<true, true>, e, e_odd);
+            else go(df_march_kernel<true, false>, e, e_odd);
         } else {
-            cudaFuncSetAttribute(df_march_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            launch_pdl(df_march_kernel<false>, grid, dim3(DM_T), smem, s, L0, D, (const float *)nullptr,
-                       (const float *)nullptr, st, ih2, partials, zc);
+            if (wide) go(df_march_kernel<false, true>, (const float *)nullptr, (const float *)nullptr);
+            else go(df_march_kernel<false, false>, (const float *)nullptr, (const float *)nullptr);
         }
         return int(grid.x * grid.y * grid.z);
     }

@@ -51,11 +51,12 @@ struct DFBox {
     int zc;           // z-chunk of the box's march grid (march work lists)
 };
 // the batched residual over a work list of df_resid_batch_grid entries: the
-// z-march (march = 1, every box df_march_usable) or the 3D-tile kernel
+// z-march (march = 1: element staging, 2: 16-byte row chunks; the smallest
+// df_march_usable over the boxes) or the 3D-tile kernel (march = 0)
 void k_df_resid_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const SolveState *st,
                       double *partials, int update, int march);
 dim3 df_resid_batch_grid(const DGeom &g, int march, int *zc);
-bool df_march_usable(const DGeom &g);
+int df_march_usable(const DGeom &g);
 // phi (double) from the current double-float buffer; partials (may be null):
 // per-block (0, sum phi, 0) on red_blocks(n) blocks
 void k_df_final(cudaStream_t s, long long n, const DFArrays &D, const SolveState *st, double *x,
