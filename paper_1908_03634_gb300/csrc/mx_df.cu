@@ -885,7 +885,7 @@ __device__ __forceinline__ void df_march_body(const Level<float> &L, const DFArr
 }
 
 template <bool UPDATE, bool WIDE>
-__global__ void __launch_bounds__(DM_T, 2)
+__global__ void __launch_bounds__(DM_T, 3)
     df_march_kernel(Level<float> L, DFArrays D, const float *__restrict__ e, const float *__restrict__ e_odd,
                     const SolveState *st, float ih2, double *part, int nzc) {
     pdl_trigger();
@@ -897,7 +897,7 @@ __global__ void __launch_bounds__(DM_T, 2)
 // batched: work[blockIdx.x] = (box, bx, by, z-chunk) over each box's march grid;
 // the box's partials start at boxes[box].part_off (block bx + nbx (by + nby bz))
 template <bool UPDATE, bool WIDE>
-__global__ void __launch_bounds__(DM_T, 2)
+__global__ void __launch_bounds__(DM_T, 3)
     df_march_batch_kernel(const DFBox *boxes, const int4 *work, const SolveState *st, double *part) {
     const int4 w = work[blockIdx.x];
     if (st[w.x].done) return;
