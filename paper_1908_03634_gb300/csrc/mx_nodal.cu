@@ -366,10 +366,15 @@ __global__ void __launch_bounds__(256) nd_restrict_march_kernel(NLevel<T> F, NLe
             for (int x = 0; x < 3; x++)
                 p[y][x] = (cz >= 0 && fa[x] >= 0 && fb[y] >= 0) ? F.r[nidx(g, fa[x], fb[y], cz)] : T(0);
     };
+    T n1[3][3], n2[3][3];  // the next coarse plane's fine planes, loaded a plane ahead
     load(2 * C0 - 1, v[0]);
+    load(2 * C0, v[1]);
+    load(2 * C0 + 1, v[2]);
     for (int Cz = C0; Cz < C1; Cz++) {
-        load(2 * Cz, v[1]);
-        load(2 * Cz + 1, v[2]);
+        if (Cz + 1 < C1) {
+            load(2 * Cz + 2, n1);
+            load(2 * Cz + 3, n2);
+        }
         T acc = T(0);
         for (int oz = 0; oz < 3; oz++) {
             const int cz = node_wrap(g, 2, 2 * Cz + oz - 1);
@@ -389,7 +394,11 @@ __global__ void __launch_bounds__(256) nd_restrict_march_kernel(NLevel<T> F, NLe
         C.f[Q] = acc / (T(8) * T(wC));
         C.e[Q] = T(0);
         for (int y = 0; y < 3; y++)
-            for (int x = 0; x < 3; x++) v[0][y][x] = v[2][y][x];
+            for (int x = 0; x < 3; x++) {
+                v[0][y][x] = v[2][y][x];
+                v[1][y][x] = n1[y][x];
+                v[2][y][x] = n2[y][x];
+            }
     }
 }
 
@@ -434,36 +443,47 @@ __global__ void __launch_bounds__(256) nd_prolong_march_kernel(NLevel<T> C, NLev
         for (int v = 0; v < nb; v++)
             for (int t = 0; t < na; t++) s += wa[t] * wb[v] * wc * p[v][t];
     };
-    T lo[2][2], hi[2][2];
-    int Clo = c0 / 2;  // the coarse plane at or below the first fine plane
-    load(Clo, lo);
-    int Chi = -1;      // coarse plane held in hi (-1: none)
-    for (int c = c0; c < c1; c++) {
-        const long long q = nidx(g, a, b, c);
-        T s = T(0);
-        if ((c & 1) == 0) {
-            if (c / 2 != Clo) {  // advance: the plane above becomes the plane below
-                if (Chi == c / 2) {
-                    for (int v = 0; v < 2; v++)
-                        for (int t = 0; t < 2; t++) lo[v][t] = hi[v][t];
-                } else {
-                    load(c / 2, lo);
-                }
-                Clo = c / 2;
+    // fine planes in pairs (2C, 2C + 1): 2C takes coarse plane C, 2C + 1 the planes C
+    // and C + 1 (wrapped); the next pair's fine values and coarse plane are loaded
+    // before this pair's stores
+    auto upper = [&](int c) {
+        int Cu = (c + 1) / 2;
+        if (gc.per[2] && Cu == gc.m[2]) Cu = 0;
+        return Cu;
+    };
+    T lo[2][2], hi[2][2], nhi[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    load(c0 / 2, lo);  // c0 is even
+    T ne0 = F.e[nidx(g, a, b, c0)], ne1 = T(0);
+    if (c0 + 1 < c1) {
+        ne1 = F.e[nidx(g, a, b, c0 + 1)];
+        load(upper(c0 + 1), nhi);
+    }
+    for (int c = c0; c < c1; c += 2) {
+        const T e0 = ne0, e1 = ne1;
+        for (int v = 0; v < 2; v++)
+            for (int t = 0; t < 2; t++) hi[v][t] = nhi[v][t];
+        if (c + 2 < c1) {
+            ne0 = F.e[nidx(g, a, b, c + 2)];
+            if (c + 3 < c1) {
+                ne1 = F.e[nidx(g, a, b, c + 3)];
+                load(upper(c + 3), nhi);
             }
-            terms(s, lo, T(1));
-        } else {
-            int Cu = (c + 1) / 2;
-            if (gc.per[2] && Cu == gc.m[2]) Cu = 0;
-            if (Chi != Cu) {
-                load(Cu, hi);
-                Chi = Cu;
-            }
-            terms(s, lo, T(0.5));
-            terms(s, hi, T(0.5));
         }
-        if (out) out[q] = F.e[q] + s;
-        else F.e[q] += s;
+        const long long q = nidx(g, a, b, c);
+        T s0 = T(0);
+        terms(s0, lo, T(1));
+        if (out) out[q] = e0 + s0;
+        else F.e[q] = e0 + s0;
+        if (c + 1 < c1) {
+            const long long q1 = q + (long long)g.m[0] * g.m[1];
+            T s1 = T(0);
+            terms(s1, lo, T(0.5));
+            terms(s1, hi, T(0.5));
+            if (out) out[q1] = e1 + s1;
+            else F.e[q1] = e1 + s1;
+        }
+        for (int v = 0; v < 2; v++)
+            for (int t = 0; t < 2; t++) lo[v][t] = hi[v][t];
     }
 }
 
