@@ -367,10 +367,25 @@ __device__ __forceinline__ void prolong_body(const Level<T> &Cl, const Level<T> 
     const int k0 = bz * zc;
     if (i >= g.n[0] || j >= g.n[1]) return;
     const int k1 = min(k0 + zc, g.n[2]);
-    for (int k = k0; k < k1; k++) {
-        const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
-        const long long C = (i >> 1) + (long long)Cl.g.n[0] * ((j >> 1) + (long long)Cl.g.n[1] * (k >> 1));
-        F.e[c] += Cl.e[C];
+    // four planes at a time: their loads are issued before any store (one plane
+    // per iteration would make a chain of dependent round trips)
+    for (int kb = k0; kb < k1; kb += 4) {
+        T fe[4], ce[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int k = kb + q;
+            if (k < k1) {
+                const long long c = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
+                const long long C = (i >> 1) + (long long)Cl.g.n[0] * ((j >> 1) + (long long)Cl.g.n[1] * (k >> 1));
+                fe[q] = F.e[c];
+                ce[q] = Cl.e[C];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int k = kb + q;
+            if (k < k1) F.e[i + (long long)g.n[0] * (j + (long long)g.n[1] * k)] = fe[q] + ce[q];
+        }
     }
 }
 
