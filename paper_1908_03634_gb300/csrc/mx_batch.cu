@@ -38,6 +38,7 @@ struct BatchPlan {
     int *d_off = nullptr, *d_cnt = nullptr;
     int4 *d_work = nullptr;
     std::vector<WorkRange> rb, rr, pr;  // per level index
+    std::vector<int> rr_zcf;            // per level index: fine planes per restriction tile (0: coarse tiles)
     WorkRange df;
     int nparts = 0;
     size_t coarse_smem = 0;
@@ -111,14 +112,41 @@ static BatchPlan *build_batch(mx_ctx *c, int nbox, const DGeom *g, const mx_opts
     B->rb.resize(B->maxdown);
     B->rr.resize(B->maxdown);
     B->pr.resize(B->maxdown);
+    B->rr_zcf.assign(B->maxdown, 0);
     for (int l = 0; l < B->maxdown; l++) {
         B->rb[l].off = int(work.size());
         for (int b = 0; b < nbox; b++)
             if (l < B->lc[b]) add_grid(work, b, rbgs_grid(B->box[b]->H32.lev[l].g, ZC));
         B->rb[l].n = int(work.size()) - B->rb[l].off;
+        // residual + restriction: the fine-cell form when every box's level has even
+        // extents, its fine planes per tile halved while the tiles fill the GPU less than
+        // four times at four blocks per SM (as for a single box)
+        bool even = true;
+        for (int b = 0; b < nbox; b++)
+            if (l < B->lc[b]) {
+                const DGeom &gf = B->box[b]->H32.lev[l].g;
+                even = even && gf.n[0] % 2 == 0 && gf.n[1] % 2 == 0 && gf.n[2] % 2 == 0;
+            }
+        int zcf = 0;
+        if (even) {
+            auto tiles = [&](int z) {
+                long long t = 0;
+                for (int b = 0; b < nbox; b++)
+                    if (l < B->lc[b]) {
+                        const dim3 gr = resid_restrict_fine_grid(B->box[b]->H32.lev[l].g, z);
+                        t += (long long)gr.x * gr.y * gr.z;
+                    }
+                return t;
+            };
+            zcf = 16;
+            while (zcf > 2 && tiles(zcf) < 4 * 4 * 152) zcf >>= 1;
+        }
+        B->rr_zcf[l] = zcf;
         B->rr[l].off = int(work.size());
         for (int b = 0; b < nbox; b++)
-            if (l < B->lc[b]) add_grid(work, b, stencil_grid(B->box[b]->H32.lev[l + 1].g));
+            if (l < B->lc[b])
+                add_grid(work, b, zcf ? resid_restrict_fine_grid(B->box[b]->H32.lev[l].g, zcf)
+                                      : stencil_grid(B->box[b]->H32.lev[l + 1].g));
         B->rr[l].n = int(work.size()) - B->rr[l].off;
         B->pr[l].off = int(work.size());
         for (int b = 0; b < nbox; b++)
@@ -223,7 +251,7 @@ static void batch_body(cudaStream_t s, mx_ctx *c, BatchPlan &B, const mx_opts &o
             k_rbgs_batch(s, B.d_levs, B.d_work + B.rb[l].off, B.rb[l].n, B.d_st, l, 0, q == 0);
             k_rbgs_batch(s, B.d_levs, B.d_work + B.rb[l].off, B.rb[l].n, B.d_st, l, 1, 0);
         }
-        k_resid_restrict_batch(s, B.d_levs, B.d_work + B.rr[l].off, B.rr[l].n, B.d_st, l);
+        k_resid_restrict_batch(s, B.d_levs, B.d_work + B.rr[l].off, B.rr[l].n, B.d_st, l, B.rr_zcf[l]);
     }
     k_coarse_vcycle_batch(s, B.d_cargs, B.d_st, B.nbox, B.coarse_smem);
     for (int l = B.maxdown - 1; l >= 0; l--) {

@@ -234,8 +234,11 @@ dim3 rbgs_grid(const DGeom &g, int zc);
 // batched multigrid phases over a work list of (box, bx, by, bz)
 void k_rbgs_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
                   int level, int colour, int zero);
+// zcf > 0: the fine-cell form, work entries are tiles of resid_restrict_fine_grid(level's
+// geometry, zcf) (every box's level has even extents); 0: tiles of the coarse level
 void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork,
-                            const SolveState *st, int level);
+                            const SolveState *st, int level, int zcf);
+dim3 resid_restrict_fine_grid(const DGeom &fine, int zcf);
 void k_prolong_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork, const SolveState *st,
                      int level);
 void k_finalize_residual_batch(cudaStream_t s, const double *partials, const int *off, const int *cnt, SolveState *st,

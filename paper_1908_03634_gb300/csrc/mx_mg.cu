@@ -285,15 +285,14 @@ __device__ __forceinline__ void resid_restrict_body(const Level<T> &F, const Lev
 // threads as coarse cells: the load latency hides on the fine level, and the
 // small levels fill the GPU.
 template <typename T>
-__global__ void __launch_bounds__(SX *SY) resid_restrict_fine_kernel(Level<T> F, Level<T> Cl, T ih2, int zcf) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void resid_restrict_fine_body(const Level<T> &F, const Level<T> &Cl, T ih2, int bx, int by,
+                                                         int bz, int zcf) {
     __shared__ T sr[2][SY][SX];
     const DGeom &g = F.g, &gc = Cl.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = blockIdx.x * SX + tx, j = blockIdx.y * SY + ty;
+    const int i = bx * SX + tx, j = by * SY + ty;
     const bool act = i < g.n[0] && j < g.n[1];
-    const int k0 = blockIdx.z * zcf, k1 = min(k0 + zcf, g.n[2]);  // k0 and zcf even
+    const int k0 = bz * zcf, k1 = min(k0 + zcf, g.n[2]);  // k0 and zcf even
     for (int k = k0; k < k1; k++) {
         T r = T(0);
         if (act) {
@@ -320,6 +319,13 @@ __global__ void __launch_bounds__(SX *SY) resid_restrict_fine_kernel(Level<T> F,
 }
 
 template <typename T>
+__global__ void __launch_bounds__(SX *SY) resid_restrict_fine_kernel(Level<T> F, Level<T> Cl, T ih2, int zcf) {
+    pdl_trigger();
+    pdl_wait();
+    resid_restrict_fine_body(F, Cl, ih2, blockIdx.x, blockIdx.y, blockIdx.z, zcf);
+}
+
+template <typename T>
 __global__ void resid_restrict_kernel(Level<T> F, Level<T> Cl, T ih2, int zc) {
     pdl_trigger();
     pdl_wait();
@@ -335,9 +341,27 @@ __global__ void resid_restrict_batch_kernel(const Level<float> *levs, const int4
     resid_restrict_body(F, C, float(1.0 / (F.g.h * F.g.h)), w.y, w.z, w.w, threadIdx.x, threadIdx.y, ZC);
 }
 
+// the fine-cell form over a work list of fine tiles (every box's level has even extents)
+__global__ void __launch_bounds__(SX *SY) resid_restrict_fine_batch_kernel(const Level<float> *levs, const int4 *work,
+                                                                          const SolveState *st, int level, int zcf) {
+    const int4 w = work[blockIdx.x];
+    if (st[w.x].done) return;
+    const Level<float> F = levs[w.x * MX_MAXLEV + level];
+    const Level<float> C = levs[w.x * MX_MAXLEV + level + 1];
+    resid_restrict_fine_body(F, C, float(1.0 / (F.g.h * F.g.h)), w.y, w.z, w.w, zcf);
+}
+
+dim3 resid_restrict_fine_grid(const DGeom &fine, int zcf) {
+    return dim3((fine.n[0] + SX - 1) / SX, (fine.n[1] + SY - 1) / SY, (fine.n[2] + zcf - 1) / zcf);
+}
+
 void k_resid_restrict_batch(cudaStream_t s, const Level<float> *levs, const int4 *work, int nwork,
-                            const SolveState *st, int level) {
-    if (nwork > 0) resid_restrict_batch_kernel<<<nwork, dim3(SX, SY), 0, s>>>(levs, work, st, level);
+                            const SolveState *st, int level, int zcf) {
+    if (nwork <= 0) return;
+    if (zcf > 0)
+        resid_restrict_fine_batch_kernel<<<nwork, dim3(SX, SY), 0, s>>>(levs, work, st, level, zcf);
+    else
+        resid_restrict_batch_kernel<<<nwork, dim3(SX, SY), 0, s>>>(levs, work, st, level);
 }
 
 template <typename T>
