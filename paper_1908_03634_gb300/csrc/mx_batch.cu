@@ -388,7 +388,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
         const int nb = stencil_blocks(gb), nbr = red_blocks(gb.N);
         const int singular = geom_singular(gb);
         setup_coefficients_on(ss, P, rho[b], beta0[b]);
-        k_mac_rhs_df(ss, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], P.D, part);
+        k_mac_rhs_df(ss, gb, ux[b], uy[b], uz[b], sbar[b], P.D, part);
         k_finalize_rhs(ss, part, nb, sb, gb.N, singular && o.remove_mean, 0);
         if (singular && !o.remove_mean) {
             MX_CUDA(c, cudaMemcpyAsync(B.h_st + b, sb, sizeof(SolveState), cudaMemcpyDeviceToHost, ss));
@@ -445,7 +445,7 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
             k_sub_scalar(ss, gb.N, phi[b], &sb->aux);
         }
         k_mac_correct(ss, gb, P.Q, phi[b], ux[b], uy[b], uz[b]);
-        k_mac_divcheck_df(ss, gb, ux[b], uy[b], uz[b], beta0[b], sbar[b], sb, part);
+        k_mac_divcheck_df(ss, gb, ux[b], uy[b], uz[b], sbar[b], P.D, sb, part);
         k_finalize_max(ss, part, nb, &sb->div_err);
     }
     if ((st = join())) return st;

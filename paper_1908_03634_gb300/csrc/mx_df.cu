@@ -114,6 +114,8 @@ __global__ void mac_coeffs_df_kernel(Level<float> L, DFArrays D, FaceQ Q, const 
                 own(g.lo[0], rc, bc, b, q);
             }
             store(L.bx, D.bxl, Q.x, c, b, q);
+            D.b0h[c] = bc.h;
+            D.b0l[c] = bc.l;
             if (j > 0 || gper(g, 1)) {
                 dfloat rs, bs;
                 if (ty > 0) {
@@ -164,7 +166,8 @@ void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, 
 }
 
 // ---- RHS f = D(beta0 U) - beta0 Sbar in double-float ----------------------------
-// The FP64 inputs are split into double-float (integer bit operations), the
+// The FP64 inputs U and Sbar are split into double-float (integer bit
+// operations), beta0 comes split from the coefficient pass (b0h, b0l), the
 // divergence is evaluated with double-float arithmetic on the FP32 pipe, and f
 // is stored as a double-float pair (fh, fl); no FP64 arithmetic per cell.
 // Face flux times 2: (beta0_L + beta0_R) U_f inside and across periodic faces,
@@ -182,8 +185,9 @@ void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, 
 template <typename F>
 __device__ __forceinline__ void df_div_block(const DGeom &g, const double *__restrict__ ux,
                                              const double *__restrict__ uy, const double *__restrict__ uz,
-                                             const double *__restrict__ beta0, const double *__restrict__ sbar,
-                                             int i, int j, int k0, int k1, dfloat hih, F fn) {
+                                             const float *__restrict__ b0h, const float *__restrict__ b0l,
+                                             const double *__restrict__ sbar, int i, int j, int k0, int k1,
+                                             dfloat hih, F fn) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long long nxy = g.nxy;
     static_assert(SX == 32, "one warp per row of the block");
@@ -191,6 +195,7 @@ __device__ __forceinline__ void df_div_block(const DGeom &g, const double *__res
     const bool act = i < nx && j < ny;
     const bool px = gper(g, 0), py = gper(g, 1), pz = gper(g, 2);
     const dfloat zero = {0.f, 0.f};
+    auto B = [&](long long q) { return dfloat{b0h[q], b0l[q]}; };
     // twice the flux at face p of axis d from the split beta0 of its low (bl)
     // and high (bh) cells: the face mean inside and across periodic faces, the
     // interior cell's value on a Dirichlet face, 0 on a wall
@@ -206,8 +211,8 @@ __device__ __forceinline__ void df_div_block(const DGeom &g, const double *__res
     long long c = act ? i + (long long)nx * (j + (long long)ny * k0) : 0;
     dfloat bo = zero, fzl = zero;
     if (act) {
-        bo = df_split(beta0[c]);
-        const dfloat bd = k0 > 0 ? df_split(beta0[c - nxy]) : (pz ? df_split(beta0[c + (long long)(nz - 1) * nxy]) : zero);
+        bo = B(c);
+        const dfloat bd = k0 > 0 ? B(c - nxy) : (pz ? B(c + (long long)(nz - 1) * nxy) : zero);
         fzl = flux2(2, k0, bd, bo, uz[c]);
     }
     for (int k = k0; k < k1; k++, c += nxy) {
@@ -217,7 +222,7 @@ __device__ __forceinline__ void df_div_block(const DGeom &g, const double *__res
         const long long fx = i + (long long)(nx + 1) * (j + (long long)ny * k);
         dfloat fxl = zero;
         if (act) {
-            if (lane == 0) bw = i > 0 ? df_split(beta0[c - 1]) : (px ? df_split(beta0[c + nx - 1]) : zero);
+            if (lane == 0) bw = i > 0 ? B(c - 1) : (px ? B(c + nx - 1) : zero);
             fxl = flux2(0, i, bw, bo, ux[fx]);
         }
         dfloat fxh;
@@ -225,17 +230,17 @@ __device__ __forceinline__ void df_div_block(const DGeom &g, const double *__res
         fxh.l = __shfl_down_sync(0xffffffffu, fxl.l, 1);
         if (act) {
             if (lane == SX - 1 || i + 1 >= nx) {
-                const dfloat be = i + 1 < nx ? df_split(beta0[c + 1]) : (px ? df_split(beta0[c - (nx - 1)]) : zero);
+                const dfloat be = i + 1 < nx ? B(c + 1) : (px ? B(c - (nx - 1)) : zero);
                 fxh = flux2(0, i + 1, bo, be, ux[fx + 1]);
             }
             const long long fy = i + (long long)nx * (j + (long long)(ny + 1) * k);
-            const dfloat bs = j > 0 ? df_split(beta0[c - nx]) : (py ? df_split(beta0[c + (long long)(ny - 1) * nx]) : zero);
-            const dfloat bn = j + 1 < ny ? df_split(beta0[c + nx])
-                                         : (py ? df_split(beta0[c - (long long)(ny - 1) * nx]) : zero);
+            const dfloat bs = j > 0 ? B(c - nx) : (py ? B(c + (long long)(ny - 1) * nx) : zero);
+            const dfloat bn = j + 1 < ny ? B(c + nx)
+                                         : (py ? B(c - (long long)(ny - 1) * nx) : zero);
             const dfloat fyl = flux2(1, j, bs, bo, uy[fy]);
             const dfloat fyh = flux2(1, j + 1, bo, bn, uy[fy + nx]);
-            const dfloat bu = k + 1 < nz ? df_split(beta0[c + nxy])
-                                         : (pz ? df_split(beta0[c - (long long)(nz - 1) * nxy]) : zero);
+            const dfloat bu = k + 1 < nz ? B(c + nxy)
+                                         : (pz ? B(c - (long long)(nz - 1) * nxy) : zero);
             const dfloat fzh = flux2(2, k + 1, bo, bu, uz[c + nxy]);
             const dfloat div = df_add(df_add(df_sub(fxh, fxl), df_sub(fyh, fyl)), df_sub(fzh, fzl));
             fn(c, df_sub(df_mul(div, hih), df_mul(bo, df_split(sbar[c]))));
@@ -257,15 +262,15 @@ __device__ __forceinline__ void df_partials(dfloat mx, float s2, dfloat s1, doub
     }
 }
 
-__global__ void mac_rhs_df_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
-                                  const double *__restrict__ uz, const double *__restrict__ beta0,
-                                  const double *__restrict__ sbar, float *__restrict__ fh, float *__restrict__ fl,
-                                  double *part, dfloat hih) {
+__global__ void __launch_bounds__(SX *SY, 5) mac_rhs_df_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                                  const double *__restrict__ uz, const float *__restrict__ b0h,
+                                  const float *__restrict__ b0l, const double *__restrict__ sbar,
+                                  float *__restrict__ fh, float *__restrict__ fl, double *part, dfloat hih) {
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     dfloat mx = {0.f, 0.f}, s1 = {0.f, 0.f};
     float s2 = 0.f;
-    df_div_block(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, dfloat v) {
+    df_div_block(g, ux, uy, uz, b0h, b0l, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih, [&](long long c, dfloat v) {
             fh[c] = v.h;
             fl[c] = v.l;
             df_absmax(mx, v);
@@ -276,15 +281,15 @@ __global__ void mac_rhs_df_kernel(DGeom g, const double *__restrict__ ux, const 
 }
 
 // max |D(beta0 U) - beta0 Sbar - c| of the projected velocity
-__global__ void mac_divcheck_df_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
-                                       const double *__restrict__ uz, const double *__restrict__ beta0,
-                                       const double *__restrict__ sbar, const SolveState *st, double *part,
-                                       dfloat hih) {
+__global__ void __launch_bounds__(SX *SY, 5) mac_divcheck_df_kernel(DGeom g, const double *__restrict__ ux, const double *__restrict__ uy,
+                                       const double *__restrict__ uz, const float *__restrict__ b0h,
+                                       const float *__restrict__ b0l, const double *__restrict__ sbar,
+                                       const SolveState *st, double *part, dfloat hih) {
     const int i = blockIdx.x * SX + threadIdx.x, j = blockIdx.y * SY + threadIdx.y;
     const int k0 = blockIdx.z * ZC;
     const dfloat cm = df_split(st->mean);
     dfloat mx = {0.f, 0.f};
-    df_div_block(g, ux, uy, uz, beta0, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
+    df_div_block(g, ux, uy, uz, b0h, b0l, sbar, i, j, k0, min(k0 + ZC, g.n[2]), hih,
                  [&](long long, dfloat v) { df_absmax(mx, df_sub(v, cm)); });
     df_partials(mx, 0.f, dfloat{0.f, 0.f}, part + 3 * flat_bid());
 }
@@ -297,14 +302,14 @@ static dfloat df_const(double v) {
 }
 
 void k_mac_rhs_df(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
-                  const double *beta0, const double *sbar, const DFArrays &D, double *partials) {
-    mac_rhs_df_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, D.fh, D.fl, partials,
-                                                               df_const(0.5 / g.h));
+                  const double *sbar, const DFArrays &D, double *partials) {
+    mac_rhs_df_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, D.b0h, D.b0l, sbar, D.fh, D.fl,
+                                                               partials, df_const(0.5 / g.h));
 }
 
 void k_mac_divcheck_df(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
-                       const double *beta0, const double *sbar, const SolveState *st, double *partials) {
-    mac_divcheck_df_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, beta0, sbar, st, partials,
+                       const double *sbar, const DFArrays &D, const SolveState *st, double *partials) {
+    mac_divcheck_df_kernel<<<stencil_grid(g), dim3(SX, SY), 0, s>>>(g, ux, uy, uz, D.b0h, D.b0l, sbar, st, partials,
                                                                     df_const(0.5 / g.h));
 }
 

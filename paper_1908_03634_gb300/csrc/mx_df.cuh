@@ -12,20 +12,22 @@ struct DFArrays {
     float *fh, *fl;          // h^2 f
     float *ph, *pl;          // phi, buffer 0
     float *ph2, *pl2;        // phi, buffer 1 (the buffers alternate with the V-cycle count)
+    float *b0h, *b0l;        // beta0 at the cell centres, split once by the coefficient pass
 };
 
 void k_mac_coeffs_df(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const double *rho, const double *beta0,
                      const FaceQ *q = nullptr);
 // f = D(beta0 U) - beta0 Sbar in double-float into (D.fh, D.fl), with per-block
 // partials (max |f|, sum f^2, sum f) on the stencil grid
+// (beta0 comes split from (D.b0h, D.b0l): k_mac_coeffs_df of the same plan must run first)
 void k_mac_rhs_df(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
-                  const double *beta0, const double *sbar, const DFArrays &D, double *partials);
+                  const double *sbar, const DFArrays &D, double *partials);
 // (D.fh, D.fl) <- h^2 (f - mean), partials of f - mean on nb grid-stride blocks
 void k_sub_mean_scale(cudaStream_t s, const DGeom &g, const SolveState *st, const DFArrays &D, double *partials,
                       int nb);
 // partials (max |D(beta0 U) - beta0 Sbar - mean|, 0, 0) on the stencil grid
 void k_mac_divcheck_df(cudaStream_t s, const DGeom &g, const double *ux, const double *uy, const double *uz,
-                       const double *beta0, const double *sbar, const SolveState *st, double *partials);
+                       const double *sbar, const DFArrays &D, const SolveState *st, double *partials);
 void k_df_from_double(cudaStream_t s, long long n, const double *x, const DFArrays &D);
 void k_df_to_double(cudaStream_t s, long long n, const DFArrays &D, double *x);
 void k_df_update(cudaStream_t s, const DGeom &g, const DFArrays &D, const float *e, const SolveState *st);

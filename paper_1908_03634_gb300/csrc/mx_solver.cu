@@ -73,6 +73,8 @@ static void carve_plan(Bump &b, MacPlan &P) {
         D.pl = b.take<float>(g.N);
         D.ph2 = b.take<float>(g.N);
         D.pl2 = b.take<float>(g.N);
+        D.b0h = b.take<float>(g.N);
+        D.b0l = b.take<float>(g.N);
         P.tmp32 = b.take<float>(g.N);
         P.H64.nlev = 0;
         P.L64 = Level<double>{};
@@ -520,7 +522,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
     // right-hand side f = D(beta0 U) - beta0 Sbar, mean removal, norms
     // (mixed: double-float f into the plan's (fh, fl); FP64: f into L64.f)
     double *f64 = P->L64.f;
-    if (o.prec == MX_PREC_MIXED) k_mac_rhs_df(s, g, ux, uy, uz, beta0, sbar, P->D, c->partials);
+    if (o.prec == MX_PREC_MIXED) k_mac_rhs_df(s, g, ux, uy, uz, sbar, P->D, c->partials);
     else k_mac_rhs(s, g, ux, uy, uz, beta0, sbar, f64, c->partials, nb);
     k_finalize_rhs(s, c->partials, nb, c->state, g.N, singular && o.remove_mean, 0);
     if (singular && !o.remove_mean) {
@@ -561,7 +563,7 @@ extern "C" mx_status mx_mac_project(mx_ctx *c, const mx_geom *geom, double *ux, 
         k_sub_scalar(s, g.N, phi, &c->state->aux);
     }
     k_mac_correct(s, g, P->Q, phi, ux, uy, uz);
-    if (o.prec == MX_PREC_MIXED) k_mac_divcheck_df(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials);
+    if (o.prec == MX_PREC_MIXED) k_mac_divcheck_df(s, g, ux, uy, uz, sbar, P->D, c->state, c->partials);
     else k_mac_divcheck(s, g, ux, uy, uz, beta0, sbar, c->state, c->partials, nb);
     k_finalize_max(s, c->partials, nb, &c->state->div_err);
     prof_end(c, s, MX_PH_FINISH, (singular ? 3 : 0) + (o.prec == MX_PREC_MIXED ? 5 : 4));
