@@ -400,16 +400,12 @@ extern "C" mx_status mx_mac_project_batched(mx_ctx *c, int nbox, const mx_geom *
         }
         k_sub_mean_scale(ss, gb, sb, P.D, part, nbr);
         k_finalize_rhs(ss, part, nbr, sb, gb.N, 0, 1);
-        if (o.use_initial_guess) {
-            k_df_from_double(ss, gb.N, phi[b], P.D);
-        } else {
-            MX_CUDA(c, cudaMemsetAsync(P.D.ph, 0, sizeof(float) * gb.N, ss));
-            MX_CUDA(c, cudaMemsetAsync(P.D.pl, 0, sizeof(float) * gb.N, ss));
-        }
+        if (o.use_initial_guess) k_df_from_double(ss, gb.N, phi[b], P.D);  // else zeroed by the first residual
     }
     if ((st = join())) return st;
-    // refinement loop over all boxes
-    k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 0, B.march);
+    // refinement loop over all boxes (from phi = 0 the first residual is f, formed elementwise)
+    if (o.use_initial_guess) k_df_resid_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_st, c->partials, 0, B.march);
+    else k_df_resid_zero_batch(s, B.d_df, B.d_work + B.df.off, B.df.n, B.d_cnt, B.d_st, c->partials);
     k_finalize_residual_batch(s, c->partials, B.d_off, B.d_cnt, B.d_st, nbox);
     MX_CUDA(c, cudaMemcpyAsync(B.h_st, B.d_st, sizeof(SolveState) * nbox, cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));

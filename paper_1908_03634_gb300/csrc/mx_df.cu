@@ -1021,6 +1021,55 @@ __global__ void df_resid_zero_kernel(long long n, const float *__restrict__ fh, 
     }
 }
 
+// The same over the batched residual's work list: the entries of box b are the
+// contiguous run starting at its part_off, so entry r of the run covers cells
+// r * 256 + t, r * 256 + t + cnt[b] * 256, ... and writes partial part_off + r,
+// the slot the stencil kernel's block of that entry writes.  It also sets the
+// box's phi buffer 0 (the one the first update reads) to zero.
+__global__ void __launch_bounds__(256) df_resid_zero_batch_kernel(const DFBox *boxes, const int4 *work,
+                                                                  const int *cnt, const SolveState *st,
+                                                                  double *part) {
+    const int4 w = work[blockIdx.x];
+    const DFBox &B = boxes[w.x];
+    const DGeom &g = B.L0.g;
+    const long long r = (long long)blockIdx.x - B.part_off, step = (long long)cnt[w.x] * 256;
+    float *__restrict__ ph = B.D.ph, *__restrict__ pl = B.D.pl;
+    if (st[w.x].done) {  // converged at the start (f = 0): phi = 0 only
+        for (long long q = r * 256 + threadIdx.x; q < g.N; q += step) {
+            ph[q] = 0.f;
+            pl[q] = 0.f;
+        }
+        return;
+    }
+    const float *__restrict__ fh = B.D.fh, *__restrict__ fl = B.D.fl;
+    float *__restrict__ rhat = B.L0.f;
+    const float c_hat = float(1.0 / (g.h * g.h)) * st[w.x].inv_scale_f;
+    float mx = 0.f, s2f = 0.f, s1f = 0.f;
+    for (long long q = r * 256 + threadIdx.x; q < g.N; q += step) {
+        float Rh, Re;
+        two_sum(fh[q], -0.f, Rh, Re);
+        Re += fl[q] - 0.f;
+        const float rh = (Rh + Re) * c_hat;
+        rhat[q] = rh;
+        ph[q] = 0.f;
+        pl[q] = 0.f;
+        mx = nmaxf(mx, fabsf(rh));
+        s2f = fmaf(rh, rh, s2f);
+        s1f += rh;
+    }
+    block_red3f(mx, s2f, s1f);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = double(mx);
+        part[3 * blockIdx.x + 1] = double(s2f);
+        part[3 * blockIdx.x + 2] = double(s1f);
+    }
+}
+
+void k_df_resid_zero_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const int *cnt,
+                           const SolveState *st, double *partials) {
+    if (nwork > 0) df_resid_zero_batch_kernel<<<nwork, 256, 0, s>>>(boxes, work, cnt, st, partials);
+}
+
 void k_df_resid_zero(cudaStream_t s, const Level<float> &L0, const DFArrays &D, const SolveState *st, double *partials) {
     const DGeom &g = L0.g;
     df_resid_zero_kernel<<<df_resid_blocks(g), DF_THREADS, 0, s>>>(g.N, D.fh, D.fl, L0.f, st, float(1.0 / (g.h * g.h)),

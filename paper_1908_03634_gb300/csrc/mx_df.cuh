@@ -52,6 +52,10 @@ struct DFBox {
     int part_off;     // first reduction partial of the box
     int zc;           // z-chunk of the box's march grid (march work lists)
 };
+// the first residual of every box from phi = 0 over the batched residual's work list
+// (cnt: entries per box), bit for bit the stencil kernels' rhat, norms in their slots
+void k_df_resid_zero_batch(cudaStream_t s, const DFBox *boxes, const int4 *work, int nwork, const int *cnt,
+                           const SolveState *st, double *partials);
 // the batched residual over a work list of df_resid_batch_grid entries: the
 // z-march (march = 1: element staging, 2: 16-byte row chunks; the smallest
 // df_march_usable over the boxes) or the 3D-tile kernel (march = 0)
