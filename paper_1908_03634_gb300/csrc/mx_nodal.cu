@@ -1095,6 +1095,46 @@ __global__ void nd_df_update_kernel(NDF D, long long M, const float *__restrict_
     }
 }
 
+// The first residual of a mixed solve from phi = 0: every coupling term of
+// the residual kernels is exactly +0 there, so the residual is f.  It is formed
+// node by node with their final expression and node weights (bit for bit
+// their rhat; the norms differ only in the grouping of the sums, and the
+// convergence decision reads the max), and phi's double-float buffer is
+// zeroed in the same pass.
+__global__ void nd_df_resid_zero_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part) {
+    const NGeom &g = L0.g;
+    const float inv = st->inv_scale_f;
+    const float ih2 = float(1.0 / (g.h * g.h));
+    const long long mxy = (long long)g.m[0] * g.m[1];
+    float mx = 0.f, s2 = 0.f, s1 = 0.f;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
+        const int c = int(q / mxy), r = int(q - c * mxy);
+        const int b = r / g.m[0], a = r - b * g.m[0];
+        const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
+                          ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f);
+        const bool wall = !g.per[2] && (c == 0 || c == g.m[2] - 1);
+        const float sc = wall ? ih2 / (12.f * (wxy * 0.5f)) : ih2 / (12.f * wxy);
+        float Rh, Re;
+        ts2(D.fh[q], -0.f, Rh, Re);
+        Re += D.fl[q] - 0.f;
+        const float R = Rh + Re;  // 12 w h^2 r
+        const float rh = R * sc * inv;
+        L0.f[q] = rh;
+        D.ph[q] = 0.f;
+        D.pl[q] = 0.f;
+        mx = nmaxf(mx, fabsf(rh));
+        s2 = fmaf(rh, rh, s2);
+        s1 += rh;
+    }
+    block_red3f(mx, s2, s1);
+    if (threadIdx.x == 0) {
+        double *p = part + 3 * blockIdx.x;
+        p[0] = double(mx);
+        p[1] = double(s2);
+        p[2] = double(s1);
+    }
+}
+
 // ---- column-marching residuals of the refinement loop -------------------------------
 
 // acc += coef * (q - p) in double-float, coef = (kh, kl), q = (qh, ql), p = (ch, cl)
@@ -2043,12 +2083,8 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         nd_rhs_final_kernel<<<nb, 256, 0, s>>>(g, P->f64, c->state, nullptr, nullptr, c->partials);
     nd_finalize_rhs_kernel<<<1, 1024, 0, s>>>(c->partials, nb, c->state, 0, 1);
     if (mixed) {
-        if (o.use_initial_guess) {
-            nd_split_kernel<<<nb, 256, 0, s>>>(phi, P->D.ph, P->D.pl, g.M);
-        } else {
-            MX_CUDA(c, cudaMemsetAsync(P->D.ph, 0, sizeof(float) * g.M, s));
-            MX_CUDA(c, cudaMemsetAsync(P->D.pl, 0, sizeof(float) * g.M, s));
-        }
+        if (o.use_initial_guess) nd_split_kernel<<<nb, 256, 0, s>>>(phi, P->D.ph, P->D.pl, g.M);
+        // else phi = 0 is set by the first residual's pass
     } else if (!o.use_initial_guess) {
         MX_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * g.M, s));
     }
@@ -2088,7 +2124,14 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         }
         residual(ss, pc);
     };
-    residual(s, c);
+    if (mixed && !o.use_initial_guess) {
+        prof_begin(c, s, MX_PH_RESID64);
+        nd_df_resid_zero_kernel<<<nb, 256, 0, s>>>(P->L32[0], P->D, (const SolveState *)c->state, c->partials);
+        k_finalize_residual(s, c->partials, nb, c->state, 1);
+        prof_end(c, s, MX_PH_RESID64, 2);
+    } else {
+        residual(s, c);
+    }
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));
     prof_flush(c);
