@@ -41,8 +41,12 @@ struct NLevel {
 struct NDF {             // double-float arrays of the finest level
     float *sh, *sl;      // sigma
     float *fh, *fl;      // 12 h^2 w f  (the scaled nodal RHS)
-    float *ph, *pl;      // phi
+    float *ph, *pl;      // phi, buffer 0
+    float *ph2, *pl2;    // phi, buffer 1: after k updates phi is in buffer k & 1
 };
+// the phi buffer after `it` updates
+__device__ __forceinline__ const float *nd_phi_h(const NDF &D, int it) { return (it & 1) ? D.ph2 : D.ph; }
+__device__ __forceinline__ const float *nd_phi_l(const NDF &D, int it) { return (it & 1) ? D.pl2 : D.pl; }
 
 struct NodalPlan {
     NGeom g;
@@ -1078,21 +1082,27 @@ __device__ __forceinline__ void ts2(float a, float b, float &s, float &e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// UPDATE: phi += scale e first (in place; nodes are updated by their own thread
-// only, and the residual pass is a separate launch).
+// phi + scale e in double-float: the update of the refinement loop
+__device__ __forceinline__ void nd_df_axpy(float ph, float pl, float ev, float sh, float sl, float &oh, float &ol) {
+    const float t = sh * ev;
+    const float te = fmaf(sh, ev, -t) + sl * ev;
+    float h, e1;
+    ts2(ph, t, h, e1);
+    const float l = pl + (te + e1);
+    ts2(h, l, oh, ol);
+}
+
+// phi (buffer it & 1) = phi (buffer (it - 1) & 1) + scale e, it = the update count
+// (the column residual's geometries; the tiled residual applies the update itself)
 __global__ void nd_df_update_kernel(NDF D, long long M, const float *__restrict__ e, const SolveState *st) {
     pdl_trigger();
     pdl_wait();
     const float sh = st->scale_h, sl = st->scale_l;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x) {
-        const float ev = e[q];
-        const float t = sh * ev;
-        const float te = fmaf(sh, ev, -t) + sl * ev;
-        float h, e1;
-        ts2(D.ph[q], t, h, e1);
-        const float l = D.pl[q] + (te + e1);
-        ts2(h, l, D.ph[q], D.pl[q]);
-    }
+    const int it = st->iter;
+    const float *__restrict__ xh = nd_phi_h(D, it - 1), *__restrict__ xl = nd_phi_l(D, it - 1);
+    float *__restrict__ yh = (it & 1) ? D.ph2 : D.ph, *__restrict__ yl = (it & 1) ? D.pl2 : D.pl;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M; q += (long long)gridDim.x * blockDim.x)
+        nd_df_axpy(xh[q], xl[q], e[q], sh, sl, yh[q], yl[q]);
 }
 
 // The first residual of a mixed solve from phi = 0: every coupling term of
@@ -1195,17 +1205,18 @@ __global__ void nd_df_col_resid_kernel(NLevel<float> L0, NDF D, const SolveState
     const float inv = st->inv_scale_f;
     const float ih2 = float(1.0 / (g.h * g.h));
     float mx = 0.f, s2 = 0.f, s1 = 0.f;
+    const float *__restrict__ xh = nd_phi_h(D, st->iter), *__restrict__ xl = nd_phi_l(D, st->iter);
     if (a < g.m[0]) {
         const ColMap m = col_map(g, a, b);
         const float wxy = ((!g.per[0] && (a == 0 || a == g.m[0] - 1)) ? 0.5f : 1.f) *
                           ((!g.per[1] && (b == 0 || b == g.m[1] - 1)) ? 0.5f : 1.f);
         float pmh[3][3], pml[3][3], p0h[3][3], p0l[3][3], pph[3][3], ppl[3][3];
         float slh[2][2], sll[2][2], shh[2][2], shl[2][2];
-        load_df_plane(g, m, D.ph, D.pl, c0 - 1, pmh, pml);
-        load_df_plane(g, m, D.ph, D.pl, c0, p0h, p0l);
+        load_df_plane(g, m, xh, xl, c0 - 1, pmh, pml);
+        load_df_plane(g, m, xh, xl, c0, p0h, p0l);
         load_df_cells(g, m, D.sh, D.sl, c0 - 1, slh, sll);
         for (int c = c0; c < c1; c++) {
-            load_df_plane(g, m, D.ph, D.pl, c + 1, pph, ppl);
+            load_df_plane(g, m, xh, xl, c + 1, pph, ppl);
             load_df_cells(g, m, D.sh, D.sl, c, shh, shl);
             const float ch = p0h[1][1], cl = p0l[1][1];
             float Sh = 0.f, Se = 0.f, kh, kl;
@@ -1278,6 +1289,7 @@ struct NdDfStage {
     float ph[DHN], pl[DHN];
     float sh[DCN], sl[DCN];
     float fh[DNT], fl[DNT];
+    float e[DHN];  // the update direction at the staged nodes (UPDATE)
 };
 
 static int nd_df_zchunk(const NGeom &g) {
@@ -1291,6 +1303,11 @@ static dim3 nd_df_tile_grid(const NGeom &g) {
     return dim3((g.m[0] + DBX - 1) / DBX, (g.m[1] + DBY - 1) / DBY, (g.m[2] + zc - 1) / zc);
 }
 
+// UPDATE: phi after it = st->iter updates is formed here from buffer (it - 1) & 1
+// and e = L0.e, node by node as nd_df_update_kernel does (the same arithmetic),
+// staged for the residual and written to buffer it & 1 at the block's own nodes;
+// without UPDATE the residual reads buffer it & 1.
+template <bool UPDATE>
 __global__ void __launch_bounds__(DNT, 2)
     nd_df_tile_resid_kernel(NLevel<float> L0, NDF D, const SolveState *st, double *part, int nzc) {
     pdl_trigger();
@@ -1326,6 +1343,16 @@ __global__ void __launch_bounds__(DNT, 2)
     }
     const bool slot1n = tid + DNT < DHN, slot1c = tid + DNT < DCN;
     const int qa = own ? a + g.m[0] * b : 0;
+    const int it = st->iter;
+    const float *__restrict__ xh = nd_phi_h(D, UPDATE ? it - 1 : it), *__restrict__ xl = nd_phi_l(D, UPDATE ? it - 1 : it);
+    float *__restrict__ yh = (it & 1) ? D.ph2 : D.ph, *__restrict__ yl = (it & 1) ? D.pl2 : D.pl;
+    const float uh = st->scale_h, ul = st->scale_l;
+    // halo slots at the block's own nodes (the updated phi is written there)
+    bool wr[2];
+    for (int k = 0; k < 2; k++) {
+        const int sl = tid + k * DNT, sx = sl % DHX - 1, sy = sl / DHX - 1;
+        wr[k] = sl < DHN && sx >= 0 && sx < DBX && sy >= 0 && sy < DBY && a0 + sx < g.m[0] && b0 + sy < g.m[1];
+    }
     // stage k: phi plane c0 + 1 + k, sigma layer c0 + k, f at plane c0 + k
     auto issue = [&](int k) {
         NdDfStage &S = sg[(k + 2) % ND_NS];
@@ -1333,11 +1360,13 @@ __global__ void __launch_bounds__(DNT, 2)
         if (c <= c1) {
             const int cz = node_wrap(g, 2, c);
             const int o = cz >= 0 ? cz * np : 0;
-            cp_async_el(&S.ph[tid], D.ph + o + no[0], 4);
-            cp_async_el(&S.pl[tid], D.pl + o + no[0], 4);
+            cp_async_el(&S.ph[tid], xh + o + no[0], 4);
+            cp_async_el(&S.pl[tid], xl + o + no[0], 4);
+            if (UPDATE) cp_async_el(&S.e[tid], L0.e + o + no[0], 4);
             if (slot1n) {
-                cp_async_el(&S.ph[tid + DNT], D.ph + o + no[1], 4);
-                cp_async_el(&S.pl[tid + DNT], D.pl + o + no[1], 4);
+                cp_async_el(&S.ph[tid + DNT], xh + o + no[1], 4);
+                cp_async_el(&S.pl[tid + DNT], xl + o + no[1], 4);
+                if (UPDATE) cp_async_el(&S.e[tid + DNT], L0.e + o + no[1], 4);
             }
         }
         if (kl >= c0 - 1 && kl <= c1 - 1) {
@@ -1356,6 +1385,26 @@ __global__ void __launch_bounds__(DNT, 2)
             cp_async_el(&S.fl[tid], D.fl + qa + kl * np, 4);
         }
         cp_async_commit();
+    };
+    // the update at this thread's halo slots of stage k (phi plane c0 + 1 + k),
+    // written out where the slot is one of the block's own nodes of [c0, c1)
+    auto update = [&](int k) {
+        NdDfStage &S = sg[(k + 2) % ND_NS];
+        const int c = c0 + 1 + k;
+        const bool wplane = c >= c0 && c < c1;
+        const long long o = (long long)c * np;
+        for (int j = 0; j < 2; j++) {
+            const int sl = tid + j * DNT;
+            if (j == 1 && !slot1n) break;
+            float h, l;
+            nd_df_axpy(S.ph[sl], S.pl[sl], S.e[sl], uh, ul, h, l);
+            S.ph[sl] = h;
+            S.pl[sl] = l;
+            if (wplane && wr[j]) {
+                yh[o + no[j]] = h;
+                yl[o + no[j]] = l;
+            }
+        }
     };
     auto get_nodes = [&](int k, float h[3][3], float l[3][3]) {
         const NdDfStage &S = sg[(k + 2) % ND_NS];
@@ -1388,6 +1437,11 @@ __global__ void __launch_bounds__(DNT, 2)
     issue(-1);
     cp_async_wait<0>();
     __syncthreads();
+    if (UPDATE) {
+        update(-2);
+        update(-1);
+        __syncthreads();
+    }
     get_nodes(-2, PH0, PL0);
     get_nodes(-1, PH1, PL1);
     get_cells(-1, SH0, SL0);
@@ -1401,6 +1455,10 @@ __global__ void __launch_bounds__(DNT, 2)
                     float ppl[3][3], float slh[2][2], float sll[2][2], float shh[2][2], float shl[2][2]) {
         cp_async_wait<2>();
         __syncthreads();
+        if (UPDATE) {
+            update(k);
+            __syncthreads();
+        }
         get_nodes(k, pph, ppl);
         get_cells(k, shh, shl);
         const int c = c0 + k;
@@ -1759,13 +1817,14 @@ __global__ void nd_rhs_final_df_kernel(NGeom g, const SolveState *st, dfloat h2x
 }
 
 // phi (double) from its double-float pair, with partials (0, sum w phi, sum w)
-__global__ void nd_df_final_sum_kernel(NGeom g, NDF D, double *__restrict__ phi, double *part) {
+__global__ void nd_df_final_sum_kernel(NGeom g, NDF D, const SolveState *st, double *__restrict__ phi, double *part) {
+    const float *__restrict__ xh = nd_phi_h(D, st->iter), *__restrict__ xl = nd_phi_l(D, st->iter);
     dfloat s1 = {0.f, 0.f};
     float s0 = 0.f;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.M; q += (long long)gridDim.x * blockDim.x) {
         int a, b, c;
         node_of(g, q, a, b, c);
-        const dfloat v = {D.ph[q], D.pl[q]};
+        const dfloat v = {xh[q], xl[q]};
         phi[q] = df_to_double(v);
         const float w = node_w(g, a, b, c);
         s1 = df_add(s1, df_scale(v, w));
@@ -1783,10 +1842,11 @@ __global__ void nd_df_final_sum_kernel(NGeom g, NDF D, double *__restrict__ phi,
 // U -= G_c phi / rho per cell from phi's double-float pair (the weighted mean
 // of phi cancels in the edge differences), in double-float
 // (also forms the cell products of the corrected U for the divergence check)
-__global__ void nd_correct_df_kernel(NGeom g, const double *__restrict__ rho, NDF D, double *__restrict__ ux,
-                                     double *__restrict__ uy, double *__restrict__ uz, dfloat i4h,
-                                     const double *__restrict__ beta0, const double *__restrict__ sbar,
+__global__ void nd_correct_df_kernel(NGeom g, const double *__restrict__ rho, NDF D, const SolveState *st,
+                                     double *__restrict__ ux, double *__restrict__ uy, double *__restrict__ uz,
+                                     dfloat i4h, const double *__restrict__ beta0, const double *__restrict__ sbar,
                                      float4 *__restrict__ P) {
+    const float *__restrict__ xh = nd_phi_h(D, st->iter), *__restrict__ xl = nd_phi_l(D, st->iter);
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     const int k0 = blockIdx.z * NRZ, k1 = min(k0 + NRZ, g.n[2]);
     if (i >= g.n[0] || j >= g.n[1]) return;
@@ -1797,10 +1857,10 @@ __global__ void nd_correct_df_kernel(NGeom g, const double *__restrict__ rho, ND
     auto face = [&](int c, dfloat p[4]) {
         const int cc = (g.per[2] && c == g.m[2]) ? 0 : c;
         const int base = m01 * cc;
-        p[0] = dfloat{D.ph[base + o00], D.pl[base + o00]};
-        p[1] = dfloat{D.ph[base + o10], D.pl[base + o10]};
-        p[2] = dfloat{D.ph[base + o01], D.pl[base + o01]};
-        p[3] = dfloat{D.ph[base + o11], D.pl[base + o11]};
+        p[0] = dfloat{xh[base + o00], xl[base + o00]};
+        p[1] = dfloat{xh[base + o10], xl[base + o10]};
+        p[2] = dfloat{xh[base + o01], xl[base + o01]};
+        p[3] = dfloat{xh[base + o11], xl[base + o11]};
     };
     dfloat lo[4], hi[4];
     face(k0, lo);
@@ -1866,6 +1926,8 @@ static void carve_nodal(Bump &b, NodalPlan &P) {
         P.D.fl = b.take<float>(P.g.M);
         P.D.ph = b.take<float>(P.g.M);
         P.D.pl = b.take<float>(P.g.M);
+        P.D.ph2 = b.take<float>(P.g.M);
+        P.D.pl2 = b.take<float>(P.g.M);
         P.cellp = b.take<float4>(2 * P.g.N);
         P.sigma64 = nullptr;
     } else {
@@ -2091,13 +2153,16 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     prof_end(c, s, MX_PH_SETUP, 0);
     const int zcap = o.tile_z ? o.tile_z : NCZ;
     // refinement loop: residual, then while not converged {V-cycle, update, residual}
-    auto residual = [&](cudaStream_t ss, mx_ctx *pc) {
+    // (upd: the tiled double-float residual also applies the loop's update)
+    const bool tiled = mixed && nd_tiled(g);
+    auto residual = [&](cudaStream_t ss, mx_ctx *pc, bool upd) {
         prof_begin(pc, ss, MX_PH_RESID64);
         int nparts = nd_col_blocks(g);
-        if (mixed && nd_tiled(g)) {
+        if (tiled) {
             const dim3 grid = nd_df_tile_grid(g);
             nparts = int(grid.x * grid.y * grid.z);
-            launch_pdl(nd_df_tile_resid_kernel, grid, dim3(DNT), sizeof(NdDfStage) * ND_NS, ss, P->L32[0], P->D,
+            auto kern = upd ? nd_df_tile_resid_kernel<true> : nd_df_tile_resid_kernel<false>;
+            launch_pdl(kern, grid, dim3(DNT), sizeof(NdDfStage) * ND_NS, ss, P->L32[0], P->D,
                        (const SolveState *)c->state, c->partials, nd_df_zchunk(g));
         } else if (mixed) {
             launch_pdl(nd_df_col_resid_kernel, nd_col_grid(g), dim3(64), 0, ss, P->L32[0], P->D,
@@ -2112,17 +2177,19 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     auto step = [&](cudaStream_t ss, mx_ctx *pc) {
         if (mixed) {
             nd_vcycle<float>(ss, P->L32, P->nlev, P->bot32, o.nu1, o.nu2, o.bottom_iters, pc, zcap, o.smoother);
-            prof_begin(pc, ss, MX_PH_UPDATE);
-            launch_pdl(nd_df_update_kernel, dim3(nb), dim3(256), 0, ss, P->D, (long long)g.M,
-                       (const float *)P->L32[0].e, (const SolveState *)c->state);
-            prof_end(pc, ss, MX_PH_UPDATE, 1);
+            if (!tiled) {
+                prof_begin(pc, ss, MX_PH_UPDATE);
+                launch_pdl(nd_df_update_kernel, dim3(nb), dim3(256), 0, ss, P->D, (long long)g.M,
+                           (const float *)P->L32[0].e, (const SolveState *)c->state);
+                prof_end(pc, ss, MX_PH_UPDATE, 1);
+            }
         } else {
             nd_vcycle<double>(ss, P->L64, P->nlev, P->bot64, o.nu1, o.nu2, o.bottom_iters, pc, zcap, o.smoother);
             prof_begin(pc, ss, MX_PH_UPDATE);
             nd_update64_kernel<<<nb, 256, 0, ss>>>(phi, P->L64[0].e, c->state, g.M);
             prof_end(pc, ss, MX_PH_UPDATE, 1);
         }
-        residual(ss, pc);
+        residual(ss, pc, tiled);
     };
     if (mixed && !o.use_initial_guess) {
         prof_begin(c, s, MX_PH_RESID64);
@@ -2130,7 +2197,7 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
         k_finalize_residual(s, c->partials, nb, c->state, 1);
         prof_end(c, s, MX_PH_RESID64, 2);
     } else {
-        residual(s, c);
+        residual(s, c, false);
     }
     MX_CUDA(c, cudaMemcpyAsync(c->hstate, c->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     MX_CUDA(c, cudaStreamSynchronize(s));
@@ -2167,15 +2234,15 @@ extern "C" mx_status mx_nodal_project(mx_ctx *c, const mx_geom *geom, double *ux
     // phi with its weighted mean removed, U -= G_c phi / rho, the divergence check
     const dim3 cgrid((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + NRZ - 1) / NRZ);
     if (mixed) {
-        nd_df_final_sum_kernel<<<nb, 256, 0, s>>>(g, P->D, phi, c->partials);
+        nd_df_final_sum_kernel<<<nb, 256, 0, s>>>(g, P->D, c->state, phi, c->partials);
     } else {
         nd_wsum_kernel<<<nb, 256, 0, s>>>(g, phi, c->partials);
     }
     nd_wmean_finalize_kernel<<<1, 1024, 0, s>>>(c->partials, nb, &c->state->aux);
     k_sub_scalar(s, g.M, phi, &c->state->aux);
     if (mixed)
-        nd_correct_df_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, P->D, ux, uy, uz, df_host(0.25 / g.h), beta0, sbar,
-                                                          P->cellp);
+        nd_correct_df_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, P->D, c->state, ux, uy, uz, df_host(0.25 / g.h),
+                                                          beta0, sbar, P->cellp);
     else nd_correct_kernel<<<cgrid, dim3(32, 8), 0, s>>>(g, rho, phi, ux, uy, uz, 0.25 / g.h);
     // divergence of the projected velocity minus Sbar_n minus c: the RHS gather with the mean subtracted
     if (mixed)
